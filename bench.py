@@ -1,0 +1,391 @@
+"""Benchmark of the plain AdpSplit training step (one view, 1M Gaussians, SH degree 3,
+1280x832): projection, binning, compositing with the dominant map, error
+statistics, top-k candidates, error regions, render backward, Adam and the
+AdpSplit operator with compaction of parameters and Adam moments.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun each rank runs an independent
+replica on its own GPU (the step has no cross-GPU exchange); the job value is the
+sum of steps over ranks divided by the slowest rank's time.
+
+The reference arm (--impl reference) times the FP64 CPU oracle on this host's
+cores on a bounded sample of the same workload (there is no released reference
+implementation of the paper to run).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd+error-stats iters/s, 1M Gaussians @1280x832"
+UNIT = "iters/s"
+WORKLOAD = dict(workload="single-view plain step: 1,000,000 Gaussians (64 clusters + 20% "
+                "background), SH degree 3, one 1280x832 camera on a radius-4 ring; target "
+                "rendered from a 1.5M-Gaussian scene; 10% candidates by error mass",
+                n_gaussians=1_000_000, width=1280, height=832, sh_degree=3, views=1,
+                cand_frac=0.10, l2="flushed between steps (256 MiB write)")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured", d
+    return 6400.0, "fallback", {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- algorithmic bytes
+
+def stage_bytes(n, n_vis, K, P, n_tiles, sh_planes, regions, k):
+    """Algorithmic DRAM bytes of each stage for one step (each input read once, each
+    output written once; see the design doc for the per-unit figures)."""
+    gbytes = 16 * (3 + sh_planes)  # one Gaussian's parameters (float4 planes)
+    return {
+        "project": n * gbytes + n * (3 * 16 + 16 + 4),
+        "bin_sort": n * 8 + n_vis * 8 * 2 * 4 + K * (8 + 2 * 16) + n_tiles * 8,
+        "render": n_tiles * 8 + K * 4 + n_vis * 48 + P * 28,
+        "error_stats": P * (12 + 12 + 4 + 4 + 4 + 1) + n * 12,
+        "select_topk": n * 8 * 8 + n * 8 * 2 + k * 4,
+        "error_regions": P * (1 + 4 + 1 + 4 + 4 + 4 + 4) + regions * 160,
+        "render_backward": (n_tiles * 8 + K * 4 + n_vis * 48 + P * (12 + 12 + 4 + 4) +
+                            n_vis * 48 * 2 + n * gbytes * 2 + n * 4),
+        "adam": n * gbytes * 7,
+        "split_plan": regions * 300 + n * 12 + k * 16,
+        "split_apply": (n + regions) * gbytes * 3 * 2,
+    }
+
+
+# --------------------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import scenes
+    from __graft_entry__ import build
+    from paper_2605_06876_b300 import ops
+    from paper_2605_06876_b300.pipeline import PlainStep, StageTimer
+
+    build()
+    torch.cuda.set_device(local_rank)
+    dev = f"cuda:{local_rank}"
+    cfg = scenes.CONFIGS[1]
+    sc = scenes.scene_clusters(2, cfg["n"], cfg["sh_degree"])
+    tg = scenes.scene_clusters(3, cfg["n_target"], cfg["sh_degree"])
+    cams = scenes.ring_cameras(3, 1, cfg["ring_radius"], cfg["width"], cfg["height"])
+    # target image: a render of the second scene (setup, outside any timing)
+    gt = ops.Gaussians.from_scene(tg, dev)
+    prt = ops.project(gt, cams)
+    bt = ops.bin_sort(gt.n, prt, cams)
+    target = ops.render(gt.n, prt, bt, cams).rgb.clone()
+    del gt, prt, bt
+    g = ops.Gaussians.from_scene(sc, dev)
+    stepper = PlainStep(g, cams, target, cfg["cand_frac"])
+    noise = torch.as_tensor(scenes.fallback_noise(5, stepper.k), device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        stepper.step(noise)
+    torch.cuda.synchronize()
+    if not stepper.check_capacity():
+        raise RuntimeError("instance or region capacity exceeded during warm-up")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    step_ms = []
+    stage_ms = {}
+    new_n = 0
+    for _ in range(args.steps):
+        flush.random_(0, 255)  # evict L2 between steps (not timed)
+        t = StageTimer(stream)
+        out = stepper.step(noise, t)
+        torch.cuda.synchronize()
+        d = t.durations()
+        for kname, val in d.items():
+            stage_ms[kname] = stage_ms.get(kname, 0.0) + val
+        step_ms.append(sum(d.values()))
+        new_n = out[3].new_n
+    barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if not stepper.check_capacity():
+        raise RuntimeError("instance or region capacity exceeded in the timed region")
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+
+    # end to end through the public API: inputs from pinned host memory each step,
+    # the split decisions read back each step
+    host = {k: v for k, v in sc.items()}
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
+              (stepper.g.mean_logit.cpu().numpy(), stepper.g.logscale.cpu().numpy(),
+               stepper.g.quat.cpu().numpy(), stepper.g.sh.cpu().numpy())]
+    tgt_h = target.cpu().pin_memory()
+    noise_h = noise.cpu().pin_memory()
+    st_h = torch.empty(stepper.k, dtype=torch.uint8).pin_memory()
+    nc_h = torch.empty(stepper.k, dtype=torch.int32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    h2d = sum(p.numel() * p.element_size() for p in pinned) + tgt_h.numel() * 4 + noise_h.numel() * 4
+    d2h = stepper.k * (1 + 4)
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        for dst, src in zip(stepper.g.tensors(), pinned):
+            dst.copy_(src.view(dst.shape), non_blocking=True)
+        target.copy_(tgt_h, non_blocking=True)
+        noise.copy_(noise_h, non_blocking=True)
+        out = stepper.step(noise)
+        st_h.copy_(out[3].status, non_blocking=True)
+        nc_h.copy_(out[3].n_children, non_blocking=True)
+        stream.synchronize()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+
+    # roofline of the dominant stage
+    n = g.n
+    n_vis = int((stepper.pr.tiles > 0).sum().item())
+    K = int(stepper.bins.n_inst.item())
+    R = int(stepper.regions.count.item())
+    sb = stage_bytes(n, n_vis, K, stepper.P, stepper.bins.ranges.shape[0], ops.sh_planes(3), R,
+                     stepper.k)
+    per_stage = {k: v / args.steps for k, v in stage_ms.items()}
+    dom = max(per_stage, key=per_stage.get)
+    peak, peak_kind, _ = _peaks()
+    achieved = sb[dom] / (per_stage[dom] * 1e-3) / 1e9
+    launches = count_launches(stepper, noise) * args.steps
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded cluster scene; random-init Gaussians, no dataset)",
+        "config": dict(WORKLOAD, parallelism=f"replicas{world}" if world > 1 else "single"),
+        "e2e": {"value": round(1e3 / e2e_ms * world, 3), "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": None, "peak_source": peak_kind},
+        "stages_ms": {k: round(v, 4) for k, v in per_stage.items()},
+        "stage_gbs": {k: round(sb[k] / (per_stage[k] * 1e-3) / 1e9, 1) for k in per_stage
+                      if k in sb and per_stage[k] > 0},
+        "workload_counts": {"visible": n_vis, "instances": K, "regions": R,
+                            "candidates": stepper.k, "new_population": new_n},
+        "clocks": clocks,
+        "gpu_launches": launches,
+    }
+    return result
+
+
+def count_launches(stepper, noise):
+    """Kernels of this library launched by one step (CUPTI trace of one extra step,
+    outside the timed region)."""
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        stepper.step(noise)
+        torch.cuda.synchronize()
+    names = [e.name for e in prof.events() if e.device_type == torch.autograd.DeviceType.CUDA]
+    return sum(1 for nm in names if "adp::" in nm or "_ZN3adp" in nm)
+
+
+# --------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(budget_s=20.0):
+    """Times the FP64 oracle, as it stands, on a bounded sample of the step and
+    scales it to one full step. Returns (seconds per full step, description, cores)."""
+    import oracle as O
+    import scenes
+
+    O.build()
+    cfg = scenes.CONFIGS[1]
+    sc = scenes.scene_clusters(2, cfg["n"], cfg["sh_degree"])
+    cam = scenes.ring_cameras(3, 1, cfg["ring_radius"], cfg["width"], cfg["height"])[0]
+    W, H = cam["width"], cam["height"]
+    th = O.theta_of(sc)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    pr = O.project(th, 3, cam)
+    t_proj = time.perf_counter() - t0
+    # compositing: a band of rows through a cropped camera (same pixels, same Gaussians)
+    rows = 16
+    band = dict(cam, height=rows, py=np.float32(float(cam["py"]) - (H // 2)))
+    t0 = time.perf_counter()
+    prb = O.project(th, 3, band)
+    rb = O.render(prb, band)
+    t_band = time.perf_counter() - t0 - t_proj  # project cost counted once
+    t_render = max(t_band, 1e-6) * (H / rows)
+    # error statistics and regions at full size on generator inputs
+    img, tgt, dom = scenes.error_stage_inputs(4, W, H, cfg["n"])
+    t0 = time.perf_counter()
+    em = O.error_map(img, tgt, 0.1, 3)
+    cnt, mass = O.gauss_stats(em["M"], dom.reshape(-1), em["E"], cfg["n"])
+    k = int(cfg["cand_frac"] * cfg["n"])
+    cand = O.topk_mass(mass, k)
+    flag = np.zeros(cfg["n"], np.uint8)
+    flag[cand] = 1
+    Me = O.erode(em["M"], W, H, 2)
+    rg = O.regions(0, W, H, Me, em["B"], dom.reshape(-1), cfg["n"], flag, tgt, 5)
+    sp = O.split(th, 3, [cam], rg, cand, cnt, np.zeros((k, 2, 3)))
+    t_err = time.perf_counter() - t0
+    # gradient: 8 visible Gaussians of median footprint, scaled by footprint area
+    # (its cost grows with the pixels of the Gaussian's box) to all visible ones
+    vis = np.nonzero(pr["tiles"] > 0)[0]
+    b = pr["box"][vis]
+    area = (b[:, 1] - b[:, 0] + 1).astype(np.float64) * (b[:, 3] - b[:, 2] + 1)
+    order = vis[np.argsort(area)]
+    mid = len(order) // 2
+    sel = np.ascontiguousarray(order[max(0, mid - 4):mid + 4], np.int32)
+    sel_area = area[np.searchsorted(vis, sel)].sum()
+    t0 = time.perf_counter()
+    O.grad(th, 3, cam, tgt, sel)
+    t_grad = (time.perf_counter() - t0) * area.sum() / max(sel_area, 1.0)
+    t0 = time.perf_counter()
+    z = np.zeros_like(th)
+    O.adam(th.copy(), z, z.copy(), z.copy(), 1)
+    t_adam = time.perf_counter() - t0
+    total = t_proj + t_render + t_err + t_grad + t_adam
+    desc = (f"oracle FP64 on {cores} threads: projection of all 1M Gaussians ({t_proj:.2f}s), "
+            f"compositing of a {rows}-row band scaled x{H / rows:.0f} ({t_band:.2f}s), full-size "
+            f"error map/top-k/regions/split on generator maps ({t_err:.2f}s), gradient of "
+            f"{len(sel)} median-footprint Gaussians scaled by box area to {len(vis)} visible "
+            f"({t_grad:.1f}s est.), Adam "
+            f"({t_adam:.2f}s)")
+    return total, desc, cores
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    per_step, desc, cores = None, None, None
+    times = []
+    for _ in range(args.warmup and 1):
+        oracle_sample()
+    for _ in range(args.steps):
+        per_step, desc, cores = oracle_sample()
+        times.append(per_step)
+    value = 1.0 / float(np.mean(times))
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(np.mean(times)) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(WORKLOAD, parallelism="cpu"), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local_rank}"))
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            per_step, desc, cores = oracle_sample()
+            res["cpu_baseline"] = {"value": 1.0 / per_step, "unit": UNIT, "cores": cores,
+                                   "kind": "oracle", "sample": desc}
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,280 @@
+/*
+ * adpsplit.h -- C ABI of the B300 (sm_103a) implementation of the AdpSplit hot
+ * path: projection, tile binning, front-to-back compositing with the dominant
+ * Gaussian map, the L1 error statistics, the AdpSplit operator with compaction of
+ * the Gaussian arrays, the hand-written render backward and Adam.
+ *
+ * Conventions shared by every call
+ *  - Pointers inside the structs and the array arguments are DEVICE pointers
+ *    owned by the caller, unless a parameter says "host". The library allocates
+ *    no device memory: scratch space comes from the caller as a workspace whose
+ *    size a *_workspace_size() query returns. float4 arrays must be 16-byte
+ *    aligned, workspaces 256-byte aligned.
+ *  - Every call is asynchronous on the given stream (a cudaStream_t; NULL is the
+ *    legacy default stream) and does not synchronise, except adp_split_plan,
+ *    which reads one integer back when asked to (see there).
+ *  - Every call returns an adp_status. A host-side argument error returns
+ *    ADP_ERR_INVALID_ARG before anything is launched; a CUDA launch error returns
+ *    ADP_ERR_CUDA. adp_last_error_string() describes the last failure of the
+ *    calling thread. No C++ exception crosses the ABI.
+ *  - Conditions only the device can see (an instance or region count beyond the
+ *    capacity the caller gave) are reported through device counters that hold
+ *    the REQUIRED size; the caller compares them with its capacity after a sync
+ *    and calls again with more room. Kernels never write past a capacity.
+ *  - Up to ADP_MAX_VIEWS views per call. Camera structs are HOST memory and are
+ *    passed to the kernels by value.
+ *
+ * Notation follows the paper (AdpSplit, Secs. 3-4 and Appendix A).
+ */
+#ifndef ADPSPLIT_H
+#define ADPSPLIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADP_API __attribute__((visibility("default")))
+#define ADP_MAX_VIEWS 32
+#define ADP_VERSION 1
+
+typedef void* adp_stream_t; /* cudaStream_t */
+
+typedef enum adp_status {
+  ADP_OK = 0,
+  ADP_ERR_INVALID_ARG = 1, /* bad sizes, NULL pointers, misalignment, small workspace */
+  ADP_ERR_CAPACITY = 2,    /* a caller-given capacity is too small (host-detected) */
+  ADP_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+  ADP_ERR_TIMEOUT = 4,     /* reserved: a bounded device wait gave up */
+  ADP_ERR_NUMERIC = 5      /* reserved: non-finite input detected */
+} adp_status;
+
+/* Split status of one candidate (Sec. 5.1). */
+enum {
+  ADP_KEEP = 0,     /* not a candidate */
+  ADP_ADAPTIVE = 1, /* N_i >= 1 children from error regions plus a parent copy */
+  ADP_FALLBACK = 2, /* no error pixel attributed in any view: vanilla split, N = 2 */
+  ADP_RESET = 3     /* pixels attributed but no region survived: kept, status reset */
+};
+
+/* OpenCV pinhole camera: x right, y down, z forward. A world point X maps to
+ * camera point R X + t (R row-major); pixel (x, y) has its centre at image
+ * coordinate (x, y); (px, py) is the principal point. Host memory. */
+typedef struct adp_camera {
+  int32_t width, height;
+  float fx, fy, px, py;
+  float R[9];
+  float t[3];
+} adp_camera;
+
+/* Hyper-parameters. adp_default_params() fills the paper's defaults (Sec. 5.1):
+ * tau_l1 0.1, r_erode 2, m_min 5, n_levels 3, n_max 19, gamma_d 2.0, gamma_c
+ * 0.15; eta 0.8 and the forward constants are the 3DGS ones the paper keeps. */
+typedef struct adp_params {
+  float tau_l1;      /* normalised L1 error threshold of the mask M (Eq. 6) */
+  int32_t r_erode;   /* erosion radius: (2r+1)^2 square window, 0 = off */
+  int32_t m_min;     /* minimum region area (Eq. 8) */
+  int32_t n_levels;  /* L error bands over [tau_l1, 1] */
+  int32_t n_max;     /* child cap per parent */
+  float gamma_d;     /* merge distance threshold (Eq. 11) */
+  float gamma_c;     /* merge colour threshold (Eq. 11) */
+  float eps_t;       /* epsilon of Eq. 10 */
+  float eta;         /* vanilla split shrink factor (Eq. 4) */
+  float scale_floor; /* lower bound on initialised child scales */
+  float near_plane;  /* cull at camera depth <= near_plane */
+  float low_pass;    /* added to the 2D covariance diagonal */
+  float alpha_min;   /* contribution threshold 1/255 */
+  float alpha_max;   /* alpha clamp 0.99 */
+  float t_min;       /* stop before blending when T (1 - alpha) < t_min */
+  int32_t tile_w;    /* tile width in pixels; tile_w * tile_h must be 256 */
+  int32_t tile_h;
+} adp_params;
+
+/* Gaussian parameters (also the layout of gradients and Adam moments), SoA of
+ * float4 planes, n entries each:
+ *   mean_logit[i] = (x, y, z, opacity logit)      opacity o = sigmoid(logit)
+ *   logscale[i]   = (log sx, log sy, log sz, 0)  scale s = exp(log s)
+ *   quat[i]       = (w, x, y, z)                 normalised before use
+ *   sh[p * n + i] = floats 4p..4p+3 of the SH list of Gaussian i, where float
+ *                   3k + ch is coefficient k of channel ch, k < K = (deg+1)^2;
+ *                   there are ceil(3K / 4) planes (1 for degree 0, 12 for 3). */
+typedef struct adp_gaussians {
+  int64_t n;
+  int32_t sh_degree; /* 0..3 */
+  int32_t reserved;
+  float* mean_logit;
+  float* logscale;
+  float* quat;
+  float* sh;
+} adp_gaussians;
+
+/* Projected Gaussians, one record per (view v, Gaussian i) at index v * n + i. */
+typedef struct adp_projected {
+  float* xy_opacity_depth; /* float4: 2D mean x, y; opacity; camera depth (opacity 0: culled) */
+  float* conic;            /* float4: A, B, C, 0 -- inverse 2D covariance [[A, B], [B, C]] */
+  float* rgb;              /* float4: r, g, b, 0 -- SH colour for this view, clamped at 0 */
+  int32_t* rect;           /* int4: tile x0, x1, y0, y1 (inclusive) of the pixel box */
+  int32_t* tiles_touched;  /* number of tiles of rect; 0 = not rendered */
+} adp_projected;
+
+/* Tile bins. Tiles are numbered view by view, row-major within a view. */
+typedef struct adp_bins {
+  int64_t capacity;      /* length of inst_gauss */
+  int32_t* inst_gauss;   /* Gaussian id per instance, ordered by (view, tile, depth, id) */
+  int32_t* tile_range;   /* [n_tiles_total][2]: [start, end) into inst_gauss */
+  int64_t* n_instances;  /* [1]: instances required (> capacity means overflow) */
+} adp_bins;
+
+/* Per-pixel render outputs; views are concatenated, each row-major. */
+typedef struct adp_image {
+  float* rgb;         /* [P][3] composited colour + T_final * background */
+  float* T_final;     /* [P] transmittance after the last blended Gaussian */
+  int32_t* n_contrib; /* [P] number of blended Gaussians */
+  int32_t* last;      /* [P] one past the tile-list position of the last blended Gaussian */
+  int32_t* dominant;  /* [P] Eq. 5: Gaussian with the largest T alpha, -1 if none */
+} adp_image;
+
+/* Error maps of Eq. 6. mask bits: 0 = M (E > tau_l1), 1 = eroded M,
+ * 4..7 = band B (0 where M = 0). */
+typedef struct adp_error_maps {
+  float* E;      /* [P] normalised L1 error (float32 decisions) */
+  uint8_t* mask; /* [P] */
+  float* minmax; /* [n_views][2] min and max of the raw L1 error per view */
+} adp_error_maps;
+
+/* Kept error regions (Eqs. 7-8) with their statistics (Sec. 4.1), ordered by
+ * (view, label). stats = (cx, cy, cov_xx, cov_xy, cov_yy, e1x, e1y, sigma1,
+ * sigma2, r, g, b): centroid, population covariance, major PCA axis with
+ * e1x > 0 (or e1y > 0 if e1x = 0), standard deviations along e1 and
+ * e2 = (-e1y, e1x), target RGB at the pixel nearest the centroid. */
+typedef struct adp_regions {
+  int64_t capacity;
+  int32_t* view;
+  int32_t* parent;   /* the dominant Gaussian of the region */
+  int32_t* label;    /* smallest linear pixel index y * W + x in the region */
+  int32_t* band;
+  int64_t* moments;  /* [cap][6]: A, sum x, sum y, sum x^2, sum xy, sum y^2 */
+  double* stats;     /* [cap][12] */
+  int64_t* count;    /* [1]: kept regions (> capacity means overflow) */
+  int32_t* labels;   /* optional [P]: label of every participating pixel, else -1 */
+} adp_regions;
+
+ADP_API int32_t adp_version(void);
+ADP_API void adp_default_params(adp_params* p);
+ADP_API const char* adp_last_error_string(void);
+
+/* --- Projection (Sec. 3, Eq. 1). ------------------------------------------
+ * EWA splatting of every Gaussian into every view: camera transform, 3D
+ * covariance R S S^T R^T, Sigma2D = J W Sigma W^T J^T + low_pass I with x/z and
+ * y/z clamped to 1.3x the half field of view in J, conic = Sigma2D^-1, opacity
+ * sigmoid(logit), SH colour along the ray from the camera centre, and the pixel
+ * box of the ellipse o exp(-d^T C d / 2) >= alpha_min. Culls depth <= near_plane,
+ * det(Sigma2D) <= 0, o < alpha_min and boxes outside the image.
+ * out: n_views * g->n records. */
+ADP_API int adp_project(const adp_gaussians* g, const adp_camera* cams, int32_t n_views,
+                        const adp_params* prm, adp_projected* out, adp_stream_t stream);
+
+/* --- Tile binning and depth sort (Eq. 1 depth order). -----------------------
+ * Sorts the visible (view, Gaussian) records by (view, depth, id), duplicates
+ * each into the tiles of its rect and sorts the instances stably by tile, so each
+ * tile's list is ordered by (depth, id); writes tile ranges. If the instance
+ * count exceeds bins->capacity nothing past the capacity is written and
+ * *bins->n_instances holds the required size. */
+ADP_API size_t adp_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t capacity);
+ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const adp_camera* cams,
+                         int32_t n_views, const adp_params* prm, adp_bins* bins, void* ws,
+                         size_t ws_bytes, adp_stream_t stream);
+
+/* --- Compositing (Eq. 1) and dominant map (Eq. 5). --------------------------
+ * Per pixel, front to back over its tile's list: alpha = min(alpha_max,
+ * o exp(power)), skipped below alpha_min, stop before blending once
+ * T (1 - alpha) < t_min. bg: host float[3] background. */
+ADP_API int adp_render(int64_t n, const adp_projected* pr, const adp_bins* bins,
+                       const adp_camera* cams, int32_t n_views, const float* bg,
+                       const adp_params* prm, adp_image* out, adp_stream_t stream);
+
+/* --- Error statistics (Eq. 6, Sec. 4.1, Sec. 5.1). --------------------------
+ * Per view: raw L1 = |I^ - I_gt|_1 over RGB, min-max normalised to E,
+ * M = [E > tau_l1], band B = min(L-1, floor(L (E - tau)/(1 - tau))); then every
+ * pixel with M = 1 and a dominant Gaussian i adds 1 to count[i] and E to
+ * mass[i] (summed over views; mass is exact: E is a float32 in (0.1, 1]).
+ * count and mass are zeroed by the call. img, target: [P][3] float32. */
+ADP_API size_t adp_error_stats_workspace_size(int32_t n_views, const adp_camera* cams);
+ADP_API int adp_error_stats(const float* img, const float* target, const int32_t* dominant,
+                            int64_t n, const adp_camera* cams, int32_t n_views,
+                            const adp_params* prm, adp_error_maps* maps, int32_t* count,
+                            double* mass, adp_stream_t stream);
+
+/* The k Gaussians with the largest mass (ties to the lower id), written to
+ * out_ids in ascending id order. */
+ADP_API size_t adp_select_topk_workspace_size(int64_t n);
+ADP_API int adp_select_topk(const double* mass, int64_t n, int64_t k, int32_t* out_ids,
+                            void* ws, size_t ws_bytes, adp_stream_t stream);
+
+/* Error regions (Eqs. 7-8): erode M by the (2 r_erode + 1)^2 square (pixels
+ * outside the image count as set), then join 8-neighbours whose eroded M is set,
+ * whose dominant Gaussian is the same split candidate and whose band is equal;
+ * keep components with area >= m_min and compute their statistics. Sets mask
+ * bit 1. candidates: device, ascending ids. */
+ADP_API size_t adp_error_regions_workspace_size(int64_t n, int32_t n_views, const adp_camera* cams);
+ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* dominant, const float* target,
+                              int64_t n, const adp_camera* cams, int32_t n_views,
+                              const int32_t* candidates, int64_t n_cand, const adp_params* prm,
+                              adp_regions* out, void* ws, size_t ws_bytes, adp_stream_t stream);
+
+/* --- The AdpSplit operator (Sec. 4, Sec. 5.1, Appendix A). ------------------
+ * Two phases sharing one workspace, which must not change in between.
+ * Plan: per candidate (device list, strictly ascending ids) its status and
+ * child count: FALLBACK if count[i] == 0, RESET if no region of i survives,
+ * else ADAPTIVE: one proposal per region (Eqs. 9-10, Appendix A), merged per
+ * parent across views (Eqs. 11-12), capped at n_max by sqrt(det Sigma) (ties to
+ * the earlier group), children in first-member (view, label) order. Computed in
+ * FP64. Writes status[n_cand], n_children[n_cand] and *d_new_n; if h_new_n is
+ * non-NULL the call copies the size back and synchronises the stream.
+ * Apply: writes the new population (out->n must equal the planned size): every
+ * non-candidate and RESET Gaussian in id order with its Adam moments, then per
+ * candidate in ascending id [parent copy with opacity o/(N_i + 1), children] or
+ * the two vanilla children mu + R (s * noise), s / (2 eta) (Eqs. 3-4), all with
+ * zero moments. noise: [n_cand][2][3] standard normal. state_in/state_out may
+ * be NULL to skip the moments. */
+ADP_API size_t adp_split_workspace_size(int64_t n, int64_t n_cand, int64_t region_capacity);
+ADP_API int adp_split_plan(const adp_gaussians* g, const adp_camera* cams, int32_t n_views,
+                           const adp_regions* regs, const int32_t* candidates, int64_t n_cand,
+                           const int32_t* count, const adp_params* prm, uint8_t* status,
+                           int32_t* n_children, int64_t* d_new_n, int64_t* h_new_n, void* ws,
+                           size_t ws_bytes, adp_stream_t stream);
+ADP_API int adp_split_apply(const adp_gaussians* g, const adp_gaussians* m_in,
+                            const adp_gaussians* v_in, const adp_regions* regs,
+                            const int32_t* candidates, int64_t n_cand, const uint8_t* status,
+                            const int32_t* n_children, const float* noise, const adp_params* prm,
+                            adp_gaussians* out, adp_gaussians* m_out, adp_gaussians* v_out,
+                            void* ws, size_t ws_bytes, adp_stream_t stream);
+
+/* --- Render backward. -------------------------------------------------------
+ * Gradient of L = sum over views of the mean L1 error |I^ - I_gt| over pixels
+ * and channels (sign(0) = 0), or, if dL_drgb is non-NULL, of the upstream
+ * gradient dL_drgb [P][3], with respect to every parameter. Per tile, back to
+ * front, transmittance recovered from T_final by division; the derivative is
+ * exact for the forward as defined (zero through the alpha clamp, the colour
+ * clamp at 0 and the clamped x/z, y/z of J). grad is zeroed and written; the
+ * per-view 2D gradients are summed over views. */
+ADP_API size_t adp_render_backward_workspace_size(int64_t n, int32_t n_views);
+ADP_API int adp_render_backward(const adp_gaussians* g, const adp_projected* pr,
+                                const adp_bins* bins, const adp_image* fwd, const float* target,
+                                const float* dL_drgb, const adp_camera* cams, int32_t n_views,
+                                const float* bg, const adp_params* prm, adp_gaussians* grad,
+                                void* ws, size_t ws_bytes, adp_stream_t stream);
+
+/* --- Adam (the baselines' optimizer, unchanged by the paper, Sec. 5.1). -----
+ * In place, bias-corrected, step >= 1. lr (host float[6]): mean, opacity
+ * logit, log-scale, quaternion, SH DC, SH rest. */
+ADP_API int adp_adam_step(adp_gaussians* param, const adp_gaussians* grad, adp_gaussians* m,
+                          adp_gaussians* v, int32_t step, const float* lr, float beta1,
+                          float beta2, float eps, adp_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADPSPLIT_H */

@@ -1,0 +1,409 @@
+// Hand-written backward of the compositing and projection.
+//
+// Pass 1 (one CTA per tile, one thread per pixel): walks the tile's list back
+// to front from each pixel's last blended Gaussian, recovering the
+// transmittance before each Gaussian as T / (1 - alpha) from T_final instead of
+// storing it, and the normalised colour behind it by the recurrence
+// R <- alpha c + (1 - alpha) R starting from the background. Per Gaussian it
+// yields dL/d(mean2d, conic, opacity, rgb); a warp reduces the 32 pixels'
+// contributions before one vector atomic per record.
+// Pass 2 (one thread per Gaussian): chains those 2D gradients through the
+// EWA projection and the SH colour of every view and sums over views, so the
+// per-Gaussian parameters are read and the gradients written once per step.
+#include "gauss_math.cuh"
+
+namespace adp {
+
+struct BwdPixArgs {
+  const float4* xyod;
+  const float4* conic;
+  const float4* rgb;
+  const int* inst;
+  const int2* ranges;
+  long long n;
+  const float* img;
+  const float* T_final;
+  const int* last;
+  const float* target;
+  const float* dL_drgb;
+  float bg[3];
+  float alpha_min, alpha_max;
+  float4* g2d;  // [V*n][3]
+};
+
+__device__ __forceinline__ void atomic_add4(float4* p, float4 v) {
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 900)
+  atomicAdd(p, v);
+#else
+  atomicAdd(&p->x, v.x);
+  atomicAdd(&p->y, v.y);
+  atomicAdd(&p->z, v.z);
+  atomicAdd(&p->w, v.w);
+#endif
+}
+
+__global__ void __launch_bounds__(256) bwd_pixel_kernel(BwdPixArgs a, CamSet cs) {
+  __shared__ float4 s_g0[256];
+  __shared__ float4 s_g1[256];
+  __shared__ float2 s_g2[256];
+  __shared__ int s_maxlast;
+  const int tile = blockIdx.x;
+  const int v = view_of_tile(cs, tile);
+  const int lt = tile - cs.tile_base[v];
+  const int txs = cs.tiles_x[v];
+  const int W = cs.cam[v].width, H = cs.cam[v].height;
+  const int px = (lt % txs) * cs.tile_w + (int)threadIdx.x % cs.tile_w;
+  const int py = (lt / txs) * cs.tile_h + (int)threadIdx.x / cs.tile_w;
+  const bool inside = px < W && py < H;
+  const float fx = (float)px, fy = (float)py;
+  const int2 range = a.ranges[tile];
+  const long long rec_base = (long long)v * a.n;
+
+  float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+  int my_last = 0;
+  if (inside) {
+    long long p = cs.pix_base[v] + (long long)py * W + px;
+    T = a.T_final[p];
+    my_last = a.last[p];
+    if (a.dL_drgb) {
+      g0 = a.dL_drgb[3 * p];
+      g1 = a.dL_drgb[3 * p + 1];
+      g2 = a.dL_drgb[3 * p + 2];
+    } else {
+      float sc = 1.f / (3.f * (float)W * (float)H);
+      float d0 = a.img[3 * p] - a.target[3 * p];
+      float d1 = a.img[3 * p + 1] - a.target[3 * p + 1];
+      float d2 = a.img[3 * p + 2] - a.target[3 * p + 2];
+      g0 = d0 > 0.f ? sc : (d0 < 0.f ? -sc : 0.f);
+      g1 = d1 > 0.f ? sc : (d1 < 0.f ? -sc : 0.f);
+      g2 = d2 > 0.f ? sc : (d2 < 0.f ? -sc : 0.f);
+    }
+  }
+  if (threadIdx.x == 0) s_maxlast = 0;
+  __syncthreads();
+  if (my_last > 0) atomicMax(&s_maxlast, my_last);
+  __syncthreads();
+  const int end = s_maxlast;
+  float R0 = a.bg[0], R1 = a.bg[1], R2 = a.bg[2];
+  for (int b1 = end; b1 > 0; b1 -= 256) {
+    int b0 = b1 - 256 > 0 ? b1 - 256 : 0;
+    int j = b0 + (int)threadIdx.x;
+    __syncthreads();
+    if (j < b1) {
+      int id = a.inst[range.x + j];
+      long long r = rec_base + id;
+      float4 p0 = a.xyod[r], p1 = a.conic[r], p2 = a.rgb[r];
+      s_g0[threadIdx.x] = make_float4(p0.x, p0.y, p1.x, p1.y);
+      s_g1[threadIdx.x] = make_float4(p1.z, p0.z, p2.x, p2.y);
+      s_g2[threadIdx.x] = make_float2(p2.z, __int_as_float(id));
+    }
+    __syncthreads();
+    for (int k = b1 - b0 - 1; k >= 0; --k) {
+      int pos = b0 + k;
+      float4 q0 = s_g0[k], q1 = s_g1[k];
+      float dmx = 0.f, dmy = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dop = 0.f, dr = 0.f, dg = 0.f,
+            db = 0.f;
+      bool hit = false;
+      if (pos < my_last) {
+        float dx, dy;
+        float ar = alpha_raw(q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, fx, fy, &dx, &dy);
+        if (ar >= a.alpha_min) {
+          hit = true;
+          float al = fminf(a.alpha_max, ar);
+          float c2 = s_g2[k].x;
+          float Tj = T / (1.f - al);
+          float dal = Tj * (g0 * (q1.z - R0) + g1 * (q1.w - R1) + g2 * (c2 - R2));
+          float wgt = Tj * al;
+          dr = wgt * g0;
+          dg = wgt * g1;
+          db = wgt * g2;
+          R0 = al * q1.z + (1.f - al) * R0;
+          R1 = al * q1.w + (1.f - al) * R1;
+          R2 = al * c2 + (1.f - al) * R2;
+          T = Tj;
+          if (ar <= a.alpha_max) {
+            float G = ar / q1.y;
+            dop = dal * G;
+            float dpow = dal * ar;
+            dA = -0.5f * dx * dx * dpow;
+            dC = -0.5f * dy * dy * dpow;
+            dB = -dx * dy * dpow;
+            dmx = -(q0.z * dx + q0.w * dy) * dpow;
+            dmy = -(q1.x * dy + q0.w * dx) * dpow;
+          }
+        }
+      }
+      unsigned any = __ballot_sync(0xffffffffu, hit);
+      if (any) {
+        dmx = warp_sum(dmx);
+        dmy = warp_sum(dmy);
+        dA = warp_sum(dA);
+        dB = warp_sum(dB);
+        dC = warp_sum(dC);
+        dop = warp_sum(dop);
+        dr = warp_sum(dr);
+        dg = warp_sum(dg);
+        db = warp_sum(db);
+        if ((threadIdx.x & 31) == 0) {
+          int id = __float_as_int(s_g2[k].y);
+          float4* g = a.g2d + 3 * (rec_base + id);
+          atomic_add4(g, make_float4(dmx, dmy, dA, dB));
+          atomic_add4(g + 1, make_float4(dC, dop, dr, dg));
+          atomicAdd(&g[2].x, db);
+        }
+      }
+    }
+  }
+}
+
+struct BwdGaussArgs {
+  const float4* mean_logit;
+  const float4* logscale;
+  const float4* quat;
+  const float* sh;
+  const int* tiles;
+  const float4* g2d;
+  long long n;
+  int deg;
+  float low_pass;
+  float4* g_ml;
+  float4* g_ls;
+  float4* g_q;
+  float* g_sh;
+};
+
+__global__ void __launch_bounds__(128) bwd_gauss_kernel(BwdGaussArgs a, CamSet cs) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const int K = sh_coeffs(a.deg);
+  const int planes = sh_planes(a.deg);
+  float4 ml = a.mean_logit[i], ls = a.logscale[i], q4 = a.quat[i];
+  float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
+  float iq = rsqrtf(qn2);
+  float qw = q4.x * iq, qx = q4.y * iq, qy = q4.z * iq, qz = q4.w * iq;
+  Mat3 Rg = rot_of_quat(qw, qx, qy, qz);
+  float s[3] = {__expf(ls.x), __expf(ls.y), __expf(ls.z)};
+  float o = 1.f / (1.f + __expf(-ml.w));
+  // Sigma3 (full)
+  float S[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      S[3 * r + c] = Rg.m[3 * r] * Rg.m[3 * c] * s[0] * s[0] + Rg.m[3 * r + 1] * Rg.m[3 * c + 1] * s[1] * s[1] +
+                     Rg.m[3 * r + 2] * Rg.m[3 * c + 2] * s[2] * s[2];
+  float gmu[3] = {0.f, 0.f, 0.f}, glogit = 0.f;
+  float G3[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma3 over views
+  float gsh[48];
+  for (int f = 0; f < 3 * K; ++f) gsh[f] = 0.f;
+  for (int v = 0; v < cs.n_views; ++v) {
+    long long rec = (long long)v * a.n + i;
+    if (a.tiles[rec] <= 0) continue;
+    float4 q0 = a.g2d[3 * rec], q1 = a.g2d[3 * rec + 1], q2 = a.g2d[3 * rec + 2];
+    float gmx = q0.x, gmy = q0.y, gA = q0.z, gB = q0.w, gC = q1.x, gop = q1.y;
+    float gcol[3] = {q1.z, q1.w, q2.x};
+    const adp_camera& cam = cs.cam[v];
+    const float* Rw = cam.R;
+    float pc[3];
+    for (int r = 0; r < 3; ++r)
+      pc[r] = Rw[3 * r] * ml.x + Rw[3 * r + 1] * ml.y + Rw[3 * r + 2] * ml.z + cam.t[r];
+    float z = pc[2], iz = 1.f / z;
+    // opacity
+    glogit += gop * o * (1.f - o);
+    // colour
+    float ccx = -(Rw[0] * cam.t[0] + Rw[3] * cam.t[1] + Rw[6] * cam.t[2]);
+    float ccy = -(Rw[1] * cam.t[0] + Rw[4] * cam.t[1] + Rw[7] * cam.t[2]);
+    float ccz = -(Rw[2] * cam.t[0] + Rw[5] * cam.t[1] + Rw[8] * cam.t[2]);
+    float d[3] = {ml.x - ccx, ml.y - ccy, ml.z - ccz};
+    float il = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    float u[3] = {d[0] * il, d[1] * il, d[2] * il};
+    float Y[16];
+    float3 dY[16];
+    sh_eval_basis(a.deg, u[0], u[1], u[2], Y);
+    float col[3] = {0.5f, 0.5f, 0.5f};
+    for (int f = 0; f < 3 * K; ++f) col[f % 3] += sh_coef(a.sh, a.n, i, f) * Y[f / 3];
+    for (int ch = 0; ch < 3; ++ch)
+      if (col[ch] < 0.f) gcol[ch] = 0.f;
+    float gu[3] = {0.f, 0.f, 0.f};
+    if (a.deg > 0) sh_eval_basis_grad(a.deg, u[0], u[1], u[2], dY);
+    for (int f = 0; f < 3 * K; ++f) {
+      float gc = gcol[f % 3];
+      gsh[f] += gc * Y[f / 3];
+      if (a.deg > 0) {
+        float cf = sh_coef(a.sh, a.n, i, f) * gc;
+        gu[0] += cf * dY[f / 3].x;
+        gu[1] += cf * dY[f / 3].y;
+        gu[2] += cf * dY[f / 3].z;
+      }
+    }
+    float ud = gu[0] * u[0] + gu[1] * u[1] + gu[2] * u[2];
+    for (int k = 0; k < 3; ++k) gmu[k] += (gu[k] - ud * u[k]) * il;
+    // EWA
+    float limx = 1.3f * (float)cam.width / (2.f * cam.fx);
+    float limy = 1.3f * (float)cam.height / (2.f * cam.fy);
+    float txz = pc[0] * iz, tyz = pc[1] * iz;
+    bool clx = txz < -limx || txz > limx, cly = tyz < -limy || tyz > limy;
+    float ux = fminf(limx, fmaxf(-limx, txz)), uy = fminf(limy, fmaxf(-limy, tyz));
+    float J00 = cam.fx * iz, J02 = -cam.fx * ux * iz, J11 = cam.fy * iz, J12 = -cam.fy * uy * iz;
+    float T0[3], T1[3];
+    for (int c = 0; c < 3; ++c) {
+      T0[c] = J00 * Rw[c] + J02 * Rw[6 + c];
+      T1[c] = J11 * Rw[3 + c] + J12 * Rw[6 + c];
+    }
+    float ST0[3], ST1[3];
+    for (int r = 0; r < 3; ++r) {
+      ST0[r] = S[3 * r] * T0[0] + S[3 * r + 1] * T0[1] + S[3 * r + 2] * T0[2];
+      ST1[r] = S[3 * r] * T1[0] + S[3 * r + 1] * T1[1] + S[3 * r + 2] * T1[2];
+    }
+    float ca = T0[0] * ST0[0] + T0[1] * ST0[1] + T0[2] * ST0[2] + a.low_pass;
+    float cb = T0[0] * ST1[0] + T0[1] * ST1[1] + T0[2] * ST1[2];
+    float cc = T1[0] * ST1[0] + T1[1] * ST1[1] + T1[2] * ST1[2] + a.low_pass;
+    float idet = 1.f / (ca * cc - cb * cb);
+    float QA = cc * idet, QB = -cb * idet, QC = ca * idet;
+    // dL/dSigma2D = -Q G_Q Q with G_Q = [[gA, gB/2], [gB/2, gC]]
+    float hB = 0.5f * gB;
+    float M00 = gA * QA + hB * QB, M01 = gA * QB + hB * QC;
+    float M10 = hB * QA + gC * QB, M11 = hB * QB + gC * QC;
+    float ga = -(QA * M00 + QB * M10);
+    float gbh = -(QA * M01 + QB * M11);  // symmetric off-diagonal entry
+    float gc2 = -(QB * M01 + QC * M11);
+    // G2 = [[ga, gbh], [gbh, gc2]]; dL/dSigma3 += T^T G2 T; dL/dT = 2 G2 T Sigma3
+    float GT0[3], GT1[3];
+    for (int c = 0; c < 3; ++c) {
+      GT0[c] = ga * T0[c] + gbh * T1[c];
+      GT1[c] = gbh * T0[c] + gc2 * T1[c];
+    }
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) G3[3 * r + c] += T0[r] * GT0[c] + T1[r] * GT1[c];
+    float dT0[3], dT1[3];
+    for (int c = 0; c < 3; ++c) {
+      dT0[c] = 2.f * (GT0[0] * S[c] + GT0[1] * S[3 + c] + GT0[2] * S[6 + c]);
+      dT1[c] = 2.f * (GT1[0] * S[c] + GT1[1] * S[3 + c] + GT1[2] * S[6 + c]);
+    }
+    // T = J W: dL/dJ = dL/dT W^T
+    float gJ00 = dT0[0] * Rw[0] + dT0[1] * Rw[1] + dT0[2] * Rw[2];
+    float gJ02 = dT0[0] * Rw[6] + dT0[1] * Rw[7] + dT0[2] * Rw[8];
+    float gJ11 = dT1[0] * Rw[3] + dT1[1] * Rw[4] + dT1[2] * Rw[5];
+    float gJ12 = dT1[0] * Rw[6] + dT1[1] * Rw[7] + dT1[2] * Rw[8];
+    float gp[3] = {0.f, 0.f, 0.f};
+    float iz2 = iz * iz;
+    gp[2] += -cam.fx * iz2 * gJ00 - cam.fy * iz2 * gJ11 + cam.fx * ux * iz2 * gJ02 +
+             cam.fy * uy * iz2 * gJ12;
+    if (!clx) {
+      gp[0] += -cam.fx * iz2 * gJ02;
+      gp[2] += cam.fx * pc[0] * iz2 * iz * gJ02;
+    }
+    if (!cly) {
+      gp[1] += -cam.fy * iz2 * gJ12;
+      gp[2] += cam.fy * pc[1] * iz2 * iz * gJ12;
+    }
+    // 2D mean
+    gp[0] += gmx * cam.fx * iz;
+    gp[1] += gmy * cam.fy * iz;
+    gp[2] += -(gmx * cam.fx * pc[0] + gmy * cam.fy * pc[1]) * iz2;
+    for (int k = 0; k < 3; ++k) gmu[k] += Rw[k] * gp[0] + Rw[3 + k] * gp[1] + Rw[6 + k] * gp[2];
+  }
+  // Sigma3 = Rg diag(s^2) Rg^T: symmetrise G3, then scales and rotation
+  float Gs[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) Gs[3 * r + c] = 0.5f * (G3[3 * r + c] + G3[3 * c + r]);
+  float GR[9];  // dL/dRg = 2 Gs Rg diag(s^2)
+  float gls[3];
+  for (int j = 0; j < 3; ++j) {
+    float acc = 0.f;
+    for (int r = 0; r < 3; ++r) {
+      float gr = 0.f;
+      for (int k = 0; k < 3; ++k) gr += Gs[3 * r + k] * Rg.m[3 * k + j];
+      GR[3 * r + j] = 2.f * gr * s[j] * s[j];
+      acc += Rg.m[3 * r + j] * gr;
+    }
+    gls[j] = 2.f * s[j] * s[j] * acc;
+  }
+  // dR/dq for the normalised quaternion
+  float gw = 2.f * (-qz * GR[1] + qy * GR[2] + qz * GR[3] - qx * GR[5] - qy * GR[6] + qx * GR[7]);
+  float gx = 2.f * (qy * GR[1] + qz * GR[2] + qy * GR[3] - 2.f * qx * GR[4] - qw * GR[5] +
+                    qz * GR[6] + qw * GR[7] - 2.f * qx * GR[8]);
+  float gy = 2.f * (-2.f * qy * GR[0] + qx * GR[1] + qw * GR[2] + qx * GR[3] + qz * GR[5] -
+                    qw * GR[6] + qz * GR[7] - 2.f * qy * GR[8]);
+  float gz = 2.f * (-2.f * qz * GR[0] - qw * GR[1] + qx * GR[2] + qw * GR[3] - 2.f * qz * GR[4] +
+                    qy * GR[5] + qx * GR[6] + qy * GR[7]);
+  float dotq = gw * qw + gx * qx + gy * qy + gz * qz;
+  a.g_ml[i] = make_float4(gmu[0], gmu[1], gmu[2], glogit);
+  a.g_ls[i] = make_float4(gls[0], gls[1], gls[2], 0.f);
+  a.g_q[i] = make_float4((gw - dotq * qw) * iq, (gx - dotq * qx) * iq, (gy - dotq * qy) * iq,
+                         (gz - dotq * qz) * iq);
+  for (int p = 0; p < planes; ++p) {
+    float v4[4];
+    for (int l = 0; l < 4; ++l) {
+      int f = 4 * p + l;
+      v4[l] = f < 3 * K ? gsh[f] : 0.f;
+    }
+    reinterpret_cast<float4*>(a.g_sh)[(long long)p * a.n + i] = make_float4(v4[0], v4[1], v4[2], v4[3]);
+  }
+}
+
+}  // namespace adp
+
+using namespace adp;
+
+extern "C" ADP_API size_t adp_render_backward_workspace_size(int64_t n, int32_t n_views) {
+  if (n < 0 || n_views < 1) return 0;
+  return carve_bytes<float4>(3 * (size_t)n * n_views);
+}
+
+extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_projected* pr,
+                                           const adp_bins* bins, const adp_image* fwd,
+                                           const float* target, const float* dL_drgb,
+                                           const adp_camera* cams, int32_t n_views,
+                                           const float* bg, const adp_params* prm,
+                                           adp_gaussians* grad, void* ws, size_t ws_bytes,
+                                           adp_stream_t stream) {
+  ADP_CHECK_ARG(g && pr && bins && fwd && grad, "NULL argument");
+  ADP_CHECK_ARG(target || dL_drgb, "one of target and dL_drgb must be given");
+  ADP_CHECK_ARG(grad->n == g->n && grad->sh_degree == g->sh_degree, "grad shape mismatch");
+  ADP_CHECK_ARG(g->sh_degree >= 0 && g->sh_degree <= 3, "sh_degree must be 0..3");
+  CamSet cs;
+  int rc = make_camset(cams, n_views, prm, &cs);
+  if (rc) return rc;
+  ADP_CHECK_ARG(g->n >= 0 && (long long)g->n * n_views < (1LL << 31), "n_views * n exceeds 2^31");
+  ADP_CHECK_ARG(aligned(ws, 256), "workspace must be 256-byte aligned");
+  size_t need = adp_render_backward_workspace_size(g->n, n_views);
+  ADP_CHECK_ARG(ws_bytes >= need, "workspace %zu bytes, need %zu", ws_bytes, need);
+  if (g->n == 0) return ADP_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  float4* g2d = static_cast<float4*>(ws);
+  ADP_CUDA(cudaMemsetAsync(g2d, 0, sizeof(float4) * 3 * (size_t)g->n * n_views, st));
+  BwdPixArgs pa;
+  pa.xyod = reinterpret_cast<const float4*>(pr->xy_opacity_depth);
+  pa.conic = reinterpret_cast<const float4*>(pr->conic);
+  pa.rgb = reinterpret_cast<const float4*>(pr->rgb);
+  pa.inst = bins->inst_gauss;
+  pa.ranges = reinterpret_cast<const int2*>(bins->tile_range);
+  pa.n = g->n;
+  pa.img = fwd->rgb;
+  pa.T_final = fwd->T_final;
+  pa.last = fwd->last;
+  pa.target = target;
+  pa.dL_drgb = dL_drgb;
+  for (int c = 0; c < 3; ++c) pa.bg[c] = bg ? bg[c] : 0.f;
+  pa.alpha_min = prm->alpha_min;
+  pa.alpha_max = prm->alpha_max;
+  pa.g2d = g2d;
+  bwd_pixel_kernel<<<cs.tile_base[n_views], 256, 0, st>>>(pa, cs);
+  ADP_LAUNCH_CHECK();
+  BwdGaussArgs ga;
+  ga.mean_logit = reinterpret_cast<const float4*>(g->mean_logit);
+  ga.logscale = reinterpret_cast<const float4*>(g->logscale);
+  ga.quat = reinterpret_cast<const float4*>(g->quat);
+  ga.sh = g->sh;
+  ga.tiles = pr->tiles_touched;
+  ga.g2d = g2d;
+  ga.n = g->n;
+  ga.deg = g->sh_degree;
+  ga.low_pass = prm->low_pass;
+  ga.g_ml = reinterpret_cast<float4*>(grad->mean_logit);
+  ga.g_ls = reinterpret_cast<float4*>(grad->logscale);
+  ga.g_q = reinterpret_cast<float4*>(grad->quat);
+  ga.g_sh = grad->sh;
+  bwd_gauss_kernel<<<grid_for(g->n, 128), 128, 0, st>>>(ga, cs);
+  ADP_LAUNCH_CHECK();
+  return ADP_OK;
+}

@@ -1,0 +1,166 @@
+// Tile binning with a depth sort (Eq. 1: Gaussians blended in depth order).
+//
+// Instead of one wide sort of (tile, depth) keys over every instance, the
+// visible (view, Gaussian) records are sorted once by (view, depth, id) -- four
+// 8-bit passes over 32-bit depth keys, plus one pass on the view -- and then
+// duplicated into their tiles in that order; a stable sort of the instances on
+// the tile index alone (2-3 passes) leaves every tile's list in (depth, id)
+// order. This moves far fewer bytes than sorting 64-bit keys over all
+// instances, and ties in depth resolve to the lower id because every pass is
+// stable over id-ordered input.
+#include "common.cuh"
+
+namespace adp {
+
+__global__ void clamp_count_kernel(const long long* K, long long cap, long long* Kc) {
+  long long k = *K;
+  *Kc = k <= cap ? k : 0;
+}
+
+__global__ void duplicate_kernel(const unsigned* vvals, const long long* offs,
+                                 const long long* d_nvis, const long long* d_K, long long cap,
+                                 const int4* rect, long long n, CamSet cs, unsigned* tkeys,
+                                 int* inst) {
+  long long N = *d_nvis;
+  if (*d_K > cap) return;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < N;
+       j += (long long)gridDim.x * blockDim.x) {
+    unsigned p = vvals[j];
+    int v = (int)(p / (unsigned long long)n);
+    int i = (int)(p - (unsigned long long)v * n);
+    int4 r = rect[p];
+    long long o = offs[j];
+    int base = cs.tile_base[v], tx = cs.tiles_x[v];
+    for (int ty = r.z; ty <= r.w; ++ty)
+      for (int tx0 = r.x; tx0 <= r.y; ++tx0) {
+        tkeys[o] = (unsigned)(base + ty * tx + tx0);
+        inst[o] = i;
+        ++o;
+      }
+  }
+}
+
+__global__ void tile_ranges_kernel(const unsigned* tkeys, const long long* d_n, int2* ranges) {
+  long long N = *d_n;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < N;
+       j += (long long)gridDim.x * blockDim.x) {
+    unsigned t = tkeys[j];
+    if (j == 0 || tkeys[j - 1] != t) ranges[t].x = (int)j;
+    if (j == N - 1 || tkeys[j + 1] != t) ranges[t].y = (int)(j + 1);
+  }
+}
+
+struct BinWs {
+  long long* counters;  // [0] visible, [1] clamped instance count
+  void* scan;
+  unsigned* vkeys;
+  unsigned* vvals;
+  long long* offs;
+  unsigned* tkeys;
+  SortWorkspace sort;
+};
+
+static size_t bin_ws_bytes(long long nv, long long cap) {
+  long long m = nv > cap ? nv : cap;
+  return carve_bytes<long long>(4) + scan_workspace_bytes(nv) + 2 * carve_bytes<unsigned>(nv) +
+         carve_bytes<long long>(nv) + carve_bytes<unsigned>(cap) + sort_workspace_bytes(m);
+}
+
+static BinWs carve_bin(Carver& c, long long nv, long long cap) {
+  BinWs w;
+  long long m = nv > cap ? nv : cap;
+  w.counters = c.take<long long>(4);
+  w.scan = c.take<char>(scan_workspace_bytes(nv));
+  w.vkeys = c.take<unsigned>(nv);
+  w.vvals = c.take<unsigned>(nv);
+  w.offs = c.take<long long>(nv);
+  w.tkeys = c.take<unsigned>(cap);
+  w.sort = carve_sort(c, m);
+  return w;
+}
+
+}  // namespace adp
+
+using namespace adp;
+
+extern "C" ADP_API size_t adp_bin_sort_workspace_size(int64_t n, int32_t n_views,
+                                                      int64_t capacity) {
+  if (n < 0 || n_views < 1 || capacity < 0) return 0;
+  return bin_ws_bytes((long long)n * n_views, capacity);
+}
+
+extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const adp_camera* cams,
+                                    int32_t n_views, const adp_params* prm, adp_bins* bins,
+                                    void* ws, size_t ws_bytes, adp_stream_t stream) {
+  ADP_CHECK_ARG(pr && bins, "NULL argument");
+  CamSet cs;
+  int rc = make_camset(cams, n_views, prm, &cs);
+  if (rc) return rc;
+  ADP_CHECK_ARG(n >= 0 && (long long)n * n_views < (1LL << 31), "n_views * n exceeds 2^31");
+  ADP_CHECK_ARG(bins->capacity >= 0 && bins->capacity < (1LL << 31), "capacity out of range");
+  ADP_CHECK_ARG(bins->tile_range && bins->n_instances && (bins->inst_gauss || bins->capacity == 0),
+                "NULL bins array");
+  ADP_CHECK_ARG(aligned(ws, 256), "workspace must be 256-byte aligned");
+  long long nv = (long long)n * n_views, cap = bins->capacity;
+  size_t need = bin_ws_bytes(nv, cap);
+  ADP_CHECK_ARG(ws_bytes >= need, "workspace %zu bytes, need %zu", ws_bytes, need);
+  cudaStream_t st = (cudaStream_t)stream;
+  long long n_tiles = cs.tile_base[n_views];
+  ADP_CUDA(cudaMemsetAsync(bins->tile_range, 0, sizeof(int2) * n_tiles, st));
+  ADP_CUDA(cudaMemsetAsync(bins->n_instances, 0, sizeof(long long), st));
+  if (nv == 0) return ADP_OK;
+  Carver c(ws, ws_bytes);
+  BinWs w = carve_bin(c, nv, cap);
+  const int* tiles = pr->tiles_touched;
+  const float4* xyod = reinterpret_cast<const float4*>(pr->xy_opacity_depth);
+
+  // 1. compact the visible records with their depth keys
+  unsigned* vkeys = w.vkeys;
+  unsigned* vvals = w.vvals;
+  rc = scan_exclusive(
+      [=] __device__(long long p) -> long long { return tiles[p] > 0 ? 1 : 0; },
+      [=] __device__(long long p, long long pre) {
+        if (tiles[p] > 0) {
+          vkeys[pre] = __float_as_uint(xyod[p].w);
+          vvals[pre] = (unsigned)p;
+        }
+      },
+      nv, nullptr, &w.counters[0], w.scan, st);
+  if (rc) return rc;
+
+  // 2. stable sort by depth, then by view
+  DigitOp passes[5];
+  int np = 0;
+  for (int s = 0; s < 32; s += 8) passes[np++] = DigitOp{s, 0u};
+  if (n_views > 1) passes[np++] = DigitOp{0, (unsigned)n};
+  rc = radix_sort_pairs(vkeys, vvals, &w.counters[0], nv, passes, np, w.sort, st);
+  if (rc) return rc;
+
+  // 3. instance offsets in sorted order; total -> n_instances
+  long long* offs = w.offs;
+  rc = scan_exclusive([=] __device__(long long j) -> long long { return tiles[vvals[j]]; },
+                      [=] __device__(long long j, long long pre) { offs[j] = pre; }, nv,
+                      &w.counters[0], (long long*)bins->n_instances, w.scan, st);
+  if (rc) return rc;
+  clamp_count_kernel<<<1, 1, 0, st>>>((const long long*)bins->n_instances, cap, &w.counters[1]);
+
+  // 4. duplicate into tiles, 5. stable sort by tile
+  if (cap > 0) {
+    duplicate_kernel<<<grid_for(nv, 256, 148 * 16), 256, 0, st>>>(
+        vvals, offs, &w.counters[0], (const long long*)bins->n_instances, cap,
+        reinterpret_cast<const int4*>(pr->rect), n, cs, w.tkeys, bins->inst_gauss);
+    ADP_LAUNCH_CHECK();
+    int bits = bits_for(n_tiles > 1 ? n_tiles - 1 : 1);
+    DigitOp tp[4];
+    int ntp = 0;
+    for (int s = 0; s < bits; s += 8) tp[ntp++] = DigitOp{s, 0u};
+    rc = radix_sort_pairs(w.tkeys, reinterpret_cast<unsigned*>(bins->inst_gauss),
+                          &w.counters[1], cap, tp, ntp, w.sort, st);
+    if (rc) return rc;
+    // 6. per-tile ranges
+    tile_ranges_kernel<<<grid_for(cap, 256, 148 * 16), 256, 0, st>>>(
+        w.tkeys, &w.counters[1], reinterpret_cast<int2*>(bins->tile_range));
+    ADP_LAUNCH_CHECK();
+  }
+  return ADP_OK;
+}

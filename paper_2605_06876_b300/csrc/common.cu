@@ -1,0 +1,275 @@
+// Error strings, defaults, camera set construction, and the non-template parts
+// of the scan and radix sort.
+#include <cstdarg>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace adp {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int make_camset(const adp_camera* cams, int n_views, const adp_params* prm, CamSet* cs) {
+  ADP_CHECK_ARG(cams != nullptr, "cams is NULL");
+  ADP_CHECK_ARG(n_views >= 1 && n_views <= ADP_MAX_VIEWS, "n_views %d outside [1, %d]", n_views,
+                ADP_MAX_VIEWS);
+  ADP_CHECK_ARG(prm != nullptr, "params is NULL");
+  ADP_CHECK_ARG(prm->tile_w > 0 && prm->tile_h > 0 && prm->tile_w * prm->tile_h == 256,
+                "tile %dx%d must have 256 pixels", prm->tile_w, prm->tile_h);
+  memset(cs, 0, sizeof(*cs));
+  cs->n_views = n_views;
+  cs->tile_w = prm->tile_w;
+  cs->tile_h = prm->tile_h;
+  cs->tile_base[0] = 0;
+  cs->pix_base[0] = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const adp_camera& c = cams[v];
+    ADP_CHECK_ARG(c.width > 0 && c.height > 0 && c.width <= 16384 && c.height <= 16384,
+                  "view %d: bad size %dx%d", v, c.width, c.height);
+    ADP_CHECK_ARG(c.fx > 0 && c.fy > 0, "view %d: focal lengths must be positive", v);
+    cs->cam[v] = c;
+    cs->tiles_x[v] = (c.width + prm->tile_w - 1) / prm->tile_w;
+    cs->tiles_y[v] = (c.height + prm->tile_h - 1) / prm->tile_h;
+    long long nt = (long long)cs->tile_base[v] + (long long)cs->tiles_x[v] * cs->tiles_y[v];
+    ADP_CHECK_ARG(nt < (1LL << 30), "too many tiles");
+    cs->tile_base[v + 1] = (int)nt;
+    cs->pix_base[v + 1] = cs->pix_base[v] + (long long)c.width * c.height;
+  }
+  return ADP_OK;
+}
+
+__global__ void fill_i32_kernel(int* p, long long n, int v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+// ----------------------------------------------------------------- scan
+
+__global__ void scan_blocksums_kernel(long long* bsum, long long nb_max, long long n,
+                                      const long long* d_n, long long* total) {
+  __shared__ long long s_warp[32];
+  __shared__ long long s_carry;
+  long long N = device_count(d_n, n);
+  long long nb = (N + SCAN_TILE - 1) / SCAN_TILE;
+  if (nb > nb_max) nb = nb_max;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (long long base = 0; base < nb; base += blockDim.x) {
+    long long i = base + threadIdx.x;
+    long long x = i < nb ? bsum[i] : 0;
+    long long inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      long long y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[w] = inc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      long long t = threadIdx.x < (blockDim.x >> 5) ? s_warp[threadIdx.x] : 0;
+      long long ti = t;
+      for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, ti, o);
+        if (lane >= o) ti += y;
+      }
+      if (threadIdx.x < (blockDim.x >> 5)) s_warp[threadIdx.x] = ti - t;
+    }
+    __syncthreads();
+    long long excl = s_carry + s_warp[w] + inc - x;
+    if (i < nb) bsum[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) s_carry = excl + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = s_carry;
+}
+
+// ----------------------------------------------------------------- radix sort
+
+__global__ void rs_hist_kernel(const unsigned* keys, const unsigned* vals, const long long* d_n,
+                               long long tiles_max, DigitOp op, unsigned* hist) {
+  __shared__ unsigned s_hist[RS_BINS];
+  long long N = *d_n;
+  long long nt = (N + RS_TILE - 1) / RS_TILE;
+  if (nt > tiles_max) nt = tiles_max;
+  for (long long t = blockIdx.x; t < nt; t += gridDim.x) {
+    s_hist[threadIdx.x] = 0;
+    __syncthreads();
+    long long base = t * RS_TILE;
+#pragma unroll 4
+    for (int k = 0; k < RS_ROUNDS; ++k) {
+      long long i = base + (long long)k * RS_THREADS + threadIdx.x;
+      if (i < N) atomicAdd(&s_hist[op(keys[i], vals[i])], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * tiles_max + t] = s_hist[threadIdx.x];
+    __syncthreads();
+  }
+}
+
+// One block per digit: exclusive scan of that digit's per-tile counts.
+__global__ void rs_scan_kernel(unsigned* hist, const long long* d_n, long long tiles_max,
+                               unsigned* digit_tot) {
+  __shared__ unsigned s_warp[RS_WARPS];
+  __shared__ unsigned s_carry;
+  long long N = *d_n;
+  long long nt = (N + RS_TILE - 1) / RS_TILE;
+  if (nt > tiles_max) nt = tiles_max;
+  unsigned* row = hist + (size_t)blockIdx.x * tiles_max;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (long long base = 0; base < nt; base += RS_THREADS) {
+    long long i = base + threadIdx.x;
+    unsigned x = i < nt ? row[i] : 0u;
+    unsigned inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[w] = inc;
+    __syncthreads();
+    unsigned wpre = 0;
+    for (int k = 0; k < w; ++k) wpre += s_warp[k];
+    unsigned excl = s_carry + wpre + inc - x;
+    if (i < nt) row[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == RS_THREADS - 1) s_carry = excl + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) digit_tot[blockIdx.x] = s_carry;
+}
+
+__global__ void __launch_bounds__(RS_THREADS)
+    rs_scatter_kernel(const unsigned* keys_in, const unsigned* vals_in, unsigned* keys_out,
+                      unsigned* vals_out, const long long* d_n, long long tiles_max, DigitOp op,
+                      const unsigned* hist, const unsigned* digit_tot) {
+  __shared__ unsigned s_base[RS_BINS];           // exclusive scan of digit totals
+  __shared__ unsigned s_whist[RS_WARPS][RS_BINS];  // per-warp counts, then warp prefixes
+  long long N = *d_n;
+  long long nt = (N + RS_TILE - 1) / RS_TILE;
+  if (nt > tiles_max) nt = tiles_max;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // exclusive scan of the 256 digit totals (once per block)
+  {
+    unsigned x = digit_tot[threadIdx.x];
+    unsigned inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    __shared__ unsigned s_w[RS_WARPS];
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    unsigned pre = 0;
+    for (int k = 0; k < warp; ++k) pre += s_w[k];
+    s_base[threadIdx.x] = pre + inc - x;
+    __syncthreads();
+  }
+  const unsigned lt = lanemask_lt();
+  for (long long t = blockIdx.x; t < nt; t += gridDim.x) {
+    for (int d = threadIdx.x; d < RS_WARPS * RS_BINS; d += RS_THREADS) (&s_whist[0][0])[d] = 0;
+    __syncthreads();
+    long long base = t * RS_TILE + (long long)warp * (RS_ROUNDS * 32);
+    unsigned key[RS_ROUNDS], val[RS_ROUNDS], dig[RS_ROUNDS], off[RS_ROUNDS];
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+      long long i = base + r * 32 + lane;
+      bool valid = i < N;
+      key[r] = valid ? keys_in[i] : 0u;
+      val[r] = valid ? vals_in[i] : 0u;
+      unsigned d = valid ? op(key[r], val[r]) : (unsigned)RS_BINS;
+      dig[r] = d;
+      unsigned peers = __match_any_sync(0xffffffffu, d);
+      unsigned before = valid ? s_whist[warp][d] : 0u;
+      off[r] = before + __popc(peers & lt);
+      __syncwarp();
+      if (valid && (peers & lt) == 0) s_whist[warp][d] = before + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    {  // per-digit exclusive prefix over warps
+      int d = threadIdx.x;
+      unsigned run = 0;
+      for (int w2 = 0; w2 < RS_WARPS; ++w2) {
+        unsigned c = s_whist[w2][d];
+        s_whist[w2][d] = run;
+        run += c;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+      long long i = base + r * 32 + lane;
+      if (i < N) {
+        unsigned d = dig[r];
+        unsigned pos = s_base[d] + hist[(size_t)d * tiles_max + t] + s_whist[warp][d] + off[r];
+        keys_out[pos] = key[r];
+        vals_out[pos] = val[r];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+int radix_sort_pairs(unsigned* keys, unsigned* vals, const long long* d_n, long long n_max,
+                     const DigitOp* passes, int n_passes, const SortWorkspace& w,
+                     cudaStream_t st) {
+  if (n_max <= 0 || n_passes <= 0) return ADP_OK;
+  unsigned *ka = keys, *va = vals, *kb = w.keys_alt, *vb = w.vals_alt;
+  long long grid = w.tiles_max < 148 * 8 ? w.tiles_max : 148 * 8;
+  for (int p = 0; p < n_passes; ++p) {
+    rs_hist_kernel<<<(unsigned)grid, RS_THREADS, 0, st>>>(ka, va, d_n, w.tiles_max, passes[p],
+                                                           w.hist);
+    rs_scan_kernel<<<RS_BINS, RS_THREADS, 0, st>>>(w.hist, d_n, w.tiles_max, w.digit_tot);
+    rs_scatter_kernel<<<(unsigned)grid, RS_THREADS, 0, st>>>(ka, va, kb, vb, d_n, w.tiles_max,
+                                                              passes[p], w.hist, w.digit_tot);
+    ADP_LAUNCH_CHECK();
+    unsigned* tk = ka; ka = kb; kb = tk;
+    unsigned* tv = va; va = vb; vb = tv;
+  }
+  if (ka != keys) {  // odd pass count: results live in the alternate buffers
+    ADP_CUDA(cudaMemcpyAsync(keys, ka, sizeof(unsigned) * n_max, cudaMemcpyDeviceToDevice, st));
+    ADP_CUDA(cudaMemcpyAsync(vals, va, sizeof(unsigned) * n_max, cudaMemcpyDeviceToDevice, st));
+  }
+  return ADP_OK;
+}
+
+}  // namespace adp
+
+extern "C" {
+
+ADP_API int32_t adp_version(void) { return ADP_VERSION; }
+
+ADP_API const char* adp_last_error_string(void) { return adp::g_err; }
+
+ADP_API void adp_default_params(adp_params* p) {
+  if (!p) return;
+  p->tau_l1 = 0.1f;
+  p->r_erode = 2;
+  p->m_min = 5;
+  p->n_levels = 3;
+  p->n_max = 19;
+  p->gamma_d = 2.0f;
+  p->gamma_c = 0.15f;
+  p->eps_t = 1e-8f;
+  p->eta = 0.8f;
+  p->scale_floor = 1e-7f;
+  p->near_plane = 0.2f;
+  p->low_pass = 0.3f;
+  p->alpha_min = 1.0f / 255.0f;
+  p->alpha_max = 0.99f;
+  p->t_min = 1e-4f;
+  p->tile_w = 16;
+  p->tile_h = 16;
+}
+
+}  // extern "C"

@@ -1,0 +1,645 @@
+// Error statistics of AdpSplit (Eq. 6, Eqs. 7-8, Secs. 4.1 and 5.1):
+//  - per view, the raw L1 error and its min/max (block reduction + atomics),
+//    then the min-max normalised E, mask M and band B, decided in float32 with
+//    correctly rounded operations, and the per-Gaussian attribution (count,
+//    mass) with warp-aggregated atomics;
+//  - top-k error mass by an 8-pass radix select on the 64-bit mass keys;
+//  - erosion (separable min filter), 8-connected labelling by a lock-free
+//    union-find whose roots are the smallest pixel index of each component,
+//    exact int64 region moments, the area filter and the FP64 region statistics.
+#include "common.cuh"
+
+namespace adp {
+
+// ------------------------------------------------------------------ error map
+
+__global__ void err_raw_kernel(const float* img, const float* tgt, CamSet cs, float* raw,
+                               unsigned* minmax_bits) {
+  const int v = blockIdx.y;
+  const long long P = (long long)cs.cam[v].width * cs.cam[v].height;
+  const long long base = cs.pix_base[v];
+  unsigned lo = 0x7f800000u, hi = 0u;  // +inf, 0 as float bits (raw >= 0)
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < P;
+       u += (long long)gridDim.x * blockDim.x) {
+    long long p = base + u;
+    float d0 = fabsf(__fsub_rn(img[3 * p], tgt[3 * p]));
+    float d1 = fabsf(__fsub_rn(img[3 * p + 1], tgt[3 * p + 1]));
+    float d2 = fabsf(__fsub_rn(img[3 * p + 2], tgt[3 * p + 2]));
+    float r = __fadd_rn(__fadd_rn(d0, d1), d2);
+    raw[p] = r;
+    unsigned b = __float_as_uint(r);
+    lo = min(lo, b);
+    hi = max(hi, b);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&minmax_bits[2 * v], lo);
+    atomicMax(&minmax_bits[2 * v + 1], hi);
+  }
+}
+
+__global__ void err_init_minmax_kernel(unsigned* mm, int n_views) {
+  int v = threadIdx.x;
+  if (v < n_views) {
+    mm[2 * v] = 0x7f800000u;
+    mm[2 * v + 1] = 0u;
+  }
+}
+
+// E, M, B and the per-Gaussian attribution of pre-erosion error pixels.
+__global__ void err_norm_kernel(float* E, uint8_t* mask, const unsigned* minmax_bits,
+                                const int* dominant, long long n, CamSet cs, float tau, int L,
+                                int* count, double* mass) {
+  __shared__ float s_val[8][32];
+  const int v = blockIdx.y;
+  const long long P = (long long)cs.cam[v].width * cs.cam[v].height;
+  const long long base = cs.pix_base[v];
+  const float mn = __uint_as_float(minmax_bits[2 * v]);
+  const float mx = __uint_as_float(minmax_bits[2 * v + 1]);
+  const float range = __fsub_rn(mx, mn);
+  const float one_minus_tau = __fsub_rn(1.0f, tau);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // whole warps iterate together so the match below sees every lane
+  for (long long u0 = blockIdx.x * (long long)blockDim.x; u0 < P;
+       u0 += (long long)gridDim.x * blockDim.x) {
+    long long u = u0 + threadIdx.x;
+    int key = -1;
+    float e = 0.f;
+    if (u < P) {
+      long long p = base + u;
+      e = range > 0.f ? __fdiv_rn(__fsub_rn(E[p], mn), range) : 0.f;
+      E[p] = e;
+      bool m = e > tau;
+      int b = 0;
+      if (m) {
+        float t = __fdiv_rn(__fmul_rn(__fsub_rn(e, tau), (float)L), one_minus_tau);
+        b = (int)floorf(t);
+        b = b > L - 1 ? L - 1 : (b < 0 ? 0 : b);
+      }
+      mask[p] = (uint8_t)((m ? 1 : 0) | (b << 4));
+      int d = dominant[p];
+      if (m && d >= 0 && d < n) key = d;
+    }
+    unsigned peers = __match_any_sync(0xffffffffu, key);
+    s_val[warp][lane] = e;
+    __syncwarp();
+    if (key >= 0 && (peers & lanemask_lt()) == 0) {
+      double s = 0.0;
+      for (unsigned m = peers; m; m &= m - 1) s += (double)s_val[warp][__ffs(m) - 1];
+      atomicAdd(&count[key], __popc(peers));
+      atomicAdd(&mass[key], s);
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------ top-k
+
+struct SelectState {
+  unsigned long long prefix;  // selected high digits of the threshold key
+  unsigned long long mask;    // which bits of prefix are fixed
+  long long remaining;        // how many of the keys matching prefix to take
+  long long pad;
+};
+
+__global__ void topk_hist_kernel(const double* mass, long long n, int shift,
+                                 const SelectState* st, unsigned* hist) {
+  __shared__ unsigned s_h[256];
+  s_h[threadIdx.x] = 0;
+  __syncthreads();
+  unsigned long long pre = st->prefix, msk = st->mask;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long k = (unsigned long long)__double_as_longlong(mass[i]);
+    if ((k & msk) == pre) atomicAdd(&s_h[(k >> shift) & 255ull], 1u);
+  }
+  __syncthreads();
+  if (s_h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], s_h[threadIdx.x]);
+}
+
+// Picks the digit (scanning from the largest) holding the remaining-th largest key.
+__global__ void topk_pick_kernel(unsigned* hist, int shift, SelectState* st) {
+  if (threadIdx.x != 0) return;
+  long long rem = st->remaining, cum = 0;
+  int b = 255;
+  for (; b > 0; --b) {
+    if (cum + hist[b] >= rem) break;
+    cum += hist[b];
+  }
+  st->remaining = rem - cum;
+  st->prefix |= (unsigned long long)b << shift;
+  st->mask |= 255ull << shift;
+  for (int k = 0; k < 256; ++k) hist[k] = 0;
+}
+
+// ------------------------------------------------------------------ erosion
+
+// Horizontal then vertical AND over radius r; outside the image counts as set.
+__global__ void erode_h_kernel(const uint8_t* mask, uint8_t* tmp, CamSet cs, int r) {
+  const int v = blockIdx.y;
+  const int W = cs.cam[v].width, H = cs.cam[v].height;
+  const long long P = (long long)W * H, base = cs.pix_base[v];
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < P;
+       u += (long long)gridDim.x * blockDim.x) {
+    int x = (int)(u % W);
+    const uint8_t* row = mask + base + (u - x);
+    uint8_t ok = 1;
+    for (int d = -r; d <= r && ok; ++d) {
+      int xx = x + d;
+      if (xx >= 0 && xx < W) ok = row[xx] & 1;
+    }
+    tmp[base + u] = ok;
+  }
+}
+
+__global__ void erode_v_kernel(const uint8_t* tmp, uint8_t* mask, CamSet cs, int r) {
+  const int v = blockIdx.y;
+  const int W = cs.cam[v].width, H = cs.cam[v].height;
+  const long long P = (long long)W * H, base = cs.pix_base[v];
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < P;
+       u += (long long)gridDim.x * blockDim.x) {
+    int x = (int)(u % W), y = (int)(u / W);
+    uint8_t ok = 1;
+    for (int d = -r; d <= r && ok; ++d) {
+      int yy = y + d;
+      if (yy >= 0 && yy < H) ok = tmp[base + (long long)yy * W + x];
+    }
+    uint8_t m = mask[base + u];
+    mask[base + u] = (uint8_t)((m & ~2) | (ok ? 2 : 0));
+  }
+}
+
+// ------------------------------------------------------------------ labelling
+
+__device__ __forceinline__ int uf_find(volatile int* L, int a) {
+  int b = L[a];
+  while (b != a) {
+    a = b;
+    b = L[a];
+  }
+  return a;
+}
+
+// Joins the sets of a and b; every link points to a smaller index, so each
+// component ends rooted at its smallest pixel index.
+__device__ void uf_unite(int* L, int a, int b) {
+  volatile int* VL = L;
+  for (int guard = 0; guard < (1 << 24); ++guard) {
+    a = uf_find(VL, a);
+    b = uf_find(VL, b);
+    if (a == b) return;
+    if (a > b) {
+      int t = a;
+      a = b;
+      b = t;
+    }
+    int old = atomicMin(&L[b], a);
+    if (old == b) return;
+    b = old;
+  }
+}
+
+__device__ __forceinline__ bool region_pixel(const uint8_t* mask, const int* dom,
+                                             const uint8_t* cand, long long n, long long p) {
+  int d = dom[p];
+  return (mask[p] & 2) && d >= 0 && d < n && cand[d];
+}
+
+__global__ void ccl_init_kernel(const uint8_t* mask, const int* dom, const uint8_t* cand,
+                                long long n, long long P, int* L) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
+       p += (long long)gridDim.x * blockDim.x)
+    L[p] = region_pixel(mask, dom, cand, n, p) ? (int)p : -1;
+}
+
+__global__ void ccl_union_kernel(const uint8_t* mask, const int* dom, CamSet cs, int* L) {
+  const int v = blockIdx.y;
+  const int W = cs.cam[v].width, H = cs.cam[v].height;
+  const long long P = (long long)W * H, base = cs.pix_base[v];
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < P;
+       u += (long long)gridDim.x * blockDim.x) {
+    long long p = base + u;
+    if (L[p] < 0) continue;
+    int x = (int)(u % W), y = (int)(u / W);
+    int d = dom[p];
+    uint8_t b = mask[p] >> 4;
+    const int nx[4] = {-1, -1, 0, 1}, ny[4] = {0, -1, -1, -1};
+    for (int k = 0; k < 4; ++k) {
+      int xx = x + nx[k], yy = y + ny[k];
+      if (xx < 0 || xx >= W || yy < 0) continue;
+      long long q = base + (long long)yy * W + xx;
+      if (L[q] < 0 || dom[q] != d || (mask[q] >> 4) != b) continue;
+      uf_unite(L, (int)p, (int)q);
+    }
+  }
+}
+
+__global__ void ccl_flatten_kernel(int* L, long long P) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
+       p += (long long)gridDim.x * blockDim.x) {
+    if (L[p] >= 0) L[p] = uf_find(L, (int)p);
+  }
+}
+
+__global__ void zero_i64_kernel(long long* p, const long long* d_n, int per) {
+  long long N = *d_n * per;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] = 0;
+}
+
+// Exact int64 moments per root, warp-aggregated over pixels sharing a root.
+__global__ void moments_kernel(const int* L, const int* slot, CamSet cs, long long* mom) {
+  __shared__ long long s_xy[8][32][2];
+  const int v = blockIdx.y;
+  const int W = cs.cam[v].width, H = cs.cam[v].height;
+  const long long P = (long long)W * H, base = cs.pix_base[v];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (long long u0 = blockIdx.x * (long long)blockDim.x; u0 < P;
+       u0 += (long long)gridDim.x * blockDim.x) {
+    long long u = u0 + threadIdx.x;
+    int s = -1;
+    long long x = 0, y = 0;
+    if (u < P) {
+      int r = L[base + u];
+      if (r >= 0) {
+        s = slot[r];
+        x = u % W;
+        y = u / W;
+      }
+    }
+    unsigned peers = __match_any_sync(0xffffffffu, s);
+    s_xy[warp][lane][0] = x;
+    s_xy[warp][lane][1] = y;
+    __syncwarp();
+    if (s >= 0 && (peers & lanemask_lt()) == 0) {
+      long long a = 0, sx = 0, sy = 0, sxx = 0, sxy = 0, syy = 0;
+      for (unsigned m = peers; m; m &= m - 1) {
+        int l = __ffs(m) - 1;
+        long long xx = s_xy[warp][l][0], yy = s_xy[warp][l][1];
+        a += 1;
+        sx += xx;
+        sy += yy;
+        sxx += xx * xx;
+        sxy += xx * yy;
+        syy += yy * yy;
+      }
+      unsigned long long* m6 = reinterpret_cast<unsigned long long*>(mom + 6LL * s);
+      atomicAdd(m6 + 0, (unsigned long long)a);
+      atomicAdd(m6 + 1, (unsigned long long)sx);
+      atomicAdd(m6 + 2, (unsigned long long)sy);
+      atomicAdd(m6 + 3, (unsigned long long)sxx);
+      atomicAdd(m6 + 4, (unsigned long long)sxy);
+      atomicAdd(m6 + 5, (unsigned long long)syy);
+    }
+    __syncwarp();
+  }
+}
+
+__device__ __forceinline__ double cov_exact(long long A, long long Sab, long long Sa, long long Sb) {
+  __int128 num = (__int128)A * Sab - (__int128)Sa * Sb;
+  return (double)num / ((double)A * (double)A);
+}
+
+struct RegionArgs {
+  const long long* mom;
+  const int* root_pix;
+  const long long* kept_idx;
+  const long long* d_nroots;
+  const int* dom;
+  const uint8_t* mask;
+  const float* tgt;
+  int m_min;
+  long long cap;
+  int* view;
+  int* parent;
+  int* label;
+  int* band;
+  long long* moments;
+  double* stats;
+};
+
+__global__ void region_stats_kernel(RegionArgs a, CamSet cs) {
+  long long N = *a.d_nroots;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N;
+       r += (long long)gridDim.x * blockDim.x) {
+    const long long* m = a.mom + 6 * r;
+    long long A = m[0];
+    if (A < a.m_min) continue;
+    long long k = a.kept_idx[r];
+    if (k >= a.cap) continue;
+    long long g = a.root_pix[r];
+    int v = 0;
+    while (v + 1 < cs.n_views && g >= cs.pix_base[v + 1]) ++v;
+    int W = cs.cam[v].width, H = cs.cam[v].height;
+    double cx = (double)m[1] / (double)A, cy = (double)m[2] / (double)A;
+    double cxx = cov_exact(A, m[3], m[1], m[1]);
+    double cxy = cov_exact(A, m[4], m[1], m[2]);
+    double cyy = cov_exact(A, m[5], m[2], m[2]);
+    // closed-form eigen-decomposition of the 2x2 covariance
+    double mid = 0.5 * (cxx + cyy), dd = 0.5 * (cxx - cyy);
+    double rad = sqrt(dd * dd + cxy * cxy);
+    double l1 = mid + rad, l2 = mid - rad;
+    double ex = 1.0, ey = 0.0;
+    if (rad > 0.0) {
+      if (dd >= 0.0) {
+        ex = dd + rad;
+        ey = cxy;
+      } else {
+        ex = cxy;
+        ey = rad - dd;
+      }
+      double nrm = sqrt(ex * ex + ey * ey);
+      ex /= nrm;
+      ey /= nrm;
+      if (ex < 0.0 || (ex == 0.0 && ey < 0.0)) {
+        ex = -ex;
+        ey = -ey;
+      }
+    }
+    int xi = (int)floor(cx + 0.5), yi = (int)floor(cy + 0.5);
+    xi = xi < 0 ? 0 : (xi > W - 1 ? W - 1 : xi);
+    yi = yi < 0 ? 0 : (yi > H - 1 ? H - 1 : yi);
+    const float* rgb = a.tgt + 3 * (cs.pix_base[v] + (long long)yi * W + xi);
+    double* s = a.stats + 12 * k;
+    s[0] = cx;
+    s[1] = cy;
+    s[2] = cxx;
+    s[3] = cxy;
+    s[4] = cyy;
+    s[5] = ex;
+    s[6] = ey;
+    s[7] = sqrt(l1 > 0.0 ? l1 : 0.0);
+    s[8] = sqrt(l2 > 0.0 ? l2 : 0.0);
+    s[9] = rgb[0];
+    s[10] = rgb[1];
+    s[11] = rgb[2];
+    a.view[k] = v;
+    a.parent[k] = a.dom[g];
+    a.label[k] = (int)(g - cs.pix_base[v]);
+    a.band[k] = a.mask[g] >> 4;
+    for (int j = 0; j < 6; ++j) a.moments[6 * k + j] = m[j];
+  }
+}
+
+__global__ void labels_out_kernel(const int* L, const long long* mom, const int* slot, int m_min,
+                                  CamSet cs, int* labels) {
+  const int v = blockIdx.y;
+  const long long P = (long long)cs.cam[v].width * cs.cam[v].height, base = cs.pix_base[v];
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < P;
+       u += (long long)gridDim.x * blockDim.x) {
+    int r = L[base + u];
+    labels[base + u] = r >= 0 ? (int)(r - base) : -1;
+  }
+}
+
+__global__ void scatter_flag_kernel(const int* ids, long long k, long long n, uint8_t* flag) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < k;
+       i += (long long)gridDim.x * blockDim.x) {
+    int id = ids[i];
+    if (id >= 0 && id < n) flag[id] = 1;
+  }
+}
+
+__global__ void iota_kernel(int* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (int)i;
+}
+
+static long long total_pixels(const CamSet& cs) { return cs.pix_base[cs.n_views]; }
+static unsigned view_grid(const CamSet& cs) {
+  long long mx = 0;
+  for (int v = 0; v < cs.n_views; ++v) {
+    long long P = (long long)cs.cam[v].width * cs.cam[v].height;
+    if (P > mx) mx = P;
+  }
+  long long g = (mx + 255) / 256;
+  return (unsigned)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
+}
+
+}  // namespace adp
+
+using namespace adp;
+
+// ------------------------------------------------------------------ error stats
+
+extern "C" ADP_API size_t adp_error_stats_workspace_size(int32_t n_views, const adp_camera* cams) {
+  (void)n_views;
+  (void)cams;
+  return 0;
+}
+
+extern "C" ADP_API int adp_error_stats(const float* img, const float* target,
+                                       const int32_t* dominant, int64_t n,
+                                       const adp_camera* cams, int32_t n_views,
+                                       const adp_params* prm, adp_error_maps* maps,
+                                       int32_t* count, double* mass, adp_stream_t stream) {
+  ADP_CHECK_ARG(img && target && dominant && maps && maps->E && maps->mask && maps->minmax,
+                "NULL argument");
+  ADP_CHECK_ARG(n >= 0 && n < (1LL << 31), "n out of range");
+  ADP_CHECK_ARG(n == 0 || (count && mass), "NULL count/mass");
+  CamSet cs;
+  int rc = make_camset(cams, n_views, prm, &cs);
+  if (rc) return rc;
+  ADP_CHECK_ARG(prm->n_levels >= 1 && prm->n_levels <= 15, "n_levels must be 1..15");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n > 0) {
+    ADP_CUDA(cudaMemsetAsync(count, 0, sizeof(int) * n, st));
+    ADP_CUDA(cudaMemsetAsync(mass, 0, sizeof(double) * n, st));
+  }
+  unsigned* mm = reinterpret_cast<unsigned*>(maps->minmax);
+  err_init_minmax_kernel<<<1, 32, 0, st>>>(mm, n_views);
+  dim3 grid(view_grid(cs), n_views);
+  err_raw_kernel<<<grid, 256, 0, st>>>(img, target, cs, maps->E, mm);
+  err_norm_kernel<<<grid, 256, 0, st>>>(maps->E, maps->mask, mm, dominant, n, cs, prm->tau_l1,
+                                        prm->n_levels, count, mass);
+  ADP_LAUNCH_CHECK();
+  return ADP_OK;
+}
+
+// ------------------------------------------------------------------ top-k
+
+extern "C" ADP_API size_t adp_select_topk_workspace_size(int64_t n) {
+  if (n < 0) return 0;
+  return carve_bytes<SelectState>(1) + carve_bytes<unsigned>(256) + carve_bytes<uint8_t>(n) +
+         scan_workspace_bytes(n) + carve_bytes<long long>(2);
+}
+
+extern "C" ADP_API int adp_select_topk(const double* mass, int64_t n, int64_t k, int32_t* out_ids,
+                                       void* ws, size_t ws_bytes, adp_stream_t stream) {
+  ADP_CHECK_ARG(n >= 0 && n < (1LL << 31) && k >= 0, "bad n or k");
+  ADP_CHECK_ARG(k == 0 || (mass && out_ids), "NULL argument");
+  ADP_CHECK_ARG(aligned(ws, 256), "workspace must be 256-byte aligned");
+  size_t need = adp_select_topk_workspace_size(n);
+  ADP_CHECK_ARG(ws_bytes >= need, "workspace %zu bytes, need %zu", ws_bytes, need);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (k > n) k = n;
+  if (k == 0) return ADP_OK;
+  if (k == n) {
+    iota_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(out_ids, n);
+    ADP_LAUNCH_CHECK();
+    return ADP_OK;
+  }
+  Carver c(ws, ws_bytes);
+  SelectState* ss = c.take<SelectState>(1);
+  unsigned* hist = c.take<unsigned>(256);
+  uint8_t* sel = c.take<uint8_t>(n);
+  void* sw = c.take<char>(scan_workspace_bytes(n));
+  long long* cnt = c.take<long long>(2);
+  SelectState init = {0ull, 0ull, (long long)k, 0};
+  ADP_CUDA(cudaMemcpyAsync(ss, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+  ADP_CUDA(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned), st));
+  unsigned g = grid_for(n, 256, 148 * 8);
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    topk_hist_kernel<<<g, 256, 0, st>>>(mass, n, shift, ss, hist);
+    topk_pick_kernel<<<1, 32, 0, st>>>(hist, shift, ss);
+  }
+  ADP_LAUNCH_CHECK();
+  // keys above the threshold, plus the first `remaining` equal ones by id
+  const SelectState* css = ss;
+  int rc = scan_exclusive(
+      [=] __device__(long long i) -> long long {
+        return (unsigned long long)__double_as_longlong(mass[i]) == css->prefix ? 1 : 0;
+      },
+      [=] __device__(long long i, long long pre) {
+        unsigned long long key = (unsigned long long)__double_as_longlong(mass[i]);
+        sel[i] = key > css->prefix || (key == css->prefix && pre < css->remaining);
+      },
+      n, nullptr, &cnt[0], sw, st);
+  if (rc) return rc;
+  return scan_exclusive([=] __device__(long long i) -> long long { return sel[i]; },
+                        [=] __device__(long long i, long long pre) {
+                          if (sel[i]) out_ids[pre] = (int)i;
+                        },
+                        n, nullptr, &cnt[1], sw, st);
+}
+
+// ------------------------------------------------------------------ regions
+
+struct RegionWs {
+  int* L;
+  int* slot;
+  int* root_pix;
+  long long* mom;
+  long long* kept_idx;
+  uint8_t* cand;
+  uint8_t* tmp;
+  void* scan;
+  long long* counters;
+};
+
+static size_t region_ws_bytes(long long n, long long P) {
+  return 3 * carve_bytes<int>(P) + carve_bytes<long long>(6 * P) + carve_bytes<long long>(P) +
+         carve_bytes<uint8_t>(n) + carve_bytes<uint8_t>(P) + scan_workspace_bytes(P) +
+         carve_bytes<long long>(4);
+}
+
+extern "C" ADP_API size_t adp_error_regions_workspace_size(int64_t n, int32_t n_views,
+                                                           const adp_camera* cams) {
+  if (!cams || n_views < 1 || n_views > ADP_MAX_VIEWS || n < 0) return 0;
+  long long P = 0;
+  for (int v = 0; v < n_views; ++v) P += (long long)cams[v].width * cams[v].height;
+  return region_ws_bytes(n, P);
+}
+
+extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* dominant,
+                                         const float* target, int64_t n, const adp_camera* cams,
+                                         int32_t n_views, const int32_t* candidates,
+                                         int64_t n_cand, const adp_params* prm,
+                                         adp_regions* out, void* ws, size_t ws_bytes,
+                                         adp_stream_t stream) {
+  ADP_CHECK_ARG(maps && maps->mask && dominant && target && out && out->count, "NULL argument");
+  ADP_CHECK_ARG(n >= 0 && n < (1LL << 31) && n_cand >= 0 && n_cand <= n, "bad n or n_cand");
+  ADP_CHECK_ARG(n_cand == 0 || candidates, "NULL candidates");
+  ADP_CHECK_ARG(out->capacity >= 0, "negative capacity");
+  ADP_CHECK_ARG(out->capacity == 0 || (out->view && out->parent && out->label && out->band &&
+                                       out->moments && out->stats),
+                "NULL region array");
+  CamSet cs;
+  int rc = make_camset(cams, n_views, prm, &cs);
+  if (rc) return rc;
+  ADP_CHECK_ARG(prm->r_erode >= 0 && prm->r_erode <= 64, "r_erode must be 0..64");
+  long long P = total_pixels(cs);
+  ADP_CHECK_ARG(P < (1LL << 31), "too many pixels");
+  ADP_CHECK_ARG(aligned(ws, 256), "workspace must be 256-byte aligned");
+  size_t need = region_ws_bytes(n, P);
+  ADP_CHECK_ARG(ws_bytes >= need, "workspace %zu bytes, need %zu", ws_bytes, need);
+  cudaStream_t st = (cudaStream_t)stream;
+  Carver c(ws, ws_bytes);
+  RegionWs w;
+  w.L = c.take<int>(P);
+  w.slot = c.take<int>(P);
+  w.root_pix = c.take<int>(P);
+  w.mom = c.take<long long>(6 * P);
+  w.kept_idx = c.take<long long>(P);
+  w.cand = c.take<uint8_t>(n);
+  w.tmp = c.take<uint8_t>(P);
+  w.scan = c.take<char>(scan_workspace_bytes(P));
+  w.counters = c.take<long long>(4);
+
+  dim3 grid(view_grid(cs), n_views);
+  // erosion -> mask bit 1
+  erode_h_kernel<<<grid, 256, 0, st>>>(maps->mask, w.tmp, cs, prm->r_erode);
+  erode_v_kernel<<<grid, 256, 0, st>>>(w.tmp, maps->mask, cs, prm->r_erode);
+  // candidate flags
+  if (n > 0) ADP_CUDA(cudaMemsetAsync(w.cand, 0, n, st));
+  if (n_cand > 0)
+    scatter_flag_kernel<<<grid_for(n_cand, 256, 4096), 256, 0, st>>>(candidates, n_cand, n,
+                                                                      w.cand);
+  // labelling
+  unsigned gp = grid_for(P, 256, 148 * 16);
+  ccl_init_kernel<<<gp, 256, 0, st>>>(maps->mask, dominant, w.cand, n, P, w.L);
+  ccl_union_kernel<<<grid, 256, 0, st>>>(maps->mask, dominant, cs, w.L);
+  ccl_flatten_kernel<<<gp, 256, 0, st>>>(w.L, P);
+  ADP_LAUNCH_CHECK();
+  // roots -> slots
+  int* L = w.L;
+  int* slot = w.slot;
+  int* root_pix = w.root_pix;
+  rc = scan_exclusive([=] __device__(long long p) -> long long { return L[p] == p ? 1 : 0; },
+                      [=] __device__(long long p, long long pre) {
+                        if (L[p] == p) {
+                          slot[p] = (int)pre;
+                          root_pix[pre] = (int)p;
+                        }
+                      },
+                      P, nullptr, &w.counters[0], w.scan, st);
+  if (rc) return rc;
+  zero_i64_kernel<<<gp, 256, 0, st>>>(w.mom, &w.counters[0], 6);
+  moments_kernel<<<grid, 256, 0, st>>>(w.L, w.slot, cs, w.mom);
+  ADP_LAUNCH_CHECK();
+  // area filter: kept index of every root, total -> out->count
+  const long long* mom = w.mom;
+  long long* kept = w.kept_idx;
+  int m_min = prm->m_min;
+  rc = scan_exclusive(
+      [=] __device__(long long r) -> long long { return mom[6 * r] >= m_min ? 1 : 0; },
+      [=] __device__(long long r, long long pre) { kept[r] = pre; }, P, &w.counters[0],
+      (long long*)out->count, w.scan, st);
+  if (rc) return rc;
+  RegionArgs ra;
+  ra.mom = w.mom;
+  ra.root_pix = w.root_pix;
+  ra.kept_idx = w.kept_idx;
+  ra.d_nroots = &w.counters[0];
+  ra.dom = dominant;
+  ra.mask = maps->mask;
+  ra.tgt = target;
+  ra.m_min = prm->m_min;
+  ra.cap = out->capacity;
+  ra.view = out->view;
+  ra.parent = out->parent;
+  ra.label = out->label;
+  ra.band = out->band;
+  ra.moments = (long long*)out->moments;
+  ra.stats = out->stats;
+  region_stats_kernel<<<gp, 256, 0, st>>>(ra, cs);
+  if (out->labels)
+    labels_out_kernel<<<grid, 256, 0, st>>>(w.L, w.mom, w.slot, prm->m_min, cs, out->labels);
+  ADP_LAUNCH_CHECK();
+  return ADP_OK;
+}

@@ -1,0 +1,112 @@
+// Device math shared by the forward and backward kernels: quaternion rotation,
+// the real SH basis (3DGS sign convention) and its gradient, and the per-pixel
+// alpha evaluation that forward and backward must compute identically.
+#pragma once
+
+#include "common.cuh"
+
+namespace adp {
+
+// Real SH normalisation constants up to degree 3 (3DGS basis signs).
+#define SHC0 0.28209479177387814f
+#define SHC1 0.4886025119029199f
+#define SHC2_0 1.0925484305920792f
+#define SHC2_2 0.31539156525252005f
+#define SHC2_4 0.5462742152960396f
+#define SHC3_0 0.5900435899266435f
+#define SHC3_1 2.890611442640554f
+#define SHC3_2 0.4570457994644658f
+#define SHC3_3 0.3731763325901154f
+#define SHC3_5 1.445305721320277f
+
+struct Mat3 {
+  float m[9];
+};
+
+// Rotation (row-major) of the normalised quaternion q = (w, x, y, z).
+__device__ __forceinline__ Mat3 rot_of_quat(float w, float x, float y, float z) {
+  Mat3 R;
+  R.m[0] = 1.f - 2.f * (y * y + z * z);
+  R.m[1] = 2.f * (x * y - w * z);
+  R.m[2] = 2.f * (x * z + w * y);
+  R.m[3] = 2.f * (x * y + w * z);
+  R.m[4] = 1.f - 2.f * (x * x + z * z);
+  R.m[5] = 2.f * (y * z - w * x);
+  R.m[6] = 2.f * (x * z - w * y);
+  R.m[7] = 2.f * (y * z + w * x);
+  R.m[8] = 1.f - 2.f * (x * x + y * y);
+  return R;
+}
+
+// Basis values Y[k], k < (deg+1)^2, at unit direction (x, y, z).
+__device__ __forceinline__ void sh_eval_basis(int deg, float x, float y, float z, float* Y) {
+  Y[0] = SHC0;
+  if (deg < 1) return;
+  Y[1] = -SHC1 * y;
+  Y[2] = SHC1 * z;
+  Y[3] = -SHC1 * x;
+  if (deg < 2) return;
+  float xx = x * x, yy = y * y, zz = z * z;
+  Y[4] = SHC2_0 * x * y;
+  Y[5] = -SHC2_0 * y * z;
+  Y[6] = SHC2_2 * (2.f * zz - xx - yy);
+  Y[7] = -SHC2_0 * x * z;
+  Y[8] = SHC2_4 * (xx - yy);
+  if (deg < 3) return;
+  Y[9] = -SHC3_0 * y * (3.f * xx - yy);
+  Y[10] = SHC3_1 * x * y * z;
+  Y[11] = -SHC3_2 * y * (4.f * zz - xx - yy);
+  Y[12] = SHC3_3 * z * (2.f * zz - 3.f * xx - 3.f * yy);
+  Y[13] = -SHC3_2 * x * (4.f * zz - xx - yy);
+  Y[14] = SHC3_5 * z * (xx - yy);
+  Y[15] = -SHC3_0 * x * (xx - 3.f * yy);
+}
+
+// Partial derivatives of the basis with respect to the (unnormalised
+// coordinates of the) direction: dY[k] = (dY/dx, dY/dy, dY/dz).
+__device__ __forceinline__ void sh_eval_basis_grad(int deg, float x, float y, float z,
+                                                   float3* dY) {
+  dY[0] = make_float3(0.f, 0.f, 0.f);
+  if (deg < 1) return;
+  dY[1] = make_float3(0.f, -SHC1, 0.f);
+  dY[2] = make_float3(0.f, 0.f, SHC1);
+  dY[3] = make_float3(-SHC1, 0.f, 0.f);
+  if (deg < 2) return;
+  float xx = x * x, yy = y * y, zz = z * z;
+  dY[4] = make_float3(SHC2_0 * y, SHC2_0 * x, 0.f);
+  dY[5] = make_float3(0.f, -SHC2_0 * z, -SHC2_0 * y);
+  dY[6] = make_float3(-2.f * SHC2_2 * x, -2.f * SHC2_2 * y, 4.f * SHC2_2 * z);
+  dY[7] = make_float3(-SHC2_0 * z, 0.f, -SHC2_0 * x);
+  dY[8] = make_float3(2.f * SHC2_4 * x, -2.f * SHC2_4 * y, 0.f);
+  if (deg < 3) return;
+  dY[9] = make_float3(-SHC3_0 * 6.f * x * y, -SHC3_0 * (3.f * xx - 3.f * yy), 0.f);
+  dY[10] = make_float3(SHC3_1 * y * z, SHC3_1 * x * z, SHC3_1 * x * y);
+  dY[11] = make_float3(SHC3_2 * 2.f * x * y, -SHC3_2 * (4.f * zz - xx - 3.f * yy),
+                       -SHC3_2 * 8.f * y * z);
+  dY[12] = make_float3(-SHC3_3 * 6.f * x * z, -SHC3_3 * 6.f * y * z,
+                       SHC3_3 * (6.f * zz - 3.f * xx - 3.f * yy));
+  dY[13] = make_float3(-SHC3_2 * (4.f * zz - 3.f * xx - yy), SHC3_2 * 2.f * x * y,
+                       -SHC3_2 * 8.f * x * z);
+  dY[14] = make_float3(SHC3_5 * 2.f * x * z, -SHC3_5 * 2.f * y * z, SHC3_5 * (xx - yy));
+  dY[15] = make_float3(-SHC3_0 * (3.f * xx - 3.f * yy), SHC3_0 * 6.f * x * y, 0.f);
+}
+
+// Reads SH float k*3+ch of Gaussian i from the float4 planes.
+__device__ __forceinline__ float sh_coef(const float* sh, long long n, long long i, int f) {
+  return sh[((long long)(f >> 2) * n + i) * 4 + (f & 3)];
+}
+
+// alpha at pixel (px, py) for a Gaussian with 2D mean (mx, my), conic (A, B, C)
+// and opacity o: returns o * exp(power), or 0 if power > 0. Both compositing
+// directions call this so their decisions agree bit for bit.
+__device__ __forceinline__ float alpha_raw(float mx, float my, float A, float B, float C, float o,
+                                           float px, float py, float* dx_out, float* dy_out) {
+  float dx = mx - px, dy = my - py;
+  *dx_out = dx;
+  *dy_out = dy;
+  float power = -0.5f * (A * dx * dx + C * dy * dy) - B * dx * dy;
+  if (power > 0.f) return 0.f;
+  return o * __expf(power);
+}
+
+}  // namespace adp

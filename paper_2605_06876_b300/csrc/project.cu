@@ -1,0 +1,168 @@
+// EWA projection of every Gaussian into every view (Sec. 3, Eq. 1): one thread
+// per (view, Gaussian), float4 plane loads, one record of three float4 + int4
+// rect + tile count written per pair.
+#include "gauss_math.cuh"
+
+namespace adp {
+
+struct ProjectArgs {
+  const float4* mean_logit;
+  const float4* logscale;
+  const float4* quat;
+  const float* sh;
+  long long n;
+  int deg;
+  float near_plane, low_pass, alpha_min;
+  float4* xy_op_depth;
+  float4* conic;
+  float4* rgb;
+  int4* rect;
+  int* tiles;
+};
+
+__global__ void __launch_bounds__(256) project_kernel(ProjectArgs a, CamSet cs) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int v = blockIdx.y;
+  if (i >= a.n) return;
+  const adp_camera& cam = cs.cam[v];
+  long long rec = (long long)v * a.n + i;
+  const float* Rw = cam.R;
+
+  float4 ml = a.mean_logit[i];
+  float pcx = Rw[0] * ml.x + Rw[1] * ml.y + Rw[2] * ml.z + cam.t[0];
+  float pcy = Rw[3] * ml.x + Rw[4] * ml.y + Rw[5] * ml.z + cam.t[1];
+  float pcz = Rw[6] * ml.x + Rw[7] * ml.y + Rw[8] * ml.z + cam.t[2];
+  float o = 1.f / (1.f + __expf(-ml.w));
+  bool vis = pcz > a.near_plane && o >= a.alpha_min;
+
+  float4 out0 = make_float4(0.f, 0.f, 0.f, 0.f), out1 = out0, out2 = out0;
+  int4 rc = make_int4(0, -1, 0, -1);
+  int nt = 0;
+  if (vis) {
+    float4 ls = a.logscale[i];
+    float4 q = a.quat[i];
+    float qn = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    Mat3 Rg = rot_of_quat(q.x * qn, q.y * qn, q.z * qn, q.w * qn);
+    float s2[3] = {__expf(2.f * ls.x), __expf(2.f * ls.y), __expf(2.f * ls.z)};
+    // Sigma = Rg diag(s^2) Rg^T (symmetric, six entries)
+    float S[6];
+    S[0] = Rg.m[0] * Rg.m[0] * s2[0] + Rg.m[1] * Rg.m[1] * s2[1] + Rg.m[2] * Rg.m[2] * s2[2];
+    S[1] = Rg.m[0] * Rg.m[3] * s2[0] + Rg.m[1] * Rg.m[4] * s2[1] + Rg.m[2] * Rg.m[5] * s2[2];
+    S[2] = Rg.m[0] * Rg.m[6] * s2[0] + Rg.m[1] * Rg.m[7] * s2[1] + Rg.m[2] * Rg.m[8] * s2[2];
+    S[3] = Rg.m[3] * Rg.m[3] * s2[0] + Rg.m[4] * Rg.m[4] * s2[1] + Rg.m[5] * Rg.m[5] * s2[2];
+    S[4] = Rg.m[3] * Rg.m[6] * s2[0] + Rg.m[4] * Rg.m[7] * s2[1] + Rg.m[5] * Rg.m[8] * s2[2];
+    S[5] = Rg.m[6] * Rg.m[6] * s2[0] + Rg.m[7] * Rg.m[7] * s2[1] + Rg.m[8] * Rg.m[8] * s2[2];
+    // J with x/z, y/z clamped to 1.3x the half field of view
+    float inv_z = 1.f / pcz;
+    float limx = 1.3f * (float)cam.width / (2.f * cam.fx);
+    float limy = 1.3f * (float)cam.height / (2.f * cam.fy);
+    float ux = fminf(limx, fmaxf(-limx, pcx * inv_z));
+    float uy = fminf(limy, fmaxf(-limy, pcy * inv_z));
+    float j00 = cam.fx * inv_z, j02 = -cam.fx * ux * inv_z;
+    float j11 = cam.fy * inv_z, j12 = -cam.fy * uy * inv_z;
+    // T = J W (2x3)
+    float T0[3], T1[3];
+    for (int c = 0; c < 3; ++c) {
+      T0[c] = j00 * Rw[c] + j02 * Rw[6 + c];
+      T1[c] = j11 * Rw[3 + c] + j12 * Rw[6 + c];
+    }
+    // Sigma2D = T Sigma T^T
+    float ST0[3] = {S[0] * T0[0] + S[1] * T0[1] + S[2] * T0[2],
+                    S[1] * T0[0] + S[3] * T0[1] + S[4] * T0[2],
+                    S[2] * T0[0] + S[4] * T0[1] + S[5] * T0[2]};
+    float ST1[3] = {S[0] * T1[0] + S[1] * T1[1] + S[2] * T1[2],
+                    S[1] * T1[0] + S[3] * T1[1] + S[4] * T1[2],
+                    S[2] * T1[0] + S[4] * T1[1] + S[5] * T1[2]};
+    float ca = T0[0] * ST0[0] + T0[1] * ST0[1] + T0[2] * ST0[2] + a.low_pass;
+    float cb = T0[0] * ST1[0] + T0[1] * ST1[1] + T0[2] * ST1[2];
+    float cc = T1[0] * ST1[0] + T1[1] * ST1[1] + T1[2] * ST1[2] + a.low_pass;
+    float det = ca * cc - cb * cb;
+    if (det > 0.f) {
+      float idet = 1.f / det;
+      float mx = cam.fx * pcx * inv_z + cam.px;
+      float my = cam.fy * pcy * inv_z + cam.py;
+      // pixel box of o exp(-d^T C d / 2) >= alpha_min
+      float k = 2.f * __logf(o / a.alpha_min);
+      k = fmaxf(k, 0.f);
+      float hx = sqrtf(k * ca), hy = sqrtf(k * cc);
+      float x0 = fmaxf(ceilf(mx - hx), 0.f), x1 = fminf(floorf(mx + hx), (float)(cam.width - 1));
+      float y0 = fmaxf(ceilf(my - hy), 0.f), y1 = fminf(floorf(my + hy), (float)(cam.height - 1));
+      if (x0 <= x1 && y0 <= y1) {
+        rc = make_int4((int)x0 / cs.tile_w, (int)x1 / cs.tile_w, (int)y0 / cs.tile_h,
+                       (int)y1 / cs.tile_h);
+        nt = (rc.y - rc.x + 1) * (rc.w - rc.z + 1);
+        // colour from the direction camera centre -> mean
+        float ccx = -(Rw[0] * cam.t[0] + Rw[3] * cam.t[1] + Rw[6] * cam.t[2]);
+        float ccy = -(Rw[1] * cam.t[0] + Rw[4] * cam.t[1] + Rw[7] * cam.t[2]);
+        float ccz = -(Rw[2] * cam.t[0] + Rw[5] * cam.t[1] + Rw[8] * cam.t[2]);
+        float dx = ml.x - ccx, dy = ml.y - ccy, dz = ml.z - ccz;
+        float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+        float Y[16];
+        sh_eval_basis(a.deg, dx * il, dy * il, dz * il, Y);
+        int K = sh_coeffs(a.deg);
+        float col[3] = {0.5f, 0.5f, 0.5f};
+        int P = sh_planes(a.deg);
+        for (int p = 0; p < P; ++p) {
+          float4 c4 = reinterpret_cast<const float4*>(a.sh)[(long long)p * a.n + i];
+          float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+          for (int l = 0; l < 4; ++l) {
+            int f = 4 * p + l;
+            if (f < 3 * K) col[f % 3] += cv[l] * Y[f / 3];
+          }
+        }
+        out0 = make_float4(mx, my, o, pcz);
+        out1 = make_float4(cc * idet, -cb * idet, ca * idet, 0.f);
+        out2 = make_float4(fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f), 0.f);
+      }
+    }
+  }
+  a.xy_op_depth[rec] = out0;
+  a.conic[rec] = out1;
+  a.rgb[rec] = out2;
+  a.rect[rec] = rc;
+  a.tiles[rec] = nt;
+}
+
+}  // namespace adp
+
+using namespace adp;
+
+extern "C" ADP_API int adp_project(const adp_gaussians* g, const adp_camera* cams, int32_t n_views,
+                                   const adp_params* prm, adp_projected* out,
+                                   adp_stream_t stream) {
+  ADP_CHECK_ARG(g && out, "NULL argument");
+  ADP_CHECK_ARG(g->n >= 0 && g->n < (1LL << 31), "n = %lld out of range", (long long)g->n);
+  ADP_CHECK_ARG(g->sh_degree >= 0 && g->sh_degree <= 3, "sh_degree must be 0..3");
+  CamSet cs;
+  int rc = make_camset(cams, n_views, prm, &cs);
+  if (rc) return rc;
+  ADP_CHECK_ARG((long long)n_views * g->n < (1LL << 31), "n_views * n exceeds 2^31");
+  if (g->n == 0) return ADP_OK;
+  ADP_CHECK_ARG(g->mean_logit && g->logscale && g->quat && g->sh, "NULL Gaussian array");
+  ADP_CHECK_ARG(out->xy_opacity_depth && out->conic && out->rgb && out->rect && out->tiles_touched,
+                "NULL projected array");
+  ADP_CHECK_ARG(aligned(g->mean_logit, 16) && aligned(g->logscale, 16) && aligned(g->quat, 16) &&
+                    aligned(g->sh, 16) && aligned(out->xy_opacity_depth, 16) &&
+                    aligned(out->conic, 16) && aligned(out->rgb, 16) && aligned(out->rect, 16),
+                "float4 arrays must be 16-byte aligned");
+  ProjectArgs a;
+  a.mean_logit = reinterpret_cast<const float4*>(g->mean_logit);
+  a.logscale = reinterpret_cast<const float4*>(g->logscale);
+  a.quat = reinterpret_cast<const float4*>(g->quat);
+  a.sh = g->sh;
+  a.n = g->n;
+  a.deg = g->sh_degree;
+  a.near_plane = prm->near_plane;
+  a.low_pass = prm->low_pass;
+  a.alpha_min = prm->alpha_min;
+  a.xy_op_depth = reinterpret_cast<float4*>(out->xy_opacity_depth);
+  a.conic = reinterpret_cast<float4*>(out->conic);
+  a.rgb = reinterpret_cast<float4*>(out->rgb);
+  a.rect = reinterpret_cast<int4*>(out->rect);
+  a.tiles = out->tiles_touched;
+  dim3 grid(grid_for(g->n, 256), n_views);
+  project_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(a, cs);
+  ADP_LAUNCH_CHECK();
+  return ADP_OK;
+}

@@ -1,0 +1,132 @@
+// Front-to-back alpha compositing (Eq. 1) with the dominant Gaussian map (Eq. 5).
+// One CTA per tile (256 pixels, one per thread); the tile's depth-sorted list is
+// staged through shared memory 256 Gaussians at a time, each thread gathering one
+// record; a block-wide vote ends the tile once every pixel has stopped.
+#include "gauss_math.cuh"
+
+namespace adp {
+
+struct RenderArgs {
+  const float4* xyod;
+  const float4* conic;
+  const float4* rgb;
+  const int* inst;
+  const int2* ranges;
+  long long n;
+  float bg[3];
+  float alpha_min, alpha_max, t_min;
+  float* out_rgb;
+  float* out_T;
+  int* out_n;
+  int* out_last;
+  int* out_dom;
+};
+
+__global__ void __launch_bounds__(256) render_kernel(RenderArgs a, CamSet cs) {
+  __shared__ float4 s_g0[256];  // mx, my, A, B
+  __shared__ float4 s_g1[256];  // C, opacity, r, g
+  __shared__ float2 s_g2[256];  // b, id (as int bits)
+  const int tile = blockIdx.x;
+  const int v = view_of_tile(cs, tile);
+  const int lt = tile - cs.tile_base[v];
+  const int txs = cs.tiles_x[v];
+  const int W = cs.cam[v].width, H = cs.cam[v].height;
+  const int px = (lt % txs) * cs.tile_w + (int)threadIdx.x % cs.tile_w;
+  const int py = (lt / txs) * cs.tile_h + (int)threadIdx.x / cs.tile_w;
+  const bool inside = px < W && py < H;
+  const float fx = (float)px, fy = (float)py;
+  const int2 range = a.ranges[tile];
+  const int count = range.y - range.x;
+  const long long rec_base = (long long)v * a.n;
+
+  float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, best = -1.f;
+  int dom = -1, ncon = 0, last = 0;
+  bool done = !inside;
+  for (int b0 = 0; b0 < count; b0 += 256) {
+    if (__syncthreads_count(done) == 256) break;
+    int j = b0 + (int)threadIdx.x;
+    if (j < count) {
+      int id = a.inst[range.x + j];
+      long long r = rec_base + id;
+      float4 p0 = a.xyod[r], p1 = a.conic[r], p2 = a.rgb[r];
+      s_g0[threadIdx.x] = make_float4(p0.x, p0.y, p1.x, p1.y);
+      s_g1[threadIdx.x] = make_float4(p1.z, p0.z, p2.x, p2.y);
+      s_g2[threadIdx.x] = make_float2(p2.z, __int_as_float(id));
+    }
+    __syncthreads();
+    if (!done) {
+      int cnt = min(256, count - b0);
+      for (int k = 0; k < cnt; ++k) {
+        float4 g0 = s_g0[k], g1 = s_g1[k];
+        float dx, dy;
+        float al = alpha_raw(g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, fx, fy, &dx, &dy);
+        if (al < a.alpha_min) continue;
+        al = fminf(a.alpha_max, al);
+        float test = T * (1.f - al);
+        if (test < a.t_min) {
+          done = true;
+          break;
+        }
+        float w = T * al;
+        float2 g2 = s_g2[k];
+        c0 += w * g1.z;
+        c1 += w * g1.w;
+        c2 += w * g2.x;
+        if (w > best) {
+          best = w;
+          dom = __float_as_int(g2.y);
+        }
+        T = test;
+        ++ncon;
+        last = b0 + k + 1;
+      }
+    }
+  }
+  if (inside) {
+    long long p = cs.pix_base[v] + (long long)py * W + px;
+    a.out_rgb[3 * p + 0] = c0 + T * a.bg[0];
+    a.out_rgb[3 * p + 1] = c1 + T * a.bg[1];
+    a.out_rgb[3 * p + 2] = c2 + T * a.bg[2];
+    a.out_T[p] = T;
+    a.out_n[p] = ncon;
+    a.out_last[p] = last;
+    a.out_dom[p] = dom;
+  }
+}
+
+}  // namespace adp
+
+using namespace adp;
+
+extern "C" ADP_API int adp_render(int64_t n, const adp_projected* pr, const adp_bins* bins,
+                                  const adp_camera* cams, int32_t n_views, const float* bg,
+                                  const adp_params* prm, adp_image* out, adp_stream_t stream) {
+  ADP_CHECK_ARG(pr && bins && out, "NULL argument");
+  CamSet cs;
+  int rc = make_camset(cams, n_views, prm, &cs);
+  if (rc) return rc;
+  ADP_CHECK_ARG(n >= 0 && (long long)n * n_views < (1LL << 31), "n_views * n exceeds 2^31");
+  ADP_CHECK_ARG(out->rgb && out->T_final && out->n_contrib && out->last && out->dominant,
+                "NULL image array");
+  ADP_CHECK_ARG(bins->tile_range, "NULL tile ranges");
+  RenderArgs a;
+  a.xyod = reinterpret_cast<const float4*>(pr->xy_opacity_depth);
+  a.conic = reinterpret_cast<const float4*>(pr->conic);
+  a.rgb = reinterpret_cast<const float4*>(pr->rgb);
+  a.inst = bins->inst_gauss;
+  a.ranges = reinterpret_cast<const int2*>(bins->tile_range);
+  a.n = n;
+  for (int c = 0; c < 3; ++c) a.bg[c] = bg ? bg[c] : 0.f;
+  a.alpha_min = prm->alpha_min;
+  a.alpha_max = prm->alpha_max;
+  a.t_min = prm->t_min;
+  a.out_rgb = out->rgb;
+  a.out_T = out->T_final;
+  a.out_n = out->n_contrib;
+  a.out_last = out->last;
+  a.out_dom = out->dominant;
+  int n_tiles = cs.tile_base[n_views];
+  render_kernel<<<n_tiles, 256, 0, (cudaStream_t)stream>>>(a, cs);
+  ADP_LAUNCH_CHECK();
+  return ADP_OK;
+}

@@ -1,0 +1,843 @@
+// The AdpSplit operator (Sec. 4, Sec. 5.1, Appendix A) and the compaction of the
+// Gaussian arrays.
+//
+// Plan: regions are grouped by candidate with a stable radix sort on the
+// candidate index (keeping their (view, label) order), one thread per region
+// builds the child proposal (Eqs. 9-10, Appendix A), and one thread per
+// candidate merges its proposals (Eqs. 11-12: pairwise test, union-find,
+// enclosing covariance from an analytic 3x3 eigen-decomposition), applies the
+// n_max cap and writes the surviving children into a per-region child table.
+// Scans give every kept Gaussian its new index and every candidate the offset
+// of its appended block. This stage is small next to rendering, so it runs in
+// FP64, which keeps every integer outcome (statuses, child counts) stable.
+// Apply: gathers kept Gaussians (with Adam moments) and writes appended ones.
+#include "gauss_math.cuh"
+
+namespace adp {
+
+struct Prop {
+  double mu[3];
+  double R[9];  // row-major, columns are the child's axes
+  double s[3];
+  double rgb[3];
+};
+
+struct SplitWs {
+  int* cand_of;        // [n] candidate index or -1
+  unsigned* rkeys;     // [Rcap]
+  unsigned* rvals;     // [Rcap]
+  int2* seg;           // [n_cand] sorted-region range of each candidate
+  Prop* props;         // [Rcap]
+  int* uf;             // [Rcap]
+  double* ext;         // [Rcap]
+  float4* kids;        // [Rcap][4] child table: mean, quat, logscale, dc
+  long long* keep_new; // [n]
+  long long* app_off;  // [n_cand]
+  long long* counters; // [0] regions in use, [1] kept, [2] appended, [3] new n
+  void* scan;
+  SortWorkspace sort;
+};
+
+static size_t split_ws_bytes(long long n, long long nc, long long rc) {
+  long long sm = n > nc ? n : nc;
+  return carve_bytes<int>(n) + 2 * carve_bytes<unsigned>(rc) + carve_bytes<int2>(nc) +
+         carve_bytes<Prop>(rc) + carve_bytes<int>(rc) + carve_bytes<double>(rc) +
+         carve_bytes<float4>(4 * rc) + carve_bytes<long long>(n) + carve_bytes<long long>(nc) +
+         carve_bytes<long long>(4) + scan_workspace_bytes(sm) + sort_workspace_bytes(rc);
+}
+
+static SplitWs carve_split(Carver& c, long long n, long long nc, long long rc) {
+  SplitWs w;
+  long long sm = n > nc ? n : nc;
+  w.cand_of = c.take<int>(n);
+  w.rkeys = c.take<unsigned>(rc);
+  w.rvals = c.take<unsigned>(rc);
+  w.seg = c.take<int2>(nc);
+  w.props = c.take<Prop>(rc);
+  w.uf = c.take<int>(rc);
+  w.ext = c.take<double>(rc);
+  w.kids = c.take<float4>(4 * rc);
+  w.keep_new = c.take<long long>(n);
+  w.app_off = c.take<long long>(nc);
+  w.counters = c.take<long long>(4);
+  w.scan = c.take<char>(scan_workspace_bytes(sm));
+  w.sort = carve_sort(c, rc);
+  return w;
+}
+
+// ------------------------------------------------------------------ fp64 helpers
+
+__device__ __forceinline__ double dot3d(const double* a, const double* b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+__device__ __forceinline__ void cross3d(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+__device__ __forceinline__ double clipd(double x, double a) {
+  double m = fabs(x) < a ? fabs(x) : a;
+  return x < 0.0 ? -m : m;
+}
+
+__device__ void quat_rot_d(float4 q, double* R) {
+  double w = q.x, x = q.y, y = q.z, z = q.w;
+  double nq = sqrt(w * w + x * x + y * y + z * z);
+  w /= nq; x /= nq; y /= nq; z /= nq;
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+}
+
+// Unit quaternion (w >= 0) of a rotation matrix, from its largest diagonal term.
+__device__ float4 rot_quat_d(const double* R) {
+  double m00 = R[0], m11 = R[4], m22 = R[8];
+  double w, x, y, z;
+  double tr = m00 + m11 + m22;
+  if (tr >= m00 && tr >= m11 && tr >= m22) {
+    double r = sqrt(1.0 + tr);
+    w = 0.5 * r; double f = 0.5 / r;
+    x = (R[7] - R[5]) * f; y = (R[2] - R[6]) * f; z = (R[3] - R[1]) * f;
+  } else if (m00 >= m11 && m00 >= m22) {
+    double r = sqrt(1.0 + m00 - m11 - m22);
+    x = 0.5 * r; double f = 0.5 / r;
+    w = (R[7] - R[5]) * f; y = (R[1] + R[3]) * f; z = (R[2] + R[6]) * f;
+  } else if (m11 >= m22) {
+    double r = sqrt(1.0 - m00 + m11 - m22);
+    y = 0.5 * r; double f = 0.5 / r;
+    w = (R[2] - R[6]) * f; x = (R[1] + R[3]) * f; z = (R[5] + R[7]) * f;
+  } else {
+    double r = sqrt(1.0 - m00 - m11 + m22);
+    z = 0.5 * r; double f = 0.5 / r;
+    w = (R[3] - R[1]) * f; x = (R[2] + R[6]) * f; y = (R[5] + R[7]) * f;
+  }
+  double nq = sqrt(w * w + x * x + y * y + z * z);
+  if (w < 0) nq = -nq;
+  return make_float4((float)(w / nq), (float)(x / nq), (float)(y / nq), (float)(z / nq));
+}
+
+// Eigenvectors (columns of E, right-handed) and eigenvalues of a symmetric
+// 3x3 matrix: trigonometric closed form for the eigenvalues, cross products of
+// the rows of A - lambda I for the eigenvectors; a repeated eigenvalue takes any
+// orthonormal basis of its eigenspace.
+__device__ void sym3_eigen(const double* A, double* lam, double* E) {
+  double a00 = A[0], a01 = A[1], a02 = A[2], a11 = A[4], a12 = A[5], a22 = A[8];
+  double p1 = a01 * a01 + a02 * a02 + a12 * a12;
+  double q = (a00 + a11 + a22) / 3.0;
+  double scale = fabs(a00) + fabs(a11) + fabs(a22) + 2.0 * sqrt(p1) + 1e-300;
+  for (int i = 0; i < 9; ++i) E[i] = (i % 4 == 0) ? 1.0 : 0.0;
+  if (p1 <= 1e-30 * scale * scale) {
+    lam[0] = a00; lam[1] = a11; lam[2] = a22;
+    return;
+  }
+  double p2 = (a00 - q) * (a00 - q) + (a11 - q) * (a11 - q) + (a22 - q) * (a22 - q) + 2.0 * p1;
+  double p = sqrt(p2 / 6.0);
+  double B[9];
+  for (int i = 0; i < 9; ++i) B[i] = (A[i] - ((i % 4 == 0) ? q : 0.0)) / p;
+  double detB = B[0] * (B[4] * B[8] - B[5] * B[7]) - B[1] * (B[3] * B[8] - B[5] * B[6]) +
+                B[2] * (B[3] * B[7] - B[4] * B[6]);
+  double r = fmin(1.0, fmax(-1.0, 0.5 * detB));
+  double phi = acos(r) / 3.0;
+  double l1 = q + 2.0 * p * cos(phi);
+  double l3 = q + 2.0 * p * cos(phi + 2.0943951023931957);
+  double l2 = 3.0 * q - l1 - l3;
+  lam[0] = l1; lam[1] = l2; lam[2] = l3;
+  double tol = 1e-9 * (fabs(l1) + fabs(l3) + 1e-300);
+  // eigenvector of a simple eigenvalue lm: the best cross product of two rows
+  auto simple_vec = [&](double lm, double* v) {
+    double r0[3] = {a00 - lm, a01, a02}, r1[3] = {a01, a11 - lm, a12}, r2[3] = {a02, a12, a22 - lm};
+    double c0[3], c1[3], c2[3];
+    cross3d(r0, r1, c0);
+    cross3d(r0, r2, c1);
+    cross3d(r1, r2, c2);
+    double n0 = dot3d(c0, c0), n1 = dot3d(c1, c1), n2 = dot3d(c2, c2);
+    const double* c = c0;
+    double nb = n0;
+    if (n1 > nb) { c = c1; nb = n1; }
+    if (n2 > nb) { c = c2; nb = n2; }
+    double inv = 1.0 / sqrt(nb);
+    for (int i = 0; i < 3; ++i) v[i] = c[i] * inv;
+  };
+  // a unit vector orthogonal to v (the largest column of A - lm I projected off v)
+  auto orth_in_space = [&](double lm, const double* v, double* out) {
+    double cols[3][3] = {{a00 - lm, a01, a02}, {a01, a11 - lm, a12}, {a02, a12, a22 - lm}};
+    double best = -1.0;
+    for (int k = 0; k < 3; ++k) {
+      double c[3] = {cols[k][0], cols[k][1], cols[k][2]};
+      double pr = dot3d(c, v);
+      for (int i = 0; i < 3; ++i) c[i] -= pr * v[i];
+      double nn = dot3d(c, c);
+      if (nn > best) {
+        best = nn;
+        for (int i = 0; i < 3; ++i) out[i] = c[i];
+      }
+    }
+    if (best <= 0.0) {  // fall back to any perpendicular
+      double t[3] = {fabs(v[0]) < 0.9 ? 1.0 : 0.0, fabs(v[0]) < 0.9 ? 0.0 : 1.0, 0.0};
+      double pr = dot3d(t, v);
+      for (int i = 0; i < 3; ++i) out[i] = t[i] - pr * v[i];
+      best = dot3d(out, out);
+    }
+    double inv = 1.0 / sqrt(best);
+    for (int i = 0; i < 3; ++i) out[i] *= inv;
+  };
+  double v1[3], v2[3], v3[3];
+  if (l1 - l3 <= tol) {
+    return;  // all equal: identity basis
+  } else if (l1 - l2 <= tol) {  // top pair repeated, l3 simple
+    simple_vec(l3, v3);
+    orth_in_space(l3, v3, v1);
+    cross3d(v3, v1, v2);
+  } else if (l2 - l3 <= tol) {  // bottom pair repeated, l1 simple
+    simple_vec(l1, v1);
+    orth_in_space(l1, v1, v2);
+    cross3d(v1, v2, v3);
+  } else {
+    simple_vec(l1, v1);
+    simple_vec(l3, v3);
+    cross3d(v3, v1, v2);
+    double n2 = sqrt(dot3d(v2, v2));
+    for (int i = 0; i < 3; ++i) v2[i] /= n2;
+    cross3d(v1, v2, v3);
+  }
+  for (int i = 0; i < 3; ++i) {
+    E[3 * i + 0] = v1[i];
+    E[3 * i + 1] = v2[i];
+    E[3 * i + 2] = v3[i];
+  }
+}
+
+__device__ __forceinline__ void sigma_of(const Prop& p, double* S) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double acc = 0;
+      for (int k = 0; k < 3; ++k) acc += p.R[3 * i + k] * p.s[k] * p.s[k] * p.R[3 * j + k];
+      S[3 * i + j] = acc;
+    }
+}
+
+// sqrt(d^T Sigma^-1 d) with Sigma^-1 = R diag(s^-2) R^T
+__device__ __forceinline__ double mahal_d(const Prop& p, const double* d) {
+  double acc = 0;
+  for (int k = 0; k < 3; ++k) {
+    double c = p.R[k] * d[0] + p.R[3 + k] * d[1] + p.R[6 + k] * d[2];
+    acc += c * c / (p.s[k] * p.s[k]);
+  }
+  return sqrt(acc);
+}
+
+// ------------------------------------------------------------------ plan kernels
+
+__global__ void cand_of_kernel(const int* cand, long long nc, long long n, int* cand_of) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc;
+       c += (long long)gridDim.x * blockDim.x) {
+    int i = cand[c];
+    if (i >= 0 && i < n) cand_of[i] = (int)c;
+  }
+}
+
+__global__ void region_keys_kernel(const int* parent, const long long* d_count, long long cap,
+                                   const int* cand_of, long long n, unsigned nc, unsigned* keys,
+                                   unsigned* vals, long long* used) {
+  long long R = *d_count;
+  if (R > cap) R = cap;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *used = R;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < R;
+       r += (long long)gridDim.x * blockDim.x) {
+    int p = parent[r];
+    int c = (p >= 0 && p < n) ? cand_of[p] : -1;
+    keys[r] = c >= 0 ? (unsigned)c : nc;
+    vals[r] = (unsigned)r;
+  }
+}
+
+__global__ void seg_kernel(const unsigned* keys, const long long* d_n, unsigned nc, int2* seg) {
+  long long N = *d_n;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < N;
+       j += (long long)gridDim.x * blockDim.x) {
+    unsigned k = keys[j];
+    if (k >= nc) continue;
+    if (j == 0 || keys[j - 1] != k) seg[k].x = (int)j;
+    if (j == N - 1 || keys[j + 1] != k) seg[k].y = (int)(j + 1);
+  }
+}
+
+struct ProposalArgs {
+  const float4* mean_logit;
+  const float4* logscale;
+  const float4* quat;
+  const int* r_view;
+  const int* r_parent;
+  const double* r_stats;
+  const unsigned* keys;
+  const unsigned* vals;
+  const long long* d_n;
+  unsigned nc;
+  double eps_t, scale_floor;
+  Prop* props;
+};
+
+// One child proposal per region (Eqs. 9-10 and Appendix A), in FP64.
+__global__ void proposal_kernel(ProposalArgs a, CamSet cs) {
+  long long N = *a.d_n;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < N;
+       j += (long long)gridDim.x * blockDim.x) {
+    if (a.keys[j] >= a.nc) continue;
+    int r = (int)a.vals[j];
+    int i = a.r_parent[r];
+    const adp_camera& cam = cs.cam[a.r_view[r]];
+    const double* st = a.r_stats + 12LL * r;
+    float4 ml = a.mean_logit[i], ls = a.logscale[i];
+    double mu[3] = {ml.x, ml.y, ml.z};
+    double sp[3] = {exp((double)ls.x), exp((double)ls.y), exp((double)ls.z)};
+    double Rp[9];
+    quat_rot_d(a.quat[i], Rp);
+    double Rw[9], tw[3];
+    for (int k = 0; k < 9; ++k) Rw[k] = cam.R[k];
+    for (int k = 0; k < 3; ++k) tw[k] = cam.t[k];
+    double o[3], u[3], w[3], zv[3];
+    for (int k = 0; k < 3; ++k) {
+      o[k] = -(Rw[k] * tw[0] + Rw[3 + k] * tw[1] + Rw[6 + k] * tw[2]);
+      u[k] = Rw[k];
+      w[k] = Rw[3 + k];
+      zv[k] = Rw[6 + k];
+    }
+    double dcam[3] = {(st[0] - (double)cam.px) / (double)cam.fx,
+                      (st[1] - (double)cam.py) / (double)cam.fy, 1.0};
+    double d[3];
+    for (int k = 0; k < 3; ++k) d[k] = Rw[k] * dcam[0] + Rw[3 + k] * dcam[1] + Rw[6 + k] * dcam[2];
+    double dn = sqrt(dot3d(d, d));
+    for (int k = 0; k < 3; ++k) d[k] /= dn;
+    // Sigma^-1 d and t* (Eq. 10)
+    double Ad[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+      double c = Rp[k] * d[0] + Rp[3 + k] * d[1] + Rp[6 + k] * d[2];
+      c /= sp[k] * sp[k];
+      for (int m = 0; m < 3; ++m) Ad[m] += Rp[3 * m + k] * c;
+    }
+    double b[3] = {mu[0] - o[0], mu[1] - o[1], mu[2] - o[2]};
+    double ts = dot3d(b, Ad) / (dot3d(d, Ad) + a.eps_t);
+    Prop p;
+    for (int k = 0; k < 3; ++k) p.mu[k] = o[k] + ts * d[k];
+    double tz = ts / sqrt(dot3d(dcam, dcam));
+    double smax = fmax(sp[0], fmax(sp[1], sp[2]));
+    double e1x = st[5], e1y = st[6], e2x = -st[6], e2y = st[5];
+    double w1x = clipd(e1x * st[7] * tz / (double)cam.fx, smax * fabs(e1x));
+    double w1y = clipd(e1y * st[7] * tz / (double)cam.fy, smax * fabs(e1y));
+    double w2x = clipd(e2x * st[8] * tz / (double)cam.fx, smax * fabs(e2x));
+    double w2y = clipd(e2y * st[8] * tz / (double)cam.fy, smax * fabs(e2y));
+    double a1[3], a2[3];
+    for (int k = 0; k < 3; ++k) {
+      a1[k] = w1x * u[k] + w1y * w[k];
+      a2[k] = w2x * u[k] + w2y * w[k];
+    }
+    double n1 = sqrt(dot3d(a1, a1)), n2 = sqrt(dot3d(a2, a2));
+    p.s[0] = fmax(n1, a.scale_floor);
+    p.s[1] = fmax(n2, a.scale_floor);
+    p.s[2] = p.s[1];
+    double u1[3], u2[3];
+    for (int k = 0; k < 3; ++k) u1[k] = n1 < 1e-12 ? u[k] : a1[k] / n1;
+    double pr = dot3d(a2, u1), r2[3];
+    for (int k = 0; k < 3; ++k) r2[k] = a2[k] - pr * u1[k];
+    double nr = sqrt(dot3d(r2, r2));
+    if (nr < 1e-12) {
+      cross3d(zv, u1, u2);
+    } else {
+      for (int k = 0; k < 3; ++k) u2[k] = r2[k] / nr;
+    }
+    double c12[3];
+    cross3d(u1, u2, c12);
+    if (dot3d(c12, zv) < 0.0)
+      for (int k = 0; k < 3; ++k) u2[k] = -u2[k];
+    for (int k = 0; k < 3; ++k) {
+      p.R[3 * k + 0] = u1[k];
+      p.R[3 * k + 1] = u2[k];
+      p.R[3 * k + 2] = zv[k];
+      p.rgb[k] = st[9 + k];
+    }
+    a.props[j] = p;
+  }
+}
+
+__device__ __forceinline__ int uf_root(int* uf, int a) {
+  while (uf[a] != a) a = uf[a];
+  return a;
+}
+
+__device__ void store_child(float4* kid, const double* mu, const double* R, const double* s,
+                            const double* rgb) {
+  kid[0] = make_float4((float)mu[0], (float)mu[1], (float)mu[2], 0.f);
+  kid[1] = rot_quat_d(R);
+  kid[2] = make_float4((float)log(s[0]), (float)log(s[1]), (float)log(s[2]), 0.f);
+  const double C0 = 0.28209479177387814;
+  kid[3] = make_float4((float)((rgb[0] - 0.5) / C0), (float)((rgb[1] - 0.5) / C0),
+                       (float)((rgb[2] - 0.5) / C0), 0.f);
+}
+
+struct MergeArgs {
+  const int* cand;
+  const int* count;
+  const int2* seg;
+  const Prop* props;
+  int* uf;
+  double* ext;
+  float4* kids;
+  long long nc;
+  double gamma_d, gamma_c, scale_floor;
+  int n_max;
+  uint8_t* status;
+  int* n_children;
+};
+
+// One thread per candidate: status, merge (Eqs. 11-12), cap, child table.
+__global__ void merge_kernel(MergeArgs a) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.nc;
+       c += (long long)gridDim.x * blockDim.x) {
+    int i = a.cand[c];
+    int2 sg = a.seg[c];
+    int s0 = sg.x, M = sg.y - sg.x;
+    if (a.count[i] == 0) {
+      a.status[c] = ADP_FALLBACK;
+      a.n_children[c] = 0;
+      continue;
+    }
+    if (M <= 0) {
+      a.status[c] = ADP_RESET;
+      a.n_children[c] = 0;
+      continue;
+    }
+    a.status[c] = ADP_ADAPTIVE;
+    int* uf = a.uf + s0;
+    for (int m = 0; m < M; ++m) uf[m] = m;
+    for (int x = 0; x < M; ++x) {
+      const Prop& px = a.props[s0 + x];
+      for (int y = x + 1; y < M; ++y) {
+        const Prop& py = a.props[s0 + y];
+        double dc = fmax(fabs(px.rgb[0] - py.rgb[0]),
+                         fmax(fabs(px.rgb[1] - py.rgb[1]), fabs(px.rgb[2] - py.rgb[2])));
+        if (dc > a.gamma_c) continue;
+        double d[3] = {py.mu[0] - px.mu[0], py.mu[1] - px.mu[1], py.mu[2] - px.mu[2]};
+        double dist = mahal_d(px, d) + mahal_d(py, d);
+        if (dist > a.gamma_d) continue;
+        int rx = uf_root(uf, x), ry = uf_root(uf, y);
+        if (rx < ry) uf[ry] = rx;
+        else if (ry < rx) uf[rx] = ry;
+      }
+    }
+    for (int m = 0; m < M; ++m) uf[m] = uf_root(uf, m);
+    // groups in first-member order, written to the child table in place
+    int ng = 0;
+    for (int g = 0; g < M; ++g) {
+      if (uf[g] != g) continue;
+      int cnt = 0;
+      double gm[3] = {0, 0, 0}, gc[3] = {0, 0, 0}, Sb[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      int last = g;
+      for (int m = g; m < M; ++m) {
+        if (uf[m] != g) continue;
+        const Prop& p = a.props[s0 + m];
+        double S[9];
+        sigma_of(p, S);
+        for (int k = 0; k < 3; ++k) {
+          gm[k] += p.mu[k];
+          gc[k] += p.rgb[k];
+        }
+        for (int k = 0; k < 9; ++k) Sb[k] += S[k];
+        ++cnt;
+        last = m;
+      }
+      double mu[3], rgb[3], R[9], s[3];
+      if (cnt == 1) {  // Eq. 12 reduces to the member itself
+        const Prop& p = a.props[s0 + g];
+        for (int k = 0; k < 3; ++k) {
+          mu[k] = p.mu[k];
+          rgb[k] = p.rgb[k];
+          s[k] = p.s[k];
+        }
+        for (int k = 0; k < 9; ++k) R[k] = p.R[k];
+      } else {
+        for (int k = 0; k < 3; ++k) {
+          mu[k] = gm[k] / cnt;
+          rgb[k] = gc[k] / cnt;
+        }
+        for (int k = 0; k < 9; ++k) Sb[k] /= cnt;
+        double ev[3];
+        sym3_eigen(Sb, ev, R);
+        double lam[3] = {0, 0, 0};
+        for (int m = g; m <= last; ++m) {
+          if (uf[m] != g) continue;
+          const Prop& p = a.props[s0 + m];
+          double S[9];
+          sigma_of(p, S);
+          for (int r = 0; r < 3; ++r) {
+            double e[3] = {R[r], R[3 + r], R[6 + r]};
+            double Se[3];
+            for (int k = 0; k < 3; ++k) Se[k] = S[3 * k] * e[0] + S[3 * k + 1] * e[1] + S[3 * k + 2] * e[2];
+            double dm[3] = {p.mu[0] - mu[0], p.mu[1] - mu[1], p.mu[2] - mu[2]};
+            double reach = fabs(dot3d(e, dm)) + sqrt(fmax(dot3d(e, Se), 0.0));
+            lam[r] = fmax(lam[r], reach * reach);
+          }
+        }
+        double c0[3] = {R[0], R[3], R[6]}, c1[3] = {R[1], R[4], R[7]}, c2[3] = {R[2], R[5], R[8]}, cc[3];
+        cross3d(c0, c1, cc);
+        if (dot3d(cc, c2) < 0.0) {
+          R[2] = -R[2]; R[5] = -R[5]; R[8] = -R[8];
+        }
+        for (int r = 0; r < 3; ++r) s[r] = fmax(sqrt(lam[r]), a.scale_floor);
+      }
+      a.ext[s0 + ng] = s[0] * s[1] * s[2];
+      store_child(a.kids + 4LL * (s0 + ng), mu, R, s, rgb);
+      ++ng;
+    }
+    // cap: keep the n_max largest extents (ties to the earlier group), in group order
+    int kept = 0;
+    for (int gk = 0; gk < ng; ++gk) {
+      double e = a.ext[s0 + gk];
+      int rank = 0;
+      for (int h = 0; h < ng; ++h) {
+        double eh = a.ext[s0 + h];
+        if (eh > e || (eh == e && h < gk)) ++rank;
+      }
+      if (rank < a.n_max) {
+        if (kept != gk)
+          for (int q = 0; q < 4; ++q) a.kids[4LL * (s0 + kept) + q] = a.kids[4LL * (s0 + gk) + q];
+        ++kept;
+      }
+    }
+    a.n_children[c] = kept;
+  }
+}
+
+__global__ void new_n_kernel(long long* counters) { counters[3] = counters[1] + counters[2]; }
+
+// ------------------------------------------------------------------ apply kernels
+
+struct GaussPtrs {
+  float4* ml;
+  float4* ls;
+  float4* q;
+  float4* sh;
+  long long n;
+};
+
+static inline GaussPtrs gp_of(const adp_gaussians* g) {
+  GaussPtrs p;
+  p.ml = reinterpret_cast<float4*>(g->mean_logit);
+  p.ls = reinterpret_cast<float4*>(g->logscale);
+  p.q = reinterpret_cast<float4*>(g->quat);
+  p.sh = reinterpret_cast<float4*>(g->sh);
+  p.n = g->n;
+  return p;
+}
+
+struct ApplyArgs {
+  GaussPtrs in, min_, vin, out, mout, vout;
+  bool has_m_in, has_v_in, has_m_out, has_v_out;
+  int planes;
+  const int* cand_of;
+  const uint8_t* status;
+  const long long* keep_new;
+};
+
+__device__ __forceinline__ void copy_gauss(const GaussPtrs& s, long long i, const GaussPtrs& d,
+                                           long long j, int planes) {
+  d.ml[j] = s.ml[i];
+  d.ls[j] = s.ls[i];
+  d.q[j] = s.q[i];
+  for (int p = 0; p < planes; ++p) d.sh[(long long)p * d.n + j] = s.sh[(long long)p * s.n + i];
+}
+
+__device__ __forceinline__ void zero_gauss(const GaussPtrs& d, long long j, int planes) {
+  float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  d.ml[j] = z;
+  d.ls[j] = z;
+  d.q[j] = z;
+  for (int p = 0; p < planes; ++p) d.sh[(long long)p * d.n + j] = z;
+}
+
+__global__ void apply_keep_kernel(ApplyArgs a) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.in.n;
+       i += (long long)gridDim.x * blockDim.x) {
+    int c = a.cand_of[i];
+    if (c >= 0 && a.status[c] != ADP_RESET) continue;
+    long long j = a.keep_new[i];
+    if (j >= a.out.n) continue;
+    copy_gauss(a.in, i, a.out, j, a.planes);
+    if (a.has_m_out) {
+      if (a.has_m_in) copy_gauss(a.min_, i, a.mout, j, a.planes);
+      else zero_gauss(a.mout, j, a.planes);
+    }
+    if (a.has_v_out) {
+      if (a.has_v_in) copy_gauss(a.vin, i, a.vout, j, a.planes);
+      else zero_gauss(a.vout, j, a.planes);
+    }
+  }
+}
+
+struct AppendArgs {
+  GaussPtrs in, out, mout, vout;
+  bool has_m_out, has_v_out;
+  int planes;
+  const int* cand;
+  long long nc;
+  const uint8_t* status;
+  const int* n_children;
+  const int2* seg;
+  const float4* kids;
+  const long long* app_off;
+  const long long* counters;
+  const float* noise;
+  double eta;
+};
+
+__global__ void apply_append_kernel(AppendArgs a) {
+  long long n_keep = a.counters[1];
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.nc;
+       c += (long long)gridDim.x * blockDim.x) {
+    uint8_t stt = a.status[c];
+    if (stt == ADP_RESET) continue;
+    int i = a.cand[c];
+    long long o = n_keep + a.app_off[c];
+    float4 ml = a.in.ml[i], ls = a.in.ls[i], q = a.in.q[i];
+    int nout = stt == ADP_ADAPTIVE ? 1 + a.n_children[c] : 2;
+    if (o + nout > a.out.n) continue;
+    if (stt == ADP_FALLBACK) {
+      double Rp[9];
+      quat_rot_d(q, Rp);
+      double sp[3] = {exp((double)ls.x), exp((double)ls.y), exp((double)ls.z)};
+      double shrink = log(2.0 * a.eta);
+      for (int ch = 0; ch < 2; ++ch) {
+        const float* z = a.noise + 6 * c + 3 * ch;
+        double dl[3] = {sp[0] * z[0], sp[1] * z[1], sp[2] * z[2]};
+        double m[3];
+        for (int r = 0; r < 3; ++r)
+          m[r] = (double)(r == 0 ? ml.x : (r == 1 ? ml.y : ml.z)) + Rp[3 * r] * dl[0] +
+                 Rp[3 * r + 1] * dl[1] + Rp[3 * r + 2] * dl[2];
+        long long j = o + ch;
+        copy_gauss(a.in, i, a.out, j, a.planes);
+        a.out.ml[j] = make_float4((float)m[0], (float)m[1], (float)m[2], ml.w);
+        a.out.ls[j] = make_float4((float)((double)ls.x - shrink), (float)((double)ls.y - shrink),
+                                  (float)((double)ls.z - shrink), ls.w);
+      }
+    } else {
+      int N = a.n_children[c];
+      // parent copy: opacity o / (N + 1), everything else unchanged
+      double op = 1.0 / (1.0 + exp(-(double)ml.w));
+      double on = op / (double)(N + 1);
+      copy_gauss(a.in, i, a.out, o, a.planes);
+      a.out.ml[o] = make_float4(ml.x, ml.y, ml.z, (float)log(on / (1.0 - on)));
+      int s0 = a.seg[c].x;
+      for (int k = 0; k < N; ++k) {
+        long long j = o + 1 + k;
+        const float4* kid = a.kids + 4LL * (s0 + k);
+        float4 km = kid[0], kq = kid[1], kl = kid[2], kd = kid[3];
+        a.out.ml[j] = make_float4(km.x, km.y, km.z, ml.w);
+        a.out.ls[j] = make_float4(kl.x, kl.y, kl.z, 0.f);
+        a.out.q[j] = kq;
+        for (int p = 0; p < a.planes; ++p)
+          a.out.sh[(long long)p * a.out.n + j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        a.out.sh[j] = make_float4(kd.x, kd.y, kd.z, 0.f);
+      }
+    }
+    for (long long j = o; j < o + nout; ++j) {
+      if (a.has_m_out) zero_gauss(a.mout, j, a.planes);
+      if (a.has_v_out) zero_gauss(a.vout, j, a.planes);
+    }
+  }
+}
+
+static bool gauss_ok(const adp_gaussians* g) {
+  return g && g->mean_logit && g->logscale && g->quat && g->sh && aligned(g->mean_logit, 16) &&
+         aligned(g->logscale, 16) && aligned(g->quat, 16) && aligned(g->sh, 16);
+}
+
+}  // namespace adp
+
+using namespace adp;
+
+extern "C" ADP_API size_t adp_split_workspace_size(int64_t n, int64_t n_cand,
+                                                   int64_t region_capacity) {
+  if (n < 0 || n_cand < 0 || region_capacity < 0) return 0;
+  return split_ws_bytes(n, n_cand, region_capacity);
+}
+
+extern "C" ADP_API int adp_split_plan(const adp_gaussians* g, const adp_camera* cams,
+                                      int32_t n_views, const adp_regions* regs,
+                                      const int32_t* candidates, int64_t n_cand,
+                                      const int32_t* count, const adp_params* prm,
+                                      uint8_t* status, int32_t* n_children, int64_t* d_new_n,
+                                      int64_t* h_new_n, void* ws, size_t ws_bytes,
+                                      adp_stream_t stream) {
+  ADP_CHECK_ARG(gauss_ok(g) || (g && g->n == 0), "bad Gaussian arrays");
+  ADP_CHECK_ARG(regs && regs->count && count && d_new_n, "NULL argument");
+  ADP_CHECK_ARG(g->n >= 0 && g->n < (1LL << 31), "n out of range");
+  ADP_CHECK_ARG(n_cand >= 0 && n_cand <= g->n, "n_cand out of range");
+  ADP_CHECK_ARG(n_cand == 0 || (candidates && status && n_children), "NULL candidate arrays");
+  ADP_CHECK_ARG(regs->capacity >= 0 && regs->capacity < (1LL << 31), "region capacity out of range");
+  ADP_CHECK_ARG(regs->capacity == 0 || (regs->view && regs->parent && regs->stats),
+                "NULL region arrays");
+  CamSet cs;
+  int rc = make_camset(cams, n_views, prm, &cs);
+  if (rc) return rc;
+  ADP_CHECK_ARG(prm->n_max >= 0, "n_max must be >= 0");
+  ADP_CHECK_ARG(aligned(ws, 256), "workspace must be 256-byte aligned");
+  long long n = g->n, nc = n_cand, rcap = regs->capacity;
+  size_t need = split_ws_bytes(n, nc, rcap);
+  ADP_CHECK_ARG(ws_bytes >= need, "workspace %zu bytes, need %zu", ws_bytes, need);
+  cudaStream_t st = (cudaStream_t)stream;
+  Carver c(ws, ws_bytes);
+  SplitWs w = carve_split(c, n, nc, rcap);
+  ADP_CUDA(cudaMemsetAsync(w.counters, 0, 4 * sizeof(long long), st));
+  if (n > 0) ADP_CUDA(cudaMemsetAsync(w.cand_of, 0xff, sizeof(int) * n, st));
+  if (nc > 0) {
+    ADP_CUDA(cudaMemsetAsync(w.seg, 0, sizeof(int2) * nc, st));
+    cand_of_kernel<<<grid_for(nc, 256, 4096), 256, 0, st>>>(candidates, nc, n, w.cand_of);
+  }
+  if (rcap > 0) {
+    region_keys_kernel<<<grid_for(rcap, 256, 4096), 256, 0, st>>>(
+        regs->parent, (const long long*)regs->count, rcap, w.cand_of, n, (unsigned)nc, w.rkeys,
+        w.rvals, &w.counters[0]);
+    int bits = bits_for(nc);
+    DigitOp passes[4];
+    int np = 0;
+    for (int s = 0; s < bits; s += 8) passes[np++] = DigitOp{s, 0u};
+    rc = radix_sort_pairs(w.rkeys, w.rvals, &w.counters[0], rcap, passes, np, w.sort, st);
+    if (rc) return rc;
+    seg_kernel<<<grid_for(rcap, 256, 4096), 256, 0, st>>>(w.rkeys, &w.counters[0], (unsigned)nc,
+                                                          w.seg);
+    ProposalArgs pa;
+    pa.mean_logit = reinterpret_cast<const float4*>(g->mean_logit);
+    pa.logscale = reinterpret_cast<const float4*>(g->logscale);
+    pa.quat = reinterpret_cast<const float4*>(g->quat);
+    pa.r_view = regs->view;
+    pa.r_parent = regs->parent;
+    pa.r_stats = regs->stats;
+    pa.keys = w.rkeys;
+    pa.vals = w.rvals;
+    pa.d_n = &w.counters[0];
+    pa.nc = (unsigned)nc;
+    pa.eps_t = prm->eps_t;
+    pa.scale_floor = prm->scale_floor;
+    pa.props = w.props;
+    proposal_kernel<<<grid_for(rcap, 128, 4096), 128, 0, st>>>(pa, cs);
+    ADP_LAUNCH_CHECK();
+  }
+  if (nc > 0) {
+    MergeArgs ma;
+    ma.cand = candidates;
+    ma.count = count;
+    ma.seg = w.seg;
+    ma.props = w.props;
+    ma.uf = w.uf;
+    ma.ext = w.ext;
+    ma.kids = w.kids;
+    ma.nc = nc;
+    ma.gamma_d = prm->gamma_d;
+    ma.gamma_c = prm->gamma_c;
+    ma.scale_floor = prm->scale_floor;
+    ma.n_max = prm->n_max;
+    ma.status = status;
+    ma.n_children = n_children;
+    merge_kernel<<<grid_for(nc, 64, 4096), 64, 0, st>>>(ma);
+    ADP_LAUNCH_CHECK();
+  }
+  // new indices of kept Gaussians and offsets of appended blocks
+  const int* cand_of = w.cand_of;
+  long long* keep_new = w.keep_new;
+  const uint8_t* cstatus = status;
+  rc = scan_exclusive(
+      [=] __device__(long long i) -> long long {
+        int cc = cand_of[i];
+        return (cc < 0 || cstatus[cc] == ADP_RESET) ? 1 : 0;
+      },
+      [=] __device__(long long i, long long pre) { keep_new[i] = pre; }, n, nullptr,
+      &w.counters[1], w.scan, st);
+  if (rc) return rc;
+  if (nc > 0) {
+    const int* nch = n_children;
+    long long* app_off = w.app_off;
+    rc = scan_exclusive(
+        [=] __device__(long long cc) -> long long {
+          uint8_t s = cstatus[cc];
+          return s == ADP_ADAPTIVE ? 1 + nch[cc] : (s == ADP_FALLBACK ? 2 : 0);
+        },
+        [=] __device__(long long cc, long long pre) { app_off[cc] = pre; }, nc, nullptr,
+        &w.counters[2], w.scan, st);
+    if (rc) return rc;
+  }
+  new_n_kernel<<<1, 1, 0, st>>>(w.counters);
+  ADP_CUDA(cudaMemcpyAsync(d_new_n, &w.counters[3], sizeof(long long), cudaMemcpyDeviceToDevice, st));
+  ADP_LAUNCH_CHECK();
+  if (h_new_n) {
+    ADP_CUDA(cudaMemcpyAsync(h_new_n, &w.counters[3], sizeof(long long), cudaMemcpyDeviceToHost, st));
+    ADP_CUDA(cudaStreamSynchronize(st));
+  }
+  return ADP_OK;
+}
+
+extern "C" ADP_API int adp_split_apply(const adp_gaussians* g, const adp_gaussians* m_in,
+                                       const adp_gaussians* v_in, const adp_regions* regs,
+                                       const int32_t* candidates, int64_t n_cand,
+                                       const uint8_t* status, const int32_t* n_children,
+                                       const float* noise, const adp_params* prm,
+                                       adp_gaussians* out, adp_gaussians* m_out,
+                                       adp_gaussians* v_out, void* ws, size_t ws_bytes,
+                                       adp_stream_t stream) {
+  ADP_CHECK_ARG(g && out && regs && prm, "NULL argument");
+  ADP_CHECK_ARG(gauss_ok(g) || g->n == 0, "bad input Gaussian arrays");
+  ADP_CHECK_ARG(gauss_ok(out) || out->n == 0, "bad output Gaussian arrays");
+  ADP_CHECK_ARG(out->sh_degree == g->sh_degree, "sh_degree mismatch");
+  ADP_CHECK_ARG(n_cand >= 0 && n_cand <= g->n, "n_cand out of range");
+  ADP_CHECK_ARG(n_cand == 0 || (candidates && status && n_children && noise), "NULL candidate arrays");
+  ADP_CHECK_ARG(!m_in || (gauss_ok(m_in) && m_in->n == g->n), "bad m_in");
+  ADP_CHECK_ARG(!v_in || (gauss_ok(v_in) && v_in->n == g->n), "bad v_in");
+  ADP_CHECK_ARG(!m_out || (gauss_ok(m_out) && m_out->n == out->n), "bad m_out");
+  ADP_CHECK_ARG(!v_out || (gauss_ok(v_out) && v_out->n == out->n), "bad v_out");
+  ADP_CHECK_ARG(aligned(ws, 256), "workspace must be 256-byte aligned");
+  long long n = g->n, nc = n_cand, rcap = regs->capacity;
+  size_t need = split_ws_bytes(n, nc, rcap);
+  ADP_CHECK_ARG(ws_bytes >= need, "workspace %zu bytes, need %zu", ws_bytes, need);
+  cudaStream_t st = (cudaStream_t)stream;
+  Carver c(ws, ws_bytes);
+  SplitWs w = carve_split(c, n, nc, rcap);
+  int planes = sh_planes(g->sh_degree);
+  GaussPtrs gin = gp_of(g), gout = gp_of(out);
+  ApplyArgs aa;
+  aa.in = gin;
+  aa.out = gout;
+  aa.has_m_in = m_in != nullptr;
+  aa.has_v_in = v_in != nullptr;
+  aa.has_m_out = m_out != nullptr;
+  aa.has_v_out = v_out != nullptr;
+  if (m_in) aa.min_ = gp_of(m_in);
+  if (v_in) aa.vin = gp_of(v_in);
+  if (m_out) aa.mout = gp_of(m_out);
+  if (v_out) aa.vout = gp_of(v_out);
+  aa.planes = planes;
+  aa.cand_of = w.cand_of;
+  aa.status = status;
+  aa.keep_new = w.keep_new;
+  if (n > 0) apply_keep_kernel<<<grid_for(n, 256, 148 * 16), 256, 0, st>>>(aa);
+  if (nc > 0) {
+    AppendArgs ap;
+    ap.in = gin;
+    ap.out = gout;
+    ap.has_m_out = m_out != nullptr;
+    ap.has_v_out = v_out != nullptr;
+    if (m_out) ap.mout = gp_of(m_out);
+    if (v_out) ap.vout = gp_of(v_out);
+    ap.planes = planes;
+    ap.cand = candidates;
+    ap.nc = nc;
+    ap.status = status;
+    ap.n_children = n_children;
+    ap.seg = w.seg;
+    ap.kids = w.kids;
+    ap.app_off = w.app_off;
+    ap.counters = w.counters;
+    ap.noise = noise;
+    ap.eta = prm->eta;
+    apply_append_kernel<<<grid_for(nc, 128, 4096), 128, 0, st>>>(ap);
+  }
+  ADP_LAUNCH_CHECK();
+  return ADP_OK;
+}

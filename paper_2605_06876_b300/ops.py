@@ -1,0 +1,433 @@
+"""Thin torch-side binding of the C ABI: device buffers as torch tensors, one
+Python function per entry point. Argument marshalling only -- every step of the
+hot path runs in libadpsplit.so; there is no CPU or PyTorch fallback."""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _abi as A
+
+F32, I32, I64, U8, F64 = torch.float32, torch.int32, torch.int64, torch.uint8, torch.float64
+
+
+def sh_coeffs(deg):
+    return (deg + 1) ** 2
+
+
+def sh_planes(deg):
+    return (3 * sh_coeffs(deg) + 3) // 4
+
+
+def _p(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def n_tiles(cams, tile_w=16, tile_h=16):
+    return sum(((int(c["width"]) + tile_w - 1) // tile_w) * ((int(c["height"]) + tile_h - 1) // tile_h)
+               for c in cams)
+
+
+def n_pixels(cams):
+    return sum(int(c["width"]) * int(c["height"]) for c in cams)
+
+
+def workspace(nbytes, device="cuda"):
+    return torch.empty(max(int(nbytes), 256), dtype=U8, device=device)
+
+
+# --------------------------------------------------------------------------- Gaussians
+
+class Gaussians:
+    """Gaussian parameters (or gradients / Adam moments) as float4 planes."""
+
+    def __init__(self, n, sh_degree, device="cuda", zero=True):
+        alloc = torch.zeros if zero else torch.empty
+        self.n = int(n)
+        self.sh_degree = int(sh_degree)
+        self.mean_logit = alloc((self.n, 4), dtype=F32, device=device)
+        self.logscale = alloc((self.n, 4), dtype=F32, device=device)
+        self.quat = alloc((self.n, 4), dtype=F32, device=device)
+        self.sh = alloc((sh_planes(sh_degree), self.n, 4), dtype=F32, device=device)
+
+    @classmethod
+    def from_scene(cls, scene, device="cuda"):
+        n = scene["mean"].shape[0]
+        deg = int(scene["sh_degree"])
+        g = cls(n, deg, device, zero=False)
+        ml = np.concatenate([scene["mean"], scene["logit"][:, None]], 1)
+        ls = np.concatenate([scene["logscale"], np.zeros((n, 1), np.float32)], 1)
+        flat = scene["sh"].reshape(n, -1)
+        pad = np.zeros((n, 4 * sh_planes(deg)), np.float32)
+        pad[:, :flat.shape[1]] = flat
+        sh = pad.reshape(n, -1, 4).transpose(1, 0, 2)
+        g.mean_logit.copy_(torch.from_numpy(np.ascontiguousarray(ml, np.float32)))
+        g.logscale.copy_(torch.from_numpy(np.ascontiguousarray(ls, np.float32)))
+        g.quat.copy_(torch.from_numpy(np.ascontiguousarray(scene["quat"], np.float32)))
+        g.sh.copy_(torch.from_numpy(np.ascontiguousarray(sh, np.float32)))
+        return g
+
+    def to_scene(self):
+        n, deg = self.n, self.sh_degree
+        K = sh_coeffs(deg)
+        ml = self.mean_logit.cpu().numpy()
+        sh = self.sh.cpu().numpy().transpose(1, 0, 2).reshape(n, -1)[:, :3 * K]
+        return {"mean": ml[:, :3].copy(), "logit": ml[:, 3].copy(),
+                "logscale": self.logscale.cpu().numpy()[:, :3].copy(),
+                "quat": self.quat.cpu().numpy().copy(), "sh": sh.reshape(n, K, 3).copy(),
+                "sh_degree": deg}
+
+    def tensors(self):
+        return [self.mean_logit, self.logscale, self.quat, self.sh]
+
+    def zeros_like(self):
+        return Gaussians(self.n, self.sh_degree, self.mean_logit.device)
+
+    def clone(self):
+        g = Gaussians(self.n, self.sh_degree, self.mean_logit.device, zero=False)
+        for d, s in zip(g.tensors(), self.tensors()):
+            d.copy_(s)
+        return g
+
+    def c(self):
+        return A.AdpGaussians(self.n, self.sh_degree, 0, _p(self.mean_logit), _p(self.logscale),
+                              _p(self.quat), _p(self.sh))
+
+
+# --------------------------------------------------------------------------- buffers
+
+@dataclass
+class Projected:
+    xyod: torch.Tensor
+    conic: torch.Tensor
+    rgb: torch.Tensor
+    rect: torch.Tensor
+    tiles: torch.Tensor
+
+    @classmethod
+    def alloc(cls, records, device="cuda"):
+        return cls(torch.empty((records, 4), dtype=F32, device=device),
+                   torch.empty((records, 4), dtype=F32, device=device),
+                   torch.empty((records, 4), dtype=F32, device=device),
+                   torch.empty((records, 4), dtype=I32, device=device),
+                   torch.empty(records, dtype=I32, device=device))
+
+    def c(self):
+        return A.AdpProjected(_p(self.xyod), _p(self.conic), _p(self.rgb), _p(self.rect),
+                              _p(self.tiles))
+
+
+@dataclass
+class Bins:
+    inst: torch.Tensor
+    ranges: torch.Tensor
+    n_inst: torch.Tensor
+
+    @classmethod
+    def alloc(cls, capacity, tiles, device="cuda"):
+        return cls(torch.empty(max(int(capacity), 1), dtype=I32, device=device),
+                   torch.empty((tiles, 2), dtype=I32, device=device),
+                   torch.zeros(1, dtype=I64, device=device))
+
+    @property
+    def capacity(self):
+        return self.inst.numel()
+
+    def c(self):
+        return A.AdpBins(self.capacity, _p(self.inst), _p(self.ranges), _p(self.n_inst))
+
+
+@dataclass
+class Image:
+    rgb: torch.Tensor
+    T: torch.Tensor
+    n_contrib: torch.Tensor
+    last: torch.Tensor
+    dominant: torch.Tensor
+
+    @classmethod
+    def alloc(cls, P, device="cuda"):
+        return cls(torch.empty((P, 3), dtype=F32, device=device),
+                   torch.empty(P, dtype=F32, device=device), torch.empty(P, dtype=I32, device=device),
+                   torch.empty(P, dtype=I32, device=device), torch.empty(P, dtype=I32, device=device))
+
+    def c(self):
+        return A.AdpImage(_p(self.rgb), _p(self.T), _p(self.n_contrib), _p(self.last),
+                          _p(self.dominant))
+
+
+@dataclass
+class ErrorMaps:
+    E: torch.Tensor
+    mask: torch.Tensor
+    minmax: torch.Tensor
+
+    @classmethod
+    def alloc(cls, P, V, device="cuda"):
+        return cls(torch.empty(P, dtype=F32, device=device), torch.empty(P, dtype=U8, device=device),
+                   torch.empty((V, 2), dtype=F32, device=device))
+
+    def c(self):
+        return A.AdpErrorMaps(_p(self.E), _p(self.mask), _p(self.minmax))
+
+
+@dataclass
+class Regions:
+    view: torch.Tensor
+    parent: torch.Tensor
+    label: torch.Tensor
+    band: torch.Tensor
+    moments: torch.Tensor
+    stats: torch.Tensor
+    count: torch.Tensor
+    labels: torch.Tensor = None
+
+    @classmethod
+    def alloc(cls, capacity, P=None, device="cuda"):
+        cap = max(int(capacity), 1)
+        mk = lambda *s, dt: torch.empty(s, dtype=dt, device=device)
+        return cls(mk(cap, dt=I32), mk(cap, dt=I32), mk(cap, dt=I32), mk(cap, dt=I32),
+                   mk(cap, 6, dt=I64), mk(cap, 12, dt=F64), torch.zeros(1, dtype=I64, device=device),
+                   None if P is None else mk(P, dt=I32))
+
+    @classmethod
+    def from_arrays(cls, view, parent, label, stats, band=None, moments=None, device="cuda"):
+        """A region table given by the caller (e.g. from another implementation)."""
+        R = len(view)
+        r = cls.alloc(max(R, 1), None, device)
+        t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=device)
+        if R:
+            r.view[:R] = t(view, I32)
+            r.parent[:R] = t(parent, I32)
+            r.label[:R] = t(label, I32)
+            r.stats[:R] = t(stats, F64)
+            r.band[:R] = t(band if band is not None else np.zeros(R), I32)
+            r.moments[:R] = t(moments if moments is not None else np.zeros((R, 6)), I64)
+        r.count[0] = R
+        return r
+
+    @property
+    def capacity(self):
+        return self.view.numel()
+
+    def c(self):
+        return A.AdpRegions(self.capacity, _p(self.view), _p(self.parent), _p(self.label),
+                            _p(self.band), _p(self.moments), _p(self.stats), _p(self.count),
+                            _p(self.labels))
+
+    def to_numpy(self):
+        R = min(int(self.count.item()), self.capacity)
+        return {"view": self.view[:R].cpu().numpy(), "parent": self.parent[:R].cpu().numpy(),
+                "label": self.label[:R].cpu().numpy(), "band": self.band[:R].cpu().numpy(),
+                "moments": self.moments[:R].cpu().numpy(), "stats": self.stats[:R].cpu().numpy()}
+
+
+# --------------------------------------------------------------------------- entry points
+
+def project(g: Gaussians, cams, params=None, out: Projected = None, stream=None):
+    """adp_project: EWA projection into every view."""
+    params = params or A.default_params()
+    ca = A.cameras(cams)
+    out = out or Projected.alloc(len(cams) * g.n, g.mean_logit.device)
+    gc, oc = g.c(), out.c()
+    A.check(A.lib().adp_project(C.byref(gc), ca, len(cams), C.byref(params), C.byref(oc),
+                                _stream(stream)), "adp_project")
+    return out
+
+
+def bin_sort_workspace_size(n, n_views, capacity):
+    return A.lib().adp_bin_sort_workspace_size(n, n_views, capacity)
+
+
+def bin_sort(n, pr: Projected, cams, params=None, capacity=None, bins: Bins = None, ws=None,
+             stream=None, grow=True):
+    """adp_bin_sort. With grow=True an overflowing capacity is enlarged and the call
+    repeated (this reads the instance count back, a synchronisation)."""
+    params = params or A.default_params()
+    ca = A.cameras(cams)
+    V = len(cams)
+    dev = pr.xyod.device
+    if bins is None:
+        if capacity is None:
+            capacity = max(1024, int(pr.tiles.sum().item() * 1.0) + 1)
+        bins = Bins.alloc(capacity, n_tiles(cams, params.tile_w, params.tile_h), dev)
+    need = bin_sort_workspace_size(n, V, bins.capacity)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    pc, bc = pr.c(), bins.c()
+    A.check(A.lib().adp_bin_sort(n, C.byref(pc), ca, V, C.byref(params), C.byref(bc), _p(ws),
+                                 ws.numel(), _stream(stream)), "adp_bin_sort")
+    if grow:
+        k = int(bins.n_inst.item())
+        if k > bins.capacity:
+            return bin_sort(n, pr, cams, params, capacity=int(k * 1.25) + 1, stream=stream)
+    return bins
+
+
+def render(n, pr: Projected, bins: Bins, cams, bg=(0.0, 0.0, 0.0), params=None, out: Image = None,
+           stream=None):
+    """adp_render: compositing and dominant map."""
+    params = params or A.default_params()
+    ca = A.cameras(cams)
+    out = out or Image.alloc(n_pixels(cams), pr.xyod.device)
+    bgc = (C.c_float * 3)(*[float(x) for x in bg])
+    pc, bc, oc = pr.c(), bins.c(), out.c()
+    A.check(A.lib().adp_render(n, C.byref(pc), C.byref(bc), ca, len(cams), bgc, C.byref(params),
+                               C.byref(oc), _stream(stream)), "adp_render")
+    return out
+
+
+def error_stats(img, target, dominant, n, cams, params=None, maps: ErrorMaps = None, count=None,
+                mass=None, stream=None):
+    """adp_error_stats: E, M, bands, per-Gaussian count and mass."""
+    params = params or A.default_params()
+    ca = A.cameras(cams)
+    dev = img.device
+    maps = maps or ErrorMaps.alloc(n_pixels(cams), len(cams), dev)
+    count = count if count is not None else torch.empty(max(n, 1), dtype=I32, device=dev)
+    mass = mass if mass is not None else torch.empty(max(n, 1), dtype=F64, device=dev)
+    mc = maps.c()
+    A.check(A.lib().adp_error_stats(_p(img), _p(target), _p(dominant), n, ca, len(cams),
+                                    C.byref(params), C.byref(mc), _p(count), _p(mass),
+                                    _stream(stream)), "adp_error_stats")
+    return maps, count, mass
+
+
+def select_topk(mass, n, k, out=None, ws=None, stream=None):
+    """adp_select_topk: ids of the k largest masses, ascending."""
+    k = min(int(k), int(n))
+    out = out if out is not None else torch.empty(max(k, 1), dtype=I32, device=mass.device)
+    need = A.lib().adp_select_topk_workspace_size(n)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, mass.device)
+    A.check(A.lib().adp_select_topk(_p(mass), n, k, _p(out), _p(ws), ws.numel(), _stream(stream)),
+            "adp_select_topk")
+    return out[:k]
+
+
+def error_regions(maps: ErrorMaps, dominant, target, n, cams, candidates, params=None,
+                  capacity=None, regions: Regions = None, ws=None, stream=None, labels=False,
+                  grow=True):
+    """adp_error_regions: erosion, 8-connected regions, area filter, statistics."""
+    params = params or A.default_params()
+    ca = A.cameras(cams)
+    V = len(cams)
+    dev = maps.E.device
+    P = n_pixels(cams)
+    if regions is None:
+        regions = Regions.alloc(capacity or max(1024, P // 64), P if labels else None, dev)
+    need = A.lib().adp_error_regions_workspace_size(n, V, ca)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    nc = 0 if candidates is None else int(candidates.numel())
+    mc, rc = maps.c(), regions.c()
+    A.check(A.lib().adp_error_regions(C.byref(mc), _p(dominant), _p(target), n, ca, V,
+                                      _p(candidates) if nc else None, nc, C.byref(params),
+                                      C.byref(rc), _p(ws), ws.numel(), _stream(stream)),
+            "adp_error_regions")
+    if grow:
+        cnt = int(regions.count.item())
+        if cnt > regions.capacity:
+            return error_regions(maps, dominant, target, n, cams, candidates, params,
+                                 int(cnt * 1.25) + 1, None, None, stream, labels, False)
+    return regions
+
+
+def split_workspace_size(n, n_cand, region_capacity):
+    return A.lib().adp_split_workspace_size(n, n_cand, region_capacity)
+
+
+@dataclass
+class SplitPlan:
+    status: torch.Tensor
+    n_children: torch.Tensor
+    new_n: int
+    ws: torch.Tensor
+    d_new_n: torch.Tensor
+
+
+def split_plan(g: Gaussians, cams, regions: Regions, candidates, count, params=None, ws=None,
+               stream=None):
+    """adp_split_plan: statuses and child counts; reads the new size back (one sync)."""
+    params = params or A.default_params()
+    ca = A.cameras(cams)
+    dev = g.mean_logit.device
+    nc = int(candidates.numel())
+    need = split_workspace_size(g.n, nc, regions.capacity)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    status = torch.empty(max(nc, 1), dtype=U8, device=dev)
+    nch = torch.empty(max(nc, 1), dtype=I32, device=dev)
+    d_new_n = torch.empty(1, dtype=I64, device=dev)
+    h_new_n = C.c_int64(0)
+    gc, rc = g.c(), regions.c()
+    A.check(A.lib().adp_split_plan(C.byref(gc), ca, len(cams), C.byref(rc), _p(candidates), nc,
+                                   _p(count), C.byref(params), _p(status), _p(nch), _p(d_new_n),
+                                   C.byref(h_new_n), _p(ws), ws.numel(), _stream(stream)),
+            "adp_split_plan")
+    return SplitPlan(status[:nc], nch[:nc], int(h_new_n.value), ws, d_new_n)
+
+
+def split_apply(g: Gaussians, plan: SplitPlan, regions: Regions, candidates, noise, params=None,
+                m_in: Gaussians = None, v_in: Gaussians = None, with_state=True, stream=None):
+    """adp_split_apply: the new population (and Adam moments)."""
+    params = params or A.default_params()
+    dev = g.mean_logit.device
+    out = Gaussians(plan.new_n, g.sh_degree, dev, zero=False)
+    m_out = Gaussians(plan.new_n, g.sh_degree, dev, zero=False) if with_state else None
+    v_out = Gaussians(plan.new_n, g.sh_degree, dev, zero=False) if with_state else None
+    nc = int(candidates.numel())
+    if noise is None:
+        noise = torch.zeros((max(nc, 1), 2, 3), dtype=F32, device=dev)
+    gc, oc, rc = g.c(), out.c(), regions.c()
+    mic = m_in.c() if m_in is not None else None
+    vic = v_in.c() if v_in is not None else None
+    moc = m_out.c() if m_out is not None else None
+    voc = v_out.c() if v_out is not None else None
+    ref = lambda s: C.byref(s) if s is not None else None
+    A.check(A.lib().adp_split_apply(C.byref(gc), ref(mic), ref(vic), C.byref(rc), _p(candidates), nc,
+                                    _p(plan.status), _p(plan.n_children), _p(noise),
+                                    C.byref(params), C.byref(oc), ref(moc), ref(voc), _p(plan.ws),
+                                    plan.ws.numel(), _stream(stream)), "adp_split_apply")
+    return out, m_out, v_out
+
+
+def render_backward(g: Gaussians, pr: Projected, bins: Bins, fwd: Image, cams, target=None,
+                    dL_drgb=None, bg=(0.0, 0.0, 0.0), params=None, grad: Gaussians = None, ws=None,
+                    stream=None):
+    """adp_render_backward: gradients of the L1 loss (or of dL_drgb) for every parameter."""
+    params = params or A.default_params()
+    ca = A.cameras(cams)
+    V = len(cams)
+    dev = g.mean_logit.device
+    grad = grad or Gaussians(g.n, g.sh_degree, dev, zero=False)
+    need = A.lib().adp_render_backward_workspace_size(g.n, V)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    bgc = (C.c_float * 3)(*[float(x) for x in bg])
+    gc, pc, bc, fc, grc = g.c(), pr.c(), bins.c(), fwd.c(), grad.c()
+    A.check(A.lib().adp_render_backward(C.byref(gc), C.byref(pc), C.byref(bc), C.byref(fc),
+                                        _p(target), _p(dL_drgb), ca, V, bgc, C.byref(params),
+                                        C.byref(grc), _p(ws), ws.numel(), _stream(stream)),
+            "adp_render_backward")
+    return grad
+
+
+ADAM_LR = (1.6e-4, 0.05, 0.005, 0.001, 0.0025, 0.0025 / 20.0)
+
+
+def adam_step(param: Gaussians, grad: Gaussians, m: Gaussians, v: Gaussians, step, lr=ADAM_LR,
+              beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+    """adp_adam_step: one in-place bias-corrected Adam step."""
+    lrc = (C.c_float * 6)(*[float(x) for x in lr])
+    pc, gc, mc, vc = param.c(), grad.c(), m.c(), v.c()
+    A.check(A.lib().adp_adam_step(C.byref(pc), C.byref(gc), C.byref(mc), C.byref(vc), int(step),
+                                  lrc, beta1, beta2, eps, _stream(stream)), "adp_adam_step")

@@ -1,0 +1,119 @@
+"""One plain AdpSplit training step over preallocated device buffers.
+
+A step runs the whole hot path on one stream: projection, binning and depth sort,
+compositing with the dominant map, error statistics, top-k candidate choice by
+error mass, error regions, the render backward of the L1 loss, one Adam step, and
+the AdpSplit operator (plan, one read-back of the new population size, apply). The
+new population is returned; the step's own population is updated only by Adam, so
+repeated steps see the same workload.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _abi as A
+from . import ops
+
+
+class StageTimer:
+    """CUDA events around each stage, on the stream the stages run on."""
+
+    def __init__(self, stream=None):
+        self.stream = stream
+        self.events = []
+
+    def mark(self, name):
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(self.stream)
+        self.events.append((name, ev))
+
+    def durations(self):
+        out = {}
+        for (name, a), (_, b) in zip(self.events[:-1], self.events[1:]):
+            out[name] = out.get(name, 0.0) + a.elapsed_time(b)
+        return out
+
+
+class PlainStep:
+    def __init__(self, g: ops.Gaussians, cams, target, cand_frac=0.1, params=None,
+                 bg=(0.0, 0.0, 0.0), lr=ops.ADAM_LR, bins_margin=1.15, region_margin=1.25):
+        self.g = g
+        self.cams = list(cams)
+        self.V = len(self.cams)
+        self.target = target
+        self.params = params or A.default_params()
+        self.bg = bg
+        self.lr = lr
+        self.dev = g.mean_logit.device
+        n = g.n
+        self.k = max(1, int(round(cand_frac * n)))
+        self.P = ops.n_pixels(self.cams)
+        self.m, self.v = g.zeros_like(), g.zeros_like()
+        self.grad = ops.Gaussians(n, g.sh_degree, self.dev, zero=False)
+        self.pr = ops.Projected.alloc(self.V * n, self.dev)
+        self.img = ops.Image.alloc(self.P, self.dev)
+        self.maps = ops.ErrorMaps.alloc(self.P, self.V, self.dev)
+        self.count = torch.empty(n, dtype=torch.int32, device=self.dev)
+        self.mass = torch.empty(n, dtype=torch.float64, device=self.dev)
+        self.cand = torch.empty(self.k, dtype=torch.int32, device=self.dev)
+        self.adam_t = 0
+        # size the instance and region buffers from one probing pass
+        ops.project(g, self.cams, self.params, self.pr)
+        probe = ops.bin_sort(n, self.pr, self.cams, self.params)
+        k_inst = int(probe.n_inst.item())
+        self.bins = ops.Bins.alloc(int(k_inst * bins_margin) + 1024,
+                                   ops.n_tiles(self.cams, self.params.tile_w, self.params.tile_h),
+                                   self.dev)
+        self.ws_bins = ops.workspace(ops.bin_sort_workspace_size(n, self.V, self.bins.capacity), self.dev)
+        ops.bin_sort(n, self.pr, self.cams, self.params, bins=self.bins, ws=self.ws_bins, grow=False)
+        ops.render(n, self.pr, self.bins, self.cams, bg, self.params, self.img)
+        ops.error_stats(self.img.rgb, target, self.img.dominant, n, self.cams, self.params,
+                        self.maps, self.count, self.mass)
+        ops.select_topk(self.mass, n, self.k, self.cand)
+        probe_r = ops.error_regions(self.maps, self.img.dominant, target, n, self.cams, self.cand,
+                                    self.params)
+        cap = int(int(probe_r.count.item()) * region_margin) + 1024
+        self.regions = ops.Regions.alloc(cap, None, self.dev)
+        ca = A.cameras(self.cams)
+        self.ws_regions = ops.workspace(A.lib().adp_error_regions_workspace_size(n, self.V, ca), self.dev)
+        self.ws_topk = ops.workspace(A.lib().adp_select_topk_workspace_size(n), self.dev)
+        self.ws_bwd = ops.workspace(A.lib().adp_render_backward_workspace_size(n, self.V), self.dev)
+        self.ws_split = ops.workspace(ops.split_workspace_size(n, self.k, cap), self.dev)
+        torch.cuda.synchronize()
+
+    def step(self, noise, timer: StageTimer = None):
+        """One step; returns (new Gaussians, new m, new v, split plan)."""
+        g, cams, prm, n = self.g, self.cams, self.params, self.g.n
+        mark = timer.mark if timer else (lambda name: None)
+        mark("project")
+        ops.project(g, cams, prm, self.pr)
+        mark("bin_sort")
+        ops.bin_sort(n, self.pr, cams, prm, bins=self.bins, ws=self.ws_bins, grow=False)
+        mark("render")
+        ops.render(n, self.pr, self.bins, cams, self.bg, prm, self.img)
+        mark("error_stats")
+        ops.error_stats(self.img.rgb, self.target, self.img.dominant, n, cams, prm, self.maps,
+                        self.count, self.mass)
+        mark("select_topk")
+        ops.select_topk(self.mass, n, self.k, self.cand, ws=self.ws_topk)
+        mark("error_regions")
+        ops.error_regions(self.maps, self.img.dominant, self.target, n, cams, self.cand, prm,
+                          regions=self.regions, ws=self.ws_regions, grow=False)
+        mark("render_backward")
+        ops.render_backward(g, self.pr, self.bins, self.img, cams, target=self.target, bg=self.bg,
+                            params=prm, grad=self.grad, ws=self.ws_bwd)
+        mark("adam")
+        self.adam_t += 1
+        ops.adam_step(g, self.grad, self.m, self.v, self.adam_t, self.lr)
+        mark("split_plan")
+        plan = ops.split_plan(g, cams, self.regions, self.cand, self.count, prm, ws=self.ws_split)
+        mark("split_apply")
+        new_g, new_m, new_v = ops.split_apply(g, plan, self.regions, self.cand, noise, prm,
+                                              m_in=self.m, v_in=self.v)
+        mark("end")
+        return new_g, new_m, new_v, plan
+
+    def check_capacity(self):
+        """True if the last step's instances and regions fit their buffers."""
+        return (int(self.bins.n_inst.item()) <= self.bins.capacity and
+                int(self.regions.count.item()) <= self.regions.capacity)

@@ -243,12 +243,18 @@ def error_stage_inputs(seed, width, height, n_gauss, n_cells=None, bg_frac=0.05,
         cx, cy = rng.uniform(0, width), rng.uniform(0, height)
         sx, sy = rng.uniform(1.5, 12.0), rng.uniform(1.5, 12.0)
         th = rng.uniform(0, math.pi)
+        amp = rng.uniform(-0.8, 0.8, size=3)
         c, s = math.cos(th), math.sin(th)
-        dx, dy = xx - cx, yy - cy
+        rad = 6.0 * max(sx, sy)  # the patch is negligible beyond six deviations
+        x0, x1 = max(0, int(cx - rad)), min(width, int(cx + rad) + 1)
+        y0, y1 = max(0, int(cy - rad)), min(height, int(cy + rad) + 1)
+        if x0 >= x1 or y0 >= y1:
+            continue
+        dx, dy = xx[y0:y1, x0:x1] - cx, yy[y0:y1, x0:x1] - cy
         u = (c * dx + s * dy) / sx
         v = (-s * dx + c * dy) / sy
         g = np.exp(-0.5 * (u * u + v * v))
-        tgt += g[..., None] * rng.uniform(-0.8, 0.8, size=3)
+        tgt[y0:y1, x0:x1] += g[..., None] * amp
     tgt = np.clip(tgt, 0.0, 1.0)
     return _f32(img), _f32(tgt), dominant
 

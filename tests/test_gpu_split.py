@@ -1,0 +1,188 @@
+"""GPU parity of the AdpSplit operator and compaction, the backward and Adam
+against the FP64 oracle.
+
+The split stage runs in FP64 on both sides, so statuses and child counts must be
+identical; the new population is compared value by value (children through their
+covariance R diag(s^2) R^T, which is invariant to the sign and order freedom of the
+axes). Gradients are compared with the oracle's complex-step derivative.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import scenes
+from gpu_util import DEV, c0_inputs, np_, small_cluster_inputs
+from paper_2605_06876_b300 import ops
+
+pytestmark = pytest.mark.gpu
+
+
+def _sigma(ls, q):
+    R = O.quat_to_rot(q)
+    s = np.exp(np.asarray(ls, np.float64))
+    return np.einsum("nij,nj,nkj->nik", R, s * s, R)
+
+
+def _oracle_case(sc, cams, targets, k):
+    out = O.plain_step(sc, cams, targets, k_cand=k,
+                       noise=scenes.fallback_noise(7, k).astype(np.float64))
+    return out
+
+
+def _gpu_split(sc, cams, orc, noise):
+    g = ops.Gaussians.from_scene(sc, DEV)
+    rg = orc["regions"]
+    regs = ops.Regions.from_arrays(rg["view"], rg["parent"], rg["label"], rg["stats"], rg["band"],
+                                   rg["moments"], DEV)
+    cand = torch.as_tensor(orc["cand"], device=DEV)
+    count = torch.as_tensor(orc["count"], device=DEV)
+    rng = np.random.default_rng(3)
+    m_in = ops.Gaussians.from_scene({**sc, **{k: rng.normal(size=sc[k].shape).astype(np.float32)
+                                              for k in ("mean", "logit", "logscale", "quat", "sh")}}, DEV)
+    v_in = m_in.clone()
+    plan = ops.split_plan(g, cams, regs, cand, count)
+    out, m_out, v_out = ops.split_apply(g, plan, regs, cand, torch.as_tensor(noise, device=DEV),
+                                        m_in=m_in, v_in=v_in)
+    torch.cuda.synchronize()
+    return g, plan, out, m_in, m_out
+
+
+def _compare_split(sc, orc, plan, out, m_in, m_out):
+    sp = orc["split"]
+    assert np.array_equal(np_(plan.status), sp["status"])
+    assert np.array_equal(np_(plan.n_children), sp["n_children"])
+    assert plan.new_n == sp["new_n"] == out.n
+    got = O.theta_of(out.to_scene())
+    ref = sp["theta"]
+    n = sc["mean"].shape[0]
+    cand = set(orc["cand"].tolist())
+    keep = [i for i in range(n) if i not in cand or sp["status"][list(orc["cand"]).index(i)] == O.RESET]
+    nk = len(keep)
+    assert np.array_equal(got[:nk], ref[:nk])  # kept Gaussians copied bit for bit
+    mk = O.theta_of(m_out.to_scene())
+    assert np.array_equal(mk[:nk], O.theta_of(m_in.to_scene())[keep])
+    assert not mk[nk:].any()
+    # appended Gaussians: centres, opacities, colours, covariances
+    np.testing.assert_allclose(got[nk:, :3], ref[nk:, :3], rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(got[nk:, 3], ref[nk:, 3], rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(got[nk:, 11:], ref[nk:, 11:], rtol=1e-5, atol=1e-5)
+    Sg = _sigma(got[nk:, 4:7], got[nk:, 7:11])
+    Sr = _sigma(ref[nk:, 4:7], ref[nk:, 7:11])
+    scale = np.abs(Sr).reshape(len(Sr), -1).max(1)[:, None, None]
+    assert np.all(np.abs(Sg - Sr) <= 1e-5 * scale + 1e-12)
+
+
+def test_split_c0_matches_oracle():
+    sc, cam, target = c0_inputs()
+    k = 200
+    orc = _oracle_case(sc, [cam], [target], k)
+    noise = scenes.fallback_noise(7, k)
+    g, plan, out, m_in, m_out = _gpu_split(sc, [cam], orc, noise)
+    st = orc["split"]["status"]
+    assert (st == O.ADAPTIVE).sum() > 50
+    _compare_split(sc, orc, plan, out, m_in, m_out)
+
+
+def test_split_multiview_with_merges():
+    """Several views of a cluster scene: proposals from different views of one
+    parent merge (Eqs. 11-12) and the cap binds for some parents."""
+    sc, cams = small_cluster_inputs(6000, 240, 160, views=4, seed=12)
+    tg = scenes.scene_clusters(99, 9000, 3)
+    targets = []
+    for cam in cams:
+        r = O.render(O.project(O.theta_of(tg), 3, cam), cam)
+        targets.append(r["rgb"].astype(np.float32).reshape(cam["height"], cam["width"], 3))
+    k = 600
+    orc = O.plain_step(sc, cams, targets, k_cand=k, sp=O.SplitParams(n_max=4),
+                       noise=scenes.fallback_noise(8, k).astype(np.float64))
+    from paper_2605_06876_b300 import _abi
+    prm = _abi.default_params(n_max=4)
+    g = ops.Gaussians.from_scene(sc, DEV)
+    rg = orc["regions"]
+    regs = ops.Regions.from_arrays(rg["view"], rg["parent"], rg["label"], rg["stats"], rg["band"],
+                                   rg["moments"], DEV)
+    cand = torch.as_tensor(orc["cand"], device=DEV)
+    plan = ops.split_plan(g, cams, regs, cand, torch.as_tensor(orc["count"], device=DEV), prm)
+    out, _, _ = ops.split_apply(g, plan, regs, cand,
+                                torch.as_tensor(scenes.fallback_noise(8, k), device=DEV), prm,
+                                with_state=False)
+    torch.cuda.synchronize()
+    sp = orc["split"]
+    assert np.array_equal(np_(plan.status), sp["status"])
+    assert np.array_equal(np_(plan.n_children), sp["n_children"])
+    assert (sp["n_children"] == 4).sum() > 0
+    # at least one parent had more regions than children (merge or cap)
+    per_parent = np.bincount(rg["parent"], minlength=sc["mean"].shape[0])[orc["cand"]]
+    assert np.any(per_parent > sp["n_children"])
+    got = O.theta_of(out.to_scene())
+    ref = sp["theta"]
+    np.testing.assert_allclose(got[:, :4], ref[:, :4], rtol=1e-5, atol=1e-5)
+    Sg, Sr = _sigma(got[:, 4:7], got[:, 7:11]), _sigma(ref[:, 4:7], ref[:, 7:11])
+    scale = np.abs(Sr).reshape(len(Sr), -1).max(1)[:, None, None]
+    assert np.all(np.abs(Sg - Sr) <= 1e-5 * scale + 1e-12)
+
+
+def test_backward_matches_oracle_gradient():
+    """64 Gaussians at 32x32, SH degree 3: the GPU gradient of the mean L1 loss
+    equals the oracle's complex-step derivative of its FP64 forward."""
+    sc, cam = scenes.subscene_for_gradients(0)
+    tsc, _ = scenes.subscene_for_gradients(1, n=48)
+    tr = O.render(O.project(O.theta_of(tsc), 3, cam), cam)
+    target = tr["rgb"].astype(np.float32).reshape(32, 32, 3)
+    g, pr, bins, img = __import__("gpu_util").gpu_forward(sc, [cam])
+    tgt = torch.as_tensor(target.reshape(-1, 3), device=DEV)
+    grad = ops.render_backward(g, pr, bins, img, [cam], target=tgt)
+    torch.cuda.synchronize()
+    got = O.theta_of(grad.to_scene())
+    ref = O.grad(O.theta_of(sc), 3, cam, target)
+    groups = {"mean": slice(0, 3), "logit": slice(3, 4), "logscale": slice(4, 7),
+              "quat": slice(7, 11), "sh": slice(11, 59)}
+    for name, sl in groups.items():
+        a, b = got[:, sl], ref[:, sl]
+        tol = 2e-3 * np.abs(b).max() + 1e-12
+        assert np.abs(a - b).max() <= tol, (name, np.abs(a - b).max(), tol)
+    assert np.abs(ref).max() > 0
+
+
+def test_backward_upstream_gradient_and_views_sum():
+    """With an explicit dL/dI the gradient is linear in it; two identical views
+    give twice the gradient of one."""
+    sc, cams = small_cluster_inputs(3000, 128, 96, seed=21)
+    cam = cams[0]
+    g = ops.Gaussians.from_scene(sc, DEV)
+    pr1 = ops.project(g, [cam]); b1 = ops.bin_sort(g.n, pr1, [cam]); i1 = ops.render(g.n, pr1, b1, [cam])
+    up = torch.randn((cam["width"] * cam["height"], 3), device=DEV)
+    ga = ops.render_backward(g, pr1, b1, i1, [cam], dL_drgb=up)
+    gb = ops.render_backward(g, pr1, b1, i1, [cam], dL_drgb=2 * up)
+    pr2 = ops.project(g, [cam, cam]); b2 = ops.bin_sort(g.n, pr2, [cam, cam])
+    i2 = ops.render(g.n, pr2, b2, [cam, cam])
+    gc = ops.render_backward(g, pr2, b2, i2, [cam, cam], dL_drgb=torch.cat([up, up]))
+    torch.cuda.synchronize()
+    for a, b, c in zip(ga.tensors(), gb.tensors(), gc.tensors()):
+        sc_ = a.abs().max().item() + 1e-30
+        assert (2 * a - b).abs().max().item() <= 1e-5 * sc_
+        assert (2 * a - c).abs().max().item() <= 1e-4 * sc_
+
+
+def test_adam_matches_oracle():
+    rng = np.random.default_rng(4)
+    n, deg = 1000, 3
+    mk = lambda: {"mean": rng.normal(size=(n, 3)).astype(np.float32),
+                  "logit": rng.normal(size=n).astype(np.float32),
+                  "logscale": rng.normal(size=(n, 3)).astype(np.float32),
+                  "quat": rng.normal(size=(n, 4)).astype(np.float32),
+                  "sh": rng.normal(size=(n, 16, 3)).astype(np.float32), "sh_degree": deg}
+    p, gr, m = mk(), mk(), mk()
+    v = {k: (np.abs(x) if k != "sh_degree" else x) for k, x in mk().items()}
+    G = [ops.Gaussians.from_scene(d, DEV) for d in (p, gr, m, v)]
+    for step in (1, 2, 3):
+        ops.adam_step(G[0], G[1], G[2], G[3], step)
+    torch.cuda.synchronize()
+    th, g_, m_, v_ = (O.theta_of(d) for d in (p, gr, m, v))
+    for step in (1, 2, 3):
+        O.adam(th, g_, m_, v_, step)
+    np.testing.assert_allclose(O.theta_of(G[0].to_scene()), th, rtol=2e-5, atol=2e-6)
+    np.testing.assert_allclose(O.theta_of(G[2].to_scene()), m_, rtol=2e-5, atol=1e-6)
