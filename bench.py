@@ -230,7 +230,7 @@ def run_ours(args, rank, world, local_rank):
     dom = max(per_stage, key=per_stage.get)
     peak, peak_kind, _ = _peaks()
     achieved = sb[dom] / (per_stage[dom] * 1e-3) / 1e9
-    launches = count_launches(stepper, noise) * args.steps
+    launches = None if args.no_launch_count else count_launches(stepper, noise) * args.steps
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
@@ -359,6 +359,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-launch-count", action="store_true",
+                    help="skip the CUPTI kernel count (for runs under ncu)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

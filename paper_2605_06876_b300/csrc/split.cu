@@ -5,7 +5,7 @@
 // candidate index (keeping their (view, label) order), one thread per region
 // builds the child proposal (Eqs. 9-10, Appendix A), and one thread per
 // candidate merges its proposals (Eqs. 11-12: pairwise test, union-find,
-// enclosing covariance from an analytic 3x3 eigen-decomposition), applies the
+// enclosing covariance from a Jacobi 3x3 eigen-decomposition), applies the
 // n_max cap and writes the surviving children into a per-region child table.
 // Scans give every kept Gaussian its new index and every candidate the offset
 // of its appended block. This stage is small next to rendering, so it runs in
@@ -116,94 +116,45 @@ __device__ float4 rot_quat_d(const double* R) {
   return make_float4((float)(w / nq), (float)(x / nq), (float)(y / nq), (float)(z / nq));
 }
 
-// Eigenvectors (columns of E, right-handed) and eigenvalues of a symmetric
-// 3x3 matrix: trigonometric closed form for the eigenvalues, cross products of
-// the rows of A - lambda I for the eigenvectors; a repeated eigenvalue takes any
-// orthonormal basis of its eigenspace.
+// Eigen-decomposition of a symmetric 3x3 matrix by cyclic Jacobi rotations
+// (Rutishauser's update form); E gets the eigenvectors as columns. Jacobi keeps
+// eigenvectors accurate when eigenvalues are close, which the merged covariances
+// of clipped, nearly isotropic children need. At most 50 sweeps.
 __device__ void sym3_eigen(const double* A, double* lam, double* E) {
-  double a00 = A[0], a01 = A[1], a02 = A[2], a11 = A[4], a12 = A[5], a22 = A[8];
-  double p1 = a01 * a01 + a02 * a02 + a12 * a12;
-  double q = (a00 + a11 + a22) / 3.0;
-  double scale = fabs(a00) + fabs(a11) + fabs(a22) + 2.0 * sqrt(p1) + 1e-300;
-  for (int i = 0; i < 9; ++i) E[i] = (i % 4 == 0) ? 1.0 : 0.0;
-  if (p1 <= 1e-30 * scale * scale) {
-    lam[0] = a00; lam[1] = a11; lam[2] = a22;
-    return;
-  }
-  double p2 = (a00 - q) * (a00 - q) + (a11 - q) * (a11 - q) + (a22 - q) * (a22 - q) + 2.0 * p1;
-  double p = sqrt(p2 / 6.0);
-  double B[9];
-  for (int i = 0; i < 9; ++i) B[i] = (A[i] - ((i % 4 == 0) ? q : 0.0)) / p;
-  double detB = B[0] * (B[4] * B[8] - B[5] * B[7]) - B[1] * (B[3] * B[8] - B[5] * B[6]) +
-                B[2] * (B[3] * B[7] - B[4] * B[6]);
-  double r = fmin(1.0, fmax(-1.0, 0.5 * detB));
-  double phi = acos(r) / 3.0;
-  double l1 = q + 2.0 * p * cos(phi);
-  double l3 = q + 2.0 * p * cos(phi + 2.0943951023931957);
-  double l2 = 3.0 * q - l1 - l3;
-  lam[0] = l1; lam[1] = l2; lam[2] = l3;
-  double tol = 1e-9 * (fabs(l1) + fabs(l3) + 1e-300);
-  // eigenvector of a simple eigenvalue lm: the best cross product of two rows
-  auto simple_vec = [&](double lm, double* v) {
-    double r0[3] = {a00 - lm, a01, a02}, r1[3] = {a01, a11 - lm, a12}, r2[3] = {a02, a12, a22 - lm};
-    double c0[3], c1[3], c2[3];
-    cross3d(r0, r1, c0);
-    cross3d(r0, r2, c1);
-    cross3d(r1, r2, c2);
-    double n0 = dot3d(c0, c0), n1 = dot3d(c1, c1), n2 = dot3d(c2, c2);
-    const double* c = c0;
-    double nb = n0;
-    if (n1 > nb) { c = c1; nb = n1; }
-    if (n2 > nb) { c = c2; nb = n2; }
-    double inv = 1.0 / sqrt(nb);
-    for (int i = 0; i < 3; ++i) v[i] = c[i] * inv;
-  };
-  // a unit vector orthogonal to v (the largest column of A - lm I projected off v)
-  auto orth_in_space = [&](double lm, const double* v, double* out) {
-    double cols[3][3] = {{a00 - lm, a01, a02}, {a01, a11 - lm, a12}, {a02, a12, a22 - lm}};
-    double best = -1.0;
-    for (int k = 0; k < 3; ++k) {
-      double c[3] = {cols[k][0], cols[k][1], cols[k][2]};
-      double pr = dot3d(c, v);
-      for (int i = 0; i < 3; ++i) c[i] -= pr * v[i];
-      double nn = dot3d(c, c);
-      if (nn > best) {
-        best = nn;
-        for (int i = 0; i < 3; ++i) out[i] = c[i];
+  double a[3][3], v[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      a[i][j] = A[3 * i + j];
+      v[i][j] = i == j ? 1.0 : 0.0;
+    }
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+    double dia = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+    if (off == 0.0 || off <= 1e-32 * dia) break;
+    for (int pq = 0; pq < 3; ++pq) {
+      int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+      double apq = a[p][q];
+      if (apq == 0.0) continue;
+      double tau = (a[q][q] - a[p][p]) / (2.0 * apq);
+      double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+      double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+      int r = 3 - p - q;  // the untouched index
+      double arp = a[r][p], arq = a[r][q];
+      a[r][p] = a[p][r] = c * arp - s * arq;
+      a[r][q] = a[q][r] = s * arp + c * arq;
+      a[p][p] -= t * apq;
+      a[q][q] += t * apq;
+      a[p][q] = a[q][p] = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        double vkp = v[k][p], vkq = v[k][q];
+        v[k][p] = c * vkp - s * vkq;
+        v[k][q] = s * vkp + c * vkq;
       }
     }
-    if (best <= 0.0) {  // fall back to any perpendicular
-      double t[3] = {fabs(v[0]) < 0.9 ? 1.0 : 0.0, fabs(v[0]) < 0.9 ? 0.0 : 1.0, 0.0};
-      double pr = dot3d(t, v);
-      for (int i = 0; i < 3; ++i) out[i] = t[i] - pr * v[i];
-      best = dot3d(out, out);
-    }
-    double inv = 1.0 / sqrt(best);
-    for (int i = 0; i < 3; ++i) out[i] *= inv;
-  };
-  double v1[3], v2[3], v3[3];
-  if (l1 - l3 <= tol) {
-    return;  // all equal: identity basis
-  } else if (l1 - l2 <= tol) {  // top pair repeated, l3 simple
-    simple_vec(l3, v3);
-    orth_in_space(l3, v3, v1);
-    cross3d(v3, v1, v2);
-  } else if (l2 - l3 <= tol) {  // bottom pair repeated, l1 simple
-    simple_vec(l1, v1);
-    orth_in_space(l1, v1, v2);
-    cross3d(v1, v2, v3);
-  } else {
-    simple_vec(l1, v1);
-    simple_vec(l3, v3);
-    cross3d(v3, v1, v2);
-    double n2 = sqrt(dot3d(v2, v2));
-    for (int i = 0; i < 3; ++i) v2[i] /= n2;
-    cross3d(v1, v2, v3);
   }
   for (int i = 0; i < 3; ++i) {
-    E[3 * i + 0] = v1[i];
-    E[3 * i + 1] = v2[i];
-    E[3 * i + 2] = v3[i];
+    lam[i] = a[i][i];
+    for (int j = 0; j < 3; ++j) E[3 * i + j] = v[i][j];
   }
 }
 

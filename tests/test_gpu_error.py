@@ -68,7 +68,7 @@ def test_select_topk_bit_exact():
         assert np.array_equal(got, O.topk_mass(mass, k)), k
 
 
-@pytest.mark.parametrize("sizes,n_gauss,r", [([(97, 61)], 30, 1), ([(1280, 832)], 3000, 2),
+@pytest.mark.parametrize("sizes,n_gauss,r", [([(150, 110)], 30, 1), ([(1280, 832)], 3000, 2),
                                              ([(160, 100), (90, 70)], 200, 0)])
 def test_regions_bit_exact(sizes, n_gauss, r):
     img, tgt, dom = _inputs(sizes, n_gauss, 23)
