@@ -46,7 +46,12 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons during the timed region."""
+    """nvidia-smi clocks and throttle reasons, timestamped, every 20 ms; the
+    summary keeps the samples inside the timed window [t0, t1]."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
@@ -55,40 +60,47 @@ class ClockSampler:
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.fh = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}",
+                                          f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0, t1):
+        import datetime as dt
+
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.05)
         self.proc.terminate()
         self.proc.wait()
         self.fh.close()
-        sm, mx, reasons = [], [], set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                ts = dt.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(f[2]), float(f[3]),
+                             [nm for nm, v in zip(names, f[6:10]) if v.lower() == "active"]))
             except ValueError:
                 continue
-            for name, val in zip(names, f[5:9]):
-                if val.lower() == "active":
-                    reasons.add(name)
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        note = "inside the timed region"
+        if not inside and rows:  # a very short timed region: nearest samples
+            rows.sort(key=lambda r: min(abs(r[0] - t0), abs(r[0] - t1)))
+            inside = rows[:3]
+            note = "nearest samples to a timed region shorter than the sampling period"
+        sm = [r[1] for r in inside]
+        reasons = sorted({x for r in inside for x in r[3]})
         return {"sm_mhz": float(np.median(sm)) if sm else None,
-                "sm_max_mhz": float(max(mx)) if mx else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "sm_max_mhz": float(max(r[2] for r in inside)) if inside else None,
+                "reasons": reasons, "samples": len(inside), "window": note}
 
 
 # --------------------------------------------------------------------------- algorithmic bytes
@@ -141,6 +153,8 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
+    sampler = ClockSampler(local_rank)
+    sampler.start()
     for _ in range(args.warmup):
         stepper.step(noise)
     torch.cuda.synchronize()
@@ -152,10 +166,9 @@ def run_ours(args, rank, world, local_rank):
             import torch.distributed as dist
             dist.barrier()
 
-    sampler = ClockSampler(local_rank)
-    sampler.start()
     barrier()
     torch.cuda.synchronize()
+    t_wall0 = time.time()
     step_ms = []
     stage_ms = {}
     new_n = 0
@@ -171,7 +184,7 @@ def run_ours(args, rank, world, local_rank):
         new_n = out[3].new_n
     barrier()
     torch.cuda.synchronize()
-    clocks = sampler.stop()
+    clocks = sampler.stop(t_wall0, time.time())
     if not stepper.check_capacity():
         raise RuntimeError("instance or region capacity exceeded in the timed region")
     total_ms = float(sum(step_ms))

@@ -174,11 +174,17 @@ __global__ void erode_v_kernel(const uint8_t* tmp, uint8_t* mask, CamSet cs, int
 
 // ------------------------------------------------------------------ labelling
 
+// Root of a with path halving: each visited node is re-pointed at its
+// grandparent. A node is re-pointed only while it is not a root and only to one
+// of its own ancestors, so a concurrent link made by uf_unite is never lost: a
+// union whose atomicMin finds its node already re-pointed retries from there.
 __device__ __forceinline__ int uf_find(volatile int* L, int a) {
-  int b = L[a];
-  while (b != a) {
-    a = b;
-    b = L[a];
+  int p = L[a];
+  while (p != a) {
+    int gp = L[p];
+    if (gp != p) L[a] = gp;
+    a = p;
+    p = gp;
   }
   return a;
 }
