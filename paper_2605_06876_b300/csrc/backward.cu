@@ -6,7 +6,7 @@
 // storing it, and the normalised colour behind it by the recurrence
 // R <- alpha c + (1 - alpha) R starting from the background. Per Gaussian it
 // yields dL/d(mean2d, conic, opacity, rgb); a warp reduces the 32 pixels'
-// contributions before one vector atomic per record.
+// contributions (a reduce-scatter) before nine scalar atomics per record.
 // Pass 2 (one thread per Gaussian): chains those 2D gradients through the
 // EWA projection and the SH colour of every view and sums over views, so the
 // per-Gaussian parameters are read and the gradients written once per step.
@@ -31,15 +31,35 @@ struct BwdPixArgs {
   float4* g2d;  // [V*n][3]
 };
 
-__device__ __forceinline__ void atomic_add4(float4* p, float4 v) {
-#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 900)
-  atomicAdd(p, v);
-#else
-  atomicAdd(&p->x, v.x);
-  atomicAdd(&p->y, v.y);
-  atomicAdd(&p->z, v.z);
-  atomicAdd(&p->w, v.w);
-#endif
+// Reduce-scatter of eight per-lane values across the warp by recursive halving:
+// at each of three levels a lane keeps half of its values and sends the other
+// half to its partner, then two plain steps finish. Lane l ends with the warp
+// total of value index ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 + ((l >> 2) & 1)
+// (the same in all four lanes of its quad): nine shuffles instead of forty.
+__device__ __forceinline__ float reduce_scatter8(const float* v, int* idx) {
+  const int lane = threadIdx.x & 31;
+  const bool b16 = (lane >> 4) & 1, b8 = (lane >> 3) & 1, b4 = (lane >> 2) & 1;
+  float u[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float keep = b16 ? v[4 + i] : v[i];
+    float send = b16 ? v[i] : v[4 + i];
+    u[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  float w[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    float keep = b8 ? u[2 + i] : u[i];
+    float send = b8 ? u[i] : u[2 + i];
+    w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float keep = b4 ? w[1] : w[0];
+  float send = b4 ? w[0] : w[1];
+  float x = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  x += __shfl_xor_sync(0xffffffffu, x, 2);
+  x += __shfl_xor_sync(0xffffffffu, x, 1);
+  *idx = (b16 ? 4 : 0) + (b8 ? 2 : 0) + (b4 ? 1 : 0);
+  return x;
 }
 
 __global__ void __launch_bounds__(256) bwd_pixel_kernel(BwdPixArgs a, CamSet cs) {
@@ -135,22 +155,15 @@ __global__ void __launch_bounds__(256) bwd_pixel_kernel(BwdPixArgs a, CamSet cs)
       }
       unsigned any = __ballot_sync(0xffffffffu, hit);
       if (any) {
-        dmx = warp_sum(dmx);
-        dmy = warp_sum(dmy);
-        dA = warp_sum(dA);
-        dB = warp_sum(dB);
-        dC = warp_sum(dC);
-        dop = warp_sum(dop);
-        dr = warp_sum(dr);
-        dg = warp_sum(dg);
+        float v8[8] = {dmx, dmy, dA, dB, dC, dop, dr, dg};
+        int idx;
+        float sum = reduce_scatter8(v8, &idx);
         db = warp_sum(db);
-        if ((threadIdx.x & 31) == 0) {
-          int id = __float_as_int(s_g2[k].y);
-          float4* g = a.g2d + 3 * (rec_base + id);
-          atomic_add4(g, make_float4(dmx, dmy, dA, dB));
-          atomic_add4(g + 1, make_float4(dC, dop, dr, dg));
-          atomicAdd(&g[2].x, db);
-        }
+        int id = __float_as_int(s_g2[k].y);
+        float* g = reinterpret_cast<float*>(a.g2d + 3 * (rec_base + id));
+        const int lane = threadIdx.x & 31;
+        if ((lane & 3) == 0) atomicAdd(g + idx, sum);
+        if (lane == 0) atomicAdd(g + 8, db);
       }
     }
   }
@@ -177,6 +190,16 @@ __global__ void __launch_bounds__(128) bwd_gauss_kernel(BwdGaussArgs a, CamSet c
   if (i >= a.n) return;
   const int K = sh_coeffs(a.deg);
   const int planes = sh_planes(a.deg);
+  bool seen = false;
+  for (int v = 0; v < cs.n_views; ++v) seen |= a.tiles[(long long)v * a.n + i] > 0;
+  if (!seen) {  // rendered in no view: every gradient is zero
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    a.g_ml[i] = z;
+    a.g_ls[i] = z;
+    a.g_q[i] = z;
+    for (int p = 0; p < planes; ++p) reinterpret_cast<float4*>(a.g_sh)[(long long)p * a.n + i] = z;
+    return;
+  }
   float4 ml = a.mean_logit[i], ls = a.logscale[i], q4 = a.quat[i];
   float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
   float iq = rsqrtf(qn2);

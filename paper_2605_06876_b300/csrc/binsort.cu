@@ -17,26 +17,33 @@ __global__ void clamp_count_kernel(const long long* K, long long cap, long long*
   *Kc = k <= cap ? k : 0;
 }
 
+// One thread per instance k: the record owning k is found by binary search in
+// the instance offsets, and k's tile is its position within the record's tile
+// rectangle (row-major). Balanced whatever a Gaussian's footprint, and the
+// writes of consecutive threads are consecutive.
 __global__ void duplicate_kernel(const unsigned* vvals, const long long* offs,
                                  const long long* d_nvis, const long long* d_K, long long cap,
                                  const int4* rect, long long n, CamSet cs, unsigned* tkeys,
                                  int* inst) {
-  long long N = *d_nvis;
-  if (*d_K > cap) return;
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < N;
-       j += (long long)gridDim.x * blockDim.x) {
-    unsigned p = vvals[j];
+  const long long N = *d_nvis, K = *d_K;
+  if (K > cap || N == 0) return;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < K;
+       k += (long long)gridDim.x * blockDim.x) {
+    long long lo = 0, hi = N - 1;  // last j with offs[j] <= k
+    while (lo < hi) {
+      long long mid = (lo + hi + 1) >> 1;
+      if (offs[mid] <= k) lo = mid;
+      else hi = mid - 1;
+    }
+    unsigned p = vvals[lo];
     int v = (int)(p / (unsigned long long)n);
     int i = (int)(p - (unsigned long long)v * n);
     int4 r = rect[p];
-    long long o = offs[j];
-    int base = cs.tile_base[v], tx = cs.tiles_x[v];
-    for (int ty = r.z; ty <= r.w; ++ty)
-      for (int tx0 = r.x; tx0 <= r.y; ++tx0) {
-        tkeys[o] = (unsigned)(base + ty * tx + tx0);
-        inst[o] = i;
-        ++o;
-      }
+    int w = r.y - r.x + 1;
+    int t = (int)(k - offs[lo]);
+    int ty = r.z + t / w, tx = r.x + t % w;
+    tkeys[k] = (unsigned)(cs.tile_base[v] + ty * cs.tiles_x[v] + tx);
+    inst[k] = i;
   }
 }
 
@@ -146,7 +153,7 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
 
   // 4. duplicate into tiles, 5. stable sort by tile
   if (cap > 0) {
-    duplicate_kernel<<<grid_for(nv, 256, 148 * 16), 256, 0, st>>>(
+    duplicate_kernel<<<grid_for(cap, 256, 148 * 32), 256, 0, st>>>(
         vvals, offs, &w.counters[0], (const long long*)bins->n_instances, cap,
         reinterpret_cast<const int4*>(pr->rect), n, cs, w.tkeys, bins->inst_gauss);
     ADP_LAUNCH_CHECK();

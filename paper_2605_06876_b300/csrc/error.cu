@@ -4,8 +4,9 @@
 //    correctly rounded operations, and the per-Gaussian attribution (count,
 //    mass) with warp-aggregated atomics;
 //  - top-k error mass by an 8-pass radix select on the 64-bit mass keys;
-//  - erosion (separable min filter), 8-connected labelling by a lock-free
-//    union-find whose roots are the smallest pixel index of each component,
+//  - erosion (separable min filter), 8-connected labelling by a union-find whose
+//    roots are the smallest pixel index of each component (per 32x32 tile in
+//    shared memory first, then across tile borders in global memory),
 //    exact int64 region moments, the area filter and the FP64 region statistics.
 #include "common.cuh"
 
@@ -120,19 +121,35 @@ __global__ void topk_hist_kernel(const double* mass, long long n, int shift,
   if (s_h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], s_h[threadIdx.x]);
 }
 
-// Picks the digit (scanning from the largest) holding the remaining-th largest key.
+// Picks the digit holding the remaining-th largest key: a suffix sum of the 256
+// bin counts (from the largest digit down) and the one bin where it first
+// reaches the remaining count. One block of 256 threads.
 __global__ void topk_pick_kernel(unsigned* hist, int shift, SelectState* st) {
-  if (threadIdx.x != 0) return;
-  long long rem = st->remaining, cum = 0;
-  int b = 255;
-  for (; b > 0; --b) {
-    if (cum + hist[b] >= rem) break;
-    cum += hist[b];
+  __shared__ long long s_w[8];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int b = 255 - t;  // thread t handles digit 255 - t, so prefixes run downwards
+  long long c = hist[b];
+  long long inc = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    long long y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
   }
-  st->remaining = rem - cum;
-  st->prefix |= (unsigned long long)b << shift;
-  st->mask |= 255ull << shift;
-  for (int k = 0; k < 256; ++k) hist[k] = 0;
+  if (lane == 31) s_w[w] = inc;
+  __syncthreads();
+  long long pre = 0;
+  for (int k = 0; k < w; ++k) pre += s_w[k];
+  long long suf = pre + inc;  // count of keys in digits >= b
+  __syncthreads();
+  const long long rem = st->remaining;
+  long long above = suf - c;  // keys in digits > b
+  const bool pick = suf >= rem && above < rem;  // exactly one digit satisfies this
+  __syncthreads();
+  if (pick) {
+    st->remaining = rem - above;
+    st->prefix |= (unsigned long long)b << shift;
+    st->mask |= 255ull << shift;
+  }
+  hist[b] = 0;
 }
 
 // ------------------------------------------------------------------ erosion
@@ -221,25 +238,118 @@ __global__ void ccl_init_kernel(const uint8_t* mask, const int* dom, const uint8
     L[p] = region_pixel(mask, dom, cand, n, p) ? (int)p : -1;
 }
 
-__global__ void ccl_union_kernel(const uint8_t* mask, const int* dom, CamSet cs, int* L) {
+// Same-class test of two participating pixels: equal dominant Gaussian and band.
+__device__ __forceinline__ bool same_class(const int* L, const int* dom, const uint8_t* mask,
+                                           long long p, long long q) {
+  return L[q] >= 0 && dom[q] == dom[p] && (mask[q] >> 4) == (mask[p] >> 4);
+}
+
+constexpr int CCL_T = 32;  // labelling tile edge (32 x 32 pixels per CTA)
+
+__device__ __forceinline__ int sfind(volatile int* l, int a) {
+  int p = l[a];
+  while (p != a) {
+    int gp = l[p];
+    if (gp != p) l[a] = gp;
+    a = p;
+    p = gp;
+  }
+  return a;
+}
+
+__device__ void sunite(int* l, int a, int b) {
+  volatile int* vl = l;
+  for (int guard = 0; guard < 4096; ++guard) {
+    a = sfind(vl, a);
+    b = sfind(vl, b);
+    if (a == b) return;
+    if (a > b) {
+      int t = a;
+      a = b;
+      b = t;
+    }
+    int old = atomicMin(&l[b], a);
+    if (old == b) return;
+    b = old;
+  }
+}
+
+// Labelling inside one 32x32 tile in shared memory, then every pixel points at
+// its tile-local root by global index. The skip rules drop edges that another
+// edge of the 8-neighbourhood already implies: up-left when left or up is
+// joined, up-right when up is joined.
+__global__ void __launch_bounds__(256) ccl_local_kernel(const uint8_t* mask, const int* dom,
+                                                        CamSet cs, int* L) {
+  __shared__ int s_l[CCL_T * CCL_T];
+  __shared__ int s_d[CCL_T * CCL_T];
+  __shared__ uint8_t s_b[CCL_T * CCL_T];
+  const int v = blockIdx.y;
+  const int W = cs.cam[v].width, H = cs.cam[v].height;
+  const int ntx = (W + CCL_T - 1) / CCL_T, nty = (H + CCL_T - 1) / CCL_T;
+  if ((int)blockIdx.x >= ntx * nty) return;
+  const int tx0 = (blockIdx.x % ntx) * CCL_T, ty0 = (blockIdx.x / ntx) * CCL_T;
+  const long long base = cs.pix_base[v];
+  for (int li = threadIdx.x; li < CCL_T * CCL_T; li += blockDim.x) {
+    int x = tx0 + (li & (CCL_T - 1)), y = ty0 + li / CCL_T;
+    int lab = -1, d = -1;
+    uint8_t b = 0;
+    if (x < W && y < H) {
+      long long p = base + (long long)y * W + x;
+      if (L[p] >= 0) {
+        lab = li;
+        d = dom[p];
+        b = mask[p] >> 4;
+      }
+    }
+    s_l[li] = lab;
+    s_d[li] = d;
+    s_b[li] = b;
+  }
+  __syncthreads();
+  for (int li = threadIdx.x; li < CCL_T * CCL_T; li += blockDim.x) {
+    if (s_l[li] < 0) continue;
+    int lx = li & (CCL_T - 1), ly = li / CCL_T;
+    auto same = [&](int q) { return s_l[q] >= 0 && s_d[q] == s_d[li] && s_b[q] == s_b[li]; };
+    bool left = lx > 0 && same(li - 1);
+    bool up = ly > 0 && same(li - CCL_T);
+    if (left) sunite(s_l, li, li - 1);
+    if (up) sunite(s_l, li, li - CCL_T);
+    if (!left && !up && lx > 0 && ly > 0 && same(li - CCL_T - 1)) sunite(s_l, li, li - CCL_T - 1);
+    if (!up && lx < CCL_T - 1 && ly > 0 && same(li - CCL_T + 1)) sunite(s_l, li, li - CCL_T + 1);
+  }
+  __syncthreads();
+  for (int li = threadIdx.x; li < CCL_T * CCL_T; li += blockDim.x) {
+    int x = tx0 + (li & (CCL_T - 1)), y = ty0 + li / CCL_T;
+    if (x >= W || y >= H || s_l[li] < 0) continue;
+    int r = sfind(s_l, li);
+    int rx = tx0 + (r & (CCL_T - 1)), ry = ty0 + r / CCL_T;
+    L[base + (long long)y * W + x] = (int)(base + (long long)ry * W + rx);
+  }
+}
+
+// The edges of the 8-neighbourhood that cross a tile border, with the same skip
+// rules, joined in the global union-find.
+__global__ void ccl_border_kernel(const uint8_t* mask, const int* dom, CamSet cs, int* L) {
   const int v = blockIdx.y;
   const int W = cs.cam[v].width, H = cs.cam[v].height;
   const long long P = (long long)W * H, base = cs.pix_base[v];
   for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < P;
        u += (long long)gridDim.x * blockDim.x) {
+    int x = (int)(u % W), y = (int)(u / W);
+    int lx = x & (CCL_T - 1), ly = y & (CCL_T - 1);
+    if (lx != 0 && ly != 0 && lx != CCL_T - 1) continue;
     long long p = base + u;
     if (L[p] < 0) continue;
-    int x = (int)(u % W), y = (int)(u / W);
-    int d = dom[p];
-    uint8_t b = mask[p] >> 4;
-    const int nx[4] = {-1, -1, 0, 1}, ny[4] = {0, -1, -1, -1};
-    for (int k = 0; k < 4; ++k) {
-      int xx = x + nx[k], yy = y + ny[k];
-      if (xx < 0 || xx >= W || yy < 0) continue;
-      long long q = base + (long long)yy * W + xx;
-      if (L[q] < 0 || dom[q] != d || (mask[q] >> 4) != b) continue;
-      uf_unite(L, (int)p, (int)q);
-    }
+    bool left = x > 0 && same_class(L, dom, mask, p, p - 1);
+    bool up = y > 0 && same_class(L, dom, mask, p, p - W);
+    if (left && lx == 0) uf_unite(L, (int)p, (int)(p - 1));
+    if (up && ly == 0) uf_unite(L, (int)p, (int)(p - W));
+    if (!left && !up && x > 0 && y > 0 && (lx == 0 || ly == 0) &&
+        same_class(L, dom, mask, p, p - W - 1))
+      uf_unite(L, (int)p, (int)(p - W - 1));
+    if (!up && x < W - 1 && y > 0 && (lx == CCL_T - 1 || ly == 0) &&
+        same_class(L, dom, mask, p, p - W + 1))
+      uf_unite(L, (int)p, (int)(p - W + 1));
   }
 }
 
@@ -502,7 +612,7 @@ extern "C" ADP_API int adp_select_topk(const double* mass, int64_t n, int64_t k,
   unsigned g = grid_for(n, 256, 148 * 8);
   for (int shift = 56; shift >= 0; shift -= 8) {
     topk_hist_kernel<<<g, 256, 0, st>>>(mass, n, shift, ss, hist);
-    topk_pick_kernel<<<1, 32, 0, st>>>(hist, shift, ss);
+    topk_pick_kernel<<<1, 256, 0, st>>>(hist, shift, ss);
   }
   ADP_LAUNCH_CHECK();
   // keys above the threshold, plus the first `remaining` equal ones by id
@@ -599,7 +709,15 @@ extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* do
   // labelling
   unsigned gp = grid_for(P, 256, 148 * 16);
   ccl_init_kernel<<<gp, 256, 0, st>>>(maps->mask, dominant, w.cand, n, P, w.L);
-  ccl_union_kernel<<<grid, 256, 0, st>>>(maps->mask, dominant, cs, w.L);
+  {
+    int max_tiles = 0;
+    for (int v = 0; v < n_views; ++v) {
+      int t = ((cs.cam[v].width + CCL_T - 1) / CCL_T) * ((cs.cam[v].height + CCL_T - 1) / CCL_T);
+      max_tiles = t > max_tiles ? t : max_tiles;
+    }
+    ccl_local_kernel<<<dim3(max_tiles, n_views), 256, 0, st>>>(maps->mask, dominant, cs, w.L);
+    ccl_border_kernel<<<grid, 256, 0, st>>>(maps->mask, dominant, cs, w.L);
+  }
   ccl_flatten_kernel<<<gp, 256, 0, st>>>(w.L, P);
   ADP_LAUNCH_CHECK();
   // roots -> slots
