@@ -1,5 +1,5 @@
 // One bias-corrected Adam step over every parameter plane (the optimizer the
-// paper leaves unchanged, Sec. 5.1): one thread per Gaussian, float4 traffic,
+// paper leaves unchanged, Sec. 5.1): one thread per float4 of each plane,
 // parameters, moments and gradients each read once and written once.
 #include "common.cuh"
 
@@ -37,16 +37,23 @@ __device__ __forceinline__ void adam4(float4* P, const float4* G, float4* M, flo
   V[idx] = v;
 }
 
+// blockIdx.y selects the plane: 0 mean+logit, 1 log-scale, 2 quaternion,
+// 3.. SH planes; each thread updates one float4 of it.
 __global__ void adam_kernel(AdamArgs a) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= a.n) return;
-  float lr_ml[4] = {a.lr[0], a.lr[0], a.lr[0], a.lr[1]};
-  float lr_ls[4] = {a.lr[2], a.lr[2], a.lr[2], 0.f};
-  float lr_q[4] = {a.lr[3], a.lr[3], a.lr[3], a.lr[3]};
-  adam4(a.p_ml, a.g_ml, a.m_ml, a.v_ml, i, lr_ml, a);
-  adam4(a.p_ls, a.g_ls, a.m_ls, a.v_ls, i, lr_ls, a);
-  adam4(a.p_q, a.g_q, a.m_q, a.v_q, i, lr_q, a);
-  for (int p = 0; p < a.planes; ++p) {
+  const int q = blockIdx.y;
+  if (q == 0) {
+    float lr4[4] = {a.lr[0], a.lr[0], a.lr[0], a.lr[1]};
+    adam4(a.p_ml, a.g_ml, a.m_ml, a.v_ml, i, lr4, a);
+  } else if (q == 1) {
+    float lr4[4] = {a.lr[2], a.lr[2], a.lr[2], 0.f};
+    adam4(a.p_ls, a.g_ls, a.m_ls, a.v_ls, i, lr4, a);
+  } else if (q == 2) {
+    float lr4[4] = {a.lr[3], a.lr[3], a.lr[3], a.lr[3]};
+    adam4(a.p_q, a.g_q, a.m_q, a.v_q, i, lr4, a);
+  } else {
+    const int p = q - 3;
     float lr4[4];
     for (int l = 0; l < 4; ++l) lr4[l] = (4 * p + l) < 3 ? a.lr[4] : a.lr[5];
     adam4(a.p_sh, a.g_sh, a.m_sh, a.v_sh, (long long)p * a.n + i, lr4, a);
@@ -83,7 +90,7 @@ extern "C" ADP_API int adp_adam_step(adp_gaussians* param, const adp_gaussians* 
   a.eps = eps;
   a.bc1 = 1.f - powf(beta1, (float)step);
   a.bc2 = 1.f - powf(beta2, (float)step);
-  adam_kernel<<<grid_for(param->n, 256), 256, 0, (cudaStream_t)stream>>>(a);
+  adam_kernel<<<dim3(grid_for(param->n, 256), 3 + a.planes), 256, 0, (cudaStream_t)stream>>>(a);
   ADP_LAUNCH_CHECK();
   return ADP_OK;
 }

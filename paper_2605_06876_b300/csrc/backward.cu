@@ -7,7 +7,7 @@
 // R <- alpha c + (1 - alpha) R starting from the background. Per Gaussian it
 // yields dL/d(mean2d, conic, opacity, rgb); a warp reduces the 32 pixels'
 // contributions (a reduce-scatter) before nine scalar atomics per record.
-// Pass 2 (one thread per Gaussian): chains those 2D gradients through the
+// Pass 2 (one thread per visible Gaussian): chains those 2D gradients through the
 // EWA projection and the SH colour of every view and sums over views, so the
 // per-Gaussian parameters are read and the gradients written once per step.
 #include "gauss_math.cuh"
@@ -101,7 +101,9 @@ __global__ void __launch_bounds__(256) bwd_pixel_kernel(BwdPixArgs a, CamSet cs)
   }
   if (threadIdx.x == 0) s_maxlast = 0;
   __syncthreads();
-  if (my_last > 0) atomicMax(&s_maxlast, my_last);
+  int warp_last = my_last;  // positions at or beyond it have no work in this warp
+  for (int o = 16; o > 0; o >>= 1) warp_last = max(warp_last, __shfl_xor_sync(0xffffffffu, warp_last, o));
+  if ((threadIdx.x & 31) == 0 && warp_last > 0) atomicMax(&s_maxlast, warp_last);
   __syncthreads();
   const int end = s_maxlast;
   float R0 = a.bg[0], R1 = a.bg[1], R2 = a.bg[2];
@@ -118,20 +120,21 @@ __global__ void __launch_bounds__(256) bwd_pixel_kernel(BwdPixArgs a, CamSet cs)
       s_g2[threadIdx.x] = make_float2(p2.z, __int_as_float(id));
     }
     __syncthreads();
-    for (int k = b1 - b0 - 1; k >= 0; --k) {
+    const int kmax = min(b1, warp_last) - b0;  // warp-uniform
+    for (int k = kmax - 1; k >= 0; --k) {
       int pos = b0 + k;
       float4 q0 = s_g0[k], q1 = s_g1[k];
       float dmx = 0.f, dmy = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dop = 0.f, dr = 0.f, dg = 0.f,
             db = 0.f;
       bool hit = false;
       if (pos < my_last) {
-        float dx, dy;
-        float ar = alpha_raw(q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, fx, fy, &dx, &dy);
+        float dx, dy, G;
+        float ar = alpha_raw_g(q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, fx, fy, &dx, &dy, &G);
         if (ar >= a.alpha_min) {
           hit = true;
           float al = fminf(a.alpha_max, ar);
           float c2 = s_g2[k].x;
-          float Tj = T / (1.f - al);
+          float Tj = T * __frcp_rn(1.f - al);
           float dal = Tj * (g0 * (q1.z - R0) + g1 * (q1.w - R1) + g2 * (c2 - R2));
           float wgt = Tj * al;
           dr = wgt * g0;
@@ -142,7 +145,6 @@ __global__ void __launch_bounds__(256) bwd_pixel_kernel(BwdPixArgs a, CamSet cs)
           R2 = al * c2 + (1.f - al) * R2;
           T = Tj;
           if (ar <= a.alpha_max) {
-            float G = ar / q1.y;
             dop = dal * G;
             float dpow = dal * ar;
             dA = -0.5f * dx * dx * dpow;
@@ -183,23 +185,47 @@ struct BwdGaussArgs {
   float4* g_ls;
   float4* g_q;
   float* g_sh;
+  const int* list;
+  const unsigned long long* n_list;
 };
 
+// Zeroes the gradient of every Gaussian rendered in no view and appends the
+// others to a list (warp-aggregated), so the heavy chain-rule pass runs on full
+// warps of visible Gaussians only. The list order does not affect the results.
+__global__ void bwd_visible_kernel(const int* tiles, long long n, int n_views, int planes,
+                                   float4* g_ml, float4* g_ls, float4* g_q, float4* g_sh,
+                                   int* list, unsigned long long* count) {
+  for (long long i0 = blockIdx.x * (long long)blockDim.x; i0 < n;
+       i0 += (long long)gridDim.x * blockDim.x) {
+    long long i = i0 + threadIdx.x;
+    bool seen = false;
+    if (i < n) {
+      for (int v = 0; v < n_views; ++v) seen |= tiles[(long long)v * n + i] > 0;
+      if (!seen) {
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        g_ml[i] = z;
+        g_ls[i] = z;
+        g_q[i] = z;
+        for (int p = 0; p < planes; ++p) g_sh[(long long)p * n + i] = z;
+      }
+    }
+    unsigned m = __ballot_sync(0xffffffffu, seen);
+    if (m) {
+      unsigned long long base = 0;
+      int lane = threadIdx.x & 31;
+      if (lane == __ffs(m) - 1) base = atomicAdd(count, (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+      if (seen) list[base + __popc(m & lanemask_lt())] = (int)i;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(128) bwd_gauss_kernel(BwdGaussArgs a, CamSet cs) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)*a.n_list) return;
+  const long long i = a.list[t];
   const int K = sh_coeffs(a.deg);
   const int planes = sh_planes(a.deg);
-  bool seen = false;
-  for (int v = 0; v < cs.n_views; ++v) seen |= a.tiles[(long long)v * a.n + i] > 0;
-  if (!seen) {  // rendered in no view: every gradient is zero
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    a.g_ml[i] = z;
-    a.g_ls[i] = z;
-    a.g_q[i] = z;
-    for (int p = 0; p < planes; ++p) reinterpret_cast<float4*>(a.g_sh)[(long long)p * a.n + i] = z;
-    return;
-  }
   float4 ml = a.mean_logit[i], ls = a.logscale[i], q4 = a.quat[i];
   float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
   float iq = rsqrtf(qn2);
@@ -369,7 +395,8 @@ using namespace adp;
 
 extern "C" ADP_API size_t adp_render_backward_workspace_size(int64_t n, int32_t n_views) {
   if (n < 0 || n_views < 1) return 0;
-  return carve_bytes<float4>(3 * (size_t)n * n_views);
+  return carve_bytes<float4>(3 * (size_t)n * n_views) + carve_bytes<int>(n) +
+         carve_bytes<unsigned long long>(1);
 }
 
 extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_projected* pr,
@@ -392,8 +419,12 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   ADP_CHECK_ARG(ws_bytes >= need, "workspace %zu bytes, need %zu", ws_bytes, need);
   if (g->n == 0) return ADP_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  float4* g2d = static_cast<float4*>(ws);
+  Carver cv(ws, ws_bytes);
+  float4* g2d = cv.take<float4>(3 * (size_t)g->n * n_views);
+  int* list = cv.take<int>(g->n);
+  unsigned long long* n_list = cv.take<unsigned long long>(1);
   ADP_CUDA(cudaMemsetAsync(g2d, 0, sizeof(float4) * 3 * (size_t)g->n * n_views, st));
+  ADP_CUDA(cudaMemsetAsync(n_list, 0, sizeof(unsigned long long), st));
   BwdPixArgs pa;
   pa.xyod = reinterpret_cast<const float4*>(pr->xy_opacity_depth);
   pa.conic = reinterpret_cast<const float4*>(pr->conic);
@@ -426,6 +457,11 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   ga.g_ls = reinterpret_cast<float4*>(grad->logscale);
   ga.g_q = reinterpret_cast<float4*>(grad->quat);
   ga.g_sh = grad->sh;
+  ga.list = list;
+  ga.n_list = n_list;
+  bwd_visible_kernel<<<grid_for(g->n, 256, 148 * 16), 256, 0, st>>>(
+      pr->tiles_touched, g->n, n_views, sh_planes(g->sh_degree), ga.g_ml, ga.g_ls, ga.g_q,
+      reinterpret_cast<float4*>(grad->sh), list, n_list);
   bwd_gauss_kernel<<<grid_for(g->n, 128), 128, 0, st>>>(ga, cs);
   ADP_LAUNCH_CHECK();
   return ADP_OK;

@@ -148,37 +148,48 @@ __global__ void rs_scan_kernel(unsigned* hist, const long long* d_n, long long t
   if (threadIdx.x == 0) digit_tot[blockIdx.x] = s_carry;
 }
 
+// Block-wide exclusive scan of one value per thread (RS_THREADS threads).
+__device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned* s_w) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned inc = x;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_w[warp] = inc;
+  __syncthreads();
+  unsigned pre = 0;
+  for (int k = 0; k < warp; ++k) pre += s_w[k];
+  __syncthreads();
+  return pre + inc - x;
+}
+
+// Stable scatter of one pass. Ranks come from warp match masks in item order;
+// the tile is first reordered by digit in shared memory, so each digit's run is
+// written to global memory by consecutive threads.
 __global__ void __launch_bounds__(RS_THREADS)
     rs_scatter_kernel(const unsigned* keys_in, const unsigned* vals_in, unsigned* keys_out,
                       unsigned* vals_out, const long long* d_n, long long tiles_max, DigitOp op,
                       const unsigned* hist, const unsigned* digit_tot) {
-  __shared__ unsigned s_base[RS_BINS];           // exclusive scan of digit totals
+  __shared__ unsigned s_base[RS_BINS];             // global start of every digit
   __shared__ unsigned s_whist[RS_WARPS][RS_BINS];  // per-warp counts, then warp prefixes
+  __shared__ unsigned s_lbase[RS_BINS];            // start of every digit within the tile
+  __shared__ unsigned s_gpos[RS_BINS];             // global start of the tile's digit run
+  __shared__ unsigned s_w[RS_WARPS];
+  __shared__ unsigned s_keys[RS_TILE];
+  __shared__ unsigned s_vals[RS_TILE];
   long long N = *d_n;
   long long nt = (N + RS_TILE - 1) / RS_TILE;
   if (nt > tiles_max) nt = tiles_max;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // exclusive scan of the 256 digit totals (once per block)
-  {
-    unsigned x = digit_tot[threadIdx.x];
-    unsigned inc = x;
-    for (int o = 1; o < 32; o <<= 1) {
-      unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
-    }
-    __shared__ unsigned s_w[RS_WARPS];
-    if (lane == 31) s_w[warp] = inc;
-    __syncthreads();
-    unsigned pre = 0;
-    for (int k = 0; k < warp; ++k) pre += s_w[k];
-    s_base[threadIdx.x] = pre + inc - x;
-    __syncthreads();
-  }
+  s_base[threadIdx.x] = block_excl_scan(digit_tot[threadIdx.x], s_w);
   const unsigned lt = lanemask_lt();
   for (long long t = blockIdx.x; t < nt; t += gridDim.x) {
     for (int d = threadIdx.x; d < RS_WARPS * RS_BINS; d += RS_THREADS) (&s_whist[0][0])[d] = 0;
     __syncthreads();
-    long long base = t * RS_TILE + (long long)warp * (RS_ROUNDS * 32);
+    const long long tile0 = t * RS_TILE;
+    const int in_tile = (int)min((long long)RS_TILE, N - tile0);
+    const long long base = tile0 + (long long)warp * (RS_ROUNDS * 32);
     unsigned key[RS_ROUNDS], val[RS_ROUNDS], dig[RS_ROUNDS], off[RS_ROUNDS];
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
@@ -196,7 +207,8 @@ __global__ void __launch_bounds__(RS_THREADS)
       __syncwarp();
     }
     __syncthreads();
-    {  // per-digit exclusive prefix over warps
+    unsigned cnt;
+    {  // per-digit exclusive prefix over warps, and the tile's count of the digit
       int d = threadIdx.x;
       unsigned run = 0;
       for (int w2 = 0; w2 < RS_WARPS; ++w2) {
@@ -204,17 +216,29 @@ __global__ void __launch_bounds__(RS_THREADS)
         s_whist[w2][d] = run;
         run += c;
       }
+      cnt = run;
     }
+    unsigned lb = block_excl_scan(cnt, s_w);
+    s_lbase[threadIdx.x] = lb;
+    s_gpos[threadIdx.x] = s_base[threadIdx.x] + hist[(size_t)threadIdx.x * tiles_max + t];
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
       long long i = base + r * 32 + lane;
       if (i < N) {
         unsigned d = dig[r];
-        unsigned pos = s_base[d] + hist[(size_t)d * tiles_max + t] + s_whist[warp][d] + off[r];
-        keys_out[pos] = key[r];
-        vals_out[pos] = val[r];
+        unsigned lpos = s_lbase[d] + s_whist[warp][d] + off[r];
+        s_keys[lpos] = key[r];
+        s_vals[lpos] = val[r];
       }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < in_tile; j += RS_THREADS) {
+      unsigned k = s_keys[j], vv = s_vals[j];
+      unsigned d = op(k, vv);
+      unsigned pos = s_gpos[d] + (unsigned)j - s_lbase[d];
+      keys_out[pos] = k;
+      vals_out[pos] = vv;
     }
     __syncthreads();
   }

@@ -2,7 +2,7 @@
 //  - per view, the raw L1 error and its min/max (block reduction + atomics),
 //    then the min-max normalised E, mask M and band B, decided in float32 with
 //    correctly rounded operations, and the per-Gaussian attribution (count,
-//    mass) with warp-aggregated atomics;
+//    mass) with warp-aggregated integer atomics (mass in exact fixed point);
 //  - top-k error mass by an 8-pass radix select on the 64-bit mass keys;
 //  - erosion (separable min filter), 8-connected labelling by a union-find whose
 //    roots are the smallest pixel index of each component (per 32x32 tile in
@@ -53,11 +53,12 @@ __global__ void err_init_minmax_kernel(unsigned* mm, int n_views) {
 // E, M, B and the per-Gaussian attribution of pre-erosion error pixels.
 __global__ void err_norm_kernel(float* E, uint8_t* mask, const unsigned* minmax_bits,
                                 const int* dominant, long long n, CamSet cs, float tau, int L,
-                                int* count, double* mass) {
-  __shared__ float s_val[8][32];
+                                int mass_shift, int* count, double* mass) {
+  __shared__ unsigned long long s_val[8][32];
   const int v = blockIdx.y;
   const long long P = (long long)cs.cam[v].width * cs.cam[v].height;
   const long long base = cs.pix_base[v];
+  const float mass_scale = __int_as_float((127 + mass_shift) << 23);  // 2^mass_shift
   const float mn = __uint_as_float(minmax_bits[2 * v]);
   const float mx = __uint_as_float(minmax_bits[2 * v + 1]);
   const float range = __fsub_rn(mx, mn);
@@ -85,16 +86,45 @@ __global__ void err_norm_kernel(float* E, uint8_t* mask, const unsigned* minmax_
       if (m && d >= 0 && d < n) key = d;
     }
     unsigned peers = __match_any_sync(0xffffffffu, key);
-    s_val[warp][lane] = e;
+    // E * 2^mass_shift is an integer for every E above the threshold, so the
+    // sums are exact and independent of the order of the atomics
+    s_val[warp][lane] = __float2ull_rn(e * mass_scale);
     __syncwarp();
     if (key >= 0 && (peers & lanemask_lt()) == 0) {
-      double s = 0.0;
-      for (unsigned m = peers; m; m &= m - 1) s += (double)s_val[warp][__ffs(m) - 1];
+      unsigned long long q = 0;
+      for (unsigned m = peers; m; m &= m - 1) q += s_val[warp][__ffs(m) - 1];
       atomicAdd(&count[key], __popc(peers));
-      atomicAdd(&mass[key], s);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&mass[key]), q);
     }
     __syncwarp();
   }
+}
+
+// Converts the fixed-point mass sums (held in the mass array) to doubles in place.
+__global__ void mass_finalize_kernel(double* mass, long long n, int mass_shift) {
+  const double inv = ldexp(1.0, -mass_shift);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long q = reinterpret_cast<unsigned long long*>(mass)[i];
+    mass[i] = (double)q * inv;
+  }
+}
+
+// Scale exponent for the fixed-point mass: a float32 E > tau >= 2^e is a
+// multiple of 2^(e - 23), so E * 2^(23 - e) is an integer. Capped at 36 so that
+// 2^28 pixels of E <= 1 still fit in 64 bits (below tau = 2^-13 the sums round
+// to 2^-36).
+static int mass_shift_for(float tau) {
+  int e = -4;
+  if (tau > 0.f) {
+    int ex;
+    frexpf(tau, &ex);  // tau = f * 2^ex, f in [0.5, 1)
+    e = ex - 1;
+  } else {
+    e = -13;
+  }
+  int sh = 23 - e;
+  return sh < 0 ? 0 : (sh > 36 ? 36 : sh);
 }
 
 // ------------------------------------------------------------------ top-k
@@ -571,8 +601,10 @@ extern "C" ADP_API int adp_error_stats(const float* img, const float* target,
   err_init_minmax_kernel<<<1, 32, 0, st>>>(mm, n_views);
   dim3 grid(view_grid(cs), n_views);
   err_raw_kernel<<<grid, 256, 0, st>>>(img, target, cs, maps->E, mm);
+  const int shift = mass_shift_for(prm->tau_l1);
   err_norm_kernel<<<grid, 256, 0, st>>>(maps->E, maps->mask, mm, dominant, n, cs, prm->tau_l1,
-                                        prm->n_levels, count, mass);
+                                        prm->n_levels, shift, count, mass);
+  if (n > 0) mass_finalize_kernel<<<grid_for(n, 256, 148 * 16), 256, 0, st>>>(mass, n, shift);
   ADP_LAUNCH_CHECK();
   return ADP_OK;
 }

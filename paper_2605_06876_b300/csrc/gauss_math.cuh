@@ -96,17 +96,20 @@ __device__ __forceinline__ float sh_coef(const float* sh, long long n, long long
   return sh[((long long)(f >> 2) * n + i) * 4 + (f & 3)];
 }
 
-// alpha at pixel (px, py) for a Gaussian with 2D mean (mx, my), conic (A, B, C)
-// and opacity o: returns o * exp(power), or 0 if power > 0. Both compositing
-// directions call this so their decisions agree bit for bit.
-__device__ __forceinline__ float alpha_raw(float mx, float my, float A, float B, float C, float o,
-                                           float px, float py, float* dx_out, float* dy_out) {
+// alpha_raw = o * G at pixel (px, py) for a Gaussian with 2D mean (mx, my),
+// conic (A, B, C) and opacity o, with the footprint G = exp(power) (0 where the
+// quadratic form is negative). Forward and backward both call this function, so
+// their decisions agree bit for bit.
+__device__ __forceinline__ float alpha_raw_g(float mx, float my, float A, float B, float C,
+                                             float o, float px, float py, float* dx_out,
+                                             float* dy_out, float* G_out) {
   float dx = mx - px, dy = my - py;
   *dx_out = dx;
   *dy_out = dy;
   float power = -0.5f * (A * dx * dx + C * dy * dy) - B * dx * dy;
-  if (power > 0.f) return 0.f;
-  return o * __expf(power);
+  float G = power > 0.f ? 0.f : __expf(power);
+  *G_out = G;
+  return power > 0.f ? 0.f : o * G;
 }
 
 }  // namespace adp

@@ -58,8 +58,8 @@ __global__ void __launch_bounds__(256) render_kernel(RenderArgs a, CamSet cs) {
       int cnt = min(256, count - b0);
       for (int k = 0; k < cnt; ++k) {
         float4 g0 = s_g0[k], g1 = s_g1[k];
-        float dx, dy;
-        float al = alpha_raw(g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, fx, fy, &dx, &dy);
+        float dx, dy, G;
+        float al = alpha_raw_g(g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, fx, fy, &dx, &dy, &G);
         if (al < a.alpha_min) continue;
         al = fminf(a.alpha_max, al);
         float test = T * (1.f - al);
