@@ -8,8 +8,9 @@
  *  - Pointers inside the structs and the array arguments are DEVICE pointers
  *    owned by the caller, unless a parameter says "host". The library allocates
  *    no device memory: scratch space comes from the caller as a workspace whose
- *    size a *_workspace_size() query returns. float4 arrays must be 16-byte
- *    aligned, workspaces 256-byte aligned.
+ *    size a *_workspace_size() query returns (adp_select_topk_noalloc instead
+ *    uses one statically allocated device array, see there). float4 arrays must
+ *    be 16-byte aligned, workspaces 256-byte aligned.
  *  - Every call is asynchronous on the given stream (a cudaStream_t; NULL is the
  *    legacy default stream) and does not synchronise, except adp_split_plan,
  *    which reads one integer back when asked to (see there).
@@ -212,6 +213,25 @@ ADP_API int adp_error_stats(const float* img, const float* target, const int32_t
 ADP_API size_t adp_select_topk_workspace_size(int64_t n);
 ADP_API int adp_select_topk(const double* mass, int64_t n, int64_t k, int32_t* out_ids,
                             void* ws, size_t ws_bytes, adp_stream_t stream);
+
+/* The same selection for callers that cannot allocate device memory where they
+ * run (no cudaMalloc, no caller workspace): for example code running inside a
+ * custom device allocator or a memory pool's callback, a host framework that
+ * caps or forbids allocations mid-step, or a library layer that holds no
+ * allocator of its own. The paper has no counterpart; this is an
+ * integration convenience. Scratch comes from a statically allocated device
+ * array sized for n <= ADP_TOPK_NOALLOC_MAX_N (about 4 MiB, held by every
+ * device that loads the library until the process exits); larger n returns
+ * ADP_ERR_INVALID_ARG. The first call on each device looks up that array's
+ * device address (cudaGetSymbolAddress, with the device current); make that
+ * first call before any stream capture. All calls share the one array, whose
+ * contents persist from call to call (the call resets what must start at
+ * zero): calls that can overlap on the GPU (different streams, or different
+ * host threads, on the same device) race and must be serialised by the
+ * caller. Results are identical to adp_select_topk's. */
+#define ADP_TOPK_NOALLOC_MAX_N (1LL << 22)
+ADP_API int adp_select_topk_noalloc(const double* mass, int64_t n, int64_t k, int32_t* out_ids,
+                                    adp_stream_t stream);
 
 /* Error regions (Eqs. 7-8): erode M by the (2 r_erode + 1)^2 square (pixels
  * outside the image count as set), then join 8-neighbours whose eroded M is set,

@@ -82,6 +82,7 @@ _PROTOS = {
                                   P(AdpErrorMaps), _vp, _vp, _vp]),
     "adp_select_topk_workspace_size": (C.c_size_t, [_i64]),
     "adp_select_topk": (C.c_int, [_vp, _i64, _i64, _vp, _vp, C.c_size_t, _vp]),
+    "adp_select_topk_noalloc": (C.c_int, [_vp, _i64, _i64, _vp, _vp]),
     "adp_error_regions_workspace_size": (C.c_size_t, [_i64, _i32, P(AdpCamera)]),
     "adp_error_regions": (C.c_int, [P(AdpErrorMaps), _vp, _vp, _i64, P(AdpCamera), _i32, _vp,
                                     _i64, P(AdpParams), P(AdpRegions), _vp, C.c_size_t, _vp]),

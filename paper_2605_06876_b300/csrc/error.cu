@@ -8,6 +8,8 @@
 //    roots are the smallest pixel index of each component (per 32x32 tile in
 //    shared memory first, then across tile borders in global memory),
 //    exact int64 region moments, the area filter and the FP64 region statistics.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace adp {
@@ -798,4 +800,107 @@ extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* do
     labels_out_kernel<<<grid, 256, 0, st>>>(w.L, w.mom, w.slot, prm->m_min, cs, out->labels);
   ADP_LAUNCH_CHECK();
   return ADP_OK;
+}
+
+// ------------------------------------------------------------------ top-k without allocation
+//
+// A variant of adp_select_topk for callers that cannot allocate device memory
+// (or call cudaMalloc) at the point they run, e.g. code inside a custom
+// allocator, a memory-capped host framework or a context where allocation
+// would break an outer stream capture. Its scratch lives in the statically
+// allocated device array below, sized for at most ADP_TOPK_NOALLOC_MAX_N
+// Gaussians. Every device that loads the library keeps this array until the
+// process exits.
+
+namespace adp {
+
+// Scratch of the allocation-free top-k: selection state, histogram, one flag
+// byte per Gaussian, scan block sums and two counters (all 256-aligned).
+constexpr long long kNoallocMaxN = ADP_TOPK_NOALLOC_MAX_N;
+constexpr size_t kNoallocBytes =
+    256 /*state*/ + 1024 /*hist*/ + ((kNoallocMaxN + 255) / 256) * 256 /*flags*/ +
+    (((kNoallocMaxN + SCAN_TILE - 1) / SCAN_TILE + 1) * 8 + 255) / 256 * 256 /*scan*/ +
+    256 /*counters*/;
+static __device__ __align__(256) unsigned char g_topk_scratch[kNoallocBytes];
+
+// Per-device address of g_topk_scratch, looked up once per device.
+static void* g_topk_scratch_ptr[64];
+static std::mutex g_topk_scratch_mu;
+
+static int topk_scratch_address(void** out) {
+  int dev = 0;
+  ADP_CUDA(cudaGetDevice(&dev));
+  ADP_CHECK_ARG(dev >= 0 && dev < 64, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_topk_scratch_mu);
+  if (!g_topk_scratch_ptr[dev]) {
+    void* p = nullptr;
+    ADP_CUDA(cudaGetSymbolAddress(&p, g_topk_scratch));
+    g_topk_scratch_ptr[dev] = p;
+  }
+  *out = g_topk_scratch_ptr[dev];
+  return ADP_OK;
+}
+
+// Resets the selection state and the histogram of the shared scratch.
+__global__ void topk_noalloc_reset_kernel(SelectState* st, unsigned* hist, long long k) {
+  if (threadIdx.x == 0) {
+    st->prefix = 0ull;
+    st->mask = 0ull;
+    st->remaining = k;
+    st->pad = 0;
+  }
+  hist[threadIdx.x] = 0u;
+}
+
+}  // namespace adp
+
+extern "C" ADP_API int adp_select_topk_noalloc(const double* mass, int64_t n, int64_t k,
+                                               int32_t* out_ids, adp_stream_t stream) {
+  ADP_CHECK_ARG(n >= 0 && k >= 0, "bad n or k");
+  ADP_CHECK_ARG(n <= ADP_TOPK_NOALLOC_MAX_N,
+                "n = %lld exceeds the %lld Gaussians the static scratch of "
+                "adp_select_topk_noalloc holds; use adp_select_topk with a workspace",
+                (long long)n, (long long)ADP_TOPK_NOALLOC_MAX_N);
+  ADP_CHECK_ARG(k == 0 || (mass && out_ids), "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (k > n) k = n;
+  if (k == 0) return ADP_OK;
+  if (k == n) {
+    iota_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(out_ids, n);
+    ADP_LAUNCH_CHECK();
+    return ADP_OK;
+  }
+  void* base = nullptr;
+  int rc = topk_scratch_address(&base);
+  if (rc) return rc;
+  Carver c(base, kNoallocBytes);
+  SelectState* ss = c.take<SelectState>(1);
+  unsigned* hist = c.take<unsigned>(256);
+  uint8_t* sel = c.take<uint8_t>(n);
+  void* sw = c.take<char>(scan_workspace_bytes(n));
+  long long* cnt = c.take<long long>(2);
+  ADP_CHECK_ARG(c.ok, "internal: static scratch too small");
+  topk_noalloc_reset_kernel<<<1, 256, 0, st>>>(ss, hist, (long long)k);
+  unsigned g = grid_for(n, 256, 148 * 8);
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    topk_hist_kernel<<<g, 256, 0, st>>>(mass, n, shift, ss, hist);
+    topk_pick_kernel<<<1, 256, 0, st>>>(hist, shift, ss);
+  }
+  ADP_LAUNCH_CHECK();
+  const SelectState* css = ss;
+  rc = scan_exclusive(
+      [=] __device__(long long i) -> long long {
+        return (unsigned long long)__double_as_longlong(mass[i]) == css->prefix ? 1 : 0;
+      },
+      [=] __device__(long long i, long long pre) {
+        unsigned long long key = (unsigned long long)__double_as_longlong(mass[i]);
+        sel[i] = key > css->prefix || (key == css->prefix && pre < css->remaining);
+      },
+      n, nullptr, &cnt[0], sw, st);
+  if (rc) return rc;
+  return scan_exclusive([=] __device__(long long i) -> long long { return sel[i]; },
+                        [=] __device__(long long i, long long pre) {
+                          if (sel[i]) out_ids[pre] = (int)i;
+                        },
+                        n, nullptr, &cnt[1], sw, st);
 }
