@@ -171,7 +171,7 @@ def run_ours(args, rank, world, local_rank):
     t_wall0 = time.time()
     step_ms = []
     stage_ms = {}
-    new_n = 0
+    last_plan = None
     for _ in range(args.steps):
         flush.random_(0, 255)  # evict L2 between steps (not timed)
         t = StageTimer(stream)
@@ -181,12 +181,13 @@ def run_ours(args, rank, world, local_rank):
         for kname, val in d.items():
             stage_ms[kname] = stage_ms.get(kname, 0.0) + val
         step_ms.append(sum(d.values()))
-        new_n = out[3].new_n
+        last_plan = out[3]
     barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop(t_wall0, time.time())
-    if not stepper.check_capacity():
-        raise RuntimeError("instance or region capacity exceeded in the timed region")
+    if not stepper.check_capacity(last_plan):
+        raise RuntimeError("instance, region or population capacity exceeded in the timed region")
+    new_n = int(last_plan.d_new_n.item())
     total_ms = float(sum(step_ms))
     if world > 1:
         import torch.distributed as dist

@@ -111,9 +111,11 @@ typedef struct adp_gaussians {
   float* sh;
 } adp_gaussians;
 
-/* Projected Gaussians, one record per (view v, Gaussian i) at index v * n + i. */
+/* Projected Gaussians, one record per (view v, Gaussian i) at index v * n + i.
+ * A culled record has tiles_touched = 0 and an empty rect; its other fields are
+ * unspecified. */
 typedef struct adp_projected {
-  float* xy_opacity_depth; /* float4: 2D mean x, y; opacity; camera depth (opacity 0: culled) */
+  float* xy_opacity_depth; /* float4: 2D mean x, y; opacity; camera depth */
   float* conic;            /* float4: A, B, C, 0 -- inverse 2D covariance [[A, B], [B, C]] */
   float* rgb;              /* float4: r, g, b, 0 -- SH colour for this view, clamped at 0 */
   int32_t* rect;           /* int4: tile x0, x1, y0, y1 (inclusive) of the pixel box */
@@ -253,12 +255,16 @@ ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* dominant, con
  * the earlier group), children in first-member (view, label) order. Computed in
  * FP64. Writes status[n_cand], n_children[n_cand] and *d_new_n; if h_new_n is
  * non-NULL the call copies the size back and synchronises the stream.
- * Apply: writes the new population (out->n must equal the planned size): every
- * non-candidate and RESET Gaussian in id order with its Adam moments, then per
- * candidate in ascending id [parent copy with opacity o/(N_i + 1), children] or
- * the two vanilla children mu + R (s * noise), s / (2 eta) (Eqs. 3-4), all with
- * zero moments. noise: [n_cand][2][3] standard normal. state_in/state_out may
- * be NULL to skip the moments. */
+ * Apply: writes the new population into out, whose n is its CAPACITY (plane
+ * stride); the population occupies entries [0, *d_new_n). If the planned size
+ * exceeds out->n nothing is written (compare *d_new_n with out->n after a
+ * sync), so a caller may pass buffers sized for the largest possible result,
+ * n + n_cand * (n_max + 1), and never synchronise. Order: every non-candidate
+ * and RESET Gaussian in id order with its Adam moments, then per candidate in
+ * ascending id [parent copy with opacity o/(N_i + 1), children] or the two
+ * vanilla children mu + R (s * noise), s / (2 eta) (Eqs. 3-4), all with zero
+ * moments. noise: [n_cand][2][3] standard normal. m_in/v_in/m_out/v_out may be
+ * NULL to skip the moments; m_out and v_out have out->n entries. */
 ADP_API size_t adp_split_workspace_size(int64_t n, int64_t n_cand, int64_t region_capacity);
 ADP_API int adp_split_plan(const adp_gaussians* g, const adp_camera* cams, int32_t n_views,
                            const adp_regions* regs, const int32_t* candidates, int64_t n_cand,

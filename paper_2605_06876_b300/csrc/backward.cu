@@ -1,6 +1,6 @@
 // Hand-written backward of the compositing and projection.
 //
-// Pass 1 (one CTA per tile, one thread per pixel): walks the tile's list back
+// Pass 1 (one CTA per tile, two pixels per thread): walks the tile's list back
 // to front from each pixel's last blended Gaussian, recovering the
 // transmittance before each Gaussian as T / (1 - alpha) from T_final instead of
 // storing it, and the normalised colour behind it by the recurrence
@@ -62,7 +62,47 @@ __device__ __forceinline__ float reduce_scatter8(const float* v, int* idx) {
   return x;
 }
 
-__global__ void __launch_bounds__(256) bwd_pixel_kernel(BwdPixArgs a, CamSet cs) {
+// Two pixels per thread (local pixels t and t + 128 of the 256-pixel tile, the
+// same column eight rows apart for 16x16 tiles): the staged Gaussian is read once
+// for both, and one warp reduction covers 64 pixels.
+constexpr int BWD_THREADS = 128;
+
+struct PixState {
+  float T, R0, R1, R2, g0, g1, g2, fx, fy;
+  int last;
+};
+
+// Contribution of one staged Gaussian to one pixel's gradients (adds into v[9]).
+__device__ __forceinline__ bool bwd_contrib(PixState& s, int pos, float4 q0, float4 q1, float c2,
+                                            float amin, float amax, float* v) {
+  if (pos >= s.last) return false;
+  float dx, dy, G;
+  float ar = alpha_raw_g(q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, s.fx, s.fy, &dx, &dy, &G);
+  if (ar < amin) return false;
+  float al = fminf(amax, ar);
+  float Tj = s.T * __frcp_rn(1.f - al);
+  float dal = Tj * (s.g0 * (q1.z - s.R0) + s.g1 * (q1.w - s.R1) + s.g2 * (c2 - s.R2));
+  float wgt = Tj * al;
+  v[6] += wgt * s.g0;
+  v[7] += wgt * s.g1;
+  v[8] += wgt * s.g2;
+  s.R0 = al * q1.z + (1.f - al) * s.R0;
+  s.R1 = al * q1.w + (1.f - al) * s.R1;
+  s.R2 = al * c2 + (1.f - al) * s.R2;
+  s.T = Tj;
+  if (ar <= amax) {
+    v[5] += dal * G;
+    float dpow = dal * ar;
+    v[2] += -0.5f * dx * dx * dpow;
+    v[4] += -0.5f * dy * dy * dpow;
+    v[3] += -dx * dy * dpow;
+    v[0] += -(q0.z * dx + q0.w * dy) * dpow;
+    v[1] += -(q1.x * dy + q0.w * dx) * dpow;
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(BWD_THREADS) bwd_pixel_kernel(BwdPixArgs a, CamSet cs) {
   __shared__ float4 s_g0[256];
   __shared__ float4 s_g1[256];
   __shared__ float2 s_g2[256];
@@ -72,98 +112,78 @@ __global__ void __launch_bounds__(256) bwd_pixel_kernel(BwdPixArgs a, CamSet cs)
   const int lt = tile - cs.tile_base[v];
   const int txs = cs.tiles_x[v];
   const int W = cs.cam[v].width, H = cs.cam[v].height;
-  const int px = (lt % txs) * cs.tile_w + (int)threadIdx.x % cs.tile_w;
-  const int py = (lt / txs) * cs.tile_h + (int)threadIdx.x / cs.tile_w;
-  const bool inside = px < W && py < H;
-  const float fx = (float)px, fy = (float)py;
   const int2 range = a.ranges[tile];
   const long long rec_base = (long long)v * a.n;
+  const float sc = 1.f / (3.f * (float)W * (float)H);
 
-  float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-  int my_last = 0;
-  if (inside) {
-    long long p = cs.pix_base[v] + (long long)py * W + px;
-    T = a.T_final[p];
-    my_last = a.last[p];
-    if (a.dL_drgb) {
-      g0 = a.dL_drgb[3 * p];
-      g1 = a.dL_drgb[3 * p + 1];
-      g2 = a.dL_drgb[3 * p + 2];
-    } else {
-      float sc = 1.f / (3.f * (float)W * (float)H);
-      float d0 = a.img[3 * p] - a.target[3 * p];
-      float d1 = a.img[3 * p + 1] - a.target[3 * p + 1];
-      float d2 = a.img[3 * p + 2] - a.target[3 * p + 2];
-      g0 = d0 > 0.f ? sc : (d0 < 0.f ? -sc : 0.f);
-      g1 = d1 > 0.f ? sc : (d1 < 0.f ? -sc : 0.f);
-      g2 = d2 > 0.f ? sc : (d2 < 0.f ? -sc : 0.f);
+  PixState ps[2];
+  int warp_last = 0;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int li = (int)threadIdx.x + h * BWD_THREADS;
+    const int px = (lt % txs) * cs.tile_w + li % cs.tile_w;
+    const int py = (lt / txs) * cs.tile_h + li / cs.tile_w;
+    PixState& s = ps[h];
+    s.fx = (float)px;
+    s.fy = (float)py;
+    s.T = 1.f;
+    s.R0 = a.bg[0];
+    s.R1 = a.bg[1];
+    s.R2 = a.bg[2];
+    s.g0 = s.g1 = s.g2 = 0.f;
+    s.last = 0;
+    if (px < W && py < H) {
+      long long p = cs.pix_base[v] + (long long)py * W + px;
+      s.T = a.T_final[p];
+      s.last = a.last[p];
+      if (a.dL_drgb) {
+        s.g0 = a.dL_drgb[3 * p];
+        s.g1 = a.dL_drgb[3 * p + 1];
+        s.g2 = a.dL_drgb[3 * p + 2];
+      } else {
+        float d0 = a.img[3 * p] - a.target[3 * p];
+        float d1 = a.img[3 * p + 1] - a.target[3 * p + 1];
+        float d2 = a.img[3 * p + 2] - a.target[3 * p + 2];
+        s.g0 = d0 > 0.f ? sc : (d0 < 0.f ? -sc : 0.f);
+        s.g1 = d1 > 0.f ? sc : (d1 < 0.f ? -sc : 0.f);
+        s.g2 = d2 > 0.f ? sc : (d2 < 0.f ? -sc : 0.f);
+      }
     }
+    warp_last = max(warp_last, s.last);
   }
   if (threadIdx.x == 0) s_maxlast = 0;
   __syncthreads();
-  int warp_last = my_last;  // positions at or beyond it have no work in this warp
   for (int o = 16; o > 0; o >>= 1) warp_last = max(warp_last, __shfl_xor_sync(0xffffffffu, warp_last, o));
   if ((threadIdx.x & 31) == 0 && warp_last > 0) atomicMax(&s_maxlast, warp_last);
   __syncthreads();
   const int end = s_maxlast;
-  float R0 = a.bg[0], R1 = a.bg[1], R2 = a.bg[2];
+  const int lane = threadIdx.x & 31;
   for (int b1 = end; b1 > 0; b1 -= 256) {
-    int b0 = b1 - 256 > 0 ? b1 - 256 : 0;
-    int j = b0 + (int)threadIdx.x;
+    const int b0 = b1 - 256 > 0 ? b1 - 256 : 0;
     __syncthreads();
-    if (j < b1) {
-      int id = a.inst[range.x + j];
+    for (int j = (int)threadIdx.x; j < b1 - b0; j += BWD_THREADS) {
+      int id = a.inst[range.x + b0 + j];
       long long r = rec_base + id;
       float4 p0 = a.xyod[r], p1 = a.conic[r], p2 = a.rgb[r];
-      s_g0[threadIdx.x] = make_float4(p0.x, p0.y, p1.x, p1.y);
-      s_g1[threadIdx.x] = make_float4(p1.z, p0.z, p2.x, p2.y);
-      s_g2[threadIdx.x] = make_float2(p2.z, __int_as_float(id));
+      s_g0[j] = make_float4(p0.x, p0.y, p1.x, p1.y);
+      s_g1[j] = make_float4(p1.z, p0.z, p2.x, p2.y);
+      s_g2[j] = make_float2(p2.z, __int_as_float(id));
     }
     __syncthreads();
     const int kmax = min(b1, warp_last) - b0;  // warp-uniform
     for (int k = kmax - 1; k >= 0; --k) {
-      int pos = b0 + k;
-      float4 q0 = s_g0[k], q1 = s_g1[k];
-      float dmx = 0.f, dmy = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dop = 0.f, dr = 0.f, dg = 0.f,
-            db = 0.f;
-      bool hit = false;
-      if (pos < my_last) {
-        float dx, dy, G;
-        float ar = alpha_raw_g(q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, fx, fy, &dx, &dy, &G);
-        if (ar >= a.alpha_min) {
-          hit = true;
-          float al = fminf(a.alpha_max, ar);
-          float c2 = s_g2[k].x;
-          float Tj = T * __frcp_rn(1.f - al);
-          float dal = Tj * (g0 * (q1.z - R0) + g1 * (q1.w - R1) + g2 * (c2 - R2));
-          float wgt = Tj * al;
-          dr = wgt * g0;
-          dg = wgt * g1;
-          db = wgt * g2;
-          R0 = al * q1.z + (1.f - al) * R0;
-          R1 = al * q1.w + (1.f - al) * R1;
-          R2 = al * c2 + (1.f - al) * R2;
-          T = Tj;
-          if (ar <= a.alpha_max) {
-            dop = dal * G;
-            float dpow = dal * ar;
-            dA = -0.5f * dx * dx * dpow;
-            dC = -0.5f * dy * dy * dpow;
-            dB = -dx * dy * dpow;
-            dmx = -(q0.z * dx + q0.w * dy) * dpow;
-            dmy = -(q1.x * dy + q0.w * dx) * dpow;
-          }
-        }
-      }
-      unsigned any = __ballot_sync(0xffffffffu, hit);
-      if (any) {
-        float v8[8] = {dmx, dmy, dA, dB, dC, dop, dr, dg};
+      const int pos = b0 + k;
+      const float4 q0 = s_g0[k], q1 = s_g1[k];
+      const float c2 = s_g2[k].x;
+      float vals[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      bool hit = bwd_contrib(ps[0], pos, q0, q1, c2, a.alpha_min, a.alpha_max, vals);
+      hit |= bwd_contrib(ps[1], pos, q0, q1, c2, a.alpha_min, a.alpha_max, vals);
+      if (__ballot_sync(0xffffffffu, hit)) {
         int idx;
-        float sum = reduce_scatter8(v8, &idx);
-        db = warp_sum(db);
+        float sum = reduce_scatter8(vals, &idx);
+        float db = warp_sum(vals[8]);
         int id = __float_as_int(s_g2[k].y);
         float* g = reinterpret_cast<float*>(a.g2d + 3 * (rec_base + id));
-        const int lane = threadIdx.x & 31;
         if ((lane & 3) == 0) atomicAdd(g + idx, sum);
         if (lane == 0) atomicAdd(g + 8, db);
       }
@@ -441,7 +461,7 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   pa.alpha_min = prm->alpha_min;
   pa.alpha_max = prm->alpha_max;
   pa.g2d = g2d;
-  bwd_pixel_kernel<<<cs.tile_base[n_views], 256, 0, st>>>(pa, cs);
+  bwd_pixel_kernel<<<cs.tile_base[n_views], BWD_THREADS, 0, st>>>(pa, cs);
   ADP_LAUNCH_CHECK();
   BwdGaussArgs ga;
   ga.mean_logit = reinterpret_cast<const float4*>(g->mean_logit);

@@ -8,6 +8,8 @@
 // order. This moves far fewer bytes than sorting 64-bit keys over all
 // instances, and ties in depth resolve to the lower id because every pass is
 // stable over id-ordered input.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace adp {
@@ -17,33 +19,58 @@ __global__ void clamp_count_kernel(const long long* K, long long cap, long long*
   *Kc = k <= cap ? k : 0;
 }
 
-// One thread per instance k: the record owning k is found by binary search in
-// the instance offsets, and k's tile is its position within the record's tile
-// rectangle (row-major). Balanced whatever a Gaussian's footprint, and the
-// writes of consecutive threads are consecutive.
-__global__ void duplicate_kernel(const unsigned* vvals, const long long* offs,
-                                 const long long* d_nvis, const long long* d_K, long long cap,
-                                 const int4* rect, long long n, CamSet cs, unsigned* tkeys,
-                                 int* inst) {
+// Load-balanced duplication: each CTA takes a chunk of DUP_CHUNK consecutive
+// instances, stages the instance offsets of the records that own them in shared
+// memory (one global binary search per chunk end), and every thread finds its
+// instance's record by a binary search in shared memory. k's tile is its
+// position within the record's tile rectangle (row-major). Balanced whatever a
+// Gaussian's footprint, and consecutive threads write consecutive instances.
+constexpr int DUP_CHUNK = 2048;
+
+__device__ __forceinline__ long long last_le(const long long* offs, long long n, long long k) {
+  long long lo = 0, hi = n - 1;  // last j with offs[j] <= k (offs[0] = 0 <= k)
+  while (lo < hi) {
+    long long mid = (lo + hi + 1) >> 1;
+    if (offs[mid] <= k) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) duplicate_kernel(const unsigned* vvals, const long long* offs,
+                                                        const long long* d_nvis, const long long* d_K,
+                                                        long long cap, const int4* rect, long long n,
+                                                        CamSet cs, unsigned* tkeys, int* inst) {
+  __shared__ long long s_off[DUP_CHUNK];
+  __shared__ long long s_j[2];
   const long long N = *d_nvis, K = *d_K;
   if (K > cap || N == 0) return;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < K;
-       k += (long long)gridDim.x * blockDim.x) {
-    long long lo = 0, hi = N - 1;  // last j with offs[j] <= k
-    while (lo < hi) {
-      long long mid = (lo + hi + 1) >> 1;
-      if (offs[mid] <= k) lo = mid;
-      else hi = mid - 1;
+  for (long long k0 = (long long)blockIdx.x * DUP_CHUNK; k0 < K; k0 += (long long)gridDim.x * DUP_CHUNK) {
+    const long long k1 = min(k0 + DUP_CHUNK, K);
+    if (threadIdx.x < 2) s_j[threadIdx.x] = last_le(offs, N, threadIdx.x == 0 ? k0 : k1 - 1);
+    __syncthreads();
+    const long long j0 = s_j[0];
+    const int cnt = (int)(s_j[1] - j0 + 1);  // <= k1 - k0: every record owns >= 1 instance
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) s_off[q] = offs[j0 + q];
+    __syncthreads();
+    for (long long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+      int lo = 0, hi = cnt - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= k) lo = mid;
+        else hi = mid - 1;
+      }
+      unsigned p = vvals[j0 + lo];
+      int v = (int)(p / (unsigned long long)n);
+      int i = (int)(p - (unsigned long long)v * n);
+      int4 r = rect[p];
+      int w = r.y - r.x + 1;
+      int t = (int)(k - s_off[lo]);
+      int ty = r.z + t / w, tx = r.x + t % w;
+      tkeys[k] = (unsigned)(cs.tile_base[v] + ty * cs.tiles_x[v] + tx);
+      inst[k] = i;
     }
-    unsigned p = vvals[lo];
-    int v = (int)(p / (unsigned long long)n);
-    int i = (int)(p - (unsigned long long)v * n);
-    int4 r = rect[p];
-    int w = r.y - r.x + 1;
-    int t = (int)(k - offs[lo]);
-    int ty = r.z + t / w, tx = r.x + t % w;
-    tkeys[k] = (unsigned)(cs.tile_base[v] + ty * cs.tiles_x[v] + tx);
-    inst[k] = i;
+    __syncthreads();
   }
 }
 
@@ -153,7 +180,8 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
 
   // 4. duplicate into tiles, 5. stable sort by tile
   if (cap > 0) {
-    duplicate_kernel<<<grid_for(cap, 256, 148 * 32), 256, 0, st>>>(
+    duplicate_kernel<<<(unsigned)std::min<long long>((cap + DUP_CHUNK - 1) / DUP_CHUNK, 148 * 8), 256,
+                       0, st>>>(
         vvals, offs, &w.counters[0], (const long long*)bins->n_instances, cap,
         reinterpret_cast<const int4*>(pr->rect), n, cs, w.tkeys, bins->inst_gauss);
     ADP_LAUNCH_CHECK();

@@ -8,6 +8,7 @@
 //    roots are the smallest pixel index of each component (per 32x32 tile in
 //    shared memory first, then across tile borders in global memory),
 //    exact int64 region moments, the area filter and the FP64 region statistics.
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -38,9 +39,24 @@ __global__ void err_raw_kernel(const float* img, const float* tgt, CamSet cs, fl
     lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
     hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
   }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMin(&minmax_bits[2 * v], lo);
-    atomicMax(&minmax_bits[2 * v + 1], hi);
+  __shared__ unsigned s_lo[32], s_hi[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    s_lo[w] = lo;
+    s_hi[w] = hi;
+  }
+  __syncthreads();
+  if (w == 0) {  // one pair of atomics per block
+    lo = lane < nw ? s_lo[lane] : 0x7f800000u;
+    hi = lane < nw ? s_hi[lane] : 0u;
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      atomicMin(&minmax_bits[2 * v], lo);
+      atomicMax(&minmax_bits[2 * v + 1], hi);
+    }
   }
 }
 
@@ -602,7 +618,8 @@ extern "C" ADP_API int adp_error_stats(const float* img, const float* target,
   unsigned* mm = reinterpret_cast<unsigned*>(maps->minmax);
   err_init_minmax_kernel<<<1, 32, 0, st>>>(mm, n_views);
   dim3 grid(view_grid(cs), n_views);
-  err_raw_kernel<<<grid, 256, 0, st>>>(img, target, cs, maps->E, mm);
+  err_raw_kernel<<<dim3(std::min(grid.x, 148u * 4u), n_views), 256, 0, st>>>(img, target, cs,
+                                                                            maps->E, mm);
   const int shift = mass_shift_for(prm->tau_l1);
   err_norm_kernel<<<grid, 256, 0, st>>>(maps->E, maps->mask, mm, dominant, n, cs, prm->tau_l1,
                                         prm->n_levels, shift, count, mass);

@@ -1,6 +1,7 @@
-// EWA projection of every Gaussian into every view (Sec. 3, Eq. 1): one thread
-// per (view, Gaussian), float4 plane loads, one record of three float4 + int4
-// rect + tile count written per pair.
+// EWA projection of every Gaussian into every view (Sec. 3, Eq. 1): float4 plane
+// loads, one record of three float4 + int4 rect + tile count per (view,
+// Gaussian). Records of culled pairs get only tiles_touched = 0 and an empty
+// rect; their other fields are left unwritten (nothing reads them).
 #include "gauss_math.cuh"
 
 namespace adp {
@@ -20,10 +21,8 @@ struct ProjectArgs {
   int* tiles;
 };
 
-__global__ void __launch_bounds__(256) project_kernel(ProjectArgs a, CamSet cs) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  int v = blockIdx.y;
-  if (i >= a.n) return;
+// Full projection of Gaussian i into view v; writes its record.
+__device__ void project_one(const ProjectArgs& a, const CamSet& cs, long long i, int v) {
   const adp_camera& cam = cs.cam[v];
   long long rec = (long long)v * a.n + i;
   const float* Rw = cam.R;
@@ -34,7 +33,6 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a, CamSet cs) 
   float pcz = Rw[6] * ml.x + Rw[7] * ml.y + Rw[8] * ml.z + cam.t[2];
   float o = 1.f / (1.f + __expf(-ml.w));
   bool vis = pcz > a.near_plane && o >= a.alpha_min;
-
   float4 out0 = make_float4(0.f, 0.f, 0.f, 0.f), out1 = out0, out2 = out0;
   int4 rc = make_int4(0, -1, 0, -1);
   int nt = 0;
@@ -124,6 +122,66 @@ __global__ void __launch_bounds__(256) project_kernel(ProjectArgs a, CamSet cs) 
   a.tiles[rec] = nt;
 }
 
+// Conservative screen test from the mean, the largest scale and the opacity:
+// the ellipse's box half-width is at most sqrt(k (|J row|^2 s_max^2 + low_pass))
+// with k = 2 ln(o / alpha_min), so a Gaussian whose bound misses the image
+// (with a margin) cannot touch it. Culled records get tiles_touched = 0.
+__device__ bool maybe_visible(const ProjectArgs& a, const CamSet& cs, long long i, int v) {
+  const adp_camera& cam = cs.cam[v];
+  const float* Rw = cam.R;
+  float4 ml = a.mean_logit[i];
+  float pcz = Rw[6] * ml.x + Rw[7] * ml.y + Rw[8] * ml.z + cam.t[2];
+  float o = 1.f / (1.f + __expf(-ml.w));
+  if (!(pcz > a.near_plane && o >= a.alpha_min)) return false;
+  float4 ls = a.logscale[i];
+  float pcx = Rw[0] * ml.x + Rw[1] * ml.y + Rw[2] * ml.z + cam.t[0];
+  float pcy = Rw[3] * ml.x + Rw[4] * ml.y + Rw[5] * ml.z + cam.t[1];
+  float iz = 1.f / pcz;
+  float limx = 1.3f * (float)cam.width / (2.f * cam.fx);
+  float limy = 1.3f * (float)cam.height / (2.f * cam.fy);
+  float ux = fminf(limx, fmaxf(-limx, pcx * iz)), uy = fminf(limy, fmaxf(-limy, pcy * iz));
+  float smax2 = __expf(2.f * fmaxf(ls.x, fmaxf(ls.y, ls.z)));
+  float k = fmaxf(2.f * __logf(o / a.alpha_min), 0.f) * 1.01f;
+  float jx = cam.fx * iz, jy = cam.fy * iz;
+  float hx = sqrtf(k * (jx * jx * (1.f + ux * ux) * smax2 * 1.01f + a.low_pass)) + 1.f;
+  float hy = sqrtf(k * (jy * jy * (1.f + uy * uy) * smax2 * 1.01f + a.low_pass)) + 1.f;
+  float mx = cam.fx * pcx * iz + cam.px, my = cam.fy * pcy * iz + cam.py;
+  return mx + hx >= 0.f && mx - hx <= (float)(cam.width - 1) && my + hy >= 0.f &&
+         my - hy <= (float)(cam.height - 1);
+}
+
+constexpr int PROJ_THREADS = 256;
+constexpr int PROJ_CHUNK = 1024;
+
+// Each CTA takes PROJ_CHUNK Gaussians of one view: a cheap pass culls most of
+// them, the survivors are compacted in shared memory and projected by full
+// warps, so the expensive EWA and SH work is not diluted by culled lanes.
+__global__ void __launch_bounds__(PROJ_THREADS) project_kernel(ProjectArgs a, CamSet cs) {
+  __shared__ int s_list[PROJ_CHUNK];
+  __shared__ int s_cnt;
+  const int v = blockIdx.y;
+  for (long long c0 = (long long)blockIdx.x * PROJ_CHUNK; c0 < a.n;
+       c0 += (long long)gridDim.x * PROJ_CHUNK) {
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < PROJ_CHUNK; q += PROJ_THREADS) {
+      long long i = c0 + q;
+      if (i >= a.n) break;
+      if (maybe_visible(a, cs, i, v)) {
+        s_list[atomicAdd(&s_cnt, 1)] = q;
+      } else {
+        long long rec = (long long)v * a.n + i;
+        a.tiles[rec] = 0;
+        a.rect[rec] = make_int4(0, -1, 0, -1);
+      }
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+    for (int q = threadIdx.x; q < cnt; q += PROJ_THREADS) project_one(a, cs, c0 + s_list[q], v);
+    __syncthreads();
+  }
+}
+
 }  // namespace adp
 
 using namespace adp;
@@ -161,8 +219,8 @@ extern "C" ADP_API int adp_project(const adp_gaussians* g, const adp_camera* cam
   a.rgb = reinterpret_cast<float4*>(out->rgb);
   a.rect = reinterpret_cast<int4*>(out->rect);
   a.tiles = out->tiles_touched;
-  dim3 grid(grid_for(g->n, 256), n_views);
-  project_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(a, cs);
+  dim3 grid((unsigned)((g->n + PROJ_CHUNK - 1) / PROJ_CHUNK), n_views);
+  project_kernel<<<grid, PROJ_THREADS, 0, (cudaStream_t)stream>>>(a, cs);
   ADP_LAUNCH_CHECK();
   return ADP_OK;
 }

@@ -1,7 +1,7 @@
 // Front-to-back alpha compositing (Eq. 1) with the dominant Gaussian map (Eq. 5).
-// One CTA per tile (256 pixels, one per thread); the tile's depth-sorted list is
-// staged through shared memory 256 Gaussians at a time, each thread gathering one
-// record; a block-wide vote ends the tile once every pixel has stopped.
+// One CTA per tile (256 pixels, two per thread); the tile's depth-sorted list is
+// staged through shared memory 256 Gaussians at a time, each thread gathering two
+// records; a block-wide vote ends the tile once every pixel has stopped.
 #include "gauss_math.cuh"
 
 namespace adp {
@@ -22,7 +22,40 @@ struct RenderArgs {
   int* out_dom;
 };
 
-__global__ void __launch_bounds__(256) render_kernel(RenderArgs a, CamSet cs) {
+constexpr int RENDER_THREADS = 128;  // two pixels per thread
+
+struct FwdPix {
+  float T, c0, c1, c2, best, fx, fy;
+  int dom, ncon, last;
+  bool done;
+};
+
+__device__ __forceinline__ void fwd_step(FwdPix& s, int pos, float4 g0, float4 g1, float2 g2,
+                                         float amin, float amax, float tmin) {
+  if (s.done) return;
+  float dx, dy, G;
+  float al = alpha_raw_g(g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, s.fx, s.fy, &dx, &dy, &G);
+  if (al < amin) return;
+  al = fminf(amax, al);
+  float test = s.T * (1.f - al);
+  if (test < tmin) {
+    s.done = true;
+    return;
+  }
+  float w = s.T * al;
+  s.c0 += w * g1.z;
+  s.c1 += w * g1.w;
+  s.c2 += w * g2.x;
+  if (w > s.best) {
+    s.best = w;
+    s.dom = __float_as_int(g2.y);
+  }
+  s.T = test;
+  ++s.ncon;
+  s.last = pos + 1;
+}
+
+__global__ void __launch_bounds__(RENDER_THREADS) render_kernel(RenderArgs a, CamSet cs) {
   __shared__ float4 s_g0[256];  // mx, my, A, B
   __shared__ float4 s_g1[256];  // C, opacity, r, g
   __shared__ float2 s_g2[256];  // b, id (as int bits)
@@ -31,66 +64,64 @@ __global__ void __launch_bounds__(256) render_kernel(RenderArgs a, CamSet cs) {
   const int lt = tile - cs.tile_base[v];
   const int txs = cs.tiles_x[v];
   const int W = cs.cam[v].width, H = cs.cam[v].height;
-  const int px = (lt % txs) * cs.tile_w + (int)threadIdx.x % cs.tile_w;
-  const int py = (lt / txs) * cs.tile_h + (int)threadIdx.x / cs.tile_w;
-  const bool inside = px < W && py < H;
-  const float fx = (float)px, fy = (float)py;
   const int2 range = a.ranges[tile];
   const int count = range.y - range.x;
   const long long rec_base = (long long)v * a.n;
 
-  float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, best = -1.f;
-  int dom = -1, ncon = 0, last = 0;
-  bool done = !inside;
+  FwdPix ps[2];
+  bool inside[2];
+  int pxs[2], pys[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int li = (int)threadIdx.x + h * RENDER_THREADS;
+    pxs[h] = (lt % txs) * cs.tile_w + li % cs.tile_w;
+    pys[h] = (lt / txs) * cs.tile_h + li / cs.tile_w;
+    inside[h] = pxs[h] < W && pys[h] < H;
+    FwdPix& s = ps[h];
+    s.T = 1.f;
+    s.c0 = s.c1 = s.c2 = 0.f;
+    s.best = -1.f;
+    s.fx = (float)pxs[h];
+    s.fy = (float)pys[h];
+    s.dom = -1;
+    s.ncon = 0;
+    s.last = 0;
+    s.done = !inside[h];
+  }
   for (int b0 = 0; b0 < count; b0 += 256) {
-    if (__syncthreads_count(done) == 256) break;
-    int j = b0 + (int)threadIdx.x;
-    if (j < count) {
-      int id = a.inst[range.x + j];
+    if (__syncthreads_count(ps[0].done && ps[1].done) == RENDER_THREADS) break;
+    for (int j = (int)threadIdx.x; j < 256 && b0 + j < count; j += RENDER_THREADS) {
+      int id = a.inst[range.x + b0 + j];
       long long r = rec_base + id;
       float4 p0 = a.xyod[r], p1 = a.conic[r], p2 = a.rgb[r];
-      s_g0[threadIdx.x] = make_float4(p0.x, p0.y, p1.x, p1.y);
-      s_g1[threadIdx.x] = make_float4(p1.z, p0.z, p2.x, p2.y);
-      s_g2[threadIdx.x] = make_float2(p2.z, __int_as_float(id));
+      s_g0[j] = make_float4(p0.x, p0.y, p1.x, p1.y);
+      s_g1[j] = make_float4(p1.z, p0.z, p2.x, p2.y);
+      s_g2[j] = make_float2(p2.z, __int_as_float(id));
     }
     __syncthreads();
-    if (!done) {
+    if (!(ps[0].done && ps[1].done)) {
       int cnt = min(256, count - b0);
       for (int k = 0; k < cnt; ++k) {
         float4 g0 = s_g0[k], g1 = s_g1[k];
-        float dx, dy, G;
-        float al = alpha_raw_g(g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, fx, fy, &dx, &dy, &G);
-        if (al < a.alpha_min) continue;
-        al = fminf(a.alpha_max, al);
-        float test = T * (1.f - al);
-        if (test < a.t_min) {
-          done = true;
-          break;
-        }
-        float w = T * al;
         float2 g2 = s_g2[k];
-        c0 += w * g1.z;
-        c1 += w * g1.w;
-        c2 += w * g2.x;
-        if (w > best) {
-          best = w;
-          dom = __float_as_int(g2.y);
-        }
-        T = test;
-        ++ncon;
-        last = b0 + k + 1;
+        fwd_step(ps[0], b0 + k, g0, g1, g2, a.alpha_min, a.alpha_max, a.t_min);
+        fwd_step(ps[1], b0 + k, g0, g1, g2, a.alpha_min, a.alpha_max, a.t_min);
+        if (ps[0].done && ps[1].done) break;
       }
     }
   }
-  if (inside) {
-    long long p = cs.pix_base[v] + (long long)py * W + px;
-    a.out_rgb[3 * p + 0] = c0 + T * a.bg[0];
-    a.out_rgb[3 * p + 1] = c1 + T * a.bg[1];
-    a.out_rgb[3 * p + 2] = c2 + T * a.bg[2];
-    a.out_T[p] = T;
-    a.out_n[p] = ncon;
-    a.out_last[p] = last;
-    a.out_dom[p] = dom;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (!inside[h]) continue;
+    const FwdPix& s = ps[h];
+    long long p = cs.pix_base[v] + (long long)pys[h] * W + pxs[h];
+    a.out_rgb[3 * p + 0] = s.c0 + s.T * a.bg[0];
+    a.out_rgb[3 * p + 1] = s.c1 + s.T * a.bg[1];
+    a.out_rgb[3 * p + 2] = s.c2 + s.T * a.bg[2];
+    a.out_T[p] = s.T;
+    a.out_n[p] = s.ncon;
+    a.out_last[p] = s.last;
+    a.out_dom[p] = s.dom;
   }
 }
 
@@ -126,7 +157,7 @@ extern "C" ADP_API int adp_render(int64_t n, const adp_projected* pr, const adp_
   a.out_last = out->last;
   a.out_dom = out->dominant;
   int n_tiles = cs.tile_base[n_views];
-  render_kernel<<<n_tiles, 256, 0, (cudaStream_t)stream>>>(a, cs);
+  render_kernel<<<n_tiles, RENDER_THREADS, 0, (cudaStream_t)stream>>>(a, cs);
   ADP_LAUNCH_CHECK();
   return ADP_OK;
 }

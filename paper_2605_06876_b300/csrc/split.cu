@@ -482,6 +482,7 @@ static inline GaussPtrs gp_of(const adp_gaussians* g) {
 
 struct ApplyArgs {
   GaussPtrs in, min_, vin, out, mout, vout;
+  const long long* counters;  // [1] kept, [3] new size
   bool has_m_in, has_v_in, has_m_out, has_v_out;
   int planes;
   const int* cand_of;
@@ -506,6 +507,7 @@ __device__ __forceinline__ void zero_gauss(const GaussPtrs& d, long long j, int 
 }
 
 __global__ void apply_keep_kernel(ApplyArgs a) {
+  if (a.counters[3] > a.out.n) return;  // the new population does not fit: write nothing
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.in.n;
        i += (long long)gridDim.x * blockDim.x) {
     int c = a.cand_of[i];
@@ -541,6 +543,7 @@ struct AppendArgs {
 };
 
 __global__ void apply_append_kernel(AppendArgs a) {
+  if (a.counters[3] > a.out.n) return;  // the new population does not fit: write nothing
   long long n_keep = a.counters[1];
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.nc;
        c += (long long)gridDim.x * blockDim.x) {
@@ -741,8 +744,8 @@ extern "C" ADP_API int adp_split_apply(const adp_gaussians* g, const adp_gaussia
   ADP_CHECK_ARG(n_cand == 0 || (candidates && status && n_children && noise), "NULL candidate arrays");
   ADP_CHECK_ARG(!m_in || (gauss_ok(m_in) && m_in->n == g->n), "bad m_in");
   ADP_CHECK_ARG(!v_in || (gauss_ok(v_in) && v_in->n == g->n), "bad v_in");
-  ADP_CHECK_ARG(!m_out || (gauss_ok(m_out) && m_out->n == out->n), "bad m_out");
-  ADP_CHECK_ARG(!v_out || (gauss_ok(v_out) && v_out->n == out->n), "bad v_out");
+  ADP_CHECK_ARG(!m_out || (gauss_ok(m_out) && m_out->n == out->n), "bad m_out (its n must equal out->n)");
+  ADP_CHECK_ARG(!v_out || (gauss_ok(v_out) && v_out->n == out->n), "bad v_out (its n must equal out->n)");
   ADP_CHECK_ARG(aligned(ws, 256), "workspace must be 256-byte aligned");
   long long n = g->n, nc = n_cand, rcap = regs->capacity;
   size_t need = split_ws_bytes(n, nc, rcap);
@@ -767,6 +770,7 @@ extern "C" ADP_API int adp_split_apply(const adp_gaussians* g, const adp_gaussia
   aa.cand_of = w.cand_of;
   aa.status = status;
   aa.keep_new = w.keep_new;
+  aa.counters = w.counters;
   if (n > 0) apply_keep_kernel<<<grid_for(n, 256, 148 * 16), 256, 0, st>>>(aa);
   if (nc > 0) {
     AppendArgs ap;

@@ -355,8 +355,9 @@ class SplitPlan:
 
 
 def split_plan(g: Gaussians, cams, regions: Regions, candidates, count, params=None, ws=None,
-               stream=None):
-    """adp_split_plan: statuses and child counts; reads the new size back (one sync)."""
+               stream=None, sync=True):
+    """adp_split_plan: statuses and child counts. With sync=True the new size is read
+    back (one synchronisation); otherwise it stays on the device (plan.d_new_n)."""
     params = params or A.default_params()
     ca = A.cameras(cams)
     dev = g.mean_logit.device
@@ -371,19 +372,24 @@ def split_plan(g: Gaussians, cams, regions: Regions, candidates, count, params=N
     gc, rc = g.c(), regions.c()
     A.check(A.lib().adp_split_plan(C.byref(gc), ca, len(cams), C.byref(rc), _p(candidates), nc,
                                    _p(count), C.byref(params), _p(status), _p(nch), _p(d_new_n),
-                                   C.byref(h_new_n), _p(ws), ws.numel(), _stream(stream)),
-            "adp_split_plan")
-    return SplitPlan(status[:nc], nch[:nc], int(h_new_n.value), ws, d_new_n)
+                                   C.byref(h_new_n) if sync else None, _p(ws), ws.numel(),
+                                   _stream(stream)), "adp_split_plan")
+    return SplitPlan(status[:nc], nch[:nc], int(h_new_n.value) if sync else None, ws, d_new_n)
 
 
 def split_apply(g: Gaussians, plan: SplitPlan, regions: Regions, candidates, noise, params=None,
-                m_in: Gaussians = None, v_in: Gaussians = None, with_state=True, stream=None):
-    """adp_split_apply: the new population (and Adam moments)."""
+                m_in: Gaussians = None, v_in: Gaussians = None, with_state=True, stream=None,
+                out: Gaussians = None, m_out: Gaussians = None, v_out: Gaussians = None):
+    """adp_split_apply: the new population (and Adam moments). Given out (and m_out,
+    v_out) the population is written into those capacity buffers (entries
+    [0, plan.d_new_n)); otherwise buffers of exactly the planned size are made."""
     params = params or A.default_params()
     dev = g.mean_logit.device
-    out = Gaussians(plan.new_n, g.sh_degree, dev, zero=False)
-    m_out = Gaussians(plan.new_n, g.sh_degree, dev, zero=False) if with_state else None
-    v_out = Gaussians(plan.new_n, g.sh_degree, dev, zero=False) if with_state else None
+    if out is None:
+        new_n = plan.new_n if plan.new_n is not None else int(plan.d_new_n.item())
+        out = Gaussians(new_n, g.sh_degree, dev, zero=False)
+        m_out = Gaussians(new_n, g.sh_degree, dev, zero=False) if with_state else None
+        v_out = Gaussians(new_n, g.sh_degree, dev, zero=False) if with_state else None
     nc = int(candidates.numel())
     if noise is None:
         noise = torch.zeros((max(nc, 1), 2, 3), dtype=F32, device=dev)

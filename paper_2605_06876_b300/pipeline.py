@@ -3,9 +3,10 @@
 A step runs the whole hot path on one stream: projection, binning and depth sort,
 compositing with the dominant map, error statistics, top-k candidate choice by
 error mass, error regions, the render backward of the L1 loss, one Adam step, and
-the AdpSplit operator (plan, one read-back of the new population size, apply). The
-new population is returned; the step's own population is updated only by Adam, so
-repeated steps see the same workload.
+the AdpSplit operator (plan and apply into buffers sized for the largest possible
+result, so no step synchronises with the host). The new population (the first
+plan.d_new_n entries of the returned buffers) is returned; the step's own population
+is updated only by Adam, so repeated steps see the same workload.
 """
 from __future__ import annotations
 
@@ -79,6 +80,11 @@ class PlainStep:
         self.ws_topk = ops.workspace(A.lib().adp_select_topk_workspace_size(n), self.dev)
         self.ws_bwd = ops.workspace(A.lib().adp_render_backward_workspace_size(n, self.V), self.dev)
         self.ws_split = ops.workspace(ops.split_workspace_size(n, self.k, cap), self.dev)
+        # the largest population a split can produce: no read-back inside a step
+        self.out_capacity = n + self.k * (self.params.n_max + 1)
+        self.out = ops.Gaussians(self.out_capacity, g.sh_degree, self.dev, zero=False)
+        self.m_out = ops.Gaussians(self.out_capacity, g.sh_degree, self.dev, zero=False)
+        self.v_out = ops.Gaussians(self.out_capacity, g.sh_degree, self.dev, zero=False)
         torch.cuda.synchronize()
 
     def step(self, noise, timer: StageTimer = None):
@@ -106,14 +112,18 @@ class PlainStep:
         self.adam_t += 1
         ops.adam_step(g, self.grad, self.m, self.v, self.adam_t, self.lr)
         mark("split_plan")
-        plan = ops.split_plan(g, cams, self.regions, self.cand, self.count, prm, ws=self.ws_split)
+        plan = ops.split_plan(g, cams, self.regions, self.cand, self.count, prm, ws=self.ws_split,
+                              sync=False)
         mark("split_apply")
-        new_g, new_m, new_v = ops.split_apply(g, plan, self.regions, self.cand, noise, prm,
-                                              m_in=self.m, v_in=self.v)
+        ops.split_apply(g, plan, self.regions, self.cand, noise, prm, m_in=self.m, v_in=self.v,
+                        out=self.out, m_out=self.m_out, v_out=self.v_out)
         mark("end")
-        return new_g, new_m, new_v, plan
+        return self.out, self.m_out, self.v_out, plan
 
-    def check_capacity(self):
-        """True if the last step's instances and regions fit their buffers."""
-        return (int(self.bins.n_inst.item()) <= self.bins.capacity and
-                int(self.regions.count.item()) <= self.regions.capacity)
+    def check_capacity(self, plan=None):
+        """True if the last step's instances, regions (and population) fit their buffers."""
+        ok = (int(self.bins.n_inst.item()) <= self.bins.capacity and
+              int(self.regions.count.item()) <= self.regions.capacity)
+        if plan is not None:
+            ok = ok and int(plan.d_new_n.item()) <= self.out_capacity
+        return ok

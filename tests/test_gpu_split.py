@@ -186,3 +186,35 @@ def test_adam_matches_oracle():
         O.adam(th, g_, m_, v_, step)
     np.testing.assert_allclose(O.theta_of(G[0].to_scene()), th, rtol=2e-5, atol=2e-6)
     np.testing.assert_allclose(O.theta_of(G[2].to_scene()), m_, rtol=2e-5, atol=1e-6)
+
+
+def test_split_apply_into_capacity_buffers_without_sync():
+    """Planning without reading the size back and applying into buffers sized for
+    the largest possible result gives the same population in the first new_n
+    entries; a capacity below the planned size leaves the buffers untouched."""
+    sc, cam, target = c0_inputs()
+    k = 200
+    orc = _oracle_case(sc, [cam], [target], k)
+    g = ops.Gaussians.from_scene(sc, DEV)
+    rg = orc["regions"]
+    regs = ops.Regions.from_arrays(rg["view"], rg["parent"], rg["label"], rg["stats"], rg["band"],
+                                   rg["moments"], DEV)
+    cand = torch.as_tensor(orc["cand"], device=DEV)
+    count = torch.as_tensor(orc["count"], device=DEV)
+    noise = torch.as_tensor(scenes.fallback_noise(7, k), device=DEV)
+    plan = ops.split_plan(g, [cam], regs, cand, count, sync=False)
+    assert plan.new_n is None
+    cap = g.n + k * 20
+    big = ops.Gaussians(cap, 0, DEV, zero=True)
+    ops.split_apply(g, plan, regs, cand, noise, with_state=False, out=big)
+    exact, _, _ = ops.split_apply(g, plan, regs, cand, noise, with_state=False)
+    torch.cuda.synchronize()
+    new_n = int(plan.d_new_n.item())
+    assert new_n == orc["split"]["new_n"] == exact.n
+    for a, b in zip(big.tensors(), exact.tensors()):
+        sl = (slice(None), slice(0, new_n)) if a.dim() == 3 else (slice(0, new_n),)
+        assert torch.equal(a[sl], b)
+    small = ops.Gaussians(new_n - 1, 0, DEV, zero=True)
+    ops.split_apply(g, plan, regs, cand, noise, with_state=False, out=small)
+    torch.cuda.synchronize()
+    assert all(int(t.abs().sum().item()) == 0 for t in small.tensors())
