@@ -160,6 +160,12 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     if not stepper.check_capacity():
         raise RuntimeError("instance or region capacity exceeded during warm-up")
+    use_graph = not args.no_graph
+    if use_graph:
+        stepper.capture(noise)
+        for _ in range(args.warmup):
+            stepper.replay()
+        torch.cuda.synchronize()
 
     def barrier():
         if world > 1:
@@ -170,21 +176,31 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t_wall0 = time.time()
     step_ms = []
-    stage_ms = {}
     last_plan = None
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
         flush.random_(0, 255)  # evict L2 between steps (not timed)
-        t = StageTimer(stream)
-        out = stepper.step(noise, t)
+        ev0.record(stream)
+        out = stepper.replay() if use_graph else stepper.step(noise)
+        ev1.record(stream)
         torch.cuda.synchronize()
-        d = t.durations()
-        for kname, val in d.items():
-            stage_ms[kname] = stage_ms.get(kname, 0.0) + val
-        step_ms.append(sum(d.values()))
+        step_ms.append(ev0.elapsed_time(ev1))
         last_plan = out[3]
     barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop(t_wall0, time.time())
+    # per-stage breakdown and the dominant kernel's duration: the same steps run
+    # eagerly with CUDA events between stages on the launching stream
+    stage_ms = {}
+    stage_steps = max(1, min(args.steps, 20))
+    for _ in range(stage_steps):
+        flush.random_(0, 255)
+        t = StageTimer(stream)
+        stepper.step(noise, t)
+        torch.cuda.synchronize()
+        for kname, val in t.durations().items():
+            stage_ms[kname] = stage_ms.get(kname, 0.0) + val
     if not stepper.check_capacity(last_plan):
         raise RuntimeError("instance, region or population capacity exceeded in the timed region")
     new_n = int(last_plan.d_new_n.item())
@@ -220,7 +236,7 @@ def run_ours(args, rank, world, local_rank):
             dst.copy_(src.view(dst.shape), non_blocking=True)
         target.copy_(tgt_h, non_blocking=True)
         noise.copy_(noise_h, non_blocking=True)
-        out = stepper.step(noise)
+        out = stepper.replay() if use_graph else stepper.step(noise)
         st_h.copy_(out[3].status, non_blocking=True)
         nc_h.copy_(out[3].n_children, non_blocking=True)
         stream.synchronize()
@@ -240,7 +256,7 @@ def run_ours(args, rank, world, local_rank):
     R = int(stepper.regions.count.item())
     sb = stage_bytes(n, n_vis, K, stepper.P, stepper.bins.ranges.shape[0], ops.sh_planes(3), R,
                      stepper.k)
-    per_stage = {k: v / args.steps for k, v in stage_ms.items()}
+    per_stage = {k: v / stage_steps for k, v in stage_ms.items()}
     dom = max(per_stage, key=per_stage.get)
     peak, peak_kind, _ = _peaks()
     achieved = sb[dom] / (per_stage[dom] * 1e-3) / 1e9
@@ -256,7 +272,8 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": None, "peak_source": peak_kind},
-        "stages_ms": {k: round(v, 4) for k, v in per_stage.items()},
+        "graph": use_graph,
+        "stages_ms_eager": {k: round(v, 4) for k, v in per_stage.items()},
         "stage_gbs": {k: round(sb[k] / (per_stage[k] * 1e-3) / 1e9, 1) for k in per_stage
                       if k in sb and per_stage[k] > 0},
         "workload_counts": {"visible": n_vis, "instances": K, "regions": R,
@@ -373,6 +390,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly")
     ap.add_argument("--no-launch-count", action="store_true",
                     help="skip the CUPTI kernel count (for runs under ncu)")
     args = ap.parse_args()

@@ -294,11 +294,13 @@ ADP_API int adp_render_backward(const adp_gaussians* g, const adp_projected* pr,
                                 void* ws, size_t ws_bytes, adp_stream_t stream);
 
 /* --- Adam (the baselines' optimizer, unchanged by the paper, Sec. 5.1). -----
- * In place, bias-corrected, step >= 1. lr (host float[6]): mean, opacity
- * logit, log-scale, quaternion, SH DC, SH rest. */
+ * In place, bias-corrected. The step number t >= 1 is `step`, or, if d_step
+ * (device int32) is non-NULL, *d_step, which the call then increments on the
+ * device -- so a step replayed from a captured CUDA graph advances t. lr (host
+ * float[6]): mean, opacity logit, log-scale, quaternion, SH DC, SH rest. */
 ADP_API int adp_adam_step(adp_gaussians* param, const adp_gaussians* grad, adp_gaussians* m,
-                          adp_gaussians* v, int32_t step, const float* lr, float beta1,
-                          float beta2, float eps, adp_stream_t stream);
+                          adp_gaussians* v, int32_t step, int32_t* d_step, const float* lr,
+                          float beta1, float beta2, float eps, adp_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -99,7 +99,7 @@ _PROTOS = {
                                       _vp, _vp, P(AdpCamera), _i32, P(C.c_float), P(AdpParams),
                                       P(AdpGaussians), _vp, C.c_size_t, _vp]),
     "adp_adam_step": (C.c_int, [P(AdpGaussians), P(AdpGaussians), P(AdpGaussians),
-                                P(AdpGaussians), _i32, P(C.c_float), C.c_float, C.c_float,
+                                P(AdpGaussians), _i32, _vp, P(C.c_float), C.c_float, C.c_float,
                                 C.c_float, _vp]),
 }
 

@@ -14,24 +14,31 @@ struct AdamArgs {
   int planes;
   float lr[6];
   float b1, b2, eps, bc1, bc2;
+  const int* d_step;  // if set, the step number is read here (bias corrections on device)
 };
 
 __device__ __forceinline__ float adam1(float& p, float g, float& m, float& v, float lr,
-                                       const AdamArgs& a) {
+                                       const AdamArgs& a, float bc1, float bc2) {
   m = a.b1 * m + (1.f - a.b1) * g;
   v = a.b2 * v + (1.f - a.b2) * g * g;
-  float mh = m / a.bc1, vh = v / a.bc2;
+  float mh = m / bc1, vh = v / bc2;
   p -= lr * mh / (sqrtf(vh) + a.eps);
   return p;
 }
 
 __device__ __forceinline__ void adam4(float4* P, const float4* G, float4* M, float4* V,
                                       long long idx, const float* lr4, const AdamArgs& a) {
+  float bc1 = a.bc1, bc2 = a.bc2;
+  if (a.d_step) {
+    const float t = (float)*a.d_step;
+    bc1 = 1.f - powf(a.b1, t);
+    bc2 = 1.f - powf(a.b2, t);
+  }
   float4 p = P[idx], g = G[idx], m = M[idx], v = V[idx];
-  adam1(p.x, g.x, m.x, v.x, lr4[0], a);
-  adam1(p.y, g.y, m.y, v.y, lr4[1], a);
-  adam1(p.z, g.z, m.z, v.z, lr4[2], a);
-  adam1(p.w, g.w, m.w, v.w, lr4[3], a);
+  adam1(p.x, g.x, m.x, v.x, lr4[0], a, bc1, bc2);
+  adam1(p.y, g.y, m.y, v.y, lr4[1], a, bc1, bc2);
+  adam1(p.z, g.z, m.z, v.z, lr4[2], a, bc1, bc2);
+  adam1(p.w, g.w, m.w, v.w, lr4[3], a, bc1, bc2);
   P[idx] = p;
   M[idx] = m;
   V[idx] = v;
@@ -60,16 +67,18 @@ __global__ void adam_kernel(AdamArgs a) {
   }
 }
 
+__global__ void adam_step_advance_kernel(int* d_step) { *d_step += 1; }
+
 }  // namespace adp
 
 using namespace adp;
 
 extern "C" ADP_API int adp_adam_step(adp_gaussians* param, const adp_gaussians* grad,
                                      adp_gaussians* m, adp_gaussians* v, int32_t step,
-                                     const float* lr, float beta1, float beta2, float eps,
-                                     adp_stream_t stream) {
+                                     int32_t* d_step, const float* lr, float beta1, float beta2,
+                                     float eps, adp_stream_t stream) {
   ADP_CHECK_ARG(param && grad && m && v && lr, "NULL argument");
-  ADP_CHECK_ARG(step >= 1, "step must be >= 1");
+  ADP_CHECK_ARG(d_step || step >= 1, "step must be >= 1");
   ADP_CHECK_ARG(grad->n == param->n && m->n == param->n && v->n == param->n, "size mismatch");
   ADP_CHECK_ARG(param->sh_degree >= 0 && param->sh_degree <= 3, "sh_degree must be 0..3");
   if (param->n == 0) return ADP_OK;
@@ -88,9 +97,11 @@ extern "C" ADP_API int adp_adam_step(adp_gaussians* param, const adp_gaussians* 
   a.b1 = beta1;
   a.b2 = beta2;
   a.eps = eps;
-  a.bc1 = 1.f - powf(beta1, (float)step);
-  a.bc2 = 1.f - powf(beta2, (float)step);
+  a.d_step = d_step;
+  a.bc1 = d_step ? 1.f : 1.f - powf(beta1, (float)step);
+  a.bc2 = d_step ? 1.f : 1.f - powf(beta2, (float)step);
   adam_kernel<<<dim3(grid_for(param->n, 256), 3 + a.planes), 256, 0, (cudaStream_t)stream>>>(a);
+  if (d_step) adam_step_advance_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(d_step);
   ADP_LAUNCH_CHECK();
   return ADP_OK;
 }

@@ -205,45 +205,10 @@ struct BwdGaussArgs {
   float4* g_ls;
   float4* g_q;
   float* g_sh;
-  const int* list;
-  const unsigned long long* n_list;
 };
 
-// Zeroes the gradient of every Gaussian rendered in no view and appends the
-// others to a list (warp-aggregated), so the heavy chain-rule pass runs on full
-// warps of visible Gaussians only. The list order does not affect the results.
-__global__ void bwd_visible_kernel(const int* tiles, long long n, int n_views, int planes,
-                                   float4* g_ml, float4* g_ls, float4* g_q, float4* g_sh,
-                                   int* list, unsigned long long* count) {
-  for (long long i0 = blockIdx.x * (long long)blockDim.x; i0 < n;
-       i0 += (long long)gridDim.x * blockDim.x) {
-    long long i = i0 + threadIdx.x;
-    bool seen = false;
-    if (i < n) {
-      for (int v = 0; v < n_views; ++v) seen |= tiles[(long long)v * n + i] > 0;
-      if (!seen) {
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        g_ml[i] = z;
-        g_ls[i] = z;
-        g_q[i] = z;
-        for (int p = 0; p < planes; ++p) g_sh[(long long)p * n + i] = z;
-      }
-    }
-    unsigned m = __ballot_sync(0xffffffffu, seen);
-    if (m) {
-      unsigned long long base = 0;
-      int lane = threadIdx.x & 31;
-      if (lane == __ffs(m) - 1) base = atomicAdd(count, (unsigned long long)__popc(m));
-      base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-      if (seen) list[base + __popc(m & lanemask_lt())] = (int)i;
-    }
-  }
-}
-
-__global__ void __launch_bounds__(128) bwd_gauss_kernel(BwdGaussArgs a, CamSet cs) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)*a.n_list) return;
-  const long long i = a.list[t];
+// Chain rule of one visible Gaussian, summed over views.
+__device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
   const int K = sh_coeffs(a.deg);
   const int planes = sh_planes(a.deg);
   float4 ml = a.mean_logit[i], ls = a.logscale[i], q4 = a.quat[i];
@@ -409,14 +374,49 @@ __global__ void __launch_bounds__(128) bwd_gauss_kernel(BwdGaussArgs a, CamSet c
   }
 }
 
+constexpr int BWDG_THREADS = 128;
+constexpr int BWDG_CHUNK = 512;
+
+// Each CTA takes BWDG_CHUNK Gaussians: those rendered in no view get zero
+// gradients at once, the others are compacted in shared memory and chained by
+// full warps, so the heavy per-Gaussian work is not diluted by idle lanes.
+__global__ void __launch_bounds__(BWDG_THREADS) bwd_gauss_kernel(BwdGaussArgs a, CamSet cs) {
+  __shared__ int s_list[BWDG_CHUNK];
+  __shared__ int s_cnt;
+  const int planes = sh_planes(a.deg);
+  for (long long c0 = (long long)blockIdx.x * BWDG_CHUNK; c0 < a.n;
+       c0 += (long long)gridDim.x * BWDG_CHUNK) {
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < BWDG_CHUNK; q += BWDG_THREADS) {
+      long long i = c0 + q;
+      if (i >= a.n) break;
+      bool seen = false;
+      for (int v = 0; v < cs.n_views; ++v) seen |= a.tiles[(long long)v * a.n + i] > 0;
+      if (seen) {
+        s_list[atomicAdd(&s_cnt, 1)] = q;
+      } else {
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        a.g_ml[i] = z;
+        a.g_ls[i] = z;
+        a.g_q[i] = z;
+        for (int p = 0; p < planes; ++p) reinterpret_cast<float4*>(a.g_sh)[(long long)p * a.n + i] = z;
+      }
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+    for (int q = threadIdx.x; q < cnt; q += BWDG_THREADS) bwd_one(a, cs, c0 + s_list[q]);
+    __syncthreads();
+  }
+}
+
 }  // namespace adp
 
 using namespace adp;
 
 extern "C" ADP_API size_t adp_render_backward_workspace_size(int64_t n, int32_t n_views) {
   if (n < 0 || n_views < 1) return 0;
-  return carve_bytes<float4>(3 * (size_t)n * n_views) + carve_bytes<int>(n) +
-         carve_bytes<unsigned long long>(1);
+  return carve_bytes<float4>(3 * (size_t)n * n_views);
 }
 
 extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_projected* pr,
@@ -441,10 +441,7 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   cudaStream_t st = (cudaStream_t)stream;
   Carver cv(ws, ws_bytes);
   float4* g2d = cv.take<float4>(3 * (size_t)g->n * n_views);
-  int* list = cv.take<int>(g->n);
-  unsigned long long* n_list = cv.take<unsigned long long>(1);
   ADP_CUDA(cudaMemsetAsync(g2d, 0, sizeof(float4) * 3 * (size_t)g->n * n_views, st));
-  ADP_CUDA(cudaMemsetAsync(n_list, 0, sizeof(unsigned long long), st));
   BwdPixArgs pa;
   pa.xyod = reinterpret_cast<const float4*>(pr->xy_opacity_depth);
   pa.conic = reinterpret_cast<const float4*>(pr->conic);
@@ -477,12 +474,7 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   ga.g_ls = reinterpret_cast<float4*>(grad->logscale);
   ga.g_q = reinterpret_cast<float4*>(grad->quat);
   ga.g_sh = grad->sh;
-  ga.list = list;
-  ga.n_list = n_list;
-  bwd_visible_kernel<<<grid_for(g->n, 256, 148 * 16), 256, 0, st>>>(
-      pr->tiles_touched, g->n, n_views, sh_planes(g->sh_degree), ga.g_ml, ga.g_ls, ga.g_q,
-      reinterpret_cast<float4*>(grad->sh), list, n_list);
-  bwd_gauss_kernel<<<grid_for(g->n, 128), 128, 0, st>>>(ga, cs);
+  bwd_gauss_kernel<<<(unsigned)((g->n + BWDG_CHUNK - 1) / BWDG_CHUNK), BWDG_THREADS, 0, st>>>(ga, cs);
   ADP_LAUNCH_CHECK();
   return ADP_OK;
 }

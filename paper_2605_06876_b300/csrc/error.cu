@@ -200,6 +200,17 @@ __global__ void topk_pick_kernel(unsigned* hist, int shift, SelectState* st) {
   hist[b] = 0;
 }
 
+// Initial selection state (nothing fixed, k keys to take) and an empty histogram.
+__global__ void topk_reset_kernel(SelectState* st, unsigned* hist, long long k) {
+  if (threadIdx.x == 0) {
+    st->prefix = 0ull;
+    st->mask = 0ull;
+    st->remaining = k;
+    st->pad = 0;
+  }
+  hist[threadIdx.x] = 0u;
+}
+
 // ------------------------------------------------------------------ erosion
 
 // Horizontal then vertical AND over radius r; outside the image counts as set.
@@ -657,9 +668,7 @@ extern "C" ADP_API int adp_select_topk(const double* mass, int64_t n, int64_t k,
   uint8_t* sel = c.take<uint8_t>(n);
   void* sw = c.take<char>(scan_workspace_bytes(n));
   long long* cnt = c.take<long long>(2);
-  SelectState init = {0ull, 0ull, (long long)k, 0};
-  ADP_CUDA(cudaMemcpyAsync(ss, &init, sizeof(init), cudaMemcpyHostToDevice, st));
-  ADP_CUDA(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned), st));
+  topk_reset_kernel<<<1, 256, 0, st>>>(ss, hist, (long long)k);
   unsigned g = grid_for(n, 256, 148 * 8);
   for (int shift = 56; shift >= 0; shift -= 8) {
     topk_hist_kernel<<<g, 256, 0, st>>>(mass, n, shift, ss, hist);

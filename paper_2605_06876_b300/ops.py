@@ -432,8 +432,14 @@ ADAM_LR = (1.6e-4, 0.05, 0.005, 0.001, 0.0025, 0.0025 / 20.0)
 
 def adam_step(param: Gaussians, grad: Gaussians, m: Gaussians, v: Gaussians, step, lr=ADAM_LR,
               beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
-    """adp_adam_step: one in-place bias-corrected Adam step."""
+    """adp_adam_step: one in-place bias-corrected Adam step. `step` is an int, or a
+    device int32 tensor of one element holding the step number (advanced by the call)."""
     lrc = (C.c_float * 6)(*[float(x) for x in lr])
     pc, gc, mc, vc = param.c(), grad.c(), m.c(), v.c()
-    A.check(A.lib().adp_adam_step(C.byref(pc), C.byref(gc), C.byref(mc), C.byref(vc), int(step),
-                                  lrc, beta1, beta2, eps, _stream(stream)), "adp_adam_step")
+    if isinstance(step, torch.Tensor):
+        host_step, d_step = 0, _p(step)
+    else:
+        host_step, d_step = int(step), None
+    A.check(A.lib().adp_adam_step(C.byref(pc), C.byref(gc), C.byref(mc), C.byref(vc), host_step,
+                                  d_step, lrc, beta1, beta2, eps, _stream(stream)),
+            "adp_adam_step")

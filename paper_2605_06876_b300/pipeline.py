@@ -57,7 +57,8 @@ class PlainStep:
         self.count = torch.empty(n, dtype=torch.int32, device=self.dev)
         self.mass = torch.empty(n, dtype=torch.float64, device=self.dev)
         self.cand = torch.empty(self.k, dtype=torch.int32, device=self.dev)
-        self.adam_t = 0
+        self.adam_t = torch.ones(1, dtype=torch.int32, device=self.dev)  # Adam step, on device
+        self.graph = None
         # size the instance and region buffers from one probing pass
         ops.project(g, self.cams, self.params, self.pr)
         probe = ops.bin_sort(n, self.pr, self.cams, self.params)
@@ -109,7 +110,6 @@ class PlainStep:
         ops.render_backward(g, self.pr, self.bins, self.img, cams, target=self.target, bg=self.bg,
                             params=prm, grad=self.grad, ws=self.ws_bwd)
         mark("adam")
-        self.adam_t += 1
         ops.adam_step(g, self.grad, self.m, self.v, self.adam_t, self.lr)
         mark("split_plan")
         plan = ops.split_plan(g, cams, self.regions, self.cand, self.count, prm, ws=self.ws_split,
@@ -119,6 +119,24 @@ class PlainStep:
                         out=self.out, m_out=self.m_out, v_out=self.v_out)
         mark("end")
         return self.out, self.m_out, self.v_out, plan
+
+    def capture(self, noise):
+        """Captures one step in a CUDA graph (no step synchronises with the host, and
+        every buffer is preallocated, so the whole step replays as one launch)."""
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.step(noise)
+        torch.cuda.current_stream().wait_stream(side)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.graph_out = self.step(noise)
+        return self.graph_out
+
+    def replay(self):
+        """One step from the captured graph; returns what the captured step returned."""
+        self.graph.replay()
+        return self.graph_out
 
     def check_capacity(self, plan=None):
         """True if the last step's instances, regions (and population) fit their buffers."""
