@@ -105,6 +105,14 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- algorithmic bytes
 
+# FP32 operations (an FMA counts 2) of the compositing inner loops: evaluating
+# alpha at one pixel for one Gaussian, blending it in the forward, and the
+# contribution of one blended pair to the 2D gradients in the backward.
+FLOP_EVAL = 16
+FLOP_BLEND_FWD = 12
+FLOP_BLEND_BWD = 56
+
+
 def stage_bytes(n, n_vis, K, P, n_tiles, sh_planes, regions, k):
     """Algorithmic DRAM bytes of each stage for one step (each input read once, each
     output written once; see the design doc for the per-unit figures)."""
@@ -161,8 +169,9 @@ def run_ours(args, rank, world, local_rank):
     if not stepper.check_capacity():
         raise RuntimeError("instance or region capacity exceeded during warm-up")
     use_graph = not args.no_graph
+    timer = StageTimer()
     if use_graph:
-        stepper.capture(noise)
+        stepper.capture(noise, timer)
         for _ in range(args.warmup):
             stepper.replay()
         torch.cuda.synchronize()
@@ -177,30 +186,27 @@ def run_ours(args, rank, world, local_rank):
     t_wall0 = time.time()
     step_ms = []
     last_plan = None
+    stage_ms = {}
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
         flush.random_(0, 255)  # evict L2 between steps (not timed)
         ev0.record(stream)
-        out = stepper.replay() if use_graph else stepper.step(noise)
+        if use_graph:
+            out = stepper.replay()  # re-records the captured stage events
+        else:
+            timer = StageTimer(stream)
+            out = stepper.step(noise, timer)
         ev1.record(stream)
         torch.cuda.synchronize()
         step_ms.append(ev0.elapsed_time(ev1))
+        for kname, val in timer.durations().items():  # stages of this step
+            stage_ms[kname] = stage_ms.get(kname, 0.0) + val
         last_plan = out[3]
     barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop(t_wall0, time.time())
-    # per-stage breakdown and the dominant kernel's duration: the same steps run
-    # eagerly with CUDA events between stages on the launching stream
-    stage_ms = {}
-    stage_steps = max(1, min(args.steps, 20))
-    for _ in range(stage_steps):
-        flush.random_(0, 255)
-        t = StageTimer(stream)
-        stepper.step(noise, t)
-        torch.cuda.synchronize()
-        for kname, val in t.durations().items():
-            stage_ms[kname] = stage_ms.get(kname, 0.0) + val
+    stage_steps = args.steps
     if not stepper.check_capacity(last_plan):
         raise RuntimeError("instance, region or population capacity exceeded in the timed region")
     new_n = int(last_plan.d_new_n.item())
@@ -258,8 +264,26 @@ def run_ours(args, rank, world, local_rank):
                      stepper.k)
     per_stage = {k: v / stage_steps for k, v in stage_ms.items()}
     dom = max(per_stage, key=per_stage.get)
-    peak, peak_kind, _ = _peaks()
-    achieved = sb[dom] / (per_stage[dom] * 1e-3) / 1e9
+    peak, peak_kind, peaks = _peaks()
+    # exact per-pixel work of the last step: list positions evaluated up to the last
+    # blended Gaussian, and blended (pixel, Gaussian) pairs
+    n_eval = int(stepper.img.last.sum().item())
+    n_blend = int(stepper.img.n_contrib.sum().item())
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clock_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    alu_peak = sm_count * 128 * 2 * clock_mhz * 1e6 / 1e12  # TFLOP/s, FP32 FMA = 2
+    flops = {"render": n_eval * FLOP_EVAL + n_blend * FLOP_BLEND_FWD,
+             "render_backward": n_eval * FLOP_EVAL + n_blend * FLOP_BLEND_BWD}
+    if dom in flops:
+        ach = flops[dom] / (per_stage[dom] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": round(ach, 2), "peak": round(alu_peak, 1),
+                "unit": "TFLOP/s", "frac": round(ach / alu_peak, 4), "traffic": None,
+                "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz"}
+    else:
+        ach = sb[dom] / (per_stage[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
+                "peak_source": peak_kind}
     launches = None if args.no_launch_count else count_launches(stepper, noise) * args.steps
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
@@ -269,14 +293,15 @@ def run_ours(args, rank, world, local_rank):
         "config": dict(WORKLOAD, parallelism=f"replicas{world}" if world > 1 else "single"),
         "e2e": {"value": round(1e3 / e2e_ms * world, 3), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
-                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": None, "peak_source": peak_kind},
+        "roofline": roof,
+        "step_hbm": {"algorithmic_bytes": int(sum(sb.values())),
+                     "frac": round(sum(sb.values()) / (ms_per_step * 1e-3) / 1e9 / peak, 4)},
         "graph": use_graph,
-        "stages_ms_eager": {k: round(v, 4) for k, v in per_stage.items()},
+        "stages_ms": {k: round(v, 4) for k, v in per_stage.items()},
         "stage_gbs": {k: round(sb[k] / (per_stage[k] * 1e-3) / 1e9, 1) for k in per_stage
                       if k in sb and per_stage[k] > 0},
         "workload_counts": {"visible": n_vis, "instances": K, "regions": R,
+                            "pixel_evaluations": n_eval, "blended_pairs": n_blend,
                             "candidates": stepper.k, "new_population": new_n},
         "clocks": clocks,
         "gpu_launches": launches,

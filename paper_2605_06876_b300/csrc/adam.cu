@@ -27,13 +27,8 @@ __device__ __forceinline__ float adam1(float& p, float g, float& m, float& v, fl
 }
 
 __device__ __forceinline__ void adam4(float4* P, const float4* G, float4* M, float4* V,
-                                      long long idx, const float* lr4, const AdamArgs& a) {
-  float bc1 = a.bc1, bc2 = a.bc2;
-  if (a.d_step) {
-    const float t = (float)*a.d_step;
-    bc1 = 1.f - powf(a.b1, t);
-    bc2 = 1.f - powf(a.b2, t);
-  }
+                                      long long idx, const float* lr4, const AdamArgs& a,
+                                      float bc1, float bc2) {
   float4 p = P[idx], g = G[idx], m = M[idx], v = V[idx];
   adam1(p.x, g.x, m.x, v.x, lr4[0], a, bc1, bc2);
   adam1(p.y, g.y, m.y, v.y, lr4[1], a, bc1, bc2);
@@ -47,23 +42,36 @@ __device__ __forceinline__ void adam4(float4* P, const float4* G, float4* M, flo
 // blockIdx.y selects the plane: 0 mean+logit, 1 log-scale, 2 quaternion,
 // 3.. SH planes; each thread updates one float4 of it.
 __global__ void adam_kernel(AdamArgs a) {
+  __shared__ float s_bc[2];
+  if (threadIdx.x == 0) {  // bias corrections, once per block
+    float bc1 = a.bc1, bc2 = a.bc2;
+    if (a.d_step) {
+      const float t = (float)*a.d_step;
+      bc1 = 1.f - powf(a.b1, t);
+      bc2 = 1.f - powf(a.b2, t);
+    }
+    s_bc[0] = bc1;
+    s_bc[1] = bc2;
+  }
+  __syncthreads();
+  const float bc1 = s_bc[0], bc2 = s_bc[1];
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const int q = blockIdx.y;
   if (q == 0) {
     float lr4[4] = {a.lr[0], a.lr[0], a.lr[0], a.lr[1]};
-    adam4(a.p_ml, a.g_ml, a.m_ml, a.v_ml, i, lr4, a);
+    adam4(a.p_ml, a.g_ml, a.m_ml, a.v_ml, i, lr4, a, bc1, bc2);
   } else if (q == 1) {
     float lr4[4] = {a.lr[2], a.lr[2], a.lr[2], 0.f};
-    adam4(a.p_ls, a.g_ls, a.m_ls, a.v_ls, i, lr4, a);
+    adam4(a.p_ls, a.g_ls, a.m_ls, a.v_ls, i, lr4, a, bc1, bc2);
   } else if (q == 2) {
     float lr4[4] = {a.lr[3], a.lr[3], a.lr[3], a.lr[3]};
-    adam4(a.p_q, a.g_q, a.m_q, a.v_q, i, lr4, a);
+    adam4(a.p_q, a.g_q, a.m_q, a.v_q, i, lr4, a, bc1, bc2);
   } else {
     const int p = q - 3;
     float lr4[4];
     for (int l = 0; l < 4; ++l) lr4[l] = (4 * p + l) < 3 ? a.lr[4] : a.lr[5];
-    adam4(a.p_sh, a.g_sh, a.m_sh, a.v_sh, (long long)p * a.n + i, lr4, a);
+    adam4(a.p_sh, a.g_sh, a.m_sh, a.v_sh, (long long)p * a.n + i, lr4, a, bc1, bc2);
   }
 }
 

@@ -17,22 +17,44 @@ from . import ops
 
 
 class StageTimer:
-    """CUDA events around each stage, on the stream the stages run on."""
+    """CUDA timing events between stages, on the stream the stages run on. The
+    events are recorded with cudaEventRecordExternal, so inside a CUDA-graph
+    capture they become event-record nodes and every replay re-records them: the
+    stage durations of the latest replay (or eager step) come from durations()."""
 
     def __init__(self, stream=None):
+        from cuda.bindings import runtime as rt
+
+        self.rt = rt
         self.stream = stream
         self.events = []
 
     def mark(self, name):
-        ev = torch.cuda.Event(enable_timing=True)
-        ev.record(self.stream)
+        rt = self.rt
+        err, ev = rt.cudaEventCreateWithFlags(rt.cudaEventDefault)
+        if err != rt.cudaError_t.cudaSuccess:
+            raise RuntimeError(f"cudaEventCreateWithFlags: {err}")
+        s = (self.stream or torch.cuda.current_stream()).cuda_stream
+        (err,) = rt.cudaEventRecordWithFlags(ev, s, rt.cudaEventRecordExternal)
+        if err != rt.cudaError_t.cudaSuccess:
+            raise RuntimeError(f"cudaEventRecordWithFlags: {err}")
         self.events.append((name, ev))
 
     def durations(self):
         out = {}
         for (name, a), (_, b) in zip(self.events[:-1], self.events[1:]):
-            out[name] = out.get(name, 0.0) + a.elapsed_time(b)
+            err, ms = self.rt.cudaEventElapsedTime(a, b)
+            if err != self.rt.cudaError_t.cudaSuccess:
+                raise RuntimeError(f"cudaEventElapsedTime: {err}")
+            out[name] = out.get(name, 0.0) + ms
         return out
+
+    def __del__(self):
+        try:
+            for _, ev in self.events:
+                self.rt.cudaEventDestroy(ev)
+        except Exception:
+            pass
 
 
 class PlainStep:
@@ -120,9 +142,10 @@ class PlainStep:
         mark("end")
         return self.out, self.m_out, self.v_out, plan
 
-    def capture(self, noise):
+    def capture(self, noise, timer: StageTimer = None):
         """Captures one step in a CUDA graph (no step synchronises with the host, and
-        every buffer is preallocated, so the whole step replays as one launch)."""
+        every buffer is preallocated, so the whole step replays as one launch). A
+        timer's stage events are captured with it and re-recorded by each replay."""
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
@@ -130,7 +153,7 @@ class PlainStep:
         torch.cuda.current_stream().wait_stream(side)
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph):
-            self.graph_out = self.step(noise)
+            self.graph_out = self.step(noise, timer)
         return self.graph_out
 
     def replay(self):
