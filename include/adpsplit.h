@@ -182,9 +182,13 @@ ADP_API int adp_project(const adp_gaussians* g, const adp_camera* cams, int32_t 
 /* --- Tile binning and depth sort (Eq. 1 depth order). -----------------------
  * Sorts the visible (view, Gaussian) records by (view, depth, id), duplicates
  * each into the tiles of its rect and sorts the instances stably by tile, so each
- * tile's list is ordered by (depth, id); writes tile ranges. If the instance
- * count exceeds bins->capacity nothing past the capacity is written and
- * *bins->n_instances holds the required size. */
+ * tile's list is ordered by (depth, id); writes tile ranges. A tile's list holds
+ * the Gaussians whose alpha ellipse o exp(-d^T C d / 2) >= alpha_min can reach
+ * one of its pixel centres (a conservative float32 test: every contributing
+ * Gaussian is listed, and no listed one contributes to a pixel it cannot reach).
+ * If the instance count (all tiles of every rect) exceeds bins->capacity
+ * nothing past the capacity is written and *bins->n_instances holds the
+ * required size. */
 ADP_API size_t adp_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t capacity);
 ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const adp_camera* cams,
                          int32_t n_views, const adp_params* prm, adp_bins* bins, void* ws,

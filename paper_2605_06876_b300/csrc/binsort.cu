@@ -7,7 +7,9 @@
 // the tile index alone (2-3 passes) leaves every tile's list in (depth, id)
 // order. This moves far fewer bytes than sorting 64-bit keys over all
 // instances, and ties in depth resolve to the lower id because every pass is
-// stable over id-ordered input.
+// stable over id-ordered input. Instances whose alpha ellipse misses their tile
+// (the rectangle of tiles overestimates a rotated ellipse) are dropped from the
+// tile lists, which changes no pixel's contributors.
 #include <algorithm>
 
 #include "common.cuh"
@@ -26,6 +28,32 @@ __global__ void clamp_count_kernel(const long long* K, long long cap, long long*
 // position within the record's tile rectangle (row-major). Balanced whatever a
 // Gaussian's footprint, and consecutive threads write consecutive instances.
 constexpr int DUP_CHUNK = 2048;
+constexpr unsigned TILE_NONE = 0xffffffffu;  // sorts after every real tile
+
+// Whether the ellipse q(d) = d^T C d <= k around the 2D mean (the pixels where
+// o exp(-q/2) >= alpha_min) reaches the rectangle of pixel centres
+// [x0, x1] x [y0, y1]: the minimum of the convex quadratic over the rectangle is
+// 0 if the mean is inside, else it lies on an edge, where the 1-D minimum is the
+// clamped stationary point. A small relative and absolute margin keeps the test
+// conservative under float32 rounding, so no contributing pixel is ever lost.
+__device__ __forceinline__ bool ellipse_meets_rect(float mx, float my, float A, float B, float C,
+                                                   float k, float x0, float x1, float y0,
+                                                   float y1) {
+  if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
+  float qmin = 3.4e38f;
+  // vertical edges x = x0, x1: q(dy) = A dx^2 + 2 B dx dy + C dy^2
+  for (int e = 0; e < 2; ++e) {
+    float dx = (e ? x1 : x0) - mx;
+    float dy = fminf(fmaxf(-B * dx / C, y0 - my), y1 - my);
+    qmin = fminf(qmin, A * dx * dx + 2.f * B * dx * dy + C * dy * dy);
+  }
+  for (int e = 0; e < 2; ++e) {  // horizontal edges y = y0, y1
+    float dy = (e ? y1 : y0) - my;
+    float dx = fminf(fmaxf(-B * dy / A, x0 - mx), x1 - mx);
+    qmin = fminf(qmin, A * dx * dx + 2.f * B * dx * dy + C * dy * dy);
+  }
+  return qmin <= k * 1.0001f + 1e-3f;
+}
 
 __device__ __forceinline__ long long last_le(const long long* offs, long long n, long long k) {
   long long lo = 0, hi = n - 1;  // last j with offs[j] <= k (offs[0] = 0 <= k)
@@ -39,8 +67,10 @@ __device__ __forceinline__ long long last_le(const long long* offs, long long n,
 
 __global__ void __launch_bounds__(256) duplicate_kernel(const unsigned* vvals, const long long* offs,
                                                         const long long* d_nvis, const long long* d_K,
-                                                        long long cap, const int4* rect, long long n,
-                                                        CamSet cs, unsigned* tkeys, int* inst) {
+                                                        long long cap, const int4* rect,
+                                                        const float4* xyod, const float4* conic,
+                                                        float alpha_min, long long n, CamSet cs,
+                                                        unsigned* tkeys, int* inst) {
   __shared__ long long s_off[DUP_CHUNK];
   __shared__ long long s_j[2];
   const long long N = *d_nvis, K = *d_K;
@@ -67,18 +97,29 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const unsigned* vvals, c
       int w = r.y - r.x + 1;
       int t = (int)(k - s_off[lo]);
       int ty = r.z + t / w, tx = r.x + t % w;
-      tkeys[k] = (unsigned)(cs.tile_base[v] + ty * cs.tiles_x[v] + tx);
+      unsigned key = (unsigned)(cs.tile_base[v] + ty * cs.tiles_x[v] + tx);
+      if (w * (r.w - r.z + 1) > 1) {  // a one-tile rectangle always meets its ellipse
+        float4 xy = xyod[p], cn = conic[p];
+        float kk = 2.f * __logf(xy.z / alpha_min);
+        float x0 = (float)(tx * cs.tile_w), y0 = (float)(ty * cs.tile_h);
+        float x1 = fminf(x0 + (float)(cs.tile_w - 1), (float)(cs.cam[v].width - 1));
+        float y1 = fminf(y0 + (float)(cs.tile_h - 1), (float)(cs.cam[v].height - 1));
+        if (!ellipse_meets_rect(xy.x, xy.y, cn.x, cn.y, cn.z, kk, x0, x1, y0, y1)) key = TILE_NONE;
+      }
+      tkeys[k] = key;
       inst[k] = i;
     }
     __syncthreads();
   }
 }
 
-__global__ void tile_ranges_kernel(const unsigned* tkeys, const long long* d_n, int2* ranges) {
+__global__ void tile_ranges_kernel(const unsigned* tkeys, const long long* d_n, unsigned n_tiles,
+                                   int2* ranges) {
   long long N = *d_n;
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < N;
        j += (long long)gridDim.x * blockDim.x) {
     unsigned t = tkeys[j];
+    if (t >= n_tiles) continue;  // instances whose ellipse misses the tile
     if (j == 0 || tkeys[j - 1] != t) ranges[t].x = (int)j;
     if (j == N - 1 || tkeys[j + 1] != t) ranges[t].y = (int)(j + 1);
   }
@@ -183,9 +224,11 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
     duplicate_kernel<<<(unsigned)std::min<long long>((cap + DUP_CHUNK - 1) / DUP_CHUNK, 148 * 8), 256,
                        0, st>>>(
         vvals, offs, &w.counters[0], (const long long*)bins->n_instances, cap,
-        reinterpret_cast<const int4*>(pr->rect), n, cs, w.tkeys, bins->inst_gauss);
+        reinterpret_cast<const int4*>(pr->rect), xyod,
+        reinterpret_cast<const float4*>(pr->conic), prm->alpha_min, n, cs, w.tkeys,
+        bins->inst_gauss);
     ADP_LAUNCH_CHECK();
-    int bits = bits_for(n_tiles > 1 ? n_tiles - 1 : 1);
+    int bits = bits_for(n_tiles);  // the filtered key TILE_NONE sorts after every tile
     DigitOp tp[4];
     int ntp = 0;
     for (int s = 0; s < bits; s += 8) tp[ntp++] = DigitOp{s, 0u};
@@ -194,7 +237,7 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
     if (rc) return rc;
     // 6. per-tile ranges
     tile_ranges_kernel<<<grid_for(cap, 256, 148 * 16), 256, 0, st>>>(
-        w.tkeys, &w.counters[1], reinterpret_cast<int2*>(bins->tile_range));
+        w.tkeys, &w.counters[1], (unsigned)n_tiles, reinterpret_cast<int2*>(bins->tile_range));
     ADP_LAUNCH_CHECK();
   }
   return ADP_OK;

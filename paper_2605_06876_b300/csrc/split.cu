@@ -19,6 +19,7 @@ struct Prop {
   double mu[3];
   double R[9];  // row-major, columns are the child's axes
   double s[3];
+  double is2[3];  // 1 / s^2 (FP64 division is slow here: done once per proposal)
   double rgb[3];
 };
 
@@ -172,7 +173,7 @@ __device__ __forceinline__ double mahal_d(const Prop& p, const double* d) {
   double acc = 0;
   for (int k = 0; k < 3; ++k) {
     double c = p.R[k] * d[0] + p.R[3 + k] * d[1] + p.R[6 + k] * d[2];
-    acc += c * c / (p.s[k] * p.s[k]);
+    acc += c * c * p.is2[k];
   }
   return sqrt(acc);
 }
@@ -286,6 +287,7 @@ __global__ void proposal_kernel(ProposalArgs a, CamSet cs) {
     p.s[0] = fmax(n1, a.scale_floor);
     p.s[1] = fmax(n2, a.scale_floor);
     p.s[2] = p.s[1];
+    for (int k = 0; k < 3; ++k) p.is2[k] = 1.0 / (p.s[k] * p.s[k]);
     double u1[3], u2[3];
     for (int k = 0; k < 3; ++k) u1[k] = n1 < 1e-12 ? u[k] : a1[k] / n1;
     double pr = dot3d(a2, u1), r2[3];
