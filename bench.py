@@ -285,6 +285,14 @@ def run_ours(args, rank, world, local_rank):
                 "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
                 "peak_source": peak_kind}
     launches = None if args.no_launch_count else count_launches(stepper, noise) * args.steps
+    batched = None
+    if args.batch_views > 1:
+        cfg1 = scenes.CONFIGS[1]
+        del stepper.out, stepper.m_out, stepper.v_out
+        torch.cuda.empty_cache()
+        batched = batched_vs_plain(g, tg, dev, args.batch_views, max(3, min(args.steps, 20)), flush,
+                                   cfg1["width"], cfg1["height"], cfg1["ring_radius"],
+                                   autotune=args.autotune)
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
@@ -298,6 +306,7 @@ def run_ours(args, rank, world, local_rank):
                      "frac": round(sum(sb.values()) / (ms_per_step * 1e-3) / 1e9 / peak, 4)},
         "graph": use_graph,
         "stages_ms": {k: round(v, 4) for k, v in per_stage.items()},
+        "batched_vs_plain": batched,
         "stage_gbs": {k: round(sb[k] / (per_stage[k] * 1e-3) / 1e9, 1) for k in per_stage
                       if k in sb and per_stage[k] > 0},
         "workload_counts": {"visible": n_vis, "instances": K, "regions": R,
@@ -307,6 +316,68 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
     }
     return result
+
+
+def batched_vs_plain(g, tg, dev, n_views, steps, flush, width, height, radius, seed=11,
+                     resolutions=None, autotune=False):
+    """fwd + bwd + error statistics for n_views views: one batched launch per stage
+    over all views against n_views one-view launch sequences (both as CUDA graphs,
+    L2 flushed before each repetition). Returns times and the speedup."""
+    import torch
+
+    import scenes
+    from paper_2605_06876_b300 import ops
+    from paper_2605_06876_b300.pipeline import ViewStages, capture_graph
+
+    if resolutions is None:
+        cams = scenes.ring_cameras(seed, n_views, radius, width, height)
+    else:
+        cams = scenes.hemisphere_cameras(seed, n_views, radius, resolutions)
+    gt = ops.Gaussians.from_scene(tg, dev)
+    prt = ops.project(gt, cams)
+    target = ops.render(gt.n, prt, ops.bin_sort(gt.n, prt, cams), cams).rgb.clone()
+    del gt, prt
+    params, tune_ms = None, None
+    if autotune:
+        from paper_2605_06876_b300.autotune import tune_tile_shape
+
+        params, tune_ms = tune_tile_shape(g, cams, target)
+        torch.cuda.empty_cache()
+    batched = ViewStages(g, cams, target, params=params)
+    offs = np.cumsum([0] + [c["width"] * c["height"] for c in cams])
+    grad = ops.Gaussians(g.n, g.sh_degree, dev, zero=False)
+    plain = [ViewStages(g, [c], target[offs[v]:offs[v + 1]], params=params, grad=grad)
+             for v, c in enumerate(cams)]
+    gb = capture_graph(batched.run)
+    gp = capture_graph(lambda: [p.run() for p in plain])
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, graph in (("batched", gb), ("plain", gp)):
+        for _ in range(3):
+            graph.replay()
+        ts = []
+        for _ in range(steps):
+            flush.random_(0, 255)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        res[name] = float(np.mean(ts))
+    ok = batched.fits() and all(p.fits() for p in plain)
+    if not ok:
+        raise RuntimeError("instance capacity exceeded in the batched/plain comparison")
+    return {"views": n_views, "gaussians": g.n,
+            "resolution": f"{width}x{height}" if resolutions is None else "uneven 640x416..1600x1056",
+            "batched_ms": round(res["batched"], 4), "plain_ms": round(res["plain"], 4),
+            "speedup": round(res["plain"] / res["batched"], 3),
+            "views_per_s_batched": round(1e3 * n_views / res["batched"], 1),
+            "views_per_s_plain": round(1e3 * n_views / res["plain"], 1),
+            "tile": [batched.params.tile_w, batched.params.tile_h],
+            "autotune_ms": None if tune_ms is None else {f"{k[0]}x{k[1]}": round(v, 4)
+                                                         for k, v in tune_ms.items()}}
 
 
 def count_launches(stepper, noise):
@@ -416,6 +487,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the tile shape of the batched comparison with the autotuner")
+    ap.add_argument("--batch-views", type=int, default=16,
+                    help="views of the batched-vs-plain comparison (0 or 1: skip)")
     ap.add_argument("--no-launch-count", action="store_true",
                     help="skip the CUPTI kernel count (for runs under ncu)")
     args = ap.parse_args()

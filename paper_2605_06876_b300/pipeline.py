@@ -168,3 +168,59 @@ class PlainStep:
         if plan is not None:
             ok = ok and int(plan.d_new_n.item()) <= self.out_capacity
         return ok
+
+
+class ViewStages:
+    """The view-dependent stages of a step -- projection, binning, compositing,
+    error statistics and the render backward -- for a set of views, each launched
+    once over all of them. Used to compare one batched launch over V views with V
+    one-view launches (pass a shared `grad` to the one-view instances)."""
+
+    def __init__(self, g: ops.Gaussians, cams, target, params=None, bg=(0.0, 0.0, 0.0),
+                 grad: ops.Gaussians = None, bins_margin=1.15):
+        self.g, self.cams, self.target = g, list(cams), target
+        self.params = params or A.default_params()
+        self.bg = bg
+        self.dev = g.mean_logit.device
+        n, V = g.n, len(self.cams)
+        self.P = ops.n_pixels(self.cams)
+        self.pr = ops.Projected.alloc(V * n, self.dev)
+        self.img = ops.Image.alloc(self.P, self.dev)
+        self.maps = ops.ErrorMaps.alloc(self.P, V, self.dev)
+        self.count = torch.empty(n, dtype=torch.int32, device=self.dev)
+        self.mass = torch.empty(n, dtype=torch.float64, device=self.dev)
+        self.grad = grad if grad is not None else ops.Gaussians(n, g.sh_degree, self.dev, zero=False)
+        ops.project(g, self.cams, self.params, self.pr)
+        probe = ops.bin_sort(n, self.pr, self.cams, self.params)
+        cap = int(int(probe.n_inst.item()) * bins_margin) + 1024
+        self.bins = ops.Bins.alloc(cap, ops.n_tiles(self.cams, self.params.tile_w,
+                                                     self.params.tile_h), self.dev)
+        self.ws_bins = ops.workspace(ops.bin_sort_workspace_size(n, V, cap), self.dev)
+        self.ws_bwd = ops.workspace(A.lib().adp_render_backward_workspace_size(n, V), self.dev)
+        torch.cuda.synchronize()
+
+    def run(self):
+        g, cams, prm, n = self.g, self.cams, self.params, self.g.n
+        ops.project(g, cams, prm, self.pr)
+        ops.bin_sort(n, self.pr, cams, prm, bins=self.bins, ws=self.ws_bins, grow=False)
+        ops.render(n, self.pr, self.bins, cams, self.bg, prm, self.img)
+        ops.error_stats(self.img.rgb, self.target, self.img.dominant, n, cams, prm, self.maps,
+                        self.count, self.mass)
+        ops.render_backward(g, self.pr, self.bins, self.img, cams, target=self.target, bg=self.bg,
+                            params=prm, grad=self.grad, ws=self.ws_bwd)
+
+    def fits(self):
+        return int(self.bins.n_inst.item()) <= self.bins.capacity
+
+
+def capture_graph(fn):
+    """A CUDA graph of fn() (run once eagerly on a side stream first)."""
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fn()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        fn()
+    return graph

@@ -76,3 +76,23 @@ def test_graph_replay_matches_eager_step():
         sl = (slice(None), slice(0, n_new)) if a.dim() == 3 else (slice(0, n_new),)
         torch.testing.assert_close(a[sl], b[sl], rtol=1e-4, atol=1e-5)
     assert int(graphed.adam_t.item()) == 2
+
+
+def test_autotuner_picks_a_legal_shape_with_identical_results():
+    from paper_2605_06876_b300.autotune import SHAPES, tune_tile_shape
+    from paper_2605_06876_b300.pipeline import ViewStages
+
+    sc, cams = small_cluster_inputs(20000, 320, 208, views=2, seed=41)
+    g = ops.Gaussians.from_scene(sc, DEV)
+    P = sum(c["width"] * c["height"] for c in cams)
+    target = torch.rand((P, 3), device=DEV)
+    params, times = tune_tile_shape(g, cams, target, reps=2)
+    assert (params.tile_w, params.tile_h) in SHAPES and len(times) == len(SHAPES)
+    assert times[(params.tile_w, params.tile_h)] == min(times.values())
+    ref = ViewStages(g, cams, target)
+    ref.run()
+    got = ViewStages(g, cams, target, params=params)
+    got.run()
+    torch.cuda.synchronize()
+    assert torch.equal(ref.img.rgb, got.img.rgb) and torch.equal(ref.img.dominant, got.img.dominant)
+    assert torch.equal(ref.count, got.count) and torch.equal(ref.mass, got.mass)
