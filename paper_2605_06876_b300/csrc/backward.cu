@@ -27,7 +27,7 @@ struct BwdPixArgs {
   const float* target;
   const float* dL_drgb;
   float bg[3];
-  float alpha_min, alpha_max;
+  float alpha_min, alpha_max, log2_alpha_min;
   float4* g2d;  // [V*n][3]
 };
 
@@ -62,50 +62,59 @@ __device__ __forceinline__ float reduce_scatter8(const float* v, int* idx) {
   return x;
 }
 
-// Two pixels per thread (local pixels t and t + 128 of the 256-pixel tile, the
-// same column eight rows apart for 16x16 tiles): the staged Gaussian is read once
-// for both, and one warp reduction covers 64 pixels.
+// Two horizontally adjacent pixels per thread, staged Gaussians in the form the
+// forward uses (so every alpha test agrees with the forward's), a warp-uniform
+// skip of Gaussians that reach none of the warp's rows, and one warp reduction
+// per staged Gaussian covering the warp's 64 pixels.
 constexpr int BWD_THREADS = 128;
+constexpr int BWD_STAGE = 256;
 
 struct PixState {
   float T, R0, R1, R2, g0, g1, g2, fx, fy;
   int last;
 };
 
-// Contribution of one staged Gaussian to one pixel's gradients (adds into v[9]).
-__device__ __forceinline__ bool bwd_contrib(PixState& s, int pos, float4 q0, float4 q1, float c2,
-                                            float amin, float amax, float* v) {
+// Contribution of one staged Gaussian to one pixel's gradients (adds into v[9]):
+// v = (d mean x, d mean y, d conic A, d conic B, d conic C, d opacity, d r, d g, d b).
+__device__ __forceinline__ bool bwd_contrib(PixState& s, int pos, const Staged& g, float amax,
+                                            float l2amin, float* v) {
   if (pos >= s.last) return false;
-  float dx, dy, G;
-  float ar = alpha_raw_g(q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, s.fx, s.fy, &dx, &dy, &G);
-  if (ar < amin) return false;
-  float al = fminf(amax, ar);
-  float Tj = s.T * __frcp_rn(1.f - al);
-  float dal = Tj * (s.g0 * (q1.z - s.R0) + s.g1 * (q1.w - s.R1) + s.g2 * (c2 - s.R2));
-  float wgt = Tj * al;
+  float dx, dy;
+  const float q = log2_alpha(g.g0, g.g1, s.fx, s.fy, &dx, &dy);
+  if (q < l2amin) return false;
+  const float ar = exp2f(q);
+  const float al = fminf(amax, ar);
+  const float Tj = s.T * __frcp_rn(1.f - al);
+  const float c0 = g.g1.z, c1 = g.g1.w, c2 = g.g2.x;
+  const float dal = Tj * (s.g0 * (c0 - s.R0) + s.g1 * (c1 - s.R1) + s.g2 * (c2 - s.R2));
+  const float wgt = Tj * al;
   v[6] += wgt * s.g0;
   v[7] += wgt * s.g1;
   v[8] += wgt * s.g2;
-  s.R0 = al * q1.z + (1.f - al) * s.R0;
-  s.R1 = al * q1.w + (1.f - al) * s.R1;
+  s.R0 = al * c0 + (1.f - al) * s.R0;
+  s.R1 = al * c1 + (1.f - al) * s.R1;
   s.R2 = al * c2 + (1.f - al) * s.R2;
   s.T = Tj;
   if (ar <= amax) {
-    v[5] += dal * G;
-    float dpow = dal * ar;
+    // alpha = o exp(power): d alpha / d o = alpha / o, d alpha / d power = alpha
+    v[5] += dal * ar * g.g2.z;
+    const float dpow = dal * ar;
     v[2] += -0.5f * dx * dx * dpow;
     v[4] += -0.5f * dy * dy * dpow;
     v[3] += -dx * dy * dpow;
-    v[0] += -(q0.z * dx + q0.w * dy) * dpow;
-    v[1] += -(q1.x * dy + q0.w * dx) * dpow;
+    // -(A dx + B dy) = (2 a dx + b dy) / log2(e), with a, b the staged log2 conic
+    const float dpk = dpow * (1.f / kLog2e);
+    v[0] += fmaf(2.f * g.g0.z, dx, g.g0.w * dy) * dpk;
+    v[1] += fmaf(2.f * g.g1.x, dy, g.g0.w * dx) * dpk;
   }
   return true;
 }
 
 __global__ void __launch_bounds__(BWD_THREADS) bwd_pixel_kernel(BwdPixArgs a, CamSet cs) {
-  __shared__ float4 s_g0[256];
-  __shared__ float4 s_g1[256];
-  __shared__ float2 s_g2[256];
+  __shared__ float4 s_g0[BWD_STAGE];
+  __shared__ float4 s_g1[BWD_STAGE];
+  __shared__ float4 s_g2[BWD_STAGE];
+  __shared__ float2 s_y[BWD_STAGE];
   __shared__ int s_maxlast;
   const int tile = blockIdx.x;
   const int v = view_of_tile(cs, tile);
@@ -115,14 +124,18 @@ __global__ void __launch_bounds__(BWD_THREADS) bwd_pixel_kernel(BwdPixArgs a, Ca
   const int2 range = a.ranges[tile];
   const long long rec_base = (long long)v * a.n;
   const float sc = 1.f / (3.f * (float)W * (float)H);
+  const int tx0 = (lt % txs) * cs.tile_w, ty0 = (lt / txs) * cs.tile_h;
+  const int warp = threadIdx.x >> 5;
+  const float wy0 = (float)(ty0 + (64 * warp) / cs.tile_w);
+  const float wy1 = (float)(ty0 + (64 * warp + 63) / cs.tile_w);
 
   PixState ps[2];
   int warp_last = 0;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const int li = (int)threadIdx.x + h * BWD_THREADS;
-    const int px = (lt % txs) * cs.tile_w + li % cs.tile_w;
-    const int py = (lt / txs) * cs.tile_h + li / cs.tile_w;
+    const int li = 2 * (int)threadIdx.x + h;
+    const int px = tx0 + li % cs.tile_w;
+    const int py = ty0 + li / cs.tile_w;
     PixState& s = ps[h];
     s.fx = (float)px;
     s.fy = (float)py;
@@ -158,34 +171,39 @@ __global__ void __launch_bounds__(BWD_THREADS) bwd_pixel_kernel(BwdPixArgs a, Ca
   __syncthreads();
   const int end = s_maxlast;
   const int lane = threadIdx.x & 31;
-  for (int b1 = end; b1 > 0; b1 -= 256) {
-    const int b0 = b1 - 256 > 0 ? b1 - 256 : 0;
+  for (int b1 = end; b1 > 0; b1 -= BWD_STAGE) {
+    const int b0 = b1 - BWD_STAGE > 0 ? b1 - BWD_STAGE : 0;
     __syncthreads();
     for (int j = (int)threadIdx.x; j < b1 - b0; j += BWD_THREADS) {
       int id = a.inst[range.x + b0 + j];
       long long r = rec_base + id;
-      float4 p0 = a.xyod[r], p1 = a.conic[r], p2 = a.rgb[r];
-      s_g0[j] = make_float4(p0.x, p0.y, p1.x, p1.y);
-      s_g1[j] = make_float4(p1.z, p0.z, p2.x, p2.y);
-      s_g2[j] = make_float2(p2.z, __int_as_float(id));
+      Staged g = stage_gaussian(a.xyod[r], a.conic[r], a.rgb[r], id, a.alpha_min);
+      s_g0[j] = g.g0;
+      s_g1[j] = g.g1;
+      s_g2[j] = g.g2;
+      s_y[j] = g.y;
     }
     __syncthreads();
     const int kmax = min(b1, warp_last) - b0;  // warp-uniform
     for (int k = kmax - 1; k >= 0; --k) {
+      const float2 yr = s_y[k];
+      if (yr.y < wy0 || yr.x > wy1) continue;  // warp-uniform: no row of this warp reached
+      Staged g;
+      g.g0 = s_g0[k];
+      g.g1 = s_g1[k];
+      g.g2 = s_g2[k];
       const int pos = b0 + k;
-      const float4 q0 = s_g0[k], q1 = s_g1[k];
-      const float c2 = s_g2[k].x;
       float vals[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      bool hit = bwd_contrib(ps[0], pos, q0, q1, c2, a.alpha_min, a.alpha_max, vals);
-      hit |= bwd_contrib(ps[1], pos, q0, q1, c2, a.alpha_min, a.alpha_max, vals);
+      bool hit = bwd_contrib(ps[0], pos, g, a.alpha_max, a.log2_alpha_min, vals);
+      hit |= bwd_contrib(ps[1], pos, g, a.alpha_max, a.log2_alpha_min, vals);
       if (__ballot_sync(0xffffffffu, hit)) {
         int idx;
         float sum = reduce_scatter8(vals, &idx);
         float db = warp_sum(vals[8]);
-        int id = __float_as_int(s_g2[k].y);
-        float* g = reinterpret_cast<float*>(a.g2d + 3 * (rec_base + id));
-        if ((lane & 3) == 0) atomicAdd(g + idx, sum);
-        if (lane == 0) atomicAdd(g + 8, db);
+        int id = __float_as_int(g.g2.y);
+        float* gp = reinterpret_cast<float*>(a.g2d + 3 * (rec_base + id));
+        if ((lane & 3) == 0) atomicAdd(gp + idx, sum);
+        if (lane == 0) atomicAdd(gp + 8, db);
       }
     }
   }
@@ -457,6 +475,7 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   for (int c = 0; c < 3; ++c) pa.bg[c] = bg ? bg[c] : 0.f;
   pa.alpha_min = prm->alpha_min;
   pa.alpha_max = prm->alpha_max;
+  pa.log2_alpha_min = log2f(prm->alpha_min);
   pa.g2d = g2d;
   bwd_pixel_kernel<<<cs.tile_base[n_views], BWD_THREADS, 0, st>>>(pa, cs);
   ADP_LAUNCH_CHECK();

@@ -1,6 +1,6 @@
 // Device math shared by the forward and backward kernels: quaternion rotation,
-// the real SH basis (3DGS sign convention) and its gradient, and the per-pixel
-// alpha evaluation that forward and backward must compute identically.
+// the real SH basis (3DGS sign convention) and its gradient, and the staged
+// per-Gaussian form and alpha evaluation that forward and backward share.
 #pragma once
 
 #include "common.cuh"
@@ -96,20 +96,44 @@ __device__ __forceinline__ float sh_coef(const float* sh, long long n, long long
   return sh[((long long)(f >> 2) * n + i) * 4 + (f & 3)];
 }
 
-// alpha_raw = o * G at pixel (px, py) for a Gaussian with 2D mean (mx, my),
-// conic (A, B, C) and opacity o, with the footprint G = exp(power) (0 where the
-// quadratic form is negative). Forward and backward both call this function, so
-// their decisions agree bit for bit.
-__device__ __forceinline__ float alpha_raw_g(float mx, float my, float A, float B, float C,
-                                             float o, float px, float py, float* dx_out,
-                                             float* dy_out, float* G_out) {
-  float dx = mx - px, dy = my - py;
+// A projected Gaussian as the compositing loops stage it in shared memory:
+// 2D mean, the conic scaled into log2 units (a = -A log2(e) / 2, b = -B log2(e),
+// c = -C log2(e) / 2), log2 of the opacity, its reciprocal, the colour, the id,
+// and the rows its alpha ellipse can reach.
+struct Staged {
+  float4 g0;  // mx, my, a, b
+  float4 g1;  // c, log2(o), r, g
+  float4 g2;  // blue, id (int bits), 1/o, 0
+  float2 y;   // lowest and highest image row the ellipse reaches
+};
+
+constexpr float kLog2e = 1.4426950408889634f;
+
+__device__ __forceinline__ Staged stage_gaussian(float4 xyod, float4 conic, float4 rgb, int id,
+                                                 float alpha_min) {
+  Staged s;
+  const float o = xyod.z;
+  s.g0 = make_float4(xyod.x, xyod.y, -0.5f * kLog2e * conic.x, -kLog2e * conic.y);
+  s.g1 = make_float4(-0.5f * kLog2e * conic.z, __log2f(o), rgb.x, rgb.y);
+  s.g2 = make_float4(rgb.z, __int_as_float(id), 1.f / o, 0.f);
+  // rows of the ellipse o exp(-d^T C d / 2) >= alpha_min: |dy| <= sqrt(k S_yy) with
+  // S_yy = A / det(C), k = 2 ln(o / alpha_min); widened so the skip is conservative
+  const float det = conic.x * conic.z - conic.y * conic.y;
+  const float k = fmaxf(2.f * __logf(o / alpha_min), 0.f);
+  const float hy = sqrtf(k * conic.x / det) * 1.001f + 0.01f;
+  s.y = make_float2(xyod.y - hy, xyod.y + hy);
+  return s;
+}
+
+// log2 of alpha_raw = o exp(-d^T C d / 2) at pixel (px, py), with d = mean - pixel.
+// Forward and backward both evaluate it (and compare it with log2(alpha_min))
+// through this function, so their decisions agree bit for bit.
+__device__ __forceinline__ float log2_alpha(const float4& g0, const float4& g1, float px, float py,
+                                            float* dx_out, float* dy_out) {
+  const float dx = g0.x - px, dy = g0.y - py;
   *dx_out = dx;
   *dy_out = dy;
-  float power = -0.5f * (A * dx * dx + C * dy * dy) - B * dx * dy;
-  float G = power > 0.f ? 0.f : __expf(power);
-  *G_out = G;
-  return power > 0.f ? 0.f : o * G;
+  return fmaf(g0.z, dx * dx, fmaf(g1.x, dy * dy, fmaf(g0.w, dx * dy, g1.y)));
 }
 
 }  // namespace adp

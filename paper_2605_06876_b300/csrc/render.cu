@@ -1,7 +1,9 @@
 // Front-to-back alpha compositing (Eq. 1) with the dominant Gaussian map (Eq. 5).
-// One CTA per tile (256 pixels, two per thread); the tile's depth-sorted list is
-// staged through shared memory 256 Gaussians at a time, each thread gathering two
-// records; a block-wide vote ends the tile once every pixel has stopped.
+// One CTA per tile (256 pixels, two horizontally adjacent ones per thread); the
+// tile's depth-sorted list is staged through shared memory 256 Gaussians at a
+// time in a precomputed form (alpha in log2 units, the rows each ellipse
+// reaches), a warp skips Gaussians that reach none of its rows, and a block-wide
+// vote ends the tile once every pixel has stopped.
 #include "gauss_math.cuh"
 
 namespace adp {
@@ -14,7 +16,7 @@ struct RenderArgs {
   const int2* ranges;
   long long n;
   float bg[3];
-  float alpha_min, alpha_max, t_min;
+  float alpha_min, alpha_max, t_min, log2_alpha_min;
   float* out_rgb;
   float* out_T;
   int* out_n;
@@ -22,7 +24,8 @@ struct RenderArgs {
   int* out_dom;
 };
 
-constexpr int RENDER_THREADS = 128;  // two pixels per thread
+constexpr int RENDER_THREADS = 128;  // two horizontally adjacent pixels per thread
+constexpr int STAGE = 256;           // Gaussians staged per batch
 
 struct FwdPix {
   float T, c0, c1, c2, best, fx, fy;
@@ -30,25 +33,25 @@ struct FwdPix {
   bool done;
 };
 
-__device__ __forceinline__ void fwd_step(FwdPix& s, int pos, float4 g0, float4 g1, float2 g2,
-                                         float amin, float amax, float tmin) {
+__device__ __forceinline__ void fwd_step(FwdPix& s, int pos, const Staged& g, float amax,
+                                         float tmin, float l2amin) {
   if (s.done) return;
-  float dx, dy, G;
-  float al = alpha_raw_g(g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, s.fx, s.fy, &dx, &dy, &G);
-  if (al < amin) return;
-  al = fminf(amax, al);
-  float test = s.T * (1.f - al);
+  float dx, dy;
+  const float q = log2_alpha(g.g0, g.g1, s.fx, s.fy, &dx, &dy);
+  if (q < l2amin) return;
+  const float al = fminf(amax, exp2f(q));
+  const float test = s.T * (1.f - al);
   if (test < tmin) {
     s.done = true;
     return;
   }
-  float w = s.T * al;
-  s.c0 += w * g1.z;
-  s.c1 += w * g1.w;
-  s.c2 += w * g2.x;
+  const float w = s.T * al;
+  s.c0 += w * g.g1.z;
+  s.c1 += w * g.g1.w;
+  s.c2 += w * g.g2.x;
   if (w > s.best) {
     s.best = w;
-    s.dom = __float_as_int(g2.y);
+    s.dom = __float_as_int(g.g2.y);
   }
   s.T = test;
   ++s.ncon;
@@ -56,9 +59,10 @@ __device__ __forceinline__ void fwd_step(FwdPix& s, int pos, float4 g0, float4 g
 }
 
 __global__ void __launch_bounds__(RENDER_THREADS) render_kernel(RenderArgs a, CamSet cs) {
-  __shared__ float4 s_g0[256];  // mx, my, A, B
-  __shared__ float4 s_g1[256];  // C, opacity, r, g
-  __shared__ float2 s_g2[256];  // b, id (as int bits)
+  __shared__ float4 s_g0[STAGE];
+  __shared__ float4 s_g1[STAGE];
+  __shared__ float4 s_g2[STAGE];
+  __shared__ float2 s_y[STAGE];
   const int tile = blockIdx.x;
   const int v = view_of_tile(cs, tile);
   const int lt = tile - cs.tile_base[v];
@@ -67,15 +71,20 @@ __global__ void __launch_bounds__(RENDER_THREADS) render_kernel(RenderArgs a, Ca
   const int2 range = a.ranges[tile];
   const int count = range.y - range.x;
   const long long rec_base = (long long)v * a.n;
+  const int tx0 = (lt % txs) * cs.tile_w, ty0 = (lt / txs) * cs.tile_h;
+  const int warp = threadIdx.x >> 5;
+  // the rows this warp's 64 pixels cover
+  const float wy0 = (float)(ty0 + (64 * warp) / cs.tile_w);
+  const float wy1 = (float)(ty0 + (64 * warp + 63) / cs.tile_w);
 
   FwdPix ps[2];
   bool inside[2];
   int pxs[2], pys[2];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const int li = (int)threadIdx.x + h * RENDER_THREADS;
-    pxs[h] = (lt % txs) * cs.tile_w + li % cs.tile_w;
-    pys[h] = (lt / txs) * cs.tile_h + li / cs.tile_w;
+    const int li = 2 * (int)threadIdx.x + h;
+    pxs[h] = tx0 + li % cs.tile_w;
+    pys[h] = ty0 + li / cs.tile_w;
     inside[h] = pxs[h] < W && pys[h] < H;
     FwdPix& s = ps[h];
     s.T = 1.f;
@@ -88,24 +97,29 @@ __global__ void __launch_bounds__(RENDER_THREADS) render_kernel(RenderArgs a, Ca
     s.last = 0;
     s.done = !inside[h];
   }
-  for (int b0 = 0; b0 < count; b0 += 256) {
+  for (int b0 = 0; b0 < count; b0 += STAGE) {
     if (__syncthreads_count(ps[0].done && ps[1].done) == RENDER_THREADS) break;
-    for (int j = (int)threadIdx.x; j < 256 && b0 + j < count; j += RENDER_THREADS) {
+    for (int j = (int)threadIdx.x; j < STAGE && b0 + j < count; j += RENDER_THREADS) {
       int id = a.inst[range.x + b0 + j];
       long long r = rec_base + id;
-      float4 p0 = a.xyod[r], p1 = a.conic[r], p2 = a.rgb[r];
-      s_g0[j] = make_float4(p0.x, p0.y, p1.x, p1.y);
-      s_g1[j] = make_float4(p1.z, p0.z, p2.x, p2.y);
-      s_g2[j] = make_float2(p2.z, __int_as_float(id));
+      Staged g = stage_gaussian(a.xyod[r], a.conic[r], a.rgb[r], id, a.alpha_min);
+      s_g0[j] = g.g0;
+      s_g1[j] = g.g1;
+      s_g2[j] = g.g2;
+      s_y[j] = g.y;
     }
     __syncthreads();
     if (!(ps[0].done && ps[1].done)) {
-      int cnt = min(256, count - b0);
+      const int cnt = min(STAGE, count - b0);
       for (int k = 0; k < cnt; ++k) {
-        float4 g0 = s_g0[k], g1 = s_g1[k];
-        float2 g2 = s_g2[k];
-        fwd_step(ps[0], b0 + k, g0, g1, g2, a.alpha_min, a.alpha_max, a.t_min);
-        fwd_step(ps[1], b0 + k, g0, g1, g2, a.alpha_min, a.alpha_max, a.t_min);
+        const float2 yr = s_y[k];
+        if (yr.y < wy0 || yr.x > wy1) continue;  // warp-uniform: no row of this warp reached
+        Staged g;
+        g.g0 = s_g0[k];
+        g.g1 = s_g1[k];
+        g.g2 = s_g2[k];
+        fwd_step(ps[0], b0 + k, g, a.alpha_max, a.t_min, a.log2_alpha_min);
+        fwd_step(ps[1], b0 + k, g, a.alpha_max, a.t_min, a.log2_alpha_min);
         if (ps[0].done && ps[1].done) break;
       }
     }
@@ -151,6 +165,7 @@ extern "C" ADP_API int adp_render(int64_t n, const adp_projected* pr, const adp_
   a.alpha_min = prm->alpha_min;
   a.alpha_max = prm->alpha_max;
   a.t_min = prm->t_min;
+  a.log2_alpha_min = log2f(prm->alpha_min);
   a.out_rgb = out->rgb;
   a.out_T = out->T_final;
   a.out_n = out->n_contrib;
