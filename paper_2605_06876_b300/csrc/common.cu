@@ -53,45 +53,6 @@ __global__ void fill_i32_kernel(int* p, long long n, int v) {
 
 // ----------------------------------------------------------------- scan
 
-__global__ void scan_blocksums_kernel(long long* bsum, long long nb_max, long long n,
-                                      const long long* d_n, long long* total) {
-  __shared__ long long s_warp[32];
-  __shared__ long long s_carry;
-  long long N = device_count(d_n, n);
-  long long nb = (N + SCAN_TILE - 1) / SCAN_TILE;
-  if (nb > nb_max) nb = nb_max;
-  if (threadIdx.x == 0) s_carry = 0;
-  __syncthreads();
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (long long base = 0; base < nb; base += blockDim.x) {
-    long long i = base + threadIdx.x;
-    long long x = i < nb ? bsum[i] : 0;
-    long long inc = x;
-    for (int o = 1; o < 32; o <<= 1) {
-      long long y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
-    }
-    if (lane == 31) s_warp[w] = inc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      long long t = threadIdx.x < (blockDim.x >> 5) ? s_warp[threadIdx.x] : 0;
-      long long ti = t;
-      for (int o = 1; o < 32; o <<= 1) {
-        long long y = __shfl_up_sync(0xffffffffu, ti, o);
-        if (lane >= o) ti += y;
-      }
-      if (threadIdx.x < (blockDim.x >> 5)) s_warp[threadIdx.x] = ti - t;
-    }
-    __syncthreads();
-    long long excl = s_carry + s_warp[w] + inc - x;
-    if (i < nb) bsum[i] = excl;
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) s_carry = excl + x;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0 && total) *total = s_carry;
-}
-
 // ----------------------------------------------------------------- radix sort
 
 __global__ void rs_hist_kernel(const unsigned* keys, const unsigned* vals, const long long* d_n,

@@ -106,67 +106,63 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 // ----------------------------------------------------------------- scan
 
-// Exclusive prefix sum of n int64 values produced by a functor load(i),
-// reduce-then-scan in three launches. The count is either a host value or read
-// from device memory (d_n != nullptr, with n_max an upper bound sizing grids).
+// Exclusive prefix sum of n int64 values produced by a functor load(i), in one
+// launch with decoupled look-back: each CTA takes the next tile from a ticket
+// counter, publishes its tile total, then its inclusive prefix once the totals
+// before it are known, reading up to 32 predecessors at a time. A CTA only ever
+// waits on tiles handed out before its own ticket, which are being processed by
+// CTAs already running, so the waits end; each is still bounded, and a bound
+// that runs out sets *err and leaves the result undefined. The count is a host
+// value or read from device memory (d_n != nullptr, n an upper bound).
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 16;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+constexpr unsigned long long SCAN_FLAG_A = 1ull << 62;  // tile total published
+constexpr unsigned long long SCAN_FLAG_P = 2ull << 62;  // inclusive prefix published
+constexpr unsigned long long SCAN_VALUE = (1ull << 62) - 1;
+constexpr int SCAN_SPIN_LIMIT = 1 << 22;
 
-inline int64_t scan_blocks(int64_t n_max) { return (n_max + SCAN_TILE - 1) / SCAN_TILE; }
-inline size_t scan_workspace_bytes(int64_t n_max) {
-  return carve_bytes<long long>(scan_blocks(n_max) + 1);
+__host__ __device__ inline long long scan_blocks(long long n_max) {
+  return (n_max + SCAN_TILE - 1) / SCAN_TILE;
+}
+// status words [0, nb), ticket, error flag
+inline size_t scan_workspace_bytes(long long n_max) {
+  return carve_bytes<unsigned long long>(scan_blocks(n_max) + 4);
 }
 
 __device__ __forceinline__ long long device_count(const long long* d_n, long long n) {
   return d_n ? *d_n : n;
 }
 
-template <class Load>
-__global__ void scan_reduce_kernel(Load load, long long n, const long long* d_n, long long* bsum) {
-  __shared__ long long s[SCAN_THREADS / 32];
-  long long N = device_count(d_n, n);
-  long long base = (long long)blockIdx.x * SCAN_TILE;
-  long long acc = 0;
-  if (base < N) {
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-      long long i = base + (long long)k * SCAN_THREADS + threadIdx.x;
-      if (i < N) acc += load(i);
-    }
-  }
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    long long t = 0;
-    for (int w = 0; w < SCAN_THREADS / 32; ++w) t += s[w];
-    bsum[blockIdx.x] = t;
-  }
-}
-
-// Single block: exclusive scan of the block sums in place; total to *total.
-__global__ void scan_blocksums_kernel(long long* bsum, long long nb_max, long long n,
-                                      const long long* d_n, long long* total);
-
 template <class Load, class Store>
-__global__ void scan_downsweep_kernel(Load load, Store store, long long n, const long long* d_n,
-                                      const long long* bsum) {
+__global__ void __launch_bounds__(SCAN_THREADS)
+    scan_lookback_kernel(Load load, Store store, long long n, const long long* d_n,
+                         unsigned long long* status, long long* total) {
   __shared__ long long s_warp[SCAN_THREADS / 32];
-  long long N = device_count(d_n, n);
-  long long base = (long long)blockIdx.x * SCAN_TILE;
-  if (base >= N) return;
-  // blocked arrangement: thread t owns items base + t*ITEMS .. + ITEMS-1
+  __shared__ long long s_excl;
+  __shared__ long long s_tile;
+  const long long N = device_count(d_n, n);
+  const long long nb = (N + SCAN_TILE - 1) / SCAN_TILE;
+  unsigned long long* ticket = status + scan_blocks(n) + 1;
+  unsigned long long* err = ticket + 1;
+  if (threadIdx.x == 0) s_tile = (long long)atomicAdd(ticket, 1ull);
+  __syncthreads();
+  const long long tile = s_tile;
+  if (tile >= nb) {
+    if (nb == 0 && tile == 0 && threadIdx.x == 0 && total) *total = 0;
+    return;
+  }
+  const long long base = tile * SCAN_TILE;
+  const long long first = base + (long long)threadIdx.x * SCAN_ITEMS;
   long long v[SCAN_ITEMS];
   long long tsum = 0;
-  long long first = base + (long long)threadIdx.x * SCAN_ITEMS;
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) {
-    long long i = first + k;
+    const long long i = first + k;
     v[k] = i < N ? load(i) : 0;
     tsum += v[k];
   }
-  // block exclusive scan of tsum
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   long long inc = tsum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -175,27 +171,74 @@ __global__ void scan_downsweep_kernel(Load load, Store store, long long n, const
   }
   if (lane == 31) s_warp[w] = inc;
   __syncthreads();
-  long long wpre = 0;
-  for (int k = 0; k < w; ++k) wpre += s_warp[k];
-  long long run = bsum[blockIdx.x] + wpre + inc - tsum;
+  long long wpre = 0, agg = 0;
+  for (int k = 0; k < SCAN_THREADS / 32; ++k) {
+    if (k < w) wpre += s_warp[k];
+    agg += s_warp[k];
+  }
+  if (w == 0) {  // publish, then look back
+    volatile unsigned long long* vs = status;
+    if (tile == 0) {
+      if (lane == 0) {
+        __threadfence();
+        atomicExch(status, SCAN_FLAG_P | (unsigned long long)agg);
+        s_excl = 0;
+      }
+    } else {
+      if (lane == 0) atomicExch(status + tile, SCAN_FLAG_A | (unsigned long long)agg);
+      long long excl = 0;
+      long long end = tile;  // window covers [end - 32, end)
+      bool done = false;
+      while (!done) {
+        const long long j = end - 1 - lane;
+        unsigned long long word = SCAN_FLAG_P;  // before tile 0: an empty prefix
+        if (j >= 0) {
+          int spins = 0;
+          do {
+            word = vs[j];
+          } while ((word >> 62) == 0 && ++spins < SCAN_SPIN_LIMIT);
+          if ((word >> 62) == 0) {
+            atomicExch(err, 1ull);
+            word = SCAN_FLAG_P;  // give up: stop the look-back here
+          }
+        }
+        const unsigned pmask = __ballot_sync(0xffffffffu, (word >> 62) == 2);
+        // sum the totals from the nearest inclusive prefix (lowest lane) to the window end
+        const int stop = pmask ? __ffs(pmask) - 1 : 31;
+        long long val = (lane <= stop && j >= 0) ? (long long)(word & SCAN_VALUE) : 0;
+        for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+        excl += val;
+        if (pmask) done = true;
+        end -= 32;
+      }
+      if (lane == 0) {
+        __threadfence();
+        atomicExch(status + tile, SCAN_FLAG_P | (unsigned long long)(excl + agg));
+        s_excl = excl;
+      }
+    }
+  }
+  __syncthreads();
+  long long run = s_excl + wpre + inc - tsum;
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) {
-    long long i = first + k;
+    const long long i = first + k;
     if (i < N) store(i, run);
     run += v[k];
   }
+  if (tile == nb - 1 && threadIdx.x == 0 && total) *total = s_excl + agg;
 }
 
-// Exclusive scan: store(i, prefix_i). total (device, may be null) receives the sum.
+// Exclusive scan: store(i, prefix_i); total (device, may be null) receives the sum.
 template <class Load, class Store>
 int scan_exclusive(Load load, Store store, long long n_max, const long long* d_n,
                    long long* total, void* ws, cudaStream_t st) {
   long long nb = scan_blocks(n_max);
   if (nb == 0) nb = 1;
-  long long* bsum = static_cast<long long*>(ws);
-  scan_reduce_kernel<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(load, n_max, d_n, bsum);
-  scan_blocksums_kernel<<<1, 1024, 0, st>>>(bsum, nb, n_max, d_n, total);
-  scan_downsweep_kernel<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(load, store, n_max, d_n, bsum);
+  unsigned long long* status = static_cast<unsigned long long*>(ws);
+  ADP_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)(nb + 3), st));
+  scan_lookback_kernel<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(load, store, n_max, d_n, status,
+                                                              total);
   ADP_LAUNCH_CHECK();
   return ADP_OK;
 }
