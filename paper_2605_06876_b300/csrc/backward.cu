@@ -7,7 +7,7 @@
 // R <- alpha c + (1 - alpha) R starting from the background. Per Gaussian it
 // yields dL/d(mean2d, conic, opacity, rgb); a warp reduces the 32 pixels'
 // contributions (a reduce-scatter) before nine scalar atomics per record.
-// Pass 2 (one thread per visible Gaussian): chains those 2D gradients through the
+// Pass 2 (one thread per visible Gaussian, from a compacted list): chains those 2D gradients through the
 // EWA projection and the SH colour of every view and sums over views, so the
 // per-Gaussian parameters are read and the gradients written once per step.
 #include "gauss_math.cuh"
@@ -392,40 +392,47 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
   }
 }
 
-constexpr int BWDG_THREADS = 128;
-constexpr int BWDG_CHUNK = 512;
-
-// Each CTA takes BWDG_CHUNK Gaussians: those rendered in no view get zero
-// gradients at once, the others are compacted in shared memory and chained by
-// full warps, so the heavy per-Gaussian work is not diluted by idle lanes.
-__global__ void __launch_bounds__(BWDG_THREADS) bwd_gauss_kernel(BwdGaussArgs a, CamSet cs) {
-  __shared__ int s_list[BWDG_CHUNK];
+// Zeroes the gradient of every Gaussian rendered in no view and appends the
+// others to a list, with one atomic per block (the list order does not change
+// any result), so the chain-rule pass runs on full warps of visible Gaussians.
+__global__ void __launch_bounds__(256) bwd_visible_kernel(const int* tiles, long long n,
+                                                          int n_views, int planes, float4* g_ml,
+                                                          float4* g_ls, float4* g_q, float4* g_sh,
+                                                          int* list, unsigned long long* count) {
   __shared__ int s_cnt;
-  const int planes = sh_planes(a.deg);
-  for (long long c0 = (long long)blockIdx.x * BWDG_CHUNK; c0 < a.n;
-       c0 += (long long)gridDim.x * BWDG_CHUNK) {
+  __shared__ unsigned long long s_base;
+  __shared__ int s_local[256];
+  for (long long i0 = blockIdx.x * (long long)blockDim.x; i0 < n;
+       i0 += (long long)gridDim.x * blockDim.x) {
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
-    for (int q = threadIdx.x; q < BWDG_CHUNK; q += BWDG_THREADS) {
-      long long i = c0 + q;
-      if (i >= a.n) break;
+    const long long i = i0 + threadIdx.x;
+    if (i < n) {
       bool seen = false;
-      for (int v = 0; v < cs.n_views; ++v) seen |= a.tiles[(long long)v * a.n + i] > 0;
+      for (int v = 0; v < n_views; ++v) seen |= tiles[(long long)v * n + i] > 0;
       if (seen) {
-        s_list[atomicAdd(&s_cnt, 1)] = q;
+        s_local[atomicAdd(&s_cnt, 1)] = (int)i;
       } else {
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        a.g_ml[i] = z;
-        a.g_ls[i] = z;
-        a.g_q[i] = z;
-        for (int p = 0; p < planes; ++p) reinterpret_cast<float4*>(a.g_sh)[(long long)p * a.n + i] = z;
+        g_ml[i] = z;
+        g_ls[i] = z;
+        g_q[i] = z;
+        for (int p = 0; p < planes; ++p) g_sh[(long long)p * n + i] = z;
       }
     }
     __syncthreads();
-    const int cnt = s_cnt;
-    for (int q = threadIdx.x; q < cnt; q += BWDG_THREADS) bwd_one(a, cs, c0 + s_list[q]);
+    if (threadIdx.x == 0 && s_cnt) s_base = atomicAdd(count, (unsigned long long)s_cnt);
+    __syncthreads();
+    if ((int)threadIdx.x < s_cnt) list[s_base + threadIdx.x] = s_local[threadIdx.x];
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(128) bwd_gauss_kernel(BwdGaussArgs a, CamSet cs,
+                                                        const int* list,
+                                                        const unsigned long long* n_list) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < (long long)*n_list) bwd_one(a, cs, list[t]);
 }
 
 }  // namespace adp
@@ -434,7 +441,8 @@ using namespace adp;
 
 extern "C" ADP_API size_t adp_render_backward_workspace_size(int64_t n, int32_t n_views) {
   if (n < 0 || n_views < 1) return 0;
-  return carve_bytes<float4>(3 * (size_t)n * n_views);
+  return carve_bytes<float4>(3 * (size_t)n * n_views) + carve_bytes<int>(n) +
+         carve_bytes<unsigned long long>(1);
 }
 
 extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_projected* pr,
@@ -459,7 +467,10 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   cudaStream_t st = (cudaStream_t)stream;
   Carver cv(ws, ws_bytes);
   float4* g2d = cv.take<float4>(3 * (size_t)g->n * n_views);
+  int* list = cv.take<int>(g->n);
+  unsigned long long* n_list = cv.take<unsigned long long>(1);
   ADP_CUDA(cudaMemsetAsync(g2d, 0, sizeof(float4) * 3 * (size_t)g->n * n_views, st));
+  ADP_CUDA(cudaMemsetAsync(n_list, 0, sizeof(unsigned long long), st));
   BwdPixArgs pa;
   pa.xyod = reinterpret_cast<const float4*>(pr->xy_opacity_depth);
   pa.conic = reinterpret_cast<const float4*>(pr->conic);
@@ -493,7 +504,10 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   ga.g_ls = reinterpret_cast<float4*>(grad->logscale);
   ga.g_q = reinterpret_cast<float4*>(grad->quat);
   ga.g_sh = grad->sh;
-  bwd_gauss_kernel<<<(unsigned)((g->n + BWDG_CHUNK - 1) / BWDG_CHUNK), BWDG_THREADS, 0, st>>>(ga, cs);
+  bwd_visible_kernel<<<grid_for(g->n, 256, 148 * 16), 256, 0, st>>>(
+      pr->tiles_touched, g->n, n_views, sh_planes(g->sh_degree), ga.g_ml, ga.g_ls, ga.g_q,
+      reinterpret_cast<float4*>(grad->sh), list, n_list);
+  bwd_gauss_kernel<<<grid_for(g->n, 128), 128, 0, st>>>(ga, cs, list, n_list);
   ADP_LAUNCH_CHECK();
   return ADP_OK;
 }

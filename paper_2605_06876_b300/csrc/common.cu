@@ -65,11 +65,15 @@ __global__ void rs_hist_kernel(const unsigned* keys, const unsigned* vals, const
     s_hist[threadIdx.x] = 0;
     __syncthreads();
     long long base = t * RS_TILE;
-#pragma unroll 4
-    for (int k = 0; k < RS_ROUNDS; ++k) {
+    unsigned d[RS_ROUNDS];
+#pragma unroll
+    for (int k = 0; k < RS_ROUNDS; ++k) {  // all loads first, then the shared atomics
       long long i = base + (long long)k * RS_THREADS + threadIdx.x;
-      if (i < N) atomicAdd(&s_hist[op(keys[i], vals[i])], 1u);
+      d[k] = i < N ? (op.divisor ? op(0u, vals[i]) : op(keys[i], 0u)) : (unsigned)RS_BINS;
     }
+#pragma unroll
+    for (int k = 0; k < RS_ROUNDS; ++k)
+      if (d[k] < (unsigned)RS_BINS) atomicAdd(&s_hist[d[k]], 1u);
     __syncthreads();
     hist[(size_t)threadIdx.x * tiles_max + t] = s_hist[threadIdx.x];
     __syncthreads();
@@ -153,11 +157,15 @@ __global__ void __launch_bounds__(RS_THREADS)
     const long long base = tile0 + (long long)warp * (RS_ROUNDS * 32);
     unsigned key[RS_ROUNDS], val[RS_ROUNDS], dig[RS_ROUNDS], off[RS_ROUNDS];
 #pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {  // issue every load before the ranking loop
+      long long i = base + r * 32 + lane;
+      key[r] = i < N ? keys_in[i] : 0u;
+      val[r] = i < N ? vals_in[i] : 0u;
+    }
+#pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
       long long i = base + r * 32 + lane;
       bool valid = i < N;
-      key[r] = valid ? keys_in[i] : 0u;
-      val[r] = valid ? vals_in[i] : 0u;
       unsigned d = valid ? op(key[r], val[r]) : (unsigned)RS_BINS;
       dig[r] = d;
       unsigned peers = __match_any_sync(0xffffffffu, d);

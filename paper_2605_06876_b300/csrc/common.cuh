@@ -251,7 +251,7 @@ int scan_exclusive(Load load, Store store, long long n_max, const long long* d_n
 // match masks in item order.
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ROUNDS = 16;  // items per lane
+constexpr int RS_ROUNDS = 8;  // items per lane
 constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
 constexpr int RS_BINS = 256;
 

@@ -3,10 +3,11 @@
 //
 // Plan: regions are grouped by candidate with a stable radix sort on the
 // candidate index (keeping their (view, label) order), one thread per region
-// builds the child proposal (Eqs. 9-10, Appendix A), and one thread per
-// candidate merges its proposals (Eqs. 11-12: pairwise test, union-find,
-// enclosing covariance from a Jacobi 3x3 eigen-decomposition), applies the
-// n_max cap and writes the surviving children into a per-region child table.
+// builds the child proposal (Eqs. 9-10, Appendix A), and one warp per
+// candidate with several proposals merges them (Eqs. 11-12: pairwise tests over
+// the lanes, union-find, enclosing covariance from a Jacobi 3x3
+// eigen-decomposition), applies the n_max cap and writes the surviving children
+// into a per-region child table.
 // Scans give every kept Gaussian its new index and every candidate the offset
 // of its appended block. This stage is small next to rendering, so it runs in
 // FP64, which keeps every integer outcome (statuses, child counts) stable.
@@ -30,6 +31,7 @@ struct SplitWs {
   int2* seg;           // [n_cand] sorted-region range of each candidate
   Prop* props;         // [Rcap]
   int* uf;             // [Rcap]
+  int* groups;         // [Rcap] root of each group, per candidate segment
   double* ext;         // [Rcap]
   float4* kids;        // [Rcap][4] child table: mean, quat, logscale, dc
   long long* keep_new; // [n]
@@ -42,7 +44,7 @@ struct SplitWs {
 static size_t split_ws_bytes(long long n, long long nc, long long rc) {
   long long sm = n > nc ? n : nc;
   return carve_bytes<int>(n) + 2 * carve_bytes<unsigned>(rc) + carve_bytes<int2>(nc) +
-         carve_bytes<Prop>(rc) + carve_bytes<int>(rc) + carve_bytes<double>(rc) +
+         carve_bytes<Prop>(rc) + 2 * carve_bytes<int>(rc) + carve_bytes<double>(rc) +
          carve_bytes<float4>(4 * rc) + carve_bytes<long long>(n) + carve_bytes<long long>(nc) +
          carve_bytes<long long>(4) + scan_workspace_bytes(sm) + sort_workspace_bytes(rc);
 }
@@ -56,6 +58,7 @@ static SplitWs carve_split(Carver& c, long long n, long long nc, long long rc) {
   w.seg = c.take<int2>(nc);
   w.props = c.take<Prop>(rc);
   w.uf = c.take<int>(rc);
+  w.groups = c.take<int>(rc);
   w.ext = c.take<double>(rc);
   w.kids = c.take<float4>(4 * rc);
   w.keep_new = c.take<long long>(n);
@@ -312,11 +315,6 @@ __global__ void proposal_kernel(ProposalArgs a, CamSet cs) {
   }
 }
 
-__device__ __forceinline__ int uf_root(int* uf, int a) {
-  while (uf[a] != a) a = uf[a];
-  return a;
-}
-
 __device__ void store_child(float4* kid, const double* mu, const double* R, const double* s,
                             const double* rgb) {
   kid[0] = make_float4((float)mu[0], (float)mu[1], (float)mu[2], 0.f);
@@ -333,6 +331,7 @@ struct MergeArgs {
   const int2* seg;
   const Prop* props;
   int* uf;
+  int* groups;
   double* ext;
   float4* kids;
   long long nc;
@@ -342,121 +341,204 @@ struct MergeArgs {
   int* n_children;
 };
 
-// One thread per candidate: status, merge (Eqs. 11-12), cap, child table.
-__global__ void merge_kernel(MergeArgs a) {
+// Eq. 11 between two proposals.
+__device__ __forceinline__ bool merge_edge(const Prop& px, const Prop& py, double gamma_d,
+                                           double gamma_c) {
+  double dc = fmax(fabs(px.rgb[0] - py.rgb[0]),
+                   fmax(fabs(px.rgb[1] - py.rgb[1]), fabs(px.rgb[2] - py.rgb[2])));
+  if (dc > gamma_c) return false;
+  double d[3] = {py.mu[0] - px.mu[0], py.mu[1] - px.mu[1], py.mu[2] - px.mu[2]};
+  return mahal_d(px, d) + mahal_d(py, d) <= gamma_d;
+}
+
+// Merged parameters of the group rooted at proposal g (members m >= g with
+// uf[m] == g), Eq. 12; a one-member group is the proposal itself.
+__device__ void merged_group(const MergeArgs& a, int s0, int M, int g, double* mu, double* rgb,
+                             double* R, double* s) {
+  const int* uf = a.uf + s0;
+  int cnt = 0, last = g;
+  double gm[3] = {0, 0, 0}, gc[3] = {0, 0, 0}, Sb[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int m = g; m < M; ++m) {
+    if (uf[m] != g) continue;
+    const Prop& p = a.props[s0 + m];
+    double S[9];
+    sigma_of(p, S);
+    for (int k = 0; k < 3; ++k) {
+      gm[k] += p.mu[k];
+      gc[k] += p.rgb[k];
+    }
+    for (int k = 0; k < 9; ++k) Sb[k] += S[k];
+    ++cnt;
+    last = m;
+  }
+  if (cnt == 1) {
+    const Prop& p = a.props[s0 + g];
+    for (int k = 0; k < 3; ++k) {
+      mu[k] = p.mu[k];
+      rgb[k] = p.rgb[k];
+      s[k] = p.s[k];
+    }
+    for (int k = 0; k < 9; ++k) R[k] = p.R[k];
+    return;
+  }
+  for (int k = 0; k < 3; ++k) {
+    mu[k] = gm[k] / cnt;
+    rgb[k] = gc[k] / cnt;
+  }
+  for (int k = 0; k < 9; ++k) Sb[k] /= cnt;
+  double ev[3];
+  sym3_eigen(Sb, ev, R);
+  double lam[3] = {0, 0, 0};
+  for (int m = g; m <= last; ++m) {
+    if (uf[m] != g) continue;
+    const Prop& p = a.props[s0 + m];
+    double S[9];
+    sigma_of(p, S);
+    for (int r = 0; r < 3; ++r) {
+      double e[3] = {R[r], R[3 + r], R[6 + r]};
+      double Se[3];
+      for (int k = 0; k < 3; ++k) Se[k] = S[3 * k] * e[0] + S[3 * k + 1] * e[1] + S[3 * k + 2] * e[2];
+      double dm[3] = {p.mu[0] - mu[0], p.mu[1] - mu[1], p.mu[2] - mu[2]};
+      double reach = fabs(dot3d(e, dm)) + sqrt(fmax(dot3d(e, Se), 0.0));
+      lam[r] = fmax(lam[r], reach * reach);
+    }
+  }
+  double c0[3] = {R[0], R[3], R[6]}, c1[3] = {R[1], R[4], R[7]}, c2[3] = {R[2], R[5], R[8]}, cc[3];
+  cross3d(c0, c1, cc);
+  if (dot3d(cc, c2) < 0.0) {
+    R[2] = -R[2];
+    R[5] = -R[5];
+    R[8] = -R[8];
+  }
+  for (int r = 0; r < 3; ++r) s[r] = fmax(sqrt(lam[r]), a.scale_floor);
+}
+
+// One thread per candidate: statuses, and the whole answer for candidates with
+// at most one proposal (the common case); candidates with more are left to
+// merge_warp_kernel.
+__global__ void merge_status_kernel(MergeArgs a) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.nc;
        c += (long long)gridDim.x * blockDim.x) {
-    int i = a.cand[c];
-    int2 sg = a.seg[c];
-    int s0 = sg.x, M = sg.y - sg.x;
+    const int i = a.cand[c];
+    const int2 sg = a.seg[c];
+    const int M = sg.y - sg.x;
     if (a.count[i] == 0) {
       a.status[c] = ADP_FALLBACK;
       a.n_children[c] = 0;
-      continue;
-    }
-    if (M <= 0) {
+    } else if (M <= 0) {
       a.status[c] = ADP_RESET;
       a.n_children[c] = 0;
-      continue;
+    } else {
+      a.status[c] = ADP_ADAPTIVE;
+      if (M == 1) {
+        const Prop& p = a.props[sg.x];
+        if (a.n_max >= 1) store_child(a.kids + 4LL * sg.x, p.mu, p.R, p.s, p.rgb);
+        a.n_children[c] = a.n_max >= 1 ? 1 : 0;
+      }
     }
-    a.status[c] = ADP_ADAPTIVE;
+  }
+}
+
+__device__ __forceinline__ int uf_root_v(volatile int* uf, int x) {
+  int p = uf[x];
+  while (p != x) {
+    x = p;
+    p = uf[x];
+  }
+  return x;
+}
+
+// One warp per candidate with two or more proposals: the pairwise tests of
+// Eq. 11 are spread over the lanes and joined in a union-find whose links point
+// to smaller indices (so every group is rooted at its first member); groups are
+// numbered in first-member order, merged one per lane (Eq. 12), capped at n_max
+// by extent (ties to the earlier group) and written to the child table in order.
+__global__ void merge_warp_kernel(MergeArgs a) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long c = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); c < a.nc;
+       c += warps) {
+    const int2 sg = a.seg[c];
+    const int s0 = sg.x, M = sg.y - sg.x;
+    if (M < 2 || a.count[a.cand[c]] == 0) continue;
     int* uf = a.uf + s0;
-    for (int m = 0; m < M; ++m) uf[m] = m;
-    for (int x = 0; x < M; ++x) {
+    volatile int* vuf = uf;
+    for (int m = lane; m < M; m += 32) uf[m] = m;
+    __syncwarp();
+    for (int x = 0; x < M - 1; ++x) {
       const Prop& px = a.props[s0 + x];
-      for (int y = x + 1; y < M; ++y) {
-        const Prop& py = a.props[s0 + y];
-        double dc = fmax(fabs(px.rgb[0] - py.rgb[0]),
-                         fmax(fabs(px.rgb[1] - py.rgb[1]), fabs(px.rgb[2] - py.rgb[2])));
-        if (dc > a.gamma_c) continue;
-        double d[3] = {py.mu[0] - px.mu[0], py.mu[1] - px.mu[1], py.mu[2] - px.mu[2]};
-        double dist = mahal_d(px, d) + mahal_d(py, d);
-        if (dist > a.gamma_d) continue;
-        int rx = uf_root(uf, x), ry = uf_root(uf, y);
-        if (rx < ry) uf[ry] = rx;
-        else if (ry < rx) uf[rx] = ry;
-      }
-    }
-    for (int m = 0; m < M; ++m) uf[m] = uf_root(uf, m);
-    // groups in first-member order, written to the child table in place
-    int ng = 0;
-    for (int g = 0; g < M; ++g) {
-      if (uf[g] != g) continue;
-      int cnt = 0;
-      double gm[3] = {0, 0, 0}, gc[3] = {0, 0, 0}, Sb[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-      int last = g;
-      for (int m = g; m < M; ++m) {
-        if (uf[m] != g) continue;
-        const Prop& p = a.props[s0 + m];
-        double S[9];
-        sigma_of(p, S);
-        for (int k = 0; k < 3; ++k) {
-          gm[k] += p.mu[k];
-          gc[k] += p.rgb[k];
-        }
-        for (int k = 0; k < 9; ++k) Sb[k] += S[k];
-        ++cnt;
-        last = m;
-      }
-      double mu[3], rgb[3], R[9], s[3];
-      if (cnt == 1) {  // Eq. 12 reduces to the member itself
-        const Prop& p = a.props[s0 + g];
-        for (int k = 0; k < 3; ++k) {
-          mu[k] = p.mu[k];
-          rgb[k] = p.rgb[k];
-          s[k] = p.s[k];
-        }
-        for (int k = 0; k < 9; ++k) R[k] = p.R[k];
-      } else {
-        for (int k = 0; k < 3; ++k) {
-          mu[k] = gm[k] / cnt;
-          rgb[k] = gc[k] / cnt;
-        }
-        for (int k = 0; k < 9; ++k) Sb[k] /= cnt;
-        double ev[3];
-        sym3_eigen(Sb, ev, R);
-        double lam[3] = {0, 0, 0};
-        for (int m = g; m <= last; ++m) {
-          if (uf[m] != g) continue;
-          const Prop& p = a.props[s0 + m];
-          double S[9];
-          sigma_of(p, S);
-          for (int r = 0; r < 3; ++r) {
-            double e[3] = {R[r], R[3 + r], R[6 + r]};
-            double Se[3];
-            for (int k = 0; k < 3; ++k) Se[k] = S[3 * k] * e[0] + S[3 * k + 1] * e[1] + S[3 * k + 2] * e[2];
-            double dm[3] = {p.mu[0] - mu[0], p.mu[1] - mu[1], p.mu[2] - mu[2]};
-            double reach = fabs(dot3d(e, dm)) + sqrt(fmax(dot3d(e, Se), 0.0));
-            lam[r] = fmax(lam[r], reach * reach);
+      for (int y = x + 1 + lane; y < M; y += 32) {
+        if (!merge_edge(px, a.props[s0 + y], a.gamma_d, a.gamma_c)) continue;
+        int u = x, w = y;
+        for (int guard = 0; guard < 4096; ++guard) {  // lock-free union, min-rooted
+          u = uf_root_v(vuf, u);
+          w = uf_root_v(vuf, w);
+          if (u == w) break;
+          if (u > w) {
+            int t = u;
+            u = w;
+            w = t;
           }
+          int old = atomicMin(&uf[w], u);
+          if (old == w) break;
+          w = old;
         }
-        double c0[3] = {R[0], R[3], R[6]}, c1[3] = {R[1], R[4], R[7]}, c2[3] = {R[2], R[5], R[8]}, cc[3];
-        cross3d(c0, c1, cc);
-        if (dot3d(cc, c2) < 0.0) {
-          R[2] = -R[2]; R[5] = -R[5]; R[8] = -R[8];
-        }
-        for (int r = 0; r < 3; ++r) s[r] = fmax(sqrt(lam[r]), a.scale_floor);
-      }
-      a.ext[s0 + ng] = s[0] * s[1] * s[2];
-      store_child(a.kids + 4LL * (s0 + ng), mu, R, s, rgb);
-      ++ng;
-    }
-    // cap: keep the n_max largest extents (ties to the earlier group), in group order
-    int kept = 0;
-    for (int gk = 0; gk < ng; ++gk) {
-      double e = a.ext[s0 + gk];
-      int rank = 0;
-      for (int h = 0; h < ng; ++h) {
-        double eh = a.ext[s0 + h];
-        if (eh > e || (eh == e && h < gk)) ++rank;
-      }
-      if (rank < a.n_max) {
-        if (kept != gk)
-          for (int q = 0; q < 4; ++q) a.kids[4LL * (s0 + kept) + q] = a.kids[4LL * (s0 + gk) + q];
-        ++kept;
       }
     }
-    a.n_children[c] = kept;
+    __syncwarp();
+    __threadfence_block();
+    for (int m = lane; m < M; m += 32) uf[m] = uf_root_v(vuf, m);
+    __syncwarp();
+    // groups in first-member order
+    int ng = 0;
+    for (int base = 0; base < M; base += 32) {
+      const int m = base + lane;
+      const bool root = m < M && uf[m] == m;
+      const unsigned msk = __ballot_sync(0xffffffffu, root);
+      if (root) a.groups[s0 + ng + __popc(msk & lanemask_lt())] = m;
+      ng += __popc(msk);
+    }
+    __syncwarp();
+    for (int gi = lane; gi < ng; gi += 32) {
+      double mu[3], rgb[3], R[9], sc[3];
+      merged_group(a, s0, M, a.groups[s0 + gi], mu, rgb, R, sc);
+      a.ext[s0 + gi] = sc[0] * sc[1] * sc[2];
+      store_child(a.kids + 4LL * (s0 + gi), mu, R, sc, rgb);
+    }
+    __syncwarp();
+    // cap, then compaction in group order (positions never pass their source)
+    int kept_total = 0;
+    for (int base = 0; base < ng; base += 32) {
+      const int gk = base + lane;
+      bool keep = false;
+      float4 k0, k1, k2, k3;
+      if (gk < ng) {
+        const double e = a.ext[s0 + gk];
+        int rank = 0;
+        for (int h = 0; h < ng && rank < a.n_max; ++h) {
+          const double eh = a.ext[s0 + h];
+          rank += (eh > e || (eh == e && h < gk)) ? 1 : 0;
+        }
+        keep = rank < a.n_max;
+        const float4* src = a.kids + 4LL * (s0 + gk);
+        k0 = src[0];
+        k1 = src[1];
+        k2 = src[2];
+        k3 = src[3];
+      }
+      const unsigned msk = __ballot_sync(0xffffffffu, keep);
+      __syncwarp();
+      if (keep) {
+        float4* dst = a.kids + 4LL * (s0 + kept_total + __popc(msk & lanemask_lt()));
+        dst[0] = k0;
+        dst[1] = k1;
+        dst[2] = k2;
+        dst[3] = k3;
+      }
+      kept_total += __popc(msk);
+      __syncwarp();
+    }
+    if (lane == 0) a.n_children[c] = kept_total;
   }
 }
 
@@ -684,6 +766,7 @@ extern "C" ADP_API int adp_split_plan(const adp_gaussians* g, const adp_camera* 
     ma.seg = w.seg;
     ma.props = w.props;
     ma.uf = w.uf;
+    ma.groups = w.groups;
     ma.ext = w.ext;
     ma.kids = w.kids;
     ma.nc = nc;
@@ -693,7 +776,8 @@ extern "C" ADP_API int adp_split_plan(const adp_gaussians* g, const adp_camera* 
     ma.n_max = prm->n_max;
     ma.status = status;
     ma.n_children = n_children;
-    merge_kernel<<<grid_for(nc, 64, 4096), 64, 0, st>>>(ma);
+    merge_status_kernel<<<grid_for(nc, 256, 4096), 256, 0, st>>>(ma);
+    merge_warp_kernel<<<grid_for(nc * 32, 128, 4096), 128, 0, st>>>(ma);
     ADP_LAUNCH_CHECK();
   }
   // new indices of kept Gaussians and offsets of appended blocks
