@@ -1,14 +1,16 @@
 // Hand-written backward of the compositing and projection.
 //
-// Pass 1 (one CTA per tile, two pixels per thread): walks the tile's list back
-// to front from each pixel's last blended Gaussian, recovering the
+// Pass 1 (one CTA per tile, several pixels per thread): walks the tile's list
+// back to front from each pixel's last blended Gaussian, recovering the
 // transmittance before each Gaussian as T / (1 - alpha) from T_final instead of
 // storing it, and the normalised colour behind it by the recurrence
-// R <- alpha c + (1 - alpha) R starting from the background. Per Gaussian it
-// yields dL/d(mean2d, conic, opacity, rgb); a warp reduces the 32 pixels'
-// contributions (a reduce-scatter) before nine scalar atomics per record.
-// Pass 2 (one thread per visible Gaussian, from a compacted list): chains those 2D gradients through the
-// EWA projection and the SH colour of every view and sums over views, so the
+// R <- R + alpha (c - R) starting from the background. Per (view, Gaussian) it
+// accumulates pixel moments of dL/dalpha (and the colour gradient); a warp
+// reduces its pixels' contributions (a reduce-scatter) before nine scalar
+// atomics per record.
+// Pass 2 (one thread per visible Gaussian, from a compacted list): turns the
+// moments into dL/d(mean2d, conic, opacity), chains them through the EWA
+// projection and the SH colour of every view and sums over views, so the
 // per-Gaussian parameters are read and the gradients written once per step.
 #include "gauss_math.cuh"
 
@@ -62,55 +64,29 @@ __device__ __forceinline__ float reduce_scatter8(const float* v, int* idx) {
   return x;
 }
 
-// Two horizontally adjacent pixels per thread, staged Gaussians in the form the
+// PX horizontally adjacent pixels per thread, staged Gaussians in the form the
 // forward uses (so every alpha test agrees with the forward's), a warp-uniform
-// skip of Gaussians that reach none of the warp's rows, and one warp reduction
-// per staged Gaussian covering the warp's 64 pixels.
-constexpr int BWD_THREADS = 128;
+// skip of Gaussians that reach none of the warp's rows, a branch-free per-pixel
+// update, and one warp reduction per staged Gaussian covering the warp's pixels.
+//
+// What is reduced and accumulated per (view, Gaussian) are moments of
+// k = dL/dalpha * alpha over the pixels (alpha below the 0.99 clamp only) with
+// d = mean - pixel: S = sum k, Sx = sum k dx, Sy = sum k dy, Sxx, Sxy, Syy, and
+// the colour gradient sum T alpha dL/dpix. With alpha = o exp(power) and
+// power = -(A dx^2 + 2 B dx dy + C dy^2) / 2 they give dL/do = S / o,
+// dL/dA = -Sxx / 2, dL/dB = -Sxy, dL/dC = -Syy / 2, dL/dmean = -(A Sx + B Sy,
+// B Sx + C Sy); the per-Gaussian pass applies these. A thread's pixels share
+// dy, so Sy, Sxy, Syy follow from its S and Sx.
+#ifndef ADP_BWD_PX
+#define ADP_BWD_PX 4
+#endif
+constexpr int BWD_PX = ADP_BWD_PX;
 constexpr int BWD_STAGE = 256;
 
-struct PixState {
-  float T, R0, R1, R2, g0, g1, g2, fx, fy;
-  int last;
-};
-
-// Contribution of one staged Gaussian to one pixel's gradients (adds into v[9]):
-// v = (d mean x, d mean y, d conic A, d conic B, d conic C, d opacity, d r, d g, d b).
-__device__ __forceinline__ bool bwd_contrib(PixState& s, int pos, const Staged& g, float amax,
-                                            float l2amin, float* v) {
-  if (pos >= s.last) return false;
-  float dx, dy;
-  const float q = log2_alpha(g.g0, g.g1, s.fx, s.fy, &dx, &dy);
-  if (q < l2amin) return false;
-  const float ar = exp2f(q);
-  const float al = fminf(amax, ar);
-  const float Tj = s.T * __frcp_rn(1.f - al);
-  const float c0 = g.g1.z, c1 = g.g1.w, c2 = g.g2.x;
-  const float dal = Tj * (s.g0 * (c0 - s.R0) + s.g1 * (c1 - s.R1) + s.g2 * (c2 - s.R2));
-  const float wgt = Tj * al;
-  v[6] += wgt * s.g0;
-  v[7] += wgt * s.g1;
-  v[8] += wgt * s.g2;
-  s.R0 = al * c0 + (1.f - al) * s.R0;
-  s.R1 = al * c1 + (1.f - al) * s.R1;
-  s.R2 = al * c2 + (1.f - al) * s.R2;
-  s.T = Tj;
-  if (ar <= amax) {
-    // alpha = o exp(power): d alpha / d o = alpha / o, d alpha / d power = alpha
-    v[5] += dal * ar * g.g2.z;
-    const float dpow = dal * ar;
-    v[2] += -0.5f * dx * dx * dpow;
-    v[4] += -0.5f * dy * dy * dpow;
-    v[3] += -dx * dy * dpow;
-    // -(A dx + B dy) = (2 a dx + b dy) / log2(e), with a, b the staged log2 conic
-    const float dpk = dpow * (1.f / kLog2e);
-    v[0] += fmaf(2.f * g.g0.z, dx, g.g0.w * dy) * dpk;
-    v[1] += fmaf(2.f * g.g1.x, dy, g.g0.w * dx) * dpk;
-  }
-  return true;
-}
-
-__global__ void __launch_bounds__(BWD_THREADS) bwd_pixel_kernel(BwdPixArgs a, CamSet cs) {
+template <int PX>
+__global__ void __launch_bounds__(TileLanes<PX>::THREADS)
+    bwd_pixel_kernel(BwdPixArgs a, CamSet cs) {
+  constexpr int NT = TileLanes<PX>::THREADS;
   __shared__ float4 s_g0[BWD_STAGE];
   __shared__ float4 s_g1[BWD_STAGE];
   __shared__ float4 s_g2[BWD_STAGE];
@@ -126,43 +102,45 @@ __global__ void __launch_bounds__(BWD_THREADS) bwd_pixel_kernel(BwdPixArgs a, Ca
   const float sc = 1.f / (3.f * (float)W * (float)H);
   const int tx0 = (lt % txs) * cs.tile_w, ty0 = (lt / txs) * cs.tile_h;
   const int warp = threadIdx.x >> 5;
-  const float wy0 = (float)(ty0 + (64 * warp) / cs.tile_w);
-  const float wy1 = (float)(ty0 + (64 * warp + 63) / cs.tile_w);
+  const float wy0 = (float)(ty0 + (TileLanes<PX>::WARP_PIXELS * warp) / cs.tile_w);
+  const float wy1 =
+      (float)(ty0 + (TileLanes<PX>::WARP_PIXELS * (warp + 1) - 1) / cs.tile_w);
+  const int li0 = PX * (int)threadIdx.x;
+  const int px0 = tx0 + li0 % cs.tile_w, py = ty0 + li0 / cs.tile_w;
+  const float fy = (float)py;
+  const float amax = a.alpha_max, l2amin = a.log2_alpha_min;
 
-  PixState ps[2];
+  // per pixel: transmittance, colour behind, dL/dpixel, last blended position
+  float T[PX], R0[PX], R1[PX], R2[PX], G0[PX], G1[PX], G2[PX];
+  int last[PX];
   int warp_last = 0;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int li = 2 * (int)threadIdx.x + h;
-    const int px = tx0 + li % cs.tile_w;
-    const int py = ty0 + li / cs.tile_w;
-    PixState& s = ps[h];
-    s.fx = (float)px;
-    s.fy = (float)py;
-    s.T = 1.f;
-    s.R0 = a.bg[0];
-    s.R1 = a.bg[1];
-    s.R2 = a.bg[2];
-    s.g0 = s.g1 = s.g2 = 0.f;
-    s.last = 0;
+  for (int h = 0; h < PX; ++h) {
+    T[h] = 1.f;
+    R0[h] = a.bg[0];
+    R1[h] = a.bg[1];
+    R2[h] = a.bg[2];
+    G0[h] = G1[h] = G2[h] = 0.f;
+    last[h] = 0;
+    const int px = px0 + h;
     if (px < W && py < H) {
       long long p = cs.pix_base[v] + (long long)py * W + px;
-      s.T = a.T_final[p];
-      s.last = a.last[p];
+      T[h] = a.T_final[p];
+      last[h] = a.last[p];
       if (a.dL_drgb) {
-        s.g0 = a.dL_drgb[3 * p];
-        s.g1 = a.dL_drgb[3 * p + 1];
-        s.g2 = a.dL_drgb[3 * p + 2];
+        G0[h] = a.dL_drgb[3 * p];
+        G1[h] = a.dL_drgb[3 * p + 1];
+        G2[h] = a.dL_drgb[3 * p + 2];
       } else {
         float d0 = a.img[3 * p] - a.target[3 * p];
         float d1 = a.img[3 * p + 1] - a.target[3 * p + 1];
         float d2 = a.img[3 * p + 2] - a.target[3 * p + 2];
-        s.g0 = d0 > 0.f ? sc : (d0 < 0.f ? -sc : 0.f);
-        s.g1 = d1 > 0.f ? sc : (d1 < 0.f ? -sc : 0.f);
-        s.g2 = d2 > 0.f ? sc : (d2 < 0.f ? -sc : 0.f);
+        G0[h] = d0 > 0.f ? sc : (d0 < 0.f ? -sc : 0.f);
+        G1[h] = d1 > 0.f ? sc : (d1 < 0.f ? -sc : 0.f);
+        G2[h] = d2 > 0.f ? sc : (d2 < 0.f ? -sc : 0.f);
       }
     }
-    warp_last = max(warp_last, s.last);
+    warp_last = max(warp_last, last[h]);
   }
   if (threadIdx.x == 0) s_maxlast = 0;
   __syncthreads();
@@ -174,7 +152,7 @@ __global__ void __launch_bounds__(BWD_THREADS) bwd_pixel_kernel(BwdPixArgs a, Ca
   for (int b1 = end; b1 > 0; b1 -= BWD_STAGE) {
     const int b0 = b1 - BWD_STAGE > 0 ? b1 - BWD_STAGE : 0;
     __syncthreads();
-    for (int j = (int)threadIdx.x; j < b1 - b0; j += BWD_THREADS) {
+    for (int j = (int)threadIdx.x; j < b1 - b0; j += NT) {
       int id = a.inst[range.x + b0 + j];
       long long r = rec_base + id;
       Staged g = stage_gaussian(a.xyod[r], a.conic[r], a.rgb[r], id, a.alpha_min);
@@ -188,22 +166,46 @@ __global__ void __launch_bounds__(BWD_THREADS) bwd_pixel_kernel(BwdPixArgs a, Ca
     for (int k = kmax - 1; k >= 0; --k) {
       const float2 yr = s_y[k];
       if (yr.y < wy0 || yr.x > wy1) continue;  // warp-uniform: no row of this warp reached
-      Staged g;
-      g.g0 = s_g0[k];
-      g.g1 = s_g1[k];
-      g.g2 = s_g2[k];
+      const float4 g0 = s_g0[k], g1 = s_g1[k], g2 = s_g2[k];
+      const RowQ rq = row_q(g0, g1, fy);
       const int pos = b0 + k;
-      float vals[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      bool hit = bwd_contrib(ps[0], pos, g, a.alpha_max, a.log2_alpha_min, vals);
-      hit |= bwd_contrib(ps[1], pos, g, a.alpha_max, a.log2_alpha_min, vals);
+      float S = 0.f, Sx = 0.f, Sxx = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+      bool hit = false;
+#pragma unroll
+      for (int h = 0; h < PX; ++h) {
+        float dx;
+        const float q = pix_q(g0, rq, (float)(px0 + h), &dx);
+        const bool p = pos < last[h] && q >= l2amin;  // blended in the forward
+        hit = hit || p;
+        const float ar = ex2_approx(q);
+        const float al = p ? fminf(amax, ar) : 0.f;
+        const float Tj = T[h] * rcp_approx(1.f - al);  // transmittance before this Gaussian
+        const float d0 = g1.z - R0[h], d1 = g1.w - R1[h], d2 = g2.x - R2[h];
+        const float dal = Tj * fmaf(G0[h], d0, fmaf(G1[h], d1, G2[h] * d2));
+        const float wgt = Tj * al;
+        C0 = fmaf(wgt, G0[h], C0);
+        C1 = fmaf(wgt, G1[h], C1);
+        C2 = fmaf(wgt, G2[h], C2);
+        R0[h] = fmaf(al, d0, R0[h]);
+        R1[h] = fmaf(al, d1, R1[h]);
+        R2[h] = fmaf(al, d2, R2[h]);
+        T[h] = Tj;
+        const float kk = (p && ar <= amax) ? dal * ar : 0.f;  // zero through the clamp
+        S += kk;
+        const float t = dx * kk;
+        Sx += t;
+        Sxx = fmaf(dx, t, Sxx);
+      }
       if (__ballot_sync(0xffffffffu, hit)) {
+        const float dy = rq.dy;
+        float vals[8] = {S, Sx, dy * S, Sxx, dy * Sx, dy * dy * S, C0, C1};
         int idx;
         float sum = reduce_scatter8(vals, &idx);
-        float db = warp_sum(vals[8]);
-        int id = __float_as_int(g.g2.y);
+        float cb = warp_sum(C2);
+        int id = __float_as_int(g2.y);
         float* gp = reinterpret_cast<float*>(a.g2d + 3 * (rec_base + id));
         if ((lane & 3) == 0) atomicAdd(gp + idx, sum);
-        if (lane == 0) atomicAdd(gp + 8, db);
+        if (lane == 0) atomicAdd(gp + 8, cb);
       }
     }
   }
@@ -249,8 +251,10 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
   for (int v = 0; v < cs.n_views; ++v) {
     long long rec = (long long)v * a.n + i;
     if (a.tiles[rec] <= 0) continue;
+    // pixel moments of dL/dalpha * alpha (see the per-pixel pass)
     float4 q0 = a.g2d[3 * rec], q1 = a.g2d[3 * rec + 1], q2 = a.g2d[3 * rec + 2];
-    float gmx = q0.x, gmy = q0.y, gA = q0.z, gB = q0.w, gC = q1.x, gop = q1.y;
+    const float mS = q0.x, mSx = q0.y, mSy = q0.z;
+    float gA = -0.5f * q0.w, gB = -q1.x, gC = -0.5f * q1.y;
     float gcol[3] = {q1.z, q1.w, q2.x};
     const adp_camera& cam = cs.cam[v];
     const float* Rw = cam.R;
@@ -258,8 +262,8 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
     for (int r = 0; r < 3; ++r)
       pc[r] = Rw[3 * r] * ml.x + Rw[3 * r + 1] * ml.y + Rw[3 * r + 2] * ml.z + cam.t[r];
     float z = pc[2], iz = 1.f / z;
-    // opacity
-    glogit += gop * o * (1.f - o);
+    // opacity: dL/do = S / o, do/dlogit = o (1 - o)
+    glogit += mS * (1.f - o);
     // colour
     float ccx = -(Rw[0] * cam.t[0] + Rw[3] * cam.t[1] + Rw[6] * cam.t[2]);
     float ccy = -(Rw[1] * cam.t[0] + Rw[4] * cam.t[1] + Rw[7] * cam.t[2]);
@@ -347,7 +351,8 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
       gp[1] += -cam.fy * iz2 * gJ12;
       gp[2] += cam.fy * pc[1] * iz2 * iz * gJ12;
     }
-    // 2D mean
+    // 2D mean: dL/dmean = -(Q [Sx, Sy])
+    const float gmx = -(QA * mSx + QB * mSy), gmy = -(QB * mSx + QC * mSy);
     gp[0] += gmx * cam.fx * iz;
     gp[1] += gmy * cam.fy * iz;
     gp[2] += -(gmx * cam.fx * pc[0] + gmy * cam.fy * pc[1]) * iz2;
@@ -488,7 +493,7 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   pa.alpha_max = prm->alpha_max;
   pa.log2_alpha_min = log2f(prm->alpha_min);
   pa.g2d = g2d;
-  bwd_pixel_kernel<<<cs.tile_base[n_views], BWD_THREADS, 0, st>>>(pa, cs);
+  bwd_pixel_kernel<BWD_PX><<<cs.tile_base[n_views], TileLanes<BWD_PX>::THREADS, 0, st>>>(pa, cs);
   ADP_LAUNCH_CHECK();
   BwdGaussArgs ga;
   ga.mean_logit = reinterpret_cast<const float4*>(g->mean_logit);

@@ -125,15 +125,50 @@ __device__ __forceinline__ Staged stage_gaussian(float4 xyod, float4 conic, floa
   return s;
 }
 
-// log2 of alpha_raw = o exp(-d^T C d / 2) at pixel (px, py), with d = mean - pixel.
-// Forward and backward both evaluate it (and compare it with log2(alpha_min))
-// through this function, so their decisions agree bit for bit.
-__device__ __forceinline__ float log2_alpha(const float4& g0, const float4& g1, float px, float py,
-                                            float* dx_out, float* dy_out) {
-  const float dx = g0.x - px, dy = g0.y - py;
-  *dx_out = dx;
-  *dy_out = dy;
-  return fmaf(g0.z, dx * dx, fmaf(g1.x, dy * dy, fmaf(g0.w, dx * dy, g1.y)));
+// log2 of alpha_raw = o exp(-d^T C d / 2) at a pixel, with d = mean - pixel,
+// written as q = dx (a dx + b dy) + (c dy^2 + log2 o) in the staged log2 conic
+// (a, b, c): the bracketed term and b dy depend only on the pixel row, so a
+// thread computes them once for its pixels of one row. Forward and backward
+// both evaluate q through these two functions, and the value of a pixel does not
+// depend on which thread computes it, so their decisions agree bit for bit for
+// every tile shape.
+struct RowQ {
+  float dy, bdy, e;
+};
+
+__device__ __forceinline__ RowQ row_q(const float4& g0, const float4& g1, float py) {
+  RowQ r;
+  r.dy = g0.y - py;
+  r.bdy = g0.w * r.dy;
+  r.e = fmaf(g1.x * r.dy, r.dy, g1.y);
+  return r;
 }
+
+__device__ __forceinline__ float pix_q(const float4& g0, const RowQ& r, float px, float* dx) {
+  *dx = g0.x - px;
+  return fmaf(*dx, fmaf(g0.z, *dx, r.bdy), r.e);
+}
+
+// 2^x and 1/x from the special-function unit (relative error about 2^-22;
+// subnormal results flush to zero, which only ever meets alphas already below
+// the 1/255 cut).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Pixel layout of a 256-pixel tile with PX horizontally adjacent pixels per
+// thread (PX divides every supported tile width).
+template <int PX>
+struct TileLanes {
+  static constexpr int THREADS = 256 / PX;
+  static constexpr int WARP_PIXELS = 32 * PX;
+};
 
 }  // namespace adp

@@ -1,10 +1,16 @@
 // Front-to-back alpha compositing (Eq. 1) with the dominant Gaussian map (Eq. 5).
-// One CTA per tile (256 pixels, two horizontally adjacent ones per thread); the
+// One CTA per tile (256 pixels, PX horizontally adjacent ones per thread); the
 // tile's depth-sorted list is staged through shared memory 256 Gaussians at a
 // time in a precomputed form (alpha in log2 units, the rows each ellipse
-// reaches), a warp skips Gaussians that reach none of its rows, and a block-wide
-// vote ends the tile once every pixel has stopped.
+// reaches), a warp skips Gaussians that reach none of its rows, the per-pixel
+// update is branch-free (a pixel that has stopped, or that a Gaussian misses,
+// takes a zero weight), a warp leaves the batch once all its pixels have
+// stopped and a block-wide vote ends the tile.
 #include "gauss_math.cuh"
+
+#ifndef ADP_RENDER_PX
+#define ADP_RENDER_PX 4
+#endif
 
 namespace adp {
 
@@ -24,41 +30,12 @@ struct RenderArgs {
   int* out_dom;
 };
 
-constexpr int RENDER_THREADS = 128;  // two horizontally adjacent pixels per thread
-constexpr int STAGE = 256;           // Gaussians staged per batch
+constexpr int RENDER_PX = ADP_RENDER_PX;
+constexpr int STAGE = 256;  // Gaussians staged per batch
 
-struct FwdPix {
-  float T, c0, c1, c2, best, fx, fy;
-  int dom, ncon, last;
-  bool done;
-};
-
-__device__ __forceinline__ void fwd_step(FwdPix& s, int pos, const Staged& g, float amax,
-                                         float tmin, float l2amin) {
-  if (s.done) return;
-  float dx, dy;
-  const float q = log2_alpha(g.g0, g.g1, s.fx, s.fy, &dx, &dy);
-  if (q < l2amin) return;
-  const float al = fminf(amax, exp2f(q));
-  const float test = s.T * (1.f - al);
-  if (test < tmin) {
-    s.done = true;
-    return;
-  }
-  const float w = s.T * al;
-  s.c0 += w * g.g1.z;
-  s.c1 += w * g.g1.w;
-  s.c2 += w * g.g2.x;
-  if (w > s.best) {
-    s.best = w;
-    s.dom = __float_as_int(g.g2.y);
-  }
-  s.T = test;
-  ++s.ncon;
-  s.last = pos + 1;
-}
-
-__global__ void __launch_bounds__(RENDER_THREADS) render_kernel(RenderArgs a, CamSet cs) {
+template <int PX>
+__global__ void __launch_bounds__(TileLanes<PX>::THREADS) render_kernel(RenderArgs a, CamSet cs) {
+  constexpr int NT = TileLanes<PX>::THREADS;
   __shared__ float4 s_g0[STAGE];
   __shared__ float4 s_g1[STAGE];
   __shared__ float4 s_g2[STAGE];
@@ -73,33 +50,33 @@ __global__ void __launch_bounds__(RENDER_THREADS) render_kernel(RenderArgs a, Ca
   const long long rec_base = (long long)v * a.n;
   const int tx0 = (lt % txs) * cs.tile_w, ty0 = (lt / txs) * cs.tile_h;
   const int warp = threadIdx.x >> 5;
-  // the rows this warp's 64 pixels cover
-  const float wy0 = (float)(ty0 + (64 * warp) / cs.tile_w);
-  const float wy1 = (float)(ty0 + (64 * warp + 63) / cs.tile_w);
+  // the rows this warp's pixels cover
+  const float wy0 = (float)(ty0 + (TileLanes<PX>::WARP_PIXELS * warp) / cs.tile_w);
+  const float wy1 =
+      (float)(ty0 + (TileLanes<PX>::WARP_PIXELS * (warp + 1) - 1) / cs.tile_w);
+  const int li0 = PX * (int)threadIdx.x;
+  const int px0 = tx0 + li0 % cs.tile_w, py = ty0 + li0 / cs.tile_w;
+  const float fy = (float)py;
+  const float amax = a.alpha_max, tmin = a.t_min, l2amin = a.log2_alpha_min;
 
-  FwdPix ps[2];
-  bool inside[2];
-  int pxs[2], pys[2];
+  float T[PX], c0[PX], c1[PX], c2[PX], best[PX];
+  int dom[PX], ncon[PX], last[PX];
+  bool done[PX];
+  bool all_done = true;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int li = 2 * (int)threadIdx.x + h;
-    pxs[h] = tx0 + li % cs.tile_w;
-    pys[h] = ty0 + li / cs.tile_w;
-    inside[h] = pxs[h] < W && pys[h] < H;
-    FwdPix& s = ps[h];
-    s.T = 1.f;
-    s.c0 = s.c1 = s.c2 = 0.f;
-    s.best = -1.f;
-    s.fx = (float)pxs[h];
-    s.fy = (float)pys[h];
-    s.dom = -1;
-    s.ncon = 0;
-    s.last = 0;
-    s.done = !inside[h];
+  for (int h = 0; h < PX; ++h) {
+    T[h] = 1.f;
+    c0[h] = c1[h] = c2[h] = 0.f;
+    best[h] = 0.f;  // every blended weight T alpha is > 0
+    dom[h] = -1;
+    ncon[h] = 0;
+    last[h] = 0;
+    done[h] = !(px0 + h < W && py < H);
+    all_done = all_done && done[h];
   }
   for (int b0 = 0; b0 < count; b0 += STAGE) {
-    if (__syncthreads_count(ps[0].done && ps[1].done) == RENDER_THREADS) break;
-    for (int j = (int)threadIdx.x; j < STAGE && b0 + j < count; j += RENDER_THREADS) {
+    if (__syncthreads_count(all_done) == NT) break;
+    for (int j = (int)threadIdx.x; j < STAGE && b0 + j < count; j += NT) {
       int id = a.inst[range.x + b0 + j];
       long long r = rec_base + id;
       Staged g = stage_gaussian(a.xyod[r], a.conic[r], a.rgb[r], id, a.alpha_min);
@@ -109,33 +86,52 @@ __global__ void __launch_bounds__(RENDER_THREADS) render_kernel(RenderArgs a, Ca
       s_y[j] = g.y;
     }
     __syncthreads();
-    if (!(ps[0].done && ps[1].done)) {
-      const int cnt = min(STAGE, count - b0);
-      for (int k = 0; k < cnt; ++k) {
-        const float2 yr = s_y[k];
-        if (yr.y < wy0 || yr.x > wy1) continue;  // warp-uniform: no row of this warp reached
-        Staged g;
-        g.g0 = s_g0[k];
-        g.g1 = s_g1[k];
-        g.g2 = s_g2[k];
-        fwd_step(ps[0], b0 + k, g, a.alpha_max, a.t_min, a.log2_alpha_min);
-        fwd_step(ps[1], b0 + k, g, a.alpha_max, a.t_min, a.log2_alpha_min);
-        if (ps[0].done && ps[1].done) break;
+    if (__all_sync(0xffffffffu, all_done)) continue;
+    const int cnt = min(STAGE, count - b0);
+    for (int k = 0; k < cnt; ++k) {
+      const float2 yr = s_y[k];
+      if (yr.y < wy0 || yr.x > wy1) continue;  // warp-uniform: no row of this warp reached
+      const float4 g0 = s_g0[k], g1 = s_g1[k], g2 = s_g2[k];
+      const RowQ rq = row_q(g0, g1, fy);
+      const int id = __float_as_int(g2.y);
+      all_done = true;
+#pragma unroll
+      for (int h = 0; h < PX; ++h) {
+        float dx;
+        const float q = pix_q(g0, rq, (float)(px0 + h), &dx);
+        const bool live = !done[h] && q >= l2amin;
+        const float al = fminf(amax, ex2_approx(q));
+        const float test = T[h] * (1.f - al);
+        const bool stop = live && test < tmin;  // stop before blending (T would drop below t_min)
+        const bool blend = live && !stop;
+        done[h] = done[h] || stop;
+        const float w = blend ? T[h] * al : 0.f;
+        c0[h] = fmaf(w, g1.z, c0[h]);
+        c1[h] = fmaf(w, g1.w, c1[h]);
+        c2[h] = fmaf(w, g2.x, c2[h]);
+        if (w > best[h]) {  // strict: the earliest of equal weights wins
+          best[h] = w;
+          dom[h] = id;
+        }
+        T[h] = blend ? test : T[h];
+        ncon[h] += blend ? 1 : 0;
+        last[h] = blend ? b0 + k + 1 : last[h];
+        all_done = all_done && done[h];
       }
+      if (__all_sync(0xffffffffu, all_done)) break;
     }
   }
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    if (!inside[h]) continue;
-    const FwdPix& s = ps[h];
-    long long p = cs.pix_base[v] + (long long)pys[h] * W + pxs[h];
-    a.out_rgb[3 * p + 0] = s.c0 + s.T * a.bg[0];
-    a.out_rgb[3 * p + 1] = s.c1 + s.T * a.bg[1];
-    a.out_rgb[3 * p + 2] = s.c2 + s.T * a.bg[2];
-    a.out_T[p] = s.T;
-    a.out_n[p] = s.ncon;
-    a.out_last[p] = s.last;
-    a.out_dom[p] = s.dom;
+  for (int h = 0; h < PX; ++h) {
+    if (!(px0 + h < W && py < H)) continue;
+    long long p = cs.pix_base[v] + (long long)py * W + px0 + h;
+    a.out_rgb[3 * p + 0] = c0[h] + T[h] * a.bg[0];
+    a.out_rgb[3 * p + 1] = c1[h] + T[h] * a.bg[1];
+    a.out_rgb[3 * p + 2] = c2[h] + T[h] * a.bg[2];
+    a.out_T[p] = T[h];
+    a.out_n[p] = ncon[h];
+    a.out_last[p] = last[h];
+    a.out_dom[p] = dom[h];
   }
 }
 
@@ -172,7 +168,8 @@ extern "C" ADP_API int adp_render(int64_t n, const adp_projected* pr, const adp_
   a.out_last = out->last;
   a.out_dom = out->dominant;
   int n_tiles = cs.tile_base[n_views];
-  render_kernel<<<n_tiles, RENDER_THREADS, 0, (cudaStream_t)stream>>>(a, cs);
+  render_kernel<RENDER_PX>
+      <<<n_tiles, TileLanes<RENDER_PX>::THREADS, 0, (cudaStream_t)stream>>>(a, cs);
   ADP_LAUNCH_CHECK();
   return ADP_OK;
 }
