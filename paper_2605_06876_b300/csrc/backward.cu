@@ -227,10 +227,13 @@ struct BwdGaussArgs {
   float* g_sh;
 };
 
-// Chain rule of one visible Gaussian, summed over views.
+// Chain rule of one visible Gaussian, summed over views. The SH degree is a
+// template parameter so that every SH array index is a constant and the arrays
+// stay in registers.
+template <int DEG>
 __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
-  const int K = sh_coeffs(a.deg);
-  const int planes = sh_planes(a.deg);
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int planes = (3 * K + 3) / 4;
   float4 ml = a.mean_logit[i], ls = a.logscale[i], q4 = a.quat[i];
   float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
   float iq = rsqrtf(qn2);
@@ -246,7 +249,8 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
                      Rg.m[3 * r + 2] * Rg.m[3 * c + 2] * s[2] * s[2];
   float gmu[3] = {0.f, 0.f, 0.f}, glogit = 0.f;
   float G3[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma3 over views
-  float gsh[48];
+  float gsh[3 * K];
+#pragma unroll
   for (int f = 0; f < 3 * K; ++f) gsh[f] = 0.f;
   for (int v = 0; v < cs.n_views; ++v) {
     long long rec = (long long)v * a.n + i;
@@ -272,22 +276,37 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
     float il = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     float u[3] = {d[0] * il, d[1] * il, d[2] * il};
     float Y[16];
-    float3 dY[16];
-    sh_eval_basis(a.deg, u[0], u[1], u[2], Y);
+    sh_eval_basis(DEG, u[0], u[1], u[2], Y);
+    float shc[4 * planes];  // this Gaussian's SH coefficients
+#pragma unroll
+    for (int p = 0; p < planes; ++p) {
+      const float4 c4 = reinterpret_cast<const float4*>(a.sh)[(long long)p * a.n + i];
+      shc[4 * p] = c4.x;
+      shc[4 * p + 1] = c4.y;
+      shc[4 * p + 2] = c4.z;
+      shc[4 * p + 3] = c4.w;
+    }
     float col[3] = {0.5f, 0.5f, 0.5f};
-    for (int f = 0; f < 3 * K; ++f) col[f % 3] += sh_coef(a.sh, a.n, i, f) * Y[f / 3];
+#pragma unroll
+    for (int f = 0; f < 3 * K; ++f) col[f % 3] += shc[f] * Y[f / 3];
+#pragma unroll
     for (int ch = 0; ch < 3; ++ch)
       if (col[ch] < 0.f) gcol[ch] = 0.f;
     float gu[3] = {0.f, 0.f, 0.f};
-    if (a.deg > 0) sh_eval_basis_grad(a.deg, u[0], u[1], u[2], dY);
-    for (int f = 0; f < 3 * K; ++f) {
-      float gc = gcol[f % 3];
-      gsh[f] += gc * Y[f / 3];
-      if (a.deg > 0) {
-        float cf = sh_coef(a.sh, a.n, i, f) * gc;
-        gu[0] += cf * dY[f / 3].x;
-        gu[1] += cf * dY[f / 3].y;
-        gu[2] += cf * dY[f / 3].z;
+    float3 dY[16];
+    if (DEG > 0) sh_eval_basis_grad(DEG, u[0], u[1], u[2], dY);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      float wj = 0.f;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        gsh[3 * j + ch] += gcol[ch] * Y[j];
+        wj += shc[3 * j + ch] * gcol[ch];
+      }
+      if (DEG > 0) {
+        gu[0] += wj * dY[j].x;
+        gu[1] += wj * dY[j].y;
+        gu[2] += wj * dY[j].z;
       }
     }
     float ud = gu[0] * u[0] + gu[1] * u[1] + gu[2] * u[2];
@@ -387,8 +406,10 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
   a.g_ls[i] = make_float4(gls[0], gls[1], gls[2], 0.f);
   a.g_q[i] = make_float4((gw - dotq * qw) * iq, (gx - dotq * qx) * iq, (gy - dotq * qy) * iq,
                          (gz - dotq * qz) * iq);
+#pragma unroll
   for (int p = 0; p < planes; ++p) {
     float v4[4];
+#pragma unroll
     for (int l = 0; l < 4; ++l) {
       int f = 4 * p + l;
       v4[l] = f < 3 * K ? gsh[f] : 0.f;
@@ -433,11 +454,12 @@ __global__ void __launch_bounds__(256) bwd_visible_kernel(const int* tiles, long
   }
 }
 
+template <int DEG>
 __global__ void __launch_bounds__(128) bwd_gauss_kernel(BwdGaussArgs a, CamSet cs,
                                                         const int* list,
                                                         const unsigned long long* n_list) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t < (long long)*n_list) bwd_one(a, cs, list[t]);
+  if (t < (long long)*n_list) bwd_one<DEG>(a, cs, list[t]);
 }
 
 }  // namespace adp
@@ -512,7 +534,13 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   bwd_visible_kernel<<<grid_for(g->n, 256, 148 * 16), 256, 0, st>>>(
       pr->tiles_touched, g->n, n_views, sh_planes(g->sh_degree), ga.g_ml, ga.g_ls, ga.g_q,
       reinterpret_cast<float4*>(grad->sh), list, n_list);
-  bwd_gauss_kernel<<<grid_for(g->n, 128), 128, 0, st>>>(ga, cs, list, n_list);
+  const unsigned gb = grid_for(g->n, 128);
+  switch (g->sh_degree) {
+    case 0: bwd_gauss_kernel<0><<<gb, 128, 0, st>>>(ga, cs, list, n_list); break;
+    case 1: bwd_gauss_kernel<1><<<gb, 128, 0, st>>>(ga, cs, list, n_list); break;
+    case 2: bwd_gauss_kernel<2><<<gb, 128, 0, st>>>(ga, cs, list, n_list); break;
+    default: bwd_gauss_kernel<3><<<gb, 128, 0, st>>>(ga, cs, list, n_list); break;
+  }
   ADP_LAUNCH_CHECK();
   return ADP_OK;
 }

@@ -21,7 +21,9 @@ struct ProjectArgs {
   int* tiles;
 };
 
-// Full projection of Gaussian i into view v; writes its record.
+// Full projection of Gaussian i into view v; writes its record. The SH degree
+// is a template parameter so that the SH arrays stay in registers.
+template <int DEG>
 __device__ void project_one(const ProjectArgs& a, const CamSet& cs, long long i, int v) {
   const adp_camera& cam = cs.cam[v];
   long long rec = (long long)v * a.n + i;
@@ -96,10 +98,11 @@ __device__ void project_one(const ProjectArgs& a, const CamSet& cs, long long i,
         float dx = ml.x - ccx, dy = ml.y - ccy, dz = ml.z - ccz;
         float il = rsqrtf(dx * dx + dy * dy + dz * dz);
         float Y[16];
-        sh_eval_basis(a.deg, dx * il, dy * il, dz * il, Y);
-        int K = sh_coeffs(a.deg);
+        sh_eval_basis(DEG, dx * il, dy * il, dz * il, Y);
+        constexpr int K = (DEG + 1) * (DEG + 1);
         float col[3] = {0.5f, 0.5f, 0.5f};
-        int P = sh_planes(a.deg);
+        constexpr int P = (3 * K + 3) / 4;
+#pragma unroll
         for (int p = 0; p < P; ++p) {
           float4 c4 = reinterpret_cast<const float4*>(a.sh)[(long long)p * a.n + i];
           float cv[4] = {c4.x, c4.y, c4.z, c4.w};
@@ -156,6 +159,7 @@ constexpr int PROJ_CHUNK = 1024;
 // Each CTA takes PROJ_CHUNK Gaussians of one view: a cheap pass culls most of
 // them, the survivors are compacted in shared memory and projected by full
 // warps, so the expensive EWA and SH work is not diluted by culled lanes.
+template <int DEG>
 __global__ void __launch_bounds__(PROJ_THREADS) project_kernel(ProjectArgs a, CamSet cs) {
   __shared__ int s_list[PROJ_CHUNK];
   __shared__ int s_cnt;
@@ -177,7 +181,7 @@ __global__ void __launch_bounds__(PROJ_THREADS) project_kernel(ProjectArgs a, Ca
     }
     __syncthreads();
     const int cnt = s_cnt;
-    for (int q = threadIdx.x; q < cnt; q += PROJ_THREADS) project_one(a, cs, c0 + s_list[q], v);
+    for (int q = threadIdx.x; q < cnt; q += PROJ_THREADS) project_one<DEG>(a, cs, c0 + s_list[q], v);
     __syncthreads();
   }
 }
@@ -220,7 +224,13 @@ extern "C" ADP_API int adp_project(const adp_gaussians* g, const adp_camera* cam
   a.rect = reinterpret_cast<int4*>(out->rect);
   a.tiles = out->tiles_touched;
   dim3 grid((unsigned)((g->n + PROJ_CHUNK - 1) / PROJ_CHUNK), n_views);
-  project_kernel<<<grid, PROJ_THREADS, 0, (cudaStream_t)stream>>>(a, cs);
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (g->sh_degree) {
+    case 0: project_kernel<0><<<grid, PROJ_THREADS, 0, st>>>(a, cs); break;
+    case 1: project_kernel<1><<<grid, PROJ_THREADS, 0, st>>>(a, cs); break;
+    case 2: project_kernel<2><<<grid, PROJ_THREADS, 0, st>>>(a, cs); break;
+    default: project_kernel<3><<<grid, PROJ_THREADS, 0, st>>>(a, cs); break;
+  }
   ADP_LAUNCH_CHECK();
   return ADP_OK;
 }
