@@ -113,7 +113,7 @@ FLOP_BLEND_FWD = 12
 FLOP_BLEND_BWD = 56
 
 
-def stage_bytes(n, n_vis, K, P, n_tiles, sh_planes, regions, k):
+def stage_bytes(n, n_vis, K, P, n_tiles, sh_planes, regions, k, kept, appended):
     """Algorithmic DRAM bytes of each stage for one step (each input read once, each
     output written once; see the design doc for the per-unit figures)."""
     gbytes = 16 * (3 + sh_planes)  # one Gaussian's parameters (float4 planes)
@@ -126,9 +126,13 @@ def stage_bytes(n, n_vis, K, P, n_tiles, sh_planes, regions, k):
         "error_regions": P * (1 + 4 + 1 + 4 + 4 + 4 + 4) + regions * 160,
         "render_backward": (n_tiles * 8 + K * 4 + n_vis * 48 + P * (12 + 12 + 4 + 4) +
                             n_vis * 48 * 2 + n * gbytes * 2 + n * 4),
+        # Adam: read parameter, gradient, m, v; write parameter, m, v
         "adam": n * gbytes * 7,
+        "adam_rows": k * gbytes * 7,
         "split_plan": regions * 300 + n * 12 + k * 16,
-        "split_apply": (n + regions) * gbytes * 3 * 2,
+        # compaction with the fused Adam step: kept rows as in Adam, the parents
+        # read, appended rows written with zero moments, the row maps read
+        "split_apply": kept * gbytes * 7 + k * gbytes + appended * gbytes * 3 + n * 16,
     }
 
 
@@ -260,8 +264,10 @@ def run_ours(args, rank, world, local_rank):
     n_vis = int((stepper.pr.tiles > 0).sum().item())
     K = int(stepper.bins.n_inst.item())
     R = int(stepper.regions.count.item())
+    st_ = last_plan.status.long()
+    appended = int(((st_ == 1) * (1 + last_plan.n_children.long()) + (st_ == 2) * 2).sum().item())
     sb = stage_bytes(n, n_vis, K, stepper.P, stepper.bins.ranges.shape[0], ops.sh_planes(3), R,
-                     stepper.k)
+                     stepper.k, new_n - appended, appended)
     per_stage = {k: v / stage_steps for k, v in stage_ms.items()}
     dom = max(per_stage, key=per_stage.get)
     peak, peak_kind, peaks = _peaks()

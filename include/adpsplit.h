@@ -281,6 +281,27 @@ ADP_API int adp_split_apply(const adp_gaussians* g, const adp_gaussians* m_in,
                             const int32_t* n_children, const float* noise, const adp_params* prm,
                             adp_gaussians* out, adp_gaussians* m_out, adp_gaussians* v_out,
                             void* ws, size_t ws_bytes, adp_stream_t stream);
+/* The compaction with the step's Adam update fused into it (one pass over the
+ * parameters and moments instead of two). Equivalent, bit for bit, to
+ * adp_adam_step on every row of g followed by adp_split_plan and
+ * adp_split_apply, provided the candidate rows got their step first from
+ * adp_adam_step_rows (the plan reads the candidates' updated parameters): each
+ * kept non-candidate row is read with its gradient grad (same layout as g) and
+ * moments, updated, and written to its new row; RESET candidates are copied as
+ * they are; appended rows are as in adp_split_apply. m_in, v_in, m_out and v_out
+ * are required. step, d_step, lr, beta1, beta2, eps as in adp_adam_step; the
+ * call advances *d_step after the compaction. If the planned size exceeds
+ * out->n nothing is written and the non-candidate rows keep their old state (a
+ * caller that sizes out for n + n_cand * (n_max + 1) never meets this). */
+ADP_API int adp_split_apply_adam(const adp_gaussians* g, const adp_gaussians* grad,
+                                 const adp_gaussians* m_in, const adp_gaussians* v_in,
+                                 const adp_regions* regs, const int32_t* candidates,
+                                 int64_t n_cand, const uint8_t* status,
+                                 const int32_t* n_children, const float* noise,
+                                 const adp_params* prm, int32_t step, int32_t* d_step,
+                                 const float* lr, float beta1, float beta2, float eps,
+                                 adp_gaussians* out, adp_gaussians* m_out, adp_gaussians* v_out,
+                                 void* ws, size_t ws_bytes, adp_stream_t stream);
 
 /* --- Render backward. -------------------------------------------------------
  * Gradient of L = sum over views of the mean L1 error |I^ - I_gt| over pixels
@@ -305,6 +326,14 @@ ADP_API int adp_render_backward(const adp_gaussians* g, const adp_projected* pr,
 ADP_API int adp_adam_step(adp_gaussians* param, const adp_gaussians* grad, adp_gaussians* m,
                           adp_gaussians* v, int32_t step, int32_t* d_step, const float* lr,
                           float beta1, float beta2, float eps, adp_stream_t stream);
+/* The same update on the listed rows only (device int32 ids in [0, n), no
+ * repeats), e.g. the split candidates before adp_split_plan when the
+ * compaction applies the step to the other rows (adp_split_apply_adam).
+ * Reads *d_step (if non-NULL) but does not advance it. */
+ADP_API int adp_adam_step_rows(adp_gaussians* param, const adp_gaussians* grad, adp_gaussians* m,
+                               adp_gaussians* v, const int32_t* rows, int64_t n_rows,
+                               int32_t step, const int32_t* d_step, const float* lr, float beta1,
+                               float beta2, float eps, adp_stream_t stream);
 
 #ifdef __cplusplus
 }

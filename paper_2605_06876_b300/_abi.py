@@ -94,6 +94,11 @@ _PROTOS = {
                                   P(AdpRegions), _vp, _i64, _vp, _vp, _vp, P(AdpParams),
                                   P(AdpGaussians), P(AdpGaussians), P(AdpGaussians), _vp,
                                   C.c_size_t, _vp]),
+    "adp_split_apply_adam": (C.c_int, [P(AdpGaussians), P(AdpGaussians), P(AdpGaussians),
+                                       P(AdpGaussians), P(AdpRegions), _vp, _i64, _vp, _vp, _vp,
+                                       P(AdpParams), _i32, _vp, P(C.c_float), C.c_float,
+                                       C.c_float, C.c_float, P(AdpGaussians), P(AdpGaussians),
+                                       P(AdpGaussians), _vp, C.c_size_t, _vp]),
     "adp_render_backward_workspace_size": (C.c_size_t, [_i64, _i32]),
     "adp_render_backward": (C.c_int, [P(AdpGaussians), P(AdpProjected), P(AdpBins), P(AdpImage),
                                       _vp, _vp, P(AdpCamera), _i32, P(C.c_float), P(AdpParams),
@@ -101,6 +106,9 @@ _PROTOS = {
     "adp_adam_step": (C.c_int, [P(AdpGaussians), P(AdpGaussians), P(AdpGaussians),
                                 P(AdpGaussians), _i32, _vp, P(C.c_float), C.c_float, C.c_float,
                                 C.c_float, _vp]),
+    "adp_adam_step_rows": (C.c_int, [P(AdpGaussians), P(AdpGaussians), P(AdpGaussians),
+                                     P(AdpGaussians), _vp, _i64, _i32, _vp, P(C.c_float),
+                                     C.c_float, C.c_float, C.c_float, _vp]),
 }
 
 _lib = None

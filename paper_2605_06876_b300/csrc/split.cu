@@ -12,6 +12,7 @@
 // of its appended block. This stage is small next to rendering, so it runs in
 // FP64, which keeps every integer outcome (statuses, child counts) stable.
 // Apply: gathers kept Gaussians (with Adam moments) and writes appended ones.
+#include "adam.cuh"
 #include "gauss_math.cuh"
 
 namespace adp {
@@ -566,6 +567,8 @@ static inline GaussPtrs gp_of(const adp_gaussians* g) {
 
 struct ApplyArgs {
   GaussPtrs in, min_, vin, out, mout, vout;
+  GaussPtrs grad;  // with the fused Adam step: the gradients of in
+  AdamHyper adam;
   const long long* counters;  // [1] kept, [3] new size
   bool has_m_in, has_v_in, has_m_out, has_v_out;
   int planes;
@@ -590,24 +593,42 @@ __device__ __forceinline__ void zero_gauss(const GaussPtrs& d, long long j, int 
   for (int p = 0; p < planes; ++p) d.sh[(long long)p * d.n + j] = z;
 }
 
+__device__ __forceinline__ float4* plane_of(const GaussPtrs& g, int q, long long i) {
+  return q == 0 ? g.ml + i : q == 1 ? g.ls + i : q == 2 ? g.q + i : g.sh + (long long)(q - 3) * g.n + i;
+}
+
+// Kept rows: one thread per (row, plane), blockIdx.y the plane (0 mean+logit,
+// 1 log-scale, 2 quaternion, 3.. SH), so a block streams one plane of the
+// parameters, moments (and gradients) and the row maps stay in L2 across planes.
+// With ADAM, each kept non-candidate row gets the update adp_adam_step makes,
+// bit for bit (candidates got theirs before the plan); moments in and out are
+// then required.
+template <bool ADAM>
 __global__ void apply_keep_kernel(ApplyArgs a) {
-  if (a.counters[3] > a.out.n) return;  // the new population does not fit: write nothing
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.in.n;
-       i += (long long)gridDim.x * blockDim.x) {
-    int c = a.cand_of[i];
-    if (c >= 0 && a.status[c] != ADP_RESET) continue;
-    long long j = a.keep_new[i];
-    if (j >= a.out.n) continue;
-    copy_gauss(a.in, i, a.out, j, a.planes);
-    if (a.has_m_out) {
-      if (a.has_m_in) copy_gauss(a.min_, i, a.mout, j, a.planes);
-      else zero_gauss(a.mout, j, a.planes);
-    }
-    if (a.has_v_out) {
-      if (a.has_v_in) copy_gauss(a.vin, i, a.vout, j, a.planes);
-      else zero_gauss(a.vout, j, a.planes);
-    }
+  const int q = blockIdx.y;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= a.in.n) return;
+  // every load of the row first (the maps and the streams are independent), so a
+  // thread waits for one memory latency; removed candidate rows are read in vain
+  const long long n_new = a.counters[3];
+  const int c = a.cand_of[i];
+  const long long j = a.keep_new[i];
+  float4 p = *plane_of(a.in, q, i);
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 m = a.has_m_in ? *plane_of(a.min_, q, i) : z;
+  float4 v = a.has_v_in ? *plane_of(a.vin, q, i) : z;
+  float4 g = ADAM ? *plane_of(a.grad, q, i) : z;
+  if (n_new > a.out.n) return;  // the new population does not fit: write nothing
+  if (c >= 0 && a.status[c] != ADP_RESET) return;
+  if (j >= a.out.n) return;
+  if (ADAM && c < 0) {  // candidates got their step before the plan
+    float lr4[4];
+    adam_plane_lr(a.adam, q, lr4);
+    adam_vec4(p, g, m, v, lr4, a.adam, adam_bias(a.adam));
   }
+  *plane_of(a.out, q, j) = p;
+  if (a.has_m_out) *plane_of(a.mout, q, j) = m;
+  if (a.has_v_out) *plane_of(a.vout, q, j) = v;
 }
 
 struct AppendArgs {
@@ -626,60 +647,61 @@ struct AppendArgs {
   double eta;
 };
 
+// Appended rows: one thread per new row. Its candidate is the last one whose
+// block starts at or before it (binary search over the block offsets); the row
+// is the parent copy (opacity o / (N + 1)) or child k - 1 of an ADAPTIVE
+// candidate, or vanilla child k of a FALLBACK one (mu + R (s * noise), s/(2 eta));
+// every appended row gets zero moments.
 __global__ void apply_append_kernel(AppendArgs a) {
   if (a.counters[3] > a.out.n) return;  // the new population does not fit: write nothing
-  long long n_keep = a.counters[1];
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.nc;
-       c += (long long)gridDim.x * blockDim.x) {
-    uint8_t stt = a.status[c];
-    if (stt == ADP_RESET) continue;
-    int i = a.cand[c];
-    long long o = n_keep + a.app_off[c];
-    float4 ml = a.in.ml[i], ls = a.in.ls[i], q = a.in.q[i];
-    int nout = stt == ADP_ADAPTIVE ? 1 + a.n_children[c] : 2;
-    if (o + nout > a.out.n) continue;
+  const long long n_keep = a.counters[1], n_app = a.counters[2];
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n_app;
+       r += (long long)gridDim.x * blockDim.x) {
+    long long lo = 0, hi = a.nc - 1;  // largest c with app_off[c] <= r
+    while (lo < hi) {
+      const long long mid = (lo + hi + 1) >> 1;
+      if (a.app_off[mid] <= r) lo = mid;
+      else hi = mid - 1;
+    }
+    const long long c = lo;
+    const int k = (int)(r - a.app_off[c]);
+    const int i = a.cand[c];
+    const long long j = n_keep + r;
+    const uint8_t stt = a.status[c];
+    const float4 ml = a.in.ml[i], ls = a.in.ls[i], q = a.in.q[i];
     if (stt == ADP_FALLBACK) {
       double Rp[9];
       quat_rot_d(q, Rp);
-      double sp[3] = {exp((double)ls.x), exp((double)ls.y), exp((double)ls.z)};
-      double shrink = log(2.0 * a.eta);
-      for (int ch = 0; ch < 2; ++ch) {
-        const float* z = a.noise + 6 * c + 3 * ch;
-        double dl[3] = {sp[0] * z[0], sp[1] * z[1], sp[2] * z[2]};
-        double m[3];
-        for (int r = 0; r < 3; ++r)
-          m[r] = (double)(r == 0 ? ml.x : (r == 1 ? ml.y : ml.z)) + Rp[3 * r] * dl[0] +
-                 Rp[3 * r + 1] * dl[1] + Rp[3 * r + 2] * dl[2];
-        long long j = o + ch;
-        copy_gauss(a.in, i, a.out, j, a.planes);
-        a.out.ml[j] = make_float4((float)m[0], (float)m[1], (float)m[2], ml.w);
-        a.out.ls[j] = make_float4((float)((double)ls.x - shrink), (float)((double)ls.y - shrink),
-                                  (float)((double)ls.z - shrink), ls.w);
-      }
+      const double sp[3] = {exp((double)ls.x), exp((double)ls.y), exp((double)ls.z)};
+      const double shrink = log(2.0 * a.eta);
+      const float* z = a.noise + 6 * c + 3 * k;
+      const double dl[3] = {sp[0] * z[0], sp[1] * z[1], sp[2] * z[2]};
+      double m[3];
+      for (int rr = 0; rr < 3; ++rr)
+        m[rr] = (double)(rr == 0 ? ml.x : (rr == 1 ? ml.y : ml.z)) + Rp[3 * rr] * dl[0] +
+                Rp[3 * rr + 1] * dl[1] + Rp[3 * rr + 2] * dl[2];
+      copy_gauss(a.in, i, a.out, j, a.planes);
+      a.out.ml[j] = make_float4((float)m[0], (float)m[1], (float)m[2], ml.w);
+      a.out.ls[j] = make_float4((float)((double)ls.x - shrink), (float)((double)ls.y - shrink),
+                                (float)((double)ls.z - shrink), ls.w);
+    } else if (k == 0) {  // parent copy: opacity o / (N + 1), everything else unchanged
+      const int N = a.n_children[c];
+      const double op = 1.0 / (1.0 + exp(-(double)ml.w));
+      const double on = op / (double)(N + 1);
+      copy_gauss(a.in, i, a.out, j, a.planes);
+      a.out.ml[j] = make_float4(ml.x, ml.y, ml.z, (float)log(on / (1.0 - on)));
     } else {
-      int N = a.n_children[c];
-      // parent copy: opacity o / (N + 1), everything else unchanged
-      double op = 1.0 / (1.0 + exp(-(double)ml.w));
-      double on = op / (double)(N + 1);
-      copy_gauss(a.in, i, a.out, o, a.planes);
-      a.out.ml[o] = make_float4(ml.x, ml.y, ml.z, (float)log(on / (1.0 - on)));
-      int s0 = a.seg[c].x;
-      for (int k = 0; k < N; ++k) {
-        long long j = o + 1 + k;
-        const float4* kid = a.kids + 4LL * (s0 + k);
-        float4 km = kid[0], kq = kid[1], kl = kid[2], kd = kid[3];
-        a.out.ml[j] = make_float4(km.x, km.y, km.z, ml.w);
-        a.out.ls[j] = make_float4(kl.x, kl.y, kl.z, 0.f);
-        a.out.q[j] = kq;
-        for (int p = 0; p < a.planes; ++p)
-          a.out.sh[(long long)p * a.out.n + j] = make_float4(0.f, 0.f, 0.f, 0.f);
-        a.out.sh[j] = make_float4(kd.x, kd.y, kd.z, 0.f);
-      }
+      const float4* kid = a.kids + 4LL * (a.seg[c].x + k - 1);
+      const float4 km = kid[0], kq = kid[1], kl = kid[2], kd = kid[3];
+      a.out.ml[j] = make_float4(km.x, km.y, km.z, ml.w);
+      a.out.ls[j] = make_float4(kl.x, kl.y, kl.z, 0.f);
+      a.out.q[j] = kq;
+      a.out.sh[j] = make_float4(kd.x, kd.y, kd.z, 0.f);
+      for (int p = 1; p < a.planes; ++p)
+        a.out.sh[(long long)p * a.out.n + j] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    for (long long j = o; j < o + nout; ++j) {
-      if (a.has_m_out) zero_gauss(a.mout, j, a.planes);
-      if (a.has_v_out) zero_gauss(a.vout, j, a.planes);
-    }
+    if (a.has_m_out) zero_gauss(a.mout, j, a.planes);
+    if (a.has_v_out) zero_gauss(a.vout, j, a.planes);
   }
 }
 
@@ -814,14 +836,13 @@ extern "C" ADP_API int adp_split_plan(const adp_gaussians* g, const adp_camera* 
   return ADP_OK;
 }
 
-extern "C" ADP_API int adp_split_apply(const adp_gaussians* g, const adp_gaussians* m_in,
-                                       const adp_gaussians* v_in, const adp_regions* regs,
-                                       const int32_t* candidates, int64_t n_cand,
-                                       const uint8_t* status, const int32_t* n_children,
-                                       const float* noise, const adp_params* prm,
-                                       adp_gaussians* out, adp_gaussians* m_out,
-                                       adp_gaussians* v_out, void* ws, size_t ws_bytes,
-                                       adp_stream_t stream) {
+static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
+                            const AdamHyper* adam, const adp_gaussians* m_in,
+                            const adp_gaussians* v_in, const adp_regions* regs,
+                            const int32_t* candidates, int64_t n_cand, const uint8_t* status,
+                            const int32_t* n_children, const float* noise, const adp_params* prm,
+                            adp_gaussians* out, adp_gaussians* m_out, adp_gaussians* v_out,
+                            void* ws, size_t ws_bytes, cudaStream_t st) {
   ADP_CHECK_ARG(g && out && regs && prm, "NULL argument");
   ADP_CHECK_ARG(gauss_ok(g) || g->n == 0, "bad input Gaussian arrays");
   ADP_CHECK_ARG(gauss_ok(out) || out->n == 0, "bad output Gaussian arrays");
@@ -832,11 +853,15 @@ extern "C" ADP_API int adp_split_apply(const adp_gaussians* g, const adp_gaussia
   ADP_CHECK_ARG(!v_in || (gauss_ok(v_in) && v_in->n == g->n), "bad v_in");
   ADP_CHECK_ARG(!m_out || (gauss_ok(m_out) && m_out->n == out->n), "bad m_out (its n must equal out->n)");
   ADP_CHECK_ARG(!v_out || (gauss_ok(v_out) && v_out->n == out->n), "bad v_out (its n must equal out->n)");
+  if (adam) {
+    ADP_CHECK_ARG(m_in && v_in && m_out && v_out, "the fused Adam step needs all four moment arrays");
+    ADP_CHECK_ARG(grad && (gauss_ok(grad) || g->n == 0) && grad->n == g->n &&
+                      grad->sh_degree == g->sh_degree, "bad grad");
+  }
   ADP_CHECK_ARG(aligned(ws, 256), "workspace must be 256-byte aligned");
   long long n = g->n, nc = n_cand, rcap = regs->capacity;
   size_t need = split_ws_bytes(n, nc, rcap);
   ADP_CHECK_ARG(ws_bytes >= need, "workspace %zu bytes, need %zu", ws_bytes, need);
-  cudaStream_t st = (cudaStream_t)stream;
   Carver c(ws, ws_bytes);
   SplitWs w = carve_split(c, n, nc, rcap);
   int planes = sh_planes(g->sh_degree);
@@ -852,12 +877,21 @@ extern "C" ADP_API int adp_split_apply(const adp_gaussians* g, const adp_gaussia
   if (v_in) aa.vin = gp_of(v_in);
   if (m_out) aa.mout = gp_of(m_out);
   if (v_out) aa.vout = gp_of(v_out);
+  if (adam) {
+    aa.grad = gp_of(grad);
+    aa.adam = *adam;
+  }
   aa.planes = planes;
   aa.cand_of = w.cand_of;
   aa.status = status;
   aa.keep_new = w.keep_new;
   aa.counters = w.counters;
-  if (n > 0) apply_keep_kernel<<<grid_for(n, 256, 148 * 16), 256, 0, st>>>(aa);
+  if (n > 0) {
+    if (adam)
+      apply_keep_kernel<true><<<dim3(grid_for(n, 256), 3 + planes), 256, 0, st>>>(aa);
+    else
+      apply_keep_kernel<false><<<dim3(grid_for(n, 256), 3 + planes), 256, 0, st>>>(aa);
+  }
   if (nc > 0) {
     AppendArgs ap;
     ap.in = gin;
@@ -877,8 +911,46 @@ extern "C" ADP_API int adp_split_apply(const adp_gaussians* g, const adp_gaussia
     ap.counters = w.counters;
     ap.noise = noise;
     ap.eta = prm->eta;
-    apply_append_kernel<<<grid_for(nc, 128, 4096), 128, 0, st>>>(ap);
+    // appended rows: at most n_cand * (n_max + 1), each with its own thread
+    apply_append_kernel<<<grid_for(nc * (long long)(prm->n_max > 1 ? prm->n_max + 1 : 2), 128,
+                                   148 * 32), 128, 0, st>>>(ap);
   }
   ADP_LAUNCH_CHECK();
+  return ADP_OK;
+}
+
+__global__ void split_step_advance_kernel(int* d_step) { *d_step += 1; }
+
+extern "C" ADP_API int adp_split_apply(const adp_gaussians* g, const adp_gaussians* m_in,
+                                       const adp_gaussians* v_in, const adp_regions* regs,
+                                       const int32_t* candidates, int64_t n_cand,
+                                       const uint8_t* status, const int32_t* n_children,
+                                       const float* noise, const adp_params* prm,
+                                       adp_gaussians* out, adp_gaussians* m_out,
+                                       adp_gaussians* v_out, void* ws, size_t ws_bytes,
+                                       adp_stream_t stream) {
+  return split_apply_impl(g, nullptr, nullptr, m_in, v_in, regs, candidates, n_cand, status,
+                          n_children, noise, prm, out, m_out, v_out, ws, ws_bytes,
+                          (cudaStream_t)stream);
+}
+
+extern "C" ADP_API int adp_split_apply_adam(
+    const adp_gaussians* g, const adp_gaussians* grad, const adp_gaussians* m_in,
+    const adp_gaussians* v_in, const adp_regions* regs, const int32_t* candidates, int64_t n_cand,
+    const uint8_t* status, const int32_t* n_children, const float* noise, const adp_params* prm,
+    int32_t step, int32_t* d_step, const float* lr, float beta1, float beta2, float eps,
+    adp_gaussians* out, adp_gaussians* m_out, adp_gaussians* v_out, void* ws, size_t ws_bytes,
+    adp_stream_t stream) {
+  ADP_CHECK_ARG(lr, "NULL lr");
+  ADP_CHECK_ARG(d_step || step >= 1, "step must be >= 1");
+  AdamHyper h = adam_hyper(lr, beta1, beta2, eps, step, d_step);
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = split_apply_impl(g, grad, &h, m_in, v_in, regs, candidates, n_cand, status, n_children,
+                            noise, prm, out, m_out, v_out, ws, ws_bytes, st);
+  if (rc) return rc;
+  if (d_step) {
+    split_step_advance_kernel<<<1, 1, 0, st>>>(d_step);
+    ADP_LAUNCH_CHECK();
+  }
   return ADP_OK;
 }

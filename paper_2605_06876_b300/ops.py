@@ -406,6 +406,28 @@ def split_apply(g: Gaussians, plan: SplitPlan, regions: Regions, candidates, noi
     return out, m_out, v_out
 
 
+def split_apply_adam(g: Gaussians, grad: Gaussians, m_in: Gaussians, v_in: Gaussians,
+                     plan: SplitPlan, regions: Regions, candidates, noise, step, out: Gaussians,
+                     m_out: Gaussians, v_out: Gaussians, params=None, lr=None, beta1=0.9,
+                     beta2=0.999, eps=1e-15, stream=None):
+    """adp_split_apply_adam: the compaction with the Adam step applied to every kept
+    non-candidate row on the way (candidates first via adam_step_rows)."""
+    params = params or A.default_params()
+    lrc = (C.c_float * 6)(*[float(x) for x in (lr or ADAM_LR)])
+    host_step, d_step = _step_arg(step)
+    nc = int(candidates.numel())
+    if noise is None:
+        noise = torch.zeros((max(nc, 1), 2, 3), dtype=F32, device=g.mean_logit.device)
+    gc, grc, mic, vic = g.c(), grad.c(), m_in.c(), v_in.c()
+    oc, moc, voc, rc = out.c(), m_out.c(), v_out.c(), regions.c()
+    A.check(A.lib().adp_split_apply_adam(
+        C.byref(gc), C.byref(grc), C.byref(mic), C.byref(vic), C.byref(rc), _p(candidates), nc,
+        _p(plan.status), _p(plan.n_children), _p(noise), C.byref(params), host_step, d_step, lrc,
+        beta1, beta2, eps, C.byref(oc), C.byref(moc), C.byref(voc), _p(plan.ws), plan.ws.numel(),
+        _stream(stream)), "adp_split_apply_adam")
+    return out, m_out, v_out
+
+
 def render_backward(g: Gaussians, pr: Projected, bins: Bins, fwd: Image, cams, target=None,
                     dL_drgb=None, bg=(0.0, 0.0, 0.0), params=None, grad: Gaussians = None, ws=None,
                     stream=None):
@@ -436,10 +458,26 @@ def adam_step(param: Gaussians, grad: Gaussians, m: Gaussians, v: Gaussians, ste
     device int32 tensor of one element holding the step number (advanced by the call)."""
     lrc = (C.c_float * 6)(*[float(x) for x in lr])
     pc, gc, mc, vc = param.c(), grad.c(), m.c(), v.c()
-    if isinstance(step, torch.Tensor):
-        host_step, d_step = 0, _p(step)
-    else:
-        host_step, d_step = int(step), None
+    host_step, d_step = _step_arg(step)
     A.check(A.lib().adp_adam_step(C.byref(pc), C.byref(gc), C.byref(mc), C.byref(vc), host_step,
                                   d_step, lrc, beta1, beta2, eps, _stream(stream)),
             "adp_adam_step")
+
+
+def adam_step_rows(param: Gaussians, grad: Gaussians, m: Gaussians, v: Gaussians, rows, step,
+                   lr=ADAM_LR, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+    """adp_adam_step_rows: the Adam step on the listed rows only (a device step
+    counter is read, not advanced)."""
+    lrc = (C.c_float * 6)(*[float(x) for x in lr])
+    pc, gc, mc, vc = param.c(), grad.c(), m.c(), v.c()
+    host_step, d_step = _step_arg(step)
+    A.check(A.lib().adp_adam_step_rows(C.byref(pc), C.byref(gc), C.byref(mc), C.byref(vc),
+                                       _p(rows), int(rows.numel()), host_step, d_step, lrc, beta1,
+                                       beta2, eps, _stream(stream)), "adp_adam_step_rows")
+
+
+def _step_arg(step):
+    """(host step, device step pointer) from an int or a one-element int32 tensor."""
+    if isinstance(step, torch.Tensor):
+        return 0, _p(step)
+    return int(step), None

@@ -59,8 +59,13 @@ class StageTimer:
 
 class PlainStep:
     def __init__(self, g: ops.Gaussians, cams, target, cand_frac=0.1, params=None,
-                 bg=(0.0, 0.0, 0.0), lr=ops.ADAM_LR, bins_margin=1.15, region_margin=1.25):
+                 bg=(0.0, 0.0, 0.0), lr=ops.ADAM_LR, bins_margin=1.15, region_margin=1.25,
+                 fused_adam=True):
         self.g = g
+        # fused_adam: the Adam step of the candidates runs before the plan and the
+        # compaction applies it to every other row while copying (one pass over
+        # parameters and moments instead of two; same result bit for bit)
+        self.fused_adam = fused_adam
         self.cams = list(cams)
         self.V = len(self.cams)
         self.target = target
@@ -131,14 +136,22 @@ class PlainStep:
         mark("render_backward")
         ops.render_backward(g, self.pr, self.bins, self.img, cams, target=self.target, bg=self.bg,
                             params=prm, grad=self.grad, ws=self.ws_bwd)
-        mark("adam")
-        ops.adam_step(g, self.grad, self.m, self.v, self.adam_t, self.lr)
+        if self.fused_adam:
+            mark("adam_rows")
+            ops.adam_step_rows(g, self.grad, self.m, self.v, self.cand, self.adam_t, self.lr)
+        else:
+            mark("adam")
+            ops.adam_step(g, self.grad, self.m, self.v, self.adam_t, self.lr)
         mark("split_plan")
         plan = ops.split_plan(g, cams, self.regions, self.cand, self.count, prm, ws=self.ws_split,
                               sync=False)
         mark("split_apply")
-        ops.split_apply(g, plan, self.regions, self.cand, noise, prm, m_in=self.m, v_in=self.v,
-                        out=self.out, m_out=self.m_out, v_out=self.v_out)
+        if self.fused_adam:
+            ops.split_apply_adam(g, self.grad, self.m, self.v, plan, self.regions, self.cand, noise,
+                                 self.adam_t, self.out, self.m_out, self.v_out, prm, self.lr)
+        else:
+            ops.split_apply(g, plan, self.regions, self.cand, noise, prm, m_in=self.m, v_in=self.v,
+                            out=self.out, m_out=self.m_out, v_out=self.v_out)
         mark("end")
         return self.out, self.m_out, self.v_out, plan
 

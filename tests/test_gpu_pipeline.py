@@ -96,3 +96,51 @@ def test_autotuner_picks_a_legal_shape_with_identical_results():
     torch.cuda.synchronize()
     assert torch.equal(ref.img.rgb, got.img.rgb) and torch.equal(ref.img.dominant, got.img.dominant)
     assert torch.equal(ref.count, got.count) and torch.equal(ref.mass, got.mass)
+
+
+def test_fused_adam_compaction_equals_adam_then_apply():
+    """Adam on the candidate rows, the plan, then the compaction that applies the
+    step to every other row while copying gives, bit for bit, the population and
+    moments of a full Adam step followed by the plain compaction (same gradient:
+    the backward's float atomics would otherwise differ in the last bits)."""
+    st, noise = _stepper(seed=37)
+    st.step(noise)  # fills the regions, candidates and counts of a real step
+    torch.cuda.synchronize()
+    gen = torch.Generator(DEV).manual_seed(5)
+    grad = st.g.zeros_like()
+    for t in grad.tensors():
+        t.normal_(0.0, 1e-2, generator=gen)
+    m0, v0 = st.g.zeros_like(), st.g.zeros_like()
+    for t in m0.tensors():
+        t.normal_(0.0, 1e-3, generator=gen)
+    for t in v0.tensors():
+        t.uniform_(0.0, 1e-4, generator=gen)
+    cap = st.out_capacity
+    res = []
+    for fused in (False, True):
+        g, m, v = st.g.clone(), m0.clone(), v0.clone()
+        d_step = torch.full((1,), 3, dtype=torch.int32, device=DEV)
+        out = [ops.Gaussians(cap, g.sh_degree, DEV, zero=True) for _ in range(3)]
+        if fused:
+            ops.adam_step_rows(g, grad, m, v, st.cand, d_step, st.lr)
+        else:
+            ops.adam_step(g, grad, m, v, d_step, st.lr)
+        plan = ops.split_plan(g, st.cams, st.regions, st.cand, st.count, st.params, sync=False)
+        if fused:
+            ops.split_apply_adam(g, grad, m, v, plan, st.regions, st.cand, noise, d_step, out[0],
+                                 out[1], out[2], st.params, st.lr)
+        else:
+            ops.split_apply(g, plan, st.regions, st.cand, noise, st.params, m_in=m, v_in=v,
+                            out=out[0], m_out=out[1], v_out=out[2])
+        torch.cuda.synchronize()
+        res.append((plan, out, int(d_step.item())))
+    (pp, op, sp), (pf, of, sf) = res
+    n_new = int(pp.d_new_n.item())
+    assert n_new == int(pf.d_new_n.item()) and n_new > st.g.n
+    assert torch.equal(pp.status, pf.status) and torch.equal(pp.n_children, pf.n_children)
+    assert sp == sf == 4
+    for a, b in zip(sum((x.tensors() for x in op), []), sum((x.tensors() for x in of), [])):
+        if a.dim() == 3:  # SH planes [planes][capacity][4]
+            assert torch.equal(a[:, :n_new], b[:, :n_new])
+        else:
+            assert torch.equal(a[:n_new], b[:n_new])
