@@ -149,7 +149,9 @@ def run_ours(args, rank, world, local_rank):
     build()
     torch.cuda.set_device(local_rank)
     dev = f"cuda:{local_rank}"
-    cfg = scenes.CONFIGS[1]
+    cfg = dict(scenes.CONFIGS[1])
+    if args.gaussians:  # a smaller scene of the same recipe, for profiler captures
+        cfg["n"], cfg["n_target"] = args.gaussians, args.gaussians * 3 // 2
     sc = scenes.scene_clusters(2, cfg["n"], cfg["sh_degree"])
     tg = scenes.scene_clusters(3, cfg["n_target"], cfg["sh_degree"])
     cams = scenes.ring_cameras(3, 1, cfg["ring_radius"], cfg["width"], cfg["height"])
@@ -304,7 +306,9 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded cluster scene; random-init Gaussians, no dataset)",
-        "config": dict(WORKLOAD, parallelism=f"replicas{world}" if world > 1 else "single"),
+        "config": dict(WORKLOAD, parallelism=f"replicas{world}" if world > 1 else "single",
+                       **({"n_gaussians": g.n, "note": "reduced scene for profiling"}
+                          if args.gaussians else {})),
         "e2e": {"value": round(1e3 / e2e_ms * world, 3), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "roofline": roof,
@@ -499,6 +503,8 @@ def main():
                     help="views of the batched-vs-plain comparison (0 or 1: skip)")
     ap.add_argument("--no-launch-count", action="store_true",
                     help="skip the CUPTI kernel count (for runs under ncu)")
+    ap.add_argument("--gaussians", type=int, default=0,
+                    help="scene size override for small profiler captures (default: 1M)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -34,8 +34,14 @@ class StageTimer:
         err, ev = rt.cudaEventCreateWithFlags(rt.cudaEventDefault)
         if err != rt.cudaError_t.cudaSuccess:
             raise RuntimeError(f"cudaEventCreateWithFlags: {err}")
-        s = (self.stream or torch.cuda.current_stream()).cuda_stream
-        (err,) = rt.cudaEventRecordWithFlags(ev, s, rt.cudaEventRecordExternal)
+        st = self.stream or torch.cuda.current_stream()
+        # an external record (a node of the graph) inside a capture, a plain one outside
+        err, cap = rt.cudaStreamIsCapturing(st.cuda_stream)
+        if err != rt.cudaError_t.cudaSuccess:
+            raise RuntimeError(f"cudaStreamIsCapturing: {err}")
+        active = cap == rt.cudaStreamCaptureStatus.cudaStreamCaptureStatusActive
+        flags = rt.cudaEventRecordExternal if active else rt.cudaEventRecordDefault
+        (err,) = rt.cudaEventRecordWithFlags(ev, st.cuda_stream, flags)
         if err != rt.cudaError_t.cudaSuccess:
             raise RuntimeError(f"cudaEventRecordWithFlags: {err}")
         self.events.append((name, ev))
