@@ -80,13 +80,25 @@ __device__ __forceinline__ float reduce_scatter8(const float* v, int* idx) {
 #ifndef ADP_BWD_PX
 #define ADP_BWD_PX 4
 #endif
+#ifndef ADP_BWD_MINB  // resident blocks per SM the register budget is sized for
+#define ADP_BWD_MINB 1
+#endif
 constexpr int BWD_PX = ADP_BWD_PX;
-constexpr int BWD_STAGE = 256;
+#ifndef ADP_BWD_STAGE
+#define ADP_BWD_STAGE 256
+#endif
+constexpr int BWD_STAGE = ADP_BWD_STAGE;
 
+// The thread's pixels are processed as PX / 2 horizontal pairs with the packed
+// two-lane FP32 instructions of sm_100+ (__ffma2_rn and friends round each lane
+// exactly like the scalar instruction, so the alpha test still agrees bit for bit
+// with the forward's); compares, selects and the special-function unit stay scalar.
 template <int PX>
-__global__ void __launch_bounds__(TileLanes<PX>::THREADS)
+__global__ void __launch_bounds__(TileLanes<PX>::THREADS, ADP_BWD_MINB)
     bwd_pixel_kernel(BwdPixArgs a, CamSet cs) {
+  static_assert(PX % 2 == 0, "pixels are processed in pairs");
   constexpr int NT = TileLanes<PX>::THREADS;
+  constexpr int NP = PX / 2;
   __shared__ float4 s_g0[BWD_STAGE];
   __shared__ float4 s_g1[BWD_STAGE];
   __shared__ float4 s_g2[BWD_STAGE];
@@ -109,38 +121,47 @@ __global__ void __launch_bounds__(TileLanes<PX>::THREADS)
   const int px0 = tx0 + li0 % cs.tile_w, py = ty0 + li0 / cs.tile_w;
   const float fy = (float)py;
   const float amax = a.alpha_max, l2amin = a.log2_alpha_min;
+  const float2 one2 = make_float2(1.f, 1.f), neg2 = make_float2(-1.f, -1.f);
 
-  // per pixel: transmittance, colour behind, dL/dpixel, last blended position
-  float T[PX], R0[PX], R1[PX], R2[PX], G0[PX], G1[PX], G2[PX];
+  // per pixel pair: transmittance, colour behind, dL/dpixel, minus the x coordinate
+  float2 T[NP], R0[NP], R1[NP], R2[NP], G0[NP], G1[NP], G2[NP], npx[NP];
   int last[PX];
   int warp_last = 0;
 #pragma unroll
-  for (int h = 0; h < PX; ++h) {
-    T[h] = 1.f;
-    R0[h] = a.bg[0];
-    R1[h] = a.bg[1];
-    R2[h] = a.bg[2];
-    G0[h] = G1[h] = G2[h] = 0.f;
-    last[h] = 0;
-    const int px = px0 + h;
-    if (px < W && py < H) {
-      long long p = cs.pix_base[v] + (long long)py * W + px;
-      T[h] = a.T_final[p];
-      last[h] = a.last[p];
-      if (a.dL_drgb) {
-        G0[h] = a.dL_drgb[3 * p];
-        G1[h] = a.dL_drgb[3 * p + 1];
-        G2[h] = a.dL_drgb[3 * p + 2];
-      } else {
-        float d0 = a.img[3 * p] - a.target[3 * p];
-        float d1 = a.img[3 * p + 1] - a.target[3 * p + 1];
-        float d2 = a.img[3 * p + 2] - a.target[3 * p + 2];
-        G0[h] = d0 > 0.f ? sc : (d0 < 0.f ? -sc : 0.f);
-        G1[h] = d1 > 0.f ? sc : (d1 < 0.f ? -sc : 0.f);
-        G2[h] = d2 > 0.f ? sc : (d2 < 0.f ? -sc : 0.f);
+  for (int j = 0; j < NP; ++j) {
+    float t[2], g[2][3];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int h = 2 * j + e, px = px0 + h;
+      t[e] = 1.f;
+      g[e][0] = g[e][1] = g[e][2] = 0.f;
+      last[h] = 0;
+      if (px < W && py < H) {
+        long long p = cs.pix_base[v] + (long long)py * W + px;
+        t[e] = a.T_final[p];
+        last[h] = a.last[p];
+        if (a.dL_drgb) {
+          g[e][0] = a.dL_drgb[3 * p];
+          g[e][1] = a.dL_drgb[3 * p + 1];
+          g[e][2] = a.dL_drgb[3 * p + 2];
+        } else {
+#pragma unroll
+          for (int ch = 0; ch < 3; ++ch) {
+            const float d = a.img[3 * p + ch] - a.target[3 * p + ch];
+            g[e][ch] = d > 0.f ? sc : (d < 0.f ? -sc : 0.f);
+          }
+        }
       }
+      warp_last = max(warp_last, last[h]);
     }
-    warp_last = max(warp_last, last[h]);
+    T[j] = make_float2(t[0], t[1]);
+    R0[j] = make_float2(a.bg[0], a.bg[0]);
+    R1[j] = make_float2(a.bg[1], a.bg[1]);
+    R2[j] = make_float2(a.bg[2], a.bg[2]);
+    G0[j] = make_float2(g[0][0], g[1][0]);
+    G1[j] = make_float2(g[0][1], g[1][1]);
+    G2[j] = make_float2(g[0][2], g[1][2]);
+    npx[j] = make_float2(-(float)(px0 + 2 * j), -(float)(px0 + 2 * j + 1));
   }
   if (threadIdx.x == 0) s_maxlast = 0;
   __syncthreads();
@@ -169,43 +190,59 @@ __global__ void __launch_bounds__(TileLanes<PX>::THREADS)
       const float4 g0 = s_g0[k], g1 = s_g1[k], g2 = s_g2[k];
       const RowQ rq = row_q(g0, g1, fy);
       const int pos = b0 + k;
-      float S = 0.f, Sx = 0.f, Sxx = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+      const float2 mx = make_float2(g0.x, g0.x), qa = make_float2(g0.z, g0.z);
+      const float2 qb = make_float2(rq.bdy, rq.bdy), qe = make_float2(rq.e, rq.e);
+      const float2 cr = make_float2(g1.z, g1.z), cg = make_float2(g1.w, g1.w);
+      const float2 cb = make_float2(g2.x, g2.x);
+      float2 S = make_float2(0.f, 0.f), Sx = S, Sxx = S, C0 = S, C1 = S, C2 = S;
       bool hit = false;
 #pragma unroll
-      for (int h = 0; h < PX; ++h) {
-        float dx;
-        const float q = pix_q(g0, rq, (float)(px0 + h), &dx);
-        const bool p = pos < last[h] && q >= l2amin;  // blended in the forward
-        hit = hit || p;
-        const float ar = ex2_approx(q);
-        const float al = p ? fminf(amax, ar) : 0.f;
-        const float Tj = T[h] * rcp_approx(1.f - al);  // transmittance before this Gaussian
-        const float d0 = g1.z - R0[h], d1 = g1.w - R1[h], d2 = g2.x - R2[h];
-        const float dal = Tj * fmaf(G0[h], d0, fmaf(G1[h], d1, G2[h] * d2));
-        const float wgt = Tj * al;
-        C0 = fmaf(wgt, G0[h], C0);
-        C1 = fmaf(wgt, G1[h], C1);
-        C2 = fmaf(wgt, G2[h], C2);
-        R0[h] = fmaf(al, d0, R0[h]);
-        R1[h] = fmaf(al, d1, R1[h]);
-        R2[h] = fmaf(al, d2, R2[h]);
-        T[h] = Tj;
-        const float kk = (p && ar <= amax) ? dal * ar : 0.f;  // zero through the clamp
-        S += kk;
-        const float t = dx * kk;
-        Sx += t;
-        Sxx = fmaf(dx, t, Sxx);
+      for (int j = 0; j < NP; ++j) {
+        // q = dx (a dx + b dy) + e, the same operations as pix_q
+        const float2 dx = __fadd2_rn(mx, npx[j]);
+        const float2 q = __ffma2_rn(dx, __ffma2_rn(qa, dx, qb), qe);
+        const bool p0 = pos < last[2 * j] && q.x >= l2amin;  // blended in the forward
+        const bool p1 = pos < last[2 * j + 1] && q.y >= l2amin;
+        hit = hit || p0 || p1;
+        const float ar0 = ex2_approx(q.x), ar1 = ex2_approx(q.y);
+        const float2 al = make_float2(p0 ? fminf(amax, ar0) : 0.f, p1 ? fminf(amax, ar1) : 0.f);
+        const float2 om = __ffma2_rn(al, neg2, one2);  // 1 - alpha
+        // transmittance before this Gaussian
+        const float2 Tj = __fmul2_rn(T[j], make_float2(rcp_approx(om.x), rcp_approx(om.y)));
+        const float2 d0 = __ffma2_rn(R0[j], neg2, cr);  // colour minus the colour behind
+        const float2 d1 = __ffma2_rn(R1[j], neg2, cg);
+        const float2 d2 = __ffma2_rn(R2[j], neg2, cb);
+        const float2 dal =
+            __fmul2_rn(Tj, __ffma2_rn(G0[j], d0, __ffma2_rn(G1[j], d1, __fmul2_rn(G2[j], d2))));
+        const float2 wgt = __fmul2_rn(Tj, al);
+        C0 = __ffma2_rn(wgt, G0[j], C0);
+        C1 = __ffma2_rn(wgt, G1[j], C1);
+        C2 = __ffma2_rn(wgt, G2[j], C2);
+        R0[j] = __ffma2_rn(al, d0, R0[j]);
+        R1[j] = __ffma2_rn(al, d1, R1[j]);
+        R2[j] = __ffma2_rn(al, d2, R2[j]);
+        T[j] = Tj;
+        // dL/dalpha * alpha, zero through the clamp (alpha = 0 where not blended)
+        float2 kk = __fmul2_rn(dal, al);
+        kk.x = ar0 <= amax ? kk.x : 0.f;
+        kk.y = ar1 <= amax ? kk.y : 0.f;
+        S = __fadd2_rn(S, kk);
+        const float2 t = __fmul2_rn(dx, kk);
+        Sx = __fadd2_rn(Sx, t);
+        Sxx = __ffma2_rn(dx, t, Sxx);
       }
       if (__ballot_sync(0xffffffffu, hit)) {
         const float dy = rq.dy;
-        float vals[8] = {S, Sx, dy * S, Sxx, dy * Sx, dy * dy * S, C0, C1};
+        const float s1 = S.x + S.y, sx = Sx.x + Sx.y;
+        float vals[8] = {s1, sx, dy * s1, Sxx.x + Sxx.y, dy * sx, dy * dy * s1, C0.x + C0.y,
+                         C1.x + C1.y};
         int idx;
         float sum = reduce_scatter8(vals, &idx);
-        float cb = warp_sum(C2);
+        float cbs = warp_sum(C2.x + C2.y);
         int id = __float_as_int(g2.y);
         float* gp = reinterpret_cast<float*>(a.g2d + 3 * (rec_base + id));
         if ((lane & 3) == 0) atomicAdd(gp + idx, sum);
-        if (lane == 0) atomicAdd(gp + 8, cb);
+        if (lane == 0) atomicAdd(gp + 8, cbs);
       }
     }
   }

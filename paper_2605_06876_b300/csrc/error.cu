@@ -3,7 +3,8 @@
 //    then the min-max normalised E, mask M and band B, decided in float32 with
 //    correctly rounded operations, and the per-Gaussian attribution (count,
 //    mass) with warp-aggregated integer atomics (mass in exact fixed point);
-//  - top-k error mass by an 8-pass radix select on the 64-bit mass keys;
+//  - top-k error mass by a radix select on the 64-bit mass keys, in one
+//    cooperative launch;
 //  - erosion (separable min filter), 8-connected labelling by a union-find whose
 //    roots are the smallest pixel index of each component (per 32x32 tile in
 //    shared memory first, then across tile borders in global memory),
@@ -147,68 +148,263 @@ static int mass_shift_for(float tau) {
 
 // ------------------------------------------------------------------ top-k
 
-struct SelectState {
-  unsigned long long prefix;  // selected high digits of the threshold key
-  unsigned long long mask;    // which bits of prefix are fixed
-  long long remaining;        // how many of the keys matching prefix to take
-  long long pad;
+// One-launch top-k: a cooperative kernel (every block resident) runs the radix
+// select and the final compaction with grid-wide barriers between the phases.
+// Each pass histograms one 8-bit digit of the keys that still match the chosen
+// high digits (block histograms in shared memory, summed in global memory), and
+// every block then picks the same digit from the summed histogram. A pass also
+// takes the smallest and largest matching key: once they are equal (for example
+// all the zero masses), the threshold key is known and the passes stop; they also
+// stop when the chosen digit holds exactly the keys still to take. The output is
+// the keys above the threshold and the first `remaining` keys equal to it in id
+// order, written in id order.
+constexpr int TOPK_THREADS = 1024;
+constexpr int TOPK_MAX_BLOCKS = 1024;  // bound of the grid (one block per SM)
+constexpr int TOPK_BARRIER_SPINS = 1 << 24;
+
+struct TopkCoop {
+  unsigned* hist;              // [8][256], zeroed before the launch
+  unsigned long long* mm;      // [8][2] min, max of the matching keys (preset by the caller)
+  unsigned* bar;               // barrier counter, zeroed before the launch
+  unsigned* err;               // set if a barrier wait gave up
+  long long* blk;              // [2][gridDim.x] per-block counts
+  uint8_t* sel;                // [n] selection flags
 };
 
-__global__ void topk_hist_kernel(const double* mass, long long n, int shift,
-                                 const SelectState* st, unsigned* hist) {
-  __shared__ unsigned s_h[256];
-  s_h[threadIdx.x] = 0;
+// Grid-wide barrier number `round` (1, 2, ...) over a counter that starts at zero.
+// Waits are bounded: on timeout the error flag is set and the block goes on.
+__device__ __forceinline__ void topk_grid_barrier(const TopkCoop& w, unsigned round) {
   __syncthreads();
-  unsigned long long pre = st->prefix, msk = st->mask;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    unsigned long long k = (unsigned long long)__double_as_longlong(mass[i]);
-    if ((k & msk) == pre) atomicAdd(&s_h[(k >> shift) & 255ull], 1u);
-  }
-  __syncthreads();
-  if (s_h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], s_h[threadIdx.x]);
-}
-
-// Picks the digit holding the remaining-th largest key: a suffix sum of the 256
-// bin counts (from the largest digit down) and the one bin where it first
-// reaches the remaining count. One block of 256 threads.
-__global__ void topk_pick_kernel(unsigned* hist, int shift, SelectState* st) {
-  __shared__ long long s_w[8];
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int b = 255 - t;  // thread t handles digit 255 - t, so prefixes run downwards
-  long long c = hist[b];
-  long long inc = c;
-  for (int o = 1; o < 32; o <<= 1) {
-    long long y = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += y;
-  }
-  if (lane == 31) s_w[w] = inc;
-  __syncthreads();
-  long long pre = 0;
-  for (int k = 0; k < w; ++k) pre += s_w[k];
-  long long suf = pre + inc;  // count of keys in digits >= b
-  __syncthreads();
-  const long long rem = st->remaining;
-  long long above = suf - c;  // keys in digits > b
-  const bool pick = suf >= rem && above < rem;  // exactly one digit satisfies this
-  __syncthreads();
-  if (pick) {
-    st->remaining = rem - above;
-    st->prefix |= (unsigned long long)b << shift;
-    st->mask |= 255ull << shift;
-  }
-  hist[b] = 0;
-}
-
-// Initial selection state (nothing fixed, k keys to take) and an empty histogram.
-__global__ void topk_reset_kernel(SelectState* st, unsigned* hist, long long k) {
   if (threadIdx.x == 0) {
-    st->prefix = 0ull;
-    st->mask = 0ull;
-    st->remaining = k;
-    st->pad = 0;
+    __threadfence();
+    atomicAdd(w.bar, 1u);
+    const unsigned target = round * gridDim.x;
+    volatile unsigned* vb = w.bar;
+    int spins = 0;
+    while (*vb < target) {
+      if (++spins > TOPK_BARRIER_SPINS) {
+        atomicExch(w.err, 1u);
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
   }
-  hist[threadIdx.x] = 0u;
+  __syncthreads();
+}
+
+// Block-wide exclusive scan of 0/1 flags over TOPK_THREADS threads; returns the
+// thread's prefix and sets *total.
+__device__ __forceinline__ int topk_flag_scan(bool f, int* s_w, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned b = __ballot_sync(0xffffffffu, f);
+  if (lane == 0) s_w[warp] = __popc(b);
+  __syncthreads();
+  if (warp == 0) {
+    int x = s_w[lane], inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    s_w[32 + lane] = inc - x;
+    if (lane == 31) s_w[64] = inc;
+  }
+  __syncthreads();
+  const int pre = s_w[32 + warp] + __popc(b & lanemask_lt());
+  *total = s_w[64];
+  __syncthreads();
+  return pre;
+}
+
+__global__ void __launch_bounds__(TOPK_THREADS)
+    topk_coop_kernel(const double* mass, long long n, long long k, int* out_ids, TopkCoop w) {
+  __shared__ unsigned s_h[256];
+  __shared__ unsigned long long s_lo[32], s_hi[32];
+  __shared__ int s_w[65];
+  __shared__ unsigned s_pick[3];  // digit, its count, keys in higher digits
+  __shared__ long long s_pre;
+  const unsigned long long* keys = reinterpret_cast<const unsigned long long*>(mass);
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const long long G = gridDim.x;
+  const long long chunk = ((n + G - 1) / G + TOPK_THREADS - 1) / TOPK_THREADS * TOPK_THREADS;
+  const long long c0 = blockIdx.x * chunk, c1 = min(n, c0 + chunk);
+  unsigned long long prefix = 0ull, mask = 0ull;
+  long long remaining = k;
+  unsigned round = 0;
+  for (int p = 0; p < 8; ++p) {
+    const int shift = 56 - 8 * p;
+    if (t < 256) s_h[t] = 0u;
+    __syncthreads();
+    unsigned long long lo = ~0ull, hi = 0ull;
+    for (long long i = c0 + t; i < c1; i += TOPK_THREADS) {
+      const unsigned long long key = keys[i];
+      if ((key & mask) == prefix) {
+        atomicAdd(&s_h[(key >> shift) & 255ull], 1u);
+        lo = min(lo, key);
+        hi = max(hi, key);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      s_lo[warp] = lo;
+      s_hi[warp] = hi;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      lo = s_lo[lane];
+      hi = s_hi[lane];
+      for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      }
+      if (lane == 0 && lo <= hi) {
+        atomicMin(&w.mm[2 * p], lo);
+        atomicMax(&w.mm[2 * p + 1], hi);
+      }
+    }
+    if (t < 256 && s_h[t]) atomicAdd(&w.hist[256 * p + t], s_h[t]);
+    topk_grid_barrier(w, ++round);
+    const unsigned long long glo = *(volatile unsigned long long*)&w.mm[2 * p];
+    const unsigned long long ghi = *(volatile unsigned long long*)&w.mm[2 * p + 1];
+    if (glo == ghi) {  // every key still in play is the threshold key
+      prefix = glo;
+      mask = ~0ull;
+      break;
+    }
+    if (warp < 8) {  // suffix sums over digits 255 .. 0, one digit per thread
+      const int b = 255 - t;
+      const long long c = (long long)*(volatile unsigned*)&w.hist[256 * p + b];
+      long long inc = c;
+      for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      if (lane == 31) s_lo[warp] = (unsigned long long)inc;
+      __syncwarp();
+      asm volatile("bar.sync 1, 256;");
+      long long pre = 0;
+      for (int q = 0; q < warp; ++q) pre += (long long)s_lo[q];
+      const long long suf = pre + inc, above = suf - c;
+      if (suf >= remaining && above < remaining) {
+        s_pick[0] = (unsigned)b;
+        s_pick[1] = (unsigned)c;
+        s_pick[2] = (unsigned)above;
+      }
+    }
+    __syncthreads();
+    prefix |= (unsigned long long)s_pick[0] << shift;
+    mask |= 255ull << shift;
+    remaining -= (long long)s_pick[2];
+    if ((long long)s_pick[1] == remaining) break;  // the digit's keys are all taken
+    __syncthreads();
+  }
+  // ranks of the keys equal to the threshold (under the mask), in id order
+  int tot = 0;
+  long long cnt_eq = 0;
+  for (long long i0 = c0; i0 < c1; i0 += TOPK_THREADS) {
+    const long long i = i0 + t;
+    const bool eq = i < c1 && (keys[i] & mask) == prefix;
+    topk_flag_scan(eq, s_w, &tot);
+    cnt_eq += tot;
+  }
+  if (t == 0) w.blk[blockIdx.x] = cnt_eq;
+  topk_grid_barrier(w, ++round);
+  if (warp == 0) {
+    long long x = 0;
+    for (long long b = lane; b < blockIdx.x; b += 32) x += *(volatile long long*)&w.blk[b];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) s_pre = x;
+  }
+  __syncthreads();
+  long long run = s_pre, cnt_sel = 0;
+  for (long long i0 = c0; i0 < c1; i0 += TOPK_THREADS) {
+    const long long i = i0 + t;
+    unsigned long long km = i < c1 ? (keys[i] & mask) : 0ull;
+    const bool eq = i < c1 && km == prefix;
+    const int r = topk_flag_scan(eq, s_w, &tot);
+    const bool sel = i < c1 && (km > prefix || (eq && run + r < remaining));
+    if (i < c1) w.sel[i] = sel ? 1 : 0;
+    run += tot;
+    cnt_sel += __syncthreads_count(sel);
+  }
+  if (t == 0) w.blk[G + blockIdx.x] = cnt_sel;
+  topk_grid_barrier(w, ++round);
+  if (warp == 0) {
+    long long x = 0;
+    for (long long b = lane; b < blockIdx.x; b += 32) x += *(volatile long long*)&w.blk[G + b];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) s_pre = x;
+  }
+  __syncthreads();
+  run = s_pre;
+  for (long long i0 = c0; i0 < c1; i0 += TOPK_THREADS) {
+    const long long i = i0 + t;
+    const bool sel = i < c1 && w.sel[i];
+    const int r = topk_flag_scan(sel, s_w, &tot);
+    if (sel) out_ids[run + r] = (int)i;
+    run += tot;
+  }
+}
+
+// Presets the per-pass min/max slots (min to all ones, max to zero).
+__global__ void topk_coop_init_kernel(unsigned long long* mm) {
+  if (threadIdx.x < 16) mm[threadIdx.x] = (threadIdx.x & 1) ? 0ull : ~0ull;
+}
+
+// Blocks of the cooperative top-k kernel on this device: one per SM (all resident).
+static int topk_coop_grid(int* grid) {
+  int dev = 0, sms = 0, per_sm = 0;
+  ADP_CUDA(cudaGetDevice(&dev));
+  ADP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  ADP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topk_coop_kernel, TOPK_THREADS, 0));
+  ADP_CHECK_ARG(per_sm >= 1 && sms >= 1, "the top-k kernel cannot be resident on this device");
+  *grid = sms < TOPK_MAX_BLOCKS ? sms : TOPK_MAX_BLOCKS;
+  return ADP_OK;
+}
+
+// Scratch layout of the cooperative top-k (in a workspace or the static array).
+static size_t topk_coop_bytes(long long n) {
+  return carve_bytes<unsigned>(8 * 256) + carve_bytes<unsigned long long>(16) +
+         carve_bytes<unsigned>(2) + carve_bytes<long long>(2 * TOPK_MAX_BLOCKS) +
+         carve_bytes<uint8_t>(n > 0 ? n : 1);
+}
+
+static int topk_coop_run(const double* mass, long long n, long long k, int32_t* out_ids,
+                         void* ws, size_t ws_bytes, cudaStream_t st) {
+  Carver c(ws, ws_bytes);
+  TopkCoop w;
+  w.hist = c.take<unsigned>(8 * 256);
+  w.mm = c.take<unsigned long long>(16);
+  w.bar = c.take<unsigned>(2);
+  w.err = w.bar + 1;
+  w.blk = c.take<long long>(2 * TOPK_MAX_BLOCKS);
+  w.sel = c.take<uint8_t>(n > 0 ? n : 1);
+  ADP_CHECK_ARG(c.ok, "internal: top-k scratch too small");
+  int grid = 0;
+  int rc = topk_coop_grid(&grid);
+  if (rc) return rc;
+  ADP_CUDA(cudaMemsetAsync(w.hist, 0, sizeof(unsigned) * 8 * 256, st));
+  ADP_CUDA(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st));
+  topk_coop_init_kernel<<<1, 32, 0, st>>>(w.mm);
+  ADP_LAUNCH_CHECK();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(TOPK_THREADS);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int* dummy = nullptr;
+  (void)dummy;
+  ADP_CUDA(cudaLaunchKernelEx(&cfg, topk_coop_kernel, mass, (long long)n, (long long)k,
+                              (int*)out_ids, w));
+  return ADP_OK;
 }
 
 // ------------------------------------------------------------------ erosion
@@ -217,10 +413,10 @@ __global__ void topk_reset_kernel(SelectState* st, unsigned* hist, long long k) 
 __global__ void erode_h_kernel(const uint8_t* mask, uint8_t* tmp, CamSet cs, int r) {
   const int v = blockIdx.y;
   const int W = cs.cam[v].width, H = cs.cam[v].height;
-  const long long P = (long long)W * H, base = cs.pix_base[v];
-  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < P;
-       u += (long long)gridDim.x * blockDim.x) {
-    int x = (int)(u % W);
+  const int P = W * H;  // a view has fewer than 2^31 pixels (checked by the caller)
+  const long long base = cs.pix_base[v];
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < P; u += gridDim.x * blockDim.x) {
+    const int x = u % W;
     const uint8_t* row = mask + base + (u - x);
     uint8_t ok = 1;
     for (int d = -r; d <= r && ok; ++d) {
@@ -234,10 +430,10 @@ __global__ void erode_h_kernel(const uint8_t* mask, uint8_t* tmp, CamSet cs, int
 __global__ void erode_v_kernel(const uint8_t* tmp, uint8_t* mask, CamSet cs, int r) {
   const int v = blockIdx.y;
   const int W = cs.cam[v].width, H = cs.cam[v].height;
-  const long long P = (long long)W * H, base = cs.pix_base[v];
-  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < P;
-       u += (long long)gridDim.x * blockDim.x) {
-    int x = (int)(u % W), y = (int)(u / W);
+  const int P = W * H;
+  const long long base = cs.pix_base[v];
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < P; u += gridDim.x * blockDim.x) {
+    const int y = u / W, x = u - y * W;
     uint8_t ok = 1;
     for (int d = -r; d <= r && ok; ++d) {
       int yy = y + d;
@@ -290,13 +486,6 @@ __device__ __forceinline__ bool region_pixel(const uint8_t* mask, const int* dom
   return (mask[p] & 2) && d >= 0 && d < n && cand[d];
 }
 
-__global__ void ccl_init_kernel(const uint8_t* mask, const int* dom, const uint8_t* cand,
-                                long long n, long long P, int* L) {
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
-       p += (long long)gridDim.x * blockDim.x)
-    L[p] = region_pixel(mask, dom, cand, n, p) ? (int)p : -1;
-}
-
 // Same-class test of two participating pixels: equal dominant Gaussian and band.
 __device__ __forceinline__ bool same_class(const int* L, const int* dom, const uint8_t* mask,
                                            long long p, long long q) {
@@ -333,11 +522,13 @@ __device__ void sunite(int* l, int a, int b) {
   }
 }
 
-// Labelling inside one 32x32 tile in shared memory, then every pixel points at
-// its tile-local root by global index. The skip rules drop edges that another
-// edge of the 8-neighbourhood already implies: up-left when left or up is
-// joined, up-right when up is joined.
+// Labelling inside one 32x32 tile in shared memory, then every pixel of the
+// tile gets its label: the tile-local root by global index for a participating
+// pixel (eroded mask set, dominated by a candidate), -1 for any other. The skip
+// rules drop edges that another edge of the 8-neighbourhood already implies:
+// up-left when left or up is joined, up-right when up is joined.
 __global__ void __launch_bounds__(256) ccl_local_kernel(const uint8_t* mask, const int* dom,
+                                                        const uint8_t* cand, long long n,
                                                         CamSet cs, int* L) {
   __shared__ int s_l[CCL_T * CCL_T];
   __shared__ int s_d[CCL_T * CCL_T];
@@ -353,8 +544,8 @@ __global__ void __launch_bounds__(256) ccl_local_kernel(const uint8_t* mask, con
     int lab = -1, d = -1;
     uint8_t b = 0;
     if (x < W && y < H) {
-      long long p = base + (long long)y * W + x;
-      if (L[p] >= 0) {
+      const long long p = base + (long long)y * W + x;
+      if (region_pixel(mask, dom, cand, n, p)) {
         lab = li;
         d = dom[p];
         b = mask[p] >> 4;
@@ -379,10 +570,14 @@ __global__ void __launch_bounds__(256) ccl_local_kernel(const uint8_t* mask, con
   __syncthreads();
   for (int li = threadIdx.x; li < CCL_T * CCL_T; li += blockDim.x) {
     int x = tx0 + (li & (CCL_T - 1)), y = ty0 + li / CCL_T;
-    if (x >= W || y >= H || s_l[li] < 0) continue;
-    int r = sfind(s_l, li);
-    int rx = tx0 + (r & (CCL_T - 1)), ry = ty0 + r / CCL_T;
-    L[base + (long long)y * W + x] = (int)(base + (long long)ry * W + rx);
+    if (x >= W || y >= H) continue;
+    int lab = -1;
+    if (s_l[li] >= 0) {
+      int r = sfind(s_l, li);
+      int rx = tx0 + (r & (CCL_T - 1)), ry = ty0 + r / CCL_T;
+      lab = (int)(base + (long long)ry * W + rx);
+    }
+    L[base + (long long)y * W + x] = lab;
   }
 }
 
@@ -391,10 +586,10 @@ __global__ void __launch_bounds__(256) ccl_local_kernel(const uint8_t* mask, con
 __global__ void ccl_border_kernel(const uint8_t* mask, const int* dom, CamSet cs, int* L) {
   const int v = blockIdx.y;
   const int W = cs.cam[v].width, H = cs.cam[v].height;
-  const long long P = (long long)W * H, base = cs.pix_base[v];
-  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < P;
-       u += (long long)gridDim.x * blockDim.x) {
-    int x = (int)(u % W), y = (int)(u / W);
+  const int P = W * H;
+  const long long base = cs.pix_base[v];
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < P; u += gridDim.x * blockDim.x) {
+    const int y = u / W, x = u - y * W;
     int lx = x & (CCL_T - 1), ly = y & (CCL_T - 1);
     if (lx != 0 && ly != 0 && lx != CCL_T - 1) continue;
     long long p = base + u;
@@ -431,21 +626,23 @@ __global__ void moments_kernel(const int* L, const int* slot, CamSet cs, long lo
   __shared__ long long s_xy[8][32][2];
   const int v = blockIdx.y;
   const int W = cs.cam[v].width, H = cs.cam[v].height;
-  const long long P = (long long)W * H, base = cs.pix_base[v];
+  const int P = W * H;
+  const long long base = cs.pix_base[v];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (long long u0 = blockIdx.x * (long long)blockDim.x; u0 < P;
-       u0 += (long long)gridDim.x * blockDim.x) {
-    long long u = u0 + threadIdx.x;
+  for (int u0 = blockIdx.x * blockDim.x; u0 < P; u0 += gridDim.x * blockDim.x) {
+    const int u = u0 + threadIdx.x;
     int s = -1;
     long long x = 0, y = 0;
     if (u < P) {
       int r = L[base + u];
       if (r >= 0) {
         s = slot[r];
-        x = u % W;
-        y = u / W;
+        const int yy = u / W;
+        x = u - yy * W;
+        y = yy;
       }
     }
+    if (__ballot_sync(0xffffffffu, s >= 0) == 0) continue;  // no labelled pixel in this warp
     unsigned peers = __match_any_sync(0xffffffffu, s);
     s_xy[warp][lane][0] = x;
     s_xy[warp][lane][1] = y;
@@ -563,9 +760,9 @@ __global__ void region_stats_kernel(RegionArgs a, CamSet cs) {
 __global__ void labels_out_kernel(const int* L, const long long* mom, const int* slot, int m_min,
                                   CamSet cs, int* labels) {
   const int v = blockIdx.y;
-  const long long P = (long long)cs.cam[v].width * cs.cam[v].height, base = cs.pix_base[v];
-  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < P;
-       u += (long long)gridDim.x * blockDim.x) {
+  const int P = cs.cam[v].width * cs.cam[v].height;
+  const long long base = cs.pix_base[v];
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < P; u += gridDim.x * blockDim.x) {
     int r = L[base + u];
     labels[base + u] = r >= 0 ? (int)(r - base) : -1;
   }
@@ -643,8 +840,7 @@ extern "C" ADP_API int adp_error_stats(const float* img, const float* target,
 
 extern "C" ADP_API size_t adp_select_topk_workspace_size(int64_t n) {
   if (n < 0) return 0;
-  return carve_bytes<SelectState>(1) + carve_bytes<unsigned>(256) + carve_bytes<uint8_t>(n) +
-         scan_workspace_bytes(n) + carve_bytes<long long>(2);
+  return topk_coop_bytes(n);
 }
 
 extern "C" ADP_API int adp_select_topk(const double* mass, int64_t n, int64_t k, int32_t* out_ids,
@@ -662,36 +858,7 @@ extern "C" ADP_API int adp_select_topk(const double* mass, int64_t n, int64_t k,
     ADP_LAUNCH_CHECK();
     return ADP_OK;
   }
-  Carver c(ws, ws_bytes);
-  SelectState* ss = c.take<SelectState>(1);
-  unsigned* hist = c.take<unsigned>(256);
-  uint8_t* sel = c.take<uint8_t>(n);
-  void* sw = c.take<char>(scan_workspace_bytes(n));
-  long long* cnt = c.take<long long>(2);
-  topk_reset_kernel<<<1, 256, 0, st>>>(ss, hist, (long long)k);
-  unsigned g = grid_for(n, 256, 148 * 8);
-  for (int shift = 56; shift >= 0; shift -= 8) {
-    topk_hist_kernel<<<g, 256, 0, st>>>(mass, n, shift, ss, hist);
-    topk_pick_kernel<<<1, 256, 0, st>>>(hist, shift, ss);
-  }
-  ADP_LAUNCH_CHECK();
-  // keys above the threshold, plus the first `remaining` equal ones by id
-  const SelectState* css = ss;
-  int rc = scan_exclusive(
-      [=] __device__(long long i) -> long long {
-        return (unsigned long long)__double_as_longlong(mass[i]) == css->prefix ? 1 : 0;
-      },
-      [=] __device__(long long i, long long pre) {
-        unsigned long long key = (unsigned long long)__double_as_longlong(mass[i]);
-        sel[i] = key > css->prefix || (key == css->prefix && pre < css->remaining);
-      },
-      n, nullptr, &cnt[0], sw, st);
-  if (rc) return rc;
-  return scan_exclusive([=] __device__(long long i) -> long long { return sel[i]; },
-                        [=] __device__(long long i, long long pre) {
-                          if (sel[i]) out_ids[pre] = (int)i;
-                        },
-                        n, nullptr, &cnt[1], sw, st);
+  return topk_coop_run(mass, n, k, out_ids, ws, ws_bytes, st);
 }
 
 // ------------------------------------------------------------------ regions
@@ -768,14 +935,14 @@ extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* do
                                                                       w.cand);
   // labelling
   unsigned gp = grid_for(P, 256, 148 * 16);
-  ccl_init_kernel<<<gp, 256, 0, st>>>(maps->mask, dominant, w.cand, n, P, w.L);
   {
     int max_tiles = 0;
     for (int v = 0; v < n_views; ++v) {
       int t = ((cs.cam[v].width + CCL_T - 1) / CCL_T) * ((cs.cam[v].height + CCL_T - 1) / CCL_T);
       max_tiles = t > max_tiles ? t : max_tiles;
     }
-    ccl_local_kernel<<<dim3(max_tiles, n_views), 256, 0, st>>>(maps->mask, dominant, cs, w.L);
+    ccl_local_kernel<<<dim3(max_tiles, n_views), 256, 0, st>>>(maps->mask, dominant, w.cand, n,
+                                                                cs, w.L);
     ccl_border_kernel<<<grid, 256, 0, st>>>(maps->mask, dominant, cs, w.L);
   }
   ccl_flatten_kernel<<<gp, 256, 0, st>>>(w.L, P);
@@ -844,9 +1011,8 @@ namespace adp {
 // byte per Gaussian, scan block sums and two counters (all 256-aligned).
 constexpr long long kNoallocMaxN = ADP_TOPK_NOALLOC_MAX_N;
 constexpr size_t kNoallocBytes =
-    256 /*state*/ + 1024 /*hist*/ + ((kNoallocMaxN + 255) / 256) * 256 /*flags*/ +
-    (((kNoallocMaxN + SCAN_TILE - 1) / SCAN_TILE + 1) * 8 + 255) / 256 * 256 /*scan*/ +
-    256 /*counters*/;
+    8 * 256 * 4 /*histograms*/ + 256 /*min/max*/ + 256 /*barrier*/ +
+    2 * TOPK_MAX_BLOCKS * 8 /*block counts*/ + ((kNoallocMaxN + 255) / 256) * 256 /*flags*/;
 static __device__ __align__(256) unsigned char g_topk_scratch[kNoallocBytes];
 
 // Per-device address of g_topk_scratch, looked up once per device.
@@ -865,17 +1031,6 @@ static int topk_scratch_address(void** out) {
   }
   *out = g_topk_scratch_ptr[dev];
   return ADP_OK;
-}
-
-// Resets the selection state and the histogram of the shared scratch.
-__global__ void topk_noalloc_reset_kernel(SelectState* st, unsigned* hist, long long k) {
-  if (threadIdx.x == 0) {
-    st->prefix = 0ull;
-    st->mask = 0ull;
-    st->remaining = k;
-    st->pad = 0;
-  }
-  hist[threadIdx.x] = 0u;
 }
 
 }  // namespace adp
@@ -899,34 +1054,6 @@ extern "C" ADP_API int adp_select_topk_noalloc(const double* mass, int64_t n, in
   void* base = nullptr;
   int rc = topk_scratch_address(&base);
   if (rc) return rc;
-  Carver c(base, kNoallocBytes);
-  SelectState* ss = c.take<SelectState>(1);
-  unsigned* hist = c.take<unsigned>(256);
-  uint8_t* sel = c.take<uint8_t>(n);
-  void* sw = c.take<char>(scan_workspace_bytes(n));
-  long long* cnt = c.take<long long>(2);
-  ADP_CHECK_ARG(c.ok, "internal: static scratch too small");
-  topk_noalloc_reset_kernel<<<1, 256, 0, st>>>(ss, hist, (long long)k);
-  unsigned g = grid_for(n, 256, 148 * 8);
-  for (int shift = 56; shift >= 0; shift -= 8) {
-    topk_hist_kernel<<<g, 256, 0, st>>>(mass, n, shift, ss, hist);
-    topk_pick_kernel<<<1, 256, 0, st>>>(hist, shift, ss);
-  }
-  ADP_LAUNCH_CHECK();
-  const SelectState* css = ss;
-  rc = scan_exclusive(
-      [=] __device__(long long i) -> long long {
-        return (unsigned long long)__double_as_longlong(mass[i]) == css->prefix ? 1 : 0;
-      },
-      [=] __device__(long long i, long long pre) {
-        unsigned long long key = (unsigned long long)__double_as_longlong(mass[i]);
-        sel[i] = key > css->prefix || (key == css->prefix && pre < css->remaining);
-      },
-      n, nullptr, &cnt[0], sw, st);
-  if (rc) return rc;
-  return scan_exclusive([=] __device__(long long i) -> long long { return sel[i]; },
-                        [=] __device__(long long i, long long pre) {
-                          if (sel[i]) out_ids[pre] = (int)i;
-                        },
-                        n, nullptr, &cnt[1], sw, st);
+  ADP_CHECK_ARG(topk_coop_bytes(n) <= kNoallocBytes, "internal: static scratch too small");
+  return topk_coop_run(mass, n, k, out_ids, base, kNoallocBytes, st);
 }

@@ -37,7 +37,9 @@ struct SplitWs {
   float4* kids;        // [Rcap][4] child table: mean, quat, logscale, dc
   long long* keep_new; // [n]
   long long* app_off;  // [n_cand]
-  long long* counters; // [0] regions in use, [1] kept, [2] appended, [3] new n
+  long long* counters; // [0] regions in use, [1] kept, [2] appended, [3] new n,
+                       // [4] candidates with two or more proposals
+  int* multi;          // [n_cand] those candidates, in no particular order
   void* scan;
   SortWorkspace sort;
 };
@@ -47,7 +49,8 @@ static size_t split_ws_bytes(long long n, long long nc, long long rc) {
   return carve_bytes<int>(n) + 2 * carve_bytes<unsigned>(rc) + carve_bytes<int2>(nc) +
          carve_bytes<Prop>(rc) + 2 * carve_bytes<int>(rc) + carve_bytes<double>(rc) +
          carve_bytes<float4>(4 * rc) + carve_bytes<long long>(n) + carve_bytes<long long>(nc) +
-         carve_bytes<long long>(4) + scan_workspace_bytes(sm) + sort_workspace_bytes(rc);
+         carve_bytes<long long>(8) + carve_bytes<int>(nc) + scan_workspace_bytes(sm) +
+         sort_workspace_bytes(rc);
 }
 
 static SplitWs carve_split(Carver& c, long long n, long long nc, long long rc) {
@@ -64,7 +67,8 @@ static SplitWs carve_split(Carver& c, long long n, long long nc, long long rc) {
   w.kids = c.take<float4>(4 * rc);
   w.keep_new = c.take<long long>(n);
   w.app_off = c.take<long long>(nc);
-  w.counters = c.take<long long>(4);
+  w.counters = c.take<long long>(8);
+  w.multi = c.take<int>(nc);
   w.scan = c.take<char>(scan_workspace_bytes(sm));
   w.sort = carve_sort(c, rc);
   return w;
@@ -340,6 +344,8 @@ struct MergeArgs {
   int n_max;
   uint8_t* status;
   int* n_children;
+  int* multi;                    // candidates left to merge_warp_kernel
+  unsigned long long* n_multi;   // their count
 };
 
 // Eq. 11 between two proposals.
@@ -431,6 +437,7 @@ __global__ void merge_status_kernel(MergeArgs a) {
       a.n_children[c] = 0;
     } else {
       a.status[c] = ADP_ADAPTIVE;
+      if (M >= 2) a.multi[atomicAdd(a.n_multi, 1ull)] = (int)c;  // merged by a warp
       if (M == 1) {
         const Prop& p = a.props[sg.x];
         if (a.n_max >= 1) store_child(a.kids + 4LL * sg.x, p.mu, p.R, p.s, p.rgb);
@@ -449,7 +456,8 @@ __device__ __forceinline__ int uf_root_v(volatile int* uf, int x) {
   return x;
 }
 
-// One warp per candidate with two or more proposals: the pairwise tests of
+// One warp per candidate with two or more proposals (the list merge_status_kernel
+// builds; each candidate writes only its own segment, so the order is free): the pairwise tests of
 // Eq. 11 are spread over the lanes and joined in a union-find whose links point
 // to smaller indices (so every group is rooted at its first member); groups are
 // numbered in first-member order, merged one per lane (Eq. 12), capped at n_max
@@ -457,11 +465,12 @@ __device__ __forceinline__ int uf_root_v(volatile int* uf, int x) {
 __global__ void merge_warp_kernel(MergeArgs a) {
   const int lane = threadIdx.x & 31;
   const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long c = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); c < a.nc;
-       c += warps) {
+  const long long n_multi = (long long)*a.n_multi;
+  for (long long t = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); t < n_multi;
+       t += warps) {
+    const int c = a.multi[t];
     const int2 sg = a.seg[c];
     const int s0 = sg.x, M = sg.y - sg.x;
-    if (M < 2 || a.count[a.cand[c]] == 0) continue;
     int* uf = a.uf + s0;
     volatile int* vuf = uf;
     for (int m = lane; m < M; m += 32) uf[m] = m;
@@ -746,7 +755,7 @@ extern "C" ADP_API int adp_split_plan(const adp_gaussians* g, const adp_camera* 
   cudaStream_t st = (cudaStream_t)stream;
   Carver c(ws, ws_bytes);
   SplitWs w = carve_split(c, n, nc, rcap);
-  ADP_CUDA(cudaMemsetAsync(w.counters, 0, 4 * sizeof(long long), st));
+  ADP_CUDA(cudaMemsetAsync(w.counters, 0, 8 * sizeof(long long), st));
   if (n > 0) ADP_CUDA(cudaMemsetAsync(w.cand_of, 0xff, sizeof(int) * n, st));
   if (nc > 0) {
     ADP_CUDA(cudaMemsetAsync(w.seg, 0, sizeof(int2) * nc, st));
@@ -798,8 +807,12 @@ extern "C" ADP_API int adp_split_plan(const adp_gaussians* g, const adp_camera* 
     ma.n_max = prm->n_max;
     ma.status = status;
     ma.n_children = n_children;
+    ma.multi = w.multi;
+    ma.n_multi = reinterpret_cast<unsigned long long*>(&w.counters[4]);
     merge_status_kernel<<<grid_for(nc, 256, 4096), 256, 0, st>>>(ma);
-    merge_warp_kernel<<<grid_for(nc * 32, 128, 4096), 128, 0, st>>>(ma);
+    // a resident grid (four 128-thread blocks per SM fit its registers) that loops
+    // over the device-side list
+    merge_warp_kernel<<<grid_for(nc * 32, 128, 148 * 4), 128, 0, st>>>(ma);
     ADP_LAUNCH_CHECK();
   }
   // new indices of kept Gaussians and offsets of appended blocks
@@ -911,7 +924,6 @@ static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
     ap.counters = w.counters;
     ap.noise = noise;
     ap.eta = prm->eta;
-    // appended rows: at most n_cand * (n_max + 1), each with its own thread
     apply_append_kernel<<<grid_for(nc * (long long)(prm->n_max > 1 ? prm->n_max + 1 : 2), 128,
                                    148 * 32), 128, 0, st>>>(ap);
   }
