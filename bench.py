@@ -355,7 +355,7 @@ def batched_vs_plain(g, tg, dev, n_views, steps, flush, width, height, radius, s
         torch.cuda.empty_cache()
     batched = ViewStages(g, cams, target, params=params)
     offs = np.cumsum([0] + [c["width"] * c["height"] for c in cams])
-    grad = ops.Gaussians(g.n, g.sh_degree, dev, zero=False)
+    grad = ops.Gaussians(g.n, g.sh_degree, dev, zero=False, row_mask=True)
     plain = [ViewStages(g, [c], target[offs[v]:offs[v + 1]], params=params, grad=grad)
              for v, c in enumerate(cams)]
     gb = capture_graph(batched.run)

@@ -100,7 +100,14 @@ typedef struct adp_params {
  *   quat[i]       = (w, x, y, z)                 normalised before use
  *   sh[p * n + i] = floats 4p..4p+3 of the SH list of Gaussian i, where float
  *                   3k + ch is coefficient k of channel ch, k < K = (deg+1)^2;
- *                   there are ceil(3K / 4) planes (1 for degree 0, 12 for 3). */
+ *                   there are ceil(3K / 4) planes (1 for degree 0, 12 for 3).
+ * rows (gradients only; NULL for parameters and moments): an optional device
+ * byte per row. When non-NULL, a row with rows[i] == 0 is zero by definition
+ * and the library neither reads nor writes its planes: adp_render_backward then
+ * writes the mask itself (1 for every Gaussian rendered in at least one view)
+ * instead of zeroing the other rows, and the Adam entry points skip the
+ * gradient reads of masked-out rows. Rows of Gaussians that no view renders are
+ * most rows of a large scene, so this saves two passes over their planes. */
 typedef struct adp_gaussians {
   int64_t n;
   int32_t sh_degree; /* 0..3 */
@@ -109,6 +116,7 @@ typedef struct adp_gaussians {
   float* logscale;
   float* quat;
   float* sh;
+  uint8_t* rows;
 } adp_gaussians;
 
 /* Projected Gaussians, one record per (view v, Gaussian i) at index v * n + i.

@@ -37,7 +37,7 @@ class AdpParams(C.Structure):
 
 class AdpGaussians(C.Structure):
     _fields_ = [("n", _i64), ("sh_degree", _i32), ("reserved", _i32), ("mean_logit", _vp),
-                ("logscale", _vp), ("quat", _vp), ("sh", _vp)]
+                ("logscale", _vp), ("quat", _vp), ("sh", _vp), ("rows", _vp)]
 
 
 class AdpProjected(C.Structure):

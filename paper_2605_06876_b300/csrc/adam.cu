@@ -13,6 +13,7 @@ struct AdamPlanes {
   const float4 *g_ml, *g_ls, *g_q, *g_sh;
   float4 *m_ml, *m_ls, *m_q, *m_sh;
   float4 *v_ml, *v_ls, *v_q, *v_sh;
+  const uint8_t* g_rows;  // optional gradient row mask: 0 = zero gradient, not read
   long long n;
   int planes;
 };
@@ -37,7 +38,9 @@ __device__ __forceinline__ void adam_at(const AdamPlanes& a, const AdamHyper& h,
   float4 *P, *M, *V;
   const float4* G;
   plane_ptrs(a, q, i, &P, &G, &M, &V);
-  float4 p = *P, g = *G, m = *M, v = *V;  // all loads first
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 p = *P, m = *M, v = *V;  // all loads first
+  const float4 g = (!a.g_rows || a.g_rows[i]) ? *G : z;
   const float2 bc = adam_bias(h);
   float lr4[4];
   adam_plane_lr(h, q, lr4);
@@ -85,6 +88,7 @@ static AdamPlanes adam_planes(adp_gaussians* param, const adp_gaussians* grad, a
   a.m_q = (float4*)m->quat; a.m_sh = (float4*)m->sh;
   a.v_ml = (float4*)v->mean_logit; a.v_ls = (float4*)v->logscale;
   a.v_q = (float4*)v->quat; a.v_sh = (float4*)v->sh;
+  a.g_rows = grad->rows;
   a.n = param->n;
   a.planes = sh_planes(param->sh_degree);
   return a;

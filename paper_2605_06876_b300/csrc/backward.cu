@@ -455,44 +455,56 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
   }
 }
 
-// Zeroes the gradient of every Gaussian rendered in no view and appends the
-// others to a list, with one atomic per block (the list order does not change
-// any result), so the chain-rule pass runs on full warps of visible Gaussians.
+// Zeroes the gradient of every Gaussian rendered in no view (or, for a
+// gradient with a row mask, writes the mask instead) and appends the
+// others to a list (the list order does not change any result), so the
+// chain-rule pass runs on full warps of visible Gaussians. Warps count their
+// visible lanes with a ballot; one global atomic per block reserves the block's
+// slots.
 __global__ void __launch_bounds__(256) bwd_visible_kernel(const int* tiles, long long n,
                                                           int n_views, int planes, float4* g_ml,
                                                           float4* g_ls, float4* g_q, float4* g_sh,
-                                                          int* list, unsigned long long* count) {
-  __shared__ int s_cnt;
+                                                          uint8_t* rows, int* list,
+                                                          unsigned long long* count) {
+  __shared__ unsigned s_cnt[8];
   __shared__ unsigned long long s_base;
-  __shared__ int s_local[256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (long long i0 = blockIdx.x * (long long)blockDim.x; i0 < n;
        i0 += (long long)gridDim.x * blockDim.x) {
-    if (threadIdx.x == 0) s_cnt = 0;
-    __syncthreads();
     const long long i = i0 + threadIdx.x;
-    if (i < n) {
-      bool seen = false;
+    bool seen = false;
+    if (i < n)
       for (int v = 0; v < n_views; ++v) seen |= tiles[(long long)v * n + i] > 0;
-      if (seen) {
-        s_local[atomicAdd(&s_cnt, 1)] = (int)i;
-      } else {
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        g_ml[i] = z;
-        g_ls[i] = z;
-        g_q[i] = z;
-        for (int p = 0; p < planes; ++p) g_sh[(long long)p * n + i] = z;
-      }
+    const unsigned vis = __ballot_sync(0xffffffffu, seen);
+    if (lane == 0) s_cnt[warp] = __popc(vis);
+    __syncthreads();
+    unsigned before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      const unsigned c = s_cnt[w];
+      before += w < warp ? c : 0u;
+      total += c;
     }
+    if (threadIdx.x == 0 && total) s_base = atomicAdd(count, (unsigned long long)total);
     __syncthreads();
-    if (threadIdx.x == 0 && s_cnt) s_base = atomicAdd(count, (unsigned long long)s_cnt);
-    __syncthreads();
-    if ((int)threadIdx.x < s_cnt) list[s_base + threadIdx.x] = s_local[threadIdx.x];
-    __syncthreads();
+    if (seen) list[s_base + before + __popc(vis & lanemask_lt())] = (int)i;
+    if (rows) {  // masked gradient: mark the rows; the others are never touched
+      if (i < n) rows[i] = seen ? 1 : 0;
+    } else if (i < n && !seen) {
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      g_ml[i] = z;
+      g_ls[i] = z;
+      g_q[i] = z;
+      for (int p = 0; p < planes; ++p) g_sh[(long long)p * n + i] = z;
+    }
   }
 }
 
+#ifndef ADP_BWDG_MINB  // resident 128-thread blocks per SM the register budget is sized for
+#define ADP_BWDG_MINB 1
+#endif
 template <int DEG>
-__global__ void __launch_bounds__(128) bwd_gauss_kernel(BwdGaussArgs a, CamSet cs,
+__global__ void __launch_bounds__(128, ADP_BWDG_MINB) bwd_gauss_kernel(BwdGaussArgs a, CamSet cs,
                                                         const int* list,
                                                         const unsigned long long* n_list) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -570,7 +582,7 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   ga.g_sh = grad->sh;
   bwd_visible_kernel<<<grid_for(g->n, 256, 148 * 16), 256, 0, st>>>(
       pr->tiles_touched, g->n, n_views, sh_planes(g->sh_degree), ga.g_ml, ga.g_ls, ga.g_q,
-      reinterpret_cast<float4*>(grad->sh), list, n_list);
+      reinterpret_cast<float4*>(grad->sh), grad->rows, list, n_list);
   const unsigned gb = grid_for(g->n, 128);
   switch (g->sh_degree) {
     case 0: bwd_gauss_kernel<0><<<gb, 128, 0, st>>>(ga, cs, list, n_list); break;

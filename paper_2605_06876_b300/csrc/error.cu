@@ -524,9 +524,14 @@ __device__ void sunite(int* l, int a, int b) {
 
 // Labelling inside one 32x32 tile in shared memory, then every pixel of the
 // tile gets its label: the tile-local root by global index for a participating
-// pixel (eroded mask set, dominated by a candidate), -1 for any other. The skip
-// rules drop edges that another edge of the 8-neighbourhood already implies:
-// up-left when left or up is joined, up-right when up is joined.
+// pixel (eroded mask set, dominated by a candidate), -1 for any other.
+// Row runs first: a warp labels one tile row at a time with ballots, linking every
+// pixel straight to the first pixel of its run of same-class neighbours. Then the
+// union-find joins runs across rows, with one union per place where two runs
+// start to touch: the up edge only where the left neighbour does not already
+// reach the up-left pixel, up-left only when neither left nor up is joined,
+// up-right only when up is not joined. Every link points to a smaller index, so a
+// component's root is its smallest pixel index.
 __global__ void __launch_bounds__(256) ccl_local_kernel(const uint8_t* mask, const int* dom,
                                                         const uint8_t* cand, long long n,
                                                         CamSet cs, int* L) {
@@ -539,6 +544,7 @@ __global__ void __launch_bounds__(256) ccl_local_kernel(const uint8_t* mask, con
   if ((int)blockIdx.x >= ntx * nty) return;
   const int tx0 = (blockIdx.x % ntx) * CCL_T, ty0 = (blockIdx.x / ntx) * CCL_T;
   const long long base = cs.pix_base[v];
+  const int lane = threadIdx.x & 31;
   for (int li = threadIdx.x; li < CCL_T * CCL_T; li += blockDim.x) {
     int x = tx0 + (li & (CCL_T - 1)), y = ty0 + li / CCL_T;
     int lab = -1, d = -1;
@@ -556,16 +562,29 @@ __global__ void __launch_bounds__(256) ccl_local_kernel(const uint8_t* mask, con
     s_b[li] = b;
   }
   __syncthreads();
+  auto same = [&](int a, int q) { return s_l[q] >= 0 && s_d[q] == s_d[a] && s_b[q] == s_b[a]; };
+  // row runs (a warp owns whole rows; lane = column)
   for (int li = threadIdx.x; li < CCL_T * CCL_T; li += blockDim.x) {
-    if (s_l[li] < 0) continue;
-    int lx = li & (CCL_T - 1), ly = li / CCL_T;
-    auto same = [&](int q) { return s_l[q] >= 0 && s_d[q] == s_d[li] && s_b[q] == s_b[li]; };
-    bool left = lx > 0 && same(li - 1);
-    bool up = ly > 0 && same(li - CCL_T);
-    if (left) sunite(s_l, li, li - 1);
-    if (up) sunite(s_l, li, li - CCL_T);
-    if (!left && !up && lx > 0 && ly > 0 && same(li - CCL_T - 1)) sunite(s_l, li, li - CCL_T - 1);
-    if (!up && lx < CCL_T - 1 && ly > 0 && same(li - CCL_T + 1)) sunite(s_l, li, li - CCL_T + 1);
+    const bool part = s_l[li] >= 0;
+    const bool joined_left = part && lane > 0 && same(li, li - 1);
+    const unsigned starts = __ballot_sync(0xffffffffu, part && !joined_left);
+    if (part) {
+      const unsigned upto = starts & (lane == 31 ? 0xffffffffu : ((2u << lane) - 1u));
+      s_l[li] = (li - lane) + (31 - __clz(upto));
+    }
+  }
+  __syncthreads();
+  // joins across rows
+  for (int li = threadIdx.x; li < CCL_T * CCL_T; li += blockDim.x) {
+    const int ly = li / CCL_T;
+    if (ly == 0 || s_l[li] < 0) continue;
+    const bool left = lane > 0 && same(li, li - 1);
+    const bool up = same(li, li - CCL_T);
+    const bool upleft = lane > 0 && same(li, li - CCL_T - 1);
+    const bool upright = lane < CCL_T - 1 && same(li, li - CCL_T + 1);
+    if (up && !(left && upleft)) sunite(s_l, li, li - CCL_T);
+    if (upleft && !left && !up) sunite(s_l, li, li - CCL_T - 1);
+    if (upright && !up) sunite(s_l, li, li - CCL_T + 1);
   }
   __syncthreads();
   for (int li = threadIdx.x; li < CCL_T * CCL_T; li += blockDim.x) {
@@ -621,53 +640,61 @@ __global__ void zero_i64_kernel(long long* p, const long long* d_n, int per) {
     p[i] = 0;
 }
 
-// Exact int64 moments per root, warp-aggregated over pixels sharing a root.
+// Exact int64 moments per root. Pixels of a warp that share a root are summed
+// with one warp reduction per moment (__reduce_add_sync on 32-bit integers:
+// coordinates are below 2^16, so 32 squares or products stay below 2^37 only in
+// the worst case -- hence x and y are split into 8-bit halves for the second
+// moments, each partial sum fitting 32 bits), then added to the int64 totals.
+__device__ __forceinline__ unsigned long long moment_sum(unsigned peers, unsigned x) {
+  return (unsigned long long)__reduce_add_sync(peers, x);
+}
+
 __global__ void moments_kernel(const int* L, const int* slot, CamSet cs, long long* mom) {
-  __shared__ long long s_xy[8][32][2];
   const int v = blockIdx.y;
   const int W = cs.cam[v].width, H = cs.cam[v].height;
   const int P = W * H;
   const long long base = cs.pix_base[v];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   for (int u0 = blockIdx.x * blockDim.x; u0 < P; u0 += gridDim.x * blockDim.x) {
     const int u = u0 + threadIdx.x;
     int s = -1;
-    long long x = 0, y = 0;
+    unsigned x = 0, y = 0;
     if (u < P) {
       int r = L[base + u];
       if (r >= 0) {
         s = slot[r];
-        const int yy = u / W;
-        x = u - yy * W;
-        y = yy;
+        y = (unsigned)(u / W);
+        x = (unsigned)u - y * (unsigned)W;
       }
     }
     if (__ballot_sync(0xffffffffu, s >= 0) == 0) continue;  // no labelled pixel in this warp
-    unsigned peers = __match_any_sync(0xffffffffu, s);
-    s_xy[warp][lane][0] = x;
-    s_xy[warp][lane][1] = y;
-    __syncwarp();
-    if (s >= 0 && (peers & lanemask_lt()) == 0) {
-      long long a = 0, sx = 0, sy = 0, sxx = 0, sxy = 0, syy = 0;
-      for (unsigned m = peers; m; m &= m - 1) {
-        int l = __ffs(m) - 1;
-        long long xx = s_xy[warp][l][0], yy = s_xy[warp][l][1];
-        a += 1;
-        sx += xx;
-        sy += yy;
-        sxx += xx * xx;
-        sxy += xx * yy;
-        syy += yy * yy;
+    const unsigned peers = __match_any_sync(0xffffffffu, s);
+    if (s >= 0) {
+      // x = xh 2^8 + xl with xh, xl < 2^8: x^2 = xh^2 2^16 + 2 xh xl 2^8 + xl^2, and so on;
+      // every 32-lane partial sum below fits in 32 bits
+      const unsigned xh = x >> 8, xl = x & 255u, yh = y >> 8, yl = y & 255u;
+      const unsigned long long a = (unsigned long long)__popc(peers);
+      const unsigned long long sx = moment_sum(peers, x), sy = moment_sum(peers, y);
+      const unsigned long long sxx = (moment_sum(peers, xh * xh) << 16) +
+                                     (moment_sum(peers, 2u * xh * xl) << 8) +
+                                     moment_sum(peers, xl * xl);
+      const unsigned long long syy = (moment_sum(peers, yh * yh) << 16) +
+                                     (moment_sum(peers, 2u * yh * yl) << 8) +
+                                     moment_sum(peers, yl * yl);
+      const unsigned long long sxy = (moment_sum(peers, xh * yh) << 16) +
+                                     (moment_sum(peers, xh * yl + xl * yh) << 8) +
+                                     moment_sum(peers, xl * yl);
+      if ((peers & lanemask_lt()) == 0) {
+        unsigned long long* m6 = reinterpret_cast<unsigned long long*>(mom + 6LL * s);
+        atomicAdd(m6 + 0, a);
+        atomicAdd(m6 + 1, sx);
+        atomicAdd(m6 + 2, sy);
+        atomicAdd(m6 + 3, sxx);
+        atomicAdd(m6 + 4, sxy);
+        atomicAdd(m6 + 5, syy);
       }
-      unsigned long long* m6 = reinterpret_cast<unsigned long long*>(mom + 6LL * s);
-      atomicAdd(m6 + 0, (unsigned long long)a);
-      atomicAdd(m6 + 1, (unsigned long long)sx);
-      atomicAdd(m6 + 2, (unsigned long long)sy);
-      atomicAdd(m6 + 3, (unsigned long long)sxx);
-      atomicAdd(m6 + 4, (unsigned long long)sxy);
-      atomicAdd(m6 + 5, (unsigned long long)syy);
     }
-    __syncwarp();
+    (void)lane;
   }
 }
 
@@ -906,6 +933,9 @@ extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* do
   int rc = make_camset(cams, n_views, prm, &cs);
   if (rc) return rc;
   ADP_CHECK_ARG(prm->r_erode >= 0 && prm->r_erode <= 64, "r_erode must be 0..64");
+  for (int v = 0; v < n_views; ++v)  // the moment sums split coordinates into 8-bit halves
+    ADP_CHECK_ARG(cs.cam[v].width < 65536 && cs.cam[v].height < 65536,
+                  "image sides must be below 65536");
   long long P = total_pixels(cs);
   ADP_CHECK_ARG(P < (1LL << 31), "too many pixels");
   ADP_CHECK_ARG(aligned(ws, 256), "workspace must be 256-byte aligned");

@@ -577,6 +577,7 @@ static inline GaussPtrs gp_of(const adp_gaussians* g) {
 struct ApplyArgs {
   GaussPtrs in, min_, vin, out, mout, vout;
   GaussPtrs grad;  // with the fused Adam step: the gradients of in
+  const uint8_t* grad_rows;  // optional row mask of grad: 0 = zero gradient, not read
   AdamHyper adam;
   const long long* counters;  // [1] kept, [3] new size
   bool has_m_in, has_v_in, has_m_out, has_v_out;
@@ -612,32 +613,55 @@ __device__ __forceinline__ float4* plane_of(const GaussPtrs& g, int q, long long
 // With ADAM, each kept non-candidate row gets the update adp_adam_step makes,
 // bit for bit (candidates got theirs before the plan); moments in and out are
 // then required.
+#ifndef ADP_KEEP_ROWS
+#define ADP_KEEP_ROWS 1
+#endif
+constexpr int KEEP_ROWS = ADP_KEEP_ROWS;  // rows per thread (apart by the block size)
+
 template <bool ADAM>
 __global__ void apply_keep_kernel(ApplyArgs a) {
   const int q = blockIdx.y;
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= a.in.n) return;
-  // every load of the row first (the maps and the streams are independent), so a
-  // thread waits for one memory latency; removed candidate rows are read in vain
+  const long long i0 = blockIdx.x * (long long)blockDim.x * KEEP_ROWS + threadIdx.x;
+  // every independent load of the thread's rows first (the maps and the streams),
+  // then the gradients, whose loads wait only for the row mask; removed candidate
+  // rows are read in vain
   const long long n_new = a.counters[3];
-  const int c = a.cand_of[i];
-  const long long j = a.keep_new[i];
-  float4 p = *plane_of(a.in, q, i);
   const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 m = a.has_m_in ? *plane_of(a.min_, q, i) : z;
-  float4 v = a.has_v_in ? *plane_of(a.vin, q, i) : z;
-  float4 g = ADAM ? *plane_of(a.grad, q, i) : z;
-  if (n_new > a.out.n) return;  // the new population does not fit: write nothing
-  if (c >= 0 && a.status[c] != ADP_RESET) return;
-  if (j >= a.out.n) return;
-  if (ADAM && c < 0) {  // candidates got their step before the plan
-    float lr4[4];
-    adam_plane_lr(a.adam, q, lr4);
-    adam_vec4(p, g, m, v, lr4, a.adam, adam_bias(a.adam));
+  int c[KEEP_ROWS];
+  long long j[KEEP_ROWS];
+  bool gl[KEEP_ROWS];
+  float4 p[KEEP_ROWS], m[KEEP_ROWS], v[KEEP_ROWS], g[KEEP_ROWS];
+#pragma unroll
+  for (int r = 0; r < KEEP_ROWS; ++r) {
+    const long long i = i0 + (long long)r * blockDim.x;
+    const bool in = i < a.in.n;
+    c[r] = in ? a.cand_of[i] : 0;
+    j[r] = in ? a.keep_new[i] : a.out.n;
+    gl[r] = in && ADAM && (!a.grad_rows || a.grad_rows[i]);
+    p[r] = in ? *plane_of(a.in, q, i) : z;
+    m[r] = in && a.has_m_in ? *plane_of(a.min_, q, i) : z;
+    v[r] = in && a.has_v_in ? *plane_of(a.vin, q, i) : z;
   }
-  *plane_of(a.out, q, j) = p;
-  if (a.has_m_out) *plane_of(a.mout, q, j) = m;
-  if (a.has_v_out) *plane_of(a.vout, q, j) = v;
+#pragma unroll
+  for (int r = 0; r < KEEP_ROWS; ++r) {
+    const long long i = i0 + (long long)r * blockDim.x;
+    g[r] = gl[r] ? *plane_of(a.grad, q, i) : z;
+  }
+  if (n_new > a.out.n) return;  // the new population does not fit: write nothing
+#pragma unroll
+  for (int r = 0; r < KEEP_ROWS; ++r) {
+    if (i0 + (long long)r * blockDim.x >= a.in.n) continue;
+    if (c[r] >= 0 && a.status[c[r]] != ADP_RESET) continue;
+    if (j[r] >= a.out.n) continue;
+    if (ADAM && c[r] < 0) {  // candidates got their step before the plan
+      float lr4[4];
+      adam_plane_lr(a.adam, q, lr4);
+      adam_vec4(p[r], g[r], m[r], v[r], lr4, a.adam, adam_bias(a.adam));
+    }
+    *plane_of(a.out, q, j[r]) = p[r];
+    if (a.has_m_out) *plane_of(a.mout, q, j[r]) = m[r];
+    if (a.has_v_out) *plane_of(a.vout, q, j[r]) = v[r];
+  }
 }
 
 struct AppendArgs {
@@ -890,8 +914,10 @@ static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
   if (v_in) aa.vin = gp_of(v_in);
   if (m_out) aa.mout = gp_of(m_out);
   if (v_out) aa.vout = gp_of(v_out);
+  aa.grad_rows = nullptr;
   if (adam) {
     aa.grad = gp_of(grad);
+    aa.grad_rows = grad->rows;
     aa.adam = *adam;
   }
   aa.planes = planes;
@@ -900,10 +926,11 @@ static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
   aa.keep_new = w.keep_new;
   aa.counters = w.counters;
   if (n > 0) {
+    const dim3 kg(grid_for(n, 256 * KEEP_ROWS), 3 + planes);
     if (adam)
-      apply_keep_kernel<true><<<dim3(grid_for(n, 256), 3 + planes), 256, 0, st>>>(aa);
+      apply_keep_kernel<true><<<kg, 256, 0, st>>>(aa);
     else
-      apply_keep_kernel<false><<<dim3(grid_for(n, 256), 3 + planes), 256, 0, st>>>(aa);
+      apply_keep_kernel<false><<<kg, 256, 0, st>>>(aa);
   }
   if (nc > 0) {
     AppendArgs ap;

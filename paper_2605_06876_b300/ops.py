@@ -49,7 +49,7 @@ def workspace(nbytes, device="cuda"):
 class Gaussians:
     """Gaussian parameters (or gradients / Adam moments) as float4 planes."""
 
-    def __init__(self, n, sh_degree, device="cuda", zero=True):
+    def __init__(self, n, sh_degree, device="cuda", zero=True, row_mask=False):
         alloc = torch.zeros if zero else torch.empty
         self.n = int(n)
         self.sh_degree = int(sh_degree)
@@ -57,6 +57,9 @@ class Gaussians:
         self.logscale = alloc((self.n, 4), dtype=F32, device=device)
         self.quat = alloc((self.n, 4), dtype=F32, device=device)
         self.sh = alloc((sh_planes(sh_degree), self.n, 4), dtype=F32, device=device)
+        # gradients only: rows with rows[i] == 0 are zero and never touched
+        self.rows = (torch.zeros(self.n, dtype=torch.uint8, device=device) if row_mask
+                     else None)
 
     @classmethod
     def from_scene(cls, scene, device="cuda"):
@@ -97,9 +100,23 @@ class Gaussians:
             d.copy_(s)
         return g
 
+    def dense(self):
+        """The gradient with every masked-out row written as zero (a copy)."""
+        out = Gaussians(self.n, self.sh_degree, self.mean_logit.device, zero=False)
+        keep = (self.rows != 0) if self.rows is not None else None
+        for d, s in zip(out.tensors(), self.tensors()):
+            d.copy_(s)
+            if keep is not None:
+                if d.dim() == 3:
+                    d[:, ~keep] = 0
+                else:
+                    d[~keep] = 0
+        return out
+
     def c(self):
         return A.AdpGaussians(self.n, self.sh_degree, 0, _p(self.mean_logit), _p(self.logscale),
-                              _p(self.quat), _p(self.sh))
+                              _p(self.quat), _p(self.sh),
+                              _p(self.rows) if self.rows is not None else None)
 
 
 # --------------------------------------------------------------------------- buffers

@@ -83,7 +83,9 @@ class PlainStep:
         self.k = max(1, int(round(cand_frac * n)))
         self.P = ops.n_pixels(self.cams)
         self.m, self.v = g.zeros_like(), g.zeros_like()
-        self.grad = ops.Gaussians(n, g.sh_degree, self.dev, zero=False)
+        # the gradient carries a row mask: rows of Gaussians no view renders are
+        # neither written by the backward nor read by Adam
+        self.grad = ops.Gaussians(n, g.sh_degree, self.dev, zero=False, row_mask=True)
         self.pr = ops.Projected.alloc(self.V * n, self.dev)
         self.img = ops.Image.alloc(self.P, self.dev)
         self.maps = ops.ErrorMaps.alloc(self.P, self.V, self.dev)
@@ -208,7 +210,8 @@ class ViewStages:
         self.maps = ops.ErrorMaps.alloc(self.P, V, self.dev)
         self.count = torch.empty(n, dtype=torch.int32, device=self.dev)
         self.mass = torch.empty(n, dtype=torch.float64, device=self.dev)
-        self.grad = grad if grad is not None else ops.Gaussians(n, g.sh_degree, self.dev, zero=False)
+        self.grad = grad if grad is not None else ops.Gaussians(n, g.sh_degree, self.dev,
+                                                                zero=False, row_mask=True)
         ops.project(g, self.cams, self.params, self.pr)
         probe = ops.bin_sort(n, self.pr, self.cams, self.params)
         cap = int(int(probe.n_inst.item()) * bins_margin) + 1024
