@@ -201,7 +201,7 @@ def run_ours(args, rank, world, local_rank):
         if use_graph:
             out = stepper.replay()  # re-records the captured stage events
         else:
-            timer = StageTimer(stream)
+            timer = StageTimer()
             out = stepper.step(noise, timer)
         ev1.record(stream)
         torch.cuda.synchronize()

@@ -17,16 +17,17 @@ from . import ops
 
 
 class StageTimer:
-    """CUDA timing events between stages, on the stream the stages run on. The
-    events are recorded with cudaEventRecordExternal, so inside a CUDA-graph
-    capture they become event-record nodes and every replay re-records them: the
-    stage durations of the latest replay (or eager step) come from durations()."""
+    """CUDA timing events between stages, each recorded on the stream its stage
+    runs on (the current stream at mark time). Inside a CUDA-graph capture they
+    are recorded with cudaEventRecordExternal, so they become event-record nodes
+    and every replay re-records them: the stage durations of the latest replay (or
+    eager step) come from durations(), each from a mark to the next mark on the
+    same stream (the last mark of a stream only ends the previous stage)."""
 
-    def __init__(self, stream=None):
+    def __init__(self):
         from cuda.bindings import runtime as rt
 
         self.rt = rt
-        self.stream = stream
         self.events = []
 
     def mark(self, name):
@@ -34,7 +35,7 @@ class StageTimer:
         err, ev = rt.cudaEventCreateWithFlags(rt.cudaEventDefault)
         if err != rt.cudaError_t.cudaSuccess:
             raise RuntimeError(f"cudaEventCreateWithFlags: {err}")
-        st = self.stream or torch.cuda.current_stream()
+        st = torch.cuda.current_stream()
         # an external record (a node of the graph) inside a capture, a plain one outside
         err, cap = rt.cudaStreamIsCapturing(st.cuda_stream)
         if err != rt.cudaError_t.cudaSuccess:
@@ -44,20 +45,24 @@ class StageTimer:
         (err,) = rt.cudaEventRecordWithFlags(ev, st.cuda_stream, flags)
         if err != rt.cudaError_t.cudaSuccess:
             raise RuntimeError(f"cudaEventRecordWithFlags: {err}")
-        self.events.append((name, ev))
+        self.events.append((name, ev, st.cuda_stream))
 
     def durations(self):
         out = {}
-        for (name, a), (_, b) in zip(self.events[:-1], self.events[1:]):
-            err, ms = self.rt.cudaEventElapsedTime(a, b)
-            if err != self.rt.cudaError_t.cudaSuccess:
-                raise RuntimeError(f"cudaEventElapsedTime: {err}")
-            out[name] = out.get(name, 0.0) + ms
+        by_stream = {}
+        for name, ev, sid in self.events:
+            by_stream.setdefault(sid, []).append((name, ev))
+        for evs in by_stream.values():
+            for (name, a), (_, b) in zip(evs[:-1], evs[1:]):
+                err, ms = self.rt.cudaEventElapsedTime(a, b)
+                if err != self.rt.cudaError_t.cudaSuccess:
+                    raise RuntimeError(f"cudaEventElapsedTime: {err}")
+                out[name] = out.get(name, 0.0) + ms
         return out
 
     def __del__(self):
         try:
-            for _, ev in self.events:
+            for _, ev, _ in self.events:
                 self.rt.cudaEventDestroy(ev)
         except Exception:
             pass
@@ -94,6 +99,12 @@ class PlainStep:
         self.cand = torch.empty(self.k, dtype=torch.int32, device=self.dev)
         self.adam_t = torch.ones(1, dtype=torch.int32, device=self.dev)  # Adam step, on device
         self.graph = None
+        # the error-statistics chain (error map, top-k, regions) runs on a second
+        # stream, concurrently with the render backward: both need only the
+        # forward image. The chain is a string of small latency-bound kernels, so
+        # its stream has the higher priority: its blocks are scheduled ahead of
+        # the backward's waiting ones instead of queueing behind them
+        self.side = torch.cuda.Stream(device=self.dev, priority=-1)
         # size the instance and region buffers from one probing pass
         ops.project(g, self.cams, self.params, self.pr)
         probe = ops.bin_sort(n, self.pr, self.cams, self.params)
@@ -133,17 +144,23 @@ class PlainStep:
         ops.bin_sort(n, self.pr, cams, prm, bins=self.bins, ws=self.ws_bins, grow=False)
         mark("render")
         ops.render(n, self.pr, self.bins, cams, self.bg, prm, self.img)
-        mark("error_stats")
-        ops.error_stats(self.img.rgb, self.target, self.img.dominant, n, cams, prm, self.maps,
-                        self.count, self.mass)
-        mark("select_topk")
-        ops.select_topk(self.mass, n, self.k, self.cand, ws=self.ws_topk)
-        mark("error_regions")
-        ops.error_regions(self.maps, self.img.dominant, self.target, n, cams, self.cand, prm,
-                          regions=self.regions, ws=self.ws_regions, grow=False)
+        main = torch.cuda.current_stream()
+        self.side.wait_stream(main)  # fork after the forward
+        with torch.cuda.stream(self.side):
+            mark("error_stats")
+            ops.error_stats(self.img.rgb, self.target, self.img.dominant, n, cams, prm, self.maps,
+                            self.count, self.mass)
+            mark("select_topk")
+            ops.select_topk(self.mass, n, self.k, self.cand, ws=self.ws_topk)
+            mark("error_regions")
+            ops.error_regions(self.maps, self.img.dominant, self.target, n, cams, self.cand, prm,
+                              regions=self.regions, ws=self.ws_regions, grow=False)
+            mark("error_end")
         mark("render_backward")
         ops.render_backward(g, self.pr, self.bins, self.img, cams, target=self.target, bg=self.bg,
                             params=prm, grad=self.grad, ws=self.ws_bwd)
+        mark("join")
+        main.wait_stream(self.side)  # join before the candidates' Adam step and the split
         if self.fused_adam:
             mark("adam_rows")
             ops.adam_step_rows(g, self.grad, self.m, self.v, self.cand, self.adam_t, self.lr)
@@ -219,6 +236,7 @@ class ViewStages:
                                                      self.params.tile_h), self.dev)
         self.ws_bins = ops.workspace(ops.bin_sort_workspace_size(n, V, cap), self.dev)
         self.ws_bwd = ops.workspace(A.lib().adp_render_backward_workspace_size(n, V), self.dev)
+        self.side = torch.cuda.Stream(device=self.dev, priority=-1)
         torch.cuda.synchronize()
 
     def run(self):
@@ -226,10 +244,14 @@ class ViewStages:
         ops.project(g, cams, prm, self.pr)
         ops.bin_sort(n, self.pr, cams, prm, bins=self.bins, ws=self.ws_bins, grow=False)
         ops.render(n, self.pr, self.bins, cams, self.bg, prm, self.img)
-        ops.error_stats(self.img.rgb, self.target, self.img.dominant, n, cams, prm, self.maps,
-                        self.count, self.mass)
+        main = torch.cuda.current_stream()
+        self.side.wait_stream(main)  # error statistics beside the backward, as in PlainStep
+        with torch.cuda.stream(self.side):
+            ops.error_stats(self.img.rgb, self.target, self.img.dominant, n, cams, prm, self.maps,
+                            self.count, self.mass)
         ops.render_backward(g, self.pr, self.bins, self.img, cams, target=self.target, bg=self.bg,
                             params=prm, grad=self.grad, ws=self.ws_bwd)
+        main.wait_stream(self.side)
 
     def fits(self):
         return int(self.bins.n_inst.item()) <= self.bins.capacity

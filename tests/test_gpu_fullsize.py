@@ -1,0 +1,196 @@
+"""Parity at the workloads' full sizes, in the launch configuration the bench
+uses: sampled outputs against the oracle where it can compute them one by one,
+otherwise properties that hold at any size.
+
+- 2,000,000 Gaussians at 1280x832 (the hand-backward workload): the gradient of
+  sampled Gaussians against the oracle's FP64 gradient of the same Gaussians.
+- 3,000,000 Gaussians, 16 views of uneven resolution on a radius-5 hemisphere:
+  every view of the batched launch equals the view launched alone, and sampled
+  pixels of the smallest and largest view match the oracle's brute force.
+- 5,000,000 Gaussians, 8 views at 1280x832, 20% candidates: one full step (error
+  statistics over the 8 views, top-k, regions, AdpSplit with the fused Adam
+  compaction) checked by the invariants of each stage.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import scenes
+from gpu_util import DEV, gpu_forward, np_
+from paper_2605_06876_b300 import _abi as A
+from paper_2605_06876_b300 import ops
+from paper_2605_06876_b300.pipeline import PlainStep
+
+pytestmark = pytest.mark.gpu
+
+
+def _near_gaussians(theta, cam, count):
+    """The nearest visible Gaussians whose pixel box holds 400 to 20,000 pixels:
+    near enough not to be hidden behind the splats in front (the scene surrounds
+    the camera, so far ones are often fully occluded), small enough that the
+    oracle's complex-step gradient, whose cost grows with the box, stays cheap."""
+    pr = O.project(theta, 3, cam)
+    vis = np.nonzero(pr["tiles"] > 0)[0]
+    b = pr["box"][vis]
+    area = (b[:, 1] - b[:, 0] + 1).astype(np.float64) * (b[:, 3] - b[:, 2] + 1)
+    pool = vis[(area >= 400) & (area <= 20000)]
+    order = pool[np.argsort(pr["depth"][pool], kind="stable")]
+    return np.sort(order[:count]).astype(np.int32)
+
+
+def test_backward_2m_full_size_sampled_gaussians():
+    cfg = scenes.CONFIGS[2]
+    sc = scenes.scene_clusters(4, cfg["n"], cfg["sh_degree"])
+    cam = scenes.ring_cameras(5, 1, cfg["ring_radius"], cfg["width"], cfg["height"])[0]
+    _, target, _ = scenes.error_stage_inputs(5, cfg["width"], cfg["height"], 1)
+    g, pr, bins, img = gpu_forward(sc, [cam])
+    tgt = torch.as_tensor(target.reshape(-1, 3), device=DEV)
+    grad = ops.render_backward(g, pr, bins, img, [cam], target=tgt)
+    torch.cuda.synchronize()
+    theta = O.theta_of(sc)
+    sel = _near_gaussians(theta, cam, 8)
+    got = O.theta_of(grad.to_scene())[sel]
+    want = O.grad(theta, 3, cam, target, sel=sel)
+    row_max = np.abs(want).max(1)
+    assert (row_max > 0).sum() >= 3  # most of them contribute to some pixel
+    for r in range(len(sel)):  # each Gaussian against its own gradient's scale
+        tol = 2e-3 * row_max[r] + 1e-13
+        assert np.abs(got[r] - want[r]).max() <= tol, (int(sel[r]), np.abs(got[r] - want[r]).max(), tol)
+
+
+def test_batched_uneven_views_3m_full_size():
+    cfg = scenes.CONFIGS[3]
+    sc = scenes.scene_clusters(6, cfg["n"], cfg["sh_degree"])
+    res = scenes.uneven_resolutions(7, cfg["views"])
+    cams = scenes.hemisphere_cameras(7, cfg["views"], cfg["hemisphere_radius"], res)
+    g = ops.Gaussians.from_scene(sc, DEV)
+    pr = ops.project(g, cams)
+    bins = ops.bin_sort(g.n, pr, cams)
+    img = ops.render(g.n, pr, bins, cams)
+    torch.cuda.synchronize()
+    offs = np.cumsum([0] + [c["width"] * c["height"] for c in cams])
+    for v, cam in enumerate(cams):  # each view of the batched launch equals the view alone
+        pv = ops.project(g, [cam])
+        bv = ops.bin_sort(g.n, pv, [cam])
+        iv = ops.render(g.n, pv, bv, [cam])
+        torch.cuda.synchronize()
+        assert torch.equal(img.rgb[offs[v]:offs[v + 1]], iv.rgb)
+        assert torch.equal(img.dominant[offs[v]:offs[v + 1]], iv.dominant)
+        del pv, bv, iv
+    sizes = [c["width"] * c["height"] for c in cams]
+    theta = O.theta_of(sc)
+    rng = np.random.default_rng(3)
+    for v in (int(np.argmin(sizes)), int(np.argmax(sizes))):
+        cam = cams[v]
+        pix = rng.choice(sizes[v], 60, replace=False)
+        o = O.render(O.project(theta, 3, cam), cam, pixels=pix)
+        idx = torch.as_tensor(offs[v] + pix, device=DEV)
+        rgb, dom = np_(img.rgb[idx]), np_(img.dominant[idx])
+        tie = o["tie"] != 0
+        assert tie.mean() <= 0.05
+        assert np.abs(rgb - o["rgb"]).max(1)[~tie].max() <= 2e-4
+        assert np.array_equal(dom[~tie], o["dominant"][~tie])
+
+
+def test_densification_round_5m_8_views_invariants():
+    cfg = scenes.CONFIGS[4]
+    sc = scenes.scene_clusters(8, cfg["n"], cfg["sh_degree"])
+    cams = scenes.ring_cameras(9, cfg["views"], cfg["ring_radius"], cfg["width"], cfg["height"])
+    tg = ops.Gaussians.from_scene(scenes.scene_clusters(9, cfg["n"] * 3 // 2, 3), DEV)
+    prt = ops.project(tg, cams)
+    target = ops.render(tg.n, prt, ops.bin_sort(tg.n, prt, cams), cams).rgb.clone()
+    del tg, prt
+    g0 = ops.Gaussians.from_scene(sc, DEV)
+    st = PlainStep(g0, cams, target, cfg["cand_frac"])
+    g_before = st.g.clone()
+    m_before, v_before = st.m.clone(), st.v.clone()
+    noise = torch.as_tensor(scenes.fallback_noise(10, st.k), device=DEV)
+    out, m_out, v_out, plan = st.step(noise)
+    torch.cuda.synchronize()
+    assert st.check_capacity(plan)
+    n, k, nmax = st.g.n, st.k, st.params.n_max
+
+    # error statistics: counts are the pre-erosion error pixels per dominant Gaussian
+    M = (st.maps.mask & 1).bool()
+    D = st.img.dominant.long()
+    att = M & (D >= 0)
+    assert int(st.count.sum()) == int(att.sum())
+    hist = torch.bincount(D[att], minlength=n)
+    assert torch.equal(hist.to(torch.int32), st.count)
+    assert bool(((st.mass > 0) <= (st.count > 0)).all())
+
+    # top-k by mass, ties to the lower id
+    cand = st.cand.long()
+    assert cand.numel() == k and bool((cand[1:] > cand[:-1]).all())
+    sel = torch.zeros(n, dtype=torch.bool, device=DEV)
+    sel[cand] = True
+    thr = st.mass[cand].min()
+    assert float(st.mass[~sel].max()) <= float(thr)
+    at_thr = torch.nonzero(st.mass == thr).flatten()
+    n_above = int((st.mass > thr).sum())
+    assert torch.equal(torch.nonzero(sel & (st.mass == thr)).flatten(), at_thr[:k - n_above])
+
+    # statuses and child counts
+    status, nch = plan.status.long(), plan.n_children.long()
+    cnt = st.count[cand]
+    assert bool(((status == A.ADP_FALLBACK) == (cnt == 0)).all())
+    adaptive = status == A.ADP_ADAPTIVE
+    assert bool((nch[adaptive] >= 1).all()) and bool((nch[adaptive] <= nmax).all())
+    assert not bool(nch[~adaptive].any())
+    fb = int((status == A.ADP_FALLBACK).sum())
+    new_n = int(plan.d_new_n.item())
+    assert new_n == n + fb + int(nch[adaptive].sum())
+    assert int(adaptive.sum()) > 0 and fb > 0
+
+    # kept rows: every non-candidate and RESET Gaussian, in id order, after one
+    # Adam step that equals the unfused step on the same gradient
+    keep = ~sel
+    keep[cand[status == A.ADP_RESET]] = True
+    ref, mr, vr = g_before.clone(), m_before.clone(), v_before.clone()
+    ops.adam_step(ref, st.grad, mr, vr, 1, st.lr)
+    torch.cuda.synchronize()
+    nk = int(keep.sum())
+    for a, b in ((out, ref), (m_out, mr), (v_out, vr)):
+        for ta, tb in zip(a.tensors(), b.tensors()):
+            if ta.dim() == 3:
+                assert torch.equal(ta[:, :nk], tb[:, keep])
+            else:
+                assert torch.equal(ta[:nk], tb[keep])
+
+    # appended rows: zero moments; the two vanilla children of sampled FALLBACK
+    # candidates follow mu + R (s * noise), log s - log(2 eta) of the updated parent
+    for t in m_out.tensors() + v_out.tensors():
+        part = t[:, nk:new_n] if t.dim() == 3 else t[nk:new_n]
+        assert not bool(part.any())
+    rows = (torch.where(status == A.ADP_ADAPTIVE, 1 + nch,
+                        torch.where(status == A.ADP_FALLBACK, 2, 0)))
+    start = nk + torch.cumsum(rows, 0) - rows
+    ml_o, ls_o = np_(out.mean_logit), np_(out.logscale)
+    ml_p, ls_p, q_p = np_(ref.mean_logit), np_(ref.logscale), np_(ref.quat)
+    nz = np_(noise).reshape(-1, 2, 3)
+    fb_idx = np.nonzero(np_(status) == A.ADP_FALLBACK)[0]
+    rng = np.random.default_rng(11)
+    # candidates got their Adam step before the plan: the parent is the updated row
+    for c in rng.choice(fb_idx, 50, replace=False):
+        i = int(cand[c])
+        R = O.quat_to_rot(q_p[i][None].astype(np.float64))[0]
+        s = np.exp(ls_p[i, :3].astype(np.float64))
+        for kk in range(2):
+            j = int(start[c]) + kk
+            mu = ml_p[i, :3].astype(np.float64) + R @ (s * nz[c, kk])
+            np.testing.assert_allclose(ml_o[j, :3], mu, rtol=1e-6, atol=1e-6)
+            np.testing.assert_allclose(ls_o[j, :3], ls_p[i, :3] - math.log(2 * st.params.eta),
+                                       rtol=1e-6, atol=1e-6)
+    # ADAPTIVE: parent copy with opacity o / (N + 1); children no larger than the parent
+    ad_idx = np.nonzero(np_(adaptive))[0]
+    for c in ad_idx[:200]:
+        i, j, N = int(cand[c]), int(start[c]), int(nch[c])
+        o = 1.0 / (1.0 + math.exp(-float(ml_p[i, 3])))
+        on = o / (N + 1)
+        np.testing.assert_allclose(ml_o[j, 3], math.log(on / (1.0 - on)), rtol=1e-5, atol=1e-5)
+        smax = float(np.exp(ls_p[i, :3].astype(np.float64)).max())
+        kids = np.exp(ls_o[j + 1:j + 1 + N, :3].astype(np.float64))
+        assert kids.max() <= smax * (1 + 1e-5)
