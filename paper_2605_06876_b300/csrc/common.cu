@@ -213,10 +213,101 @@ __global__ void __launch_bounds__(RS_THREADS)
   }
 }
 
+// Stable LSD radix sort of at most SMALL_SORT_MAX pairs in one block of 1024
+// threads (the data stay in global memory, L2-resident at this size): per pass a
+// shared histogram, its exclusive scan, then rounds of 1024 items in order, each
+// ranked by warp match masks and per-warp digit counts, so equal digits keep
+// their order. Results end in (ka, va).
+__global__ void __launch_bounds__(1024)
+    small_sort_kernel(unsigned* ka, unsigned* va, unsigned* kb, unsigned* vb, const long long* d_n,
+                      long long n_max, SmallPasses passes) {
+  __shared__ unsigned s_base[RS_BINS];
+  __shared__ unsigned s_run[RS_BINS];
+  __shared__ unsigned s_wc[32][RS_BINS];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  long long N = *d_n;
+  if (N > n_max) N = n_max;
+  const unsigned lt = lanemask_lt();
+  unsigned *src_k = ka, *src_v = va, *dst_k = kb, *dst_v = vb;
+  for (int p = 0; p < passes.count; ++p) {
+    const DigitOp op = passes.op[p];
+    if (t < RS_BINS) {
+      s_base[t] = 0u;
+      s_run[t] = 0u;
+    }
+    __syncthreads();
+    for (long long i = t; i < N; i += 1024) atomicAdd(&s_base[op(src_k[i], src_v[i])], 1u);
+    __syncthreads();
+    if (t < 32) {  // exclusive scan of the 256 bins, 8 per lane
+      unsigned c[8], sum = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        c[q] = s_base[8 * t + q];
+        sum += c[q];
+      }
+      unsigned inc = sum;
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      unsigned run = inc - sum;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        s_base[8 * t + q] = run;
+        run += c[q];
+      }
+    }
+    __syncthreads();
+    for (long long r0 = 0; r0 < N; r0 += 1024) {
+      for (int q = t; q < 32 * RS_BINS; q += 1024) (&s_wc[0][0])[q] = 0u;
+      __syncthreads();
+      const long long i = r0 + t;
+      const bool valid = i < N;
+      const unsigned k = valid ? src_k[i] : 0u, v = valid ? src_v[i] : 0u;
+      const unsigned d = valid ? op(k, v) : (unsigned)RS_BINS;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const unsigned rank = __popc(peers & lt);
+      if (valid && rank == 0) s_wc[warp][d] = __popc(peers);
+      __syncthreads();
+      if (t < RS_BINS) {  // prefix over warps, continuing the digit's running count
+        unsigned run = s_run[t];
+        for (int w = 0; w < 32; ++w) {
+          const unsigned c = s_wc[w][t];
+          s_wc[w][t] = run;
+          run += c;
+        }
+        s_run[t] = run;
+      }
+      __syncthreads();
+      if (valid) {
+        const unsigned pos = s_base[d] + s_wc[warp][d] + rank;
+        dst_k[pos] = k;
+        dst_v[pos] = v;
+      }
+      __syncthreads();
+    }
+    unsigned* tk = src_k; src_k = dst_k; dst_k = tk;
+    unsigned* tv = src_v; src_v = dst_v; dst_v = tv;
+  }
+  if (src_k != ka)  // odd pass count: copy back
+    for (long long i = t; i < N; i += 1024) {
+      ka[i] = src_k[i];
+      va[i] = src_v[i];
+    }
+}
+
 int radix_sort_pairs(unsigned* keys, unsigned* vals, const long long* d_n, long long n_max,
                      const DigitOp* passes, int n_passes, const SortWorkspace& w,
                      cudaStream_t st) {
   if (n_max <= 0 || n_passes <= 0) return ADP_OK;
+  if (n_max <= SMALL_SORT_MAX && n_passes <= 4) {  // one launch for a small sort
+    SmallPasses sp;
+    sp.count = n_passes;
+    for (int p = 0; p < n_passes; ++p) sp.op[p] = passes[p];
+    small_sort_kernel<<<1, 1024, 0, st>>>(keys, vals, w.keys_alt, w.vals_alt, d_n, n_max, sp);
+    ADP_LAUNCH_CHECK();
+    return ADP_OK;
+  }
   unsigned *ka = keys, *va = vals, *kb = w.keys_alt, *vb = w.vals_alt;
   long long grid = w.tiles_max < 148 * 8 ? w.tiles_max : 148 * 8;
   for (int p = 0; p < n_passes; ++p) {

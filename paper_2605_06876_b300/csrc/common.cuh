@@ -115,7 +115,10 @@ __device__ __forceinline__ T warp_sum(T v) {
 // that runs out sets *err and leaves the result undefined. The count is a host
 // value or read from device memory (d_n != nullptr, n an upper bound).
 constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_ITEMS = 16;
+#ifndef ADP_SCAN_ITEMS
+#define ADP_SCAN_ITEMS 4
+#endif
+constexpr int SCAN_ITEMS = ADP_SCAN_ITEMS;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 constexpr unsigned long long SCAN_FLAG_A = 1ull << 62;  // tile total published
 constexpr unsigned long long SCAN_FLAG_P = 2ull << 62;  // inclusive prefix published
@@ -292,6 +295,13 @@ struct DigitOp {
   }
 };
 
+// Up to four passes of a small sort (one launch; see small_sort_kernel).
+constexpr long long SMALL_SORT_MAX = 8192;
+struct SmallPasses {
+  DigitOp op[4];
+  int count;
+};
+
 __global__ void rs_hist_kernel(const unsigned* keys, const unsigned* vals, const long long* d_n,
                                long long tiles_max, DigitOp op, unsigned* hist);
 __global__ void rs_scan_kernel(unsigned* hist, const long long* d_n, long long tiles_max,
@@ -302,7 +312,8 @@ __global__ void rs_scatter_kernel(const unsigned* keys_in, const unsigned* vals_
                                   const unsigned* digit_tot);
 
 // Sorts (keys, vals) in place by the given passes. passes[k] is a DigitOp;
-// n_max bounds the device count *d_n.
+// n_max bounds the device count *d_n. Up to SMALL_SORT_MAX items (and four
+// passes) the sort runs in a single one-block launch.
 int radix_sort_pairs(unsigned* keys, unsigned* vals, const long long* d_n, long long n_max,
                      const DigitOp* passes, int n_passes, const SortWorkspace& w, cudaStream_t st);
 

@@ -5,7 +5,8 @@
 //    mass) with warp-aggregated integer atomics (mass in exact fixed point);
 //  - top-k error mass by a radix select on the 64-bit mass keys, in one
 //    cooperative launch;
-//  - erosion (separable min filter), 8-connected labelling by a union-find whose
+//  - erosion (a min filter over the tile and its halo in shared memory),
+//    8-connected labelling by a union-find whose
 //    roots are the smallest pixel index of each component (per 32x32 tile in
 //    shared memory first, then across tile borders in global memory),
 //    exact int64 region moments, the area filter and the FP64 region statistics.
@@ -410,37 +411,45 @@ static int topk_coop_run(const double* mass, long long n, long long k, int32_t* 
 // ------------------------------------------------------------------ erosion
 
 // Horizontal then vertical AND over radius r; outside the image counts as set.
-__global__ void erode_h_kernel(const uint8_t* mask, uint8_t* tmp, CamSet cs, int r) {
-  const int v = blockIdx.y;
-  const int W = cs.cam[v].width, H = cs.cam[v].height;
-  const int P = W * H;  // a view has fewer than 2^31 pixels (checked by the caller)
-  const long long base = cs.pix_base[v];
-  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < P; u += gridDim.x * blockDim.x) {
-    const int x = u % W;
-    const uint8_t* row = mask + base + (u - x);
-    uint8_t ok = 1;
-    for (int d = -r; d <= r && ok; ++d) {
-      int xx = x + d;
-      if (xx >= 0 && xx < W) ok = row[xx] & 1;
-    }
-    tmp[base + u] = ok;
-  }
-}
+// Erosion of M into mask bit 1: a pixel stays set iff every pixel of its
+// (2r+1)x(2r+1) window is set, pixels outside the image counting as set. One
+// 32x32 output tile per block: the tile and its r-wide halo are staged in shared
+// memory, eroded along rows, then along columns.
+constexpr int ERODE_T = 32;
+constexpr int ERODE_RMAX = 64;
 
-__global__ void erode_v_kernel(const uint8_t* tmp, uint8_t* mask, CamSet cs, int r) {
+__global__ void __launch_bounds__(256) erode_kernel(uint8_t* mask, CamSet cs, int r) {
+  __shared__ uint8_t s_in[(ERODE_T + 2 * ERODE_RMAX) * (ERODE_T + 2 * ERODE_RMAX)];
+  __shared__ uint8_t s_row[(ERODE_T + 2 * ERODE_RMAX) * ERODE_T];
   const int v = blockIdx.y;
   const int W = cs.cam[v].width, H = cs.cam[v].height;
-  const int P = W * H;
+  const int ntx = (W + ERODE_T - 1) / ERODE_T, nty = (H + ERODE_T - 1) / ERODE_T;
+  if ((int)blockIdx.x >= ntx * nty) return;
+  const int x0 = (blockIdx.x % ntx) * ERODE_T, y0 = (blockIdx.x / ntx) * ERODE_T;
   const long long base = cs.pix_base[v];
-  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < P; u += gridDim.x * blockDim.x) {
-    const int y = u / W, x = u - y * W;
+  const int E = ERODE_T + 2 * r;  // staged edge
+  for (int q = threadIdx.x; q < E * E; q += blockDim.x) {
+    const int yy = y0 - r + q / E, xx = x0 - r + q % E;
+    s_in[q] = (xx < 0 || yy < 0 || xx >= W || yy >= H) ? 1
+                                                        : (mask[base + (long long)yy * W + xx] & 1);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < E * ERODE_T; q += blockDim.x) {  // rows: E x 32
+    const int ry = q / ERODE_T, cx = q % ERODE_T;
     uint8_t ok = 1;
-    for (int d = -r; d <= r && ok; ++d) {
-      int yy = y + d;
-      if (yy >= 0 && yy < H) ok = tmp[base + (long long)yy * W + x];
-    }
-    uint8_t m = mask[base + u];
-    mask[base + u] = (uint8_t)((m & ~2) | (ok ? 2 : 0));
+    for (int d = 0; d <= 2 * r && ok; ++d) ok = s_in[ry * E + cx + d];
+    s_row[q] = ok;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < ERODE_T * ERODE_T; q += blockDim.x) {  // columns
+    const int cy = q / ERODE_T, cx = q % ERODE_T;
+    const int x = x0 + cx, y = y0 + cy;
+    if (x >= W || y >= H) continue;
+    uint8_t ok = 1;
+    for (int d = 0; d <= 2 * r && ok; ++d) ok = s_row[(cy + d) * ERODE_T + cx];
+    const long long p = base + (long long)y * W + x;
+    const uint8_t m = mask[p];
+    mask[p] = (uint8_t)((m & ~2) | (ok ? 2 : 0));
   }
 }
 
@@ -534,10 +543,13 @@ __device__ void sunite(int* l, int a, int b) {
 // component's root is its smallest pixel index.
 __global__ void __launch_bounds__(256) ccl_local_kernel(const uint8_t* mask, const int* dom,
                                                         const uint8_t* cand, long long n,
-                                                        CamSet cs, int* L) {
+                                                        CamSet cs, int* L, long long* part,
+                                                        int* lroots,
+                                                        unsigned long long* n_lroots) {
   __shared__ int s_l[CCL_T * CCL_T];
   __shared__ int s_d[CCL_T * CCL_T];
   __shared__ uint8_t s_b[CCL_T * CCL_T];
+  __shared__ unsigned s_m[6][CCL_T * CCL_T];  // tile-local moments per local root
   const int v = blockIdx.y;
   const int W = cs.cam[v].width, H = cs.cam[v].height;
   const int ntx = (W + CCL_T - 1) / CCL_T, nty = (H + CCL_T - 1) / CCL_T;
@@ -560,6 +572,8 @@ __global__ void __launch_bounds__(256) ccl_local_kernel(const uint8_t* mask, con
     s_l[li] = lab;
     s_d[li] = d;
     s_b[li] = b;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s_m[k][li] = 0u;
   }
   __syncthreads();
   auto same = [&](int a, int q) { return s_l[q] >= 0 && s_d[q] == s_d[a] && s_b[q] == s_b[a]; };
@@ -587,31 +601,85 @@ __global__ void __launch_bounds__(256) ccl_local_kernel(const uint8_t* mask, con
     if (upright && !up) sunite(s_l, li, li - CCL_T + 1);
   }
   __syncthreads();
+  // labels, and the moments of each tile-local component in tile coordinates
+  // (below 32, so 32-lane sums of squares fit 32 bits): one warp reduction per
+  // moment and group of lanes with the same local root, then shared atomics
   for (int li = threadIdx.x; li < CCL_T * CCL_T; li += blockDim.x) {
     int x = tx0 + (li & (CCL_T - 1)), y = ty0 + li / CCL_T;
-    if (x >= W || y >= H) continue;
-    int lab = -1;
-    if (s_l[li] >= 0) {
-      int r = sfind(s_l, li);
-      int rx = tx0 + (r & (CCL_T - 1)), ry = ty0 + r / CCL_T;
-      lab = (int)(base + (long long)ry * W + rx);
+    int r = -1;
+    if (x < W && y < H) {
+      int lab = -1;
+      if (s_l[li] >= 0) {
+        r = sfind(s_l, li);
+        int rx = tx0 + (r & (CCL_T - 1)), ry = ty0 + r / CCL_T;
+        lab = (int)(base + (long long)ry * W + rx);
+      }
+      L[base + (long long)y * W + x] = lab;
     }
-    L[base + (long long)y * W + x] = lab;
+    const unsigned peers = __match_any_sync(0xffffffffu, r);
+    if (r >= 0) {
+      const unsigned lx = (unsigned)(li & (CCL_T - 1)), ly = (unsigned)(li / CCL_T);
+      const unsigned m0 = __popc(peers), m1 = __reduce_add_sync(peers, lx);
+      const unsigned m2 = __reduce_add_sync(peers, ly), m3 = __reduce_add_sync(peers, lx * lx);
+      const unsigned m4 = __reduce_add_sync(peers, lx * ly), m5 = __reduce_add_sync(peers, ly * ly);
+      if ((peers & lanemask_lt()) == 0) {
+        atomicAdd(&s_m[0][r], m0);
+        atomicAdd(&s_m[1][r], m1);
+        atomicAdd(&s_m[2][r], m2);
+        atomicAdd(&s_m[3][r], m3);
+        atomicAdd(&s_m[4][r], m4);
+        atomicAdd(&s_m[5][r], m5);
+      }
+    }
+  }
+  __syncthreads();
+  // every local root: its moments in image coordinates (exact int64) and a list entry
+  for (int li = threadIdx.x; li < CCL_T * CCL_T; li += blockDim.x) {
+    if (s_l[li] != li) continue;  // participating roots point at themselves
+    const long long X0 = tx0, Y0 = ty0;
+    const long long A = s_m[0][li], sx = s_m[1][li], sy = s_m[2][li];
+    const long long sxx = s_m[3][li], sxy = s_m[4][li], syy = s_m[5][li];
+    const int x = tx0 + (li & (CCL_T - 1)), y = ty0 + li / CCL_T;
+    const long long p = base + (long long)y * W + x;
+    long long* m6 = part + 6 * p;
+    m6[0] = A;
+    m6[1] = A * X0 + sx;
+    m6[2] = A * Y0 + sy;
+    m6[3] = A * X0 * X0 + 2 * X0 * sx + sxx;
+    m6[4] = A * X0 * Y0 + X0 * sy + Y0 * sx + sxy;
+    m6[5] = A * Y0 * Y0 + 2 * Y0 * sy + syy;
+    lroots[atomicAdd(n_lroots, 1ull)] = (int)p;
   }
 }
 
 // The edges of the 8-neighbourhood that cross a tile border, with the same skip
-// rules, joined in the global union-find.
+// rules, joined in the global union-find. Only the pixels on a tile's top row,
+// left column and right column own such edges: CCL_BORDER of them per tile, one
+// thread each.
+constexpr int CCL_BORDER = 3 * CCL_T - 2;
+
 __global__ void ccl_border_kernel(const uint8_t* mask, const int* dom, CamSet cs, int* L) {
   const int v = blockIdx.y;
   const int W = cs.cam[v].width, H = cs.cam[v].height;
-  const int P = W * H;
+  const int ntx = (W + CCL_T - 1) / CCL_T, nty = (H + CCL_T - 1) / CCL_T;
   const long long base = cs.pix_base[v];
-  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < P; u += gridDim.x * blockDim.x) {
-    const int y = u / W, x = u - y * W;
-    int lx = x & (CCL_T - 1), ly = y & (CCL_T - 1);
-    if (lx != 0 && ly != 0 && lx != CCL_T - 1) continue;
-    long long p = base + u;
+  const int total = ntx * nty * CCL_BORDER;
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x) {
+    const int tile = u / CCL_BORDER, k = u - tile * CCL_BORDER;
+    int lx, ly;
+    if (k < CCL_T) {  // top row
+      lx = k;
+      ly = 0;
+    } else if (k < 2 * CCL_T - 1) {  // left column below the corner
+      lx = 0;
+      ly = k - CCL_T + 1;
+    } else {  // right column below the corner
+      lx = CCL_T - 1;
+      ly = k - 2 * CCL_T + 2;
+    }
+    const int x = (tile % ntx) * CCL_T + lx, y = (tile / ntx) * CCL_T + ly;
+    if (x >= W || y >= H) continue;
+    long long p = base + (long long)y * W + x;
     if (L[p] < 0) continue;
     bool left = x > 0 && same_class(L, dom, mask, p, p - 1);
     bool up = y > 0 && same_class(L, dom, mask, p, p - W);
@@ -640,61 +708,20 @@ __global__ void zero_i64_kernel(long long* p, const long long* d_n, int per) {
     p[i] = 0;
 }
 
-// Exact int64 moments per root. Pixels of a warp that share a root are summed
-// with one warp reduction per moment (__reduce_add_sync on 32-bit integers:
-// coordinates are below 2^16, so 32 squares or products stay below 2^37 only in
-// the worst case -- hence x and y are split into 8-bit halves for the second
-// moments, each partial sum fitting 32 bits), then added to the int64 totals.
-__device__ __forceinline__ unsigned long long moment_sum(unsigned peers, unsigned x) {
-  return (unsigned long long)__reduce_add_sync(peers, x);
-}
-
-__global__ void moments_kernel(const int* L, const int* slot, CamSet cs, long long* mom) {
-  const int v = blockIdx.y;
-  const int W = cs.cam[v].width, H = cs.cam[v].height;
-  const int P = W * H;
-  const long long base = cs.pix_base[v];
-  const int lane = threadIdx.x & 31;
-  for (int u0 = blockIdx.x * blockDim.x; u0 < P; u0 += gridDim.x * blockDim.x) {
-    const int u = u0 + threadIdx.x;
-    int s = -1;
-    unsigned x = 0, y = 0;
-    if (u < P) {
-      int r = L[base + u];
-      if (r >= 0) {
-        s = slot[r];
-        y = (unsigned)(u / W);
-        x = (unsigned)u - y * (unsigned)W;
-      }
-    }
-    if (__ballot_sync(0xffffffffu, s >= 0) == 0) continue;  // no labelled pixel in this warp
-    const unsigned peers = __match_any_sync(0xffffffffu, s);
-    if (s >= 0) {
-      // x = xh 2^8 + xl with xh, xl < 2^8: x^2 = xh^2 2^16 + 2 xh xl 2^8 + xl^2, and so on;
-      // every 32-lane partial sum below fits in 32 bits
-      const unsigned xh = x >> 8, xl = x & 255u, yh = y >> 8, yl = y & 255u;
-      const unsigned long long a = (unsigned long long)__popc(peers);
-      const unsigned long long sx = moment_sum(peers, x), sy = moment_sum(peers, y);
-      const unsigned long long sxx = (moment_sum(peers, xh * xh) << 16) +
-                                     (moment_sum(peers, 2u * xh * xl) << 8) +
-                                     moment_sum(peers, xl * xl);
-      const unsigned long long syy = (moment_sum(peers, yh * yh) << 16) +
-                                     (moment_sum(peers, 2u * yh * yl) << 8) +
-                                     moment_sum(peers, yl * yl);
-      const unsigned long long sxy = (moment_sum(peers, xh * yh) << 16) +
-                                     (moment_sum(peers, xh * yl + xl * yh) << 8) +
-                                     moment_sum(peers, xl * yl);
-      if ((peers & lanemask_lt()) == 0) {
-        unsigned long long* m6 = reinterpret_cast<unsigned long long*>(mom + 6LL * s);
-        atomicAdd(m6 + 0, a);
-        atomicAdd(m6 + 1, sx);
-        atomicAdd(m6 + 2, sy);
-        atomicAdd(m6 + 3, sxx);
-        atomicAdd(m6 + 4, sxy);
-        atomicAdd(m6 + 5, syy);
-      }
-    }
-    (void)lane;
+// Exact int64 moments per root: the tile-local components' moments, which the
+// labelling kernel left at their local roots, added to the slot of the final root.
+__global__ void moments_kernel(const int* lroots, const unsigned long long* n_lroots,
+                               const long long* part, const int* L, const int* slot,
+                               long long* mom) {
+  const long long N = (long long)*n_lroots;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int p = lroots[t];
+    const int s = slot[L[p]];
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(part + 6LL * p);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(mom + 6LL * s);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) atomicAdd(dst + k, src[k]);
   }
 }
 
@@ -895,16 +922,17 @@ struct RegionWs {
   int* slot;
   int* root_pix;
   long long* mom;
+  long long* part;  // [6P] moments of tile-local components, at their local roots
+  int* lroots;      // [P] the local roots
   long long* kept_idx;
   uint8_t* cand;
-  uint8_t* tmp;
   void* scan;
-  long long* counters;
+  long long* counters;  // [0] roots, [2] local roots
 };
 
 static size_t region_ws_bytes(long long n, long long P) {
-  return 3 * carve_bytes<int>(P) + carve_bytes<long long>(6 * P) + carve_bytes<long long>(P) +
-         carve_bytes<uint8_t>(n) + carve_bytes<uint8_t>(P) + scan_workspace_bytes(P) +
+  return 3 * carve_bytes<int>(P) + 2 * carve_bytes<long long>(6 * P) + carve_bytes<int>(P) +
+         carve_bytes<long long>(P) + carve_bytes<uint8_t>(n) + scan_workspace_bytes(P) +
          carve_bytes<long long>(4);
 }
 
@@ -932,7 +960,7 @@ extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* do
   CamSet cs;
   int rc = make_camset(cams, n_views, prm, &cs);
   if (rc) return rc;
-  ADP_CHECK_ARG(prm->r_erode >= 0 && prm->r_erode <= 64, "r_erode must be 0..64");
+  ADP_CHECK_ARG(prm->r_erode >= 0 && prm->r_erode <= ERODE_RMAX, "r_erode must be 0..64");
   for (int v = 0; v < n_views; ++v)  // the moment sums split coordinates into 8-bit halves
     ADP_CHECK_ARG(cs.cam[v].width < 65536 && cs.cam[v].height < 65536,
                   "image sides must be below 65536");
@@ -948,16 +976,23 @@ extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* do
   w.slot = c.take<int>(P);
   w.root_pix = c.take<int>(P);
   w.mom = c.take<long long>(6 * P);
+  w.part = c.take<long long>(6 * P);
+  w.lroots = c.take<int>(P);
   w.kept_idx = c.take<long long>(P);
   w.cand = c.take<uint8_t>(n);
-  w.tmp = c.take<uint8_t>(P);
   w.scan = c.take<char>(scan_workspace_bytes(P));
   w.counters = c.take<long long>(4);
 
   dim3 grid(view_grid(cs), n_views);
   // erosion -> mask bit 1
-  erode_h_kernel<<<grid, 256, 0, st>>>(maps->mask, w.tmp, cs, prm->r_erode);
-  erode_v_kernel<<<grid, 256, 0, st>>>(w.tmp, maps->mask, cs, prm->r_erode);
+  {
+    int max_et = 0;
+    for (int v = 0; v < n_views; ++v) {
+      int t = ((cs.cam[v].width + ERODE_T - 1) / ERODE_T) * ((cs.cam[v].height + ERODE_T - 1) / ERODE_T);
+      max_et = t > max_et ? t : max_et;
+    }
+    erode_kernel<<<dim3(max_et, n_views), 256, 0, st>>>(maps->mask, cs, prm->r_erode);
+  }
   // candidate flags
   if (n > 0) ADP_CUDA(cudaMemsetAsync(w.cand, 0, n, st));
   if (n_cand > 0)
@@ -965,6 +1000,8 @@ extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* do
                                                                       w.cand);
   // labelling
   unsigned gp = grid_for(P, 256, 148 * 16);
+  ADP_CUDA(cudaMemsetAsync(w.counters, 0, 4 * sizeof(long long), st));
+  unsigned long long* n_lroots = reinterpret_cast<unsigned long long*>(&w.counters[2]);
   {
     int max_tiles = 0;
     for (int v = 0; v < n_views; ++v) {
@@ -972,8 +1009,10 @@ extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* do
       max_tiles = t > max_tiles ? t : max_tiles;
     }
     ccl_local_kernel<<<dim3(max_tiles, n_views), 256, 0, st>>>(maps->mask, dominant, w.cand, n,
-                                                                cs, w.L);
-    ccl_border_kernel<<<grid, 256, 0, st>>>(maps->mask, dominant, cs, w.L);
+                                                                cs, w.L, w.part, w.lroots,
+                                                                n_lroots);
+    ccl_border_kernel<<<dim3(grid_for((long long)max_tiles * CCL_BORDER, 256), n_views), 256, 0,
+                        st>>>(maps->mask, dominant, cs, w.L);
   }
   ccl_flatten_kernel<<<gp, 256, 0, st>>>(w.L, P);
   ADP_LAUNCH_CHECK();
@@ -991,7 +1030,8 @@ extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* do
                       P, nullptr, &w.counters[0], w.scan, st);
   if (rc) return rc;
   zero_i64_kernel<<<gp, 256, 0, st>>>(w.mom, &w.counters[0], 6);
-  moments_kernel<<<grid, 256, 0, st>>>(w.L, w.slot, cs, w.mom);
+  moments_kernel<<<grid_for(P, 256, 148 * 8), 256, 0, st>>>(w.lroots, n_lroots, w.part, w.L,
+                                                            w.slot, w.mom);
   ADP_LAUNCH_CHECK();
   // area filter: kept index of every root, total -> out->count
   const long long* mom = w.mom;
