@@ -35,7 +35,8 @@ struct SplitWs {
   int* groups;         // [Rcap] root of each group, per candidate segment
   double* ext;         // [Rcap]
   float4* kids;        // [Rcap][4] child table: mean, quat, logscale, dc
-  long long* keep_new; // [n]
+  unsigned* dest;      // [n] new row of each Gaussian: bit 31 set for a (RESET)
+                       // candidate, all ones for a removed one
   long long* app_off;  // [n_cand]
   long long* counters; // [0] regions in use, [1] kept, [2] appended, [3] new n,
                        // [4] candidates with two or more proposals
@@ -48,7 +49,7 @@ static size_t split_ws_bytes(long long n, long long nc, long long rc) {
   long long sm = n > nc ? n : nc;
   return carve_bytes<int>(n) + 2 * carve_bytes<unsigned>(rc) + carve_bytes<int2>(nc) +
          carve_bytes<Prop>(rc) + 2 * carve_bytes<int>(rc) + carve_bytes<double>(rc) +
-         carve_bytes<float4>(4 * rc) + carve_bytes<long long>(n) + carve_bytes<long long>(nc) +
+         carve_bytes<float4>(4 * rc) + carve_bytes<unsigned>(n) + carve_bytes<long long>(nc) +
          carve_bytes<long long>(8) + carve_bytes<int>(nc) + scan_workspace_bytes(sm) +
          sort_workspace_bytes(rc);
 }
@@ -65,7 +66,7 @@ static SplitWs carve_split(Carver& c, long long n, long long nc, long long rc) {
   w.groups = c.take<int>(rc);
   w.ext = c.take<double>(rc);
   w.kids = c.take<float4>(4 * rc);
-  w.keep_new = c.take<long long>(n);
+  w.dest = c.take<unsigned>(n);
   w.app_off = c.take<long long>(nc);
   w.counters = c.take<long long>(8);
   w.multi = c.take<int>(nc);
@@ -582,9 +583,7 @@ struct ApplyArgs {
   const long long* counters;  // [1] kept, [3] new size
   bool has_m_in, has_v_in, has_m_out, has_v_out;
   int planes;
-  const int* cand_of;
-  const uint8_t* status;
-  const long long* keep_new;
+  const unsigned* dest;  // see SplitWs::dest
 };
 
 __device__ __forceinline__ void copy_gauss(const GaussPtrs& s, long long i, const GaussPtrs& d,
@@ -609,59 +608,37 @@ __device__ __forceinline__ float4* plane_of(const GaussPtrs& g, int q, long long
 
 // Kept rows: one thread per (row, plane), blockIdx.y the plane (0 mean+logit,
 // 1 log-scale, 2 quaternion, 3.. SH), so a block streams one plane of the
-// parameters, moments (and gradients) and the row maps stay in L2 across planes.
-// With ADAM, each kept non-candidate row gets the update adp_adam_step makes,
-// bit for bit (candidates got theirs before the plan); moments in and out are
-// then required.
-#ifndef ADP_KEEP_ROWS
-#define ADP_KEEP_ROWS 1
-#endif
-constexpr int KEEP_ROWS = ADP_KEEP_ROWS;  // rows per thread (apart by the block size)
-
+// parameters and moments (and gradients); the row's destination is one 32-bit
+// word, so re-reading it for every plane costs little. With ADAM, each kept
+// non-candidate row gets the update adp_adam_step makes, bit for bit (candidates
+// got theirs before the plan); moments in and out are then required.
 template <bool ADAM>
 __global__ void apply_keep_kernel(ApplyArgs a) {
   const int q = blockIdx.y;
-  const long long i0 = blockIdx.x * (long long)blockDim.x * KEEP_ROWS + threadIdx.x;
-  // every independent load of the thread's rows first (the maps and the streams),
-  // then the gradients, whose loads wait only for the row mask; removed candidate
-  // rows are read in vain
-  const long long n_new = a.counters[3];
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= a.in.n) return;
+  // every independent load first (the destination and the streams), then the
+  // gradient, whose load waits only for the row mask; removed rows are read in vain
   const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-  int c[KEEP_ROWS];
-  long long j[KEEP_ROWS];
-  bool gl[KEEP_ROWS];
-  float4 p[KEEP_ROWS], m[KEEP_ROWS], v[KEEP_ROWS], g[KEEP_ROWS];
-#pragma unroll
-  for (int r = 0; r < KEEP_ROWS; ++r) {
-    const long long i = i0 + (long long)r * blockDim.x;
-    const bool in = i < a.in.n;
-    c[r] = in ? a.cand_of[i] : 0;
-    j[r] = in ? a.keep_new[i] : a.out.n;
-    gl[r] = in && ADAM && (!a.grad_rows || a.grad_rows[i]);
-    p[r] = in ? *plane_of(a.in, q, i) : z;
-    m[r] = in && a.has_m_in ? *plane_of(a.min_, q, i) : z;
-    v[r] = in && a.has_v_in ? *plane_of(a.vin, q, i) : z;
-  }
-#pragma unroll
-  for (int r = 0; r < KEEP_ROWS; ++r) {
-    const long long i = i0 + (long long)r * blockDim.x;
-    g[r] = gl[r] ? *plane_of(a.grad, q, i) : z;
-  }
+  const long long n_new = a.counters[3];
+  const unsigned d = a.dest[i];
+  const bool gl = ADAM && (!a.grad_rows || a.grad_rows[i]);
+  float4 p = *plane_of(a.in, q, i);
+  float4 m = a.has_m_in ? *plane_of(a.min_, q, i) : z;
+  float4 v = a.has_v_in ? *plane_of(a.vin, q, i) : z;
+  const float4 g = gl ? *plane_of(a.grad, q, i) : z;
   if (n_new > a.out.n) return;  // the new population does not fit: write nothing
-#pragma unroll
-  for (int r = 0; r < KEEP_ROWS; ++r) {
-    if (i0 + (long long)r * blockDim.x >= a.in.n) continue;
-    if (c[r] >= 0 && a.status[c[r]] != ADP_RESET) continue;
-    if (j[r] >= a.out.n) continue;
-    if (ADAM && c[r] < 0) {  // candidates got their step before the plan
-      float lr4[4];
-      adam_plane_lr(a.adam, q, lr4);
-      adam_vec4(p[r], g[r], m[r], v[r], lr4, a.adam, adam_bias(a.adam));
-    }
-    *plane_of(a.out, q, j[r]) = p[r];
-    if (a.has_m_out) *plane_of(a.mout, q, j[r]) = m[r];
-    if (a.has_v_out) *plane_of(a.vout, q, j[r]) = v[r];
+  if (d == 0xffffffffu) return;  // a removed candidate
+  const long long j = d & 0x7fffffffu;
+  if (j >= a.out.n) return;
+  if (ADAM && !(d >> 31)) {  // candidates got their step before the plan
+    float lr4[4];
+    adam_plane_lr(a.adam, q, lr4);
+    adam_vec4(p, g, m, v, lr4, a.adam, adam_bias(a.adam));
   }
+  *plane_of(a.out, q, j) = p;
+  if (a.has_m_out) *plane_of(a.mout, q, j) = m;
+  if (a.has_v_out) *plane_of(a.vout, q, j) = v;
 }
 
 struct AppendArgs {
@@ -841,14 +818,19 @@ extern "C" ADP_API int adp_split_plan(const adp_gaussians* g, const adp_camera* 
   }
   // new indices of kept Gaussians and offsets of appended blocks
   const int* cand_of = w.cand_of;
-  long long* keep_new = w.keep_new;
+  unsigned* dest = w.dest;
   const uint8_t* cstatus = status;
   rc = scan_exclusive(
       [=] __device__(long long i) -> long long {
         int cc = cand_of[i];
         return (cc < 0 || cstatus[cc] == ADP_RESET) ? 1 : 0;
       },
-      [=] __device__(long long i, long long pre) { keep_new[i] = pre; }, n, nullptr,
+      [=] __device__(long long i, long long pre) {
+        const int cc = cand_of[i];
+        const bool kept = cc < 0 || cstatus[cc] == ADP_RESET;
+        dest[i] = kept ? ((unsigned)pre | (cc >= 0 ? 0x80000000u : 0u)) : 0xffffffffu;
+      },
+      n, nullptr,
       &w.counters[1], w.scan, st);
   if (rc) return rc;
   if (nc > 0) {
@@ -921,12 +903,10 @@ static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
     aa.adam = *adam;
   }
   aa.planes = planes;
-  aa.cand_of = w.cand_of;
-  aa.status = status;
-  aa.keep_new = w.keep_new;
+  aa.dest = w.dest;
   aa.counters = w.counters;
   if (n > 0) {
-    const dim3 kg(grid_for(n, 256 * KEEP_ROWS), 3 + planes);
+    const dim3 kg(grid_for(n, 256), 3 + planes);
     if (adam)
       apply_keep_kernel<true><<<kg, 256, 0, st>>>(aa);
     else
