@@ -37,6 +37,32 @@ WORKLOAD = dict(workload="single-view plain step: 1,000,000 Gaussians (64 cluste
                 cand_frac=0.10, l2="flushed between steps (256 MiB write)")
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "split_apply_traffic.json")
+
+
+def _measured_traffic(stage):
+    """DRAM bytes per launch of a stage's kernels from the committed ncu capture, if
+    the capture covers this stage and every source it was taken from is unchanged
+    (sha1 of the files); otherwise None."""
+    import hashlib
+
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("stage") != stage:
+        return None
+    for rel, digest in rec.get("sources_sha1", {}).items():
+        try:
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                if hashlib.sha1(f.read()).hexdigest() != digest:
+                    return None
+        except OSError:
+            return None
+    return rec.get("dram_bytes_per_launch")
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -124,15 +150,20 @@ def stage_bytes(n, n_vis, K, P, n_tiles, sh_planes, regions, k, kept, appended):
         "error_stats": P * (12 + 12 + 4 + 4 + 4 + 1) + n * 12,
         "select_topk": n * 8 * 8 + n * 8 * 2 + k * 4,
         "error_regions": P * (1 + 4 + 1 + 4 + 4 + 4 + 4) + regions * 160,
+        # the gradient has a row mask: parameters read and gradients written for the
+        # rendered Gaussians only, plus the mask byte and the tile counts of all
         "render_backward": (n_tiles * 8 + K * 4 + n_vis * 48 + P * (12 + 12 + 4 + 4) +
-                            n_vis * 48 * 2 + n * gbytes * 2 + n * 4),
-        # Adam: read parameter, gradient, m, v; write parameter, m, v
-        "adam": n * gbytes * 7,
-        "adam_rows": k * gbytes * 7,
+                            n_vis * 48 * 2 + n_vis * gbytes * 2 + n * (1 + 4)),
+        # Adam: read parameter, m, v (and the gradient of rendered rows); write
+        # parameter, m, v
+        "adam": n * gbytes * 6 + n_vis * gbytes + n,
+        "adam_rows": k * gbytes * 6 + min(k, n_vis) * gbytes + k * 5,
         "split_plan": regions * 300 + n * 12 + k * 16,
-        # compaction with the fused Adam step: kept rows as in Adam, the parents
-        # read, appended rows written with zero moments, the row maps read
-        "split_apply": kept * gbytes * 7 + k * gbytes + appended * gbytes * 3 + n * 16,
+        # compaction with the fused Adam step: kept rows as in Adam (gradients of
+        # rendered rows only), the parents read, appended rows written with zero
+        # moments, one destination word and one mask byte per row
+        "split_apply": (kept * gbytes * 6 + min(kept, n_vis) * gbytes + k * gbytes +
+                        appended * gbytes * 3 + n * (4 + 1)),
     }
 
 
@@ -290,8 +321,8 @@ def run_ours(args, rank, world, local_rank):
     else:
         ach = sb[dom] / (per_stage[dom] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
-                "peak_source": peak_kind}
+                "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": _measured_traffic(dom),
+                "algorithmic_bytes": int(sb[dom]), "peak_source": peak_kind}
     launches = None if args.no_launch_count else count_launches(stepper, noise) * args.steps
     batched = None
     if args.batch_views > 1:
