@@ -318,13 +318,53 @@ ADP_API int adp_split_apply_adam(const adp_gaussians* g, const adp_gaussians* gr
  * front, transmittance recovered from T_final by division; the derivative is
  * exact for the forward as defined (zero through the alpha clamp, the colour
  * clamp at 0 and the clamped x/z, y/z of J). grad is zeroed and written; the
- * per-view 2D gradients are summed over views. */
+ * per-view 2D gradients are summed over views.
+ * grad2d_accum [n] float, grad2d_visits [n] int32 (both or neither, may be NULL):
+ * the image-space statistic of the adaptive density control (Sec. 3, Eq. 2). For
+ * every Gaussian rendered in a view, the call ADDS to grad2d_accum[i] the norm of
+ * dL/d(projected 2D mean) in normalised device coordinates (pixel gradient times
+ * W/2 and H/2) and 1 to grad2d_visits[i]; the caller zeroes both at the start of
+ * a densification interval, and g_i = accum / visits is the average of Eq. 2. */
 ADP_API size_t adp_render_backward_workspace_size(int64_t n, int32_t n_views);
 ADP_API int adp_render_backward(const adp_gaussians* g, const adp_projected* pr,
                                 const adp_bins* bins, const adp_image* fwd, const float* target,
                                 const float* dL_drgb, const adp_camera* cams, int32_t n_views,
                                 const float* bg, const adp_params* prm, adp_gaussians* grad,
-                                void* ws, size_t ws_bytes, adp_stream_t stream);
+                                float* grad2d_accum, int32_t* grad2d_visits, void* ws,
+                                size_t ws_bytes, adp_stream_t stream);
+
+/* --- Adaptive density control candidates (Sec. 3, Eq. 2). -------------------
+ * With g_i = grad2d_accum[i] / grad2d_visits[i] (0 when never visited; one
+ * correctly rounded float32 division), Gaussian i is a split candidate iff
+ * g_i >= tau_g and max(s_i) > tau_s (Eq. 2), and a clone candidate iff
+ * g_i >= tau_g and max(s_i) <= tau_s (the high-gradient Gaussians of small scale
+ * the baselines clone). The scale test is made on the stored log-scales against
+ * ln(tau_s) rounded to float32. Writes the split ids and the clone ids in
+ * ascending order (each list has room for n entries; entries past the count are
+ * set to -1) and their counts to d_counts[0], d_counts[1] (device int64); no host
+ * synchronisation. The split list is the candidate list of adp_error_regions and
+ * adp_split_plan, which may be given whole, with n_cand = n: those calls skip -1
+ * entries (a -1 candidate gets status ADP_KEEP and no children). */
+ADP_API size_t adp_densify_select_workspace_size(int64_t n);
+ADP_API int adp_densify_select(const float* grad2d_accum, const int32_t* grad2d_visits,
+                               const adp_gaussians* g, float tau_g, float tau_s,
+                               int32_t* split_ids, int32_t* clone_ids, int64_t* d_counts,
+                               void* ws, size_t ws_bytes, adp_stream_t stream);
+/* Clone (the baselines' operation for small high-gradient Gaussians, Sec. 3):
+ * called after adp_split_apply or adp_split_apply_adam with the same workspace
+ * and the same n (population before the split), n_cand and region capacity. It
+ * appends to the new population pop (capacity pop->n) a copy of each listed
+ * Gaussian -- its kept row in pop, so after any Adam step the compaction applied
+ * -- at rows [planned size, planned size + count), with zero moments in m_out and
+ * v_out (optional), and sets *d_new_n to the new size. count is *d_n_clone
+ * (device int64), at most max_clone; ids are ids of the population before the
+ * split and must not be split candidates (such an entry gives an all-zero row).
+ * If the result does not fit in pop->n, nothing is written and *d_new_n holds the
+ * required size. */
+ADP_API int adp_split_clone(int64_t n, int64_t n_cand, int64_t region_capacity,
+                            const int32_t* clone_ids, const int64_t* d_n_clone, int64_t max_clone,
+                            adp_gaussians* pop, adp_gaussians* m_out, adp_gaussians* v_out,
+                            void* ws, size_t ws_bytes, int64_t* d_new_n, adp_stream_t stream);
 
 /* --- Adam (the baselines' optimizer, unchanged by the paper, Sec. 5.1). -----
  * In place, bias-corrected. The step number t >= 1 is `step`, or, if d_step

@@ -1286,10 +1286,13 @@ static void composite_c(const proj_view_t* pv, const orc_config* cfg, const doub
 /* dL/dtheta for the Gaussians in sel, with L = loss_scale * sum over pixels
  * and channels of |I^ - I_gt| for one view (loss_scale = 1 / (3 W H) gives
  * the mean; sign(0) = 0). Each Gaussian's gradient collects the pixels of its
- * own box. grad is [n_sel][11 + 3K]. */
+ * own box. grad is [n_sel][11 + 3K]. If mean2d_grad is not NULL it receives
+ * [n_sel][2], dL with respect to the projected 2D mean (pixel units) -- the
+ * image-space gradient the densification statistic of Eq. 2 accumulates. */
 ORC_API void orc_grad(int64_t n, int32_t deg, const double* theta, const orc_camera* cam,
                       const orc_config* cfg, const double* bg, const float* tgt,
-                      double loss_scale, int64_t n_sel, const int32_t* sel, double* grad) {
+                      double loss_scale, int64_t n_sel, const int32_t* sel, double* grad,
+                      double* mean2d_grad) {
   int P = 11 + 3 * (deg + 1) * (deg + 1);
   int W = cam->width;
   double* mean2d = (double*)malloc(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
@@ -1313,6 +1316,7 @@ ORC_API void orc_grad(int64_t n, int32_t deg, const double* theta, const orc_cam
       int64_t g = sel[si];
       double* gr = grad + si * P;
       for (int p = 0; p < P; ++p) gr[p] = 0.0;
+      if (mean2d_grad) mean2d_grad[2 * si] = mean2d_grad[2 * si + 1] = 0.0;
       if (tiles[g] <= 0) continue;
       const int32_t* gb = box + 4 * g;
       /* Every Gaussian that can contribute inside g's box, depth-sorted. */
@@ -1371,6 +1375,10 @@ ORC_API void orc_grad(int64_t n, int32_t deg, const double* theta, const orc_cam
             for (int ch = 0; ch < 3; ++ch) dL[j] += loss_scale * sgn[ch] * cimag(col[ch]) / h;
           }
         }
+      if (mean2d_grad) {
+        mean2d_grad[2 * si] = dL[0];
+        mean2d_grad[2 * si + 1] = dL[1];
+      }
       /* Jacobian of the projection by complex step. */
       cplx th[59];
       for (int p = 0; p < P; ++p) th[p] = theta[g * P + p];

@@ -5,11 +5,14 @@ of the benchmark are the only users. It shares no code with the CUDA path and ne
 reads anything the CUDA path produced.
 
 Every function names the step of the paper it follows; the arithmetic lives in
-adp_oracle.c. Inputs come from the `scenes` module (float32), widened to float64.
+adp_oracle.c, except the densification selection of Sec. 3 (Eq. 2) and the clone
+bookkeeping at the end of this file, which are a few plain numpy lines. Inputs
+come from the `scenes` module (float32), widened to float64.
 """
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 from dataclasses import dataclass
@@ -99,7 +102,7 @@ def _declare(L):
                             C.POINTER(OrcSplitConfig), _vp, _vp, C.c_int64, _vp, _vp, _vp]
     L.orc_split.restype = C.c_int64
     L.orc_grad.argtypes = [C.c_int64, C.c_int32, _vp, C.POINTER(OrcCamera), C.POINTER(OrcConfig),
-                           _vp, _vp, C.c_double, C.c_int64, _vp, _vp]
+                           _vp, _vp, C.c_double, C.c_int64, _vp, _vp, _vp]
     L.orc_adam.argtypes = [C.c_int64, C.c_int32, _vp, _vp, _vp, _vp, C.c_int32, _vp,
                            C.c_double, C.c_double, C.c_double]
     L.orc_version.restype = C.c_int32
@@ -397,8 +400,10 @@ def split(theta, deg, cams, regs, cand, count, noise, sp: SplitParams = SplitPar
 # --------------------------------------------------------------------------- backward, Adam
 
 def grad(theta, deg, cam, tgt_f32, sel=None, bg=(0.0, 0.0, 0.0), cfg: Config = Config(),
-         loss_scale=None):
-    """dL/dtheta of the per-view mean L1 loss (complex-step derivative of the forward)."""
+         loss_scale=None, return_mean2d=False):
+    """dL/dtheta of the per-view mean L1 loss (complex-step derivative of the forward).
+    With return_mean2d, also dL with respect to each selected Gaussian's projected 2D
+    mean in pixel units, [n_sel][2]."""
     theta = _c(theta, np.float64)
     n, P = theta.shape
     W, H = int(cam["width"]), int(cam["height"])
@@ -409,9 +414,10 @@ def grad(theta, deg, cam, tgt_f32, sel=None, bg=(0.0, 0.0, 0.0), cfg: Config = C
     tgt = _c(tgt_f32, np.float32)
     bg = _c(bg, np.float64)
     cc, cf = camera(cam), cfg.c()
+    m2 = np.zeros((sel.shape[0], 2)) if return_mean2d else None
     lib().orc_grad(n, deg, _p(theta), C.byref(cc), C.byref(cf), _p(bg), _p(tgt), loss_scale,
-                   sel.shape[0], _p(sel), _p(out))
-    return out
+                   sel.shape[0], _p(sel), _p(out), _p(m2) if return_mean2d else None)
+    return (out, m2) if return_mean2d else out
 
 
 def l1_loss(theta, deg, cam, tgt_f32, bg=(0.0, 0.0, 0.0), cfg: Config = Config()):
@@ -476,3 +482,39 @@ def plain_step(scene, cams, targets, k_cand=None, cand=None, sp: SplitParams = S
     sp_out = split(theta, deg, cams, regs, cand, count, noise, sp)
     return dict(theta=theta, views=views, count=count, mass=mass, cand=cand, regions=regs,
                 split=sp_out)
+
+
+# --------------------------------------------------------------------------- densification (Eq. 2)
+
+def densify_stat_ndc(mean2d_grad, width, height):
+    """One view's contribution to the densification statistic of Sec. 3: the norm of
+    dL/d(projected 2D mean) in normalised device coordinates (the pixel-space
+    gradient times W/2 and H/2, the scaling the baselines' statistic is kept in)."""
+    g = np.asarray(mean2d_grad, np.float64)
+    return np.hypot(g[:, 0] * (0.5 * width), g[:, 1] * (0.5 * height))
+
+
+def densify_select(accum_f32, visits_i32, logscale_f32, tau_g, tau_s):
+    """Eq. 2 and the clone rule of Sec. 3, decided in float32 on the stored values:
+    g_i = accum_i / visits_i (0 if never visited); split iff g_i >= tau_g and
+    max(s_i) > tau_s, clone iff g_i >= tau_g and max(s_i) <= tau_s. The scale test
+    compares max log s_i with ln(tau_s) rounded to float32 (exp is increasing).
+    Returns (split ids, clone ids), ascending."""
+    acc = np.asarray(accum_f32, np.float32)
+    vis = np.asarray(visits_i32, np.int32)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        g = np.where(vis > 0, acc / vis.astype(np.float32), np.float32(0.0)).astype(np.float32)
+    high = g >= np.float32(tau_g)
+    large = np.asarray(logscale_f32, np.float32)[:, :3].max(1) > np.float32(math.log(tau_s))
+    return (np.nonzero(high & large)[0].astype(np.int32),
+            np.nonzero(high & ~large)[0].astype(np.int32))
+
+
+def clone_rows(theta_new, n, split_status, cand, clone_ids):
+    """Appends to the post-split population theta_new a copy of each clone id's kept
+    row (kept rows are the non-candidates and RESET candidates, in id order)."""
+    keep = np.ones(n, bool)
+    keep[np.asarray(cand)] = np.asarray(split_status) == RESET
+    new_row = np.cumsum(keep) - 1
+    rows = new_row[np.asarray(clone_ids, np.int64)]
+    return np.concatenate([theta_new, theta_new[rows]], 0)

@@ -102,7 +102,12 @@ _PROTOS = {
     "adp_render_backward_workspace_size": (C.c_size_t, [_i64, _i32]),
     "adp_render_backward": (C.c_int, [P(AdpGaussians), P(AdpProjected), P(AdpBins), P(AdpImage),
                                       _vp, _vp, P(AdpCamera), _i32, P(C.c_float), P(AdpParams),
-                                      P(AdpGaussians), _vp, C.c_size_t, _vp]),
+                                      P(AdpGaussians), _vp, _vp, _vp, C.c_size_t, _vp]),
+    "adp_densify_select_workspace_size": (C.c_size_t, [_i64]),
+    "adp_densify_select": (C.c_int, [_vp, _vp, P(AdpGaussians), C.c_float, C.c_float, _vp, _vp,
+                                     _vp, _vp, C.c_size_t, _vp]),
+    "adp_split_clone": (C.c_int, [_i64, _i64, _i64, _vp, _vp, _i64, P(AdpGaussians),
+                                  P(AdpGaussians), P(AdpGaussians), _vp, C.c_size_t, _vp, _vp]),
     "adp_adam_step": (C.c_int, [P(AdpGaussians), P(AdpGaussians), P(AdpGaussians),
                                 P(AdpGaussians), _i32, _vp, P(C.c_float), C.c_float, C.c_float,
                                 C.c_float, _vp]),

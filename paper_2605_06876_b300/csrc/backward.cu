@@ -262,6 +262,8 @@ struct BwdGaussArgs {
   float4* g_ls;
   float4* g_q;
   float* g_sh;
+  float* g2d_accum;   // optional: += the 2D-mean gradient norm of every rendered view
+  int* g2d_visits;    // optional: += the number of those views
 };
 
 // Chain rule of one visible Gaussian, summed over views. The SH degree is a
@@ -285,6 +287,8 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
       S[3 * r + c] = Rg.m[3 * r] * Rg.m[3 * c] * s[0] * s[0] + Rg.m[3 * r + 1] * Rg.m[3 * c + 1] * s[1] * s[1] +
                      Rg.m[3 * r + 2] * Rg.m[3 * c + 2] * s[2] * s[2];
   float gmu[3] = {0.f, 0.f, 0.f}, glogit = 0.f;
+  float g2d_norm = 0.f;  // densification statistic of this Gaussian, summed over views
+  int g2d_n = 0;
   float G3[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma3 over views
   float gsh[3 * K];
 #pragma unroll
@@ -409,6 +413,11 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
     }
     // 2D mean: dL/dmean = -(Q [Sx, Sy])
     const float gmx = -(QA * mSx + QB * mSy), gmy = -(QB * mSx + QC * mSy);
+    // the image-space gradient in normalised device coordinates (x_ndc spans W / 2
+    // pixels per unit), as the adaptive density control accumulates it
+    g2d_norm += sqrtf(fmaf(gmx * 0.5f * (float)cam.width, gmx * 0.5f * (float)cam.width,
+                           (gmy * 0.5f * (float)cam.height) * (gmy * 0.5f * (float)cam.height)));
+    ++g2d_n;
     gp[0] += gmx * cam.fx * iz;
     gp[1] += gmy * cam.fy * iz;
     gp[2] += -(gmx * cam.fx * pc[0] + gmy * cam.fy * pc[1]) * iz2;
@@ -439,6 +448,10 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
   float gz = 2.f * (-2.f * qz * GR[0] - qw * GR[1] + qx * GR[2] + qw * GR[3] - 2.f * qz * GR[4] +
                     qy * GR[5] + qx * GR[6] + qy * GR[7]);
   float dotq = gw * qw + gx * qx + gy * qy + gz * qz;
+  if (a.g2d_accum) {
+    a.g2d_accum[i] += g2d_norm;
+    a.g2d_visits[i] += g2d_n;
+  }
   a.g_ml[i] = make_float4(gmu[0], gmu[1], gmu[2], glogit);
   a.g_ls[i] = make_float4(gls[0], gls[1], gls[2], 0.f);
   a.g_q[i] = make_float4((gw - dotq * qw) * iq, (gx - dotq * qx) * iq, (gy - dotq * qy) * iq,
@@ -526,10 +539,12 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
                                            const float* target, const float* dL_drgb,
                                            const adp_camera* cams, int32_t n_views,
                                            const float* bg, const adp_params* prm,
-                                           adp_gaussians* grad, void* ws, size_t ws_bytes,
+                                           adp_gaussians* grad, float* grad2d_accum,
+                                           int32_t* grad2d_visits, void* ws, size_t ws_bytes,
                                            adp_stream_t stream) {
   ADP_CHECK_ARG(g && pr && bins && fwd && grad, "NULL argument");
   ADP_CHECK_ARG(target || dL_drgb, "one of target and dL_drgb must be given");
+  ADP_CHECK_ARG(!grad2d_accum == !grad2d_visits, "give both or neither densification accumulators");
   ADP_CHECK_ARG(grad->n == g->n && grad->sh_degree == g->sh_degree, "grad shape mismatch");
   ADP_CHECK_ARG(g->sh_degree >= 0 && g->sh_degree <= 3, "sh_degree must be 0..3");
   CamSet cs;
@@ -580,6 +595,8 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   ga.g_ls = reinterpret_cast<float4*>(grad->logscale);
   ga.g_q = reinterpret_cast<float4*>(grad->quat);
   ga.g_sh = grad->sh;
+  ga.g2d_accum = grad2d_accum;
+  ga.g2d_visits = grad2d_visits;
   bwd_visible_kernel<<<grid_for(g->n, 256, 148 * 16), 256, 0, st>>>(
       pr->tiles_touched, g->n, n_views, sh_planes(g->sh_degree), ga.g_ml, ga.g_ls, ga.g_q,
       reinterpret_cast<float4*>(grad->sh), grad->rows, list, n_list);

@@ -430,7 +430,10 @@ __global__ void merge_status_kernel(MergeArgs a) {
     const int i = a.cand[c];
     const int2 sg = a.seg[c];
     const int M = sg.y - sg.x;
-    if (a.count[i] == 0) {
+    if (i < 0) {  // an unused entry of a candidate list passed whole
+      a.status[c] = ADP_KEEP;
+      a.n_children[c] = 0;
+    } else if (a.count[i] == 0) {
       a.status[c] = ADP_FALLBACK;
       a.n_children[c] = 0;
     } else if (M <= 0) {
@@ -971,5 +974,74 @@ extern "C" ADP_API int adp_split_apply_adam(
     split_step_advance_kernel<<<1, 1, 0, st>>>(d_step);
     ADP_LAUNCH_CHECK();
   }
+  return ADP_OK;
+}
+
+// ------------------------------------------------------------------ clone
+
+namespace adp {
+
+// Copies of the listed Gaussians appended after the split's rows: each copy is
+// the Gaussian's kept row of the new population (after any Adam step the
+// compaction applied), with zero moments. Nothing is written if the result does
+// not fit.
+__global__ void clone_kernel(const int* ids, const long long* d_n_clone, long long max_clone,
+                             const unsigned* dest, const long long* counters, GaussPtrs pop,
+                             GaussPtrs mout, GaussPtrs vout, bool has_m, bool has_v, int planes) {
+  long long nc = *d_n_clone;
+  if (nc > max_clone) nc = max_clone;
+  const long long base = counters[3];
+  if (base + nc > pop.n) return;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc;
+       t += (long long)gridDim.x * blockDim.x) {
+    const unsigned d = dest[ids[t]];
+    const long long j = base + t;
+    if (d >> 31) {  // a split candidate (not a kept row): an all-zero row
+      zero_gauss(pop, j, planes);
+    } else {
+      copy_gauss(pop, (long long)d, pop, j, planes);
+    }
+    if (has_m) zero_gauss(mout, j, planes);
+    if (has_v) zero_gauss(vout, j, planes);
+  }
+}
+
+__global__ void clone_size_kernel(const long long* d_n_clone, long long max_clone,
+                                  const long long* counters, int64_t* d_new_n) {
+  long long nc = *d_n_clone;
+  if (nc > max_clone) nc = max_clone;
+  *d_new_n = counters[3] + nc;
+}
+
+}  // namespace adp
+
+extern "C" ADP_API int adp_split_clone(int64_t n, int64_t n_cand, int64_t region_capacity,
+                                       const int32_t* clone_ids, const int64_t* d_n_clone,
+                                       int64_t max_clone, adp_gaussians* pop, adp_gaussians* m_out,
+                                       adp_gaussians* v_out, void* ws, size_t ws_bytes,
+                                       int64_t* d_new_n, adp_stream_t stream) {
+  ADP_CHECK_ARG(pop && d_new_n && d_n_clone, "NULL argument");
+  ADP_CHECK_ARG(gauss_ok(pop) || pop->n == 0, "bad population arrays");
+  ADP_CHECK_ARG(n >= 0 && n < (1LL << 31) && n_cand >= 0 && region_capacity >= 0, "bad sizes");
+  ADP_CHECK_ARG(max_clone >= 0 && max_clone <= n, "max_clone out of range");
+  ADP_CHECK_ARG(max_clone == 0 || clone_ids, "NULL clone ids");
+  ADP_CHECK_ARG(!m_out || (gauss_ok(m_out) && m_out->n == pop->n), "bad m_out");
+  ADP_CHECK_ARG(!v_out || (gauss_ok(v_out) && v_out->n == pop->n), "bad v_out");
+  ADP_CHECK_ARG(aligned(ws, 256), "workspace must be 256-byte aligned");
+  const size_t need = split_ws_bytes(n, n_cand, region_capacity);
+  ADP_CHECK_ARG(ws_bytes >= need, "workspace %zu bytes, need %zu", ws_bytes, need);
+  cudaStream_t st = (cudaStream_t)stream;
+  Carver c(ws, ws_bytes);
+  SplitWs w = carve_split(c, n, n_cand, region_capacity);
+  const int planes = sh_planes(pop->sh_degree);
+  GaussPtrs mo = {}, vo = {};
+  if (m_out) mo = gp_of(m_out);
+  if (v_out) vo = gp_of(v_out);
+  if (max_clone > 0)
+    clone_kernel<<<grid_for(max_clone, 256, 148 * 16), 256, 0, st>>>(
+        clone_ids, (const long long*)d_n_clone, max_clone, w.dest, w.counters, gp_of(pop), mo, vo,
+        m_out != nullptr, v_out != nullptr, planes);
+  clone_size_kernel<<<1, 1, 0, st>>>((const long long*)d_n_clone, max_clone, w.counters, d_new_n);
+  ADP_LAUNCH_CHECK();
   return ADP_OK;
 }

@@ -445,10 +445,57 @@ def split_apply_adam(g: Gaussians, grad: Gaussians, m_in: Gaussians, v_in: Gauss
     return out, m_out, v_out
 
 
+@dataclass
+class DensifySets:
+    split: torch.Tensor   # int32 [n]: the first counts[0] entries are the split ids
+    clone: torch.Tensor   # int32 [n]: the first counts[1] entries are the clone ids
+    counts: torch.Tensor  # int64 [2] on the device
+
+
+def densify_select(grad2d_accum, grad2d_visits, g: Gaussians, tau_g, tau_s, out: DensifySets = None,
+                   ws=None, stream=None):
+    """adp_densify_select: Eq. 2 split candidates and the clone candidates."""
+    dev = g.mean_logit.device
+    if out is None:
+        n1 = max(g.n, 1)
+        out = DensifySets(torch.empty(n1, dtype=I32, device=dev),
+                          torch.empty(n1, dtype=I32, device=dev),
+                          torch.zeros(2, dtype=I64, device=dev))
+    need = A.lib().adp_densify_select_workspace_size(g.n)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    gc = g.c()
+    A.check(A.lib().adp_densify_select(_p(grad2d_accum), _p(grad2d_visits), C.byref(gc),
+                                       float(tau_g), float(tau_s), _p(out.split), _p(out.clone),
+                                       _p(out.counts), _p(ws), ws.numel(), _stream(stream)),
+            "adp_densify_select")
+    return out
+
+
+def split_clone(g: Gaussians, plan: SplitPlan, regions: Regions, candidates, clone_ids, d_n_clone,
+                max_clone, out: Gaussians, m_out: Gaussians = None, v_out: Gaussians = None,
+                d_new_n=None, stream=None):
+    """adp_split_clone: copies of the clone ids appended after the split's rows (call
+    after split_apply / split_apply_adam with the same plan). Returns the device
+    new size."""
+    d_new_n = d_new_n if d_new_n is not None else torch.zeros(1, dtype=I64, device=out.mean_logit.device)
+    oc = out.c()
+    mc = m_out.c() if m_out is not None else None
+    vc = v_out.c() if v_out is not None else None
+    A.check(A.lib().adp_split_clone(
+        g.n, int(candidates.numel()), regions.capacity, _p(clone_ids), _p(d_n_clone),
+        int(max_clone), C.byref(oc), C.byref(mc) if mc is not None else None,
+        C.byref(vc) if vc is not None else None, _p(plan.ws), plan.ws.numel(), _p(d_new_n),
+        _stream(stream)), "adp_split_clone")
+    return d_new_n
+
+
 def render_backward(g: Gaussians, pr: Projected, bins: Bins, fwd: Image, cams, target=None,
                     dL_drgb=None, bg=(0.0, 0.0, 0.0), params=None, grad: Gaussians = None, ws=None,
-                    stream=None):
-    """adp_render_backward: gradients of the L1 loss (or of dL_drgb) for every parameter."""
+                    stream=None, grad2d_accum=None, grad2d_visits=None):
+    """adp_render_backward: gradients of the L1 loss (or of dL_drgb) for every parameter.
+    grad2d_accum (float32 [n]) and grad2d_visits (int32 [n]), if given, accumulate
+    the densification statistic of Eq. 2 (see adpsplit.h)."""
     params = params or A.default_params()
     ca = A.cameras(cams)
     V = len(cams)
@@ -461,7 +508,8 @@ def render_backward(g: Gaussians, pr: Projected, bins: Bins, fwd: Image, cams, t
     gc, pc, bc, fc, grc = g.c(), pr.c(), bins.c(), fwd.c(), grad.c()
     A.check(A.lib().adp_render_backward(C.byref(gc), C.byref(pc), C.byref(bc), C.byref(fc),
                                         _p(target), _p(dL_drgb), ca, V, bgc, C.byref(params),
-                                        C.byref(grc), _p(ws), ws.numel(), _stream(stream)),
+                                        C.byref(grc), _p(grad2d_accum), _p(grad2d_visits), _p(ws),
+                                        ws.numel(), _stream(stream)),
             "adp_render_backward")
     return grad
 

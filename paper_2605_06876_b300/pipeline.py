@@ -71,7 +71,7 @@ class StageTimer:
 class PlainStep:
     def __init__(self, g: ops.Gaussians, cams, target, cand_frac=0.1, params=None,
                  bg=(0.0, 0.0, 0.0), lr=ops.ADAM_LR, bins_margin=1.15, region_margin=1.25,
-                 fused_adam=True):
+                 fused_adam=True, out_capacity=None):
         self.g = g
         # fused_adam: the Adam step of the candidates runs before the plan and the
         # compaction applies it to every other row while copying (one pass over
@@ -128,7 +128,8 @@ class PlainStep:
         self.ws_bwd = ops.workspace(A.lib().adp_render_backward_workspace_size(n, self.V), self.dev)
         self.ws_split = ops.workspace(ops.split_workspace_size(n, self.k, cap), self.dev)
         # the largest population a split can produce: no read-back inside a step
-        self.out_capacity = n + self.k * (self.params.n_max + 1)
+        self.out_capacity = (out_capacity if out_capacity is not None
+                             else n + self.k * (self.params.n_max + 1))
         self.out = ops.Gaussians(self.out_capacity, g.sh_degree, self.dev, zero=False)
         self.m_out = ops.Gaussians(self.out_capacity, g.sh_degree, self.dev, zero=False)
         self.v_out = ops.Gaussians(self.out_capacity, g.sh_degree, self.dev, zero=False)
@@ -268,3 +269,104 @@ def capture_graph(fn):
     with torch.cuda.graph(graph):
         fn()
     return graph
+
+
+class DensifyStep(PlainStep):
+    """One step with the paper's own candidate choice instead of the top-k
+    workload rule: the backward accumulates the image-space statistic of Sec. 3,
+    Eq. 2 picks the split candidates (g_i >= tau_g, max s_i > tau_s) and the clone
+    candidates (g_i >= tau_g, max s_i <= tau_s), AdpSplit splits the former and the
+    latter are cloned after the compaction. The candidate lists are passed whole
+    (n entries, -1 past the device-held counts), so nothing reads a count back.
+    The statistic covers this step only (the accumulators are cleared first); the
+    output population is sized from one probing step."""
+
+    def __init__(self, g: ops.Gaussians, cams, target, tau_g=2e-4, tau_s=0.05, params=None,
+                 bg=(0.0, 0.0, 0.0), lr=ops.ADAM_LR, out_margin=1.25):
+        self.tau_g, self.tau_s = float(tau_g), float(tau_s)
+        super().__init__(g, cams, target, cand_frac=1.0, params=params, bg=bg, lr=lr,
+                         out_capacity=1)
+        n = g.n
+        self.accum = torch.zeros(n, dtype=torch.float32, device=self.dev)
+        self.visits = torch.zeros(n, dtype=torch.int32, device=self.dev)
+        self.sets = ops.densify_select(self.accum, self.visits, g, self.tau_g, self.tau_s)
+        self.ws_densify = ops.workspace(A.lib().adp_densify_select_workspace_size(n), self.dev)
+        self.d_new_n = torch.zeros(1, dtype=torch.int64, device=self.dev)
+        self.cand = self.sets.split  # the whole list: the first counts[0] entries are ids
+        # probe: one step into a population as large as the worst case of this input
+        probe_cap = n + n * (self.params.n_max + 1)
+        self._alloc_out(1)
+        noise = torch.zeros((n, 2, 3), dtype=torch.float32, device=self.dev)
+        g0 = [t.clone() for t in g.tensors()]
+        m0, v0, t0 = self.m.clone(), self.v.clone(), self.adam_t.clone()
+        self._probe = True
+        plan = self.step(noise)
+        torch.cuda.synchronize()
+        need = int(self.d_new_n.item())
+        # the probe's Adam step is undone so the first real step starts from the input
+        for d, s in zip(g.tensors(), g0):
+            d.copy_(s)
+        self.m, self.v = m0, v0
+        self.adam_t.copy_(t0)
+        self._probe = False
+        self._alloc_out(min(probe_cap, int(need * out_margin) + 1024))
+        torch.cuda.synchronize()
+        del plan
+
+    def _alloc_out(self, cap):
+        self.out_capacity = cap
+        self.out = ops.Gaussians(cap, self.g.sh_degree, self.dev, zero=False)
+        self.m_out = ops.Gaussians(cap, self.g.sh_degree, self.dev, zero=False)
+        self.v_out = ops.Gaussians(cap, self.g.sh_degree, self.dev, zero=False)
+
+    def step(self, noise, timer: StageTimer = None):
+        """One step; returns (new Gaussians, new m, new v, split plan); the new size
+        (split and clones) is self.d_new_n."""
+        g, cams, prm, n = self.g, self.cams, self.params, self.g.n
+        mark = timer.mark if timer else (lambda name: None)
+        mark("project")
+        ops.project(g, cams, prm, self.pr)
+        mark("bin_sort")
+        ops.bin_sort(n, self.pr, cams, prm, bins=self.bins, ws=self.ws_bins, grow=False)
+        mark("render")
+        ops.render(n, self.pr, self.bins, cams, self.bg, prm, self.img)
+        main = torch.cuda.current_stream()
+        self.side.wait_stream(main)
+        with torch.cuda.stream(self.side):
+            mark("error_stats")
+            ops.error_stats(self.img.rgb, self.target, self.img.dominant, n, cams, prm, self.maps,
+                            self.count, self.mass)
+            mark("error_end")
+        mark("render_backward")
+        self.accum.zero_()
+        self.visits.zero_()
+        ops.render_backward(g, self.pr, self.bins, self.img, cams, target=self.target, bg=self.bg,
+                            params=prm, grad=self.grad, ws=self.ws_bwd,
+                            grad2d_accum=self.accum, grad2d_visits=self.visits)
+        mark("densify_select")
+        ops.densify_select(self.accum, self.visits, g, self.tau_g, self.tau_s, out=self.sets,
+                           ws=self.ws_densify)
+        main.wait_stream(self.side)
+        mark("error_regions")
+        ops.error_regions(self.maps, self.img.dominant, self.target, n, cams, self.cand, prm,
+                          regions=self.regions, ws=self.ws_regions, grow=False)
+        mark("adam_rows")
+        ops.adam_step_rows(g, self.grad, self.m, self.v, self.cand, self.adam_t, self.lr)
+        mark("split_plan")
+        plan = ops.split_plan(g, cams, self.regions, self.cand, self.count, prm, ws=self.ws_split,
+                              sync=False)
+        mark("split_apply")
+        ops.split_apply_adam(g, self.grad, self.m, self.v, plan, self.regions, self.cand, noise,
+                             self.adam_t, self.out, self.m_out, self.v_out, prm, self.lr)
+        mark("clone")
+        ops.split_clone(g, plan, self.regions, self.cand, self.sets.clone, self.sets.counts[1:],
+                        n, self.out, self.m_out, self.v_out, d_new_n=self.d_new_n)
+        mark("end")
+        return self.out, self.m_out, self.v_out, plan
+
+    def check_capacity(self, plan=None):
+        ok = (int(self.bins.n_inst.item()) <= self.bins.capacity and
+              int(self.regions.count.item()) <= self.regions.capacity)
+        if plan is not None:
+            ok = ok and int(self.d_new_n.item()) <= self.out_capacity
+        return ok
