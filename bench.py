@@ -338,6 +338,9 @@ def run_ours(args, rank, world, local_rank):
         batched = batched_vs_plain(g, tg, dev, args.batch_views, max(3, min(args.steps, 20)), flush,
                                    cfg1["width"], cfg1["height"], cfg1["ring_radius"],
                                    autotune=args.autotune)
+    loop = None
+    if not args.no_train:
+        loop = densify_loop(dev)
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
@@ -356,6 +359,7 @@ def run_ours(args, rank, world, local_rank):
         "stages_ms": {k: round(v, 4) for k, v in per_stage.items()},
         "batched_vs_plain": batched,
         "eq2_step": eq2,
+        "densify_loop": loop,
         "stage_gbs": {k: round(sb[k] / (per_stage[k] * 1e-3) / 1e9, 1) for k in per_stage
                       if k in sb and per_stage[k] > 0},
         "workload_counts": {"visible": n_vis, "instances": K, "regions": R,
@@ -365,6 +369,26 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
     }
     return result
+
+
+def densify_loop(dev):
+    """The small-scale analogue of the paper's training-time comparison: a coarse
+    model (5% of a 200,000-Gaussian cluster scene's points) fitted to 48 ring views
+    at 480x320 for 6,000 iterations, densified every 100 iterations until 3,000 with
+    Eq. 2 candidates split by AdpSplit (errors of 10 sampled views) or by the
+    vanilla split; PSNR on 4 held-out views."""
+    import scenes
+    from paper_2605_06876_b300 import ops, train
+
+    gt_sc = scenes.scene_clusters(70, 200_000, 3)
+    gt = ops.Gaussians.from_scene(gt_sc, dev)
+    init = ops.Gaussians.from_scene(scenes.scene_initial_points(gt_sc, 0.05, 71), dev)
+    tr = scenes.ring_cameras(72, 48, 14.0, 480, 320)
+    te = scenes.ring_cameras(73, 4, 14.0, 480, 320)
+    res = train.compare(gt, init, tr, te, iters=6000, densify_until=3000)
+    res["config"] = ("200k-Gaussian cluster scene, 5% initial points, 48 training and 4 test "
+                     "ring views at 480x320, 6000 iterations, densification every 100 until 3000")
+    return res
 
 
 def eq2_step(g, cams, target, dev, flush, steps):
@@ -579,6 +603,8 @@ def main():
                     help="pick the tile shape of the batched comparison with the autotuner")
     ap.add_argument("--batch-views", type=int, default=16,
                     help="views of the batched-vs-plain comparison (0 or 1: skip)")
+    ap.add_argument("--no-train", action="store_true",
+                    help="skip the densification-loop comparison (vanilla split vs AdpSplit)")
     ap.add_argument("--no-eq2", action="store_true",
                     help="skip the timing of the step with the Eq. 2 candidate choice")
     ap.add_argument("--no-launch-count", action="store_true",

@@ -39,6 +39,7 @@ __all__ = [
     "fallback_noise",
     "error_stage_inputs",
     "subscene_for_gradients",
+    "scene_initial_points",
     "CONFIGS",
 ]
 
@@ -274,6 +275,30 @@ def subscene_for_gradients(seed, n=64, width=32, height=32):
     sc["logscale"] = _f32(rng.normal(-2.3, 0.3, size=(n, 3)))
     sc["logit"] = _f32(rng.uniform(-1.5, 1.5, size=n))
     return sc, camera_origin_forward(width, height, 60.0)
+
+
+def scene_initial_points(scene, frac, seed, init_scale=0.1, init_opacity=0.1):
+    """A coarse initial model in the manner of a sparse point initialisation: the
+    means of a random fraction of a scene's Gaussians, jittered by a tenth of the
+    initial scale, with isotropic scales, identity rotations, one low opacity and a
+    grey colour (zero SH)."""
+    rng = np.random.default_rng(seed)
+    n_all = scene["mean"].shape[0]
+    n = max(1, int(round(frac * n_all)))
+    idx = rng.choice(n_all, size=n, replace=False)
+    mean = scene["mean"][idx].astype(np.float64) + rng.normal(0.0, 0.1 * init_scale, size=(n, 3))
+    deg = int(scene["sh_degree"])
+    K = (deg + 1) ** 2
+    quat = np.zeros((n, 4))
+    quat[:, 0] = 1.0
+    return {
+        "mean": _f32(mean),
+        "logit": _f32(np.full(n, math.log(init_opacity / (1.0 - init_opacity)))),
+        "logscale": _f32(np.full((n, 3), math.log(init_scale))),
+        "quat": _f32(quat),
+        "sh": _f32(np.zeros((n, K, 3))),
+        "sh_degree": deg,
+    }
 
 
 # Workload recipes. Scene seed 2k and target seed 2k+1 for config k.
