@@ -327,6 +327,7 @@ def run_ours(args, rank, world, local_rank):
                     "flops": int(f)} for k, f in flops.items() if k in per_stage}
     roof_alu["peak_source"] = f"{sm_count} SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz"
     launches = None if args.no_launch_count else count_launches(stepper, noise) * args.steps
+    dssim = dssim_kernels(stepper.img.rgb, target, cams, flush, dev)
     eq2 = None
     if not args.no_eq2:
         eq2 = eq2_step(g, cams, target, dev, flush, max(3, min(args.steps, 10)))
@@ -358,6 +359,7 @@ def run_ours(args, rank, world, local_rank):
         "graph": use_graph,
         "stages_ms": {k: round(v, 4) for k, v in per_stage.items()},
         "batched_vs_plain": batched,
+        "dssim": dssim,
         "eq2_step": eq2,
         "densify_loop": loop,
         "stage_gbs": {k: round(sb[k] / (per_stage[k] * 1e-3) / 1e9, 1) for k in per_stage
@@ -369,6 +371,41 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
     }
     return result
+
+
+def dssim_kernels(img, target, cams, flush, dev, reps=10):
+    """The D-SSIM loss-term kernels (forward maps, then the image gradient) on the
+    step's render, timed by CUDA events with L2 flushed before each call, against the
+    HBM roofline: per pixel 24 B read and 36 B written by the forward, 36 + 24 B read
+    and 12 B written by the backward."""
+    import torch
+
+    from paper_2605_06876_b300 import ops
+
+    dL = torch.empty_like(img)
+    loss = torch.zeros((len(cams), 2), dtype=torch.float64, device=dev)
+    need = ops.A.lib().adp_dssim_workspace_size(len(cams), ops.A.cameras(cams))
+    ws = ops.workspace(need, dev)
+    ops.dssim_loss_grad(img, target, cams, 0.2, dL=dL, loss=loss, ws=ws)
+    stream = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        flush.random_(0, 255)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ops.dssim_loss_grad(img, target, cams, 0.2, dL=dL, loss=loss, ws=ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = float(np.mean(ts))
+    P = img.shape[0]
+    nbytes = P * (24 + 36 + 36 + 24 + 12)
+    peak, kind, _ = _peaks()
+    return {"ms": round(ms, 4), "algorithmic_bytes": int(nbytes),
+            "achieved_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+            "frac_of_hbm": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4), "peak_source": kind,
+            "ssim": round(float(loss[0, 1]), 6), "l1": round(float(loss[0, 0]), 6)}
 
 
 def densify_loop(dev):

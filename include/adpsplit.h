@@ -366,6 +366,19 @@ ADP_API int adp_split_clone(int64_t n, int64_t n_cand, int64_t region_capacity,
                             adp_gaussians* pop, adp_gaussians* m_out, adp_gaussians* v_out,
                             void* ws, size_t ws_bytes, int64_t* d_new_n, adp_stream_t stream);
 
+/* --- D-SSIM loss term (the baselines' loss, unchanged by the paper, Sec. 5.1).
+ * Per view, L = (1 - lambda) mean|I^ - I_gt| + lambda (1 - SSIM), SSIM averaged
+ * over the view's pixels and the three channels, each channel under an 11x11
+ * Gaussian window (sigma 1.5, zero padding outside the image), C1 = 0.01^2,
+ * C2 = 0.03^2. Writes dL/dI^ (float [P][3]) for adp_render_backward's dL_drgb
+ * (sign(0) = 0 in the L1 term). loss (device double [V][2], may be NULL) receives
+ * each view's mean L1 error and mean SSIM. Workspace: 36 bytes per pixel. */
+ADP_API size_t adp_dssim_workspace_size(int32_t n_views, const adp_camera* cams);
+ADP_API int adp_dssim_loss_grad(const float* img, const float* target, const adp_camera* cams,
+                                int32_t n_views, float lambda, const adp_params* prm,
+                                float* dL_drgb, double* loss, void* ws, size_t ws_bytes,
+                                adp_stream_t stream);
+
 /* --- Adam (the baselines' optimizer, unchanged by the paper, Sec. 5.1). -----
  * In place, bias-corrected. The step number t >= 1 is `step`, or, if d_step
  * (device int32) is non-NULL, *d_step, which the call then increments on the

@@ -518,3 +518,64 @@ def clone_rows(theta_new, n, split_status, cand, clone_ids):
     new_row = np.cumsum(keep) - 1
     rows = new_row[np.asarray(clone_ids, np.int64)]
     return np.concatenate([theta_new, theta_new[rows]], 0)
+
+
+# --------------------------------------------------------------------------- D-SSIM loss term
+
+def ssim_window(radius=5, sigma=1.5):
+    """The normalised 1-D Gaussian of the SSIM window (11 taps, sigma 1.5)."""
+    k = np.arange(-radius, radius + 1, dtype=np.float64)
+    w = np.exp(-k * k / (2.0 * sigma * sigma))
+    return w / w.sum()
+
+
+def _window_sum(a, w):
+    """Zero-padded 'same' sum of a [H, W] map under the separable window w."""
+    from scipy.ndimage import correlate1d
+
+    t = correlate1d(a, w, axis=1, mode="constant", cval=0.0)
+    return correlate1d(t, w, axis=0, mode="constant", cval=0.0)
+
+
+def ssim_channel(xc, yc, c1=0.01 ** 2, c2=0.03 ** 2):
+    """SSIM map of one channel ([H, W] arrays) under the 11x11 Gaussian window with
+    zero padding, and its partial derivatives with respect to the window sums of x,
+    x^2 and xy: (S, dS/dm1, dS/dq11, dS/dq12)."""
+    w = ssim_window()
+    m1, m2 = _window_sum(xc, w), _window_sum(yc, w)
+    q11, q22, q12 = _window_sum(xc * xc, w), _window_sum(yc * yc, w), _window_sum(xc * yc, w)
+    A1 = 2 * m1 * m2 + c1
+    A2 = 2 * (q12 - m1 * m2) + c2
+    B1 = m1 * m1 + m2 * m2 + c1
+    B2 = (q11 - m1 * m1) + (q22 - m2 * m2) + c2
+    S = A1 * A2 / (B1 * B2)
+    dS_dm1 = (2 * m2 * A2 - 2 * m2 * A1) / (B1 * B2) - S * (2 * m1 / B1 - 2 * m1 / B2)
+    return S, dS_dm1, -S / B2, 2 * A1 / (B1 * B2)
+
+
+def dssim_loss_grad(img, tgt, width, height, lam=0.2, return_scale=False):
+    """The baselines' loss (1 - lam) mean|x - y| + lam (1 - SSIM) of one view in FP64:
+    SSIM of each channel (ssim_channel), averaged over pixels and channels; its
+    gradient with respect to the render x through the window sums (the window is
+    symmetric, so the adjoint of a window sum is the same sum). Returns
+    (mean L1, mean SSIM, dL/dx [P][3]); with return_scale also the sum of the
+    magnitudes of the three window-sum terms of each gradient entry, which nearly
+    cancel in smooth regions (the scale of a float32 computation's rounding)."""
+    x = np.asarray(img, np.float64).reshape(height, width, 3)
+    y = np.asarray(tgt, np.float64).reshape(height, width, 3)
+    w = ssim_window()
+    N = 3.0 * width * height
+    grad = np.zeros_like(x)
+    scale = np.zeros_like(x)
+    s_total = 0.0
+    for c in range(3):
+        xc, yc = x[..., c], y[..., c]
+        S, d_m1, d_q11, d_q12 = ssim_channel(xc, yc)
+        s_total += S.sum()
+        t1, t2, t3 = _window_sum(d_m1, w), 2 * xc * _window_sum(d_q11, w), yc * _window_sum(d_q12, w)
+        grad[..., c] = -lam * (t1 + t2 + t3) / N + (1 - lam) * np.sign(xc - yc) / N
+        scale[..., c] = lam * (np.abs(t1) + np.abs(t2) + np.abs(t3)) / N
+    l1 = np.abs(x - y).sum() / N
+    if return_scale:
+        return l1, s_total / N, grad.reshape(-1, 3), scale.reshape(-1, 3)
+    return l1, s_total / N, grad.reshape(-1, 3)

@@ -108,6 +108,9 @@ _PROTOS = {
                                      _vp, _vp, C.c_size_t, _vp]),
     "adp_split_clone": (C.c_int, [_i64, _i64, _i64, _vp, _vp, _i64, P(AdpGaussians),
                                   P(AdpGaussians), P(AdpGaussians), _vp, C.c_size_t, _vp, _vp]),
+    "adp_dssim_workspace_size": (C.c_size_t, [_i32, P(AdpCamera)]),
+    "adp_dssim_loss_grad": (C.c_int, [_vp, _vp, P(AdpCamera), _i32, C.c_float, P(AdpParams),
+                                      _vp, _vp, _vp, C.c_size_t, _vp]),
     "adp_adam_step": (C.c_int, [P(AdpGaussians), P(AdpGaussians), P(AdpGaussians),
                                 P(AdpGaussians), _i32, _vp, P(C.c_float), C.c_float, C.c_float,
                                 C.c_float, _vp]),

@@ -490,6 +490,25 @@ def split_clone(g: Gaussians, plan: SplitPlan, regions: Regions, candidates, clo
     return d_new_n
 
 
+def dssim_loss_grad(img, target, cams, lam=0.2, params=None, dL=None, loss=None, ws=None,
+                    stream=None):
+    """adp_dssim_loss_grad: dL/dI for L = (1 - lam) L1 + lam (1 - SSIM) per view, and
+    (in loss, float64 [V][2]) each view's mean L1 and mean SSIM."""
+    params = params or A.default_params()
+    ca = A.cameras(cams)
+    V = len(cams)
+    dev = img.device
+    dL = dL if dL is not None else torch.empty_like(img)
+    loss = loss if loss is not None else torch.empty((V, 2), dtype=F64, device=dev)
+    need = A.lib().adp_dssim_workspace_size(V, ca)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    A.check(A.lib().adp_dssim_loss_grad(_p(img), _p(target), ca, V, float(lam), C.byref(params),
+                                        _p(dL), _p(loss), _p(ws), ws.numel(), _stream(stream)),
+            "adp_dssim_loss_grad")
+    return dL, loss
+
+
 def render_backward(g: Gaussians, pr: Projected, bins: Bins, fwd: Image, cams, target=None,
                     dL_drgb=None, bg=(0.0, 0.0, 0.0), params=None, grad: Gaussians = None, ws=None,
                     stream=None, grad2d_accum=None, grad2d_visits=None):

@@ -71,12 +71,15 @@ class StageTimer:
 class PlainStep:
     def __init__(self, g: ops.Gaussians, cams, target, cand_frac=0.1, params=None,
                  bg=(0.0, 0.0, 0.0), lr=ops.ADAM_LR, bins_margin=1.15, region_margin=1.25,
-                 fused_adam=True, out_capacity=None):
+                 fused_adam=True, out_capacity=None, dssim_lambda=0.0):
         self.g = g
         # fused_adam: the Adam step of the candidates runs before the plan and the
         # compaction applies it to every other row while copying (one pass over
         # parameters and moments instead of two; same result bit for bit)
         self.fused_adam = fused_adam
+        # dssim_lambda > 0: the baselines' loss (1 - lambda) L1 + lambda (1 - SSIM),
+        # its image gradient fed to the backward; 0 keeps the pure L1 loss
+        self.dssim_lambda = float(dssim_lambda)
         self.cams = list(cams)
         self.V = len(self.cams)
         self.target = target
@@ -126,6 +129,10 @@ class PlainStep:
         self.ws_regions = ops.workspace(A.lib().adp_error_regions_workspace_size(n, self.V, ca), self.dev)
         self.ws_topk = ops.workspace(A.lib().adp_select_topk_workspace_size(n), self.dev)
         self.ws_bwd = ops.workspace(A.lib().adp_render_backward_workspace_size(n, self.V), self.dev)
+        if self.dssim_lambda > 0:
+            self.dL = torch.empty((self.P, 3), dtype=torch.float32, device=self.dev)
+            self.loss = torch.zeros((self.V, 2), dtype=torch.float64, device=self.dev)
+            self.ws_dssim = ops.workspace(A.lib().adp_dssim_workspace_size(self.V, ca), self.dev)
         self.ws_split = ops.workspace(ops.split_workspace_size(n, self.k, cap), self.dev)
         # the largest population a split can produce: no read-back inside a step
         self.out_capacity = (out_capacity if out_capacity is not None
@@ -157,9 +164,17 @@ class PlainStep:
             ops.error_regions(self.maps, self.img.dominant, self.target, n, cams, self.cand, prm,
                               regions=self.regions, ws=self.ws_regions, grow=False)
             mark("error_end")
+        if self.dssim_lambda > 0:
+            mark("dssim")
+            ops.dssim_loss_grad(self.img.rgb, self.target, cams, self.dssim_lambda, prm,
+                                dL=self.dL, loss=self.loss, ws=self.ws_dssim)
         mark("render_backward")
-        ops.render_backward(g, self.pr, self.bins, self.img, cams, target=self.target, bg=self.bg,
-                            params=prm, grad=self.grad, ws=self.ws_bwd)
+        if self.dssim_lambda > 0:
+            ops.render_backward(g, self.pr, self.bins, self.img, cams, dL_drgb=self.dL,
+                                bg=self.bg, params=prm, grad=self.grad, ws=self.ws_bwd)
+        else:
+            ops.render_backward(g, self.pr, self.bins, self.img, cams, target=self.target,
+                                bg=self.bg, params=prm, grad=self.grad, ws=self.ws_bwd)
         mark("join")
         main.wait_stream(self.side)  # join before the candidates' Adam step and the split
         if self.fused_adam:
