@@ -159,8 +159,17 @@ static int mass_shift_for(float tau) {
 // stop when the chosen digit holds exactly the keys still to take. The output is
 // the keys above the threshold and the first `remaining` keys equal to it in id
 // order, written in id order.
-constexpr int TOPK_THREADS = 1024;
-constexpr int TOPK_MAX_BLOCKS = 1024;  // bound of the grid (one block per SM)
+#ifndef ADP_TOPK_THREADS
+#define ADP_TOPK_THREADS 256
+#endif
+#ifndef ADP_TOPK_PER_SM
+#define ADP_TOPK_PER_SM 2
+#endif
+constexpr int TOPK_THREADS = ADP_TOPK_THREADS;
+constexpr int TOPK_PER_SM = ADP_TOPK_PER_SM;  // resident blocks per SM the grid asks for
+constexpr int TOPK_MAX_BLOCKS = 1024;         // bound of the grid
+static_assert(TOPK_THREADS >= 256 && TOPK_THREADS <= 1024 && TOPK_THREADS % 32 == 0,
+              "the digit sums take 256 threads and the flag scan one warp of warp totals");
 constexpr int TOPK_BARRIER_SPINS = 1 << 24;
 
 struct TopkCoop {
@@ -202,7 +211,7 @@ __device__ __forceinline__ int topk_flag_scan(bool f, int* s_w, int* total) {
   if (lane == 0) s_w[warp] = __popc(b);
   __syncthreads();
   if (warp == 0) {
-    int x = s_w[lane], inc = x;
+    int x = lane < TOPK_THREADS / 32 ? s_w[lane] : 0, inc = x;
     for (int o = 1; o < 32; o <<= 1) {
       int y = __shfl_up_sync(0xffffffffu, inc, o);
       if (lane >= o) inc += y;
@@ -255,8 +264,8 @@ __global__ void __launch_bounds__(TOPK_THREADS)
     }
     __syncthreads();
     if (warp == 0) {
-      lo = s_lo[lane];
-      hi = s_hi[lane];
+      lo = lane < TOPK_THREADS / 32 ? s_lo[lane] : ~0ull;
+      hi = lane < TOPK_THREADS / 32 ? s_hi[lane] : 0ull;
       for (int o = 16; o > 0; o >>= 1) {
         lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
         hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
@@ -355,14 +364,16 @@ __global__ void topk_coop_init_kernel(unsigned long long* mm) {
   if (threadIdx.x < 16) mm[threadIdx.x] = (threadIdx.x & 1) ? 0ull : ~0ull;
 }
 
-// Blocks of the cooperative top-k kernel on this device: one per SM (all resident).
+// Blocks of the cooperative top-k kernel on this device: TOPK_PER_SM per SM, or
+// as many as the kernel's occupancy allows (all resident).
 static int topk_coop_grid(int* grid) {
   int dev = 0, sms = 0, per_sm = 0;
   ADP_CUDA(cudaGetDevice(&dev));
   ADP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   ADP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topk_coop_kernel, TOPK_THREADS, 0));
   ADP_CHECK_ARG(per_sm >= 1 && sms >= 1, "the top-k kernel cannot be resident on this device");
-  *grid = sms < TOPK_MAX_BLOCKS ? sms : TOPK_MAX_BLOCKS;
+  const long long g = (long long)sms * (per_sm < TOPK_PER_SM ? per_sm : TOPK_PER_SM);
+  *grid = (int)(g < TOPK_MAX_BLOCKS ? g : TOPK_MAX_BLOCKS);
   return ADP_OK;
 }
 

@@ -657,64 +657,101 @@ struct AppendArgs {
   const long long* app_off;
   const long long* counters;
   const float* noise;
-  double eta;
+  float shrink;  // ln(2 eta), rounded to float32
 };
 
-// Appended rows: one thread per new row. Its candidate is the last one whose
-// block starts at or before it (binary search over the block offsets); the row
-// is the parent copy (opacity o / (N + 1)) or child k - 1 of an ADAPTIVE
-// candidate, or vanilla child k of a FALLBACK one (mu + R (s * noise), s/(2 eta));
-// every appended row gets zero moments.
-__global__ void apply_append_kernel(AppendArgs a) {
+// Appended rows: one thread per new row, in chunks of APP_THREADS rows per
+// block. A row's candidate is the last one whose block of rows starts at or
+// before it; the block finds the candidates of its chunk with two searches in
+// global memory, stages their offsets in shared memory (at most APP_STAGE of
+// them; longer runs of candidates without rows search global memory) and each
+// thread searches there. The row is the parent copy (opacity o / (N + 1)) or
+// child k - 1 of an ADAPTIVE candidate, or vanilla child k of a FALLBACK one
+// (mu + R (s * noise), log-scale lowered by ln(2 eta)); every appended row gets
+// zero moments. The arithmetic is float32: the mean offset sums the rotated
+// noise before adding it to the mean, and the parent's new opacity logit is
+// logit(sigmoid(x) / (N + 1)) = -ln(N + (N + 1) e^-x), written for either sign
+// of x so that the exponential never overflows.
+constexpr int APP_THREADS = 128;
+constexpr int APP_STAGE = 512;
+
+__device__ __forceinline__ long long last_le_ll(const long long* off, long long lo, long long hi,
+                                               long long r) {
+  while (lo < hi) {  // last c in [lo, hi] with off[c] <= r (off[lo] <= r)
+    const long long mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= r) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ float split_parent_logit(float x, int N) {
+  const float a = (float)N, b = (float)(N + 1);
+  return x >= 0.f ? -logf(fmaf(b, expf(-x), a)) : x - logf(fmaf(a, expf(x), b));
+}
+
+__global__ void __launch_bounds__(APP_THREADS) apply_append_kernel(AppendArgs a) {
+  __shared__ long long s_off[APP_STAGE];
+  __shared__ long long s_c[2];
   if (a.counters[3] > a.out.n) return;  // the new population does not fit: write nothing
   const long long n_keep = a.counters[1], n_app = a.counters[2];
-  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n_app;
-       r += (long long)gridDim.x * blockDim.x) {
-    long long lo = 0, hi = a.nc - 1;  // largest c with app_off[c] <= r
-    while (lo < hi) {
-      const long long mid = (lo + hi + 1) >> 1;
-      if (a.app_off[mid] <= r) lo = mid;
-      else hi = mid - 1;
+  for (long long r0 = blockIdx.x * (long long)APP_THREADS; r0 < n_app;
+       r0 += (long long)gridDim.x * APP_THREADS) {
+    const long long r1 = min(r0 + APP_THREADS, n_app);
+    if (threadIdx.x < 2)
+      s_c[threadIdx.x] = last_le_ll(a.app_off, 0, a.nc - 1, threadIdx.x == 0 ? r0 : r1 - 1);
+    __syncthreads();
+    const long long c0 = s_c[0], cnt = s_c[1] - c0 + 1;
+    const bool staged = cnt <= APP_STAGE;
+    if (staged)
+      for (int q = threadIdx.x; q < cnt; q += APP_THREADS) s_off[q] = a.app_off[c0 + q];
+    __syncthreads();
+    const long long r = r0 + threadIdx.x;
+    if (r < r1) {
+      long long c, base;
+      if (staged) {
+        const long long q = last_le_ll(s_off, 0, cnt - 1, r);
+        c = c0 + q;
+        base = s_off[q];
+      } else {
+        c = last_le_ll(a.app_off, c0, c0 + cnt - 1, r);
+        base = a.app_off[c];
+      }
+      const int k = (int)(r - base);
+      const int i = a.cand[c];
+      const long long j = n_keep + r;
+      const uint8_t stt = a.status[c];
+      const float4 ml = a.in.ml[i], ls = a.in.ls[i];
+      if (stt == ADP_FALLBACK) {
+        const float4 q = a.in.q[i];
+        const float qn = 1.f / sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+        const Mat3 R = rot_of_quat(q.x * qn, q.y * qn, q.z * qn, q.w * qn);
+        const float* z = a.noise + 6 * c + 3 * k;
+        const float d0 = expf(ls.x) * z[0], d1 = expf(ls.y) * z[1], d2 = expf(ls.z) * z[2];
+        float m[3];
+        const float mu[3] = {ml.x, ml.y, ml.z};
+        for (int rr = 0; rr < 3; ++rr)
+          m[rr] = mu[rr] + fmaf(R.m[3 * rr], d0, fmaf(R.m[3 * rr + 1], d1, R.m[3 * rr + 2] * d2));
+        copy_gauss(a.in, i, a.out, j, a.planes);
+        a.out.ml[j] = make_float4(m[0], m[1], m[2], ml.w);
+        a.out.ls[j] = make_float4(ls.x - a.shrink, ls.y - a.shrink, ls.z - a.shrink, ls.w);
+      } else if (k == 0) {  // parent copy: opacity o / (N + 1), everything else unchanged
+        copy_gauss(a.in, i, a.out, j, a.planes);
+        a.out.ml[j] = make_float4(ml.x, ml.y, ml.z, split_parent_logit(ml.w, a.n_children[c]));
+      } else {
+        const float4* kid = a.kids + 4LL * (a.seg[c].x + k - 1);
+        const float4 km = kid[0], kq = kid[1], kl = kid[2], kd = kid[3];
+        a.out.ml[j] = make_float4(km.x, km.y, km.z, ml.w);
+        a.out.ls[j] = make_float4(kl.x, kl.y, kl.z, 0.f);
+        a.out.q[j] = kq;
+        a.out.sh[j] = make_float4(kd.x, kd.y, kd.z, 0.f);
+        for (int p = 1; p < a.planes; ++p)
+          a.out.sh[(long long)p * a.out.n + j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      if (a.has_m_out) zero_gauss(a.mout, j, a.planes);
+      if (a.has_v_out) zero_gauss(a.vout, j, a.planes);
     }
-    const long long c = lo;
-    const int k = (int)(r - a.app_off[c]);
-    const int i = a.cand[c];
-    const long long j = n_keep + r;
-    const uint8_t stt = a.status[c];
-    const float4 ml = a.in.ml[i], ls = a.in.ls[i], q = a.in.q[i];
-    if (stt == ADP_FALLBACK) {
-      double Rp[9];
-      quat_rot_d(q, Rp);
-      const double sp[3] = {exp((double)ls.x), exp((double)ls.y), exp((double)ls.z)};
-      const double shrink = log(2.0 * a.eta);
-      const float* z = a.noise + 6 * c + 3 * k;
-      const double dl[3] = {sp[0] * z[0], sp[1] * z[1], sp[2] * z[2]};
-      double m[3];
-      for (int rr = 0; rr < 3; ++rr)
-        m[rr] = (double)(rr == 0 ? ml.x : (rr == 1 ? ml.y : ml.z)) + Rp[3 * rr] * dl[0] +
-                Rp[3 * rr + 1] * dl[1] + Rp[3 * rr + 2] * dl[2];
-      copy_gauss(a.in, i, a.out, j, a.planes);
-      a.out.ml[j] = make_float4((float)m[0], (float)m[1], (float)m[2], ml.w);
-      a.out.ls[j] = make_float4((float)((double)ls.x - shrink), (float)((double)ls.y - shrink),
-                                (float)((double)ls.z - shrink), ls.w);
-    } else if (k == 0) {  // parent copy: opacity o / (N + 1), everything else unchanged
-      const int N = a.n_children[c];
-      const double op = 1.0 / (1.0 + exp(-(double)ml.w));
-      const double on = op / (double)(N + 1);
-      copy_gauss(a.in, i, a.out, j, a.planes);
-      a.out.ml[j] = make_float4(ml.x, ml.y, ml.z, (float)log(on / (1.0 - on)));
-    } else {
-      const float4* kid = a.kids + 4LL * (a.seg[c].x + k - 1);
-      const float4 km = kid[0], kq = kid[1], kl = kid[2], kd = kid[3];
-      a.out.ml[j] = make_float4(km.x, km.y, km.z, ml.w);
-      a.out.ls[j] = make_float4(kl.x, kl.y, kl.z, 0.f);
-      a.out.q[j] = kq;
-      a.out.sh[j] = make_float4(kd.x, kd.y, kd.z, 0.f);
-      for (int p = 1; p < a.planes; ++p)
-        a.out.sh[(long long)p * a.out.n + j] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    if (a.has_m_out) zero_gauss(a.mout, j, a.planes);
-    if (a.has_v_out) zero_gauss(a.vout, j, a.planes);
+    __syncthreads();
   }
 }
 
@@ -933,9 +970,9 @@ static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
     ap.app_off = w.app_off;
     ap.counters = w.counters;
     ap.noise = noise;
-    ap.eta = prm->eta;
-    apply_append_kernel<<<grid_for(nc * (long long)(prm->n_max > 1 ? prm->n_max + 1 : 2), 128,
-                                   148 * 32), 128, 0, st>>>(ap);
+    ap.shrink = (float)std::log(2.0 * (double)prm->eta);
+    apply_append_kernel<<<grid_for(nc * (long long)(prm->n_max > 1 ? prm->n_max + 1 : 2),
+                                   APP_THREADS, 148 * 16), APP_THREADS, 0, st>>>(ap);
   }
   ADP_LAUNCH_CHECK();
   return ADP_OK;
