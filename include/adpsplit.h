@@ -125,7 +125,8 @@ typedef struct adp_gaussians {
 typedef struct adp_projected {
   float* xy_opacity_depth; /* float4: 2D mean x, y; opacity; camera depth */
   float* conic;            /* float4: A, B, C, 0 -- inverse 2D covariance [[A, B], [B, C]] */
-  float* rgb;              /* float4: r, g, b, 0 -- SH colour for this view, clamped at 0 */
+  float* rgb;              /* float4: r, g, b, m -- SH colour for this view, clamped at 0;
+                              m = the clamped channels as a number 0..7 (bit c: channel c < 0) */
   int32_t* rect;           /* int4: tile x0, x1, y0, y1 (inclusive) of the pixel box */
   int32_t* tiles_touched;  /* number of tiles of rect; 0 = not rendered */
 } adp_projected;

@@ -58,7 +58,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = [o for o, _ in results]
     rebuilt = any(b for _, b in results)
     if force or rebuilt or not os.path.exists(LIB):
-        cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", LIB, *objs]
+        # the CUDA runtime is linked as a shared library, so that a process that also
+        # uses torch runs one runtime instance (torch's, found by soname), whose
+        # default stream orders this library's launches with torch's own
+        cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-Xlinker", "-rpath",
+               "-Xlinker", "/usr/local/cuda/lib64", "-o", LIB, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -30,7 +30,8 @@ struct BwdPixArgs {
   const float* dL_drgb;
   float bg[3];
   float alpha_min, alpha_max, log2_alpha_min;
-  float4* g2d;  // [V*n][3]
+  float4* g2d;     // [V*n][3]
+  int* tile_ctr;   // next tile to take, zero at the launch
 };
 
 // Reduce-scatter of eight per-lane values across the warp by recursive halving:
@@ -94,8 +95,8 @@ constexpr int BWD_STAGE = ADP_BWD_STAGE;
 // exactly like the scalar instruction, so the alpha test still agrees bit for bit
 // with the forward's); compares, selects and the special-function unit stay scalar.
 template <int PX>
-__global__ void __launch_bounds__(TileLanes<PX>::THREADS, ADP_BWD_MINB)
-    bwd_pixel_kernel(BwdPixArgs a, CamSet cs) {
+__device__ __forceinline__ void bwd_pixel_tile(const BwdPixArgs& a, const CamSet& cs,
+                                               const int tile) {
   static_assert(PX % 2 == 0, "pixels are processed in pairs");
   constexpr int NT = TileLanes<PX>::THREADS;
   constexpr int NP = PX / 2;
@@ -104,7 +105,6 @@ __global__ void __launch_bounds__(TileLanes<PX>::THREADS, ADP_BWD_MINB)
   __shared__ float4 s_g2[BWD_STAGE];
   __shared__ float2 s_y[BWD_STAGE];
   __shared__ int s_maxlast;
-  const int tile = blockIdx.x;
   const int v = view_of_tile(cs, tile);
   const int lt = tile - cs.tile_base[v];
   const int txs = cs.tiles_x[v];
@@ -248,12 +248,38 @@ __global__ void __launch_bounds__(TileLanes<PX>::THREADS, ADP_BWD_MINB)
   }
 }
 
+// Blocks take tiles in order from a counter (zeroed before the launch). With
+// BWD_PERSIST > 0 the grid is BWD_PERSIST resident blocks per SM, which leaves
+// registers free on every SM for the kernels of the concurrent error-statistics
+// stream: their blocks then start without waiting for tiles to retire. With 0,
+// the grid has one block per tile.
+#ifndef ADP_BWD_PERSIST
+#define ADP_BWD_PERSIST 0
+#endif
+constexpr int BWD_PERSIST = ADP_BWD_PERSIST;
+
+template <int PX>
+__global__ void __launch_bounds__(TileLanes<PX>::THREADS, ADP_BWD_MINB)
+    bwd_pixel_kernel(BwdPixArgs a, CamSet cs) {
+  __shared__ int s_tile;
+  const int n_tiles = cs.tile_base[cs.n_views];
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_ctr, 1);
+    __syncthreads();
+    const int tile = s_tile;
+    __syncthreads();  // every thread is past the previous tile and has read s_tile
+    if (tile >= n_tiles) break;
+    bwd_pixel_tile<PX>(a, cs, tile);
+  }
+}
+
 struct BwdGaussArgs {
   const float4* mean_logit;
   const float4* logscale;
   const float4* quat;
   const float* sh;
   const int* tiles;
+  const float4* rgb;  // projected colours; w holds the clamped channels
   const float4* g2d;
   long long n;
   int deg;
@@ -290,9 +316,10 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
   float g2d_norm = 0.f;  // densification statistic of this Gaussian, summed over views
   int g2d_n = 0;
   float G3[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma3 over views
-  float gsh[3 * K];
-#pragma unroll
-  for (int f = 0; f < 3 * K; ++f) gsh[f] = 0.f;
+  // SH coefficients and their gradient rows, one float4 plane at a time
+  const float4* shp = reinterpret_cast<const float4*>(a.sh) + i;
+  float4* gshp = reinterpret_cast<float4*>(a.g_sh) + i;
+  bool first_view = true;  // the SH gradient row is stored by the first view, then added to
   for (int v = 0; v < cs.n_views; ++v) {
     long long rec = (long long)v * a.n + i;
     if (a.tiles[rec] <= 0) continue;
@@ -318,38 +345,35 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
     float u[3] = {d[0] * il, d[1] * il, d[2] * il};
     float Y[16];
     sh_eval_basis(DEG, u[0], u[1], u[2], Y);
-    float shc[4 * planes];  // this Gaussian's SH coefficients
-#pragma unroll
-    for (int p = 0; p < planes; ++p) {
-      const float4 c4 = reinterpret_cast<const float4*>(a.sh)[(long long)p * a.n + i];
-      shc[4 * p] = c4.x;
-      shc[4 * p + 1] = c4.y;
-      shc[4 * p + 2] = c4.z;
-      shc[4 * p + 3] = c4.w;
-    }
-    float col[3] = {0.5f, 0.5f, 0.5f};
-#pragma unroll
-    for (int f = 0; f < 3 * K; ++f) col[f % 3] += shc[f] * Y[f / 3];
+    // channels the projection clamped at 0 pass no gradient
+    const int clamped = (int)a.rgb[rec].w;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch)
-      if (col[ch] < 0.f) gcol[ch] = 0.f;
-    float gu[3] = {0.f, 0.f, 0.f};
-    float3 dY[16];
-    if (DEG > 0) sh_eval_basis_grad(DEG, u[0], u[1], u[2], dY);
+      if (clamped & (1 << ch)) gcol[ch] = 0.f;
+    // dL/dsh = gcol Y (summed over views), and the weights w_k = sum_ch sh_k,ch gcol_ch
+    // of the basis partials in the direction gradient
+    float wk[16];
 #pragma unroll
-    for (int j = 0; j < K; ++j) {
-      float wj = 0.f;
+    for (int k = 0; k < 16; ++k) wk[k] = 0.f;
 #pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        gsh[3 * j + ch] += gcol[ch] * Y[j];
-        wj += shc[3 * j + ch] * gcol[ch];
+    for (int p = 0; p < planes; ++p) {
+      const float4 c4 = shp[(long long)p * a.n];
+      const float cf[4] = {c4.x, c4.y, c4.z, c4.w};
+      float4 o4 = first_view ? make_float4(0.f, 0.f, 0.f, 0.f) : gshp[(long long)p * a.n];
+      float g4[4] = {o4.x, o4.y, o4.z, o4.w};
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const int f = 4 * p + l;
+        if (f < 3 * K) {
+          g4[l] = fmaf(gcol[f % 3], Y[f / 3], g4[l]);
+          wk[f / 3] += cf[l] * gcol[f % 3];
+        }
       }
-      if (DEG > 0) {
-        gu[0] += wj * dY[j].x;
-        gu[1] += wj * dY[j].y;
-        gu[2] += wj * dY[j].z;
-      }
+      gshp[(long long)p * a.n] = make_float4(g4[0], g4[1], g4[2], g4[3]);
     }
+    first_view = false;
+    float gu[3] = {0.f, 0.f, 0.f};
+    if (DEG > 0) sh_grad_dot(DEG, u[0], u[1], u[2], wk, gu);
     float ud = gu[0] * u[0] + gu[1] * u[1] + gu[2] * u[2];
     for (int k = 0; k < 3; ++k) gmu[k] += (gu[k] - ud * u[k]) * il;
     // EWA
@@ -456,16 +480,6 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
   a.g_ls[i] = make_float4(gls[0], gls[1], gls[2], 0.f);
   a.g_q[i] = make_float4((gw - dotq * qw) * iq, (gx - dotq * qx) * iq, (gy - dotq * qy) * iq,
                          (gz - dotq * qz) * iq);
-#pragma unroll
-  for (int p = 0; p < planes; ++p) {
-    float v4[4];
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      int f = 4 * p + l;
-      v4[l] = f < 3 * K ? gsh[f] : 0.f;
-    }
-    reinterpret_cast<float4*>(a.g_sh)[(long long)p * a.n + i] = make_float4(v4[0], v4[1], v4[2], v4[3]);
-  }
 }
 
 // Zeroes the gradient of every Gaussian rendered in no view (or, for a
@@ -514,7 +528,7 @@ __global__ void __launch_bounds__(256) bwd_visible_kernel(const int* tiles, long
 }
 
 #ifndef ADP_BWDG_MINB  // resident 128-thread blocks per SM the register budget is sized for
-#define ADP_BWDG_MINB 1
+#define ADP_BWDG_MINB 4
 #endif
 template <int DEG>
 __global__ void __launch_bounds__(128, ADP_BWDG_MINB) bwd_gauss_kernel(BwdGaussArgs a, CamSet cs,
@@ -531,7 +545,7 @@ using namespace adp;
 extern "C" ADP_API size_t adp_render_backward_workspace_size(int64_t n, int32_t n_views) {
   if (n < 0 || n_views < 1) return 0;
   return carve_bytes<float4>(3 * (size_t)n * n_views) + carve_bytes<int>(n) +
-         carve_bytes<unsigned long long>(1);
+         carve_bytes<unsigned long long>(1) + carve_bytes<int>(1);
 }
 
 extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_projected* pr,
@@ -560,8 +574,10 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   float4* g2d = cv.take<float4>(3 * (size_t)g->n * n_views);
   int* list = cv.take<int>(g->n);
   unsigned long long* n_list = cv.take<unsigned long long>(1);
+  int* tile_ctr = cv.take<int>(1);
   ADP_CUDA(cudaMemsetAsync(g2d, 0, sizeof(float4) * 3 * (size_t)g->n * n_views, st));
   ADP_CUDA(cudaMemsetAsync(n_list, 0, sizeof(unsigned long long), st));
+  ADP_CUDA(cudaMemsetAsync(tile_ctr, 0, sizeof(int), st));
   BwdPixArgs pa;
   pa.xyod = reinterpret_cast<const float4*>(pr->xy_opacity_depth);
   pa.conic = reinterpret_cast<const float4*>(pr->conic);
@@ -579,7 +595,15 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   pa.alpha_max = prm->alpha_max;
   pa.log2_alpha_min = log2f(prm->alpha_min);
   pa.g2d = g2d;
-  bwd_pixel_kernel<BWD_PX><<<cs.tile_base[n_views], TileLanes<BWD_PX>::THREADS, 0, st>>>(pa, cs);
+  pa.tile_ctr = tile_ctr;
+  long long grid = cs.tile_base[n_views];
+  if (BWD_PERSIST > 0) {
+    int dev = 0, sms = 0;
+    ADP_CUDA(cudaGetDevice(&dev));
+    ADP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    grid = std::min<long long>(grid, (long long)sms * BWD_PERSIST);
+  }
+  bwd_pixel_kernel<BWD_PX><<<(unsigned)grid, TileLanes<BWD_PX>::THREADS, 0, st>>>(pa, cs);
   ADP_LAUNCH_CHECK();
   BwdGaussArgs ga;
   ga.mean_logit = reinterpret_cast<const float4*>(g->mean_logit);
@@ -587,6 +611,7 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   ga.quat = reinterpret_cast<const float4*>(g->quat);
   ga.sh = g->sh;
   ga.tiles = pr->tiles_touched;
+  ga.rgb = reinterpret_cast<const float4*>(pr->rgb);
   ga.g2d = g2d;
   ga.n = g->n;
   ga.deg = g->sh_degree;

@@ -132,7 +132,12 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned* s_w) {
 // Stable scatter of one pass. Ranks come from warp match masks in item order;
 // the tile is first reordered by digit in shared memory, so each digit's run is
 // written to global memory by consecutive threads.
-__global__ void __launch_bounds__(RS_THREADS)
+#ifdef ADP_RS_SCATTER_MINB
+#define ADP_RS_SCATTER_BOUNDS __launch_bounds__(RS_THREADS, ADP_RS_SCATTER_MINB)
+#else
+#define ADP_RS_SCATTER_BOUNDS __launch_bounds__(RS_THREADS)
+#endif
+__global__ void ADP_RS_SCATTER_BOUNDS
     rs_scatter_kernel(const unsigned* keys_in, const unsigned* vals_in, unsigned* keys_out,
                       unsigned* vals_out, const long long* d_n, long long tiles_max, DigitOp op,
                       const unsigned* hist, const unsigned* digit_tot) {

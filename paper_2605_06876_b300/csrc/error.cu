@@ -705,10 +705,19 @@ __global__ void ccl_border_kernel(const uint8_t* mask, const int* dom, CamSet cs
   }
 }
 
+// Every participating pixel's label becomes its root. The search only reads: a
+// thread writes nothing but its own pixel's final root, so no other write can
+// replace a root already stored (a path-halving write made here could land after
+// the owner's final write and leave a non-root ancestor in place). Concurrent
+// final writes only shorten other threads' paths to the same roots.
 __global__ void ccl_flatten_kernel(int* L, long long P) {
+  volatile int* VL = L;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
        p += (long long)gridDim.x * blockDim.x) {
-    if (L[p] >= 0) L[p] = uf_find(L, (int)p);
+    int r = VL[p];
+    if (r < 0) continue;
+    for (int q = VL[r]; q != r; q = VL[r]) r = q;
+    VL[p] = r;
   }
 }
 

@@ -91,6 +91,56 @@ __device__ __forceinline__ void sh_eval_basis_grad(int deg, float x, float y, fl
   dY[15] = make_float3(-SHC3_0 * (3.f * xx - 3.f * yy), SHC3_0 * 6.f * x * y, 0.f);
 }
 
+// g = sum_k w[k] dY[k] (the basis partials of sh_eval_basis_grad weighted by w),
+// accumulated term by term in k order without forming the partials.
+__device__ __forceinline__ void sh_grad_dot(int deg, float x, float y, float z, const float* w,
+                                            float* g) {
+  float gx = 0.f, gy = 0.f, gz = 0.f;
+  if (deg >= 1) {
+    gy = fmaf(w[1], -SHC1, gy);
+    gz = fmaf(w[2], SHC1, gz);
+    gx = fmaf(w[3], -SHC1, gx);
+  }
+  if (deg >= 2) {
+    gx = fmaf(w[4], SHC2_0 * y, gx);
+    gy = fmaf(w[4], SHC2_0 * x, gy);
+    gy = fmaf(w[5], -SHC2_0 * z, gy);
+    gz = fmaf(w[5], -SHC2_0 * y, gz);
+    gx = fmaf(w[6], -2.f * SHC2_2 * x, gx);
+    gy = fmaf(w[6], -2.f * SHC2_2 * y, gy);
+    gz = fmaf(w[6], 4.f * SHC2_2 * z, gz);
+    gx = fmaf(w[7], -SHC2_0 * z, gx);
+    gz = fmaf(w[7], -SHC2_0 * x, gz);
+    gx = fmaf(w[8], 2.f * SHC2_4 * x, gx);
+    gy = fmaf(w[8], -2.f * SHC2_4 * y, gy);
+  }
+  if (deg >= 3) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    gx = fmaf(w[9], -SHC3_0 * 6.f * x * y, gx);
+    gy = fmaf(w[9], -SHC3_0 * (3.f * xx - 3.f * yy), gy);
+    gx = fmaf(w[10], SHC3_1 * y * z, gx);
+    gy = fmaf(w[10], SHC3_1 * x * z, gy);
+    gz = fmaf(w[10], SHC3_1 * x * y, gz);
+    gx = fmaf(w[11], SHC3_2 * 2.f * x * y, gx);
+    gy = fmaf(w[11], -SHC3_2 * (4.f * zz - xx - 3.f * yy), gy);
+    gz = fmaf(w[11], -SHC3_2 * 8.f * y * z, gz);
+    gx = fmaf(w[12], -SHC3_3 * 6.f * x * z, gx);
+    gy = fmaf(w[12], -SHC3_3 * 6.f * y * z, gy);
+    gz = fmaf(w[12], SHC3_3 * (6.f * zz - 3.f * xx - 3.f * yy), gz);
+    gx = fmaf(w[13], -SHC3_2 * (4.f * zz - 3.f * xx - yy), gx);
+    gy = fmaf(w[13], SHC3_2 * 2.f * x * y, gy);
+    gz = fmaf(w[13], -SHC3_2 * 8.f * x * z, gz);
+    gx = fmaf(w[14], SHC3_5 * 2.f * x * z, gx);
+    gy = fmaf(w[14], -SHC3_5 * 2.f * y * z, gy);
+    gz = fmaf(w[14], SHC3_5 * (xx - yy), gz);
+    gx = fmaf(w[15], -SHC3_0 * (3.f * xx - 3.f * yy), gx);
+    gy = fmaf(w[15], SHC3_0 * 6.f * x * y, gy);
+  }
+  g[0] = gx;
+  g[1] = gy;
+  g[2] = gz;
+}
+
 // Reads SH float k*3+ch of Gaussian i from the float4 planes.
 __device__ __forceinline__ float sh_coef(const float* sh, long long n, long long i, int f) {
   return sh[((long long)(f >> 2) * n + i) * 4 + (f & 3)];

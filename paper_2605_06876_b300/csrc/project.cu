@@ -114,7 +114,10 @@ __device__ void project_one(const ProjectArgs& a, const CamSet& cs, long long i,
         }
         out0 = make_float4(mx, my, o, pcz);
         out1 = make_float4(cc * idet, -cb * idet, ca * idet, 0.f);
-        out2 = make_float4(fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f), 0.f);
+        // w: the channels clamped at 0 (bit c for channel c), for the backward
+        const int clamped = (col[0] < 0.f ? 1 : 0) | (col[1] < 0.f ? 2 : 0) | (col[2] < 0.f ? 4 : 0);
+        out2 = make_float4(fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f),
+                           (float)clamped);
       }
     }
   }
