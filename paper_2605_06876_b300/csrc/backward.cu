@@ -254,7 +254,7 @@ __device__ __forceinline__ void bwd_pixel_tile(const BwdPixArgs& a, const CamSet
 // stream: their blocks then start without waiting for tiles to retire. With 0,
 // the grid has one block per tile.
 #ifndef ADP_BWD_PERSIST
-#define ADP_BWD_PERSIST 0
+#define ADP_BWD_PERSIST 6
 #endif
 constexpr int BWD_PERSIST = ADP_BWD_PERSIST;
 
