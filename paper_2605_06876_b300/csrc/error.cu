@@ -705,7 +705,9 @@ __global__ void ccl_border_kernel(const uint8_t* mask, const int* dom, CamSet cs
   }
 }
 
-// Every participating pixel's label becomes its root. The search only reads: a
+// Every participating pixel's label becomes its root (only when the caller asks for
+// per-pixel labels; the moments pass finds the roots of the local roots itself). The
+// search only reads: a
 // thread writes nothing but its own pixel's final root, so no other write can
 // replace a root already stored (a path-halving write made here could land after
 // the owner's final write and leave a non-root ancestor in place). Concurrent
@@ -730,6 +732,7 @@ __global__ void zero_i64_kernel(long long* p, const long long* d_n, int per) {
 
 // Exact int64 moments per root: the tile-local components' moments, which the
 // labelling kernel left at their local roots, added to the slot of the final root.
+// The final root is found by following the labels (read only; every union is done).
 __global__ void moments_kernel(const int* lroots, const unsigned long long* n_lroots,
                                const long long* part, const int* L, const int* slot,
                                long long* mom) {
@@ -737,7 +740,9 @@ __global__ void moments_kernel(const int* lroots, const unsigned long long* n_lr
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
        t += (long long)gridDim.x * blockDim.x) {
     const int p = lroots[t];
-    const int s = slot[L[p]];
+    int r = L[p];
+    for (int q = L[r]; q != r; q = L[r]) r = q;
+    const int s = slot[r];
     const unsigned long long* src = reinterpret_cast<const unsigned long long*>(part + 6LL * p);
     unsigned long long* dst = reinterpret_cast<unsigned long long*>(mom + 6LL * s);
 #pragma unroll
@@ -1034,7 +1039,7 @@ extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* do
     ccl_border_kernel<<<dim3(grid_for((long long)max_tiles * CCL_BORDER, 256), n_views), 256, 0,
                         st>>>(maps->mask, dominant, cs, w.L);
   }
-  ccl_flatten_kernel<<<gp, 256, 0, st>>>(w.L, P);
+  if (out->labels) ccl_flatten_kernel<<<gp, 256, 0, st>>>(w.L, P);
   ADP_LAUNCH_CHECK();
   // roots -> slots
   int* L = w.L;

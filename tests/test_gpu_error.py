@@ -101,6 +101,11 @@ def test_regions_bit_exact(sizes, n_gauss, r):
     for k in ("view", "parent", "label", "band", "moments"):
         assert np.array_equal(got[k], ref[k]), k
     np.testing.assert_allclose(got["stats"], ref["stats"], rtol=1e-12, atol=1e-12)
+    # without per-pixel labels (no flatten pass: the moments pass finds the roots)
+    nolab = ops.error_regions(maps, t(dom), t(tgt), n_gauss, cams, t(cand), prm).to_numpy()
+    for k in ("view", "parent", "label", "band", "moments"):
+        assert np.array_equal(nolab[k], ref[k]), k
+    np.testing.assert_allclose(nolab["stats"], ref["stats"], rtol=1e-12, atol=1e-12)
 
 
 def test_regions_capacity_overflow_reports_count():
