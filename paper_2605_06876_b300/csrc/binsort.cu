@@ -27,7 +27,10 @@ __global__ void clamp_count_kernel(const long long* K, long long cap, long long*
 // instance's record by a binary search in shared memory. k's tile is its
 // position within the record's tile rectangle (row-major). Balanced whatever a
 // Gaussian's footprint, and consecutive threads write consecutive instances.
+// A chunk is one tile of the radix sort, so the CTA also writes that tile's
+// histogram of the tile sort's first digit (the low 8 bits of the key).
 constexpr int DUP_CHUNK = 2048;
+static_assert(DUP_CHUNK == RS_TILE, "a duplication chunk is one radix-sort tile");
 constexpr unsigned TILE_NONE = 0xffffffffu;  // sorts after every real tile
 
 // Whether the ellipse q(d) = d^T C d <= k around the 2D mean (the pixels where
@@ -70,14 +73,17 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const unsigned* vvals, c
                                                         long long cap, const int4* rect,
                                                         const float4* xyod, const float4* conic,
                                                         float alpha_min, long long n, CamSet cs,
-                                                        unsigned* tkeys, int* inst) {
+                                                        unsigned* tkeys, int* inst, unsigned* hist,
+                                                        long long tiles_max) {
   __shared__ long long s_off[DUP_CHUNK];
   __shared__ long long s_j[2];
+  __shared__ unsigned s_h[RS_BINS];
   const long long N = *d_nvis, K = *d_K;
   if (K > cap || N == 0) return;
   for (long long k0 = (long long)blockIdx.x * DUP_CHUNK; k0 < K; k0 += (long long)gridDim.x * DUP_CHUNK) {
     const long long k1 = min(k0 + DUP_CHUNK, K);
     if (threadIdx.x < 2) s_j[threadIdx.x] = last_le(offs, N, threadIdx.x == 0 ? k0 : k1 - 1);
+    for (int d = threadIdx.x; d < RS_BINS; d += blockDim.x) s_h[d] = 0u;
     __syncthreads();
     const long long j0 = s_j[0];
     const int cnt = (int)(s_j[1] - j0 + 1);  // <= k1 - k0: every record owns >= 1 instance
@@ -108,7 +114,11 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const unsigned* vvals, c
       }
       tkeys[k] = key;
       inst[k] = i;
+      atomicAdd(&s_h[key & 255u], 1u);
     }
+    __syncthreads();
+    const long long t = k0 / DUP_CHUNK;
+    for (int d = threadIdx.x; d < RS_BINS; d += blockDim.x) hist[(size_t)d * tiles_max + t] = s_h[d];
     __syncthreads();
   }
 }
@@ -226,14 +236,15 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
         vvals, offs, &w.counters[0], (const long long*)bins->n_instances, cap,
         reinterpret_cast<const int4*>(pr->rect), xyod,
         reinterpret_cast<const float4*>(pr->conic), prm->alpha_min, n, cs, w.tkeys,
-        bins->inst_gauss);
+        bins->inst_gauss, w.sort.hist, w.sort.tiles_max);
     ADP_LAUNCH_CHECK();
     int bits = bits_for(n_tiles);  // the filtered key TILE_NONE sorts after every tile
     DigitOp tp[4];
     int ntp = 0;
     for (int s = 0; s < bits; s += 8) tp[ntp++] = DigitOp{s, 0u};
+    // the first pass's tile histograms come from the duplication
     rc = radix_sort_pairs(w.tkeys, reinterpret_cast<unsigned*>(bins->inst_gauss),
-                          &w.counters[1], cap, tp, ntp, w.sort, st);
+                          &w.counters[1], cap, tp, ntp, w.sort, st, /*first_hist_done=*/true);
     if (rc) return rc;
     // 6. per-tile ranges
     tile_ranges_kernel<<<grid_for(cap, 256, 148 * 16), 256, 0, st>>>(

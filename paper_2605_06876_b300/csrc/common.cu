@@ -303,9 +303,9 @@ __global__ void __launch_bounds__(1024)
 
 int radix_sort_pairs(unsigned* keys, unsigned* vals, const long long* d_n, long long n_max,
                      const DigitOp* passes, int n_passes, const SortWorkspace& w,
-                     cudaStream_t st) {
+                     cudaStream_t st, bool first_hist_done) {
   if (n_max <= 0 || n_passes <= 0) return ADP_OK;
-  if (n_max <= SMALL_SORT_MAX && n_passes <= 4) {  // one launch for a small sort
+  if (n_max <= SMALL_SORT_MAX && n_passes <= 4 && !first_hist_done) {  // one small launch
     SmallPasses sp;
     sp.count = n_passes;
     for (int p = 0; p < n_passes; ++p) sp.op[p] = passes[p];
@@ -316,8 +316,9 @@ int radix_sort_pairs(unsigned* keys, unsigned* vals, const long long* d_n, long 
   unsigned *ka = keys, *va = vals, *kb = w.keys_alt, *vb = w.vals_alt;
   long long grid = w.tiles_max < 148 * 8 ? w.tiles_max : 148 * 8;
   for (int p = 0; p < n_passes; ++p) {
-    rs_hist_kernel<<<(unsigned)grid, RS_THREADS, 0, st>>>(ka, va, d_n, w.tiles_max, passes[p],
-                                                           w.hist);
+    if (p > 0 || !first_hist_done)
+      rs_hist_kernel<<<(unsigned)grid, RS_THREADS, 0, st>>>(ka, va, d_n, w.tiles_max, passes[p],
+                                                             w.hist);
     rs_scan_kernel<<<RS_BINS, RS_THREADS, 0, st>>>(w.hist, d_n, w.tiles_max, w.digit_tot);
     rs_scatter_kernel<<<(unsigned)grid, RS_THREADS, 0, st>>>(ka, va, kb, vb, d_n, w.tiles_max,
                                                               passes[p], w.hist, w.digit_tot);

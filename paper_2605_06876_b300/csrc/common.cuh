@@ -314,8 +314,11 @@ __global__ void rs_scatter_kernel(const unsigned* keys_in, const unsigned* vals_
 // Sorts (keys, vals) in place by the given passes. passes[k] is a DigitOp;
 // n_max bounds the device count *d_n. Up to SMALL_SORT_MAX items (and four
 // passes) the sort runs in a single one-block launch.
+// first_hist_done: the caller already wrote the first pass's per-tile histograms
+// (hist[digit * tiles_max + tile], every digit of every tile of *d_n items).
 int radix_sort_pairs(unsigned* keys, unsigned* vals, const long long* d_n, long long n_max,
-                     const DigitOp* passes, int n_passes, const SortWorkspace& w, cudaStream_t st);
+                     const DigitOp* passes, int n_passes, const SortWorkspace& w, cudaStream_t st,
+                     bool first_hist_done = false);
 
 inline int bits_for(long long v) {
   int b = 0;
