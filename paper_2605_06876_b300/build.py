@@ -1,8 +1,8 @@
 """Builds libadpsplit.so (every CUDA source of csrc/, sm_103a) in place.
 
 Objects go to _build/ next to this file and are recompiled only when a source or
-header is newer. The library links the CUDA runtime statically, so it loads
-beside any PyTorch build.
+header is newer. The library links the CUDA runtime as a shared library, so a
+process that also uses PyTorch runs a single runtime instance.
 """
 from __future__ import annotations
 

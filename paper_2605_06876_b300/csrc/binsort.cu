@@ -22,15 +22,22 @@ __global__ void clamp_count_kernel(const long long* K, long long cap, long long*
 }
 
 // Load-balanced duplication: each CTA takes a chunk of DUP_CHUNK consecutive
-// instances, stages the instance offsets of the records that own them in shared
-// memory (one global binary search per chunk end), and every thread finds its
-// instance's record by a binary search in shared memory. k's tile is its
-// position within the record's tile rectangle (row-major). Balanced whatever a
-// Gaussian's footprint, and consecutive threads write consecutive instances.
-// A chunk is one tile of the radix sort, so the CTA also writes that tile's
-// histogram of the tile sort's first digit (the low 8 bits of the key).
+// instances. The record owning the chunk's first instance comes from the offset
+// scan (chunk_first), the chunk's record offsets are staged in shared memory, and
+// the chunk is processed in sub-chunks of DUP_SUB instances: the (at most
+// DUP_SUB + 1) records a sub-chunk overlaps are loaded once, one thread each,
+// into shared memory (view, id, tile origin and width, 2D mean, conic and the
+// alpha cut-off), then every thread finds its instance's record by a binary
+// search in shared memory. k's tile is its position within the record's tile
+// rectangle (row-major). Balanced whatever a Gaussian's footprint, no dependent
+// global loads per instance, and consecutive threads write consecutive
+// instances. A chunk is one tile of the radix sort, so the CTA also writes that
+// tile's histogram of the tile sort's first digit (the low 8 bits of the key).
 constexpr int DUP_CHUNK = 2048;
+constexpr int DUP_SUB = 512;
+constexpr int DUP_THREADS = 256;
 static_assert(DUP_CHUNK == RS_TILE, "a duplication chunk is one radix-sort tile");
+static_assert(DUP_CHUNK % DUP_SUB == 0, "sub-chunks tile the chunk");
 constexpr unsigned TILE_NONE = 0xffffffffu;  // sorts after every real tile
 
 // Whether the ellipse q(d) = d^T C d <= k around the 2D mean (the pixels where
@@ -58,67 +65,83 @@ __device__ __forceinline__ bool ellipse_meets_rect(float mx, float my, float A, 
   return qmin <= k * 1.0001f + 1e-3f;
 }
 
-__device__ __forceinline__ long long last_le(const long long* offs, long long n, long long k) {
-  long long lo = 0, hi = n - 1;  // last j with offs[j] <= k (offs[0] = 0 <= k)
+// Last q in [lo, hi] with off[q] <= k (off[lo] <= k).
+__device__ __forceinline__ int last_le_s(const int* off, int lo, int hi, int k) {
   while (lo < hi) {
-    long long mid = (lo + hi + 1) >> 1;
-    if (offs[mid] <= k) lo = mid;
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= k) lo = mid;
     else hi = mid - 1;
   }
   return lo;
 }
 
-__global__ void __launch_bounds__(256) duplicate_kernel(const unsigned* vvals, const long long* offs,
-                                                        const long long* d_nvis, const long long* d_K,
-                                                        long long cap, const int4* rect,
-                                                        const float4* xyod, const float4* conic,
-                                                        float alpha_min, long long n, CamSet cs,
-                                                        unsigned* tkeys, int* inst, unsigned* hist,
-                                                        long long tiles_max) {
-  __shared__ long long s_off[DUP_CHUNK];
-  __shared__ long long s_j[2];
+__global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
+    const unsigned* vvals, const long long* offs, const int* chunk_first, const long long* d_nvis,
+    const long long* d_K, long long cap, const int4* rect, const float4* xyod, const float4* conic,
+    float alpha_min, long long n, CamSet cs, unsigned* tkeys, int* inst, unsigned* hist,
+    long long tiles_max) {
+  __shared__ int s_off[DUP_CHUNK + 1];      // record offsets of the chunk
+  __shared__ int s_i[DUP_SUB + 1];          // Gaussian id
+  __shared__ int s_org[DUP_SUB + 1];        // first tile column | first tile row << 16
+  __shared__ int s_wv[DUP_SUB + 1];         // rectangle width | view << 16 | (multi-tile) << 31
+  __shared__ float4 s_e0[DUP_SUB + 1];      // 2D mean, conic A, B
+  __shared__ float2 s_e1[DUP_SUB + 1];      // conic C, cut-off k
   __shared__ unsigned s_h[RS_BINS];
   const long long N = *d_nvis, K = *d_K;
   if (K > cap || N == 0) return;
-  for (long long k0 = (long long)blockIdx.x * DUP_CHUNK; k0 < K; k0 += (long long)gridDim.x * DUP_CHUNK) {
-    const long long k1 = min(k0 + DUP_CHUNK, K);
-    if (threadIdx.x < 2) s_j[threadIdx.x] = last_le(offs, N, threadIdx.x == 0 ? k0 : k1 - 1);
-    for (int d = threadIdx.x; d < RS_BINS; d += blockDim.x) s_h[d] = 0u;
+  const long long n_chunks = (K + DUP_CHUNK - 1) / DUP_CHUNK;
+  for (long long t = blockIdx.x; t < n_chunks; t += gridDim.x) {
+    const long long k0 = t * DUP_CHUNK;
+    const int kn = (int)min((long long)DUP_CHUNK, K - k0);  // instances in the chunk
+    const long long j0 = chunk_first[t];
+    const long long j1 = t + 1 < n_chunks ? (long long)chunk_first[t + 1] : N - 1;
+    const int cnt = (int)(j1 - j0 + 1);  // <= DUP_CHUNK + 1: every record owns >= 1 instance
+    for (int q = threadIdx.x; q < cnt; q += DUP_THREADS) s_off[q] = (int)(offs[j0 + q] - k0);
+    for (int d = threadIdx.x; d < RS_BINS; d += DUP_THREADS) s_h[d] = 0u;
     __syncthreads();
-    const long long j0 = s_j[0];
-    const int cnt = (int)(s_j[1] - j0 + 1);  // <= k1 - k0: every record owns >= 1 instance
-    for (int q = threadIdx.x; q < cnt; q += blockDim.x) s_off[q] = offs[j0 + q];
-    __syncthreads();
-    for (long long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-      int lo = 0, hi = cnt - 1;
-      while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (s_off[mid] <= k) lo = mid;
-        else hi = mid - 1;
+    for (int a0 = 0; a0 < kn; a0 += DUP_SUB) {
+      const int a1 = min(a0 + DUP_SUB, kn);
+      // records of the sub-chunk (the same search in every thread)
+      const int sa = last_le_s(s_off, 0, cnt - 1, a0);
+      const int sb = last_le_s(s_off, sa, cnt - 1, a1 - 1);
+      for (int q = threadIdx.x; q <= sb - sa; q += DUP_THREADS) {
+        const unsigned p = vvals[j0 + sa + q];
+        const int v = (int)(p / (unsigned long long)n);
+        const int4 r = rect[p];
+        const float4 xy = xyod[p], cn = conic[p];
+        const int w = r.y - r.x + 1;
+        const bool multi = w * (r.w - r.z + 1) > 1;
+        s_i[q] = (int)(p - (unsigned long long)v * n);
+        s_org[q] = r.x | (r.z << 16);
+        s_wv[q] = w | (v << 16) | (multi ? (int)0x80000000u : 0);
+        s_e0[q] = make_float4(xy.x, xy.y, cn.x, cn.y);
+        s_e1[q] = make_float2(cn.z, multi ? 2.f * __logf(xy.z / alpha_min) : 0.f);
       }
-      unsigned p = vvals[j0 + lo];
-      int v = (int)(p / (unsigned long long)n);
-      int i = (int)(p - (unsigned long long)v * n);
-      int4 r = rect[p];
-      int w = r.y - r.x + 1;
-      int t = (int)(k - s_off[lo]);
-      int ty = r.z + t / w, tx = r.x + t % w;
-      unsigned key = (unsigned)(cs.tile_base[v] + ty * cs.tiles_x[v] + tx);
-      if (w * (r.w - r.z + 1) > 1) {  // a one-tile rectangle always meets its ellipse
-        float4 xy = xyod[p], cn = conic[p];
-        float kk = 2.f * __logf(xy.z / alpha_min);
-        float x0 = (float)(tx * cs.tile_w), y0 = (float)(ty * cs.tile_h);
-        float x1 = fminf(x0 + (float)(cs.tile_w - 1), (float)(cs.cam[v].width - 1));
-        float y1 = fminf(y0 + (float)(cs.tile_h - 1), (float)(cs.cam[v].height - 1));
-        if (!ellipse_meets_rect(xy.x, xy.y, cn.x, cn.y, cn.z, kk, x0, x1, y0, y1)) key = TILE_NONE;
+      __syncthreads();
+      for (int kk = a0 + threadIdx.x; kk < a1; kk += DUP_THREADS) {
+        const int lo = last_le_s(s_off, sa, sb, kk);
+        const int q = lo - sa;
+        const int org = s_org[q], wv = s_wv[q];
+        const int w = wv & 0xffff, v = (wv >> 16) & 0x7fff;
+        const int tt = kk - s_off[lo];
+        const int ty = (org >> 16) + tt / w, tx = (org & 0xffff) + tt % w;
+        unsigned key = (unsigned)(cs.tile_base[v] + ty * cs.tiles_x[v] + tx);
+        if (wv < 0) {  // a one-tile rectangle always meets its ellipse
+          const float4 e0 = s_e0[q];
+          const float2 e1 = s_e1[q];
+          const float x0 = (float)(tx * cs.tile_w), y0 = (float)(ty * cs.tile_h);
+          const float x1 = fminf(x0 + (float)(cs.tile_w - 1), (float)(cs.cam[v].width - 1));
+          const float y1 = fminf(y0 + (float)(cs.tile_h - 1), (float)(cs.cam[v].height - 1));
+          if (!ellipse_meets_rect(e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, x0, x1, y0, y1))
+            key = TILE_NONE;
+        }
+        tkeys[k0 + kk] = key;
+        inst[k0 + kk] = s_i[q];
+        atomicAdd(&s_h[key & 255u], 1u);
       }
-      tkeys[k] = key;
-      inst[k] = i;
-      atomicAdd(&s_h[key & 255u], 1u);
+      __syncthreads();
     }
-    __syncthreads();
-    const long long t = k0 / DUP_CHUNK;
-    for (int d = threadIdx.x; d < RS_BINS; d += blockDim.x) hist[(size_t)d * tiles_max + t] = s_h[d];
+    for (int d = threadIdx.x; d < RS_BINS; d += DUP_THREADS) hist[(size_t)d * tiles_max + t] = s_h[d];
     __syncthreads();
   }
 }
@@ -142,13 +165,17 @@ struct BinWs {
   unsigned* vvals;
   long long* offs;
   unsigned* tkeys;
+  int* chunk_first;  // [cap / DUP_CHUNK + 1] record owning each chunk's first instance
   SortWorkspace sort;
 };
+
+static long long dup_chunks(long long cap) { return (cap + DUP_CHUNK - 1) / DUP_CHUNK + 1; }
 
 static size_t bin_ws_bytes(long long nv, long long cap) {
   long long m = nv > cap ? nv : cap;
   return carve_bytes<long long>(4) + scan_workspace_bytes(nv) + 2 * carve_bytes<unsigned>(nv) +
-         carve_bytes<long long>(nv) + carve_bytes<unsigned>(cap) + sort_workspace_bytes(m);
+         carve_bytes<long long>(nv) + carve_bytes<unsigned>(cap) + carve_bytes<int>(dup_chunks(cap)) +
+         sort_workspace_bytes(m);
 }
 
 static BinWs carve_bin(Carver& c, long long nv, long long cap) {
@@ -160,6 +187,7 @@ static BinWs carve_bin(Carver& c, long long nv, long long cap) {
   w.vvals = c.take<unsigned>(nv);
   w.offs = c.take<long long>(nv);
   w.tkeys = c.take<unsigned>(cap);
+  w.chunk_first = c.take<int>(dup_chunks(cap));
   w.sort = carve_sort(c, m);
   return w;
 }
@@ -222,18 +250,27 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
   if (rc) return rc;
 
   // 3. instance offsets in sorted order; total -> n_instances
+  // (and the record owning the first instance of every duplication chunk)
   long long* offs = w.offs;
+  int* chunk_first = w.chunk_first;
+  const long long n_chunk_max = (cap + DUP_CHUNK - 1) / DUP_CHUNK;
   rc = scan_exclusive([=] __device__(long long j) -> long long { return tiles[vvals[j]]; },
-                      [=] __device__(long long j, long long pre) { offs[j] = pre; }, nv,
-                      &w.counters[0], (long long*)bins->n_instances, w.scan, st);
+                      [=] __device__(long long j, long long pre) {
+                        offs[j] = pre;
+                        const long long end = pre + tiles[vvals[j]];
+                        for (long long c = (pre + DUP_CHUNK - 1) / DUP_CHUNK;
+                             c < n_chunk_max && c * DUP_CHUNK < end; ++c)
+                          chunk_first[c] = (int)j;
+                      },
+                      nv, &w.counters[0], (long long*)bins->n_instances, w.scan, st);
   if (rc) return rc;
   clamp_count_kernel<<<1, 1, 0, st>>>((const long long*)bins->n_instances, cap, &w.counters[1]);
 
   // 4. duplicate into tiles, 5. stable sort by tile
   if (cap > 0) {
-    duplicate_kernel<<<(unsigned)std::min<long long>((cap + DUP_CHUNK - 1) / DUP_CHUNK, 148 * 8), 256,
-                       0, st>>>(
-        vvals, offs, &w.counters[0], (const long long*)bins->n_instances, cap,
+    duplicate_kernel<<<(unsigned)std::min<long long>((cap + DUP_CHUNK - 1) / DUP_CHUNK, 148 * 8),
+                       DUP_THREADS, 0, st>>>(
+        vvals, offs, chunk_first, &w.counters[0], (const long long*)bins->n_instances, cap,
         reinterpret_cast<const int4*>(pr->rect), xyod,
         reinterpret_cast<const float4*>(pr->conic), prm->alpha_min, n, cs, w.tkeys,
         bins->inst_gauss, w.sort.hist, w.sort.tiles_max);

@@ -121,9 +121,9 @@ __device__ float4 rot_quat_d(const double* R) {
     z = 0.5 * r; double f = 0.5 / r;
     w = (R[3] - R[1]) * f; x = (R[2] + R[6]) * f; y = (R[5] + R[7]) * f;
   }
-  double nq = sqrt(w * w + x * x + y * y + z * z);
-  if (w < 0) nq = -nq;
-  return make_float4((float)(w / nq), (float)(x / nq), (float)(y / nq), (float)(z / nq));
+  double inq = 1.0 / sqrt(w * w + x * x + y * y + z * z);
+  if (w < 0) inq = -inq;
+  return make_float4((float)(w * inq), (float)(x * inq), (float)(y * inq), (float)(z * inq));
 }
 
 // Eigen-decomposition of a symmetric 3x3 matrix by cyclic Jacobi rotations
@@ -321,14 +321,18 @@ __global__ void proposal_kernel(ProposalArgs a, CamSet cs) {
   }
 }
 
+// The stored child is float32, so its log-scales are taken in float32 (within
+// two float ulps of the rounded FP64 logarithm, at a fraction of the cost on the
+// reduced-rate FP64 pipe) and the colour is mapped to the DC coefficient by a
+// multiplication by 1 / C0 = 2 sqrt(pi).
 __device__ void store_child(float4* kid, const double* mu, const double* R, const double* s,
                             const double* rgb) {
   kid[0] = make_float4((float)mu[0], (float)mu[1], (float)mu[2], 0.f);
   kid[1] = rot_quat_d(R);
-  kid[2] = make_float4((float)log(s[0]), (float)log(s[1]), (float)log(s[2]), 0.f);
-  const double C0 = 0.28209479177387814;
-  kid[3] = make_float4((float)((rgb[0] - 0.5) / C0), (float)((rgb[1] - 0.5) / C0),
-                       (float)((rgb[2] - 0.5) / C0), 0.f);
+  kid[2] = make_float4(logf((float)s[0]), logf((float)s[1]), logf((float)s[2]), 0.f);
+  const double inv_C0 = 3.5449077018110318;  // 1 / C0 of the degree-0 SH basis
+  kid[3] = make_float4((float)((rgb[0] - 0.5) * inv_C0), (float)((rgb[1] - 0.5) * inv_C0),
+                       (float)((rgb[2] - 0.5) * inv_C0), 0.f);
 }
 
 struct MergeArgs {
