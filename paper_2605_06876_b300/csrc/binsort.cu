@@ -27,39 +27,42 @@ __global__ void clamp_count_kernel(const long long* K, long long cap, long long*
 // the chunk is processed in sub-chunks of DUP_SUB instances: the (at most
 // DUP_SUB + 1) records a sub-chunk overlaps are loaded once, one thread each,
 // into shared memory (view, id, tile origin and width, 2D mean, conic and the
-// alpha cut-off), then every thread finds its instance's record by a binary
-// search in shared memory. k's tile is its position within the record's tile
-// rectangle (row-major). Balanced whatever a Gaussian's footprint, no dependent
-// global loads per instance, and consecutive threads write consecutive
-// instances. A chunk is one tile of the radix sort, so the CTA also writes that
+// alpha cut-off), each record also marking the slot where it starts, and an
+// inclusive max-scan over the slots gives every instance its record. Each thread
+// takes two consecutive instances. k's tile is its position within the record's
+// tile rectangle (row-major). Balanced whatever a Gaussian's footprint, no
+// dependent global loads and no search per instance, and consecutive threads
+// write consecutive instance pairs. A chunk is one tile of the radix sort, so the CTA also writes that
 // tile's histogram of the tile sort's first digit (the low 8 bits of the key).
 constexpr int DUP_CHUNK = 2048;
 constexpr int DUP_SUB = 512;
 constexpr int DUP_THREADS = 256;
 static_assert(DUP_CHUNK == RS_TILE, "a duplication chunk is one radix-sort tile");
 static_assert(DUP_CHUNK % DUP_SUB == 0, "sub-chunks tile the chunk");
+static_assert(DUP_SUB == 2 * DUP_THREADS, "each thread takes two slots of a sub-chunk");
 constexpr unsigned TILE_NONE = 0xffffffffu;  // sorts after every real tile
 
 // Whether the ellipse q(d) = d^T C d <= k around the 2D mean (the pixels where
 // o exp(-q/2) >= alpha_min) reaches the rectangle of pixel centres
 // [x0, x1] x [y0, y1]: the minimum of the convex quadratic over the rectangle is
 // 0 if the mean is inside, else it lies on an edge, where the 1-D minimum is the
-// clamped stationary point. A small relative and absolute margin keeps the test
-// conservative under float32 rounding, so no contributing pixel is ever lost.
+// clamped stationary point (dy = -B dx / C on a vertical edge, dx = -B dy / A on
+// a horizontal one; rbc = -B / C and rba = -B / A come precomputed per record).
+// A small relative and absolute margin keeps the test conservative under float32
+// rounding, so no contributing pixel is ever lost.
 __device__ __forceinline__ bool ellipse_meets_rect(float mx, float my, float A, float B, float C,
-                                                   float k, float x0, float x1, float y0,
-                                                   float y1) {
+                                                   float k, float rbc, float rba, float x0,
+                                                   float x1, float y0, float y1) {
   if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
   float qmin = 3.4e38f;
-  // vertical edges x = x0, x1: q(dy) = A dx^2 + 2 B dx dy + C dy^2
-  for (int e = 0; e < 2; ++e) {
+  for (int e = 0; e < 2; ++e) {  // vertical edges x = x0, x1: q(dy) = A dx^2 + 2 B dx dy + C dy^2
     float dx = (e ? x1 : x0) - mx;
-    float dy = fminf(fmaxf(-B * dx / C, y0 - my), y1 - my);
+    float dy = fminf(fmaxf(rbc * dx, y0 - my), y1 - my);
     qmin = fminf(qmin, A * dx * dx + 2.f * B * dx * dy + C * dy * dy);
   }
   for (int e = 0; e < 2; ++e) {  // horizontal edges y = y0, y1
     float dy = (e ? y1 : y0) - my;
-    float dx = fminf(fmaxf(-B * dy / A, x0 - mx), x1 - mx);
+    float dx = fminf(fmaxf(rba * dy, x0 - mx), x1 - mx);
     qmin = fminf(qmin, A * dx * dx + 2.f * B * dx * dy + C * dy * dy);
   }
   return qmin <= k * 1.0001f + 1e-3f;
@@ -78,18 +81,22 @@ __device__ __forceinline__ int last_le_s(const int* off, int lo, int hi, int k) 
 __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
     const unsigned* vvals, const long long* offs, const int* chunk_first, const long long* d_nvis,
     const long long* d_K, long long cap, const int4* rect, const float4* xyod, const float4* conic,
-    float alpha_min, long long n, CamSet cs, unsigned* tkeys, int* inst, unsigned* hist,
-    long long tiles_max) {
+    float alpha_min, long long n, CamSet cs, unsigned* tkeys, int* inst, bool inst_pairs,
+    unsigned* hist, long long tiles_max) {
   __shared__ int s_off[DUP_CHUNK + 1];      // record offsets of the chunk
   __shared__ int s_i[DUP_SUB + 1];          // Gaussian id
   __shared__ int s_org[DUP_SUB + 1];        // first tile column | first tile row << 16
   __shared__ int s_wv[DUP_SUB + 1];         // rectangle width | view << 16 | (multi-tile) << 31
   __shared__ float4 s_e0[DUP_SUB + 1];      // 2D mean, conic A, B
-  __shared__ float2 s_e1[DUP_SUB + 1];      // conic C, cut-off k
+  __shared__ float4 s_e1[DUP_SUB + 1];      // conic C, cut-off k, -B / C, -B / A
+  __shared__ int s_rec[DUP_SUB];            // record starting at each slot of the sub-chunk
+  __shared__ int s_wm[DUP_THREADS / 32];
   __shared__ unsigned s_h[RS_BINS];
   const long long N = *d_nvis, K = *d_K;
   if (K > cap || N == 0) return;
   const long long n_chunks = (K + DUP_CHUNK - 1) / DUP_CHUNK;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < DUP_SUB; e += DUP_THREADS) s_rec[e] = 0;
   for (long long t = blockIdx.x; t < n_chunks; t += gridDim.x) {
     const long long k0 = t * DUP_CHUNK;
     const int kn = (int)min((long long)DUP_CHUNK, K - k0);  // instances in the chunk
@@ -115,29 +122,70 @@ __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
         s_org[q] = r.x | (r.z << 16);
         s_wv[q] = w | (v << 16) | (multi ? (int)0x80000000u : 0);
         s_e0[q] = make_float4(xy.x, xy.y, cn.x, cn.y);
-        s_e1[q] = make_float2(cn.z, multi ? 2.f * __logf(xy.z / alpha_min) : 0.f);
+        s_e1[q] = multi ? make_float4(cn.z, 2.f * __logf(xy.z / alpha_min), -cn.y / cn.z,
+                                      -cn.y / cn.x)
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        // the first record may start before the sub-chunk; every other one starts
+        // inside it, each at its own slot
+        s_rec[q == 0 ? 0 : s_off[sa + q] - a0] = q;
       }
       __syncthreads();
-      for (int kk = a0 + threadIdx.x; kk < a1; kk += DUP_THREADS) {
-        const int lo = last_le_s(s_off, sa, sb, kk);
-        const int q = lo - sa;
+      // each thread takes two consecutive slots; a slot's record is the largest
+      // record index marked at or before it (an inclusive max-scan)
+      const int e0i = 2 * (int)threadIdx.x;
+      const int m0 = s_rec[e0i], m1 = s_rec[e0i + 1];
+      int run = max(m0, m1);
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, run, o);
+        if (lane >= o) run = max(run, y);
+      }
+      if (lane == 31) s_wm[warp] = run;
+      int before = __shfl_up_sync(0xffffffffu, run, 1);
+      if (lane == 0) before = 0;
+      __syncthreads();
+      for (int w2 = 0; w2 < warp; ++w2) before = max(before, s_wm[w2]);
+      s_rec[e0i] = 0;  // cleared for the next sub-chunk (each thread its own slots)
+      s_rec[e0i + 1] = 0;
+      const int qs[2] = {max(before, m0), max(before, max(m0, m1))};
+      unsigned keys[2];
+      int ids[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int kk = a0 + e0i + h;
+        keys[h] = TILE_NONE;
+        ids[h] = 0;
+        if (kk >= a1) continue;
+        const int q = qs[h];
         const int org = s_org[q], wv = s_wv[q];
         const int w = wv & 0xffff, v = (wv >> 16) & 0x7fff;
-        const int tt = kk - s_off[lo];
+        const int tt = kk - s_off[sa + q];
         const int ty = (org >> 16) + tt / w, tx = (org & 0xffff) + tt % w;
         unsigned key = (unsigned)(cs.tile_base[v] + ty * cs.tiles_x[v] + tx);
         if (wv < 0) {  // a one-tile rectangle always meets its ellipse
           const float4 e0 = s_e0[q];
-          const float2 e1 = s_e1[q];
+          const float4 e1 = s_e1[q];
           const float x0 = (float)(tx * cs.tile_w), y0 = (float)(ty * cs.tile_h);
           const float x1 = fminf(x0 + (float)(cs.tile_w - 1), (float)(cs.cam[v].width - 1));
           const float y1 = fminf(y0 + (float)(cs.tile_h - 1), (float)(cs.cam[v].height - 1));
-          if (!ellipse_meets_rect(e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, x0, x1, y0, y1))
+          if (!ellipse_meets_rect(e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w, x0, x1, y0, y1))
             key = TILE_NONE;
         }
-        tkeys[k0 + kk] = key;
-        inst[k0 + kk] = s_i[q];
+        keys[h] = key;
+        ids[h] = s_i[q];
         atomicAdd(&s_h[key & 255u], 1u);
+      }
+      const long long k = k0 + a0 + e0i;  // even, so the pair stores are 8-byte aligned
+      if (a0 + e0i + 1 < a1) {
+        *reinterpret_cast<uint2*>(tkeys + k) = make_uint2(keys[0], keys[1]);
+        if (inst_pairs) {
+          *reinterpret_cast<int2*>(inst + k) = make_int2(ids[0], ids[1]);
+        } else {
+          inst[k] = ids[0];
+          inst[k + 1] = ids[1];
+        }
+      } else if (a0 + e0i < a1) {
+        tkeys[k] = keys[0];
+        inst[k] = ids[0];
       }
       __syncthreads();
     }
@@ -273,7 +321,7 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
         vvals, offs, chunk_first, &w.counters[0], (const long long*)bins->n_instances, cap,
         reinterpret_cast<const int4*>(pr->rect), xyod,
         reinterpret_cast<const float4*>(pr->conic), prm->alpha_min, n, cs, w.tkeys,
-        bins->inst_gauss, w.sort.hist, w.sort.tiles_max);
+        bins->inst_gauss, aligned(bins->inst_gauss, 8), w.sort.hist, w.sort.tiles_max);
     ADP_LAUNCH_CHECK();
     int bits = bits_for(n_tiles);  // the filtered key TILE_NONE sorts after every tile
     DigitOp tp[4];

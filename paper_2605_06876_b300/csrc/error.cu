@@ -568,6 +568,7 @@ __global__ void __launch_bounds__(256) ccl_local_kernel(const uint8_t* mask, con
   const int tx0 = (blockIdx.x % ntx) * CCL_T, ty0 = (blockIdx.x / ntx) * CCL_T;
   const long long base = cs.pix_base[v];
   const int lane = threadIdx.x & 31;
+  bool any = false;
   for (int li = threadIdx.x; li < CCL_T * CCL_T; li += blockDim.x) {
     int x = tx0 + (li & (CCL_T - 1)), y = ty0 + li / CCL_T;
     int lab = -1, d = -1;
@@ -580,9 +581,19 @@ __global__ void __launch_bounds__(256) ccl_local_kernel(const uint8_t* mask, con
         b = mask[p] >> 4;
       }
     }
+    any = any || lab >= 0;
     s_l[li] = lab;
     s_d[li] = d;
     s_b[li] = b;
+  }
+  if (!__syncthreads_or(any)) {  // no participating pixel: every label is -1
+    for (int li = threadIdx.x; li < CCL_T * CCL_T; li += blockDim.x) {
+      int x = tx0 + (li & (CCL_T - 1)), y = ty0 + li / CCL_T;
+      if (x < W && y < H) L[base + (long long)y * W + x] = -1;
+    }
+    return;
+  }
+  for (int li = threadIdx.x; li < CCL_T * CCL_T; li += blockDim.x) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) s_m[k][li] = 0u;
   }

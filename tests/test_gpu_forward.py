@@ -77,18 +77,20 @@ def _reaching(orp, ids, tx, ty, W, H):
     return out
 
 
-@pytest.mark.parametrize("views", [1, 3])
-def test_bin_sort_tile_lists_given_identical_keys(views):
+@pytest.mark.parametrize("views,n", [(1, 8000), (1, 20000), (3, 8000)])
+def test_bin_sort_tile_lists_given_identical_keys(views, n):
     """Fed the oracle's own float32 records, every GPU tile list is the oracle's
     per-tile (depth, id) list by rectangle with the Gaussians that cannot reach
     the tile removed: it keeps the order, it is a subsequence of the rectangle
     list, and it contains every Gaussian whose alpha reaches 1/255 at one of the
     tile's pixel centres (brute force). The instance count is the rectangle
-    count (capacity semantics)."""
-    sc, cams = small_cluster_inputs(8000, 240, 160, views=views, seed=3)
+    count (capacity semantics). The sizes cover the one-block depth sort (8,000
+    records) and the multi-launch radix passes with an even pass count (20,000)
+    and, with the extra view pass, an odd one (3 x 8,000)."""
+    sc, cams = small_cluster_inputs(n, 240, 160, views=views, seed=3)
     th = O.theta_of(sc)
     orps = [O.project(th, 3, c) for c in cams]
-    n = th.shape[0]
+    assert th.shape[0] == n
     pr = oracle_projected_to_gpu(orps, n)
     bins = ops.bin_sort(n, pr, cams)
     torch.cuda.synchronize()
