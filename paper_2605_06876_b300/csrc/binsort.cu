@@ -81,8 +81,8 @@ __device__ __forceinline__ int last_le_s(const int* off, int lo, int hi, int k) 
 __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
     const unsigned* vvals, const long long* offs, const int* chunk_first, const long long* d_nvis,
     const long long* d_K, long long cap, const int4* rect, const float4* xyod, const float4* conic,
-    float alpha_min, long long n, CamSet cs, unsigned* tkeys, int* inst, bool inst_pairs,
-    unsigned* hist, long long tiles_max) {
+    float alpha_min, long long n, CamSet cs, int view_shift, unsigned* tkeys, int* inst,
+    bool inst_pairs, unsigned* hist, long long tiles_max) {
   __shared__ int s_off[DUP_CHUNK + 1];      // record offsets of the chunk
   __shared__ int s_i[DUP_SUB + 1];          // Gaussian id
   __shared__ int s_org[DUP_SUB + 1];        // first tile column | first tile row << 16
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
         const int w = wv & 0xffff, v = (wv >> 16) & 0x7fff;
         const int tt = kk - s_off[sa + q];
         const int ty = (org >> 16) + tt / w, tx = (org & 0xffff) + tt % w;
-        unsigned key = (unsigned)(cs.tile_base[v] + ty * cs.tiles_x[v] + tx);
+        unsigned key = (unsigned)(ty * cs.tiles_x[v] + tx) | ((unsigned)v << view_shift);
         if (wv < 0) {  // a one-tile rectangle always meets its ellipse
           const float4 e0 = s_e0[q];
           const float4 e1 = s_e1[q];
@@ -194,15 +194,18 @@ __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
   }
 }
 
-__global__ void tile_ranges_kernel(const unsigned* tkeys, const long long* d_n, unsigned n_tiles,
-                                   int2* ranges) {
+// Per-tile ranges from the sorted keys (view-local tile | view << view_shift).
+__global__ void tile_ranges_kernel(const unsigned* tkeys, const long long* d_n, CamSet cs,
+                                   int view_shift, int2* ranges) {
   long long N = *d_n;
+  const unsigned local_mask = (1u << view_shift) - 1u;
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < N;
        j += (long long)gridDim.x * blockDim.x) {
     unsigned t = tkeys[j];
-    if (t >= n_tiles) continue;  // instances whose ellipse misses the tile
-    if (j == 0 || tkeys[j - 1] != t) ranges[t].x = (int)j;
-    if (j == N - 1 || tkeys[j + 1] != t) ranges[t].y = (int)(j + 1);
+    if (t == TILE_NONE) continue;  // instances whose ellipse misses the tile
+    const int g = cs.tile_base[t >> view_shift] + (int)(t & local_mask);
+    if (j == 0 || tkeys[j - 1] != t) ranges[g].x = (int)j;
+    if (j == N - 1 || tkeys[j + 1] != t) ranges[g].y = (int)(j + 1);
   }
 }
 
@@ -265,6 +268,13 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
   long long nv = (long long)n * n_views, cap = bins->capacity;
   size_t need = bin_ws_bytes(nv, cap);
   ADP_CHECK_ARG(ws_bytes >= need, "workspace %zu bytes, need %zu", ws_bytes, need);
+  // instance keys: view-local tile | view << view_shift (see step 4)
+  int max_local = 0;
+  for (int v = 0; v < n_views; ++v) max_local = std::max(max_local, cs.tiles_x[v] * cs.tiles_y[v]);
+  const int tile_bits = bits_for(max_local);
+  const int view_shift = 8 * ((tile_bits + 7) / 8);
+  ADP_CHECK_ARG(view_shift <= 24 && (long long)(n_views - 1) < (1LL << (32 - view_shift)) - 1,
+                "too many tiles per view for the tile key");
   cudaStream_t st = (cudaStream_t)stream;
   long long n_tiles = cs.tile_base[n_views];
   ADP_CUDA(cudaMemsetAsync(bins->tile_range, 0, sizeof(int2) * n_tiles, st));
@@ -314,26 +324,30 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
   if (rc) return rc;
   clamp_count_kernel<<<1, 1, 0, st>>>((const long long*)bins->n_instances, cap, &w.counters[1]);
 
-  // 4. duplicate into tiles, 5. stable sort by tile
+  // 4. duplicate into tiles, 5. stable sort by tile. The instance key is the
+  // view-local tile with the view above the sorted bits: the tile sort takes
+  // only the passes the largest view needs, every (view, tile) list is still one
+  // run in (depth, id) order (the records come view-major and every pass is
+  // stable), and the runs are ordered by local tile, then view. The filtered key
+  // TILE_NONE has all sorted bits set, so it sorts after every tile.
   if (cap > 0) {
     duplicate_kernel<<<(unsigned)std::min<long long>((cap + DUP_CHUNK - 1) / DUP_CHUNK, 148 * 8),
                        DUP_THREADS, 0, st>>>(
         vvals, offs, chunk_first, &w.counters[0], (const long long*)bins->n_instances, cap,
         reinterpret_cast<const int4*>(pr->rect), xyod,
-        reinterpret_cast<const float4*>(pr->conic), prm->alpha_min, n, cs, w.tkeys,
+        reinterpret_cast<const float4*>(pr->conic), prm->alpha_min, n, cs, view_shift, w.tkeys,
         bins->inst_gauss, aligned(bins->inst_gauss, 8), w.sort.hist, w.sort.tiles_max);
     ADP_LAUNCH_CHECK();
-    int bits = bits_for(n_tiles);  // the filtered key TILE_NONE sorts after every tile
     DigitOp tp[4];
     int ntp = 0;
-    for (int s = 0; s < bits; s += 8) tp[ntp++] = DigitOp{s, 0u};
+    for (int s = 0; s < tile_bits; s += 8) tp[ntp++] = DigitOp{s, 0u};
     // the first pass's tile histograms come from the duplication
     rc = radix_sort_pairs(w.tkeys, reinterpret_cast<unsigned*>(bins->inst_gauss),
                           &w.counters[1], cap, tp, ntp, w.sort, st, /*first_hist_done=*/true);
     if (rc) return rc;
     // 6. per-tile ranges
     tile_ranges_kernel<<<grid_for(cap, 256, 148 * 16), 256, 0, st>>>(
-        w.tkeys, &w.counters[1], (unsigned)n_tiles, reinterpret_cast<int2*>(bins->tile_range));
+        w.tkeys, &w.counters[1], cs, view_shift, reinterpret_cast<int2*>(bins->tile_range));
     ADP_LAUNCH_CHECK();
   }
   return ADP_OK;
