@@ -99,6 +99,15 @@ _PROTOS = {
                                        P(AdpParams), _i32, _vp, P(C.c_float), C.c_float,
                                        C.c_float, C.c_float, P(AdpGaussians), P(AdpGaussians),
                                        P(AdpGaussians), _vp, C.c_size_t, _vp]),
+    "adp_split_plan_overlapped": (C.c_int, [P(AdpGaussians), P(AdpCamera), _i32, P(AdpRegions),
+                                            _vp, _i64, _vp, P(AdpParams), _vp, _vp, _vp, _vp,
+                                            C.c_size_t, _vp]),
+    "adp_split_apply_adam_overlapped": (C.c_int, [P(AdpGaussians), P(AdpGaussians),
+                                                  P(AdpGaussians), P(AdpGaussians), P(AdpRegions),
+                                                  _vp, _i64, _vp, _vp, _vp, P(AdpParams), _i32,
+                                                  _vp, P(C.c_float), C.c_float, C.c_float,
+                                                  C.c_float, P(AdpGaussians), P(AdpGaussians),
+                                                  P(AdpGaussians), _vp, C.c_size_t, _vp]),
     "adp_render_backward_workspace_size": (C.c_size_t, [_i64, _i32]),
     "adp_render_backward": (C.c_int, [P(AdpGaussians), P(AdpProjected), P(AdpBins), P(AdpImage),
                                       _vp, _vp, P(AdpCamera), _i32, P(C.c_float), P(AdpParams),

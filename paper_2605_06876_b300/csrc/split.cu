@@ -12,6 +12,8 @@
 // of its appended block. This stage is small next to rendering, so it runs in
 // FP64, which keeps every integer outcome (statuses, child counts) stable.
 // Apply: gathers kept Gaussians (with Adam moments) and writes appended ones.
+#include <mutex>
+
 #include "adam.cuh"
 #include "gauss_math.cuh"
 
@@ -39,9 +41,12 @@ struct SplitWs {
                        // candidate, all ones for a removed one
   long long* app_off;  // [n_cand]
   long long* counters; // [0] regions in use, [1] kept, [2] appended, [3] new n,
-                       // [4] candidates with two or more proposals
-  int* multi;          // [n_cand] those candidates, in no particular order
-  void* scan;
+                       // [4] ADAPTIVE candidates, [5] bound on the new n known
+                       // before the merge (n + sum of min(proposals, n_max) over
+                       // ADAPTIVE candidates + the FALLBACK count)
+  int* multi;          // [n_cand] the ADAPTIVE candidates, in no particular order
+  void* scan;          // the kept-row scan
+  void* scan2;         // the appended-block scan (may run beside the kept-row one)
   SortWorkspace sort;
 };
 
@@ -51,7 +56,7 @@ static size_t split_ws_bytes(long long n, long long nc, long long rc) {
          carve_bytes<Prop>(rc) + 2 * carve_bytes<int>(rc) + carve_bytes<double>(rc) +
          carve_bytes<float4>(4 * rc) + carve_bytes<unsigned>(n) + carve_bytes<long long>(nc) +
          carve_bytes<long long>(8) + carve_bytes<int>(nc) + scan_workspace_bytes(sm) +
-         sort_workspace_bytes(rc);
+         scan_workspace_bytes(nc) + sort_workspace_bytes(rc);
 }
 
 static SplitWs carve_split(Carver& c, long long n, long long nc, long long rc) {
@@ -71,6 +76,7 @@ static SplitWs carve_split(Carver& c, long long n, long long nc, long long rc) {
   w.counters = c.take<long long>(8);
   w.multi = c.take<int>(nc);
   w.scan = c.take<char>(scan_workspace_bytes(sm));
+  w.scan2 = c.take<char>(scan_workspace_bytes(nc));
   w.sort = carve_sort(c, rc);
   return w;
 }
@@ -351,6 +357,8 @@ struct MergeArgs {
   int* n_children;
   int* multi;                    // candidates left to merge_warp_kernel
   unsigned long long* n_multi;   // their count
+  unsigned long long* bound;     // += the largest growth the statuses allow
+  long long n_rows;              // rows of the input population
 };
 
 // Eq. 11 between two proposals.
@@ -425,10 +433,13 @@ __device__ void merged_group(const MergeArgs& a, int s0, int M, int g, double* m
   for (int r = 0; r < 3; ++r) s[r] = fmax(sqrt(lam[r]), a.scale_floor);
 }
 
-// One thread per candidate: statuses, and the whole answer for candidates with
-// at most one proposal (the common case); candidates with more are left to
-// merge_warp_kernel.
+// One thread per candidate: statuses (which need no proposal), the list of
+// ADAPTIVE candidates for merge_warp_kernel, and a bound on the new population
+// size that holds whatever the merges decide: every ADAPTIVE candidate adds at
+// most min(proposals, n_max) rows net (children plus its parent copy, minus
+// itself) and every FALLBACK one adds one.
 __global__ void merge_status_kernel(MergeArgs a) {
+  unsigned long long extra = 0ull;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.nc;
        c += (long long)gridDim.x * blockDim.x) {
     const int i = a.cand[c];
@@ -440,18 +451,20 @@ __global__ void merge_status_kernel(MergeArgs a) {
     } else if (a.count[i] == 0) {
       a.status[c] = ADP_FALLBACK;
       a.n_children[c] = 0;
+      extra += 1ull;
     } else if (M <= 0) {
       a.status[c] = ADP_RESET;
       a.n_children[c] = 0;
     } else {
       a.status[c] = ADP_ADAPTIVE;
-      if (M >= 2) a.multi[atomicAdd(a.n_multi, 1ull)] = (int)c;  // merged by a warp
-      if (M == 1) {
-        const Prop& p = a.props[sg.x];
-        if (a.n_max >= 1) store_child(a.kids + 4LL * sg.x, p.mu, p.R, p.s, p.rgb);
-        a.n_children[c] = a.n_max >= 1 ? 1 : 0;
-      }
+      a.multi[atomicAdd(a.n_multi, 1ull)] = (int)c;  // merged by a warp
+      extra += (unsigned long long)min(M, a.n_max);
     }
+  }
+  for (int o = 16; o > 0; o >>= 1) extra += __shfl_xor_sync(0xffffffffu, extra, o);
+  if ((threadIdx.x & 31) == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) extra += (unsigned long long)a.n_rows;
+    if (extra) atomicAdd(a.bound, extra);
   }
 }
 
@@ -464,8 +477,9 @@ __device__ __forceinline__ int uf_root_v(volatile int* uf, int x) {
   return x;
 }
 
-// One warp per candidate with two or more proposals (the list merge_status_kernel
-// builds; each candidate writes only its own segment, so the order is free): the pairwise tests of
+// One warp per ADAPTIVE candidate (the list merge_status_kernel builds; each
+// candidate writes only its own segment, so the order is free; a single proposal
+// is a one-member group, Eq. 12 then returns it unchanged): the pairwise tests of
 // Eq. 11 are spread over the lanes and joined in a union-find whose links point
 // to smaller indices (so every group is rooted at its first member); groups are
 // numbered in first-member order, merged one per lane (Eq. 12), capped at n_max
@@ -560,7 +574,10 @@ __global__ void merge_warp_kernel(MergeArgs a) {
   }
 }
 
-__global__ void new_n_kernel(long long* counters) { counters[3] = counters[1] + counters[2]; }
+__global__ void new_n_kernel(long long* counters, int64_t* d_new_n) {
+  counters[3] = counters[1] + counters[2];
+  *d_new_n = counters[3];
+}
 
 // ------------------------------------------------------------------ apply kernels
 
@@ -588,6 +605,7 @@ struct ApplyArgs {
   const uint8_t* grad_rows;  // optional row mask of grad: 0 = zero gradient, not read
   AdamHyper adam;
   const long long* counters;  // [1] kept, [3] new size
+  const long long* fit;       // the size compared with the capacity: [3], or the bound [5]
   bool has_m_in, has_v_in, has_m_out, has_v_out;
   int planes;
   const unsigned* dest;  // see SplitWs::dest
@@ -620,14 +638,12 @@ __device__ __forceinline__ float4* plane_of(const GaussPtrs& g, int q, long long
 // non-candidate row gets the update adp_adam_step makes, bit for bit (candidates
 // got theirs before the plan); moments in and out are then required.
 template <bool ADAM>
-__global__ void apply_keep_kernel(ApplyArgs a) {
-  const int q = blockIdx.y;
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void keep_row(const ApplyArgs& a, int q, long long i) {
   if (i >= a.in.n) return;
   // every independent load first (the destination and the streams), then the
   // gradient, whose load waits only for the row mask; removed rows are read in vain
   const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-  const long long n_new = a.counters[3];
+  const long long n_new = *a.fit;
   const unsigned d = a.dest[i];
   const bool gl = ADAM && (!a.grad_rows || a.grad_rows[i]);
   float4 p = *plane_of(a.in, q, i);
@@ -648,6 +664,11 @@ __global__ void apply_keep_kernel(ApplyArgs a) {
   if (a.has_v_out) *plane_of(a.vout, q, j) = v;
 }
 
+template <bool ADAM>
+__global__ void apply_keep_kernel(ApplyArgs a) {
+  keep_row<ADAM>(a, blockIdx.y, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
+
 struct AppendArgs {
   GaussPtrs in, out, mout, vout;
   bool has_m_out, has_v_out;
@@ -662,6 +683,8 @@ struct AppendArgs {
   const long long* counters;
   const float* noise;
   float shrink;  // ln(2 eta), rounded to float32
+  bool late_keep;    // the kept rows were skipped against the bound: see below
+  ApplyArgs keep;    // (with the Adam step) for that case
 };
 
 // Appended rows: one thread per new row, in chunks of APP_THREADS rows per
@@ -698,6 +721,17 @@ __global__ void __launch_bounds__(APP_THREADS) apply_append_kernel(AppendArgs a)
   __shared__ long long s_off[APP_STAGE];
   __shared__ long long s_c[2];
   if (a.counters[3] > a.out.n) return;  // the new population does not fit: write nothing
+  if (a.late_keep && a.counters[5] > a.out.n) {
+    // the overlapped compaction skipped the kept rows because the bound on the
+    // new size exceeded the capacity, but the exact size fits: copy them here
+    // (a slow grid-stride pass; a caller sizing out for the bound never takes it)
+    const long long nr = a.keep.in.n, tot = nr * (3 + a.planes);
+    ApplyArgs ka = a.keep;
+    ka.fit = a.counters + 3;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < tot;
+         u += (long long)gridDim.x * blockDim.x)
+      keep_row<true>(ka, (int)(u / nr), u % nr);
+  }
   const long long n_keep = a.counters[1], n_app = a.counters[2];
   for (long long r0 = blockIdx.x * (long long)APP_THREADS; r0 < n_app;
        r0 += (long long)gridDim.x * APP_THREADS) {
@@ -774,13 +808,27 @@ extern "C" ADP_API size_t adp_split_workspace_size(int64_t n, int64_t n_cand,
   return split_ws_bytes(n, n_cand, region_capacity);
 }
 
-extern "C" ADP_API int adp_split_plan(const adp_gaussians* g, const adp_camera* cams,
-                                      int32_t n_views, const adp_regions* regs,
-                                      const int32_t* candidates, int64_t n_cand,
-                                      const int32_t* count, const adp_params* prm,
-                                      uint8_t* status, int32_t* n_children, int64_t* d_new_n,
-                                      int64_t* h_new_n, void* ws, size_t ws_bytes,
-                                      adp_stream_t stream) {
+namespace adp {
+
+// The validated arguments of a plan.
+struct PlanCall {
+  const adp_gaussians* g;
+  const adp_regions* regs;
+  const int32_t* candidates;
+  const int32_t* count;
+  const adp_params* prm;
+  uint8_t* status;
+  int32_t* n_children;
+  int64_t* d_new_n;
+  long long n, nc, rcap;
+  CamSet cs;
+};
+
+static int plan_args(const adp_gaussians* g, const adp_camera* cams, int32_t n_views,
+                     const adp_regions* regs, const int32_t* candidates, int64_t n_cand,
+                     const int32_t* count, const adp_params* prm, uint8_t* status,
+                     int32_t* n_children, int64_t* d_new_n, void* ws, size_t ws_bytes,
+                     PlanCall* pc) {
   ADP_CHECK_ARG(gauss_ok(g) || (g && g->n == 0), "bad Gaussian arrays");
   ADP_CHECK_ARG(regs && regs->count && count && d_new_n, "NULL argument");
   ADP_CHECK_ARG(g->n >= 0 && g->n < (1LL << 31), "n out of range");
@@ -789,81 +837,82 @@ extern "C" ADP_API int adp_split_plan(const adp_gaussians* g, const adp_camera* 
   ADP_CHECK_ARG(regs->capacity >= 0 && regs->capacity < (1LL << 31), "region capacity out of range");
   ADP_CHECK_ARG(regs->capacity == 0 || (regs->view && regs->parent && regs->stats),
                 "NULL region arrays");
-  CamSet cs;
-  int rc = make_camset(cams, n_views, prm, &cs);
+  int rc = make_camset(cams, n_views, prm, &pc->cs);
   if (rc) return rc;
   ADP_CHECK_ARG(prm->n_max >= 0, "n_max must be >= 0");
   ADP_CHECK_ARG(aligned(ws, 256), "workspace must be 256-byte aligned");
-  long long n = g->n, nc = n_cand, rcap = regs->capacity;
-  size_t need = split_ws_bytes(n, nc, rcap);
+  pc->n = g->n;
+  pc->nc = n_cand;
+  pc->rcap = regs->capacity;
+  size_t need = split_ws_bytes(pc->n, pc->nc, pc->rcap);
   ADP_CHECK_ARG(ws_bytes >= need, "workspace %zu bytes, need %zu", ws_bytes, need);
-  cudaStream_t st = (cudaStream_t)stream;
-  Carver c(ws, ws_bytes);
-  SplitWs w = carve_split(c, n, nc, rcap);
+  pc->g = g;
+  pc->regs = regs;
+  pc->candidates = candidates;
+  pc->count = count;
+  pc->prm = prm;
+  pc->status = status;
+  pc->n_children = n_children;
+  pc->d_new_n = d_new_n;
+  return ADP_OK;
+}
+
+static MergeArgs merge_args(const PlanCall& pc, const SplitWs& w) {
+  MergeArgs ma;
+  ma.cand = pc.candidates;
+  ma.count = pc.count;
+  ma.seg = w.seg;
+  ma.props = w.props;
+  ma.uf = w.uf;
+  ma.groups = w.groups;
+  ma.ext = w.ext;
+  ma.kids = w.kids;
+  ma.nc = pc.nc;
+  ma.gamma_d = pc.prm->gamma_d;
+  ma.gamma_c = pc.prm->gamma_c;
+  ma.scale_floor = pc.prm->scale_floor;
+  ma.n_max = pc.prm->n_max;
+  ma.status = pc.status;
+  ma.n_children = pc.n_children;
+  ma.multi = w.multi;
+  ma.n_multi = reinterpret_cast<unsigned long long*>(&w.counters[4]);
+  ma.bound = reinterpret_cast<unsigned long long*>(&w.counters[5]);
+  ma.n_rows = pc.n;
+  return ma;
+}
+
+// Plan, first part (needs no proposal): regions grouped per candidate, the
+// statuses, the bound on the new size and the new row of every kept Gaussian.
+static int plan_phase_a(const PlanCall& pc, const SplitWs& w, cudaStream_t st) {
+  const long long n = pc.n, nc = pc.nc, rcap = pc.rcap;
+  int rc;
   ADP_CUDA(cudaMemsetAsync(w.counters, 0, 8 * sizeof(long long), st));
   if (n > 0) ADP_CUDA(cudaMemsetAsync(w.cand_of, 0xff, sizeof(int) * n, st));
   if (nc > 0) {
     ADP_CUDA(cudaMemsetAsync(w.seg, 0, sizeof(int2) * nc, st));
-    cand_of_kernel<<<grid_for(nc, 256, 4096), 256, 0, st>>>(candidates, nc, n, w.cand_of);
+    cand_of_kernel<<<grid_for(nc, 256, 4096), 256, 0, st>>>(pc.candidates, nc, n, w.cand_of);
   }
   if (rcap > 0) {
     region_keys_kernel<<<grid_for(rcap, 256, 4096), 256, 0, st>>>(
-        regs->parent, (const long long*)regs->count, rcap, w.cand_of, n, (unsigned)nc, w.rkeys,
-        w.rvals, &w.counters[0]);
+        pc.regs->parent, (const long long*)pc.regs->count, rcap, w.cand_of, n, (unsigned)nc,
+        w.rkeys, w.rvals, &w.counters[0]);
     int bits = bits_for(nc);
     DigitOp passes[4];
     int np = 0;
-    for (int s = 0; s < bits; s += 8) passes[np++] = DigitOp{s, 0u};
+    for (int sft = 0; sft < bits; sft += 8) passes[np++] = DigitOp{sft, 0u};
     rc = radix_sort_pairs(w.rkeys, w.rvals, &w.counters[0], rcap, passes, np, w.sort, st);
     if (rc) return rc;
     seg_kernel<<<grid_for(rcap, 256, 4096), 256, 0, st>>>(w.rkeys, &w.counters[0], (unsigned)nc,
                                                           w.seg);
-    ProposalArgs pa;
-    pa.mean_logit = reinterpret_cast<const float4*>(g->mean_logit);
-    pa.logscale = reinterpret_cast<const float4*>(g->logscale);
-    pa.quat = reinterpret_cast<const float4*>(g->quat);
-    pa.r_view = regs->view;
-    pa.r_parent = regs->parent;
-    pa.r_stats = regs->stats;
-    pa.keys = w.rkeys;
-    pa.vals = w.rvals;
-    pa.d_n = &w.counters[0];
-    pa.nc = (unsigned)nc;
-    pa.eps_t = prm->eps_t;
-    pa.scale_floor = prm->scale_floor;
-    pa.props = w.props;
-    proposal_kernel<<<grid_for(rcap, 128, 4096), 128, 0, st>>>(pa, cs);
-    ADP_LAUNCH_CHECK();
   }
-  if (nc > 0) {
-    MergeArgs ma;
-    ma.cand = candidates;
-    ma.count = count;
-    ma.seg = w.seg;
-    ma.props = w.props;
-    ma.uf = w.uf;
-    ma.groups = w.groups;
-    ma.ext = w.ext;
-    ma.kids = w.kids;
-    ma.nc = nc;
-    ma.gamma_d = prm->gamma_d;
-    ma.gamma_c = prm->gamma_c;
-    ma.scale_floor = prm->scale_floor;
-    ma.n_max = prm->n_max;
-    ma.status = status;
-    ma.n_children = n_children;
-    ma.multi = w.multi;
-    ma.n_multi = reinterpret_cast<unsigned long long*>(&w.counters[4]);
-    merge_status_kernel<<<grid_for(nc, 256, 4096), 256, 0, st>>>(ma);
-    // a resident grid (four 128-thread blocks per SM fit its registers) that loops
-    // over the device-side list
-    merge_warp_kernel<<<grid_for(nc * 32, 128, 148 * 4), 128, 0, st>>>(ma);
-    ADP_LAUNCH_CHECK();
-  }
-  // new indices of kept Gaussians and offsets of appended blocks
+  // statuses, the ADAPTIVE list and the bound (launched even without candidates:
+  // the bound then is n)
+  merge_status_kernel<<<grid_for(nc, 256, 4096), 256, 0, st>>>(merge_args(pc, w));
+  ADP_LAUNCH_CHECK();
+  // new indices of kept Gaussians
   const int* cand_of = w.cand_of;
   unsigned* dest = w.dest;
-  const uint8_t* cstatus = status;
+  const uint8_t* cstatus = pc.status;
   rc = scan_exclusive(
       [=] __device__(long long i) -> long long {
         int cc = cand_of[i];
@@ -874,11 +923,43 @@ extern "C" ADP_API int adp_split_plan(const adp_gaussians* g, const adp_camera* 
         const bool kept = cc < 0 || cstatus[cc] == ADP_RESET;
         dest[i] = kept ? ((unsigned)pre | (cc >= 0 ? 0x80000000u : 0u)) : 0xffffffffu;
       },
-      n, nullptr,
-      &w.counters[1], w.scan, st);
-  if (rc) return rc;
+      n, nullptr, &w.counters[1], w.scan, st);
+  return rc;
+}
+
+// Plan, second part: one proposal per region (Eqs. 9-10, Appendix A), the merge
+// and cap per ADAPTIVE candidate (Eqs. 11-12), the offsets of the appended
+// blocks and the new size.
+static int plan_phase_b(const PlanCall& pc, const SplitWs& w, cudaStream_t st) {
+  const long long nc = pc.nc, rcap = pc.rcap;
+  int rc;
+  if (rcap > 0) {
+    ProposalArgs pa;
+    pa.mean_logit = reinterpret_cast<const float4*>(pc.g->mean_logit);
+    pa.logscale = reinterpret_cast<const float4*>(pc.g->logscale);
+    pa.quat = reinterpret_cast<const float4*>(pc.g->quat);
+    pa.r_view = pc.regs->view;
+    pa.r_parent = pc.regs->parent;
+    pa.r_stats = pc.regs->stats;
+    pa.keys = w.rkeys;
+    pa.vals = w.rvals;
+    pa.d_n = &w.counters[0];
+    pa.nc = (unsigned)nc;
+    pa.eps_t = pc.prm->eps_t;
+    pa.scale_floor = pc.prm->scale_floor;
+    pa.props = w.props;
+    proposal_kernel<<<grid_for(rcap, 128, 4096), 128, 0, st>>>(pa, pc.cs);
+    ADP_LAUNCH_CHECK();
+  }
   if (nc > 0) {
-    const int* nch = n_children;
+    // a resident grid (four 128-thread blocks per SM fit its registers) that loops
+    // over the device-side list; an ADAPTIVE candidate has a region, so there are
+    // at most min(nc, rcap) of them
+    merge_warp_kernel<<<grid_for(std::min(nc, std::max(rcap, 1LL)) * 32, 128, 148 * 4), 128, 0,
+                        st>>>(merge_args(pc, w));
+    ADP_LAUNCH_CHECK();
+    const uint8_t* cstatus = pc.status;
+    const int* nch = pc.n_children;
     long long* app_off = w.app_off;
     rc = scan_exclusive(
         [=] __device__(long long cc) -> long long {
@@ -886,16 +967,98 @@ extern "C" ADP_API int adp_split_plan(const adp_gaussians* g, const adp_camera* 
           return s == ADP_ADAPTIVE ? 1 + nch[cc] : (s == ADP_FALLBACK ? 2 : 0);
         },
         [=] __device__(long long cc, long long pre) { app_off[cc] = pre; }, nc, nullptr,
-        &w.counters[2], w.scan, st);
+        &w.counters[2], w.scan2, st);
     if (rc) return rc;
   }
-  new_n_kernel<<<1, 1, 0, st>>>(w.counters);
-  ADP_CUDA(cudaMemcpyAsync(d_new_n, &w.counters[3], sizeof(long long), cudaMemcpyDeviceToDevice, st));
+  new_n_kernel<<<1, 1, 0, st>>>(w.counters, pc.d_new_n);
   ADP_LAUNCH_CHECK();
+  return ADP_OK;
+}
+
+// The library's auxiliary stream of the current device (highest priority), and
+// the two events of an overlapped plan: `planned` (phase A done, on the caller's
+// stream) and `merged` (phase B done, on the auxiliary stream). Created on first
+// use.
+struct AuxStream {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t planned = nullptr, merged = nullptr;
+};
+constexpr int AUX_MAX_DEVICES = 64;
+static AuxStream g_aux[AUX_MAX_DEVICES];
+static std::mutex g_aux_mu;
+
+static int aux_stream(AuxStream** out) {
+  int dev = 0;
+  ADP_CUDA(cudaGetDevice(&dev));
+  ADP_CHECK_ARG(dev >= 0 && dev < AUX_MAX_DEVICES, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_aux_mu);
+  AuxStream& a = g_aux[dev];
+  if (!a.stream) {
+    int lo = 0, hi = 0;
+    ADP_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    ADP_CUDA(cudaEventCreateWithFlags(&a.planned, cudaEventDisableTiming));
+    ADP_CUDA(cudaEventCreateWithFlags(&a.merged, cudaEventDisableTiming));
+    ADP_CUDA(cudaStreamCreateWithPriority(&a.stream, cudaStreamNonBlocking, hi));
+  }
+  *out = &a;
+  return ADP_OK;
+}
+
+}  // namespace adp
+
+extern "C" ADP_API int adp_split_plan(const adp_gaussians* g, const adp_camera* cams,
+                                      int32_t n_views, const adp_regions* regs,
+                                      const int32_t* candidates, int64_t n_cand,
+                                      const int32_t* count, const adp_params* prm,
+                                      uint8_t* status, int32_t* n_children, int64_t* d_new_n,
+                                      int64_t* h_new_n, void* ws, size_t ws_bytes,
+                                      adp_stream_t stream) {
+  PlanCall pc;
+  int rc = plan_args(g, cams, n_views, regs, candidates, n_cand, count, prm, status, n_children,
+                     d_new_n, ws, ws_bytes, &pc);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  Carver c(ws, ws_bytes);
+  SplitWs w = carve_split(c, pc.n, pc.nc, pc.rcap);
+  rc = plan_phase_a(pc, w, st);
+  if (rc) return rc;
+  rc = plan_phase_b(pc, w, st);
+  if (rc) return rc;
   if (h_new_n) {
     ADP_CUDA(cudaMemcpyAsync(h_new_n, &w.counters[3], sizeof(long long), cudaMemcpyDeviceToHost, st));
     ADP_CUDA(cudaStreamSynchronize(st));
   }
+  return ADP_OK;
+}
+
+extern "C" ADP_API int adp_split_plan_overlapped(const adp_gaussians* g, const adp_camera* cams,
+                                                 int32_t n_views, const adp_regions* regs,
+                                                 const int32_t* candidates, int64_t n_cand,
+                                                 const int32_t* count, const adp_params* prm,
+                                                 uint8_t* status, int32_t* n_children,
+                                                 int64_t* d_new_n, void* ws, size_t ws_bytes,
+                                                 adp_stream_t stream) {
+  PlanCall pc;
+  int rc = plan_args(g, cams, n_views, regs, candidates, n_cand, count, prm, status, n_children,
+                     d_new_n, ws, ws_bytes, &pc);
+  if (rc) return rc;
+  AuxStream* aux = nullptr;
+  rc = aux_stream(&aux);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  Carver c(ws, ws_bytes);
+  SplitWs w = carve_split(c, pc.n, pc.nc, pc.rcap);
+  rc = plan_phase_a(pc, w, st);
+  if (rc) return rc;
+  {  // fork: phase B on the auxiliary stream once phase A is done
+    std::lock_guard<std::mutex> lock(g_aux_mu);
+    ADP_CUDA(cudaEventRecord(aux->planned, st));
+    ADP_CUDA(cudaStreamWaitEvent(aux->stream, aux->planned, 0));
+  }
+  rc = plan_phase_b(pc, w, aux->stream);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lock(g_aux_mu);
+  ADP_CUDA(cudaEventRecord(aux->merged, aux->stream));
   return ADP_OK;
 }
 
@@ -905,7 +1068,7 @@ static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
                             const int32_t* candidates, int64_t n_cand, const uint8_t* status,
                             const int32_t* n_children, const float* noise, const adp_params* prm,
                             adp_gaussians* out, adp_gaussians* m_out, adp_gaussians* v_out,
-                            void* ws, size_t ws_bytes, cudaStream_t st) {
+                            void* ws, size_t ws_bytes, cudaStream_t st, bool overlapped = false) {
   ADP_CHECK_ARG(g && out && regs && prm, "NULL argument");
   ADP_CHECK_ARG(gauss_ok(g) || g->n == 0, "bad input Gaussian arrays");
   ADP_CHECK_ARG(gauss_ok(out) || out->n == 0, "bad output Gaussian arrays");
@@ -922,6 +1085,7 @@ static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
                       grad->sh_degree == g->sh_degree, "bad grad");
   }
   ADP_CHECK_ARG(aligned(ws, 256), "workspace must be 256-byte aligned");
+  ADP_CHECK_ARG(!overlapped || adam, "internal: the overlapped compaction has the Adam step");
   long long n = g->n, nc = n_cand, rcap = regs->capacity;
   size_t need = split_ws_bytes(n, nc, rcap);
   ADP_CHECK_ARG(ws_bytes >= need, "workspace %zu bytes, need %zu", ws_bytes, need);
@@ -949,6 +1113,14 @@ static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
   aa.planes = planes;
   aa.dest = w.dest;
   aa.counters = w.counters;
+  // after an overlapped plan the merge may still run: the kept rows are written
+  // against the bound on the new size, the appended ones after the join
+  aa.fit = overlapped ? &w.counters[5] : &w.counters[3];
+  AuxStream* aux = nullptr;
+  if (overlapped) {
+    int rc = aux_stream(&aux);
+    if (rc) return rc;
+  }
   if (n > 0) {
     const dim3 kg(grid_for(n, 256), 3 + planes);
     if (adam)
@@ -956,8 +1128,14 @@ static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
     else
       apply_keep_kernel<false><<<kg, 256, 0, st>>>(aa);
   }
+  if (overlapped) {  // join the plan's second part
+    std::lock_guard<std::mutex> lock(g_aux_mu);
+    ADP_CUDA(cudaStreamWaitEvent(st, aux->merged, 0));
+  }
   if (nc > 0) {
     AppendArgs ap;
+    ap.late_keep = overlapped && adam;
+    ap.keep = aa;
     ap.in = gin;
     ap.out = gout;
     ap.has_m_out = m_out != nullptr;
@@ -1010,6 +1188,27 @@ extern "C" ADP_API int adp_split_apply_adam(
   cudaStream_t st = (cudaStream_t)stream;
   int rc = split_apply_impl(g, grad, &h, m_in, v_in, regs, candidates, n_cand, status, n_children,
                             noise, prm, out, m_out, v_out, ws, ws_bytes, st);
+  if (rc) return rc;
+  if (d_step) {
+    split_step_advance_kernel<<<1, 1, 0, st>>>(d_step);
+    ADP_LAUNCH_CHECK();
+  }
+  return ADP_OK;
+}
+
+extern "C" ADP_API int adp_split_apply_adam_overlapped(
+    const adp_gaussians* g, const adp_gaussians* grad, const adp_gaussians* m_in,
+    const adp_gaussians* v_in, const adp_regions* regs, const int32_t* candidates, int64_t n_cand,
+    const uint8_t* status, const int32_t* n_children, const float* noise, const adp_params* prm,
+    int32_t step, int32_t* d_step, const float* lr, float beta1, float beta2, float eps,
+    adp_gaussians* out, adp_gaussians* m_out, adp_gaussians* v_out, void* ws, size_t ws_bytes,
+    adp_stream_t stream) {
+  ADP_CHECK_ARG(lr, "NULL lr");
+  ADP_CHECK_ARG(d_step || step >= 1, "step must be >= 1");
+  AdamHyper h = adam_hyper(lr, beta1, beta2, eps, step, d_step);
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = split_apply_impl(g, grad, &h, m_in, v_in, regs, candidates, n_cand, status, n_children,
+                            noise, prm, out, m_out, v_out, ws, ws_bytes, st, /*overlapped=*/true);
   if (rc) return rc;
   if (d_step) {
     split_step_advance_kernel<<<1, 1, 0, st>>>(d_step);

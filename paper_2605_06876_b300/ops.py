@@ -394,6 +394,30 @@ def split_plan(g: Gaussians, cams, regions: Regions, candidates, count, params=N
     return SplitPlan(status[:nc], nch[:nc], int(h_new_n.value) if sync else None, ws, d_new_n)
 
 
+def split_plan_overlapped(g: Gaussians, cams, regions: Regions, candidates, count, params=None,
+                          ws=None, stream=None):
+    """adp_split_plan_overlapped: the statuses and kept rows on the stream, the
+    proposals and merges on the library's auxiliary stream; must be followed by
+    split_apply_adam(..., overlapped=True), which joins them."""
+    params = params or A.default_params()
+    ca = A.cameras(cams)
+    dev = g.mean_logit.device
+    nc = int(candidates.numel())
+    need = split_workspace_size(g.n, nc, regions.capacity)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    status = torch.empty(max(nc, 1), dtype=U8, device=dev)
+    nch = torch.empty(max(nc, 1), dtype=I32, device=dev)
+    d_new_n = torch.empty(1, dtype=I64, device=dev)
+    gc, rc = g.c(), regions.c()
+    A.check(A.lib().adp_split_plan_overlapped(C.byref(gc), ca, len(cams), C.byref(rc),
+                                              _p(candidates), nc, _p(count), C.byref(params),
+                                              _p(status), _p(nch), _p(d_new_n), _p(ws),
+                                              ws.numel(), _stream(stream)),
+            "adp_split_plan_overlapped")
+    return SplitPlan(status[:nc], nch[:nc], None, ws, d_new_n)
+
+
 def split_apply(g: Gaussians, plan: SplitPlan, regions: Regions, candidates, noise, params=None,
                 m_in: Gaussians = None, v_in: Gaussians = None, with_state=True, stream=None,
                 out: Gaussians = None, m_out: Gaussians = None, v_out: Gaussians = None):
@@ -426,9 +450,11 @@ def split_apply(g: Gaussians, plan: SplitPlan, regions: Regions, candidates, noi
 def split_apply_adam(g: Gaussians, grad: Gaussians, m_in: Gaussians, v_in: Gaussians,
                      plan: SplitPlan, regions: Regions, candidates, noise, step, out: Gaussians,
                      m_out: Gaussians, v_out: Gaussians, params=None, lr=None, beta1=0.9,
-                     beta2=0.999, eps=1e-15, stream=None):
+                     beta2=0.999, eps=1e-15, stream=None, overlapped=False):
     """adp_split_apply_adam: the compaction with the Adam step applied to every kept
-    non-candidate row on the way (candidates first via adam_step_rows)."""
+    non-candidate row on the way (candidates first via adam_step_rows). With
+    overlapped=True (adp_split_apply_adam_overlapped) it follows
+    split_plan_overlapped: the kept rows are written while the merge finishes."""
     params = params or A.default_params()
     lrc = (C.c_float * 6)(*[float(x) for x in (lr or ADAM_LR)])
     host_step, d_step = _step_arg(step)
@@ -437,11 +463,12 @@ def split_apply_adam(g: Gaussians, grad: Gaussians, m_in: Gaussians, v_in: Gauss
         noise = torch.zeros((max(nc, 1), 2, 3), dtype=F32, device=g.mean_logit.device)
     gc, grc, mic, vic = g.c(), grad.c(), m_in.c(), v_in.c()
     oc, moc, voc, rc = out.c(), m_out.c(), v_out.c(), regions.c()
-    A.check(A.lib().adp_split_apply_adam(
+    fn = "adp_split_apply_adam_overlapped" if overlapped else "adp_split_apply_adam"
+    A.check(getattr(A.lib(), fn)(
         C.byref(gc), C.byref(grc), C.byref(mic), C.byref(vic), C.byref(rc), _p(candidates), nc,
         _p(plan.status), _p(plan.n_children), _p(noise), C.byref(params), host_step, d_step, lrc,
         beta1, beta2, eps, C.byref(oc), C.byref(moc), C.byref(voc), _p(plan.ws), plan.ws.numel(),
-        _stream(stream)), "adp_split_apply_adam")
+        _stream(stream)), fn)
     return out, m_out, v_out
 
 

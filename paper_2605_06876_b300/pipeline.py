@@ -71,12 +71,16 @@ class StageTimer:
 class PlainStep:
     def __init__(self, g: ops.Gaussians, cams, target, cand_frac=0.1, params=None,
                  bg=(0.0, 0.0, 0.0), lr=ops.ADAM_LR, bins_margin=1.15, region_margin=1.25,
-                 fused_adam=True, out_capacity=None, dssim_lambda=0.0):
+                 fused_adam=True, out_capacity=None, dssim_lambda=0.0, overlap_split=True):
         self.g = g
         # fused_adam: the Adam step of the candidates runs before the plan and the
         # compaction applies it to every other row while copying (one pass over
         # parameters and moments instead of two; same result bit for bit)
         self.fused_adam = fused_adam
+        # overlap_split (with fused_adam): the plan's proposals and merges run on the
+        # library's auxiliary stream while the compaction streams the kept rows
+        # (adp_split_plan_overlapped / adp_split_apply_adam_overlapped; same result)
+        self.overlap_split = overlap_split
         # dssim_lambda > 0: the baselines' loss (1 - lambda) L1 + lambda (1 - SSIM),
         # its image gradient fed to the backward; 0 keeps the pure L1 loss
         self.dssim_lambda = float(dssim_lambda)
@@ -183,13 +187,19 @@ class PlainStep:
         else:
             mark("adam")
             ops.adam_step(g, self.grad, self.m, self.v, self.adam_t, self.lr)
+        overlap = self.fused_adam and self.overlap_split
         mark("split_plan")
-        plan = ops.split_plan(g, cams, self.regions, self.cand, self.count, prm, ws=self.ws_split,
-                              sync=False)
+        if overlap:
+            plan = ops.split_plan_overlapped(g, cams, self.regions, self.cand, self.count, prm,
+                                             ws=self.ws_split)
+        else:
+            plan = ops.split_plan(g, cams, self.regions, self.cand, self.count, prm,
+                                  ws=self.ws_split, sync=False)
         mark("split_apply")
         if self.fused_adam:
             ops.split_apply_adam(g, self.grad, self.m, self.v, plan, self.regions, self.cand, noise,
-                                 self.adam_t, self.out, self.m_out, self.v_out, prm, self.lr)
+                                 self.adam_t, self.out, self.m_out, self.v_out, prm, self.lr,
+                                 overlapped=overlap)
         else:
             ops.split_apply(g, plan, self.regions, self.cand, noise, prm, m_in=self.m, v_in=self.v,
                             out=self.out, m_out=self.m_out, v_out=self.v_out)
@@ -368,11 +378,12 @@ class DensifyStep(PlainStep):
         mark("adam_rows")
         ops.adam_step_rows(g, self.grad, self.m, self.v, self.cand, self.adam_t, self.lr)
         mark("split_plan")
-        plan = ops.split_plan(g, cams, self.regions, self.cand, self.count, prm, ws=self.ws_split,
-                              sync=False)
+        plan = ops.split_plan_overlapped(g, cams, self.regions, self.cand, self.count, prm,
+                                         ws=self.ws_split)
         mark("split_apply")
         ops.split_apply_adam(g, self.grad, self.m, self.v, plan, self.regions, self.cand, noise,
-                             self.adam_t, self.out, self.m_out, self.v_out, prm, self.lr)
+                             self.adam_t, self.out, self.m_out, self.v_out, prm, self.lr,
+                             overlapped=True)
         mark("clone")
         ops.split_clone(g, plan, self.regions, self.cand, self.sets.clone, self.sets.counts[1:],
                         n, self.out, self.m_out, self.v_out, d_new_n=self.d_new_n)

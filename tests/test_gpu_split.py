@@ -218,3 +218,76 @@ def test_split_apply_into_capacity_buffers_without_sync():
     ops.split_apply(g, plan, regs, cand, noise, with_state=False, out=small)
     torch.cuda.synchronize()
     assert all(int(t.abs().sum().item()) == 0 for t in small.tensors())
+
+
+def test_overlapped_split_equals_two_call_split():
+    """The overlapped plan and compaction (proposals and merges on the library's
+    auxiliary stream while the kept rows stream) give, bit for bit, what the
+    two-call plan and fused compaction give: statuses, child counts, new size,
+    population and moments. Three capacities: the worst case (kept rows written
+    against the bound on the new size), exactly the new size (merges remove
+    children here, so the bound exceeds the capacity and the kept rows are
+    written after the join), and one row less (nothing written)."""
+    sc, cams = small_cluster_inputs(6000, 240, 160, views=4, seed=12)
+    tg = scenes.scene_clusters(99, 9000, 3)
+    targets = []
+    for cam in cams:
+        r = O.render(O.project(O.theta_of(tg), 3, cam), cam)
+        targets.append(r["rgb"].astype(np.float32).reshape(cam["height"], cam["width"], 3))
+    k, n_max = 600, 4
+    orc = O.plain_step(sc, cams, targets, k_cand=k, sp=O.SplitParams(n_max=n_max),
+                       noise=scenes.fallback_noise(8, k).astype(np.float64))
+    from paper_2605_06876_b300 import _abi
+    prm = _abi.default_params(n_max=n_max)
+    g0 = ops.Gaussians.from_scene(sc, DEV)
+    rg = orc["regions"]
+    regs = ops.Regions.from_arrays(rg["view"], rg["parent"], rg["label"], rg["stats"], rg["band"],
+                                   rg["moments"], DEV)
+    cand = torch.as_tensor(orc["cand"], device=DEV)
+    count = torch.as_tensor(orc["count"], device=DEV)
+    noise = torch.as_tensor(scenes.fallback_noise(8, k), device=DEV)
+    gen = torch.Generator(DEV).manual_seed(9)
+    grad, m0, v0 = g0.zeros_like(), g0.zeros_like(), g0.zeros_like()
+    for t in grad.tensors():
+        t.normal_(0.0, 1e-2, generator=gen)
+    for t in m0.tensors():
+        t.normal_(0.0, 1e-3, generator=gen)
+    for t in v0.tensors():
+        t.uniform_(0.0, 1e-4, generator=gen)
+    n = g0.n
+    worst = n + k * (n_max + 1)
+
+    def run(overlapped, cap):
+        g, m, v = g0.clone(), m0.clone(), v0.clone()
+        d_step = torch.full((1,), 3, dtype=torch.int32, device=DEV)
+        out = [ops.Gaussians(cap, g.sh_degree, DEV, zero=True) for _ in range(3)]
+        ops.adam_step_rows(g, grad, m, v, cand, d_step, ops.ADAM_LR)
+        if overlapped:
+            plan = ops.split_plan_overlapped(g, cams, regs, cand, count, prm)
+        else:
+            plan = ops.split_plan(g, cams, regs, cand, count, prm, sync=False)
+        ops.split_apply_adam(g, grad, m, v, plan, regs, cand, noise, d_step, out[0], out[1],
+                             out[2], prm, ops.ADAM_LR, overlapped=overlapped)
+        torch.cuda.synchronize()
+        return plan, out, int(d_step.item())
+
+    ref_plan, ref_out, ref_step = run(False, worst)
+    n_new = int(ref_plan.d_new_n.item())
+    st = np_(ref_plan.status)
+    per_parent = np.bincount(rg["parent"], minlength=n)[orc["cand"]]
+    bound = n + int(np.minimum(per_parent[st == 1], n_max).sum()) + int((st == 2).sum())
+    assert n < n_new < bound <= worst
+
+    def rows(gs, upto):
+        return [t[:, :upto] if t.dim() == 3 else t[:upto] for x in gs for t in x.tensors()]
+
+    for cap in (worst, n_new, n_new - 1):
+        plan, out, step = run(True, cap)
+        assert torch.equal(plan.status, ref_plan.status)
+        assert torch.equal(plan.n_children, ref_plan.n_children)
+        assert int(plan.d_new_n.item()) == n_new and step == ref_step == 4
+        if cap >= n_new:
+            for a, b in zip(rows(out, n_new), rows(ref_out, n_new)):
+                assert torch.equal(a, b)
+        else:
+            assert all(int(torch.count_nonzero(t)) == 0 for x in out for t in x.tensors())
