@@ -164,6 +164,8 @@ class PlainStep:
                             self.count, self.mass)
             mark("select_topk")
             ops.select_topk(self.mass, n, self.k, self.cand, ws=self.ws_topk)
+            cand_ready = torch.cuda.Event()
+            cand_ready.record(self.side)
             mark("error_regions")
             ops.error_regions(self.maps, self.img.dominant, self.target, n, cams, self.cand, prm,
                               regions=self.regions, ws=self.ws_regions, grow=False)
@@ -179,12 +181,15 @@ class PlainStep:
         else:
             ops.render_backward(g, self.pr, self.bins, self.img, cams, target=self.target,
                                 bg=self.bg, params=prm, grad=self.grad, ws=self.ws_bwd)
-        mark("join")
-        main.wait_stream(self.side)  # join before the candidates' Adam step and the split
         if self.fused_adam:
+            # the candidates' Adam step needs only the gradient and the candidates, so
+            # it runs beside the regions (the longer branch) instead of after them
+            main.wait_event(cand_ready)
             mark("adam_rows")
             ops.adam_step_rows(g, self.grad, self.m, self.v, self.cand, self.adam_t, self.lr)
-        else:
+        mark("join")
+        main.wait_stream(self.side)  # join before the split
+        if not self.fused_adam:
             mark("adam")
             ops.adam_step(g, self.grad, self.m, self.v, self.adam_t, self.lr)
         overlap = self.fused_adam and self.overlap_split
@@ -371,12 +376,18 @@ class DensifyStep(PlainStep):
         mark("densify_select")
         ops.densify_select(self.accum, self.visits, g, self.tau_g, self.tau_s, out=self.sets,
                            ws=self.ws_densify)
-        main.wait_stream(self.side)
-        mark("error_regions")
-        ops.error_regions(self.maps, self.img.dominant, self.target, n, cams, self.cand, prm,
-                          regions=self.regions, ws=self.ws_regions, grow=False)
+        # the regions of the selected candidates (beside the error map's stream) and
+        # the candidates' Adam step run concurrently
+        self.side.wait_stream(main)
+        with torch.cuda.stream(self.side):
+            mark("error_regions")
+            ops.error_regions(self.maps, self.img.dominant, self.target, n, cams, self.cand, prm,
+                              regions=self.regions, ws=self.ws_regions, grow=False)
+            mark("error_regions_end")
         mark("adam_rows")
         ops.adam_step_rows(g, self.grad, self.m, self.v, self.cand, self.adam_t, self.lr)
+        mark("join")
+        main.wait_stream(self.side)
         mark("split_plan")
         plan = ops.split_plan_overlapped(g, cams, self.regions, self.cand, self.count, prm,
                                          ws=self.ws_split)
