@@ -40,10 +40,10 @@ WORKLOAD = dict(workload="single-view plain step: 1,000,000 Gaussians (64 cluste
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "split_apply_traffic.json")
 
 
-def _measured_traffic(stage):
-    """DRAM bytes per launch of a stage's kernels from the committed ncu capture, if
-    the capture covers this stage and every source it was taken from is unchanged
-    (sha1 of the files); otherwise None."""
+def _measured_traffic(stage, kernel=None):
+    """DRAM bytes per launch of one kernel of a stage from the committed ncu capture,
+    if the capture covers this stage and every source it was taken from is
+    unchanged (sha1 of the files); otherwise None."""
     import hashlib
 
     try:
@@ -60,7 +60,7 @@ def _measured_traffic(stage):
                     return None
         except OSError:
             return None
-    return rec.get("dram_bytes_per_launch")
+    return rec.get("dram_bytes_per_launch", {}).get(kernel) if kernel else None
 
 
 def _peaks():
@@ -159,11 +159,13 @@ def stage_bytes(n, n_vis, K, P, n_tiles, sh_planes, regions, k, kept, appended):
         "adam": n * gbytes * 6 + n_vis * gbytes + n,
         "adam_rows": k * gbytes * 6 + min(k, n_vis) * gbytes + k * 5,
         "split_plan": regions * 300 + n * 12 + k * 16,
-        # compaction with the fused Adam step: kept rows as in Adam (gradients of
-        # rendered rows only), the parents read, appended rows written with zero
-        # moments, one destination word and one mask byte per row
-        "split_apply": (kept * gbytes * 6 + min(kept, n_vis) * gbytes + k * gbytes +
-                        appended * gbytes * 3 + n * (4 + 1)),
+        # compaction with the fused Adam step (apply_keep_kernel): kept rows as in
+        # Adam (gradients of rendered rows only), one destination word and one mask
+        # byte per row
+        "split_apply": kept * gbytes * 6 + min(kept, n_vis) * gbytes + n * (4 + 1),
+        # appended rows (apply_append_kernel): the parents read, the new rows
+        # written with zero moments
+        "split_append": k * gbytes + appended * gbytes * 3,
     }
 
 
@@ -302,15 +304,19 @@ def run_ours(args, rank, world, local_rank):
     sb = stage_bytes(n, n_vis, K, stepper.P, stepper.bins.ranges.shape[0], ops.sh_planes(3), R,
                      stepper.k, new_n - appended, appended)
     per_stage = {k: v / stage_steps for k, v in stage_ms.items()}
-    # the roofline is reported for the stage holding the step's top kernel in the
-    # ncu launch list (apply_keep_kernel, the compaction with the fused Adam step,
-    # HBM-bound); render_backward takes about as long, but it shares the SMs with
-    # the concurrent error-statistics stream, so its stage time is not its own
+    # the roofline is reported for the step's top kernel in the ncu launch list,
+    # apply_keep_kernel (the compaction of the kept rows with the fused Adam step,
+    # HBM-bound), alone in its stage: the plan's proposals and merges run beside it
+    # on the library's auxiliary stream, the appended rows follow in their own
+    # stage. render_backward takes about as long, but it shares the SMs with the
+    # concurrent error-statistics stream, so its stage time is not its own
     dom = "split_apply"
     peak, peak_kind, peaks = _peaks()
     ach = sb[dom] / (per_stage[dom] * 1e-3) / 1e9
-    roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
-            "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": _measured_traffic(dom),
+    roof = {"kernel": "apply_keep_kernel", "stage": dom, "bound": "hbm",
+            "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(ach / peak, 4),
+            "traffic": _measured_traffic(dom, "apply_keep_kernel<1>"),
             "algorithmic_bytes": int(sb[dom]), "peak_source": peak_kind}
     # the compositing stages are bound by the FP32 pipes: exact per-pixel work of the
     # last step (list positions evaluated up to the last blended Gaussian, blended

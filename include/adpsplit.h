@@ -320,25 +320,34 @@ ADP_API int adp_split_apply_adam(const adp_gaussians* g, const adp_gaussians* gr
  * size: n + sum over ADAPTIVE candidates of min(regions, n_max) + the FALLBACK
  * count), then the proposals, merges, child counts and the new size on the
  * library's auxiliary stream of the current device (highest priority), which
- * waits for that part. adp_split_apply_adam_overlapped writes the kept rows on
- * `stream` when the bound fits out->n, waits for the auxiliary stream, then
- * appends the new rows (and writes the kept rows there if only the exact size
- * fits). status is ready in stream order after the plan; n_children,
- * *d_new_n and the population only after the compaction call. Constraints:
- * the two calls come in this order, on one stream and device, from one host
- * thread, with no other overlapped plan of that device in between; the first
- * overlapped plan on a device creates the auxiliary stream and its two events,
- * so it must come before any stream capture that includes these calls (inside
- * a capture the auxiliary stream joins the capture as a forked stream). The
- * workspace is that of adp_split_plan. Arguments, ownership and errors as in
- * adp_split_plan (without h_new_n) and adp_split_apply_adam. */
+ * waits for that part. adp_split_keep_overlapped writes the kept rows (with
+ * their Adam step) on `stream` when the bound fits out->n. adp_split_append_
+ * overlapped makes `stream` wait for the auxiliary stream, appends the new rows
+ * (and writes the kept rows there if only the exact size fits) and advances
+ * *d_step. status is ready in stream order after the plan; n_children,
+ * *d_new_n and the population only after the append call. Constraints: the
+ * three calls come in this order, on one stream and device, from one host
+ * thread, with no other overlapped plan of that device in between, and with
+ * identical arguments for the last two; the first overlapped plan on a device
+ * creates the auxiliary stream and its two events, so it must come before any
+ * stream capture that includes these calls (inside a capture the auxiliary
+ * stream joins the capture as a forked stream). The workspace is that of
+ * adp_split_plan. Arguments, ownership and errors as in adp_split_plan (without
+ * h_new_n) and adp_split_apply_adam. */
 ADP_API int adp_split_plan_overlapped(const adp_gaussians* g, const adp_camera* cams,
                                       int32_t n_views, const adp_regions* regs,
                                       const int32_t* candidates, int64_t n_cand,
                                       const int32_t* count, const adp_params* prm,
                                       uint8_t* status, int32_t* n_children, int64_t* d_new_n,
                                       void* ws, size_t ws_bytes, adp_stream_t stream);
-ADP_API int adp_split_apply_adam_overlapped(
+ADP_API int adp_split_keep_overlapped(
+    const adp_gaussians* g, const adp_gaussians* grad, const adp_gaussians* m_in,
+    const adp_gaussians* v_in, const adp_regions* regs, const int32_t* candidates, int64_t n_cand,
+    const uint8_t* status, const int32_t* n_children, const float* noise, const adp_params* prm,
+    int32_t step, int32_t* d_step, const float* lr, float beta1, float beta2, float eps,
+    adp_gaussians* out, adp_gaussians* m_out, adp_gaussians* v_out, void* ws, size_t ws_bytes,
+    adp_stream_t stream);
+ADP_API int adp_split_append_overlapped(
     const adp_gaussians* g, const adp_gaussians* grad, const adp_gaussians* m_in,
     const adp_gaussians* v_in, const adp_regions* regs, const int32_t* candidates, int64_t n_cand,
     const uint8_t* status, const int32_t* n_children, const float* noise, const adp_params* prm,

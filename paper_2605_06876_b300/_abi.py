@@ -102,7 +102,13 @@ _PROTOS = {
     "adp_split_plan_overlapped": (C.c_int, [P(AdpGaussians), P(AdpCamera), _i32, P(AdpRegions),
                                             _vp, _i64, _vp, P(AdpParams), _vp, _vp, _vp, _vp,
                                             C.c_size_t, _vp]),
-    "adp_split_apply_adam_overlapped": (C.c_int, [P(AdpGaussians), P(AdpGaussians),
+    "adp_split_keep_overlapped": (C.c_int, [P(AdpGaussians), P(AdpGaussians),
+                                                  P(AdpGaussians), P(AdpGaussians), P(AdpRegions),
+                                                  _vp, _i64, _vp, _vp, _vp, P(AdpParams), _i32,
+                                                  _vp, P(C.c_float), C.c_float, C.c_float,
+                                                  C.c_float, P(AdpGaussians), P(AdpGaussians),
+                                                  P(AdpGaussians), _vp, C.c_size_t, _vp]),
+        "adp_split_append_overlapped": (C.c_int, [P(AdpGaussians), P(AdpGaussians),
                                                   P(AdpGaussians), P(AdpGaussians), P(AdpRegions),
                                                   _vp, _i64, _vp, _vp, _vp, P(AdpParams), _i32,
                                                   _vp, P(C.c_float), C.c_float, C.c_float,

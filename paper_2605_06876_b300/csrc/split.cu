@@ -1062,13 +1062,20 @@ extern "C" ADP_API int adp_split_plan_overlapped(const adp_gaussians* g, const a
   return ADP_OK;
 }
 
+// Which part of the compaction a call enqueues: everything, or, after an
+// overlapped plan, the kept rows (against the bound) or the join and the
+// appended rows.
+enum class ApplyPart { ALL, KEEP, APPEND };
+
 static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
                             const AdamHyper* adam, const adp_gaussians* m_in,
                             const adp_gaussians* v_in, const adp_regions* regs,
                             const int32_t* candidates, int64_t n_cand, const uint8_t* status,
                             const int32_t* n_children, const float* noise, const adp_params* prm,
                             adp_gaussians* out, adp_gaussians* m_out, adp_gaussians* v_out,
-                            void* ws, size_t ws_bytes, cudaStream_t st, bool overlapped = false) {
+                            void* ws, size_t ws_bytes, cudaStream_t st,
+                            ApplyPart part = ApplyPart::ALL) {
+  const bool overlapped = part != ApplyPart::ALL;
   ADP_CHECK_ARG(g && out && regs && prm, "NULL argument");
   ADP_CHECK_ARG(gauss_ok(g) || g->n == 0, "bad input Gaussian arrays");
   ADP_CHECK_ARG(gauss_ok(out) || out->n == 0, "bad output Gaussian arrays");
@@ -1121,13 +1128,14 @@ static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
     int rc = aux_stream(&aux);
     if (rc) return rc;
   }
-  if (n > 0) {
+  if (n > 0 && part != ApplyPart::APPEND) {
     const dim3 kg(grid_for(n, 256), 3 + planes);
     if (adam)
       apply_keep_kernel<true><<<kg, 256, 0, st>>>(aa);
     else
       apply_keep_kernel<false><<<kg, 256, 0, st>>>(aa);
   }
+  if (part == ApplyPart::KEEP) return ADP_OK;
   if (overlapped) {  // join the plan's second part
     std::lock_guard<std::mutex> lock(g_aux_mu);
     ADP_CUDA(cudaStreamWaitEvent(st, aux->merged, 0));
@@ -1196,25 +1204,49 @@ extern "C" ADP_API int adp_split_apply_adam(
   return ADP_OK;
 }
 
-extern "C" ADP_API int adp_split_apply_adam_overlapped(
+static int split_overlapped_part(
+    const adp_gaussians* g, const adp_gaussians* grad, const adp_gaussians* m_in,
+    const adp_gaussians* v_in, const adp_regions* regs, const int32_t* candidates, int64_t n_cand,
+    const uint8_t* status, const int32_t* n_children, const float* noise, const adp_params* prm,
+    int32_t step, int32_t* d_step, const float* lr, float beta1, float beta2, float eps,
+    adp_gaussians* out, adp_gaussians* m_out, adp_gaussians* v_out, void* ws, size_t ws_bytes,
+    adp_stream_t stream, ApplyPart part) {
+  ADP_CHECK_ARG(lr, "NULL lr");
+  ADP_CHECK_ARG(d_step || step >= 1, "step must be >= 1");
+  AdamHyper h = adam_hyper(lr, beta1, beta2, eps, step, d_step);
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = split_apply_impl(g, grad, &h, m_in, v_in, regs, candidates, n_cand, status, n_children,
+                            noise, prm, out, m_out, v_out, ws, ws_bytes, st, part);
+  if (rc) return rc;
+  if (d_step && part == ApplyPart::APPEND) {
+    split_step_advance_kernel<<<1, 1, 0, st>>>(d_step);
+    ADP_LAUNCH_CHECK();
+  }
+  return ADP_OK;
+}
+
+extern "C" ADP_API int adp_split_keep_overlapped(
     const adp_gaussians* g, const adp_gaussians* grad, const adp_gaussians* m_in,
     const adp_gaussians* v_in, const adp_regions* regs, const int32_t* candidates, int64_t n_cand,
     const uint8_t* status, const int32_t* n_children, const float* noise, const adp_params* prm,
     int32_t step, int32_t* d_step, const float* lr, float beta1, float beta2, float eps,
     adp_gaussians* out, adp_gaussians* m_out, adp_gaussians* v_out, void* ws, size_t ws_bytes,
     adp_stream_t stream) {
-  ADP_CHECK_ARG(lr, "NULL lr");
-  ADP_CHECK_ARG(d_step || step >= 1, "step must be >= 1");
-  AdamHyper h = adam_hyper(lr, beta1, beta2, eps, step, d_step);
-  cudaStream_t st = (cudaStream_t)stream;
-  int rc = split_apply_impl(g, grad, &h, m_in, v_in, regs, candidates, n_cand, status, n_children,
-                            noise, prm, out, m_out, v_out, ws, ws_bytes, st, /*overlapped=*/true);
-  if (rc) return rc;
-  if (d_step) {
-    split_step_advance_kernel<<<1, 1, 0, st>>>(d_step);
-    ADP_LAUNCH_CHECK();
-  }
-  return ADP_OK;
+  return split_overlapped_part(g, grad, m_in, v_in, regs, candidates, n_cand, status, n_children,
+                               noise, prm, step, d_step, lr, beta1, beta2, eps, out, m_out, v_out,
+                               ws, ws_bytes, stream, ApplyPart::KEEP);
+}
+
+extern "C" ADP_API int adp_split_append_overlapped(
+    const adp_gaussians* g, const adp_gaussians* grad, const adp_gaussians* m_in,
+    const adp_gaussians* v_in, const adp_regions* regs, const int32_t* candidates, int64_t n_cand,
+    const uint8_t* status, const int32_t* n_children, const float* noise, const adp_params* prm,
+    int32_t step, int32_t* d_step, const float* lr, float beta1, float beta2, float eps,
+    adp_gaussians* out, adp_gaussians* m_out, adp_gaussians* v_out, void* ws, size_t ws_bytes,
+    adp_stream_t stream) {
+  return split_overlapped_part(g, grad, m_in, v_in, regs, candidates, n_cand, status, n_children,
+                               noise, prm, step, d_step, lr, beta1, beta2, eps, out, m_out, v_out,
+                               ws, ws_bytes, stream, ApplyPart::APPEND);
 }
 
 // ------------------------------------------------------------------ clone

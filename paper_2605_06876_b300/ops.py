@@ -450,11 +450,12 @@ def split_apply(g: Gaussians, plan: SplitPlan, regions: Regions, candidates, noi
 def split_apply_adam(g: Gaussians, grad: Gaussians, m_in: Gaussians, v_in: Gaussians,
                      plan: SplitPlan, regions: Regions, candidates, noise, step, out: Gaussians,
                      m_out: Gaussians, v_out: Gaussians, params=None, lr=None, beta1=0.9,
-                     beta2=0.999, eps=1e-15, stream=None, overlapped=False):
+                     beta2=0.999, eps=1e-15, stream=None, overlapped=False, part=None):
     """adp_split_apply_adam: the compaction with the Adam step applied to every kept
     non-candidate row on the way (candidates first via adam_step_rows). With
-    overlapped=True (adp_split_apply_adam_overlapped) it follows
-    split_plan_overlapped: the kept rows are written while the merge finishes."""
+    overlapped=True it follows split_plan_overlapped: adp_split_keep_overlapped
+    writes the kept rows while the merge finishes, then adp_split_append_overlapped
+    joins and appends (part="keep" or "append" issues one of the two)."""
     params = params or A.default_params()
     lrc = (C.c_float * 6)(*[float(x) for x in (lr or ADAM_LR)])
     host_step, d_step = _step_arg(step)
@@ -463,12 +464,18 @@ def split_apply_adam(g: Gaussians, grad: Gaussians, m_in: Gaussians, v_in: Gauss
         noise = torch.zeros((max(nc, 1), 2, 3), dtype=F32, device=g.mean_logit.device)
     gc, grc, mic, vic = g.c(), grad.c(), m_in.c(), v_in.c()
     oc, moc, voc, rc = out.c(), m_out.c(), v_out.c(), regions.c()
-    fn = "adp_split_apply_adam_overlapped" if overlapped else "adp_split_apply_adam"
-    A.check(getattr(A.lib(), fn)(
-        C.byref(gc), C.byref(grc), C.byref(mic), C.byref(vic), C.byref(rc), _p(candidates), nc,
-        _p(plan.status), _p(plan.n_children), _p(noise), C.byref(params), host_step, d_step, lrc,
-        beta1, beta2, eps, C.byref(oc), C.byref(moc), C.byref(voc), _p(plan.ws), plan.ws.numel(),
-        _stream(stream)), fn)
+    if not overlapped:
+        fns = ["adp_split_apply_adam"]
+    else:
+        fns = {None: ["adp_split_keep_overlapped", "adp_split_append_overlapped"],
+               "keep": ["adp_split_keep_overlapped"],
+               "append": ["adp_split_append_overlapped"]}[part]
+    for fn in fns:
+        A.check(getattr(A.lib(), fn)(
+            C.byref(gc), C.byref(grc), C.byref(mic), C.byref(vic), C.byref(rc), _p(candidates), nc,
+            _p(plan.status), _p(plan.n_children), _p(noise), C.byref(params), host_step, d_step,
+            lrc, beta1, beta2, eps, C.byref(oc), C.byref(moc), C.byref(voc), _p(plan.ws),
+            plan.ws.numel(), _stream(stream)), fn)
     return out, m_out, v_out
 
 

@@ -201,10 +201,15 @@ class PlainStep:
             plan = ops.split_plan(g, cams, self.regions, self.cand, self.count, prm,
                                   ws=self.ws_split, sync=False)
         mark("split_apply")
-        if self.fused_adam:
+        if overlap:  # the kept rows (the dominant kernel), then the join and the appended rows
+            args = (g, self.grad, self.m, self.v, plan, self.regions, self.cand, noise, self.adam_t,
+                    self.out, self.m_out, self.v_out, prm, self.lr)
+            ops.split_apply_adam(*args, overlapped=True, part="keep")
+            mark("split_append")
+            ops.split_apply_adam(*args, overlapped=True, part="append")
+        elif self.fused_adam:
             ops.split_apply_adam(g, self.grad, self.m, self.v, plan, self.regions, self.cand, noise,
-                                 self.adam_t, self.out, self.m_out, self.v_out, prm, self.lr,
-                                 overlapped=overlap)
+                                 self.adam_t, self.out, self.m_out, self.v_out, prm, self.lr)
         else:
             ops.split_apply(g, plan, self.regions, self.cand, noise, prm, m_in=self.m, v_in=self.v,
                             out=self.out, m_out=self.m_out, v_out=self.v_out)
