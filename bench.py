@@ -60,7 +60,8 @@ def _measured_traffic(stage, kernel=None):
                     return None
         except OSError:
             return None
-    return rec.get("dram_bytes_per_launch", {}).get(kernel) if kernel else None
+    per_kernel = rec.get("dram_bytes_per_launch")
+    return per_kernel.get(kernel) if kernel and isinstance(per_kernel, dict) else None
 
 
 def _peaks():
