@@ -683,9 +683,20 @@ struct AppendArgs {
   const long long* counters;
   const float* noise;
   float shrink;  // ln(2 eta), rounded to float32
-  bool late_keep;    // the kept rows were skipped against the bound: see below
-  ApplyArgs keep;    // (with the Adam step) for that case
 };
+
+// After an overlapped plan: the kept rows skipped by apply_keep_kernel because
+// the bound on the new size exceeded the capacity, when the exact size fits (a
+// grid-stride pass over every row and plane; a caller that sizes out for the
+// bound never takes it, and the kernel then returns at once).
+__global__ void __launch_bounds__(256) late_keep_kernel(ApplyArgs a) {
+  if (a.counters[5] <= a.out.n || a.counters[3] > a.out.n) return;
+  a.fit = a.counters + 3;
+  const long long nr = a.in.n, tot = nr * (3 + a.planes);
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < tot;
+       u += (long long)gridDim.x * blockDim.x)
+    keep_row<true>(a, (int)(u / nr), u % nr);
+}
 
 // Appended rows: one thread per new row, in chunks of APP_THREADS rows per
 // block. A row's candidate is the last one whose block of rows starts at or
@@ -721,17 +732,6 @@ __global__ void __launch_bounds__(APP_THREADS) apply_append_kernel(AppendArgs a)
   __shared__ long long s_off[APP_STAGE];
   __shared__ long long s_c[2];
   if (a.counters[3] > a.out.n) return;  // the new population does not fit: write nothing
-  if (a.late_keep && a.counters[5] > a.out.n) {
-    // the overlapped compaction skipped the kept rows because the bound on the
-    // new size exceeded the capacity, but the exact size fits: copy them here
-    // (a slow grid-stride pass; a caller sizing out for the bound never takes it)
-    const long long nr = a.keep.in.n, tot = nr * (3 + a.planes);
-    ApplyArgs ka = a.keep;
-    ka.fit = a.counters + 3;
-    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < tot;
-         u += (long long)gridDim.x * blockDim.x)
-      keep_row<true>(ka, (int)(u / nr), u % nr);
-  }
   const long long n_keep = a.counters[1], n_app = a.counters[2];
   for (long long r0 = blockIdx.x * (long long)APP_THREADS; r0 < n_app;
        r0 += (long long)gridDim.x * APP_THREADS) {
@@ -1140,10 +1140,12 @@ static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
     std::lock_guard<std::mutex> lock(g_aux_mu);
     ADP_CUDA(cudaStreamWaitEvent(st, aux->merged, 0));
   }
+  if (overlapped && n > 0) {
+    late_keep_kernel<<<148 * 2, 256, 0, st>>>(aa);
+    ADP_LAUNCH_CHECK();
+  }
   if (nc > 0) {
     AppendArgs ap;
-    ap.late_keep = overlapped && adam;
-    ap.keep = aa;
     ap.in = gin;
     ap.out = gout;
     ap.has_m_out = m_out != nullptr;
