@@ -321,11 +321,10 @@ ADP_API int adp_split_apply_adam(const adp_gaussians* g, const adp_gaussians* gr
  * count), then the proposals, merges, child counts and the new size on the
  * library's auxiliary stream of the current device (highest priority), which
  * waits for that part. adp_split_keep_overlapped writes the kept rows (with
- * their Adam step) on `stream` when the bound fits out->n, and enqueues the
- * appended rows on the auxiliary stream after the merges (the two sets of rows
- * are disjoint). adp_split_append_overlapped makes `stream` wait for the
- * auxiliary stream, writes the kept rows if only the exact size fits out->n
- * (not the bound), and advances *d_step. status is ready in stream order after the plan; n_children,
+ * their Adam step) on `stream` when the bound fits out->n. adp_split_append_
+ * overlapped makes `stream` wait for the auxiliary stream, appends the new rows
+ * (and writes the kept rows there if only the exact size fits) and advances
+ * *d_step. status is ready in stream order after the plan; n_children,
  * *d_new_n and the population only after the append call. Constraints: the
  * three calls come in this order, on one stream and device, from one host
  * thread, with no other overlapped plan of that device in between, and with

@@ -1135,11 +1135,17 @@ static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
     else
       apply_keep_kernel<false><<<kg, 256, 0, st>>>(aa);
   }
-  // the appended rows: after the kept rows on `st`, or, overlapped, on the
-  // auxiliary stream right after the plan's second part (their rows are disjoint
-  // from the kept ones), so they also run beside apply_keep_kernel
-  AppendArgs ap;
+  if (part == ApplyPart::KEEP) return ADP_OK;
+  if (overlapped) {  // join the plan's second part
+    std::lock_guard<std::mutex> lock(g_aux_mu);
+    ADP_CUDA(cudaStreamWaitEvent(st, aux->merged, 0));
+  }
+  if (overlapped && n > 0) {
+    late_keep_kernel<<<148 * 2, 256, 0, st>>>(aa);
+    ADP_LAUNCH_CHECK();
+  }
   if (nc > 0) {
+    AppendArgs ap;
     ap.in = gin;
     ap.out = gout;
     ap.has_m_out = m_out != nullptr;
@@ -1157,28 +1163,9 @@ static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
     ap.counters = w.counters;
     ap.noise = noise;
     ap.shrink = (float)std::log(2.0 * (double)prm->eta);
+    apply_append_kernel<<<grid_for(nc * (long long)(prm->n_max > 1 ? prm->n_max + 1 : 2),
+                                   APP_THREADS, 148 * 16), APP_THREADS, 0, st>>>(ap);
   }
-  const unsigned app_grid =
-      grid_for(nc * (long long)(prm->n_max > 1 ? prm->n_max + 1 : 2), APP_THREADS, 148 * 16);
-  if (part == ApplyPart::KEEP) {
-    std::lock_guard<std::mutex> lock(g_aux_mu);
-    if (nc > 0) {
-      apply_append_kernel<<<app_grid, APP_THREADS, 0, aux->stream>>>(ap);
-      ADP_LAUNCH_CHECK();
-    }
-    ADP_CUDA(cudaEventRecord(aux->merged, aux->stream));
-    return ADP_OK;
-  }
-  if (overlapped) {  // join the auxiliary stream (the plan's second part, the appended rows)
-    std::lock_guard<std::mutex> lock(g_aux_mu);
-    ADP_CUDA(cudaStreamWaitEvent(st, aux->merged, 0));
-  }
-  if (overlapped && n > 0) {
-    late_keep_kernel<<<148 * 2, 256, 0, st>>>(aa);
-    ADP_LAUNCH_CHECK();
-  }
-  if (nc > 0 && !overlapped)
-    apply_append_kernel<<<app_grid, APP_THREADS, 0, st>>>(ap);
   ADP_LAUNCH_CHECK();
   return ADP_OK;
 }
