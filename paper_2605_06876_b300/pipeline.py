@@ -1,12 +1,15 @@
 """One plain AdpSplit training step over preallocated device buffers.
 
-A step runs the whole hot path on one stream: projection, binning and depth sort,
-compositing with the dominant map, error statistics, top-k candidate choice by
-error mass, error regions, the render backward of the L1 loss, one Adam step, and
-the AdpSplit operator (plan and apply into buffers sized for the largest possible
-result, so no step synchronises with the host). The new population (the first
-plan.d_new_n entries of the returned buffers) is returned; the step's own population
-is updated only by Adam, so repeated steps see the same workload.
+A step runs the whole hot path: projection, binning and depth sort, compositing with
+the dominant map, error statistics, top-k candidate choice by error mass, error
+regions, the render backward of the L1 loss, one Adam step, and the AdpSplit operator
+(plan and apply into buffers sized for the largest possible result, so no step
+synchronises with the host). The error chain runs on a second stream beside the
+backward, and the split's proposals and merges on the library's auxiliary stream
+beside the compaction; every fork is joined within the step, so a step captures into
+one CUDA graph. The new population (the first plan.d_new_n entries of the returned
+buffers) is returned; the step's own population is updated only by Adam, so repeated
+steps see the same workload.
 """
 from __future__ import annotations
 
