@@ -64,6 +64,25 @@ def _measured_traffic(stage, kernel=None):
     return per_kernel.get(kernel) if kernel and isinstance(per_kernel, dict) else None
 
 
+def max_over_ranks(x, device="cpu"):
+    """The largest x over the ranks of the default process group (x itself without
+    one): the whole job takes as long as its slowest replica."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, max_seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time
+    (weak scaling: every rank processes the same units)."""
+    return world * units_per_rank / max_seconds
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -250,14 +269,9 @@ def run_ours(args, rank, world, local_rank):
     if not stepper.check_capacity(last_plan):
         raise RuntimeError("instance, region or population capacity exceeded in the timed region")
     new_n = int(last_plan.d_new_n.item())
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(step_ms), dev)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
+    value = job_rate(args.steps, world, total_ms / 1e3)
 
     # end to end through the public API: inputs from pinned host memory each step,
     # the split decisions read back each step
@@ -288,12 +302,7 @@ def run_ours(args, rank, world, local_rank):
         stream.synchronize()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dev)
 
     # roofline of the dominant stage
     n = g.n
@@ -357,7 +366,7 @@ def run_ours(args, rank, world, local_rank):
         "config": dict(WORKLOAD, parallelism=f"replicas{world}" if world > 1 else "single",
                        **({"n_gaussians": g.n, "note": "reduced scene for profiling"}
                           if args.gaussians else {})),
-        "e2e": {"value": round(1e3 / e2e_ms * world, 3), "unit": UNIT,
+        "e2e": {"value": round(job_rate(1, world, e2e_ms / 1e3), 3), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "roofline": roof,
         "roofline_alu": roof_alu,
