@@ -102,7 +102,12 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples (kept after the run for inspection); set BENCH_CLOCKS_DIR
+        # to keep them elsewhere than the system's temporary directory
+        import tempfile
+
+        folder = os.environ.get("BENCH_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(folder, f"clocks_{os.getpid()}.csv")
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -160,8 +165,9 @@ FLOP_BLEND_BWD = 56
 
 
 def stage_bytes(n, n_vis, K, P, n_tiles, sh_planes, regions, k, kept, appended):
-    """Algorithmic DRAM bytes of each stage for one step (each input read once, each
-    output written once; see the design doc for the per-unit figures)."""
+    """Algorithmic DRAM bytes of each stage for one step: each input read once and each
+    output written once, from the per-unit figures below (bytes per Gaussian, visible
+    record, tile instance, pixel, region and candidate)."""
     gbytes = 16 * (3 + sh_planes)  # one Gaussian's parameters (float4 planes)
     return {
         "project": n * gbytes + n * (3 * 16 + 16 + 4),
