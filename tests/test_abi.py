@@ -94,3 +94,34 @@ def test_workspace_queries_and_argument_errors(abi):
     p2 = abi.default_params()
     rc = L.adp_project(C.byref(g), cams, 0, C.byref(p2), C.byref(out), None)
     assert rc == 1 and b"n_views" in L.adp_last_error_string()
+
+
+def test_overlapped_split_rejects_bad_arguments_before_any_launch(abi):
+    """The overlapped plan and both compaction calls validate on the host first (no
+    device, no auxiliary stream is touched): missing arrays, candidates without
+    their status arrays, and an unaligned workspace."""
+    L = abi.lib()
+    cams = abi.cameras([{"width": 64, "height": 32, "fx": 50, "fy": 50, "px": 31.5, "py": 15.5,
+                         "R": [1, 0, 0, 0, 1, 0, 0, 0, 1], "t": [0, 0, 0]}])
+    p = abi.default_params()
+    g = abi.AdpGaussians(0, 0, 0, None, None, None, None)
+    regs = abi.AdpRegions()
+    rc = L.adp_split_plan_overlapped(C.byref(g), cams, 1, C.byref(regs), None, 0, None,
+                                     C.byref(p), None, None, None, None, 0, None)
+    assert rc == 1 and b"NULL" in L.adp_last_error_string()
+    lr = (C.c_float * 6)(*([1e-3] * 6))
+    for name in ("adp_split_keep_overlapped", "adp_split_append_overlapped"):
+        fn = getattr(L, name)
+        rc = fn(C.byref(g), C.byref(g), C.byref(g), C.byref(g), C.byref(regs), None, 5, None,
+                None, None, C.byref(p), 1, None, lr, 0.9, 0.999, 1e-15, None, None, None,
+                None, 0, None)
+        assert rc == 1, name
+    ws = C.create_string_buffer(4096)
+    unaligned = C.c_void_p(((C.addressof(ws) + 255) & ~255) + 8)  # 8 past a 256-byte boundary
+    cnt = C.c_int64(0)
+    regs2 = abi.AdpRegions()
+    regs2.count = C.cast(C.pointer(cnt), C.c_void_p)
+    rc = L.adp_split_plan_overlapped(C.byref(g), cams, 1, C.byref(regs2), None, 0,
+                                     C.cast(C.pointer(cnt), C.c_void_p), C.byref(p), None, None,
+                                     C.cast(C.pointer(cnt), C.c_void_p), unaligned, 4000, None)
+    assert rc == 1 and b"aligned" in L.adp_last_error_string()
