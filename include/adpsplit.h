@@ -13,7 +13,10 @@
  *    be 16-byte aligned, workspaces 256-byte aligned.
  *  - Every call is asynchronous on the given stream (a cudaStream_t; NULL is the
  *    legacy default stream) and does not synchronise, except adp_split_plan,
- *    which reads one integer back when asked to (see there).
+ *    which reads one integer back when asked to (see there). The overlapped
+ *    split (adp_split_plan_overlapped and its two compaction calls) also puts
+ *    work on a stream the library keeps per device, forked from and joined back
+ *    into the given stream (see there).
  *  - Every call returns an adp_status. A host-side argument error returns
  *    ADP_ERR_INVALID_ARG before anything is launched; a CUDA launch error returns
  *    ADP_ERR_CUDA. adp_last_error_string() describes the last failure of the
