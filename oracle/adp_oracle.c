@@ -62,8 +62,13 @@ typedef struct orc_config {
   double alpha_min;  /* a Gaussian contributes iff o*exp(power) >= alpha_min */
   double alpha_max;  /* alpha is clamped to alpha_max */
   double t_min;      /* stop before blending when T*(1-alpha) < t_min */
-  double tie_rel;    /* relative band around a threshold flagged as a tie */
-  double tie_margin; /* dominant-weight margin flagged as a tie */
+  /* Tie bands (absolute). A pixel is a tie when, among the Gaussians it tests,
+   * some alpha_raw lies within tie_alpha_min of alpha_min (bit 1) or within
+   * tie_alpha_max of alpha_max (bit 4), some stop test T (1 - alpha) lies within
+   * tie_stop of t_min (bit 2), or the two largest weights T alpha differ by less
+   * than tie_margin (bit 8). Misses with alpha_raw >= alpha_min - tie_capture are
+   * kept (not blended) so that their distance to alpha_min is reported. */
+  double tie_alpha_min, tie_stop, tie_alpha_max, tie_margin, tie_capture;
   int32_t tile_w, tile_h;
 } orc_config;
 
@@ -369,7 +374,7 @@ ORC_API void orc_project(int64_t n, int32_t deg, const double* theta, const orc_
 typedef struct {
   double depth;
   int32_t id;
-  int32_t include; /* 1: alpha_raw >= alpha_min; 0: a near-threshold miss kept for tie flags */
+  int32_t include; /* 1: alpha_raw >= alpha_min; 0: a near-threshold miss kept for its distance */
   double alpha_raw;
 } contrib_t;
 
@@ -397,7 +402,7 @@ static double alpha_raw_at(const proj_view_t* pv, int64_t i, int x, int y) {
 }
 
 /* Adds Gaussian i to the pixel's list if it contributes, or records a near
- * miss (within tie_rel of alpha_min) so the tie flag can see it. */
+ * miss (within tie_capture below alpha_min) so its distance can be reported. */
 static void consider(const proj_view_t* pv, const orc_config* cfg, int64_t i, int x, int y,
                      contrib_t* list, int* cnt) {
   if (pv->tiles[i] <= 0) return;
@@ -406,7 +411,7 @@ static void consider(const proj_view_t* pv, const orc_config* cfg, int64_t i, in
   double a = alpha_raw_at(pv, i, x, y);
   if (a < 0.0) return;
   int inc = a >= cfg->alpha_min;
-  if (!inc && fabs(a / cfg->alpha_min - 1.0) >= cfg->tie_rel) return;
+  if (!inc && a < cfg->alpha_min - cfg->tie_capture) return;
   contrib_t c = {pv->depth[i], (int32_t)i, inc, a};
   list[(*cnt)++] = c;
 }
@@ -418,26 +423,29 @@ typedef struct {
   int32_t dominant;
   int32_t second;
   double margin;
+  double dist[4]; /* distances to alpha_min, t_min, alpha_max; the margin */
   int32_t tie;
 } pixel_out_t;
 
 /* Front-to-back compositing of the depth-sorted list (Eq. 1): alpha =
  * min(alpha_max, alpha_raw); stop before blending a Gaussian once
  * T (1 - alpha) < t_min. The dominant Gaussian maximises T alpha (Eq. 5); a
- * strict comparison keeps the earliest on ties. Tie bits: 1 alpha threshold,
- * 2 stop threshold, 4 alpha clamp, 8 dominant margin. */
+ * strict comparison keeps the earliest on ties. The distances cover every
+ * Gaussian tested up to and including the one that stops the pixel. Tie bits: 1
+ * alpha threshold, 2 stop threshold, 4 alpha clamp, 8 dominant margin. */
 static void composite(const proj_view_t* pv, const orc_config* cfg, const double* bg,
                       const contrib_t* list, int cnt, pixel_out_t* po) {
   double T = 1.0, col[3] = {0, 0, 0}, best = -1.0, second = -1.0;
   int dom = -1, sec = -1, n = 0, tie = 0;
+  double d_amin = 1e300, d_stop = 1e300, d_amax = 1e300;
   for (int k = 0; k < cnt; ++k) {
     double a_raw = list[k].alpha_raw;
-    if (fabs(a_raw / cfg->alpha_min - 1.0) < cfg->tie_rel) tie |= 1;
+    d_amin = fmin(d_amin, fabs(a_raw - cfg->alpha_min));
     if (!list[k].include) continue;
-    if (fabs(a_raw / cfg->alpha_max - 1.0) < cfg->tie_rel) tie |= 4;
+    d_amax = fmin(d_amax, fabs(a_raw - cfg->alpha_max));
     double a = a_raw < cfg->alpha_max ? a_raw : cfg->alpha_max;
     double test = T * (1.0 - a);
-    if (fabs(test / cfg->t_min - 1.0) < cfg->tie_rel) tie |= 2;
+    d_stop = fmin(d_stop, fabs(test - cfg->t_min));
     if (test < cfg->t_min) break;
     double w = T * a;
     const double* c = pv->rgb + 3 * (int64_t)list[k].id;
@@ -456,19 +464,27 @@ static void composite(const proj_view_t* pv, const orc_config* cfg, const double
   po->dominant = dom;
   po->second = sec;
   po->margin = (dom >= 0 && sec >= 0) ? best - second : 1e300;
-  if (dom >= 0 && sec >= 0 && po->margin < cfg->tie_margin) tie |= 8;
+  if (d_amin < cfg->tie_alpha_min) tie |= 1;
+  if (d_stop < cfg->tie_stop) tie |= 2;
+  if (d_amax < cfg->tie_alpha_max) tie |= 4;
+  if (po->margin < cfg->tie_margin) tie |= 8;
+  po->dist[0] = d_amin;
+  po->dist[1] = d_stop;
+  po->dist[2] = d_amax;
+  po->dist[3] = po->margin;
   po->tie = tie;
 }
 
 static void store_pixel(const pixel_out_t* po, int64_t j, double* out_rgb, double* out_T,
                         int32_t* out_n, int32_t* out_dom, int32_t* out_second,
-                        double* out_margin, int32_t* out_tie) {
+                        double* out_dist, int32_t* out_tie) {
   for (int ch = 0; ch < 3; ++ch) out_rgb[3 * j + ch] = po->rgb[ch];
   out_T[j] = po->T;
   out_n[j] = po->n_contrib;
   out_dom[j] = po->dominant;
   if (out_second) out_second[j] = po->second;
-  if (out_margin) out_margin[j] = po->margin;
+  if (out_dist)
+    for (int e = 0; e < 4; ++e) out_dist[4 * j + e] = po->dist[e];
   if (out_tie) out_tie[j] = po->tie;
 }
 
@@ -483,7 +499,7 @@ ORC_API void orc_render(int64_t n, const double* mean2d, const double* conic, co
                         const int32_t* tiles, int32_t W, int32_t H, const double* bg,
                         const orc_config* cfg, int64_t n_pix, const int64_t* pix,
                         double* out_rgb, double* out_T, int32_t* out_n, int32_t* out_dom,
-                        int32_t* out_second, double* out_margin, int32_t* out_tie) {
+                        int32_t* out_second, double* out_dist, int32_t* out_tie) {
   proj_view_t pv = {mean2d, conic, depth, opacity, rgb, box, tiles};
   if (pix) {
 #pragma omp parallel
@@ -497,7 +513,7 @@ ORC_API void orc_render(int64_t n, const double* mean2d, const double* conic, co
         qsort(list, (size_t)cnt, sizeof(contrib_t), contrib_cmp);
         pixel_out_t po;
         composite(&pv, cfg, bg, list, cnt, &po);
-        store_pixel(&po, j, out_rgb, out_T, out_n, out_dom, out_second, out_margin, out_tie);
+        store_pixel(&po, j, out_rgb, out_T, out_n, out_dom, out_second, out_dist, out_tie);
       }
       free(list);
     }
@@ -539,7 +555,7 @@ ORC_API void orc_render(int64_t n, const double* mean2d, const double* conic, co
       qsort(list, (size_t)cnt, sizeof(contrib_t), contrib_cmp);
       pixel_out_t po;
       composite(&pv, cfg, bg, list, cnt, &po);
-      store_pixel(&po, j, out_rgb, out_T, out_n, out_dom, out_second, out_margin, out_tie);
+      store_pixel(&po, j, out_rgb, out_T, out_n, out_dom, out_second, out_dist, out_tie);
     }
     free(list);
   }

@@ -56,8 +56,9 @@ class OrcCamera(C.Structure):
 class OrcConfig(C.Structure):
     _fields_ = [("near_plane", C.c_double), ("low_pass", C.c_double),
                 ("alpha_min", C.c_double), ("alpha_max", C.c_double), ("t_min", C.c_double),
-                ("tie_rel", C.c_double), ("tie_margin", C.c_double), ("tile_w", C.c_int32),
-                ("tile_h", C.c_int32)]
+                ("tie_alpha_min", C.c_double), ("tie_stop", C.c_double),
+                ("tie_alpha_max", C.c_double), ("tie_margin", C.c_double),
+                ("tie_capture", C.c_double), ("tile_w", C.c_int32), ("tile_h", C.c_int32)]
 
 
 class OrcSplitConfig(C.Structure):
@@ -158,20 +159,40 @@ def camera(cam) -> OrcCamera:
 
 @dataclass
 class Config:
-    """Forward conventions (3DGS defaults) and tie bands."""
+    """Forward conventions (3DGS defaults) and tie bands.
+
+    A pixel is a tie when one of the discontinuous decisions of its compositing is
+    within an absolute band of its threshold: some alpha_raw within tie_alpha_min of
+    1/255 (bit 1), some stop test T (1 - alpha) within tie_stop of 1e-4 (bit 2),
+    some alpha_raw within tie_alpha_max of the 0.99 clamp (bit 4), or the two
+    largest weights T alpha closer than tie_margin (bit 8). The defaults are the
+    stated tolerance's 1e-6 for every band. render() also returns each pixel's
+    distances to the four thresholds, so a caller can apply other bands."""
     near_plane: float = 0.2
     low_pass: float = 0.3
     alpha_min: float = 1.0 / 255.0
     alpha_max: float = 0.99
     t_min: float = 1e-4
-    tie_rel: float = 1e-4
-    tie_margin: float = 1e-5
+    tie_alpha_min: float = 1e-6
+    tie_stop: float = 1e-6
+    tie_alpha_max: float = 1e-6
+    tie_margin: float = 1e-6
+    tie_capture: float = 1e-4  # misses this close below 1/255 report their distance
     tile_w: int = 16
     tile_h: int = 16
 
     def c(self) -> OrcConfig:
         return OrcConfig(self.near_plane, self.low_pass, self.alpha_min, self.alpha_max,
-                         self.t_min, self.tie_rel, self.tie_margin, self.tile_w, self.tile_h)
+                         self.t_min, self.tie_alpha_min, self.tie_stop, self.tie_alpha_max,
+                         self.tie_margin, self.tie_capture, self.tile_w, self.tile_h)
+
+
+def tie_bits(dist, alpha_min=1e-6, stop=1e-6, alpha_max=1e-6, margin=1e-6):
+    """Tie bits (as render() sets them) of per-pixel threshold distances [P, 4]
+    under the given absolute bands."""
+    d = np.asarray(dist)
+    return ((d[:, 0] < alpha_min) * 1 + (d[:, 1] < stop) * 2 + (d[:, 2] < alpha_max) * 4 +
+            (d[:, 3] < margin) * 8).astype(np.int32)
 
 
 @dataclass
@@ -251,13 +272,14 @@ def render(proj, cam, bg=(0.0, 0.0, 0.0), cfg: Config = Config(), pixels=None):
     bg = _c(bg, np.float64)
     out = dict(rgb=np.zeros((npix, 3)), T=np.zeros(npix), n_contrib=np.zeros(npix, np.int32),
                dominant=np.zeros(npix, np.int32), second=np.zeros(npix, np.int32),
-               margin=np.zeros(npix), tie=np.zeros(npix, np.int32))
+               dist=np.zeros((npix, 4)), tie=np.zeros(npix, np.int32))
     cf = cfg.c()
     lib().orc_render(n, _p(proj["mean2d"]), _p(proj["conic"]), _p(proj["depth"]),
                      _p(proj["opacity"]), _p(proj["rgb"]), _p(proj["box"]), _p(proj["tiles"]),
                      W, H, _p(bg), C.byref(cf), npix, _p(pix), _p(out["rgb"]), _p(out["T"]),
                      _p(out["n_contrib"]), _p(out["dominant"]), _p(out["second"]),
-                     _p(out["margin"]), _p(out["tie"]))
+                     _p(out["dist"]), _p(out["tie"]))
+    out["margin"] = out["dist"][:, 3].copy()
     return out
 
 

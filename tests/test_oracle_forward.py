@@ -231,6 +231,18 @@ def test_single_splat_analytic_footprint(orc):
     np.testing.assert_allclose(rd["rgb"], a[:, None] * pr["rgb"][0][None, :], rtol=1e-13, atol=1e-15)
     np.testing.assert_allclose(rd["T"], 1 - a, rtol=1e-13)
     assert np.all(rd["dominant"][a > 0] == 0) and np.all(rd["dominant"][a == 0] == -1)
+    # distance to the 1/255 cut-off: |alpha_raw - 1/255| where the pixel tests the
+    # Gaussian (contributes, or misses by at most the capture window), else none
+    cfg = orc.Config(tie_capture=3e-3)
+    rw = orc.render(pr, cam, cfg=cfg)
+    ar = (pr["opacity"][0] * np.exp(-0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy)).reshape(-1)
+    box = pr["box"][0]
+    inbox = ((xx >= box[0]) & (xx <= box[1]) & (yy >= box[2]) & (yy <= box[3])).reshape(-1)
+    tested = inbox & (ar >= 1 / 255 - cfg.tie_capture)
+    assert tested.sum() > a.astype(bool).sum()  # some near misses are reported
+    np.testing.assert_allclose(rw["dist"][tested, 0], np.abs(ar[tested] - 1 / 255), rtol=1e-12)
+    assert np.all(rw["dist"][~tested, 0] > 1e299)
+    assert np.array_equal(rw["rgb"], rd["rgb"])  # near misses are never blended
 
 
 def _stack(opacities, dcs, w=33, h=33):
@@ -260,6 +272,44 @@ def test_three_splat_transmittance_product(orc):
     # weights w = (0.3, 0.35, 0.245): the second Gaussian dominates (Eq. 5)
     assert rd["dominant"][0] == 1 and rd["second"][0] == 0
     assert rd["n_contrib"][0] == 3
+
+
+def test_threshold_distances_of_a_stack(orc):
+    """The distances behind the tie flags, by hand at the centre pixel of the
+    three-splat stack (alpha_i = opacity_i exactly): to 1/255 the smallest
+    |alpha - 1/255|, to the stop threshold the smallest |T (1 - alpha) - 1e-4| over
+    the three stop tests, to the clamp the smallest |alpha - 0.99|, and the margin
+    w_best - w_second of the weights (0.3, 0.35, 0.245)."""
+    sc, cam = _stack([0.3, 0.5, 0.7], [(1.0, 0.0, 0.0)] * 3)
+    pr = orc.project(orc.theta_of(sc), 0, cam)
+    a = pr["opacity"]
+    rd = orc.render(pr, cam, pixels=[16 * 33 + 16])
+    tests = [1 - a[0], (1 - a[0]) * (1 - a[1]), (1 - a[0]) * (1 - a[1]) * (1 - a[2])]
+    w = sorted([a[0], (1 - a[0]) * a[1], (1 - a[0]) * (1 - a[1]) * a[2]])
+    want = [min(abs(x - 1 / 255) for x in a), min(abs(t - 1e-4) for t in tests),
+            min(abs(x - 0.99) for x in a), w[-1] - w[-2]]
+    np.testing.assert_allclose(rd["dist"][0], want, rtol=1e-12)
+    assert rd["tie"][0] == 0
+    # bands wider than a distance set that distance's bit
+    wide = orc.render(pr, cam, pixels=[16 * 33 + 16],
+                      cfg=orc.Config(tie_stop=0.2, tie_margin=0.06))
+    assert wide["tie"][0] == 2 | 8
+    assert np.array_equal(orc.tie_bits(rd["dist"], stop=0.2, margin=0.06), wide["tie"])
+
+
+def test_stop_distance_covers_the_stopping_test(orc):
+    """alpha = 0.95 five times: the stop tests are 0.05, 0.0025, 1.25e-4 and the
+    failing 6.25e-6; the nearest to 1e-4 is 1.25e-4 (distance 2.5e-5), and no test
+    after the stop counts."""
+    sc, cam = _stack([0.95] * 5, [(1.0, 1.0, 1.0)] * 5)
+    pr = orc.project(orc.theta_of(sc), 0, cam)
+    a = pr["opacity"][0]
+    rd = orc.render(pr, cam, pixels=[16 * 33 + 16])
+    tests = [(1 - a) ** k for k in (1, 2, 3, 4)]
+    np.testing.assert_allclose(rd["dist"][0, 1], min(abs(t - 1e-4) for t in tests), rtol=1e-12)
+    assert rd["tie"][0] == 0
+    near = orc.render(pr, cam, pixels=[16 * 33 + 16], cfg=orc.Config(tie_stop=3e-5))
+    assert near["tie"][0] == 2
 
 
 def test_early_stop_before_blending(orc):
