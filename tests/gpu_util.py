@@ -51,3 +51,31 @@ def small_cluster_inputs(n=20000, W=320, H=208, views=1, seed=10):
     sc = scenes.scene_clusters(seed, n, 3)
     cams = scenes.ring_cameras(seed + 1, views, 4.0, W, H)
     return sc, cams
+
+
+COLOUR_TOL = 2e-4
+
+
+def compare_render(rgb, T, n_contrib, dominant, o, label=""):
+    """Per-pixel parity of a GPU render with the oracle's (o = oracle.render with
+    its default, absolute 1e-6 tie bands): colour within COLOUR_TOL, T within 1e-4,
+    the contributor count and the dominant id exact, except at tie pixels. Every
+    disagreement must lie at a tie (a contributor's alpha or stop test within the
+    band of its threshold, or, for the dominant id alone, a weight margin within
+    the band, where the GPU's id must be the oracle's first or second). The pixels
+    excused that way must be at most 1e-4 of the pixels. Returns (tie fraction,
+    excused pixels, pixels), also printed."""
+    tie = o["tie"] != 0
+    P = len(tie)
+    err = np.abs(np.asarray(rgb, np.float64) - o["rgb"]).max(1)
+    bad = (err > COLOUR_TOL) | (np.abs(T - o["T"]) > 1e-4) | (n_contrib != o["n_contrib"])
+    dbad = dominant != o["dominant"]
+    dtie = (o["tie"] & 8) != 0
+    assert not np.any(bad & ~tie), (label, "colour/T/count outside ties", np.nonzero(bad & ~tie)[0][:10],
+                                   err[bad & ~tie][:10])
+    ok_dom = ~dbad | (tie & ~dtie) | (dtie & (dominant == o["second"]))
+    assert np.all(ok_dom), (label, "dominant outside ties", np.nonzero(~ok_dom)[0][:10])
+    excused = int((bad | dbad).sum())
+    print(f"[parity] {label}: {P} pixels, tie fraction {tie.mean():.3g}, excused {excused}")
+    assert excused <= int(1e-4 * P), (label, "excused pixels", excused, P)
+    return float(tie.mean()), excused, P

@@ -1,9 +1,11 @@
 """GPU parity of projection, binning and compositing against the FP64 oracle.
 
-Tolerances: colour max-abs <= 2e-4 on [0, 1] outside tie pixels (pixels where a
-contributor's alpha, the stop test or the dominant margin lies within the tie band
-the oracle reports); integer work (tile lists, ranges) bit-exact given identical
-keys; the dominant id equal outside ties and one of the two best candidates at ties.
+Tolerances: colour max-abs <= 2e-4 on [0, 1], T within 1e-4, contributor counts
+exact, except at tie pixels (a contributor's alpha within 1e-6 of 1/255 or of the
+0.99 clamp, or a stop test within 1e-6 of 1e-4; for the dominant id also a weight
+margin below 1e-6, where it must be one of the two best); every disagreement must
+be at a tie and the excused pixels at most 1e-4 of the pixels. Integer work (tile
+lists, ranges) bit-exact given identical keys.
 """
 import numpy as np
 import pytest
@@ -11,27 +13,16 @@ import torch
 
 import oracle as O
 import scenes
-from gpu_util import DEV, c0_inputs, gpu_forward, np_, oracle_projected_to_gpu, small_cluster_inputs
+from gpu_util import (DEV, c0_inputs, compare_render, gpu_forward, np_, oracle_projected_to_gpu,
+                      small_cluster_inputs)
 from paper_2605_06876_b300 import _abi, ops
 
 pytestmark = pytest.mark.gpu
 
-COLOUR_TOL = 2e-4
 
-
-def _compare_render(img, ord_, max_tie_frac=2e-3):
-    tie = ord_["tie"] != 0
-    assert tie.mean() <= max_tie_frac, f"tie fraction {tie.mean()}"
-    rgb = np_(img.rgb).astype(np.float64)
-    err = np.abs(rgb - ord_["rgb"]).max(1)
-    assert err[~tie].max() <= COLOUR_TOL, err[~tie].max()
-    np.testing.assert_allclose(np_(img.T)[~tie], ord_["T"][~tie], atol=1e-4)
-    dom = np_(img.dominant)
-    dtie = (ord_["tie"] & 8) != 0
-    ok = (dom == ord_["dominant"]) | (dtie & (dom == ord_["second"]))
-    assert np.all(ok[~(tie & ~dtie)]), np.nonzero(~ok)[0][:10]
-    nc = np_(img.n_contrib)
-    assert np.array_equal(nc[~tie], ord_["n_contrib"][~tie])
+def _compare_render(img, ord_, label):
+    return compare_render(np_(img.rgb), np_(img.T), np_(img.n_contrib), np_(img.dominant), ord_,
+                          label)
 
 
 def test_project_matches_oracle():
@@ -136,7 +127,7 @@ def test_render_c0_matches_oracle():
     sc, cam, _ = c0_inputs()
     g, pr, bins, img = gpu_forward(sc, [cam])
     o = O.render(O.project(O.theta_of(sc), 0, cam), cam)
-    _compare_render(img, o)
+    _compare_render(img, o, "tiny workload 128x128")
 
 
 def test_render_stage_isolated_and_background():
@@ -155,7 +146,7 @@ def test_render_stage_isolated_and_background():
     # the oracle composites the same float32-rounded records in FP64
     orp32 = {k: (v.astype(np.float32).astype(np.float64) if v.dtype == np.float64 else v)
              for k, v in orp.items()}
-    _compare_render(img, O.render(orp32, cam, bg=bg))
+    _compare_render(img, O.render(orp32, cam, bg=bg), "20k Gaussians 320x208, oracle records")
 
 
 @pytest.mark.parametrize("shape", [(8, 32), (32, 8)])
@@ -186,15 +177,15 @@ def test_batched_views_equal_views_alone():
 
 
 def test_full_size_sampled_pixels():
-    """1M Gaussians at 1280x832 (the single-view workload): sampled pixels agree
-    with the oracle's brute-force per-pixel compositing over all Gaussians."""
+    """1M Gaussians at 1280x832 (the single-view workload): 400 sampled pixels
+    agree with the oracle's brute-force per-pixel compositing over all Gaussians."""
     cfg = scenes.CONFIGS[1]
     sc = scenes.scene_clusters(2, cfg["n"], cfg["sh_degree"])
     cam = scenes.ring_cameras(3, 1, cfg["ring_radius"], cfg["width"], cfg["height"])[0]
     g, pr, bins, img = gpu_forward(sc, [cam])
     rng = np.random.default_rng(0)
-    pix = rng.choice(cfg["width"] * cfg["height"], 160, replace=False)
+    pix = rng.choice(cfg["width"] * cfg["height"], 400, replace=False)
     o = O.render(O.project(O.theta_of(sc), 3, cam), cam, pixels=pix)
     sub = ops.Image(*(t[torch.as_tensor(pix, device=DEV)] for t in
                       (img.rgb, img.T, img.n_contrib, img.last, img.dominant)))
-    _compare_render(sub, o, max_tie_frac=0.05)
+    _compare_render(sub, o, "1M Gaussians 1280x832, sampled")
