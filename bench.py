@@ -174,7 +174,9 @@ def stage_bytes(n, n_vis, K, P, n_tiles, sh_planes, regions, k, kept, appended):
         "bin_sort": n * 8 + n_vis * 8 * 2 * 4 + K * (8 + 2 * 16) + n_tiles * 8,
         "render": n_tiles * 8 + K * 4 + n_vis * 48 + P * 28,
         "error_stats": P * (12 + 12 + 4 + 4 + 4 + 1) + n * 12,
-        "select_topk": n * 8 * 8 + n * 8 * 2 + k * 4,
+        # the keys read once and the ids written: the radix select's extra passes over
+        # the keys still in play are the kernel's own cost, not algorithmic bytes
+        "select_topk": n * 8 + k * 4,
         "error_regions": P * (1 + 4 + 1 + 4 + 4 + 4 + 4) + regions * 160,
         # the gradient has a row mask: parameters read and gradients written for the
         # rendered Gaussians only, plus the mask byte and the tile counts of all
@@ -348,6 +350,7 @@ def run_ours(args, rank, world, local_rank):
                     "unit": "TFLOP/s", "frac": round(f / (per_stage[k] * 1e-3) / 1e12 / alu_peak, 4),
                     "flops": int(f)} for k, f in flops.items() if k in per_stage}
     roof_alu["peak_source"] = f"{sm_count} SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz"
+    step_bytes = sum(v for k, v in sb.items() if k in per_stage)
     launches = None if args.no_launch_count else count_launches(stepper, noise) * args.steps
     dssim = dssim_kernels(stepper.img.rgb, target, cams, flush, dev)
     eq2 = None
@@ -376,8 +379,11 @@ def run_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "roofline": roof,
         "roofline_alu": roof_alu,
-        "step_hbm": {"algorithmic_bytes": int(sum(sb.values())),
-                     "frac": round(sum(sb.values()) / (ms_per_step * 1e-3) / 1e9 / peak, 4)},
+        # the stages this step ran (the unfused "adam" entry of stage_bytes only
+        # applies to a step without the fused compaction)
+        "step_hbm": {"algorithmic_bytes": int(step_bytes),
+                     "frac": round(step_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4),
+                     "stages": sorted(k for k in sb if k in per_stage)},
         "graph": use_graph,
         "stages_ms": {k: round(v, 4) for k, v in per_stage.items()},
         "batched_vs_plain": batched,

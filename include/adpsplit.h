@@ -25,8 +25,21 @@
  *    capacity the caller gave) are reported through device counters that hold
  *    the REQUIRED size; the caller compares them with its capacity after a sync
  *    and calls again with more room. Kernels never write past a capacity.
+ *  - Device status word. The calls whose kernels wait on other blocks (the
+ *    look-back of their prefix sums, the grid barrier of the top-k) take an
+ *    int32_t* d_status (device, may be NULL). Every such wait is bounded (see
+ *    adp_set_spin_limit); one that runs out sets *d_status to ADP_ERR_TIMEOUT if
+ *    it is still ADP_OK (0), and the kernel returns normally, so the context
+ *    stays usable. The call's outputs are then undefined, and the calls that
+ *    write through the affected prefix sums write nothing past their
+ *    capacities. The word is never cleared by the library: the caller zeroes it,
+ *    passes it to the calls of a step and reads it at the step's sync point.
  *  - Up to ADP_MAX_VIEWS views per call. Camera structs are HOST memory and are
  *    passed to the kernels by value.
+ *  - The library caches per device, for the life of the process, the auxiliary
+ *    stream of the overlapped split and the device address of the static top-k
+ *    scratch. Both belong to the device's primary context, so the library must
+ *    not be used on a device after cudaDeviceReset on it.
  *
  * Notation follows the paper (AdpSplit, Secs. 3-4 and Appendix A).
  */
@@ -42,7 +55,7 @@ extern "C" {
 
 #define ADP_API __attribute__((visibility("default")))
 #define ADP_MAX_VIEWS 32
-#define ADP_VERSION 1
+#define ADP_VERSION 2
 
 typedef void* adp_stream_t; /* cudaStream_t */
 
@@ -51,7 +64,7 @@ typedef enum adp_status {
   ADP_ERR_INVALID_ARG = 1, /* bad sizes, NULL pointers, misalignment, small workspace */
   ADP_ERR_CAPACITY = 2,    /* a caller-given capacity is too small (host-detected) */
   ADP_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
-  ADP_ERR_TIMEOUT = 4,     /* reserved: a bounded device wait gave up */
+  ADP_ERR_TIMEOUT = 4,     /* a bounded device wait gave up (reported in a status word) */
   ADP_ERR_NUMERIC = 5      /* reserved: non-finite input detected */
 } adp_status;
 
@@ -94,6 +107,8 @@ typedef struct adp_params {
   float t_min;       /* stop before blending when T (1 - alpha) < t_min */
   int32_t tile_w;    /* tile width in pixels; tile_w * tile_h must be 256 */
   int32_t tile_h;
+  int32_t batch;     /* Gaussians a compositing block stages per batch: 64, 128 or 256
+                        (0 = 256); changes no result, only the speed */
 } adp_params;
 
 /* Gaussian parameters (also the layout of gradients and Adam moments), SoA of
@@ -180,6 +195,35 @@ ADP_API int32_t adp_version(void);
 ADP_API void adp_default_params(adp_params* p);
 ADP_API const char* adp_last_error_string(void);
 
+/* Constants fixed inside the library (host query, no device needed): limits,
+ * the conventions the paper leaves open that the kernels hard-code, and the
+ * default parameters. */
+typedef struct adp_constants {
+  int32_t version;           /* ADP_VERSION */
+  int32_t max_views;         /* ADP_MAX_VIEWS */
+  int32_t tile_pixels;       /* pixels of a tile (tile_w * tile_h) */
+  int32_t max_sh_degree;     /* 3 */
+  float fov_clamp;           /* x/z and y/z of the EWA Jacobian are clamped to
+                                fov_clamp * (image side / 2) / focal length */
+  float sh_coef[16];         /* real SH basis: Y_k(d) = sh_coef[k] * m_k(d) with the
+                                monomials m = 1, y, z, x, xy, yz, 2z^2-x^2-y^2, xz,
+                                x^2-y^2, y(3x^2-y^2), xyz, y(4z^2-x^2-y^2),
+                                z(2z^2-3x^2-3y^2), x(4z^2-x^2-y^2), z(x^2-y^2),
+                                x(x^2-3y^2) (3DGS sign convention) */
+  double gram_schmidt_eps;   /* residual below which Appendix A's in-plane axis
+                                falls back to z x u1 */
+  int64_t topk_noalloc_max_n;  /* ADP_TOPK_NOALLOC_MAX_N */
+  int64_t default_spin_limit;  /* poll bound of device waits by default */
+  adp_params defaults;       /* adp_default_params() */
+} adp_constants;
+ADP_API void adp_get_constants(adp_constants* c);
+
+/* Bound on the polls of every device wait launched after the call, process
+ * wide (max_polls <= 0 restores the default, about a second of polling). A
+ * small bound makes waits give up and report ADP_ERR_TIMEOUT (a test of the
+ * failure path); results of calls that timed out are undefined. */
+ADP_API void adp_set_spin_limit(int64_t max_polls);
+
 /* --- Projection (Sec. 3, Eq. 1). ------------------------------------------
  * EWA splatting of every Gaussian into every view: camera transform, 3D
  * covariance R S S^T R^T, Sigma2D = J W Sigma W^T J^T + low_pass I with x/z and
@@ -204,7 +248,7 @@ ADP_API int adp_project(const adp_gaussians* g, const adp_camera* cams, int32_t 
 ADP_API size_t adp_bin_sort_workspace_size(int64_t n, int32_t n_views, int64_t capacity);
 ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const adp_camera* cams,
                          int32_t n_views, const adp_params* prm, adp_bins* bins, void* ws,
-                         size_t ws_bytes, adp_stream_t stream);
+                         size_t ws_bytes, int32_t* d_status, adp_stream_t stream);
 
 /* --- Compositing (Eq. 1) and dominant map (Eq. 5). --------------------------
  * Per pixel, front to back over its tile's list: alpha = min(alpha_max,
@@ -227,10 +271,11 @@ ADP_API int adp_error_stats(const float* img, const float* target, const int32_t
                             double* mass, adp_stream_t stream);
 
 /* The k Gaussians with the largest mass (ties to the lower id), written to
- * out_ids in ascending id order. */
+ * out_ids in ascending id order. If a grid-barrier wait runs out (d_status),
+ * every entry is a distinct id or -1. */
 ADP_API size_t adp_select_topk_workspace_size(int64_t n);
 ADP_API int adp_select_topk(const double* mass, int64_t n, int64_t k, int32_t* out_ids,
-                            void* ws, size_t ws_bytes, adp_stream_t stream);
+                            void* ws, size_t ws_bytes, int32_t* d_status, adp_stream_t stream);
 
 /* The same selection for callers that cannot allocate device memory where they
  * run (no cudaMalloc, no caller workspace): for example code running inside a
@@ -249,7 +294,7 @@ ADP_API int adp_select_topk(const double* mass, int64_t n, int64_t k, int32_t* o
  * caller. Results are identical to adp_select_topk's. */
 #define ADP_TOPK_NOALLOC_MAX_N (1LL << 22)
 ADP_API int adp_select_topk_noalloc(const double* mass, int64_t n, int64_t k, int32_t* out_ids,
-                                    adp_stream_t stream);
+                                    int32_t* d_status, adp_stream_t stream);
 
 /* Error regions (Eqs. 7-8): erode M by the (2 r_erode + 1)^2 square (pixels
  * outside the image count as set), then join 8-neighbours whose eroded M is set,
@@ -260,7 +305,8 @@ ADP_API size_t adp_error_regions_workspace_size(int64_t n, int32_t n_views, cons
 ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* dominant, const float* target,
                               int64_t n, const adp_camera* cams, int32_t n_views,
                               const int32_t* candidates, int64_t n_cand, const adp_params* prm,
-                              adp_regions* out, void* ws, size_t ws_bytes, adp_stream_t stream);
+                              adp_regions* out, void* ws, size_t ws_bytes, int32_t* d_status,
+                              adp_stream_t stream);
 
 /* --- The AdpSplit operator (Sec. 4, Sec. 5.1, Appendix A). ------------------
  * Two phases sharing one workspace, which must not change in between.
@@ -280,13 +326,14 @@ ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* dominant, con
  * ascending id [parent copy with opacity o/(N_i + 1), children] or the two
  * vanilla children mu + R (s * noise), s / (2 eta) (Eqs. 3-4), all with zero
  * moments. noise: [n_cand][2][3] standard normal. m_in/v_in/m_out/v_out may be
- * NULL to skip the moments; m_out and v_out have out->n entries. */
+ * NULL to skip the moments; m_out and v_out have out->n entries. No output array
+ * may share a plane with an input array (ADP_ERR_INVALID_ARG). */
 ADP_API size_t adp_split_workspace_size(int64_t n, int64_t n_cand, int64_t region_capacity);
 ADP_API int adp_split_plan(const adp_gaussians* g, const adp_camera* cams, int32_t n_views,
                            const adp_regions* regs, const int32_t* candidates, int64_t n_cand,
                            const int32_t* count, const adp_params* prm, uint8_t* status,
                            int32_t* n_children, int64_t* d_new_n, int64_t* h_new_n, void* ws,
-                           size_t ws_bytes, adp_stream_t stream);
+                           size_t ws_bytes, int32_t* d_status, adp_stream_t stream);
 ADP_API int adp_split_apply(const adp_gaussians* g, const adp_gaussians* m_in,
                             const adp_gaussians* v_in, const adp_regions* regs,
                             const int32_t* candidates, int64_t n_cand, const uint8_t* status,
@@ -342,7 +389,8 @@ ADP_API int adp_split_plan_overlapped(const adp_gaussians* g, const adp_camera* 
                                       const int32_t* candidates, int64_t n_cand,
                                       const int32_t* count, const adp_params* prm,
                                       uint8_t* status, int32_t* n_children, int64_t* d_new_n,
-                                      void* ws, size_t ws_bytes, adp_stream_t stream);
+                                      void* ws, size_t ws_bytes, int32_t* d_status,
+                                      adp_stream_t stream);
 ADP_API int adp_split_keep_overlapped(
     const adp_gaussians* g, const adp_gaussians* grad, const adp_gaussians* m_in,
     const adp_gaussians* v_in, const adp_regions* regs, const int32_t* candidates, int64_t n_cand,
@@ -380,6 +428,34 @@ ADP_API int adp_render_backward(const adp_gaussians* g, const adp_projected* pr,
                                 float* grad2d_accum, int32_t* grad2d_visits, void* ws,
                                 size_t ws_bytes, adp_stream_t stream);
 
+/* --- The batched step of many views (Sec. 4.1: the V views sampled per
+ * densification step; loss and gradient unchanged, Sec. 5.1). ---------------
+ * For n_views views (up to ADP_MAX_VIEWS, uneven sizes allowed): adp_project and
+ * adp_bin_sort of all views, then ONE persistent kernel over a work queue of
+ * (view, tile) items that per tile composites the forward (Eq. 1, dominant map of
+ * Eq. 5), writes the raw L1 error |I^ - I_gt|_1 and reduces the view's min/max
+ * (Eq. 6), and walks the tile's list back to front for the gradient of the L1
+ * loss with the final transmittance and dL/dpixel still in registers; then E, M,
+ * B with the per-Gaussian count and mass (as adp_error_stats) and the
+ * per-Gaussian chain rule summed over views (as adp_render_backward). Every
+ * output equals that of adp_project, adp_bin_sort, adp_render, adp_error_stats
+ * and adp_render_backward called on the same views (bit for bit, except the
+ * gradient, whose float atomics sum in another order). Arguments are those
+ * calls': pr (n_views * n records), bins (capacity buffers; an overflow bins
+ * nothing and leaves the required size in *bins->n_instances), img and maps (all
+ * views' pixels), count and mass (n, zeroed by the call), grad (zeroed or masked
+ * rows), the optional Eq. 2 accumulators, d_status (see the conventions). The
+ * workspace size depends on n, n_views and bins->capacity. Asynchronous and
+ * capturable in a CUDA graph. */
+ADP_API size_t adp_train_step_batched_workspace_size(int64_t n, int32_t n_views, int64_t capacity);
+ADP_API int adp_train_step_batched(const adp_gaussians* g, const adp_camera* cams, int32_t n_views,
+                                   const float* target, const float* bg, const adp_params* prm,
+                                   adp_projected* pr, adp_bins* bins, adp_image* img,
+                                   adp_error_maps* maps, int32_t* count, double* mass,
+                                   adp_gaussians* grad, float* grad2d_accum,
+                                   int32_t* grad2d_visits, void* ws, size_t ws_bytes,
+                                   int32_t* d_status, adp_stream_t stream);
+
 /* --- Adaptive density control candidates (Sec. 3, Eq. 2). -------------------
  * With g_i = grad2d_accum[i] / grad2d_visits[i] (0 when never visited; one
  * correctly rounded float32 division), Gaussian i is a split candidate iff
@@ -396,7 +472,8 @@ ADP_API size_t adp_densify_select_workspace_size(int64_t n);
 ADP_API int adp_densify_select(const float* grad2d_accum, const int32_t* grad2d_visits,
                                const adp_gaussians* g, float tau_g, float tau_s,
                                int32_t* split_ids, int32_t* clone_ids, int64_t* d_counts,
-                               void* ws, size_t ws_bytes, adp_stream_t stream);
+                               void* ws, size_t ws_bytes, int32_t* d_status,
+                               adp_stream_t stream);
 /* Clone (the baselines' operation for small high-gradient Gaussians, Sec. 3):
  * called after adp_split_apply or adp_split_apply_adam with the same workspace
  * and the same n (population before the split), n_cand and region capacity. It

@@ -32,7 +32,7 @@ class AdpParams(C.Structure):
                 ("eps_t", C.c_float), ("eta", C.c_float), ("scale_floor", C.c_float),
                 ("near_plane", C.c_float), ("low_pass", C.c_float), ("alpha_min", C.c_float),
                 ("alpha_max", C.c_float), ("t_min", C.c_float), ("tile_w", _i32),
-                ("tile_h", _i32)]
+                ("tile_h", _i32), ("batch", _i32)]
 
 
 class AdpGaussians(C.Structure):
@@ -65,31 +65,41 @@ class AdpRegions(C.Structure):
                 ("labels", _vp)]
 
 
+class AdpConstants(C.Structure):
+    _fields_ = [("version", _i32), ("max_views", _i32), ("tile_pixels", _i32),
+                ("max_sh_degree", _i32), ("fov_clamp", C.c_float), ("sh_coef", C.c_float * 16),
+                ("gram_schmidt_eps", C.c_double), ("topk_noalloc_max_n", _i64),
+                ("default_spin_limit", _i64), ("defaults", AdpParams)]
+
+
 P = C.POINTER
 _PROTOS = {
     "adp_version": (_i32, []),
     "adp_default_params": (None, [P(AdpParams)]),
+    "adp_get_constants": (None, [P(AdpConstants)]),
+    "adp_set_spin_limit": (None, [_i64]),
     "adp_last_error_string": (C.c_char_p, []),
     "adp_project": (C.c_int, [P(AdpGaussians), P(AdpCamera), _i32, P(AdpParams),
                               P(AdpProjected), _vp]),
     "adp_bin_sort_workspace_size": (C.c_size_t, [_i64, _i32, _i64]),
     "adp_bin_sort": (C.c_int, [_i64, P(AdpProjected), P(AdpCamera), _i32, P(AdpParams),
-                               P(AdpBins), _vp, C.c_size_t, _vp]),
+                               P(AdpBins), _vp, C.c_size_t, _vp, _vp]),
     "adp_render": (C.c_int, [_i64, P(AdpProjected), P(AdpBins), P(AdpCamera), _i32,
                              P(C.c_float), P(AdpParams), P(AdpImage), _vp]),
     "adp_error_stats_workspace_size": (C.c_size_t, [_i32, P(AdpCamera)]),
     "adp_error_stats": (C.c_int, [_vp, _vp, _vp, _i64, P(AdpCamera), _i32, P(AdpParams),
                                   P(AdpErrorMaps), _vp, _vp, _vp]),
     "adp_select_topk_workspace_size": (C.c_size_t, [_i64]),
-    "adp_select_topk": (C.c_int, [_vp, _i64, _i64, _vp, _vp, C.c_size_t, _vp]),
-    "adp_select_topk_noalloc": (C.c_int, [_vp, _i64, _i64, _vp, _vp]),
+    "adp_select_topk": (C.c_int, [_vp, _i64, _i64, _vp, _vp, C.c_size_t, _vp, _vp]),
+    "adp_select_topk_noalloc": (C.c_int, [_vp, _i64, _i64, _vp, _vp, _vp]),
     "adp_error_regions_workspace_size": (C.c_size_t, [_i64, _i32, P(AdpCamera)]),
     "adp_error_regions": (C.c_int, [P(AdpErrorMaps), _vp, _vp, _i64, P(AdpCamera), _i32, _vp,
-                                    _i64, P(AdpParams), P(AdpRegions), _vp, C.c_size_t, _vp]),
+                                    _i64, P(AdpParams), P(AdpRegions), _vp, C.c_size_t, _vp,
+                                    _vp]),
     "adp_split_workspace_size": (C.c_size_t, [_i64, _i64, _i64]),
     "adp_split_plan": (C.c_int, [P(AdpGaussians), P(AdpCamera), _i32, P(AdpRegions), _vp, _i64,
                                  _vp, P(AdpParams), _vp, _vp, _vp, P(_i64), _vp, C.c_size_t,
-                                 _vp]),
+                                 _vp, _vp]),
     "adp_split_apply": (C.c_int, [P(AdpGaussians), P(AdpGaussians), P(AdpGaussians),
                                   P(AdpRegions), _vp, _i64, _vp, _vp, _vp, P(AdpParams),
                                   P(AdpGaussians), P(AdpGaussians), P(AdpGaussians), _vp,
@@ -101,14 +111,14 @@ _PROTOS = {
                                        P(AdpGaussians), _vp, C.c_size_t, _vp]),
     "adp_split_plan_overlapped": (C.c_int, [P(AdpGaussians), P(AdpCamera), _i32, P(AdpRegions),
                                             _vp, _i64, _vp, P(AdpParams), _vp, _vp, _vp, _vp,
-                                            C.c_size_t, _vp]),
+                                            C.c_size_t, _vp, _vp]),
     "adp_split_keep_overlapped": (C.c_int, [P(AdpGaussians), P(AdpGaussians),
                                                   P(AdpGaussians), P(AdpGaussians), P(AdpRegions),
                                                   _vp, _i64, _vp, _vp, _vp, P(AdpParams), _i32,
                                                   _vp, P(C.c_float), C.c_float, C.c_float,
                                                   C.c_float, P(AdpGaussians), P(AdpGaussians),
                                                   P(AdpGaussians), _vp, C.c_size_t, _vp]),
-        "adp_split_append_overlapped": (C.c_int, [P(AdpGaussians), P(AdpGaussians),
+    "adp_split_append_overlapped": (C.c_int, [P(AdpGaussians), P(AdpGaussians),
                                                   P(AdpGaussians), P(AdpGaussians), P(AdpRegions),
                                                   _vp, _i64, _vp, _vp, _vp, P(AdpParams), _i32,
                                                   _vp, P(C.c_float), C.c_float, C.c_float,
@@ -118,9 +128,14 @@ _PROTOS = {
     "adp_render_backward": (C.c_int, [P(AdpGaussians), P(AdpProjected), P(AdpBins), P(AdpImage),
                                       _vp, _vp, P(AdpCamera), _i32, P(C.c_float), P(AdpParams),
                                       P(AdpGaussians), _vp, _vp, _vp, C.c_size_t, _vp]),
+    "adp_train_step_batched_workspace_size": (C.c_size_t, [_i64, _i32, _i64]),
+    "adp_train_step_batched": (C.c_int, [P(AdpGaussians), P(AdpCamera), _i32, _vp, P(C.c_float),
+                                         P(AdpParams), P(AdpProjected), P(AdpBins), P(AdpImage),
+                                         P(AdpErrorMaps), _vp, _vp, P(AdpGaussians), _vp, _vp,
+                                         _vp, C.c_size_t, _vp, _vp]),
     "adp_densify_select_workspace_size": (C.c_size_t, [_i64]),
     "adp_densify_select": (C.c_int, [_vp, _vp, P(AdpGaussians), C.c_float, C.c_float, _vp, _vp,
-                                     _vp, _vp, C.c_size_t, _vp]),
+                                     _vp, _vp, C.c_size_t, _vp, _vp]),
     "adp_split_clone": (C.c_int, [_i64, _i64, _i64, _vp, _vp, _i64, P(AdpGaussians),
                                   P(AdpGaussians), P(AdpGaussians), _vp, C.c_size_t, _vp, _vp]),
     "adp_dssim_workspace_size": (C.c_size_t, [_i32, P(AdpCamera)]),
@@ -158,6 +173,13 @@ def check(rc: int, what: str):
     if rc != 0:
         msg = lib().adp_last_error_string().decode(errors="replace")
         raise RuntimeError(f"{what}: {STATUS_NAMES.get(rc, rc)}: {msg}")
+
+
+def constants() -> AdpConstants:
+    """The constants fixed inside the library (adp_get_constants)."""
+    c = AdpConstants()
+    lib().adp_get_constants(C.byref(c))
+    return c
 
 
 def default_params(**overrides) -> AdpParams:

@@ -12,7 +12,8 @@
 // moments into dL/d(mean2d, conic, opacity), chains them through the EWA
 // projection and the SH colour of every view and sums over views, so the
 // per-Gaussian parameters are read and the gradients written once per step.
-#include "gauss_math.cuh"
+#include "phases.cuh"
+#include "tile_composite.cuh"
 
 namespace adp {
 
@@ -29,55 +30,13 @@ struct BwdPixArgs {
   const float* target;
   const float* dL_drgb;
   float bg[3];
-  float alpha_min, alpha_max, log2_alpha_min;
+  CompositeConsts kc;
   float4* g2d;     // [V*n][3]
   int* tile_ctr;   // next tile to take, zero at the launch
 };
 
-// Reduce-scatter of eight per-lane values across the warp by recursive halving:
-// at each of three levels a lane keeps half of its values and sends the other
-// half to its partner, then two plain steps finish. Lane l ends with the warp
-// total of value index ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 + ((l >> 2) & 1)
-// (the same in all four lanes of its quad): nine shuffles instead of forty.
-__device__ __forceinline__ float reduce_scatter8(const float* v, int* idx) {
-  const int lane = threadIdx.x & 31;
-  const bool b16 = (lane >> 4) & 1, b8 = (lane >> 3) & 1, b4 = (lane >> 2) & 1;
-  float u[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    float keep = b16 ? v[4 + i] : v[i];
-    float send = b16 ? v[i] : v[4 + i];
-    u[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-  float w[2];
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    float keep = b8 ? u[2 + i] : u[i];
-    float send = b8 ? u[i] : u[2 + i];
-    w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-  float keep = b4 ? w[1] : w[0];
-  float send = b4 ? w[0] : w[1];
-  float x = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  x += __shfl_xor_sync(0xffffffffu, x, 2);
-  x += __shfl_xor_sync(0xffffffffu, x, 1);
-  *idx = (b16 ? 4 : 0) + (b8 ? 2 : 0) + (b4 ? 1 : 0);
-  return x;
-}
-
-// PX horizontally adjacent pixels per thread, staged Gaussians in the form the
-// forward uses (so every alpha test agrees with the forward's), a warp-uniform
-// skip of Gaussians that reach none of the warp's rows, a branch-free per-pixel
-// update, and one warp reduction per staged Gaussian covering the warp's pixels.
-//
-// What is reduced and accumulated per (view, Gaussian) are moments of
-// k = dL/dalpha * alpha over the pixels (alpha below the 0.99 clamp only) with
-// d = mean - pixel: S = sum k, Sx = sum k dx, Sy = sum k dy, Sxx, Sxy, Syy, and
-// the colour gradient sum T alpha dL/dpix. With alpha = o exp(power) and
-// power = -(A dx^2 + 2 B dx dy + C dy^2) / 2 they give dL/do = S / o,
-// dL/dA = -Sxx / 2, dL/dB = -Sxy, dL/dC = -Syy / 2, dL/dmean = -(A Sx + B Sy,
-// B Sx + C Sy); the per-Gaussian pass applies these. A thread's pixels share
-// dy, so Sy, Sxy, Syy follow from its S and Sx.
+// PX horizontally adjacent pixels per thread; the walk itself is bwd_tile
+// (tile_composite.cuh), which the fused batched kernel also runs.
 #ifndef ADP_BWD_PX
 #define ADP_BWD_PX 4
 #endif
@@ -85,61 +44,30 @@ __device__ __forceinline__ float reduce_scatter8(const float* v, int* idx) {
 #define ADP_BWD_MINB 1
 #endif
 constexpr int BWD_PX = ADP_BWD_PX;
-#ifndef ADP_BWD_STAGE
-#define ADP_BWD_STAGE 256
-#endif
-constexpr int BWD_STAGE = ADP_BWD_STAGE;
 
-// The thread's pixels are processed as PX / 2 horizontal pairs with the packed
-// two-lane FP32 instructions of sm_100+ (__ffma2_rn and friends round each lane
-// exactly like the scalar instruction, so the alpha test still agrees bit for bit
-// with the forward's); compares, selects and the special-function unit stay scalar.
-template <int PX>
+// Loads a tile's per-pixel inputs (final transmittance, last blended position,
+// dL/dpixel of the L1 loss or the given upstream gradient) and walks it.
+template <int PX, int STAGE>
 __device__ __forceinline__ void bwd_pixel_tile(const BwdPixArgs& a, const CamSet& cs,
-                                               const int tile) {
-  static_assert(PX % 2 == 0, "pixels are processed in pairs");
-  constexpr int NT = TileLanes<PX>::THREADS;
+                                               const int tile, const StageBuf& sb,
+                                               int* s_maxlast) {
   constexpr int NP = PX / 2;
-  __shared__ float4 s_g0[BWD_STAGE];
-  __shared__ float4 s_g1[BWD_STAGE];
-  __shared__ float4 s_g2[BWD_STAGE];
-  __shared__ float2 s_y[BWD_STAGE];
-  __shared__ int s_maxlast;
-  const int v = view_of_tile(cs, tile);
-  const int lt = tile - cs.tile_base[v];
-  const int txs = cs.tiles_x[v];
-  const int W = cs.cam[v].width, H = cs.cam[v].height;
-  const int2 range = a.ranges[tile];
-  const long long rec_base = (long long)v * a.n;
-  const float sc = 1.f / (3.f * (float)W * (float)H);
-  const int tx0 = (lt % txs) * cs.tile_w, ty0 = (lt / txs) * cs.tile_h;
-  const int warp = threadIdx.x >> 5;
-  const float wy0 = (float)(ty0 + (TileLanes<PX>::WARP_PIXELS * warp) / cs.tile_w);
-  const float wy1 =
-      (float)(ty0 + (TileLanes<PX>::WARP_PIXELS * (warp + 1) - 1) / cs.tile_w);
-  const int li0 = PX * (int)threadIdx.x;
-  const int px0 = tx0 + li0 % cs.tile_w, py = ty0 + li0 / cs.tile_w;
-  const float fy = (float)py;
-  const float amax = a.alpha_max, l2amin = a.log2_alpha_min;
-  const float2 one2 = make_float2(1.f, 1.f), neg2 = make_float2(-1.f, -1.f);
-
-  // per pixel pair: transmittance, colour behind, dL/dpixel, minus the x coordinate
-  float2 T[NP], R0[NP], R1[NP], R2[NP], G0[NP], G1[NP], G2[NP], npx[NP];
-  int last[PX];
-  int warp_last = 0;
+  const TileGeom<PX> t = tile_geom<PX>(cs, a.ranges, a.n, tile);
+  const float sc = 1.f / (3.f * (float)t.W * (float)t.H);
+  BwdIn<PX> in;
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
-    float t[2], g[2][3];
+    float tt[2], g[2][3];
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-      const int h = 2 * j + e, px = px0 + h;
-      t[e] = 1.f;
+      const int h = 2 * j + e;
+      tt[e] = 1.f;
       g[e][0] = g[e][1] = g[e][2] = 0.f;
-      last[h] = 0;
-      if (px < W && py < H) {
-        long long p = cs.pix_base[v] + (long long)py * W + px;
-        t[e] = a.T_final[p];
-        last[h] = a.last[p];
+      in.last[h] = 0;
+      if (pixel_in(t, h)) {
+        const long long p = t.pix_base + (long long)t.py * t.W + t.px0 + h;
+        tt[e] = a.T_final[p];
+        in.last[h] = a.last[p];
         if (a.dL_drgb) {
           g[e][0] = a.dL_drgb[3 * p];
           g[e][1] = a.dL_drgb[3 * p + 1];
@@ -152,100 +80,13 @@ __device__ __forceinline__ void bwd_pixel_tile(const BwdPixArgs& a, const CamSet
           }
         }
       }
-      warp_last = max(warp_last, last[h]);
     }
-    T[j] = make_float2(t[0], t[1]);
-    R0[j] = make_float2(a.bg[0], a.bg[0]);
-    R1[j] = make_float2(a.bg[1], a.bg[1]);
-    R2[j] = make_float2(a.bg[2], a.bg[2]);
-    G0[j] = make_float2(g[0][0], g[1][0]);
-    G1[j] = make_float2(g[0][1], g[1][1]);
-    G2[j] = make_float2(g[0][2], g[1][2]);
-    npx[j] = make_float2(-(float)(px0 + 2 * j), -(float)(px0 + 2 * j + 1));
+    in.T[j] = make_float2(tt[0], tt[1]);
+    in.G0[j] = make_float2(g[0][0], g[1][0]);
+    in.G1[j] = make_float2(g[0][1], g[1][1]);
+    in.G2[j] = make_float2(g[0][2], g[1][2]);
   }
-  if (threadIdx.x == 0) s_maxlast = 0;
-  __syncthreads();
-  for (int o = 16; o > 0; o >>= 1) warp_last = max(warp_last, __shfl_xor_sync(0xffffffffu, warp_last, o));
-  if ((threadIdx.x & 31) == 0 && warp_last > 0) atomicMax(&s_maxlast, warp_last);
-  __syncthreads();
-  const int end = s_maxlast;
-  const int lane = threadIdx.x & 31;
-  for (int b1 = end; b1 > 0; b1 -= BWD_STAGE) {
-    const int b0 = b1 - BWD_STAGE > 0 ? b1 - BWD_STAGE : 0;
-    __syncthreads();
-    for (int j = (int)threadIdx.x; j < b1 - b0; j += NT) {
-      int id = a.inst[range.x + b0 + j];
-      long long r = rec_base + id;
-      Staged g = stage_gaussian(a.xyod[r], a.conic[r], a.rgb[r], id, a.alpha_min);
-      s_g0[j] = g.g0;
-      s_g1[j] = g.g1;
-      s_g2[j] = g.g2;
-      s_y[j] = g.y;
-    }
-    __syncthreads();
-    const int kmax = min(b1, warp_last) - b0;  // warp-uniform
-    for (int k = kmax - 1; k >= 0; --k) {
-      const float2 yr = s_y[k];
-      if (yr.y < wy0 || yr.x > wy1) continue;  // warp-uniform: no row of this warp reached
-      const float4 g0 = s_g0[k], g1 = s_g1[k], g2 = s_g2[k];
-      const RowQ rq = row_q(g0, g1, fy);
-      const int pos = b0 + k;
-      const float2 mx = make_float2(g0.x, g0.x), qa = make_float2(g0.z, g0.z);
-      const float2 qb = make_float2(rq.bdy, rq.bdy), qe = make_float2(rq.e, rq.e);
-      const float2 cr = make_float2(g1.z, g1.z), cg = make_float2(g1.w, g1.w);
-      const float2 cb = make_float2(g2.x, g2.x);
-      float2 S = make_float2(0.f, 0.f), Sx = S, Sxx = S, C0 = S, C1 = S, C2 = S;
-      bool hit = false;
-#pragma unroll
-      for (int j = 0; j < NP; ++j) {
-        // q = dx (a dx + b dy) + e, the same operations as pix_q
-        const float2 dx = __fadd2_rn(mx, npx[j]);
-        const float2 q = __ffma2_rn(dx, __ffma2_rn(qa, dx, qb), qe);
-        const bool p0 = pos < last[2 * j] && q.x >= l2amin;  // blended in the forward
-        const bool p1 = pos < last[2 * j + 1] && q.y >= l2amin;
-        hit = hit || p0 || p1;
-        const float ar0 = ex2_approx(q.x), ar1 = ex2_approx(q.y);
-        const float2 al = make_float2(p0 ? fminf(amax, ar0) : 0.f, p1 ? fminf(amax, ar1) : 0.f);
-        const float2 om = __ffma2_rn(al, neg2, one2);  // 1 - alpha
-        // transmittance before this Gaussian
-        const float2 Tj = __fmul2_rn(T[j], make_float2(rcp_approx(om.x), rcp_approx(om.y)));
-        const float2 d0 = __ffma2_rn(R0[j], neg2, cr);  // colour minus the colour behind
-        const float2 d1 = __ffma2_rn(R1[j], neg2, cg);
-        const float2 d2 = __ffma2_rn(R2[j], neg2, cb);
-        const float2 dal =
-            __fmul2_rn(Tj, __ffma2_rn(G0[j], d0, __ffma2_rn(G1[j], d1, __fmul2_rn(G2[j], d2))));
-        const float2 wgt = __fmul2_rn(Tj, al);
-        C0 = __ffma2_rn(wgt, G0[j], C0);
-        C1 = __ffma2_rn(wgt, G1[j], C1);
-        C2 = __ffma2_rn(wgt, G2[j], C2);
-        R0[j] = __ffma2_rn(al, d0, R0[j]);
-        R1[j] = __ffma2_rn(al, d1, R1[j]);
-        R2[j] = __ffma2_rn(al, d2, R2[j]);
-        T[j] = Tj;
-        // dL/dalpha * alpha, zero through the clamp (alpha = 0 where not blended)
-        float2 kk = __fmul2_rn(dal, al);
-        kk.x = ar0 <= amax ? kk.x : 0.f;
-        kk.y = ar1 <= amax ? kk.y : 0.f;
-        S = __fadd2_rn(S, kk);
-        const float2 t = __fmul2_rn(dx, kk);
-        Sx = __fadd2_rn(Sx, t);
-        Sxx = __ffma2_rn(dx, t, Sxx);
-      }
-      if (__ballot_sync(0xffffffffu, hit)) {
-        const float dy = rq.dy;
-        const float s1 = S.x + S.y, sx = Sx.x + Sx.y;
-        float vals[8] = {s1, sx, dy * s1, Sxx.x + Sxx.y, dy * sx, dy * dy * s1, C0.x + C0.y,
-                         C1.x + C1.y};
-        int idx;
-        float sum = reduce_scatter8(vals, &idx);
-        float cbs = warp_sum(C2.x + C2.y);
-        int id = __float_as_int(g2.y);
-        float* gp = reinterpret_cast<float*>(a.g2d + 3 * (rec_base + id));
-        if ((lane & 3) == 0) atomicAdd(gp + idx, sum);
-        if (lane == 0) atomicAdd(gp + 8, cbs);
-      }
-    }
-  }
+  bwd_tile<PX, STAGE>(a.xyod, a.conic, a.rgb, a.inst, t, a.kc, a.bg, sb, s_maxlast, in, a.g2d);
 }
 
 // Blocks take tiles in order from a counter (zeroed before the launch). With
@@ -258,10 +99,15 @@ __device__ __forceinline__ void bwd_pixel_tile(const BwdPixArgs& a, const CamSet
 #endif
 constexpr int BWD_PERSIST = ADP_BWD_PERSIST;
 
-template <int PX>
+template <int PX, int STAGE>
 __global__ void __launch_bounds__(TileLanes<PX>::THREADS, ADP_BWD_MINB)
     bwd_pixel_kernel(BwdPixArgs a, CamSet cs) {
-  __shared__ int s_tile;
+  __shared__ float4 s_g0[STAGE];
+  __shared__ float4 s_g1[STAGE];
+  __shared__ float4 s_g2[STAGE];
+  __shared__ float2 s_y[STAGE];
+  __shared__ int s_tile, s_maxlast;
+  const StageBuf sb{s_g0, s_g1, s_g2, s_y};
   const int n_tiles = cs.tile_base[cs.n_views];
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_ctr, 1);
@@ -269,7 +115,7 @@ __global__ void __launch_bounds__(TileLanes<PX>::THREADS, ADP_BWD_MINB)
     const int tile = s_tile;
     __syncthreads();  // every thread is past the previous tile and has read s_tile
     if (tile >= n_tiles) break;
-    bwd_pixel_tile<PX>(a, cs, tile);
+    bwd_pixel_tile<PX, STAGE>(a, cs, tile, sb, &s_maxlast);
   }
 }
 
@@ -591,9 +437,7 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   pa.target = target;
   pa.dL_drgb = dL_drgb;
   for (int c = 0; c < 3; ++c) pa.bg[c] = bg ? bg[c] : 0.f;
-  pa.alpha_min = prm->alpha_min;
-  pa.alpha_max = prm->alpha_max;
-  pa.log2_alpha_min = log2f(prm->alpha_min);
+  pa.kc = CompositeConsts{prm->alpha_min, prm->alpha_max, prm->t_min, log2f(prm->alpha_min)};
   pa.g2d = g2d;
   pa.tile_ctr = tile_ctr;
   long long grid = cs.tile_base[n_views];
@@ -603,8 +447,24 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
     ADP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     grid = std::min<long long>(grid, (long long)sms * BWD_PERSIST);
   }
-  bwd_pixel_kernel<BWD_PX><<<(unsigned)grid, TileLanes<BWD_PX>::THREADS, 0, st>>>(pa, cs);
+  const dim3 pg((unsigned)grid), pb(TileLanes<BWD_PX>::THREADS);
+  switch (stage_size(prm)) {
+    case 64: bwd_pixel_kernel<BWD_PX, 64><<<pg, pb, 0, st>>>(pa, cs); break;
+    case 128: bwd_pixel_kernel<BWD_PX, 128><<<pg, pb, 0, st>>>(pa, cs); break;
+    default: bwd_pixel_kernel<BWD_PX, 256><<<pg, pb, 0, st>>>(pa, cs); break;
+  }
   ADP_LAUNCH_CHECK();
+  return backward_gauss_phase(g, pr, cs, prm, grad, grad2d_accum, grad2d_visits, g2d, list, n_list,
+                              st);
+}
+
+namespace adp {
+
+int backward_gauss_phase(const adp_gaussians* g, const adp_projected* pr, const CamSet& cs,
+                         const adp_params* prm, adp_gaussians* grad, float* grad2d_accum,
+                         int32_t* grad2d_visits, const float4* g2d, int* list,
+                         unsigned long long* n_list, cudaStream_t st) {
+  const int n_views = cs.n_views;
   BwdGaussArgs ga;
   ga.mean_logit = reinterpret_cast<const float4*>(g->mean_logit);
   ga.logscale = reinterpret_cast<const float4*>(g->logscale);
@@ -635,3 +495,5 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   ADP_LAUNCH_CHECK();
   return ADP_OK;
 }
+
+}  // namespace adp

@@ -16,9 +16,13 @@
 
 namespace adp {
 
-__global__ void clamp_count_kernel(const long long* K, long long cap, long long* Kc) {
+// The instance count the duplication and the tile sort process: the required
+// count if it fits the capacity and the offset scan completed, else 0 (nothing
+// binned).
+__global__ void clamp_count_kernel(const long long* K, long long cap,
+                                   const unsigned long long* scan_err, long long* Kc) {
   long long k = *K;
-  *Kc = k <= cap ? k : 0;
+  *Kc = (k <= cap && *scan_err == 0ull) ? k : 0;
 }
 
 // Load-balanced duplication: each CTA takes a chunk of DUP_CHUNK consecutive
@@ -92,8 +96,8 @@ __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
   __shared__ int s_rec[DUP_SUB];            // record starting at each slot of the sub-chunk
   __shared__ int s_wm[DUP_THREADS / 32];
   __shared__ unsigned s_h[RS_BINS];
-  const long long N = *d_nvis, K = *d_K;
-  if (K > cap || N == 0) return;
+  const long long N = *d_nvis, K = *d_K;  // K: the clamped count (0 = bin nothing)
+  if (K == 0 || K > cap || N == 0) return;
   const long long n_chunks = (K + DUP_CHUNK - 1) / DUP_CHUNK;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int e = threadIdx.x; e < DUP_SUB; e += DUP_THREADS) s_rec[e] = 0;
@@ -255,7 +259,8 @@ extern "C" ADP_API size_t adp_bin_sort_workspace_size(int64_t n, int32_t n_views
 
 extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const adp_camera* cams,
                                     int32_t n_views, const adp_params* prm, adp_bins* bins,
-                                    void* ws, size_t ws_bytes, adp_stream_t stream) {
+                                    void* ws, size_t ws_bytes, int32_t* d_status,
+                                    adp_stream_t stream) {
   ADP_CHECK_ARG(pr && bins, "NULL argument");
   CamSet cs;
   int rc = make_camset(cams, n_views, prm, &cs);
@@ -296,8 +301,9 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
           vvals[pre] = (unsigned)p;
         }
       },
-      nv, nullptr, &w.counters[0], w.scan, st);
+      nv, nullptr, &w.counters[0], w.scan, st, d_status);
   if (rc) return rc;
+  count_guard_kernel<<<1, 1, 0, st>>>(scan_error_flag(w.scan, nv), &w.counters[0]);
 
   // 2. stable sort by depth, then by view
   DigitOp passes[5];
@@ -320,9 +326,10 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
                              c < n_chunk_max && c * DUP_CHUNK < end; ++c)
                           chunk_first[c] = (int)j;
                       },
-                      nv, &w.counters[0], (long long*)bins->n_instances, w.scan, st);
+                      nv, &w.counters[0], (long long*)bins->n_instances, w.scan, st, d_status);
   if (rc) return rc;
-  clamp_count_kernel<<<1, 1, 0, st>>>((const long long*)bins->n_instances, cap, &w.counters[1]);
+  clamp_count_kernel<<<1, 1, 0, st>>>((const long long*)bins->n_instances, cap,
+                                      scan_error_flag(w.scan, nv), &w.counters[1]);
 
   // 4. duplicate into tiles, 5. stable sort by tile. The instance key is the
   // view-local tile with the view above the sorted bits: the tile sort takes
@@ -333,7 +340,7 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
   if (cap > 0) {
     duplicate_kernel<<<(unsigned)std::min<long long>((cap + DUP_CHUNK - 1) / DUP_CHUNK, 148 * 8),
                        DUP_THREADS, 0, st>>>(
-        vvals, offs, chunk_first, &w.counters[0], (const long long*)bins->n_instances, cap,
+        vvals, offs, chunk_first, &w.counters[0], &w.counters[1], cap,
         reinterpret_cast<const int4*>(pr->rect), xyod,
         reinterpret_cast<const float4*>(pr->conic), prm->alpha_min, n, cs, view_shift, w.tkeys,
         bins->inst_gauss, aligned(bins->inst_gauss, 8), w.sort.hist, w.sort.tiles_max);

@@ -1,13 +1,21 @@
 // Error strings, defaults, camera set construction, and the non-template parts
 // of the scan and radix sort.
+#include <atomic>
 #include <cstdarg>
 #include <cstring>
 
 #include "common.cuh"
+#include "gauss_math.cuh"
 
 namespace adp {
 
 static thread_local char g_err[512] = "";
+
+// Poll bound of every device wait (see adp_set_spin_limit). About a second of
+// polling on a B300 at the default; read at each launch.
+constexpr long long kDefaultSpinLimit = 1LL << 22;
+static std::atomic<long long> g_spin_limit{kDefaultSpinLimit};
+long long spin_limit() { return g_spin_limit.load(std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -23,6 +31,8 @@ int make_camset(const adp_camera* cams, int n_views, const adp_params* prm, CamS
   ADP_CHECK_ARG(prm != nullptr, "params is NULL");
   ADP_CHECK_ARG(prm->tile_w > 0 && prm->tile_h > 0 && prm->tile_w * prm->tile_h == 256,
                 "tile %dx%d must have 256 pixels", prm->tile_w, prm->tile_h);
+  ADP_CHECK_ARG(prm->batch == 0 || prm->batch == 64 || prm->batch == 128 || prm->batch == 256,
+                "batch %d must be 0, 64, 128 or 256", prm->batch);
   memset(cs, 0, sizeof(*cs));
   cs->n_views = n_views;
   cs->tile_w = prm->tile_w;
@@ -333,6 +343,10 @@ int radix_sort_pairs(unsigned* keys, unsigned* vals, const long long* d_n, long 
   return ADP_OK;
 }
 
+__global__ void count_guard_kernel(const unsigned long long* err, long long* count) {
+  if (*err != 0ull) *count = 0;
+}
+
 }  // namespace adp
 
 extern "C" {
@@ -340,6 +354,28 @@ extern "C" {
 ADP_API int32_t adp_version(void) { return ADP_VERSION; }
 
 ADP_API const char* adp_last_error_string(void) { return adp::g_err; }
+
+ADP_API void adp_set_spin_limit(int64_t max_polls) {
+  adp::g_spin_limit.store(max_polls > 0 ? (long long)max_polls : adp::kDefaultSpinLimit,
+                          std::memory_order_relaxed);
+}
+
+ADP_API void adp_get_constants(adp_constants* c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->version = ADP_VERSION;
+  c->max_views = ADP_MAX_VIEWS;
+  c->tile_pixels = 256;
+  c->max_sh_degree = 3;
+  c->fov_clamp = 1.3f;
+  c->gram_schmidt_eps = 1e-12;
+  const float sh[16] = {SHC0, -SHC1, SHC1, -SHC1, SHC2_0, -SHC2_0, SHC2_2, -SHC2_0, SHC2_4,
+                        -SHC3_0, SHC3_1, -SHC3_2, SHC3_3, -SHC3_2, SHC3_5, -SHC3_0};
+  for (int k = 0; k < 16; ++k) c->sh_coef[k] = sh[k];
+  c->topk_noalloc_max_n = ADP_TOPK_NOALLOC_MAX_N;
+  c->default_spin_limit = adp::kDefaultSpinLimit;
+  adp_default_params(&c->defaults);
+}
 
 ADP_API void adp_default_params(adp_params* p) {
   if (!p) return;
@@ -360,6 +396,7 @@ ADP_API void adp_default_params(adp_params* p) {
   p->t_min = 1e-4f;
   p->tile_w = 16;
   p->tile_h = 16;
+  p->batch = 256;
 }
 
 }  // extern "C"

@@ -83,6 +83,11 @@ struct CamSet {
 
 int make_camset(const adp_camera* cams, int n_views, const adp_params* prm, CamSet* cs);
 
+// Gaussians a compositing block stages per batch (validated by make_camset).
+inline int stage_size(const adp_params* prm) {
+  return prm->batch == 64 || prm->batch == 128 ? prm->batch : 256;
+}
+
 __device__ __forceinline__ int view_of_tile(const CamSet& cs, int tile) {
   int v = 0;
   while (v + 1 < cs.n_views && tile >= cs.tile_base[v + 1]) ++v;
@@ -104,6 +109,27 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// ----------------------------------------------------------------- bounded waits
+
+// Every device wait of the library (the scan's look-back, the top-k's grid
+// barrier) polls at most a bounded number of times. The bound is read on the
+// host at each launch (adp_set_spin_limit; the default is large enough never to
+// run out on a working device). A wait that runs out records ADP_ERR_TIMEOUT in
+// the caller's status word (if one was given) and in the call's own error flag,
+// and the kernel returns normally with results the call then discards or marks
+// undefined.
+long long spin_limit();
+
+__device__ __forceinline__ void report_timeout(int* d_status) {
+  if (d_status) atomicCAS(d_status, 0, (int)ADP_ERR_TIMEOUT);
+}
+
+// Sets *count to 0 if the scan whose error flag is err gave up a wait. A
+// compaction by a scan that gave up can leave gaps (entries never written)
+// below its count; consumers that index memory with the compacted entries then
+// see an empty list instead.
+__global__ void count_guard_kernel(const unsigned long long* err, long long* count);
+
 // ----------------------------------------------------------------- scan
 
 // Exclusive prefix sum of n int64 values produced by a functor load(i), in one
@@ -112,7 +138,8 @@ __device__ __forceinline__ T warp_sum(T v) {
 // before it are known, reading up to 32 predecessors at a time. A CTA only ever
 // waits on tiles handed out before its own ticket, which are being processed by
 // CTAs already running, so the waits end; each is still bounded, and a bound
-// that runs out sets *err and leaves the result undefined. The count is a host
+// that runs out sets the error flag (scan_error_flag) and *d_status and leaves
+// the prefixes too small (never larger than the true ones). The count is a host
 // value or read from device memory (d_n != nullptr, n an upper bound).
 constexpr int SCAN_THREADS = 256;
 #ifndef ADP_SCAN_ITEMS
@@ -123,7 +150,6 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 constexpr unsigned long long SCAN_FLAG_A = 1ull << 62;  // tile total published
 constexpr unsigned long long SCAN_FLAG_P = 2ull << 62;  // inclusive prefix published
 constexpr unsigned long long SCAN_VALUE = (1ull << 62) - 1;
-constexpr int SCAN_SPIN_LIMIT = 1 << 22;
 
 __host__ __device__ inline long long scan_blocks(long long n_max) {
   return (n_max + SCAN_TILE - 1) / SCAN_TILE;
@@ -131,6 +157,11 @@ __host__ __device__ inline long long scan_blocks(long long n_max) {
 // status words [0, nb), ticket, error flag
 inline size_t scan_workspace_bytes(long long n_max) {
   return carve_bytes<unsigned long long>(scan_blocks(n_max) + 4);
+}
+// The error flag of a scan's workspace: nonzero after a look-back gave up. It is
+// cleared by the next scan in the same workspace, so a consumer reads it before.
+inline const unsigned long long* scan_error_flag(const void* ws, long long n_max) {
+  return static_cast<const unsigned long long*>(ws) + scan_blocks(n_max) + 2;
 }
 
 __device__ __forceinline__ long long device_count(const long long* d_n, long long n) {
@@ -140,7 +171,8 @@ __device__ __forceinline__ long long device_count(const long long* d_n, long lon
 template <class Load, class Store>
 __global__ void __launch_bounds__(SCAN_THREADS)
     scan_lookback_kernel(Load load, Store store, long long n, const long long* d_n,
-                         unsigned long long* status, long long* total) {
+                         unsigned long long* status, long long* total, int* d_status,
+                         long long spin_max) {
   __shared__ long long s_warp[SCAN_THREADS / 32];
   __shared__ long long s_excl;
   __shared__ long long s_tile;
@@ -196,12 +228,13 @@ __global__ void __launch_bounds__(SCAN_THREADS)
         const long long j = end - 1 - lane;
         unsigned long long word = SCAN_FLAG_P;  // before tile 0: an empty prefix
         if (j >= 0) {
-          int spins = 0;
+          long long spins = 0;
           do {
             word = vs[j];
-          } while ((word >> 62) == 0 && ++spins < SCAN_SPIN_LIMIT);
+          } while ((word >> 62) == 0 && ++spins < spin_max);
           if ((word >> 62) == 0) {
             atomicExch(err, 1ull);
+            report_timeout(d_status);
             word = SCAN_FLAG_P;  // give up: stop the look-back here
           }
         }
@@ -233,15 +266,16 @@ __global__ void __launch_bounds__(SCAN_THREADS)
 }
 
 // Exclusive scan: store(i, prefix_i); total (device, may be null) receives the sum.
+// d_status (device, may be null): the caller's status word (see bounded waits).
 template <class Load, class Store>
 int scan_exclusive(Load load, Store store, long long n_max, const long long* d_n,
-                   long long* total, void* ws, cudaStream_t st) {
+                   long long* total, void* ws, cudaStream_t st, int* d_status) {
   long long nb = scan_blocks(n_max);
   if (nb == 0) nb = 1;
   unsigned long long* status = static_cast<unsigned long long*>(ws);
   ADP_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)(nb + 3), st));
   scan_lookback_kernel<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(load, store, n_max, d_n, status,
-                                                              total);
+                                                              total, d_status, spin_limit());
   ADP_LAUNCH_CHECK();
   return ADP_OK;
 }

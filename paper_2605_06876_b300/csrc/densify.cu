@@ -24,7 +24,11 @@ __device__ __forceinline__ unsigned densify_class(const float* accum, const int*
   return smax > ln_tau_s ? 1u : 2u;  // 1 split, 2 clone
 }
 
-__global__ void densify_counts_kernel(const long long* packed, int64_t* d_counts) {
+// The two counts from the packed scan total; both 0 if the scan gave up a wait
+// (its lists may have gaps), so the tail pass turns every entry into -1.
+__global__ void densify_counts_kernel(long long* packed, const unsigned long long* err,
+                                      int64_t* d_counts) {
+  if (*err != 0ull) *packed = 0;
   const unsigned long long t = (unsigned long long)*packed;
   d_counts[0] = (int64_t)(t & 0xffffffffull);
   d_counts[1] = (int64_t)(t >> 32);
@@ -56,7 +60,7 @@ extern "C" ADP_API int adp_densify_select(const float* grad2d_accum, const int32
                                           const adp_gaussians* g, float tau_g, float tau_s,
                                           int32_t* split_ids, int32_t* clone_ids,
                                           int64_t* d_counts, void* ws, size_t ws_bytes,
-                                          adp_stream_t stream) {
+                                          int32_t* d_status, adp_stream_t stream) {
   ADP_CHECK_ARG(g && d_counts, "NULL argument");
   ADP_CHECK_ARG(g->n >= 0 && g->n < (1LL << 31), "n out of range");
   ADP_CHECK_ARG(g->n == 0 || (grad2d_accum && grad2d_visits && g->logscale && split_ids &&
@@ -89,9 +93,9 @@ extern "C" ADP_API int adp_densify_select(const float* grad2d_accum, const int32
         if (k == 1u) sp[pre & 0xffffffffLL] = (int32_t)i;
         if (k == 2u) cl[(unsigned long long)pre >> 32] = (int32_t)i;
       },
-      g->n, nullptr, total, sw, st);
+      g->n, nullptr, total, sw, st, d_status);
   if (rc) return rc;
-  densify_counts_kernel<<<1, 1, 0, st>>>(total, d_counts);
+  densify_counts_kernel<<<1, 1, 0, st>>>(total, scan_error_flag(sw, g->n), d_counts);
   densify_tail_kernel<<<grid_for(g->n, 256, 148 * 16), 256, 0, st>>>(total, g->n, split_ids,
                                                                       clone_ids);
   ADP_LAUNCH_CHECK();

@@ -14,6 +14,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "phases.cuh"
 
 namespace adp {
 
@@ -170,8 +171,6 @@ constexpr int TOPK_PER_SM = ADP_TOPK_PER_SM;  // resident blocks per SM the grid
 constexpr int TOPK_MAX_BLOCKS = 1024;         // bound of the grid
 static_assert(TOPK_THREADS >= 256 && TOPK_THREADS <= 1024 && TOPK_THREADS % 32 == 0,
               "the digit sums take 256 threads and the flag scan one warp of warp totals");
-constexpr int TOPK_BARRIER_SPINS = 1 << 24;
-
 struct TopkCoop {
   unsigned* hist;              // [8][256], zeroed before the launch
   unsigned long long* mm;      // [8][2] min, max of the matching keys (preset by the caller)
@@ -179,28 +178,40 @@ struct TopkCoop {
   unsigned* err;               // set if a barrier wait gave up
   long long* blk;              // [2][gridDim.x] per-block counts
   uint8_t* sel;                // [n] selection flags
+  int* d_status;               // the caller's status word (may be null)
+  long long spin_max;          // poll bound of a barrier wait
 };
 
 // Grid-wide barrier number `round` (1, 2, ...) over a counter that starts at zero.
-// Waits are bounded: on timeout the error flag is set and the block goes on.
-__device__ __forceinline__ void topk_grid_barrier(const TopkCoop& w, unsigned round) {
+// Waits are bounded: on timeout the error flag and the caller's status word are
+// set and the barrier returns false in every thread of the block, which then
+// leaves the kernel. Every block counts itself in before waiting, so the blocks
+// still waiting pass this barrier with complete data and stop at the next one
+// (the departed block never reaches it): no block goes on from stale state.
+__device__ __forceinline__ bool topk_grid_barrier(const TopkCoop& w, unsigned round) {
+  __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     atomicAdd(w.bar, 1u);
     const unsigned target = round * gridDim.x;
     volatile unsigned* vb = w.bar;
-    int spins = 0;
+    long long spins = 0;
+    int ok = 1;
     while (*vb < target) {
-      if (++spins > TOPK_BARRIER_SPINS) {
+      if (++spins > w.spin_max) {
         atomicExch(w.err, 1u);
+        report_timeout(w.d_status);
+        ok = 0;
         break;
       }
       __nanosleep(32);
     }
     __threadfence();
+    s_ok = ok;
   }
   __syncthreads();
+  return s_ok != 0;
 }
 
 // Block-wide exclusive scan of 0/1 flags over TOPK_THREADS threads; returns the
@@ -276,7 +287,7 @@ __global__ void __launch_bounds__(TOPK_THREADS)
       }
     }
     if (t < 256 && s_h[t]) atomicAdd(&w.hist[256 * p + t], s_h[t]);
-    topk_grid_barrier(w, ++round);
+    if (!topk_grid_barrier(w, ++round)) return;
     const unsigned long long glo = *(volatile unsigned long long*)&w.mm[2 * p];
     const unsigned long long ghi = *(volatile unsigned long long*)&w.mm[2 * p + 1];
     if (glo == ghi) {  // every key still in play is the threshold key
@@ -321,7 +332,7 @@ __global__ void __launch_bounds__(TOPK_THREADS)
     cnt_eq += tot;
   }
   if (t == 0) w.blk[blockIdx.x] = cnt_eq;
-  topk_grid_barrier(w, ++round);
+  if (!topk_grid_barrier(w, ++round)) return;
   if (warp == 0) {
     long long x = 0;
     for (long long b = lane; b < blockIdx.x; b += 32) x += *(volatile long long*)&w.blk[b];
@@ -341,7 +352,7 @@ __global__ void __launch_bounds__(TOPK_THREADS)
     cnt_sel += __syncthreads_count(sel);
   }
   if (t == 0) w.blk[G + blockIdx.x] = cnt_sel;
-  topk_grid_barrier(w, ++round);
+  if (!topk_grid_barrier(w, ++round)) return;
   if (warp == 0) {
     long long x = 0;
     for (long long b = lane; b < blockIdx.x; b += 32) x += *(volatile long long*)&w.blk[G + b];
@@ -385,7 +396,7 @@ static size_t topk_coop_bytes(long long n) {
 }
 
 static int topk_coop_run(const double* mass, long long n, long long k, int32_t* out_ids,
-                         void* ws, size_t ws_bytes, cudaStream_t st) {
+                         void* ws, size_t ws_bytes, int* d_status, cudaStream_t st) {
   Carver c(ws, ws_bytes);
   TopkCoop w;
   w.hist = c.take<unsigned>(8 * 256);
@@ -394,12 +405,17 @@ static int topk_coop_run(const double* mass, long long n, long long k, int32_t* 
   w.err = w.bar + 1;
   w.blk = c.take<long long>(2 * TOPK_MAX_BLOCKS);
   w.sel = c.take<uint8_t>(n > 0 ? n : 1);
+  w.d_status = d_status;
+  w.spin_max = spin_limit();
   ADP_CHECK_ARG(c.ok, "internal: top-k scratch too small");
   int grid = 0;
   int rc = topk_coop_grid(&grid);
   if (rc) return rc;
   ADP_CUDA(cudaMemsetAsync(w.hist, 0, sizeof(unsigned) * 8 * 256, st));
   ADP_CUDA(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st));
+  // -1 everywhere first: if a barrier wait gives up, the slots of the blocks that
+  // left hold -1, which every consumer of a candidate list skips
+  ADP_CUDA(cudaMemsetAsync(out_ids, 0xff, sizeof(int32_t) * (size_t)k, st));
   topk_coop_init_kernel<<<1, 32, 0, st>>>(w.mm);
   ADP_LAUNCH_CHECK();
   cudaLaunchConfig_t cfg = {};
@@ -889,6 +905,33 @@ using namespace adp;
 
 // ------------------------------------------------------------------ error stats
 
+namespace adp {
+
+int error_minmax_init(adp_error_maps* maps, int n_views, cudaStream_t st) {
+  err_init_minmax_kernel<<<1, 32, 0, st>>>(reinterpret_cast<unsigned*>(maps->minmax), n_views);
+  ADP_LAUNCH_CHECK();
+  return ADP_OK;
+}
+
+int error_norm_phase(adp_error_maps* maps, const int32_t* dominant, long long n,
+                     const CamSet& cs, const adp_params* prm, int32_t* count, double* mass,
+                     cudaStream_t st) {
+  if (n > 0) {
+    ADP_CUDA(cudaMemsetAsync(count, 0, sizeof(int) * n, st));
+    ADP_CUDA(cudaMemsetAsync(mass, 0, sizeof(double) * n, st));
+  }
+  const unsigned* mm = reinterpret_cast<const unsigned*>(maps->minmax);
+  const dim3 grid(view_grid(cs), cs.n_views);
+  const int shift = mass_shift_for(prm->tau_l1);
+  err_norm_kernel<<<grid, 256, 0, st>>>(maps->E, maps->mask, mm, dominant, n, cs, prm->tau_l1,
+                                        prm->n_levels, shift, count, mass);
+  if (n > 0) mass_finalize_kernel<<<grid_for(n, 256, 148 * 16), 256, 0, st>>>(mass, n, shift);
+  ADP_LAUNCH_CHECK();
+  return ADP_OK;
+}
+
+}  // namespace adp
+
 extern "C" ADP_API size_t adp_error_stats_workspace_size(int32_t n_views, const adp_camera* cams) {
   (void)n_views;
   (void)cams;
@@ -909,21 +952,12 @@ extern "C" ADP_API int adp_error_stats(const float* img, const float* target,
   if (rc) return rc;
   ADP_CHECK_ARG(prm->n_levels >= 1 && prm->n_levels <= 15, "n_levels must be 1..15");
   cudaStream_t st = (cudaStream_t)stream;
-  if (n > 0) {
-    ADP_CUDA(cudaMemsetAsync(count, 0, sizeof(int) * n, st));
-    ADP_CUDA(cudaMemsetAsync(mass, 0, sizeof(double) * n, st));
-  }
   unsigned* mm = reinterpret_cast<unsigned*>(maps->minmax);
   err_init_minmax_kernel<<<1, 32, 0, st>>>(mm, n_views);
   dim3 grid(view_grid(cs), n_views);
   err_raw_kernel<<<dim3(std::min(grid.x, 148u * 4u), n_views), 256, 0, st>>>(img, target, cs,
                                                                             maps->E, mm);
-  const int shift = mass_shift_for(prm->tau_l1);
-  err_norm_kernel<<<grid, 256, 0, st>>>(maps->E, maps->mask, mm, dominant, n, cs, prm->tau_l1,
-                                        prm->n_levels, shift, count, mass);
-  if (n > 0) mass_finalize_kernel<<<grid_for(n, 256, 148 * 16), 256, 0, st>>>(mass, n, shift);
-  ADP_LAUNCH_CHECK();
-  return ADP_OK;
+  return error_norm_phase(maps, dominant, n, cs, prm, count, mass, st);
 }
 
 // ------------------------------------------------------------------ top-k
@@ -934,7 +968,8 @@ extern "C" ADP_API size_t adp_select_topk_workspace_size(int64_t n) {
 }
 
 extern "C" ADP_API int adp_select_topk(const double* mass, int64_t n, int64_t k, int32_t* out_ids,
-                                       void* ws, size_t ws_bytes, adp_stream_t stream) {
+                                       void* ws, size_t ws_bytes, int32_t* d_status,
+                                       adp_stream_t stream) {
   ADP_CHECK_ARG(n >= 0 && n < (1LL << 31) && k >= 0, "bad n or k");
   ADP_CHECK_ARG(k == 0 || (mass && out_ids), "NULL argument");
   ADP_CHECK_ARG(aligned(ws, 256), "workspace must be 256-byte aligned");
@@ -948,7 +983,7 @@ extern "C" ADP_API int adp_select_topk(const double* mass, int64_t n, int64_t k,
     ADP_LAUNCH_CHECK();
     return ADP_OK;
   }
-  return topk_coop_run(mass, n, k, out_ids, ws, ws_bytes, st);
+  return topk_coop_run(mass, n, k, out_ids, ws, ws_bytes, d_status, st);
 }
 
 // ------------------------------------------------------------------ regions
@@ -985,7 +1020,7 @@ extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* do
                                          int32_t n_views, const int32_t* candidates,
                                          int64_t n_cand, const adp_params* prm,
                                          adp_regions* out, void* ws, size_t ws_bytes,
-                                         adp_stream_t stream) {
+                                         int32_t* d_status, adp_stream_t stream) {
   ADP_CHECK_ARG(maps && maps->mask && dominant && target && out && out->count, "NULL argument");
   ADP_CHECK_ARG(n >= 0 && n < (1LL << 31) && n_cand >= 0 && n_cand <= n, "bad n or n_cand");
   ADP_CHECK_ARG(n_cand == 0 || candidates, "NULL candidates");
@@ -1063,8 +1098,9 @@ extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* do
                           root_pix[pre] = (int)p;
                         }
                       },
-                      P, nullptr, &w.counters[0], w.scan, st);
+                      P, nullptr, &w.counters[0], w.scan, st, d_status);
   if (rc) return rc;
+  count_guard_kernel<<<1, 1, 0, st>>>(scan_error_flag(w.scan, P), &w.counters[0]);
   zero_i64_kernel<<<gp, 256, 0, st>>>(w.mom, &w.counters[0], 6);
   moments_kernel<<<grid_for(P, 256, 148 * 8), 256, 0, st>>>(w.lroots, n_lroots, w.part, w.L,
                                                             w.slot, w.mom);
@@ -1076,7 +1112,7 @@ extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* do
   rc = scan_exclusive(
       [=] __device__(long long r) -> long long { return mom[6 * r] >= m_min ? 1 : 0; },
       [=] __device__(long long r, long long pre) { kept[r] = pre; }, P, &w.counters[0],
-      (long long*)out->count, w.scan, st);
+      (long long*)out->count, w.scan, st, d_status);
   if (rc) return rc;
   RegionArgs ra;
   ra.mom = w.mom;
@@ -1142,7 +1178,8 @@ static int topk_scratch_address(void** out) {
 }  // namespace adp
 
 extern "C" ADP_API int adp_select_topk_noalloc(const double* mass, int64_t n, int64_t k,
-                                               int32_t* out_ids, adp_stream_t stream) {
+                                               int32_t* out_ids, int32_t* d_status,
+                                               adp_stream_t stream) {
   ADP_CHECK_ARG(n >= 0 && k >= 0, "bad n or k");
   ADP_CHECK_ARG(n <= ADP_TOPK_NOALLOC_MAX_N,
                 "n = %lld exceeds the %lld Gaussians the static scratch of "
@@ -1161,5 +1198,5 @@ extern "C" ADP_API int adp_select_topk_noalloc(const double* mass, int64_t n, in
   int rc = topk_scratch_address(&base);
   if (rc) return rc;
   ADP_CHECK_ARG(topk_coop_bytes(n) <= kNoallocBytes, "internal: static scratch too small");
-  return topk_coop_run(mass, n, k, out_ids, base, kNoallocBytes, st);
+  return topk_coop_run(mass, n, k, out_ids, base, kNoallocBytes, d_status, st);
 }

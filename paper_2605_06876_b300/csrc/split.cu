@@ -574,8 +574,14 @@ __global__ void merge_warp_kernel(MergeArgs a) {
   }
 }
 
-__global__ void new_n_kernel(long long* counters, int64_t* d_new_n) {
-  counters[3] = counters[1] + counters[2];
+// The new size. If either scan of the plan gave up a wait, the size is set beyond
+// any capacity, so the compaction writes nothing (the caller's status word
+// holds ADP_ERR_TIMEOUT).
+__global__ void new_n_kernel(long long* counters, int64_t* d_new_n,
+                             const unsigned long long* err_keep,
+                             const unsigned long long* err_append) {
+  const bool failed = *err_keep != 0ull || (err_append && *err_append != 0ull);
+  counters[3] = failed ? (1LL << 62) : counters[1] + counters[2];
   *d_new_n = counters[3];
 }
 
@@ -793,6 +799,17 @@ __global__ void __launch_bounds__(APP_THREADS) apply_append_kernel(AppendArgs a)
   }
 }
 
+// Whether two Gaussian arrays share a plane (either may be NULL).
+static bool gauss_alias(const adp_gaussians* a, const adp_gaussians* b) {
+  if (!a || !b) return false;
+  const float* pa[4] = {a->mean_logit, a->logscale, a->quat, a->sh};
+  const float* pb[4] = {b->mean_logit, b->logscale, b->quat, b->sh};
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j)
+      if (pa[i] && pa[i] == pb[j]) return true;
+  return false;
+}
+
 static bool gauss_ok(const adp_gaussians* g) {
   return g && g->mean_logit && g->logscale && g->quat && g->sh && aligned(g->mean_logit, 16) &&
          aligned(g->logscale, 16) && aligned(g->quat, 16) && aligned(g->sh, 16);
@@ -820,6 +837,7 @@ struct PlanCall {
   uint8_t* status;
   int32_t* n_children;
   int64_t* d_new_n;
+  int32_t* d_status;
   long long n, nc, rcap;
   CamSet cs;
 };
@@ -828,7 +846,7 @@ static int plan_args(const adp_gaussians* g, const adp_camera* cams, int32_t n_v
                      const adp_regions* regs, const int32_t* candidates, int64_t n_cand,
                      const int32_t* count, const adp_params* prm, uint8_t* status,
                      int32_t* n_children, int64_t* d_new_n, void* ws, size_t ws_bytes,
-                     PlanCall* pc) {
+                     int32_t* d_status, PlanCall* pc) {
   ADP_CHECK_ARG(gauss_ok(g) || (g && g->n == 0), "bad Gaussian arrays");
   ADP_CHECK_ARG(regs && regs->count && count && d_new_n, "NULL argument");
   ADP_CHECK_ARG(g->n >= 0 && g->n < (1LL << 31), "n out of range");
@@ -854,6 +872,7 @@ static int plan_args(const adp_gaussians* g, const adp_camera* cams, int32_t n_v
   pc->status = status;
   pc->n_children = n_children;
   pc->d_new_n = d_new_n;
+  pc->d_status = d_status;
   return ADP_OK;
 }
 
@@ -923,7 +942,7 @@ static int plan_phase_a(const PlanCall& pc, const SplitWs& w, cudaStream_t st) {
         const bool kept = cc < 0 || cstatus[cc] == ADP_RESET;
         dest[i] = kept ? ((unsigned)pre | (cc >= 0 ? 0x80000000u : 0u)) : 0xffffffffu;
       },
-      n, nullptr, &w.counters[1], w.scan, st);
+      n, nullptr, &w.counters[1], w.scan, st, pc.d_status);
   return rc;
 }
 
@@ -967,10 +986,11 @@ static int plan_phase_b(const PlanCall& pc, const SplitWs& w, cudaStream_t st) {
           return s == ADP_ADAPTIVE ? 1 + nch[cc] : (s == ADP_FALLBACK ? 2 : 0);
         },
         [=] __device__(long long cc, long long pre) { app_off[cc] = pre; }, nc, nullptr,
-        &w.counters[2], w.scan2, st);
+        &w.counters[2], w.scan2, st, pc.d_status);
     if (rc) return rc;
   }
-  new_n_kernel<<<1, 1, 0, st>>>(w.counters, pc.d_new_n);
+  new_n_kernel<<<1, 1, 0, st>>>(w.counters, pc.d_new_n, scan_error_flag(w.scan, pc.n),
+                                nc > 0 ? scan_error_flag(w.scan2, nc) : nullptr);
   ADP_LAUNCH_CHECK();
   return ADP_OK;
 }
@@ -1012,10 +1032,10 @@ extern "C" ADP_API int adp_split_plan(const adp_gaussians* g, const adp_camera* 
                                       const int32_t* count, const adp_params* prm,
                                       uint8_t* status, int32_t* n_children, int64_t* d_new_n,
                                       int64_t* h_new_n, void* ws, size_t ws_bytes,
-                                      adp_stream_t stream) {
+                                      int32_t* d_status, adp_stream_t stream) {
   PlanCall pc;
   int rc = plan_args(g, cams, n_views, regs, candidates, n_cand, count, prm, status, n_children,
-                     d_new_n, ws, ws_bytes, &pc);
+                     d_new_n, ws, ws_bytes, d_status, &pc);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   Carver c(ws, ws_bytes);
@@ -1037,10 +1057,10 @@ extern "C" ADP_API int adp_split_plan_overlapped(const adp_gaussians* g, const a
                                                  const int32_t* count, const adp_params* prm,
                                                  uint8_t* status, int32_t* n_children,
                                                  int64_t* d_new_n, void* ws, size_t ws_bytes,
-                                                 adp_stream_t stream) {
+                                                 int32_t* d_status, adp_stream_t stream) {
   PlanCall pc;
   int rc = plan_args(g, cams, n_views, regs, candidates, n_cand, count, prm, status, n_children,
-                     d_new_n, ws, ws_bytes, &pc);
+                     d_new_n, ws, ws_bytes, d_status, &pc);
   if (rc) return rc;
   AuxStream* aux = nullptr;
   rc = aux_stream(&aux);
@@ -1056,9 +1076,14 @@ extern "C" ADP_API int adp_split_plan_overlapped(const adp_gaussians* g, const a
     ADP_CUDA(cudaStreamWaitEvent(aux->stream, aux->planned, 0));
   }
   rc = plan_phase_b(pc, w, aux->stream);
-  if (rc) return rc;
   std::lock_guard<std::mutex> lock(g_aux_mu);
   ADP_CUDA(cudaEventRecord(aux->merged, aux->stream));
+  if (rc) {
+    // join the fork before reporting the failure, so that a capture in progress
+    // stays valid and no later call waits on a stale event
+    ADP_CUDA(cudaStreamWaitEvent(st, aux->merged, 0));
+    return rc;
+  }
   return ADP_OK;
 }
 
@@ -1093,6 +1118,15 @@ static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
   }
   ADP_CHECK_ARG(aligned(ws, 256), "workspace must be 256-byte aligned");
   ADP_CHECK_ARG(!overlapped || adam, "internal: the overlapped compaction has the Adam step");
+  // outputs must not alias inputs: the compaction reads rows while it writes others,
+  // and in the overlapped calls the proposals read g on the auxiliary stream while
+  // the kept rows are written
+  ADP_CHECK_ARG(!gauss_alias(out, g) && !gauss_alias(out, m_in) && !gauss_alias(out, v_in) &&
+                    !gauss_alias(out, grad) && !gauss_alias(m_out, g) &&
+                    !gauss_alias(m_out, m_in) && !gauss_alias(m_out, v_in) &&
+                    !gauss_alias(v_out, g) && !gauss_alias(v_out, m_in) &&
+                    !gauss_alias(v_out, v_in),
+                "output arrays alias input arrays");
   long long n = g->n, nc = n_cand, rcap = regs->capacity;
   size_t need = split_ws_bytes(n, nc, rcap);
   ADP_CHECK_ARG(ws_bytes >= need, "workspace %zu bytes, need %zu", ws_bytes, need);
@@ -1135,7 +1169,10 @@ static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
     else
       apply_keep_kernel<false><<<kg, 256, 0, st>>>(aa);
   }
-  if (part == ApplyPart::KEEP) return ADP_OK;
+  if (part == ApplyPart::KEEP) {
+    ADP_LAUNCH_CHECK();
+    return ADP_OK;
+  }
   if (overlapped) {  // join the plan's second part
     std::lock_guard<std::mutex> lock(g_aux_mu);
     ADP_CUDA(cudaStreamWaitEvent(st, aux->merged, 0));
@@ -1260,17 +1297,19 @@ namespace adp {
 // compaction applied), with zero moments. Nothing is written if the result does
 // not fit.
 __global__ void clone_kernel(const int* ids, const long long* d_n_clone, long long max_clone,
-                             const unsigned* dest, const long long* counters, GaussPtrs pop,
-                             GaussPtrs mout, GaussPtrs vout, bool has_m, bool has_v, int planes) {
+                             long long n, const unsigned* dest, const long long* counters,
+                             GaussPtrs pop, GaussPtrs mout, GaussPtrs vout, bool has_m,
+                             bool has_v, int planes) {
   long long nc = *d_n_clone;
   if (nc > max_clone) nc = max_clone;
   const long long base = counters[3];
   if (base + nc > pop.n) return;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc;
        t += (long long)gridDim.x * blockDim.x) {
-    const unsigned d = dest[ids[t]];
+    const int id = ids[t];
+    const unsigned d = (id >= 0 && id < n) ? dest[id] : 0xffffffffu;
     const long long j = base + t;
-    if (d >> 31) {  // a split candidate (not a kept row): an all-zero row
+    if (d >> 31) {  // a split candidate (not a kept row) or no id: an all-zero row
       zero_gauss(pop, j, planes);
     } else {
       copy_gauss(pop, (long long)d, pop, j, planes);
@@ -1313,7 +1352,8 @@ extern "C" ADP_API int adp_split_clone(int64_t n, int64_t n_cand, int64_t region
   if (v_out) vo = gp_of(v_out);
   if (max_clone > 0)
     clone_kernel<<<grid_for(max_clone, 256, 148 * 16), 256, 0, st>>>(
-        clone_ids, (const long long*)d_n_clone, max_clone, w.dest, w.counters, gp_of(pop), mo, vo,
+        clone_ids, (const long long*)d_n_clone, max_clone, (long long)n, w.dest, w.counters,
+        gp_of(pop), mo, vo,
         m_out != nullptr, v_out != nullptr, planes);
   clone_size_kernel<<<1, 1, 0, st>>>((const long long*)d_n_clone, max_clone, w.counters, d_new_n);
   ADP_LAUNCH_CHECK();

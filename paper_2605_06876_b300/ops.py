@@ -44,6 +44,19 @@ def workspace(nbytes, device="cuda"):
     return torch.empty(max(int(nbytes), 256), dtype=U8, device=device)
 
 
+def status_word(device="cuda"):
+    """A zeroed device status word for the calls with bounded device waits."""
+    return torch.zeros(1, dtype=I32, device=device)
+
+
+def check_status(word, what="step"):
+    """Reads a device status word (a synchronisation) and raises if a call that
+    was given it reported an error (ADP_ERR_TIMEOUT: a bounded wait gave up)."""
+    v = int(word.item())
+    if v != 0:
+        raise RuntimeError(f"{what}: device status {A.STATUS_NAMES.get(v, v)}")
+
+
 # --------------------------------------------------------------------------- Gaussians
 
 class Gaussians:
@@ -265,7 +278,7 @@ def bin_sort_workspace_size(n, n_views, capacity):
 
 
 def bin_sort(n, pr: Projected, cams, params=None, capacity=None, bins: Bins = None, ws=None,
-             stream=None, grow=True):
+             stream=None, grow=True, status=None):
     """adp_bin_sort. With grow=True an overflowing capacity is enlarged and the call
     repeated (this reads the instance count back, a synchronisation)."""
     params = params or A.default_params()
@@ -281,11 +294,12 @@ def bin_sort(n, pr: Projected, cams, params=None, capacity=None, bins: Bins = No
         ws = workspace(need, dev)
     pc, bc = pr.c(), bins.c()
     A.check(A.lib().adp_bin_sort(n, C.byref(pc), ca, V, C.byref(params), C.byref(bc), _p(ws),
-                                 ws.numel(), _stream(stream)), "adp_bin_sort")
+                                 ws.numel(), _p(status), _stream(stream)), "adp_bin_sort")
     if grow:
         k = int(bins.n_inst.item())
         if k > bins.capacity:
-            return bin_sort(n, pr, cams, params, capacity=int(k * 1.25) + 1, stream=stream)
+            return bin_sort(n, pr, cams, params, capacity=int(k * 1.25) + 1, stream=stream,
+                            status=status)
     return bins
 
 
@@ -318,21 +332,21 @@ def error_stats(img, target, dominant, n, cams, params=None, maps: ErrorMaps = N
     return maps, count, mass
 
 
-def select_topk(mass, n, k, out=None, ws=None, stream=None):
+def select_topk(mass, n, k, out=None, ws=None, stream=None, status=None):
     """adp_select_topk: ids of the k largest masses, ascending."""
     k = min(int(k), int(n))
     out = out if out is not None else torch.empty(max(k, 1), dtype=I32, device=mass.device)
     need = A.lib().adp_select_topk_workspace_size(n)
     if ws is None or ws.numel() < need:
         ws = workspace(need, mass.device)
-    A.check(A.lib().adp_select_topk(_p(mass), n, k, _p(out), _p(ws), ws.numel(), _stream(stream)),
-            "adp_select_topk")
+    A.check(A.lib().adp_select_topk(_p(mass), n, k, _p(out), _p(ws), ws.numel(), _p(status),
+                                    _stream(stream)), "adp_select_topk")
     return out[:k]
 
 
 def error_regions(maps: ErrorMaps, dominant, target, n, cams, candidates, params=None,
                   capacity=None, regions: Regions = None, ws=None, stream=None, labels=False,
-                  grow=True):
+                  grow=True, status=None):
     """adp_error_regions: erosion, 8-connected regions, area filter, statistics."""
     params = params or A.default_params()
     ca = A.cameras(cams)
@@ -348,13 +362,13 @@ def error_regions(maps: ErrorMaps, dominant, target, n, cams, candidates, params
     mc, rc = maps.c(), regions.c()
     A.check(A.lib().adp_error_regions(C.byref(mc), _p(dominant), _p(target), n, ca, V,
                                       _p(candidates) if nc else None, nc, C.byref(params),
-                                      C.byref(rc), _p(ws), ws.numel(), _stream(stream)),
-            "adp_error_regions")
+                                      C.byref(rc), _p(ws), ws.numel(), _p(status),
+                                      _stream(stream)), "adp_error_regions")
     if grow:
         cnt = int(regions.count.item())
         if cnt > regions.capacity:
             return error_regions(maps, dominant, target, n, cams, candidates, params,
-                                 int(cnt * 1.25) + 1, None, None, stream, labels, False)
+                                 int(cnt * 1.25) + 1, None, None, stream, labels, False, status)
     return regions
 
 
@@ -372,7 +386,7 @@ class SplitPlan:
 
 
 def split_plan(g: Gaussians, cams, regions: Regions, candidates, count, params=None, ws=None,
-               stream=None, sync=True):
+               stream=None, sync=True, status_word=None):
     """adp_split_plan: statuses and child counts. With sync=True the new size is read
     back (one synchronisation); otherwise it stays on the device (plan.d_new_n)."""
     params = params or A.default_params()
@@ -390,12 +404,12 @@ def split_plan(g: Gaussians, cams, regions: Regions, candidates, count, params=N
     A.check(A.lib().adp_split_plan(C.byref(gc), ca, len(cams), C.byref(rc), _p(candidates), nc,
                                    _p(count), C.byref(params), _p(status), _p(nch), _p(d_new_n),
                                    C.byref(h_new_n) if sync else None, _p(ws), ws.numel(),
-                                   _stream(stream)), "adp_split_plan")
+                                   _p(status_word), _stream(stream)), "adp_split_plan")
     return SplitPlan(status[:nc], nch[:nc], int(h_new_n.value) if sync else None, ws, d_new_n)
 
 
 def split_plan_overlapped(g: Gaussians, cams, regions: Regions, candidates, count, params=None,
-                          ws=None, stream=None):
+                          ws=None, stream=None, status_word=None):
     """adp_split_plan_overlapped: the statuses and kept rows on the stream, the
     proposals and merges on the library's auxiliary stream; must be followed by
     split_apply_adam(..., overlapped=True), which joins them."""
@@ -413,7 +427,7 @@ def split_plan_overlapped(g: Gaussians, cams, regions: Regions, candidates, coun
     A.check(A.lib().adp_split_plan_overlapped(C.byref(gc), ca, len(cams), C.byref(rc),
                                               _p(candidates), nc, _p(count), C.byref(params),
                                               _p(status), _p(nch), _p(d_new_n), _p(ws),
-                                              ws.numel(), _stream(stream)),
+                                              ws.numel(), _p(status_word), _stream(stream)),
             "adp_split_plan_overlapped")
     return SplitPlan(status[:nc], nch[:nc], None, ws, d_new_n)
 
@@ -479,6 +493,42 @@ def split_apply_adam(g: Gaussians, grad: Gaussians, m_in: Gaussians, v_in: Gauss
     return out, m_out, v_out
 
 
+def train_step_batched(g: Gaussians, cams, target, params=None, bg=(0.0, 0.0, 0.0),
+                       pr: Projected = None, bins: Bins = None, img: Image = None,
+                       maps: ErrorMaps = None, count=None, mass=None, grad: Gaussians = None,
+                       grad2d_accum=None, grad2d_visits=None, ws=None, status=None, stream=None):
+    """adp_train_step_batched: projection, binning, the fused per-tile forward +
+    L1 error + backward over all views, error statistics and the per-Gaussian
+    gradient. Missing buffers are allocated (bins sized from the rectangle count,
+    which reads it back). Returns (pr, bins, img, maps, count, mass, grad)."""
+    params = params or A.default_params()
+    ca = A.cameras(cams)
+    V, n = len(cams), g.n
+    dev = g.mean_logit.device
+    P = n_pixels(cams)
+    pr = pr or Projected.alloc(V * n, dev)
+    if bins is None:
+        project(g, cams, params, pr, stream)
+        bins = Bins.alloc(max(1024, int(pr.tiles.sum().item()) + 1),
+                          n_tiles(cams, params.tile_w, params.tile_h), dev)
+    img = img or Image.alloc(P, dev)
+    maps = maps or ErrorMaps.alloc(P, V, dev)
+    count = count if count is not None else torch.empty(max(n, 1), dtype=I32, device=dev)
+    mass = mass if mass is not None else torch.empty(max(n, 1), dtype=F64, device=dev)
+    grad = grad or Gaussians(n, g.sh_degree, dev, zero=False, row_mask=True)
+    need = A.lib().adp_train_step_batched_workspace_size(n, V, bins.capacity)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    bgc = (C.c_float * 3)(*[float(x) for x in bg])
+    gc, pc, bc, ic, mc, grc = g.c(), pr.c(), bins.c(), img.c(), maps.c(), grad.c()
+    A.check(A.lib().adp_train_step_batched(
+        C.byref(gc), ca, V, _p(target), bgc, C.byref(params), C.byref(pc), C.byref(bc),
+        C.byref(ic), C.byref(mc), _p(count), _p(mass), C.byref(grc), _p(grad2d_accum),
+        _p(grad2d_visits), _p(ws), ws.numel(), _p(status), _stream(stream)),
+        "adp_train_step_batched")
+    return pr, bins, img, maps, count, mass, grad
+
+
 @dataclass
 class DensifySets:
     split: torch.Tensor   # int32 [n]: the first counts[0] entries are the split ids
@@ -487,7 +537,7 @@ class DensifySets:
 
 
 def densify_select(grad2d_accum, grad2d_visits, g: Gaussians, tau_g, tau_s, out: DensifySets = None,
-                   ws=None, stream=None):
+                   ws=None, stream=None, status=None):
     """adp_densify_select: Eq. 2 split candidates and the clone candidates."""
     dev = g.mean_logit.device
     if out is None:
@@ -501,8 +551,8 @@ def densify_select(grad2d_accum, grad2d_visits, g: Gaussians, tau_g, tau_s, out:
     gc = g.c()
     A.check(A.lib().adp_densify_select(_p(grad2d_accum), _p(grad2d_visits), C.byref(gc),
                                        float(tau_g), float(tau_s), _p(out.split), _p(out.clone),
-                                       _p(out.counts), _p(ws), ws.numel(), _stream(stream)),
-            "adp_densify_select")
+                                       _p(out.counts), _p(ws), ws.numel(), _p(status),
+                                       _stream(stream)), "adp_densify_select")
     return out
 
 

@@ -108,6 +108,9 @@ class PlainStep:
         self.mass = torch.empty(n, dtype=torch.float64, device=self.dev)
         self.cand = torch.empty(self.k, dtype=torch.int32, device=self.dev)
         self.adam_t = torch.ones(1, dtype=torch.int32, device=self.dev)  # Adam step, on device
+        # device status word of the calls with bounded waits (scans, top-k barrier):
+        # nonzero once one gave up; read at a sync point by check_status()
+        self.status = ops.status_word(self.dev)
         self.graph = None
         # the error-statistics chain (error map, top-k, regions) runs on a second
         # stream, concurrently with the render backward: both need only the
@@ -156,7 +159,8 @@ class PlainStep:
         mark("project")
         ops.project(g, cams, prm, self.pr)
         mark("bin_sort")
-        ops.bin_sort(n, self.pr, cams, prm, bins=self.bins, ws=self.ws_bins, grow=False)
+        ops.bin_sort(n, self.pr, cams, prm, bins=self.bins, ws=self.ws_bins, grow=False,
+                     status=self.status)
         mark("render")
         ops.render(n, self.pr, self.bins, cams, self.bg, prm, self.img)
         main = torch.cuda.current_stream()
@@ -166,12 +170,13 @@ class PlainStep:
             ops.error_stats(self.img.rgb, self.target, self.img.dominant, n, cams, prm, self.maps,
                             self.count, self.mass)
             mark("select_topk")
-            ops.select_topk(self.mass, n, self.k, self.cand, ws=self.ws_topk)
+            ops.select_topk(self.mass, n, self.k, self.cand, ws=self.ws_topk, status=self.status)
             cand_ready = torch.cuda.Event()
             cand_ready.record(self.side)
             mark("error_regions")
             ops.error_regions(self.maps, self.img.dominant, self.target, n, cams, self.cand, prm,
-                              regions=self.regions, ws=self.ws_regions, grow=False)
+                              regions=self.regions, ws=self.ws_regions, grow=False,
+                              status=self.status)
             mark("error_end")
         if self.dssim_lambda > 0:
             mark("dssim")
@@ -199,10 +204,10 @@ class PlainStep:
         mark("split_plan")
         if overlap:
             plan = ops.split_plan_overlapped(g, cams, self.regions, self.cand, self.count, prm,
-                                             ws=self.ws_split)
+                                             ws=self.ws_split, status_word=self.status)
         else:
             plan = ops.split_plan(g, cams, self.regions, self.cand, self.count, prm,
-                                  ws=self.ws_split, sync=False)
+                                  ws=self.ws_split, sync=False, status_word=self.status)
         mark("split_apply")
         if overlap:  # the kept rows (the dominant kernel), then the join and the appended rows
             args = (g, self.grad, self.m, self.v, plan, self.regions, self.cand, noise, self.adam_t,
@@ -238,8 +243,14 @@ class PlainStep:
         self.graph.replay()
         return self.graph_out
 
+    def check_status(self):
+        """Raises if a bounded device wait of any step so far gave up (reads the
+        status word: a synchronisation)."""
+        ops.check_status(self.status, type(self).__name__)
+
     def check_capacity(self, plan=None):
         """True if the last step's instances, regions (and population) fit their buffers."""
+        self.check_status()
         ok = (int(self.bins.n_inst.item()) <= self.bins.capacity and
               int(self.regions.count.item()) <= self.regions.capacity)
         if plan is not None:
@@ -293,6 +304,59 @@ class ViewStages:
         main.wait_stream(self.side)
 
     def fits(self):
+        return int(self.bins.n_inst.item()) <= self.bins.capacity
+
+
+class BatchedStep:
+    """The view-dependent part of a training step for many views in one call,
+    adp_train_step_batched: projection and binning of all views, one persistent
+    fused forward + L1-error + backward kernel over the (view, tile) work queue,
+    the error statistics and the per-Gaussian gradient summed over views. All
+    buffers are preallocated (the instance capacity from one probing pass), so
+    run() never synchronises and capture() records it as one CUDA graph."""
+
+    def __init__(self, g: ops.Gaussians, cams, target, params=None, bg=(0.0, 0.0, 0.0),
+                 bins_margin=1.15, grad2d=False):
+        self.g, self.cams, self.target = g, list(cams), target
+        self.params = params or A.default_params()
+        self.bg = bg
+        self.dev = g.mean_logit.device
+        n, V = g.n, len(self.cams)
+        self.P = ops.n_pixels(self.cams)
+        self.pr = ops.Projected.alloc(V * n, self.dev)
+        ops.project(g, self.cams, self.params, self.pr)
+        probe = ops.bin_sort(n, self.pr, self.cams, self.params)
+        cap = int(int(probe.n_inst.item()) * bins_margin) + 1024
+        del probe
+        self.bins = ops.Bins.alloc(cap, ops.n_tiles(self.cams, self.params.tile_w,
+                                                     self.params.tile_h), self.dev)
+        self.img = ops.Image.alloc(self.P, self.dev)
+        self.maps = ops.ErrorMaps.alloc(self.P, V, self.dev)
+        self.count = torch.empty(max(n, 1), dtype=torch.int32, device=self.dev)
+        self.mass = torch.empty(max(n, 1), dtype=torch.float64, device=self.dev)
+        self.grad = ops.Gaussians(n, g.sh_degree, self.dev, zero=False, row_mask=True)
+        self.accum = torch.zeros(n, dtype=torch.float32, device=self.dev) if grad2d else None
+        self.visits = torch.zeros(n, dtype=torch.int32, device=self.dev) if grad2d else None
+        self.ws = ops.workspace(A.lib().adp_train_step_batched_workspace_size(n, V, cap), self.dev)
+        self.status = ops.status_word(self.dev)
+        self.graph = None
+        torch.cuda.synchronize()
+
+    def run(self):
+        ops.train_step_batched(self.g, self.cams, self.target, self.params, self.bg, pr=self.pr,
+                               bins=self.bins, img=self.img, maps=self.maps, count=self.count,
+                               mass=self.mass, grad=self.grad, grad2d_accum=self.accum,
+                               grad2d_visits=self.visits, ws=self.ws, status=self.status)
+
+    def capture(self):
+        self.graph = capture_graph(self.run)
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
+
+    def fits(self):
+        ops.check_status(self.status, "BatchedStep")
         return int(self.bins.n_inst.item()) <= self.bins.capacity
 
 
@@ -365,7 +429,8 @@ class DensifyStep(PlainStep):
         mark("project")
         ops.project(g, cams, prm, self.pr)
         mark("bin_sort")
-        ops.bin_sort(n, self.pr, cams, prm, bins=self.bins, ws=self.ws_bins, grow=False)
+        ops.bin_sort(n, self.pr, cams, prm, bins=self.bins, ws=self.ws_bins, grow=False,
+                     status=self.status)
         mark("render")
         ops.render(n, self.pr, self.bins, cams, self.bg, prm, self.img)
         main = torch.cuda.current_stream()
@@ -383,14 +448,15 @@ class DensifyStep(PlainStep):
                             grad2d_accum=self.accum, grad2d_visits=self.visits)
         mark("densify_select")
         ops.densify_select(self.accum, self.visits, g, self.tau_g, self.tau_s, out=self.sets,
-                           ws=self.ws_densify)
+                           ws=self.ws_densify, status=self.status)
         # the regions of the selected candidates (beside the error map's stream) and
         # the candidates' Adam step run concurrently
         self.side.wait_stream(main)
         with torch.cuda.stream(self.side):
             mark("error_regions")
             ops.error_regions(self.maps, self.img.dominant, self.target, n, cams, self.cand, prm,
-                              regions=self.regions, ws=self.ws_regions, grow=False)
+                              regions=self.regions, ws=self.ws_regions, grow=False,
+                              status=self.status)
             mark("error_regions_end")
         mark("adam_rows")
         ops.adam_step_rows(g, self.grad, self.m, self.v, self.cand, self.adam_t, self.lr)
@@ -398,7 +464,7 @@ class DensifyStep(PlainStep):
         main.wait_stream(self.side)
         mark("split_plan")
         plan = ops.split_plan_overlapped(g, cams, self.regions, self.cand, self.count, prm,
-                                         ws=self.ws_split)
+                                         ws=self.ws_split, status_word=self.status)
         mark("split_apply")
         ops.split_apply_adam(g, self.grad, self.m, self.v, plan, self.regions, self.cand, noise,
                              self.adam_t, self.out, self.m_out, self.v_out, prm, self.lr,
@@ -410,6 +476,7 @@ class DensifyStep(PlainStep):
         return self.out, self.m_out, self.v_out, plan
 
     def check_capacity(self, plan=None):
+        self.check_status()
         ok = (int(self.bins.n_inst.item()) <= self.bins.capacity and
               int(self.regions.count.item()) <= self.regions.capacity)
         if plan is not None:

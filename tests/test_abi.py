@@ -40,11 +40,12 @@ def test_every_declared_symbol_is_exported(abi):
 
 def test_struct_layouts_match_header(abi, tmp_path):
     structs = ["adp_camera", "adp_params", "adp_gaussians", "adp_projected", "adp_bins",
-               "adp_image", "adp_error_maps", "adp_regions"]
+               "adp_image", "adp_error_maps", "adp_regions", "adp_constants"]
     mirror = {"adp_camera": abi.AdpCamera, "adp_params": abi.AdpParams,
               "adp_gaussians": abi.AdpGaussians, "adp_projected": abi.AdpProjected,
               "adp_bins": abi.AdpBins, "adp_image": abi.AdpImage,
-              "adp_error_maps": abi.AdpErrorMaps, "adp_regions": abi.AdpRegions}
+              "adp_error_maps": abi.AdpErrorMaps, "adp_regions": abi.AdpRegions,
+              "adp_constants": abi.AdpConstants}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "adpsplit.h"', 'int main(void){']
     for s in structs:
         lines.append(f'printf("{s} size %zu\\n", sizeof({s}));')
@@ -72,7 +73,7 @@ def test_default_params_are_the_papers(abi):
     for k in ("tau_l1", "gamma_d", "gamma_c"):
         assert abs(getattr(p, k) - g[k]) < 1e-7, k
     assert p.tile_w * p.tile_h == 256
-    assert abi.lib().adp_version() == 1
+    assert abi.lib().adp_version() == 2
 
 
 def test_workspace_queries_and_argument_errors(abi):
@@ -107,7 +108,7 @@ def test_overlapped_split_rejects_bad_arguments_before_any_launch(abi):
     g = abi.AdpGaussians(0, 0, 0, None, None, None, None)
     regs = abi.AdpRegions()
     rc = L.adp_split_plan_overlapped(C.byref(g), cams, 1, C.byref(regs), None, 0, None,
-                                     C.byref(p), None, None, None, None, 0, None)
+                                     C.byref(p), None, None, None, None, 0, None, None)
     assert rc == 1 and b"NULL" in L.adp_last_error_string()
     lr = (C.c_float * 6)(*([1e-3] * 6))
     for name in ("adp_split_keep_overlapped", "adp_split_append_overlapped"):
@@ -123,5 +124,43 @@ def test_overlapped_split_rejects_bad_arguments_before_any_launch(abi):
     regs2.count = C.cast(C.pointer(cnt), C.c_void_p)
     rc = L.adp_split_plan_overlapped(C.byref(g), cams, 1, C.byref(regs2), None, 0,
                                      C.cast(C.pointer(cnt), C.c_void_p), C.byref(p), None, None,
-                                     C.cast(C.pointer(cnt), C.c_void_p), unaligned, 4000, None)
+                                     C.cast(C.pointer(cnt), C.c_void_p), unaligned, 4000, None,
+                                     None)
     assert rc == 1 and b"aligned" in L.adp_last_error_string()
+
+
+def test_constants_match_the_oracles(abi):
+    """The constants the kernels hard-code (adp_get_constants) against the oracle's
+    own: the forward conventions and split defaults of its Config and SplitParams,
+    and the real SH basis, whose coefficients are read off the oracle's basis
+    values at a random direction (Y_k / m_k for the header's monomials m_k)."""
+    import numpy as np
+
+    import oracle as O
+
+    c = abi.constants()
+    assert c.version == abi.lib().adp_version() == 2
+    assert c.max_views == abi.ADP_MAX_VIEWS and c.tile_pixels == 256 and c.max_sh_degree == 3
+    assert c.topk_noalloc_max_n == 1 << 22 and c.default_spin_limit > 0
+    cfg, sp = O.Config(), O.SplitParams()
+    d = c.defaults
+    for k in ("near_plane", "low_pass", "alpha_min", "alpha_max", "t_min"):
+        assert abs(getattr(d, k) - getattr(cfg, k)) <= 1e-7 * abs(getattr(cfg, k)), k
+    for k in ("tau_l1", "gamma_d", "gamma_c", "eps_t", "eta", "scale_floor"):
+        assert abs(getattr(d, k) - getattr(sp, k)) <= 1e-7 * abs(getattr(sp, k)), k
+    for k in ("r_erode", "m_min", "n_levels", "n_max"):
+        assert getattr(d, k) == getattr(sp, k), k
+    assert (d.tile_w, d.tile_h) == (cfg.tile_w, cfg.tile_h)
+    rng = np.random.default_rng(5)
+    v = rng.normal(size=3)
+    x, y, z = v / np.linalg.norm(v)
+    mono = [1, y, z, x, x * y, y * z, 2 * z * z - x * x - y * y, x * z, x * x - y * y,
+            y * (3 * x * x - y * y), x * y * z, y * (4 * z * z - x * x - y * y),
+            z * (2 * z * z - 3 * x * x - 3 * y * y), x * (4 * z * z - x * x - y * y),
+            z * (x * x - y * y), x * (x * x - 3 * y * y)]
+    Y = O.sh_basis(3, np.array([[x, y, z]]))[0]
+    want = Y / np.array(mono)
+    got = np.array(list(c.sh_coef), np.float64)
+    np.testing.assert_allclose(got, want, rtol=1e-7)
+    assert abs(c.fov_clamp - 1.3) < 1e-7
+    assert c.gram_schmidt_eps == 1e-12

@@ -22,7 +22,7 @@ def _ptr(t):
 def test_noalloc_rejects_sizes_beyond_its_static_scratch():
     L = _abi.lib()
     n = (1 << 22) + 1
-    rc = L.adp_select_topk_noalloc(None, n, 5, None, None)
+    rc = L.adp_select_topk_noalloc(None, n, 5, None, None, None)
     assert rc == 1
     assert b"exceeds" in L.adp_last_error_string()
 
@@ -45,9 +45,12 @@ def test_noalloc_topk_matches_workspace_topk_on_two_calls():
         ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
         ref = torch.full((k,), -1, dtype=torch.int32, device="cuda")
         got = torch.full((k,), -2, dtype=torch.int32, device="cuda")
-        assert L.adp_select_topk(_ptr(m), n, k, _ptr(ref), _ptr(ws), ws_bytes, stream) == 0
-        assert L.adp_select_topk_noalloc(_ptr(m), n, k, _ptr(got), stream) == 0
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        assert L.adp_select_topk(_ptr(m), n, k, _ptr(ref), _ptr(ws), ws_bytes, _ptr(status),
+                                 stream) == 0
+        assert L.adp_select_topk_noalloc(_ptr(m), n, k, _ptr(got), _ptr(status), stream) == 0
         torch.cuda.synchronize()
+        assert int(status.item()) == 0  # no bounded wait gave up
         assert torch.equal(got, ref)
         # the ids are the k largest masses, ties to the lower id, ascending
         order = np.lexsort((np.arange(n), -mass))[:k]
