@@ -356,14 +356,39 @@ def run_ours(args, rank, world, local_rank):
     eq2 = None
     if not args.no_eq2:
         eq2 = eq2_step(g, cams, target, dev, flush, max(3, min(args.steps, 10)))
-    batched = None
+    batched = batched_c3 = None
     if args.batch_views > 1:
         cfg1 = scenes.CONFIGS[1]
         del stepper.out, stepper.m_out, stepper.v_out
         torch.cuda.empty_cache()
-        batched = batched_vs_plain(g, tg, dev, args.batch_views, max(3, min(args.steps, 20)), flush,
-                                   cfg1["width"], cfg1["height"], cfg1["ring_radius"],
-                                   autotune=args.autotune)
+        reps = max(3, min(args.steps, 10))
+        batched = batched_vs_plain(g, tg, dev, args.batch_views, reps, flush, cfg1["width"],
+                                   cfg1["height"], cfg1["ring_radius"],
+                                   autotune=not args.no_autotune, peak=peak, alu_peak=alu_peak)
+        if not args.no_c3:
+            cfg3 = scenes.CONFIGS[3]
+            g3 = ops.Gaussians.from_scene(scenes.scene_clusters(6, cfg3["n"], 3), dev)
+            tg3 = scenes.scene_clusters(7, cfg3["n"] * 3 // 2, 3)
+            res3 = scenes.uneven_resolutions(7, cfg3["views"])
+            batched_c3 = batched_vs_plain(g3, tg3, dev, cfg3["views"], reps, flush, None, None,
+                                          cfg3["hemisphere_radius"], seed=7, resolutions=res3,
+                                          autotune=not args.no_autotune, peak=peak,
+                                          alu_peak=alu_peak)
+            del g3, tg3
+            torch.cuda.empty_cache()
+    c2 = densify = None
+    if not args.no_workloads:
+        reps = max(3, min(args.steps, 10))
+        c2 = backward_c2(dev, flush, reps, alu_peak)
+        cfg4 = scenes.CONFIGS[4]
+        densify = {
+            "c4_5m_8views": densify_step(dev, flush, reps, cfg4["n"], cfg4["views"], 19,
+                                         cfg4["cand_frac"], 8, "5M Gaussians, 8 views, 20%"),
+            "indoor_1m_20views": densify_step(dev, flush, reps, cfg["n"], 20, 19, 0.1, 2,
+                                              "1M Gaussians, V = 20, N_max = 19"),
+            "outdoor_1m_10views": densify_step(dev, flush, reps, cfg["n"], 10, 9, 0.1, 2,
+                                               "1M Gaussians, V = 10, N_max = 9"),
+        }
     loop = None
     if not args.no_train:
         loop = densify_loop(dev)
@@ -387,6 +412,9 @@ def run_ours(args, rank, world, local_rank):
         "graph": use_graph,
         "stages_ms": {k: round(v, 4) for k, v in per_stage.items()},
         "batched_vs_plain": batched,
+        "batched_c3": batched_c3,
+        "backward_c2": c2,
+        "densify_steps": densify,
         "dssim": dssim,
         "eq2_step": eq2,
         "densify_loop": loop,
@@ -495,16 +523,57 @@ def eq2_step(g, cams, target, dev, flush, steps):
     return res
 
 
+# Algorithmic DRAM bytes of one forward + backward + error-statistics pass over
+# V views, per unit: per Gaussian the parameters read for the forward (240 B), its
+# projected record written (48) and read back by the backward (48), the parameters
+# read by the backward (240) and the gradient written (236); per visible (view,
+# Gaussian) record 52 B; per tile instance the pair written (12), one read and
+# write by the sort (24) and the id and record read by the forward and the
+# backward (2 x 52); per pixel the target (12), the image written (12) and read
+# back (12), T, the count and the dominant id (12) and the error statistics (4).
+BYTES_PER_GAUSSIAN = 240 + 48 + 48 + 240 + 236
+BYTES_PER_RECORD = 52
+BYTES_PER_INSTANCE = 12 + 24 + 2 * 52
+BYTES_PER_PIXEL = 12 + 12 + 12 + 12 + 4
+
+
+def fwd_bwd_stats_bytes(n, records, instances, pixels):
+    return (n * BYTES_PER_GAUSSIAN + records * BYTES_PER_RECORD +
+            instances * BYTES_PER_INSTANCE + pixels * BYTES_PER_PIXEL)
+
+
+def _graph_ms(graph, steps, flush):
+    import torch
+
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        graph.replay()
+    ts = []
+    for _ in range(steps):
+        flush.random_(0, 255)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.mean(ts))
+
+
 def batched_vs_plain(g, tg, dev, n_views, steps, flush, width, height, radius, seed=11,
-                     resolutions=None, autotune=False):
-    """fwd + bwd + error statistics for n_views views: one batched launch per stage
-    over all views against n_views one-view launch sequences (both as CUDA graphs,
-    L2 flushed before each repetition). Returns times and the speedup."""
+                     resolutions=None, autotune=True, peak=None, alu_peak=None):
+    """fwd + bwd + error statistics for n_views views three ways, each a CUDA graph
+    with L2 flushed before every repetition: the fused batched step
+    (adp_train_step_batched: one persistent per-tile forward + error + backward
+    kernel over all views), one launch per stage over all views, and n_views
+    one-view launch sequences (the plain path). With autotune the tile shape and
+    Gaussian batch of all three come from the autotuner."""
     import torch
 
     import scenes
     from paper_2605_06876_b300 import ops
-    from paper_2605_06876_b300.pipeline import ViewStages, capture_graph
+    from paper_2605_06876_b300.pipeline import BatchedStep, ViewStages, capture_graph
 
     if resolutions is None:
         cams = scenes.ring_cameras(seed, n_views, radius, width, height)
@@ -514,47 +583,158 @@ def batched_vs_plain(g, tg, dev, n_views, steps, flush, width, height, radius, s
     prt = ops.project(gt, cams)
     target = ops.render(gt.n, prt, ops.bin_sort(gt.n, prt, cams), cams).rgb.clone()
     del gt, prt
+    torch.cuda.empty_cache()
     params, tune_ms = None, None
     if autotune:
-        from paper_2605_06876_b300.autotune import tune_tile_shape
+        from paper_2605_06876_b300.autotune import tune
 
-        params, tune_ms = tune_tile_shape(g, cams, target)
+        params, tune_ms = tune(g, cams, target, reps=3)
         torch.cuda.empty_cache()
-    batched = ViewStages(g, cams, target, params=params)
+    res = {}
+    fused = BatchedStep(g, cams, target, params=params)
+    res["fused"] = _graph_ms(fused.capture(), steps, flush)
+    if not fused.fits():
+        raise RuntimeError("instance capacity exceeded in the fused batched step")
+    n_vis = int((fused.pr.tiles > 0).sum().item())
+    K = int(fused.bins.n_inst.item())
+    P = fused.P
+    n_eval = int(fused.img.last.sum().item())
+    n_blend = int(fused.img.n_contrib.sum().item())
+    tw, th, batch = fused.params.tile_w, fused.params.tile_h, fused.params.batch
+    del fused
+    torch.cuda.empty_cache()
+    stages = ViewStages(g, cams, target, params=params)
+    res["stages"] = _graph_ms(capture_graph(stages.run), steps, flush)
+    ok = stages.fits()
+    del stages
+    torch.cuda.empty_cache()
     offs = np.cumsum([0] + [c["width"] * c["height"] for c in cams])
     grad = ops.Gaussians(g.n, g.sh_degree, dev, zero=False, row_mask=True)
     plain = [ViewStages(g, [c], target[offs[v]:offs[v + 1]], params=params, grad=grad)
              for v, c in enumerate(cams)]
-    gb = capture_graph(batched.run)
-    gp = capture_graph(lambda: [p.run() for p in plain])
-    stream = torch.cuda.current_stream()
-    res = {}
-    for name, graph in (("batched", gb), ("plain", gp)):
-        for _ in range(3):
-            graph.replay()
-        ts = []
-        for _ in range(steps):
-            flush.random_(0, 255)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            graph.replay()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        res[name] = float(np.mean(ts))
-    ok = batched.fits() and all(p.fits() for p in plain)
+    res["plain"] = _graph_ms(capture_graph(lambda: [p.run() for p in plain]), steps, flush)
+    ok = ok and all(p.fits() for p in plain)
+    del plain
+    torch.cuda.empty_cache()
     if not ok:
         raise RuntimeError("instance capacity exceeded in the batched/plain comparison")
-    return {"views": n_views, "gaussians": g.n,
-            "resolution": f"{width}x{height}" if resolutions is None else "uneven 640x416..1600x1056",
-            "batched_ms": round(res["batched"], 4), "plain_ms": round(res["plain"], 4),
-            "speedup": round(res["plain"] / res["batched"], 3),
-            "views_per_s_batched": round(1e3 * n_views / res["batched"], 1),
-            "views_per_s_plain": round(1e3 * n_views / res["plain"], 1),
-            "tile": [batched.params.tile_w, batched.params.tile_h],
-            "autotune_ms": None if tune_ms is None else {f"{k[0]}x{k[1]}": round(v, 4)
-                                                         for k, v in tune_ms.items()}}
+    nbytes = fwd_bwd_stats_bytes(g.n, n_vis, K, P)
+    flops = n_eval * 2 * FLOP_EVAL + n_blend * (FLOP_BLEND_FWD + FLOP_BLEND_BWD)
+    fused_s = res["fused"] * 1e-3
+    out = {"views": n_views, "gaussians": g.n,
+           "resolution": (f"{width}x{height}" if resolutions is None
+                          else "uneven 640x416..1600x1056"),
+           "batched_ms": round(res["fused"], 4), "stages_ms": round(res["stages"], 4),
+           "plain_ms": round(res["plain"], 4),
+           "speedup": round(res["plain"] / res["fused"], 3),
+           "speedup_stages": round(res["plain"] / res["stages"], 3),
+           "views_per_s_batched": round(n_views / fused_s, 1),
+           "views_per_s_plain": round(1e3 * n_views / res["plain"], 1),
+           "tile": [tw, th], "batch": batch,
+           "counts": {"visible_records": n_vis, "instances": K, "pixels": P,
+                      "pixel_evaluations": n_eval, "blended_pairs": n_blend},
+           "hbm": {"algorithmic_bytes": int(nbytes),
+                   "achieved_gbs": round(nbytes / fused_s / 1e9, 1),
+                   "frac": round(nbytes / fused_s / 1e9 / peak, 4) if peak else None},
+           "fp32": {"flops": int(flops), "achieved_tflops": round(flops / fused_s / 1e12, 2),
+                    "frac": round(flops / fused_s / 1e12 / alu_peak, 4) if alu_peak else None},
+           "autotune_ms": None if tune_ms is None else {f"{k[0]}x{k[1]}/{k[2]}": round(v, 4)
+                                                        for k, v in tune_ms.items()}}
+    return out
+
+
+def backward_c2(dev, flush, steps, alu_peak):
+    """The hand backward at 2,000,000 Gaussians, one 1280x832 view: adp_render_backward
+    (per-pixel walk and per-Gaussian chain rule) of the L1 loss, as a CUDA graph."""
+    import torch
+
+    import scenes
+    from paper_2605_06876_b300 import ops
+    from paper_2605_06876_b300.pipeline import capture_graph
+
+    cfg = scenes.CONFIGS[2]
+    cams = scenes.ring_cameras(5, 1, cfg["ring_radius"], cfg["width"], cfg["height"])
+    g = ops.Gaussians.from_scene(scenes.scene_clusters(4, cfg["n"], 3), dev)
+    gt = ops.Gaussians.from_scene(scenes.scene_clusters(5, cfg["n"] * 3 // 2, 3), dev)
+    prt = ops.project(gt, cams)
+    target = ops.render(gt.n, prt, ops.bin_sort(gt.n, prt, cams), cams).rgb.clone()
+    del gt, prt
+    pr = ops.project(g, cams)
+    bins = ops.bin_sort(g.n, pr, cams)
+    img = ops.render(g.n, pr, bins, cams)
+    grad = ops.Gaussians(g.n, 3, dev, zero=False, row_mask=True)
+    ws = ops.workspace(__import__("paper_2605_06876_b300._abi", fromlist=["lib"]).lib()
+                       .adp_render_backward_workspace_size(g.n, 1), dev)
+    graph = capture_graph(lambda: ops.render_backward(g, pr, bins, img, cams, target=target,
+                                                      grad=grad, ws=ws))
+    ms = _graph_ms(graph, steps, flush)
+    n_eval = int(img.last.sum().item())
+    n_blend = int(img.n_contrib.sum().item())
+    flops = n_eval * FLOP_EVAL + n_blend * FLOP_BLEND_BWD
+    out = {"gaussians": g.n, "resolution": f"{cfg['width']}x{cfg['height']}", "ms": round(ms, 4),
+           "visible": int((pr.tiles > 0).sum().item()), "pixel_evaluations": n_eval,
+           "blended_pairs": n_blend,
+           "fp32": {"achieved_tflops": round(flops / (ms * 1e-3) / 1e12, 2),
+                    "frac": round(flops / (ms * 1e-3) / 1e12 / alu_peak, 4)}}
+    del g, pr, bins, img, grad, ws, graph
+    torch.cuda.empty_cache()
+    return out
+
+
+def densify_step(dev, flush, steps, n, views, n_max, cand_frac, scene_seed, label):
+    """One densification step over `views` sampled views (the fused batched call,
+    top-k candidates, regions, AdpSplit and the compaction with the Adam step), as a
+    CUDA graph; returns its time, the population it grows to, and the time of one
+    training step (fused batched fwd + bwd + error statistics and Adam) on that
+    grown population."""
+    import torch
+
+    import scenes
+    from paper_2605_06876_b300 import _abi as A
+    from paper_2605_06876_b300 import ops
+    from paper_2605_06876_b300.pipeline import BatchedStep, PlainStep, capture_graph
+
+    cams = scenes.ring_cameras(scene_seed + 1, views, 4.0, 1280, 832)
+    gt = ops.Gaussians.from_scene(scenes.scene_clusters(scene_seed + 1, n * 3 // 2, 3), dev)
+    prt = ops.project(gt, cams)
+    target = ops.render(gt.n, prt, ops.bin_sort(gt.n, prt, cams), cams).rgb.clone()
+    del gt, prt
+    torch.cuda.empty_cache()
+    g = ops.Gaussians.from_scene(scenes.scene_clusters(scene_seed, n, 3), dev)
+    prm = A.default_params(n_max=n_max)
+    st = PlainStep(g, cams, target, cand_frac, params=prm, fused_views=True)
+    noise = torch.as_tensor(scenes.fallback_noise(scene_seed, st.k), device=dev)
+    st.capture(noise)
+    ms = _graph_ms(st.graph, steps, flush)
+    out_g, _, _, plan = st.graph_out
+    if not st.check_capacity(plan):
+        raise RuntimeError(f"capacity exceeded in the {label} densification step")
+    new_n = int(plan.d_new_n.item())
+    status = plan.status.long()
+    res = {"workload": label, "gaussians": n, "views": views, "n_max": n_max,
+           "candidates": st.k, "step_ms": round(ms, 4), "new_population": new_n,
+           "adaptive": int((status == A.ADP_ADAPTIVE).sum().item()),
+           "fallback": int((status == A.ADP_FALLBACK).sum().item()),
+           "reset": int((status == A.ADP_RESET).sum().item())}
+    grown = ops.Gaussians(new_n, 3, dev, zero=False)
+    for d, s_ in zip(grown.tensors(), out_g.tensors()):
+        d.copy_(s_[:, :new_n] if s_.dim() == 3 else s_[:new_n])
+    del st, out_g, plan
+    torch.cuda.empty_cache()
+    bs = BatchedStep(grown, cams, target, params=prm)
+    m, v = grown.zeros_like(), grown.zeros_like()
+    t = torch.ones(1, dtype=torch.int32, device=dev)
+
+    def train():
+        bs.run()
+        ops.adam_step(grown, bs.grad, m, v, t)
+
+    res["grown_train_step_ms"] = round(_graph_ms(capture_graph(train), steps, flush), 4)
+    if not bs.fits():
+        raise RuntimeError(f"capacity exceeded in the {label} grown training step")
+    del bs, grown, m, v
+    torch.cuda.empty_cache()
+    return res
 
 
 def count_launches(stepper, noise):
@@ -664,8 +844,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly")
-    ap.add_argument("--autotune", action="store_true",
-                    help="pick the tile shape of the batched comparison with the autotuner")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default tile shape and batch in the batched comparisons")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the 2M backward and the densification-step workloads")
+    ap.add_argument("--no-c3", action="store_true",
+                    help="skip the 3M-Gaussian, 16 uneven views batched comparison")
     ap.add_argument("--batch-views", type=int, default=16,
                     help="views of the batched-vs-plain comparison (0 or 1: skip)")
     ap.add_argument("--no-train", action="store_true",

@@ -138,8 +138,7 @@ typedef struct adp_gaussians {
 } adp_gaussians;
 
 /* Projected Gaussians, one record per (view v, Gaussian i) at index v * n + i.
- * A culled record has tiles_touched = 0 and an empty rect; its other fields are
- * unspecified. */
+ * A culled record has tiles_touched = 0; its other fields are unspecified. */
 typedef struct adp_projected {
   float* xy_opacity_depth; /* float4: 2D mean x, y; opacity; camera depth */
   float* conic;            /* float4: A, B, C, 0 -- inverse 2D covariance [[A, B], [B, C]] */
@@ -445,9 +444,11 @@ ADP_API int adp_render_backward(const adp_gaussians* g, const adp_projected* pr,
  * nothing and leaves the required size in *bins->n_instances), img and maps (all
  * views' pixels), count and mass (n, zeroed by the call), grad (zeroed or masked
  * rows), the optional Eq. 2 accumulators, d_status (see the conventions). The
- * workspace size depends on n, n_views and bins->capacity. Asynchronous and
- * capturable in a CUDA graph. */
-ADP_API size_t adp_train_step_batched_workspace_size(int64_t n, int32_t n_views, int64_t capacity);
+ * workspace size depends on n, n_views and bins->capacity (0 for invalid
+ * arguments). Asynchronous and capturable in a CUDA graph. */
+ADP_API size_t adp_train_step_batched_workspace_size(int64_t n, int32_t n_views,
+                                                     const adp_camera* cams,
+                                                     const adp_params* prm, int64_t capacity);
 ADP_API int adp_train_step_batched(const adp_gaussians* g, const adp_camera* cams, int32_t n_views,
                                    const float* target, const float* bg, const adp_params* prm,
                                    adp_projected* pr, adp_bins* bins, adp_image* img,

@@ -128,7 +128,8 @@ _PROTOS = {
     "adp_render_backward": (C.c_int, [P(AdpGaussians), P(AdpProjected), P(AdpBins), P(AdpImage),
                                       _vp, _vp, P(AdpCamera), _i32, P(C.c_float), P(AdpParams),
                                       P(AdpGaussians), _vp, _vp, _vp, C.c_size_t, _vp]),
-    "adp_train_step_batched_workspace_size": (C.c_size_t, [_i64, _i32, _i64]),
+    "adp_train_step_batched_workspace_size": (C.c_size_t, [_i64, _i32, P(AdpCamera),
+                                                           P(AdpParams), _i64]),
     "adp_train_step_batched": (C.c_int, [P(AdpGaussians), P(AdpCamera), _i32, _vp, P(C.c_float),
                                          P(AdpParams), P(AdpProjected), P(AdpBins), P(AdpImage),
                                          P(AdpErrorMaps), _vp, _vp, P(AdpGaussians), _vp, _vp,

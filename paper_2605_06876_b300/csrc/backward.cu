@@ -141,8 +141,11 @@ struct BwdGaussArgs {
 // Chain rule of one visible Gaussian, summed over views. The SH degree is a
 // template parameter so that every SH array index is a constant and the arrays
 // stay in registers.
+// acc: the thread's column of a [4 * planes][BWDG_THREADS] shared-memory array in
+// which the SH gradient is summed over the views (written to the planes once).
+constexpr int BWDG_THREADS = 128;
 template <int DEG>
-__device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
+__device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i, float* acc) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int planes = (3 * K + 3) / 4;
   float4 ml = a.mean_logit[i], ls = a.logscale[i], q4 = a.quat[i];
@@ -165,7 +168,8 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
   // SH coefficients and their gradient rows, one float4 plane at a time
   const float4* shp = reinterpret_cast<const float4*>(a.sh) + i;
   float4* gshp = reinterpret_cast<float4*>(a.g_sh) + i;
-  bool first_view = true;  // the SH gradient row is stored by the first view, then added to
+#pragma unroll
+  for (int f = 0; f < 4 * planes; ++f) acc[f * BWDG_THREADS] = 0.f;
   for (int v = 0; v < cs.n_views; ++v) {
     long long rec = (long long)v * a.n + i;
     if (a.tiles[rec] <= 0) continue;
@@ -205,19 +209,15 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
     for (int p = 0; p < planes; ++p) {
       const float4 c4 = shp[(long long)p * a.n];
       const float cf[4] = {c4.x, c4.y, c4.z, c4.w};
-      float4 o4 = first_view ? make_float4(0.f, 0.f, 0.f, 0.f) : gshp[(long long)p * a.n];
-      float g4[4] = {o4.x, o4.y, o4.z, o4.w};
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
         const int f = 4 * p + l;
         if (f < 3 * K) {
-          g4[l] = fmaf(gcol[f % 3], Y[f / 3], g4[l]);
+          acc[f * BWDG_THREADS] = fmaf(gcol[f % 3], Y[f / 3], acc[f * BWDG_THREADS]);
           wk[f / 3] += cf[l] * gcol[f % 3];
         }
       }
-      gshp[(long long)p * a.n] = make_float4(g4[0], g4[1], g4[2], g4[3]);
     }
-    first_view = false;
     float gu[3] = {0.f, 0.f, 0.f};
     if (DEG > 0) sh_grad_dot(DEG, u[0], u[1], u[2], wk, gu);
     float ud = gu[0] * u[0] + gu[1] * u[1] + gu[2] * u[2];
@@ -322,6 +322,11 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i) {
     a.g2d_accum[i] += g2d_norm;
     a.g2d_visits[i] += g2d_n;
   }
+#pragma unroll
+  for (int p = 0; p < planes; ++p)
+    gshp[(long long)p * a.n] = make_float4(acc[(4 * p) * BWDG_THREADS], acc[(4 * p + 1) * BWDG_THREADS],
+                                           acc[(4 * p + 2) * BWDG_THREADS],
+                                           acc[(4 * p + 3) * BWDG_THREADS]);
   a.g_ml[i] = make_float4(gmu[0], gmu[1], gmu[2], glogit);
   a.g_ls[i] = make_float4(gls[0], gls[1], gls[2], 0.f);
   a.g_q[i] = make_float4((gw - dotq * qw) * iq, (gx - dotq * qx) * iq, (gy - dotq * qy) * iq,
@@ -377,11 +382,13 @@ __global__ void __launch_bounds__(256) bwd_visible_kernel(const int* tiles, long
 #define ADP_BWDG_MINB 4
 #endif
 template <int DEG>
-__global__ void __launch_bounds__(128, ADP_BWDG_MINB) bwd_gauss_kernel(BwdGaussArgs a, CamSet cs,
-                                                        const int* list,
-                                                        const unsigned long long* n_list) {
+__global__ void __launch_bounds__(BWDG_THREADS, ADP_BWDG_MINB)
+    bwd_gauss_kernel(BwdGaussArgs a, CamSet cs, const int* list,
+                     const unsigned long long* n_list) {
+  constexpr int planes = (3 * (DEG + 1) * (DEG + 1) + 3) / 4;
+  __shared__ float s_acc[4 * planes * BWDG_THREADS];
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t < (long long)*n_list) bwd_one<DEG>(a, cs, list[t]);
+  if (t < (long long)*n_list) bwd_one<DEG>(a, cs, list[t], s_acc + threadIdx.x);
 }
 
 }  // namespace adp
@@ -421,7 +428,8 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   int* list = cv.take<int>(g->n);
   unsigned long long* n_list = cv.take<unsigned long long>(1);
   int* tile_ctr = cv.take<int>(1);
-  ADP_CUDA(cudaMemsetAsync(g2d, 0, sizeof(float4) * 3 * (size_t)g->n * n_views, st));
+  rc = zero_visible_moments(pr->tiles_touched, (long long)g->n * n_views, g2d, st);
+  if (rc) return rc;
   ADP_CUDA(cudaMemsetAsync(n_list, 0, sizeof(unsigned long long), st));
   ADP_CUDA(cudaMemsetAsync(tile_ctr, 0, sizeof(int), st));
   BwdPixArgs pa;
@@ -460,6 +468,28 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
 
 namespace adp {
 
+// Zeroes the pixel-moment rows (three float4) of the visible records only: the
+// per-pixel pass adds to records in tile lists, and the per-Gaussian pass reads
+// records with tiles_touched > 0, so nothing reads the rows of culled records.
+__global__ void zero_visible_kernel(const int* tiles, long long n_rec, float4* g2d) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n_rec;
+       r += (long long)gridDim.x * blockDim.x) {
+    if (tiles[r] > 0) {
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      g2d[3 * r] = z;
+      g2d[3 * r + 1] = z;
+      g2d[3 * r + 2] = z;
+    }
+  }
+}
+
+int zero_visible_moments(const int* tiles, long long n_rec, float4* g2d, cudaStream_t st) {
+  if (n_rec <= 0) return ADP_OK;
+  zero_visible_kernel<<<grid_for(n_rec, 256, 148 * 16), 256, 0, st>>>(tiles, n_rec, g2d);
+  ADP_LAUNCH_CHECK();
+  return ADP_OK;
+}
+
 int backward_gauss_phase(const adp_gaussians* g, const adp_projected* pr, const CamSet& cs,
                          const adp_params* prm, adp_gaussians* grad, float* grad2d_accum,
                          int32_t* grad2d_visits, const float4* g2d, int* list,
@@ -485,12 +515,12 @@ int backward_gauss_phase(const adp_gaussians* g, const adp_projected* pr, const 
   bwd_visible_kernel<<<grid_for(g->n, 256, 148 * 16), 256, 0, st>>>(
       pr->tiles_touched, g->n, n_views, sh_planes(g->sh_degree), ga.g_ml, ga.g_ls, ga.g_q,
       reinterpret_cast<float4*>(grad->sh), grad->rows, list, n_list);
-  const unsigned gb = grid_for(g->n, 128);
+  const unsigned gb = grid_for(g->n, BWDG_THREADS);
   switch (g->sh_degree) {
-    case 0: bwd_gauss_kernel<0><<<gb, 128, 0, st>>>(ga, cs, list, n_list); break;
-    case 1: bwd_gauss_kernel<1><<<gb, 128, 0, st>>>(ga, cs, list, n_list); break;
-    case 2: bwd_gauss_kernel<2><<<gb, 128, 0, st>>>(ga, cs, list, n_list); break;
-    default: bwd_gauss_kernel<3><<<gb, 128, 0, st>>>(ga, cs, list, n_list); break;
+    case 0: bwd_gauss_kernel<0><<<gb, BWDG_THREADS, 0, st>>>(ga, cs, list, n_list); break;
+    case 1: bwd_gauss_kernel<1><<<gb, BWDG_THREADS, 0, st>>>(ga, cs, list, n_list); break;
+    case 2: bwd_gauss_kernel<2><<<gb, BWDG_THREADS, 0, st>>>(ga, cs, list, n_list); break;
+    default: bwd_gauss_kernel<3><<<gb, BWDG_THREADS, 0, st>>>(ga, cs, list, n_list); break;
   }
   ADP_LAUNCH_CHECK();
   return ADP_OK;

@@ -38,7 +38,7 @@ struct FusedArgs {
   float* raw;         // [P] raw L1 error (normalised in place later)
   unsigned* minmax;   // [V][2] float bits of the raw L1 min and max
   float4* g2d;        // [V*n][3] pixel moments of the backward, zeroed
-  int* item_ctr;      // next work item, zeroed
+  int* item_ctr;      // next work item (the tile index), zeroed
 };
 
 constexpr int FUSED_PX = ADP_FUSED_PX;
@@ -164,8 +164,12 @@ static size_t batched_ws_bytes(long long n, int n_views, long long capacity) {
 using namespace adp;
 
 extern "C" ADP_API size_t adp_train_step_batched_workspace_size(int64_t n, int32_t n_views,
+                                                                const adp_camera* cams,
+                                                                const adp_params* prm,
                                                                 int64_t capacity) {
   if (n < 0 || n_views < 1 || capacity < 0) return 0;
+  CamSet cs;
+  if (make_camset(cams, n_views, prm, &cs)) return 0;
   return batched_ws_bytes(n, n_views, capacity);
 }
 
@@ -190,6 +194,7 @@ extern "C" ADP_API int adp_train_step_batched(
                 "alpha_min and t_min must be >= 1e-18 and alpha_max < 1");
   ADP_CHECK_ARG(aligned(ws, 256), "workspace must be 256-byte aligned");
   const long long n = g->n;
+  const int n_items = cs.tile_base[n_views];
   const size_t need = batched_ws_bytes(n, n_views, bins->capacity);
   ADP_CHECK_ARG(ws_bytes >= need, "workspace %zu bytes, need %zu", ws_bytes, need);
   cudaStream_t st = (cudaStream_t)stream;
@@ -211,7 +216,8 @@ extern "C" ADP_API int adp_train_step_batched(
   if (rc) return rc;
   if (n == 0) return ADP_OK;
   // 3. the fused forward + error epilogue + backward over the (view, tile) queue
-  ADP_CUDA(cudaMemsetAsync(w.g2d, 0, sizeof(float4) * 3 * (size_t)n * n_views, st));
+  rc = zero_visible_moments(pr->tiles_touched, n * n_views, w.g2d, st);
+  if (rc) return rc;
   ADP_CUDA(cudaMemsetAsync(w.n_list, 0, sizeof(unsigned long long), st));
   ADP_CUDA(cudaMemsetAsync(w.item_ctr, 0, sizeof(int), st));
   rc = error_minmax_init(maps, n_views, st);
@@ -235,7 +241,6 @@ extern "C" ADP_API int adp_train_step_batched(
   a.minmax = reinterpret_cast<unsigned*>(maps->minmax);
   a.g2d = w.g2d;
   a.item_ctr = w.item_ctr;
-  const int n_items = cs.tile_base[n_views];
   const dim3 block(TileLanes<FUSED_PX>::THREADS);
   int grid = 0;
   switch (stage_size(prm)) {

@@ -198,18 +198,36 @@ __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
   }
 }
 
-// Per-tile ranges from the sorted keys (view-local tile | view << view_shift).
+// Per-tile ranges from the sorted keys (view-local tile | view << view_shift):
+// a list starts where the key differs from the previous one and ends where it
+// differs from the next. Each thread takes four consecutive keys (one 16-byte
+// load; the keys buffer is 256-byte aligned) and the key before them.
 __global__ void tile_ranges_kernel(const unsigned* tkeys, const long long* d_n, CamSet cs,
                                    int view_shift, int2* ranges) {
-  long long N = *d_n;
+  const long long N = *d_n;
   const unsigned local_mask = (1u << view_shift) - 1u;
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < N;
-       j += (long long)gridDim.x * blockDim.x) {
-    unsigned t = tkeys[j];
-    if (t == TILE_NONE) continue;  // instances whose ellipse misses the tile
-    const int g = cs.tile_base[t >> view_shift] + (int)(t & local_mask);
-    if (j == 0 || tkeys[j - 1] != t) ranges[g].x = (int)j;
-    if (j == N - 1 || tkeys[j + 1] != t) ranges[g].y = (int)(j + 1);
+  const long long n4 = (N + 3) / 4;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long j0 = 4 * q;
+    unsigned k[6];  // k[0]: the key before, k[5]: the key after (TILE_NONE at the ends)
+    if (j0 + 4 <= N) {
+      const uint4 v = *reinterpret_cast<const uint4*>(tkeys + j0);
+      k[1] = v.x; k[2] = v.y; k[3] = v.z; k[4] = v.w;
+    } else {
+      for (int e = 0; e < 4; ++e) k[1 + e] = j0 + e < N ? tkeys[j0 + e] : TILE_NONE;
+    }
+    k[0] = j0 > 0 ? tkeys[j0 - 1] : TILE_NONE;
+    k[5] = j0 + 4 < N ? tkeys[j0 + 4] : TILE_NONE;
+#pragma unroll
+    for (int e = 1; e <= 4; ++e) {
+      const unsigned t = k[e];
+      if (t == TILE_NONE) continue;  // instances whose ellipse misses the tile, or past N
+      const int g = cs.tile_base[t >> view_shift] + (int)(t & local_mask);
+      const long long j = j0 + e - 1;
+      if (k[e - 1] != t) ranges[g].x = (int)j;
+      if (k[e + 1] != t) ranges[g].y = (int)(j + 1);
+    }
   }
 }
 

@@ -16,6 +16,9 @@ int error_norm_phase(adp_error_maps* maps, const int32_t* dominant, long long n,
                      const CamSet& cs, const adp_params* prm, int32_t* count, double* mass,
                      cudaStream_t st);
 
+// Zeroes the three float4 pixel-moment rows of every record with tiles > 0.
+int zero_visible_moments(const int* tiles, long long n_rec, float4* g2d, cudaStream_t st);
+
 // The per-Gaussian part of the render backward: from the per-(view, Gaussian)
 // pixel moments in g2d, the chain rule through the EWA projection and the SH
 // colour of every view, summed over views, into grad (zeroed or masked rows);

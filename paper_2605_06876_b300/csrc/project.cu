@@ -1,7 +1,10 @@
 // EWA projection of every Gaussian into every view (Sec. 3, Eq. 1): float4 plane
 // loads, one record of three float4 + int4 rect + tile count per (view,
-// Gaussian). Records of culled pairs get only tiles_touched = 0 and an empty
-// rect; their other fields are left unwritten (nothing reads them).
+// Gaussian). Records of pairs culled by the cheap screen test get only
+// tiles_touched = 0; their other fields are left unwritten (nothing reads them).
+// Blocks take a chunk of Gaussians, screen it cheaply (against every view when
+// there are several, reading each Gaussian's mean and scales once) and project
+// the surviving pairs with full warps.
 #include "gauss_math.cuh"
 
 namespace adp {
@@ -21,37 +24,40 @@ struct ProjectArgs {
   int* tiles;
 };
 
-// Full projection of Gaussian i into view v; writes its record. The SH degree
-// is a template parameter so that the SH arrays stay in registers.
+// The view-independent part of a Gaussian: opacity sigmoid(logit) and the six
+// entries of Sigma = Rg diag(s^2) Rg^T.
+__device__ __forceinline__ float opacity_of(float logit) { return 1.f / (1.f + __expf(-logit)); }
+
+__device__ __forceinline__ void sigma3(float4 ls, float4 q, float* S) {
+  float qn = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+  Mat3 Rg = rot_of_quat(q.x * qn, q.y * qn, q.z * qn, q.w * qn);
+  float s2[3] = {__expf(2.f * ls.x), __expf(2.f * ls.y), __expf(2.f * ls.z)};
+  S[0] = Rg.m[0] * Rg.m[0] * s2[0] + Rg.m[1] * Rg.m[1] * s2[1] + Rg.m[2] * Rg.m[2] * s2[2];
+  S[1] = Rg.m[0] * Rg.m[3] * s2[0] + Rg.m[1] * Rg.m[4] * s2[1] + Rg.m[2] * Rg.m[5] * s2[2];
+  S[2] = Rg.m[0] * Rg.m[6] * s2[0] + Rg.m[1] * Rg.m[7] * s2[1] + Rg.m[2] * Rg.m[8] * s2[2];
+  S[3] = Rg.m[3] * Rg.m[3] * s2[0] + Rg.m[4] * Rg.m[4] * s2[1] + Rg.m[5] * Rg.m[5] * s2[2];
+  S[4] = Rg.m[3] * Rg.m[6] * s2[0] + Rg.m[4] * Rg.m[7] * s2[1] + Rg.m[5] * Rg.m[8] * s2[2];
+  S[5] = Rg.m[6] * Rg.m[6] * s2[0] + Rg.m[7] * Rg.m[7] * s2[1] + Rg.m[8] * Rg.m[8] * s2[2];
+}
+
+// EWA projection of a Gaussian (mean ml, opacity o, Sigma S, SH planes shp[0..P))
+// into view v; writes record v * n + i. Both projection kernels call this, so a
+// view's records do not depend on how many views share the launch.
 template <int DEG>
-__device__ void project_one(const ProjectArgs& a, const CamSet& cs, long long i, int v) {
+__device__ __forceinline__ void project_view(const ProjectArgs& a, const CamSet& cs, long long i,
+                                             int v, float4 ml, float o, const float* S,
+                                             const float4* shp) {
   const adp_camera& cam = cs.cam[v];
   long long rec = (long long)v * a.n + i;
   const float* Rw = cam.R;
-
-  float4 ml = a.mean_logit[i];
   float pcx = Rw[0] * ml.x + Rw[1] * ml.y + Rw[2] * ml.z + cam.t[0];
   float pcy = Rw[3] * ml.x + Rw[4] * ml.y + Rw[5] * ml.z + cam.t[1];
   float pcz = Rw[6] * ml.x + Rw[7] * ml.y + Rw[8] * ml.z + cam.t[2];
-  float o = 1.f / (1.f + __expf(-ml.w));
   bool vis = pcz > a.near_plane && o >= a.alpha_min;
   float4 out0 = make_float4(0.f, 0.f, 0.f, 0.f), out1 = out0, out2 = out0;
   int4 rc = make_int4(0, -1, 0, -1);
   int nt = 0;
   if (vis) {
-    float4 ls = a.logscale[i];
-    float4 q = a.quat[i];
-    float qn = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-    Mat3 Rg = rot_of_quat(q.x * qn, q.y * qn, q.z * qn, q.w * qn);
-    float s2[3] = {__expf(2.f * ls.x), __expf(2.f * ls.y), __expf(2.f * ls.z)};
-    // Sigma = Rg diag(s^2) Rg^T (symmetric, six entries)
-    float S[6];
-    S[0] = Rg.m[0] * Rg.m[0] * s2[0] + Rg.m[1] * Rg.m[1] * s2[1] + Rg.m[2] * Rg.m[2] * s2[2];
-    S[1] = Rg.m[0] * Rg.m[3] * s2[0] + Rg.m[1] * Rg.m[4] * s2[1] + Rg.m[2] * Rg.m[5] * s2[2];
-    S[2] = Rg.m[0] * Rg.m[6] * s2[0] + Rg.m[1] * Rg.m[7] * s2[1] + Rg.m[2] * Rg.m[8] * s2[2];
-    S[3] = Rg.m[3] * Rg.m[3] * s2[0] + Rg.m[4] * Rg.m[4] * s2[1] + Rg.m[5] * Rg.m[5] * s2[2];
-    S[4] = Rg.m[3] * Rg.m[6] * s2[0] + Rg.m[4] * Rg.m[7] * s2[1] + Rg.m[5] * Rg.m[8] * s2[2];
-    S[5] = Rg.m[6] * Rg.m[6] * s2[0] + Rg.m[7] * Rg.m[7] * s2[1] + Rg.m[8] * Rg.m[8] * s2[2];
     // J with x/z, y/z clamped to 1.3x the half field of view
     float inv_z = 1.f / pcz;
     float limx = 1.3f * (float)cam.width / (2.f * cam.fx);
@@ -104,7 +110,7 @@ __device__ void project_one(const ProjectArgs& a, const CamSet& cs, long long i,
         constexpr int P = (3 * K + 3) / 4;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-          float4 c4 = reinterpret_cast<const float4*>(a.sh)[(long long)p * a.n + i];
+          const float4 c4 = shp[p];
           float cv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
           for (int l = 0; l < 4; ++l) {
@@ -128,18 +134,33 @@ __device__ void project_one(const ProjectArgs& a, const CamSet& cs, long long i,
   a.tiles[rec] = nt;
 }
 
+// Full projection of Gaussian i into view v (the one-view kernel's compacted
+// survivors). The SH degree is a template parameter so that the SH arrays stay in
+// registers.
+template <int DEG>
+__device__ void project_one(const ProjectArgs& a, const CamSet& cs, long long i, int v) {
+  constexpr int P = (3 * (DEG + 1) * (DEG + 1) + 3) / 4;
+  const float4 ml = a.mean_logit[i];
+  const float o = opacity_of(ml.w);
+  float S[6];
+  sigma3(a.logscale[i], a.quat[i], S);
+  float4 shp[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) shp[p] = reinterpret_cast<const float4*>(a.sh)[(long long)p * a.n + i];
+  project_view<DEG>(a, cs, i, v, ml, o, S, shp);
+}
+
 // Conservative screen test from the mean, the largest scale and the opacity:
 // the ellipse's box half-width is at most sqrt(k (|J row|^2 s_max^2 + low_pass))
 // with k = 2 ln(o / alpha_min), so a Gaussian whose bound misses the image
 // (with a margin) cannot touch it. Culled records get tiles_touched = 0.
-__device__ bool maybe_visible(const ProjectArgs& a, const CamSet& cs, long long i, int v) {
+__device__ __forceinline__ bool maybe_visible(const ProjectArgs& a, const CamSet& cs, int v,
+                                              float4 ml, float4 ls) {
   const adp_camera& cam = cs.cam[v];
   const float* Rw = cam.R;
-  float4 ml = a.mean_logit[i];
   float pcz = Rw[6] * ml.x + Rw[7] * ml.y + Rw[8] * ml.z + cam.t[2];
-  float o = 1.f / (1.f + __expf(-ml.w));
+  float o = opacity_of(ml.w);
   if (!(pcz > a.near_plane && o >= a.alpha_min)) return false;
-  float4 ls = a.logscale[i];
   float pcx = Rw[0] * ml.x + Rw[1] * ml.y + Rw[2] * ml.z + cam.t[0];
   float pcy = Rw[3] * ml.x + Rw[4] * ml.y + Rw[5] * ml.z + cam.t[1];
   float iz = 1.f / pcz;
@@ -154,6 +175,45 @@ __device__ bool maybe_visible(const ProjectArgs& a, const CamSet& cs, long long 
   float mx = cam.fx * pcx * iz + cam.px, my = cam.fy * pcy * iz + cam.py;
   return mx + hx >= 0.f && mx - hx <= (float)(cam.width - 1) && my + hy >= 0.f &&
          my - hy <= (float)(cam.height - 1);
+}
+
+// A culled record: only its tile count (0) is written; nothing reads the rest.
+__device__ __forceinline__ void write_culled(const ProjectArgs& a, long long rec) {
+  a.tiles[rec] = 0;
+}
+
+// Several views: each block takes a chunk of VIEWS_CHUNK Gaussians; a thread
+// reads one Gaussian's mean and scales once and screens it against every view,
+// the surviving (view, Gaussian) pairs are compacted in shared memory, and the
+// block projects them with full warps (the chunk's parameters are then in L1).
+constexpr int VIEWS_THREADS = 256;
+constexpr int VIEWS_CHUNK = 256;
+template <int DEG>
+__global__ void __launch_bounds__(VIEWS_THREADS) project_views_kernel(ProjectArgs a, CamSet cs) {
+  __shared__ int s_list[VIEWS_CHUNK * ADP_MAX_VIEWS];
+  __shared__ int s_cnt;
+  for (long long c0 = (long long)blockIdx.x * VIEWS_CHUNK; c0 < a.n;
+       c0 += (long long)gridDim.x * VIEWS_CHUNK) {
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < VIEWS_CHUNK; q += VIEWS_THREADS) {
+      const long long i = c0 + q;
+      if (i >= a.n) break;
+      const float4 ml = a.mean_logit[i];
+      const float4 ls = a.logscale[i];
+      for (int v = 0; v < cs.n_views; ++v) {
+        if (maybe_visible(a, cs, v, ml, ls)) s_list[atomicAdd(&s_cnt, 1)] = (v << 16) | q;
+        else write_culled(a, (long long)v * a.n + i);
+      }
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+    for (int e = threadIdx.x; e < cnt; e += VIEWS_THREADS) {
+      const int w = s_list[e];
+      project_one<DEG>(a, cs, c0 + (w & 0xffff), w >> 16);
+    }
+    __syncthreads();
+  }
 }
 
 constexpr int PROJ_THREADS = 256;
@@ -174,12 +234,10 @@ __global__ void __launch_bounds__(PROJ_THREADS) project_kernel(ProjectArgs a, Ca
     for (int q = threadIdx.x; q < PROJ_CHUNK; q += PROJ_THREADS) {
       long long i = c0 + q;
       if (i >= a.n) break;
-      if (maybe_visible(a, cs, i, v)) {
+      if (maybe_visible(a, cs, v, a.mean_logit[i], a.logscale[i])) {
         s_list[atomicAdd(&s_cnt, 1)] = q;
       } else {
-        long long rec = (long long)v * a.n + i;
-        a.tiles[rec] = 0;
-        a.rect[rec] = make_int4(0, -1, 0, -1);
+        write_culled(a, (long long)v * a.n + i);
       }
     }
     __syncthreads();
@@ -226,13 +284,23 @@ extern "C" ADP_API int adp_project(const adp_gaussians* g, const adp_camera* cam
   a.rgb = reinterpret_cast<float4*>(out->rgb);
   a.rect = reinterpret_cast<int4*>(out->rect);
   a.tiles = out->tiles_touched;
-  dim3 grid((unsigned)((g->n + PROJ_CHUNK - 1) / PROJ_CHUNK), n_views);
   cudaStream_t st = (cudaStream_t)stream;
-  switch (g->sh_degree) {
-    case 0: project_kernel<0><<<grid, PROJ_THREADS, 0, st>>>(a, cs); break;
-    case 1: project_kernel<1><<<grid, PROJ_THREADS, 0, st>>>(a, cs); break;
-    case 2: project_kernel<2><<<grid, PROJ_THREADS, 0, st>>>(a, cs); break;
-    default: project_kernel<3><<<grid, PROJ_THREADS, 0, st>>>(a, cs); break;
+  if (n_views == 1) {  // survivors compacted to full warps
+    dim3 grid((unsigned)((g->n + PROJ_CHUNK - 1) / PROJ_CHUNK), n_views);
+    switch (g->sh_degree) {
+      case 0: project_kernel<0><<<grid, PROJ_THREADS, 0, st>>>(a, cs); break;
+      case 1: project_kernel<1><<<grid, PROJ_THREADS, 0, st>>>(a, cs); break;
+      case 2: project_kernel<2><<<grid, PROJ_THREADS, 0, st>>>(a, cs); break;
+      default: project_kernel<3><<<grid, PROJ_THREADS, 0, st>>>(a, cs); break;
+    }
+  } else {  // chunks of Gaussians screened against every view
+    const unsigned grid = (unsigned)((g->n + VIEWS_CHUNK - 1) / VIEWS_CHUNK);
+    switch (g->sh_degree) {
+      case 0: project_views_kernel<0><<<grid, VIEWS_THREADS, 0, st>>>(a, cs); break;
+      case 1: project_views_kernel<1><<<grid, VIEWS_THREADS, 0, st>>>(a, cs); break;
+      case 2: project_views_kernel<2><<<grid, VIEWS_THREADS, 0, st>>>(a, cs); break;
+      default: project_views_kernel<3><<<grid, VIEWS_THREADS, 0, st>>>(a, cs); break;
+    }
   }
   ADP_LAUNCH_CHECK();
   return ADP_OK;

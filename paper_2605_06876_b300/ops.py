@@ -516,7 +516,8 @@ def train_step_batched(g: Gaussians, cams, target, params=None, bg=(0.0, 0.0, 0.
     count = count if count is not None else torch.empty(max(n, 1), dtype=I32, device=dev)
     mass = mass if mass is not None else torch.empty(max(n, 1), dtype=F64, device=dev)
     grad = grad or Gaussians(n, g.sh_degree, dev, zero=False, row_mask=True)
-    need = A.lib().adp_train_step_batched_workspace_size(n, V, bins.capacity)
+    need = A.lib().adp_train_step_batched_workspace_size(n, V, ca, C.byref(params),
+                                                         bins.capacity)
     if ws is None or ws.numel() < need:
         ws = workspace(need, dev)
     bgc = (C.c_float * 3)(*[float(x) for x in bg])

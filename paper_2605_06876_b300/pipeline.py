@@ -74,8 +74,16 @@ class StageTimer:
 class PlainStep:
     def __init__(self, g: ops.Gaussians, cams, target, cand_frac=0.1, params=None,
                  bg=(0.0, 0.0, 0.0), lr=ops.ADAM_LR, bins_margin=1.15, region_margin=1.25,
-                 fused_adam=True, out_capacity=None, dssim_lambda=0.0, overlap_split=True):
+                 fused_adam=True, out_capacity=None, dssim_lambda=0.0, overlap_split=True,
+                 fused_views=False):
         self.g = g
+        # fused_views: projection, binning, compositing, error statistics and the L1
+        # backward of all views as one adp_train_step_batched call (its persistent
+        # per-tile forward + error + backward kernel) instead of five calls with the
+        # error statistics on the side stream; the top-k and regions then follow
+        self.fused_views = bool(fused_views)
+        if self.fused_views and dssim_lambda > 0:
+            raise ValueError("the fused views step differentiates the L1 loss only")
         # fused_adam: the Adam step of the candidates runs before the plan and the
         # compaction applies it to every other row while copying (one pass over
         # parameters and moments instead of two; same result bit for bit)
@@ -139,6 +147,11 @@ class PlainStep:
         self.ws_regions = ops.workspace(A.lib().adp_error_regions_workspace_size(n, self.V, ca), self.dev)
         self.ws_topk = ops.workspace(A.lib().adp_select_topk_workspace_size(n), self.dev)
         self.ws_bwd = ops.workspace(A.lib().adp_render_backward_workspace_size(n, self.V), self.dev)
+        if self.fused_views:
+            import ctypes
+
+            self.ws_views = ops.workspace(A.lib().adp_train_step_batched_workspace_size(
+                n, self.V, ca, ctypes.byref(self.params), self.bins.capacity), self.dev)
         if self.dssim_lambda > 0:
             self.dL = torch.empty((self.P, 3), dtype=torch.float32, device=self.dev)
             self.loss = torch.zeros((self.V, 2), dtype=torch.float64, device=self.dev)
@@ -156,6 +169,8 @@ class PlainStep:
         """One step; returns (new Gaussians, new m, new v, split plan)."""
         g, cams, prm, n = self.g, self.cams, self.params, self.g.n
         mark = timer.mark if timer else (lambda name: None)
+        if self.fused_views:
+            return self._step_fused_views(noise, mark)
         mark("project")
         ops.project(g, cams, prm, self.pr)
         mark("bin_sort")
@@ -221,6 +236,39 @@ class PlainStep:
         else:
             ops.split_apply(g, plan, self.regions, self.cand, noise, prm, m_in=self.m, v_in=self.v,
                             out=self.out, m_out=self.m_out, v_out=self.v_out)
+        mark("end")
+        return self.out, self.m_out, self.v_out, plan
+
+    def _step_fused_views(self, noise, mark):
+        """The step with the view-dependent stages in one adp_train_step_batched call."""
+        g, cams, prm, n = self.g, self.cams, self.params, self.g.n
+        mark("views")
+        ops.train_step_batched(g, cams, self.target, prm, self.bg, pr=self.pr, bins=self.bins,
+                               img=self.img, maps=self.maps, count=self.count, mass=self.mass,
+                               grad=self.grad, ws=self.ws_views, status=self.status)
+        mark("select_topk")
+        ops.select_topk(self.mass, n, self.k, self.cand, ws=self.ws_topk, status=self.status)
+        main = torch.cuda.current_stream()
+        self.side.wait_stream(main)
+        with torch.cuda.stream(self.side):  # the regions beside the candidates' Adam step
+            mark("error_regions")
+            ops.error_regions(self.maps, self.img.dominant, self.target, n, cams, self.cand, prm,
+                              regions=self.regions, ws=self.ws_regions, grow=False,
+                              status=self.status)
+            mark("error_end")
+        mark("adam_rows")
+        ops.adam_step_rows(g, self.grad, self.m, self.v, self.cand, self.adam_t, self.lr)
+        mark("join")
+        main.wait_stream(self.side)
+        mark("split_plan")
+        plan = ops.split_plan_overlapped(g, cams, self.regions, self.cand, self.count, prm,
+                                         ws=self.ws_split, status_word=self.status)
+        mark("split_apply")
+        args = (g, self.grad, self.m, self.v, plan, self.regions, self.cand, noise, self.adam_t,
+                self.out, self.m_out, self.v_out, prm, self.lr)
+        ops.split_apply_adam(*args, overlapped=True, part="keep")
+        mark("split_append")
+        ops.split_apply_adam(*args, overlapped=True, part="append")
         mark("end")
         return self.out, self.m_out, self.v_out, plan
 
@@ -337,7 +385,10 @@ class BatchedStep:
         self.grad = ops.Gaussians(n, g.sh_degree, self.dev, zero=False, row_mask=True)
         self.accum = torch.zeros(n, dtype=torch.float32, device=self.dev) if grad2d else None
         self.visits = torch.zeros(n, dtype=torch.int32, device=self.dev) if grad2d else None
-        self.ws = ops.workspace(A.lib().adp_train_step_batched_workspace_size(n, V, cap), self.dev)
+        import ctypes
+
+        self.ws = ops.workspace(A.lib().adp_train_step_batched_workspace_size(
+            n, V, A.cameras(self.cams), ctypes.byref(self.params), cap), self.dev)
         self.status = ops.status_word(self.dev)
         self.graph = None
         torch.cuda.synchronize()

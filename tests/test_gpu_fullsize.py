@@ -9,7 +9,12 @@ otherwise properties that hold at any size.
   pixels of the smallest and largest view match the oracle's brute force.
 - 5,000,000 Gaussians, 8 views at 1280x832, 20% candidates: one full step (error
   statistics over the 8 views, top-k, regions, AdpSplit with the fused Adam
-  compaction) checked by the invariants of each stage.
+  compaction) checked by the invariants of each stage, then stage by stage
+  against the oracle on the GPU's own image, dominant map and updated
+  parameters: E, M and B bit for bit, counts and masses exactly, the top-k ids,
+  the region table (integers exactly, statistics within 1e-12), and the oracle's
+  split of those regions (statuses and child counts exactly, appended centres
+  within 1e-6).
 """
 import math
 
@@ -181,6 +186,7 @@ def test_densification_round_5m_8_views_invariants():
             np.testing.assert_allclose(ml_o[j, :3], mu, rtol=1e-6, atol=1e-6)
             np.testing.assert_allclose(ls_o[j, :3], ls_p[i, :3] - math.log(2 * st.params.eta),
                                        rtol=1e-6, atol=1e-6)
+    _c4_against_oracle(st, cams, target, plan, out, noise)
     # ADAPTIVE: parent copy with opacity o / (N + 1); children no larger than the parent
     ad_idx = np.nonzero(np_(adaptive))[0]
     for c in ad_idx[:200]:
@@ -191,3 +197,60 @@ def test_densification_round_5m_8_views_invariants():
         smax = float(np.exp(ls_p[i, :3].astype(np.float64)).max())
         kids = np.exp(ls_o[j + 1:j + 1 + N, :3].astype(np.float64))
         assert kids.max() <= smax * (1 + 1e-5)
+
+
+def _c4_against_oracle(st, cams, target, plan, out, noise):
+    """The 5M-Gaussian, 8-view step against the oracle, stage-isolated: each stage
+    of the oracle takes the GPU's inputs of that stage (the float32 image and
+    dominant map, the candidates, the parameters the plan read)."""
+    n, k = st.g.n, st.k
+    sp = O.SplitParams()
+    img, tgt, D = np_(st.img.rgb), np_(target), np_(st.img.dominant)
+    E_g, mask_g = np_(st.maps.E), np_(st.maps.mask)
+    count, mass = np.zeros(n, np.int32), np.zeros(n, np.float64)
+    offs = np.cumsum([0] + [c["width"] * c["height"] for c in cams])
+    errs = []
+    for v, cam in enumerate(cams):
+        W, H = cam["width"], cam["height"]
+        sl = slice(offs[v], offs[v + 1])
+        em = O.error_map(img[sl].reshape(H, W, 3), tgt[sl].reshape(H, W, 3), sp.tau_l1,
+                         sp.n_levels)
+        assert np.array_equal(em["E"], E_g[sl])
+        assert np.array_equal(em["M"], mask_g[sl] & 1)
+        assert np.array_equal(em["B"], mask_g[sl] >> 4)
+        O.gauss_stats(em["M"], D[sl], em["E"], n, count, mass)
+        errs.append(em)
+    assert np.array_equal(count, np_(st.count)) and np.array_equal(mass, np_(st.mass))
+    cand = O.topk_mass(mass, k)
+    assert np.array_equal(cand, np_(st.cand))
+    flag = np.zeros(n, np.uint8)
+    flag[cand] = 1
+    parts = []
+    for v, cam in enumerate(cams):
+        W, H = cam["width"], cam["height"]
+        sl = slice(offs[v], offs[v + 1])
+        Me = O.erode(errs[v]["M"], W, H, sp.r_erode)
+        assert np.array_equal(Me, (mask_g[sl] >> 1) & 1)
+        parts.append(O.regions(v, W, H, Me, errs[v]["B"], D[sl], n, flag,
+                               tgt[sl].reshape(H, W, 3), sp.m_min))
+    rg = O.concat_regions(parts)
+    got = st.regions.to_numpy()
+    assert len(rg["view"]) == len(got["view"]) > 0
+    for key in ("view", "parent", "label", "band", "moments"):
+        assert np.array_equal(rg[key], got[key]), key
+    np.testing.assert_allclose(got["stats"], rg["stats"], rtol=1e-12, atol=1e-12)
+    # the split of those regions, from the parameters the plan read (the
+    # candidates after their Adam step, every other row as before the step)
+    theta = O.theta_of(st.g.to_scene())
+    res = O.split(theta, 3, cams, rg, cand, count, np_(noise).astype(np.float64).reshape(k, 2, 3),
+                  sp)
+    assert np.array_equal(res["status"], np_(plan.status))
+    assert np.array_equal(res["n_children"], np_(plan.n_children))
+    new_n = int(plan.d_new_n.item())
+    assert res["new_n"] == new_n
+    keep = np.ones(n, bool)
+    keep[cand] = False
+    keep[cand[res["status"] == O.RESET]] = True
+    nk = int(keep.sum())
+    ml = np_(out.mean_logit)[nk:new_n, :3].astype(np.float64)
+    np.testing.assert_allclose(ml, res["theta"][nk:, :3], rtol=1e-6, atol=1e-6)

@@ -78,24 +78,30 @@ def test_graph_replay_matches_eager_step():
     assert int(graphed.adam_t.item()) == 2
 
 
-def test_autotuner_picks_a_legal_shape_with_identical_results():
-    from paper_2605_06876_b300.autotune import SHAPES, tune_tile_shape
-    from paper_2605_06876_b300.pipeline import ViewStages
+def test_autotuner_picks_a_legal_shape_and_batch_with_identical_results():
+    """The tuner times the fused batched step under every tile shape and per-block
+    Gaussian batch and keeps the fastest; the tuned step gives the same image,
+    error statistics and gradient as the default one."""
+    from paper_2605_06876_b300.autotune import BATCHES, SHAPES, tune
+    from paper_2605_06876_b300.pipeline import BatchedStep
 
     sc, cams = small_cluster_inputs(20000, 320, 208, views=2, seed=41)
     g = ops.Gaussians.from_scene(sc, DEV)
     P = sum(c["width"] * c["height"] for c in cams)
     target = torch.rand((P, 3), device=DEV)
-    params, times = tune_tile_shape(g, cams, target, reps=2)
-    assert (params.tile_w, params.tile_h) in SHAPES and len(times) == len(SHAPES)
-    assert times[(params.tile_w, params.tile_h)] == min(times.values())
-    ref = ViewStages(g, cams, target)
+    params, times = tune(g, cams, target, reps=2)
+    best = (params.tile_w, params.tile_h, params.batch)
+    assert best[:2] in SHAPES and best[2] in BATCHES
+    assert len(times) == len(SHAPES) * len(BATCHES) and times[best] == min(times.values())
+    ref = BatchedStep(g, cams, target)
     ref.run()
-    got = ViewStages(g, cams, target, params=params)
+    got = BatchedStep(g, cams, target, params=params)
     got.run()
     torch.cuda.synchronize()
     assert torch.equal(ref.img.rgb, got.img.rgb) and torch.equal(ref.img.dominant, got.img.dominant)
     assert torch.equal(ref.count, got.count) and torch.equal(ref.mass, got.mass)
+    for a, b in zip(ref.grad.dense().tensors(), got.grad.dense().tensors()):
+        torch.testing.assert_close(a, b, rtol=1e-4, atol=1e-6 * float(b.abs().max()))
 
 
 def test_fused_adam_compaction_equals_adam_then_apply():
