@@ -737,6 +737,44 @@ def densify_step(dev, flush, steps, n, views, n_max, cand_frac, scene_seed, labe
     return res
 
 
+def run_batched_only(args, local_rank):
+    """Only the fused batched step (fwd + bwd + error statistics over --batch-views
+    ring views of the single-view workload's scene, or --gaussians of it), as a
+    CUDA graph: --warmup replays, then --steps timed ones with L2 flushed before
+    each. For profiler captures of the batched kernels."""
+    import torch
+
+    import scenes
+    from __graft_entry__ import build
+    from paper_2605_06876_b300 import _abi as A
+    from paper_2605_06876_b300 import ops
+    from paper_2605_06876_b300.pipeline import BatchedStep
+
+    build()
+    torch.cuda.set_device(local_rank)
+    dev = f"cuda:{local_rank}"
+    cfg = dict(scenes.CONFIGS[1])
+    n = args.gaussians or cfg["n"]
+    V = max(1, args.batch_views)
+    cams = scenes.ring_cameras(11, V, cfg["ring_radius"], cfg["width"], cfg["height"])
+    gt = ops.Gaussians.from_scene(scenes.scene_clusters(3, n * 3 // 2, 3), dev)
+    prt = ops.project(gt, cams)
+    target = ops.render(gt.n, prt, ops.bin_sort(gt.n, prt, cams), cams).rgb.clone()
+    del gt, prt
+    g = ops.Gaussians.from_scene(scenes.scene_clusters(2, n, 3), dev)
+    st = BatchedStep(g, cams, target, params=A.default_params(batch=args.batch))
+    graph = st.capture()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        graph.replay()
+    ms = _graph_ms(graph, args.steps, flush) if args.steps > 0 else None
+    if not st.fits():
+        raise RuntimeError("instance capacity exceeded")
+    return {"metric": "batched fwd+bwd+error-stats views/s", "views": V, "gaussians": n,
+            "batch": st.params.batch, "ms": ms,
+            "value": None if ms is None else round(1e3 * V / ms, 1), "unit": "views/s"}
+
+
 def count_launches(stepper, noise):
     """Kernels of this library launched by one step (CUPTI trace of one extra step,
     outside the timed region)."""
@@ -846,6 +884,10 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default tile shape and batch in the batched comparisons")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="time only the fused batched step (--batch-views views; profiler use)")
+    ap.add_argument("--batch", type=int, default=64,
+                    help="Gaussians staged per compositing batch in --only-batched")
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the 2M backward and the densification-step workloads")
     ap.add_argument("--no-c3", action="store_true",
@@ -868,6 +910,9 @@ def main():
         res = run_reference(args, rank, world)
         if res is not None:
             print(json.dumps(res))
+        return
+    if args.only_batched:
+        print(json.dumps(run_batched_only(args, local_rank)))
         return
     if world > 1:
         import torch

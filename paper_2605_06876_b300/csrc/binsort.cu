@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
   __shared__ int s_i[DUP_SUB + 1];          // Gaussian id
   __shared__ int s_org[DUP_SUB + 1];        // first tile column | first tile row << 16
   __shared__ int s_wv[DUP_SUB + 1];         // rectangle width | view << 16 | (multi-tile) << 31
+  __shared__ float s_iw[DUP_SUB + 1];       // 1 / rectangle width
   __shared__ float4 s_e0[DUP_SUB + 1];      // 2D mean, conic A, B
   __shared__ float4 s_e1[DUP_SUB + 1];      // conic C, cut-off k, -B / C, -B / A
   __shared__ int s_rec[DUP_SUB];            // record starting at each slot of the sub-chunk
@@ -125,6 +126,7 @@ __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
         s_i[q] = (int)(p - (unsigned long long)v * n);
         s_org[q] = r.x | (r.z << 16);
         s_wv[q] = w | (v << 16) | (multi ? (int)0x80000000u : 0);
+        s_iw[q] = 1.f / (float)w;
         s_e0[q] = make_float4(xy.x, xy.y, cn.x, cn.y);
         s_e1[q] = multi ? make_float4(cn.z, 2.f * __logf(xy.z / alpha_min), -cn.y / cn.z,
                                       -cn.y / cn.x)
@@ -163,7 +165,18 @@ __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
         const int org = s_org[q], wv = s_wv[q];
         const int w = wv & 0xffff, v = (wv >> 16) & 0x7fff;
         const int tt = kk - s_off[sa + q];
-        const int ty = (org >> 16) + tt / w, tx = (org & 0xffff) + tt % w;
+        // tt = row * w + col: the quotient from the float reciprocal (tt < 2^16, so
+        // it is off by at most one) and one correction step
+        int qd = __float2int_rd(__int2float_rn(tt) * s_iw[q]);
+        int rm = tt - qd * w;
+        if (rm < 0) {
+          --qd;
+          rm += w;
+        } else if (rm >= w) {
+          ++qd;
+          rm -= w;
+        }
+        const int ty = (org >> 16) + qd, tx = (org & 0xffff) + rm;
         unsigned key = (unsigned)(ty * cs.tiles_x[v] + tx) | ((unsigned)v << view_shift);
         if (wv < 0) {  // a one-tile rectangle always meets its ellipse
           const float4 e0 = s_e0[q];
