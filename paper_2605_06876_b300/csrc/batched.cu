@@ -17,6 +17,9 @@
 #ifndef ADP_FUSED_PX
 #define ADP_FUSED_PX 4
 #endif
+#ifndef ADP_FUSED_MINB  // resident blocks per SM the register budget is sized for
+#define ADP_FUSED_MINB 1
+#endif
 
 namespace adp {
 
@@ -44,7 +47,7 @@ struct FusedArgs {
 constexpr int FUSED_PX = ADP_FUSED_PX;
 
 template <int PX, int STAGE>
-__global__ void __launch_bounds__(TileLanes<PX>::THREADS, 1)
+__global__ void __launch_bounds__(TileLanes<PX>::THREADS, ADP_FUSED_MINB)
     fused_tile_kernel(FusedArgs a, CamSet cs) {
   constexpr int NT = TileLanes<PX>::THREADS;
   constexpr int NP = PX / 2;

@@ -8,8 +8,9 @@
 // order. This moves far fewer bytes than sorting 64-bit keys over all
 // instances, and ties in depth resolve to the lower id because every pass is
 // stable over id-ordered input. Instances whose alpha ellipse misses their tile
-// (the rectangle of tiles overestimates a rotated ellipse) are dropped from the
-// tile lists, which changes no pixel's contributors.
+// (the rectangle of tiles overestimates a rotated ellipse, about a fifth of the
+// instances) are dropped by the first pass of the tile sort, which changes no
+// pixel's contributors.
 #include <algorithm>
 
 #include "common.cuh"
@@ -27,23 +28,24 @@ __global__ void clamp_count_kernel(const long long* K, long long cap,
 
 // Load-balanced duplication: each CTA takes a chunk of DUP_CHUNK consecutive
 // instances. The record owning the chunk's first instance comes from the offset
-// scan (chunk_first), the chunk's record offsets are staged in shared memory, and
-// the chunk is processed in sub-chunks of DUP_SUB instances: the (at most
-// DUP_SUB + 1) records a sub-chunk overlaps are loaded once, one thread each,
-// into shared memory (view, id, tile origin and width, 2D mean, conic and the
-// alpha cut-off), each record also marking the slot where it starts, and an
-// inclusive max-scan over the slots gives every instance its record. Each thread
-// takes two consecutive instances. k's tile is its position within the record's
-// tile rectangle (row-major). Balanced whatever a Gaussian's footprint, no
-// dependent global loads and no search per instance, and consecutive threads
-// write consecutive instance pairs. A chunk is one tile of the radix sort, so the CTA also writes that
-// tile's histogram of the tile sort's first digit (the low 8 bits of the key).
+// scan (chunk_first), and the chunk's record offsets are staged in shared memory.
+// The records the chunk overlaps (usually a few dozen, at most DUP_CHUNK + 1) are
+// loaded once, up to DUP_REC at a time, one thread each, into shared memory (view,
+// id, tile origin, width and its reciprocal, 2D mean, conic and the alpha cut-off);
+// each record marks the slot of the chunk where it starts, and an inclusive
+// max-scan over the slots gives every instance its record, with no search per
+// instance. Each thread takes DUP_ITEMS consecutive instances. k's tile is its
+// position within the record's tile rectangle (row-major). Balanced whatever a
+// Gaussian's footprint, one round of dependent loads per chunk (not per sub-chunk),
+// and each thread stores its instances as 16-byte vectors. A chunk is one tile of
+// the radix sort, so the CTA also writes that tile's histogram of the tile sort's
+// first digit (the low 8 bits of the key).
 constexpr int DUP_CHUNK = 2048;
-constexpr int DUP_SUB = 512;
 constexpr int DUP_THREADS = 256;
+constexpr int DUP_ITEMS = DUP_CHUNK / DUP_THREADS;
+constexpr int DUP_REC = 512;
 static_assert(DUP_CHUNK == RS_TILE, "a duplication chunk is one radix-sort tile");
-static_assert(DUP_CHUNK % DUP_SUB == 0, "sub-chunks tile the chunk");
-static_assert(DUP_SUB == 2 * DUP_THREADS, "each thread takes two slots of a sub-chunk");
+static_assert(DUP_ITEMS == 8, "two 16-byte stores of keys and of ids per thread");
 constexpr unsigned TILE_NONE = 0xffffffffu;  // sorts after every real tile
 
 // Whether the ellipse q(d) = d^T C d <= k around the 2D mean (the pixels where
@@ -72,36 +74,27 @@ __device__ __forceinline__ bool ellipse_meets_rect(float mx, float my, float A, 
   return qmin <= k * 1.0001f + 1e-3f;
 }
 
-// Last q in [lo, hi] with off[q] <= k (off[lo] <= k).
-__device__ __forceinline__ int last_le_s(const int* off, int lo, int hi, int k) {
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (off[mid] <= k) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
 __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
     const unsigned* vvals, const long long* offs, const int* chunk_first, const long long* d_nvis,
     const long long* d_K, long long cap, const int4* rect, const float4* xyod, const float4* conic,
     float alpha_min, long long n, CamSet cs, int view_shift, unsigned* tkeys, int* inst,
-    bool inst_pairs, unsigned* hist, long long tiles_max) {
-  __shared__ int s_off[DUP_CHUNK + 1];      // record offsets of the chunk
-  __shared__ int s_i[DUP_SUB + 1];          // Gaussian id
-  __shared__ int s_org[DUP_SUB + 1];        // first tile column | first tile row << 16
-  __shared__ int s_wv[DUP_SUB + 1];         // rectangle width | view << 16 | (multi-tile) << 31
-  __shared__ float s_iw[DUP_SUB + 1];       // 1 / rectangle width
-  __shared__ float4 s_e0[DUP_SUB + 1];      // 2D mean, conic A, B
-  __shared__ float4 s_e1[DUP_SUB + 1];      // conic C, cut-off k, -B / C, -B / A
-  __shared__ int s_rec[DUP_SUB];            // record starting at each slot of the sub-chunk
+    bool inst_vec, unsigned* hist, long long tiles_max) {
+  __shared__ int s_off[DUP_CHUNK + 1];  // record offsets of the chunk (the first may be < 0)
+  __shared__ int s_i[DUP_REC];          // Gaussian id
+  __shared__ int s_org[DUP_REC];        // first tile column | first tile row << 16
+  __shared__ int s_wv[DUP_REC];         // rectangle width | view << 16 | (multi-tile) << 31
+  __shared__ float s_iw[DUP_REC];       // 1 / rectangle width
+  __shared__ float4 s_e0[DUP_REC];      // 2D mean, conic A, B
+  __shared__ float4 s_e1[DUP_REC];      // conic C, cut-off k, -B / C, -B / A
+  __shared__ int s_rec[DUP_CHUNK];      // 1 + batch record starting at each slot, else 0
   __shared__ int s_wm[DUP_THREADS / 32];
   __shared__ unsigned s_h[RS_BINS];
   const long long N = *d_nvis, K = *d_K;  // K: the clamped count (0 = bin nothing)
   if (K == 0 || K > cap || N == 0) return;
   const long long n_chunks = (K + DUP_CHUNK - 1) / DUP_CHUNK;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int e = threadIdx.x; e < DUP_SUB; e += DUP_THREADS) s_rec[e] = 0;
+  const int e0 = DUP_ITEMS * (int)threadIdx.x;  // the thread's first slot
+  for (int e = threadIdx.x; e < DUP_CHUNK; e += DUP_THREADS) s_rec[e] = 0;
   for (long long t = blockIdx.x; t < n_chunks; t += gridDim.x) {
     const long long k0 = t * DUP_CHUNK;
     const int kn = (int)min((long long)DUP_CHUNK, K - k0);  // instances in the chunk
@@ -111,13 +104,19 @@ __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
     for (int q = threadIdx.x; q < cnt; q += DUP_THREADS) s_off[q] = (int)(offs[j0 + q] - k0);
     for (int d = threadIdx.x; d < RS_BINS; d += DUP_THREADS) s_h[d] = 0u;
     __syncthreads();
-    for (int a0 = 0; a0 < kn; a0 += DUP_SUB) {
-      const int a1 = min(a0 + DUP_SUB, kn);
-      // records of the sub-chunk (the same search in every thread)
-      const int sa = last_le_s(s_off, 0, cnt - 1, a0);
-      const int sb = last_le_s(s_off, sa, cnt - 1, a1 - 1);
-      for (int q = threadIdx.x; q <= sb - sa; q += DUP_THREADS) {
-        const unsigned p = vvals[j0 + sa + q];
+    unsigned keys[DUP_ITEMS];
+    int ids[DUP_ITEMS];
+#pragma unroll
+    for (int h = 0; h < DUP_ITEMS; ++h) {
+      keys[h] = TILE_NONE;
+      ids[h] = 0;
+    }
+    for (int rb = 0; rb < cnt; rb += DUP_REC) {  // record batches (one in the common case)
+      const int rn = min(DUP_REC, cnt - rb);
+      const int a0 = max(s_off[rb], 0);                        // the batch's slots
+      const int a1 = rb + rn < cnt ? min(s_off[rb + rn], kn) : kn;  // [a0, a1)
+      for (int q = threadIdx.x; q < rn; q += DUP_THREADS) {
+        const unsigned p = vvals[j0 + rb + q];
         const int v = (int)(p / (unsigned long long)n);
         const int4 r = rect[p];
         const float4 xy = xyod[p], cn = conic[p];
@@ -131,41 +130,40 @@ __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
         s_e1[q] = multi ? make_float4(cn.z, 2.f * __logf(xy.z / alpha_min), -cn.y / cn.z,
                                       -cn.y / cn.x)
                         : make_float4(0.f, 0.f, 0.f, 0.f);
-        // the first record may start before the sub-chunk; every other one starts
-        // inside it, each at its own slot
-        s_rec[q == 0 ? 0 : s_off[sa + q] - a0] = q;
+        // the chunk's first record may start before it (mark slot 0); the last one
+        // listed may start exactly at the next chunk (no slot here)
+        const int slot = max(s_off[rb + q], 0);
+        if (slot < kn) s_rec[slot] = q + 1;
       }
       __syncthreads();
-      // each thread takes two consecutive slots; a slot's record is the largest
-      // record index marked at or before it (an inclusive max-scan)
-      const int e0i = 2 * (int)threadIdx.x;
-      const int m0 = s_rec[e0i], m1 = s_rec[e0i + 1];
-      int run = max(m0, m1);
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, run, o);
-        if (lane >= o) run = max(run, y);
+      // each slot's record: the largest mark at or before it (an inclusive max-scan)
+      int mk[DUP_ITEMS];
+      int run = 0;
+#pragma unroll
+      for (int h = 0; h < DUP_ITEMS; ++h) {
+        run = max(run, s_rec[e0 + h]);
+        mk[h] = run;
       }
-      if (lane == 31) s_wm[warp] = run;
-      int before = __shfl_up_sync(0xffffffffu, run, 1);
+      int inc = run;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc = max(inc, y);
+      }
+      if (lane == 31) s_wm[warp] = inc;
+      int before = __shfl_up_sync(0xffffffffu, inc, 1);
       if (lane == 0) before = 0;
       __syncthreads();
       for (int w2 = 0; w2 < warp; ++w2) before = max(before, s_wm[w2]);
-      s_rec[e0i] = 0;  // cleared for the next sub-chunk (each thread its own slots)
-      s_rec[e0i + 1] = 0;
-      const int qs[2] = {max(before, m0), max(before, max(m0, m1))};
-      unsigned keys[2];
-      int ids[2];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int kk = a0 + e0i + h;
-        keys[h] = TILE_NONE;
-        ids[h] = 0;
-        if (kk >= a1) continue;
-        const int q = qs[h];
+      for (int h = 0; h < DUP_ITEMS; ++h) {
+        const int kk = e0 + h;
+        s_rec[kk] = 0;  // cleared for the next batch (each thread its own slots)
+        if (kk < a0 || kk >= a1) continue;
+        const int q = max(before, mk[h]) - 1;
         const int org = s_org[q], wv = s_wv[q];
         const int w = wv & 0xffff, v = (wv >> 16) & 0x7fff;
-        const int tt = kk - s_off[sa + q];
-        // tt = row * w + col: the quotient from the float reciprocal (tt < 2^16, so
+        const int tt = kk - s_off[rb + q];
+        // tt = row * w + col: the quotient from the float reciprocal (tt < 2^24, so
         // it is off by at most one) and one correction step
         int qd = __float2int_rd(__int2float_rn(tt) * s_iw[q]);
         int rm = tt - qd * w;
@@ -179,35 +177,43 @@ __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
         const int ty = (org >> 16) + qd, tx = (org & 0xffff) + rm;
         unsigned key = (unsigned)(ty * cs.tiles_x[v] + tx) | ((unsigned)v << view_shift);
         if (wv < 0) {  // a one-tile rectangle always meets its ellipse
-          const float4 e0 = s_e0[q];
-          const float4 e1 = s_e1[q];
+          const float4 f0 = s_e0[q];
+          const float4 f1 = s_e1[q];
           const float x0 = (float)(tx * cs.tile_w), y0 = (float)(ty * cs.tile_h);
           const float x1 = fminf(x0 + (float)(cs.tile_w - 1), (float)(cs.cam[v].width - 1));
           const float y1 = fminf(y0 + (float)(cs.tile_h - 1), (float)(cs.cam[v].height - 1));
-          if (!ellipse_meets_rect(e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w, x0, x1, y0, y1))
+          if (!ellipse_meets_rect(f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w, x0, x1, y0, y1))
             key = TILE_NONE;
         }
         keys[h] = key;
         ids[h] = s_i[q];
-        atomicAdd(&s_h[key & 255u], 1u);
+        if (key != TILE_NONE) atomicAdd(&s_h[key & 255u], 1u);  // the sort drops the others
       }
-      const long long k = k0 + a0 + e0i;  // even, so the pair stores are 8-byte aligned
-      if (a0 + e0i + 1 < a1) {
-        *reinterpret_cast<uint2*>(tkeys + k) = make_uint2(keys[0], keys[1]);
-        if (inst_pairs) {
-          *reinterpret_cast<int2*>(inst + k) = make_int2(ids[0], ids[1]);
-        } else {
-          inst[k] = ids[0];
-          inst[k + 1] = ids[1];
-        }
-      } else if (a0 + e0i < a1) {
-        tkeys[k] = keys[0];
-        inst[k] = ids[0];
-      }
-      __syncthreads();
+      __syncthreads();  // the batch's records and marks are no longer read
     }
-    for (int d = threadIdx.x; d < RS_BINS; d += DUP_THREADS) hist[(size_t)d * tiles_max + t] = s_h[d];
+    const long long k = k0 + e0;  // a multiple of 8: 16-byte aligned stores
+    if (e0 + DUP_ITEMS <= kn) {
+      uint4* kv = reinterpret_cast<uint4*>(tkeys + k);
+      kv[0] = make_uint4(keys[0], keys[1], keys[2], keys[3]);
+      kv[1] = make_uint4(keys[4], keys[5], keys[6], keys[7]);
+      if (inst_vec) {
+        int4* iv = reinterpret_cast<int4*>(inst + k);
+        iv[0] = make_int4(ids[0], ids[1], ids[2], ids[3]);
+        iv[1] = make_int4(ids[4], ids[5], ids[6], ids[7]);
+      } else {
+#pragma unroll
+        for (int h = 0; h < DUP_ITEMS; ++h) inst[k + h] = ids[h];
+      }
+    } else {
+#pragma unroll
+      for (int h = 0; h < DUP_ITEMS; ++h)
+        if (e0 + h < kn) {
+          tkeys[k + h] = keys[h];
+          inst[k + h] = ids[h];
+        }
+    }
     __syncthreads();
+    for (int d = threadIdx.x; d < RS_BINS; d += DUP_THREADS) hist[(size_t)d * tiles_max + t] = s_h[d];
   }
 }
 
@@ -245,7 +251,7 @@ __global__ void tile_ranges_kernel(const unsigned* tkeys, const long long* d_n, 
 }
 
 struct BinWs {
-  long long* counters;  // [0] visible, [1] clamped instance count
+  long long* counters;  // [0] visible; [1] clamped instance count, then the kept ones
   void* scan;
   unsigned* vkeys;
   unsigned* vvals;
@@ -366,22 +372,26 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
   // view-local tile with the view above the sorted bits: the tile sort takes
   // only the passes the largest view needs, every (view, tile) list is still one
   // run in (depth, id) order (the records come view-major and every pass is
-  // stable), and the runs are ordered by local tile, then view. The filtered key
-  // TILE_NONE has all sorted bits set, so it sorts after every tile.
+  // stable), and the runs are ordered by local tile, then view. Instances whose
+  // ellipse misses their tile get the key TILE_NONE, which the first pass drops.
   if (cap > 0) {
     duplicate_kernel<<<(unsigned)std::min<long long>((cap + DUP_CHUNK - 1) / DUP_CHUNK, 148 * 8),
                        DUP_THREADS, 0, st>>>(
         vvals, offs, chunk_first, &w.counters[0], &w.counters[1], cap,
         reinterpret_cast<const int4*>(pr->rect), xyod,
         reinterpret_cast<const float4*>(pr->conic), prm->alpha_min, n, cs, view_shift, w.tkeys,
-        bins->inst_gauss, aligned(bins->inst_gauss, 8), w.sort.hist, w.sort.tiles_max);
+        bins->inst_gauss, aligned(bins->inst_gauss, 16), w.sort.hist, w.sort.tiles_max);
     ADP_LAUNCH_CHECK();
     DigitOp tp[4];
     int ntp = 0;
     for (int s = 0; s < tile_bits; s += 8) tp[ntp++] = DigitOp{s, 0u};
-    // the first pass's tile histograms come from the duplication
+    // the first pass's tile histograms come from the duplication, which leaves out the
+    // instances whose ellipse misses their tile; the first pass drops them and the
+    // count becomes the kept instances
+    static_assert(TILE_NONE == RS_DROP_KEY, "the filtered key is the sort's drop key");
     rc = radix_sort_pairs(w.tkeys, reinterpret_cast<unsigned*>(bins->inst_gauss),
-                          &w.counters[1], cap, tp, ntp, w.sort, st, /*first_hist_done=*/true);
+                          &w.counters[1], cap, tp, ntp, w.sort, st, /*first_hist_done=*/true,
+                          /*drop_none=*/true);
     if (rc) return rc;
     // 6. per-tile ranges
     tile_ranges_kernel<<<grid_for(cap, 256, 148 * 16), 256, 0, st>>>(

@@ -150,7 +150,7 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned* s_w) {
 __global__ void ADP_RS_SCATTER_BOUNDS
     rs_scatter_kernel(const unsigned* keys_in, const unsigned* vals_in, unsigned* keys_out,
                       unsigned* vals_out, const long long* d_n, long long tiles_max, DigitOp op,
-                      const unsigned* hist, const unsigned* digit_tot) {
+                      const unsigned* hist, const unsigned* digit_tot, bool drop_none) {
   __shared__ unsigned s_base[RS_BINS];             // global start of every digit
   __shared__ unsigned s_whist[RS_WARPS][RS_BINS];  // per-warp counts, then warp prefixes
   __shared__ unsigned s_lbase[RS_BINS];            // start of every digit within the tile
@@ -158,6 +158,7 @@ __global__ void ADP_RS_SCATTER_BOUNDS
   __shared__ unsigned s_w[RS_WARPS];
   __shared__ unsigned s_keys[RS_TILE];
   __shared__ unsigned s_vals[RS_TILE];
+  __shared__ unsigned s_kept;                      // items of the tile that are written
   long long N = *d_n;
   long long nt = (N + RS_TILE - 1) / RS_TILE;
   if (nt > tiles_max) nt = tiles_max;
@@ -180,7 +181,7 @@ __global__ void ADP_RS_SCATTER_BOUNDS
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
       long long i = base + r * 32 + lane;
-      bool valid = i < N;
+      bool valid = i < N && !(drop_none && key[r] == RS_DROP_KEY);
       unsigned d = valid ? op(key[r], val[r]) : (unsigned)RS_BINS;
       dig[r] = d;
       unsigned peers = __match_any_sync(0xffffffffu, d);
@@ -204,12 +205,12 @@ __global__ void ADP_RS_SCATTER_BOUNDS
     }
     unsigned lb = block_excl_scan(cnt, s_w);
     s_lbase[threadIdx.x] = lb;
+    if (threadIdx.x == RS_BINS - 1) s_kept = lb + cnt;
     s_gpos[threadIdx.x] = s_base[threadIdx.x] + hist[(size_t)threadIdx.x * tiles_max + t];
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
-      long long i = base + r * 32 + lane;
-      if (i < N) {
+      if (dig[r] < (unsigned)RS_BINS) {  // in range and not dropped
         unsigned d = dig[r];
         unsigned lpos = s_lbase[d] + s_whist[warp][d] + off[r];
         s_keys[lpos] = key[r];
@@ -217,7 +218,8 @@ __global__ void ADP_RS_SCATTER_BOUNDS
       }
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < in_tile; j += RS_THREADS) {
+    const int kept = (int)s_kept;
+    for (int j = threadIdx.x; j < kept; j += RS_THREADS) {
       unsigned k = s_keys[j], vv = s_vals[j];
       unsigned d = op(k, vv);
       unsigned pos = s_gpos[d] + (unsigned)j - s_lbase[d];
@@ -311,9 +313,23 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
-int radix_sort_pairs(unsigned* keys, unsigned* vals, const long long* d_n, long long n_max,
+// After a pass that dropped items: the count the later passes sort.
+__global__ void rs_kept_count_kernel(const unsigned* digit_tot, long long* d_n) {
+  __shared__ unsigned long long s_sum[RS_BINS / 32];
+  unsigned long long x = digit_tot[threadIdx.x];
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < RS_BINS / 32; ++w) t += s_sum[w];
+    *d_n = (long long)t;
+  }
+}
+
+int radix_sort_pairs(unsigned* keys, unsigned* vals, long long* d_n, long long n_max,
                      const DigitOp* passes, int n_passes, const SortWorkspace& w,
-                     cudaStream_t st, bool first_hist_done) {
+                     cudaStream_t st, bool first_hist_done, bool drop_none) {
   if (n_max <= 0 || n_passes <= 0) return ADP_OK;
   if (n_max <= SMALL_SORT_MAX && n_passes <= 4 && !first_hist_done) {  // one small launch
     SmallPasses sp;
@@ -330,8 +346,10 @@ int radix_sort_pairs(unsigned* keys, unsigned* vals, const long long* d_n, long 
       rs_hist_kernel<<<(unsigned)grid, RS_THREADS, 0, st>>>(ka, va, d_n, w.tiles_max, passes[p],
                                                              w.hist);
     rs_scan_kernel<<<RS_BINS, RS_THREADS, 0, st>>>(w.hist, d_n, w.tiles_max, w.digit_tot);
+    const bool drop = drop_none && first_hist_done && p == 0;
     rs_scatter_kernel<<<(unsigned)grid, RS_THREADS, 0, st>>>(ka, va, kb, vb, d_n, w.tiles_max,
-                                                              passes[p], w.hist, w.digit_tot);
+                                                              passes[p], w.hist, w.digit_tot, drop);
+    if (drop) rs_kept_count_kernel<<<1, RS_BINS, 0, st>>>(w.digit_tot, d_n);
     ADP_LAUNCH_CHECK();
     unsigned* tk = ka; ka = kb; kb = tk;
     unsigned* tv = va; va = vb; vb = tv;

@@ -343,16 +343,22 @@ __global__ void rs_scan_kernel(unsigned* hist, const long long* d_n, long long t
 __global__ void rs_scatter_kernel(const unsigned* keys_in, const unsigned* vals_in,
                                   unsigned* keys_out, unsigned* vals_out, const long long* d_n,
                                   long long tiles_max, DigitOp op, const unsigned* hist,
-                                  const unsigned* digit_tot);
+                                  const unsigned* digit_tot, bool drop_none);
+
+// Key that a sort may drop (see radix_sort_pairs): all bits set.
+constexpr unsigned RS_DROP_KEY = 0xffffffffu;
 
 // Sorts (keys, vals) in place by the given passes. passes[k] is a DigitOp;
 // n_max bounds the device count *d_n. Up to SMALL_SORT_MAX items (and four
 // passes) the sort runs in a single one-block launch.
 // first_hist_done: the caller already wrote the first pass's per-tile histograms
 // (hist[digit * tiles_max + tile], every digit of every tile of *d_n items).
-int radix_sort_pairs(unsigned* keys, unsigned* vals, const long long* d_n, long long n_max,
+// drop_none (with first_hist_done and a writable count): the first pass drops the
+// items whose key is RS_DROP_KEY (the caller's histograms leave them out) and sets
+// *d_n to the items kept, which the later passes sort.
+int radix_sort_pairs(unsigned* keys, unsigned* vals, long long* d_n, long long n_max,
                      const DigitOp* passes, int n_passes, const SortWorkspace& w, cudaStream_t st,
-                     bool first_hist_done = false);
+                     bool first_hist_done = false, bool drop_none = false);
 
 inline int bits_for(long long v) {
   int b = 0;

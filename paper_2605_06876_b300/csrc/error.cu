@@ -428,8 +428,6 @@ static int topk_coop_run(const double* mass, long long n, long long k, int32_t* 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const int* dummy = nullptr;
-  (void)dummy;
   ADP_CUDA(cudaLaunchKernelEx(&cfg, topk_coop_kernel, mass, (long long)n, (long long)k,
                               (int*)out_ids, w));
   return ADP_OK;
