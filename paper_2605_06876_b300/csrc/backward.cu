@@ -142,10 +142,13 @@ struct BwdGaussArgs {
 // template parameter so that every SH array index is a constant and the arrays
 // stay in registers.
 // acc: the thread's column of a [4 * planes][BWDG_THREADS] shared-memory array in
-// which the SH gradient is summed over the views (written to the planes once).
+// which the SH gradient is summed over the views (written to the planes once);
+// shc: the same for the Gaussian's SH coefficients, read from global memory once
+// instead of once per view.
 constexpr int BWDG_THREADS = 128;
 template <int DEG>
-__device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i, float* acc) {
+__device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i, float* acc,
+                        float* shc) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int planes = (3 * K + 3) / 4;
   float4 ml = a.mean_logit[i], ls = a.logscale[i], q4 = a.quat[i];
@@ -168,6 +171,14 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i, fl
   // SH coefficients and their gradient rows, one float4 plane at a time
   const float4* shp = reinterpret_cast<const float4*>(a.sh) + i;
   float4* gshp = reinterpret_cast<float4*>(a.g_sh) + i;
+#pragma unroll
+  for (int p = 0; p < planes; ++p) {
+    const float4 c4 = shp[(long long)p * a.n];
+    shc[(4 * p) * BWDG_THREADS] = c4.x;
+    shc[(4 * p + 1) * BWDG_THREADS] = c4.y;
+    shc[(4 * p + 2) * BWDG_THREADS] = c4.z;
+    shc[(4 * p + 3) * BWDG_THREADS] = c4.w;
+  }
 #pragma unroll
   for (int f = 0; f < 4 * planes; ++f) acc[f * BWDG_THREADS] = 0.f;
   for (int v = 0; v < cs.n_views; ++v) {
@@ -207,8 +218,8 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i, fl
     for (int k = 0; k < 16; ++k) wk[k] = 0.f;
 #pragma unroll
     for (int p = 0; p < planes; ++p) {
-      const float4 c4 = shp[(long long)p * a.n];
-      const float cf[4] = {c4.x, c4.y, c4.z, c4.w};
+      const float cf[4] = {shc[(4 * p) * BWDG_THREADS], shc[(4 * p + 1) * BWDG_THREADS],
+                           shc[(4 * p + 2) * BWDG_THREADS], shc[(4 * p + 3) * BWDG_THREADS]};
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
         const int f = 4 * p + l;
@@ -217,6 +228,9 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i, fl
           wk[f / 3] += cf[l] * gcol[f % 3];
         }
       }
+      // one plane at a time: keeps the compiler from hoisting every plane's
+      // shared-memory loads (and their registers) to the top of the loop
+      asm volatile("" ::: "memory");
     }
     float gu[3] = {0.f, 0.f, 0.f};
     if (DEG > 0) sh_grad_dot(DEG, u[0], u[1], u[2], wk, gu);
@@ -387,8 +401,9 @@ __global__ void __launch_bounds__(BWDG_THREADS, ADP_BWDG_MINB)
                      const unsigned long long* n_list) {
   constexpr int planes = (3 * (DEG + 1) * (DEG + 1) + 3) / 4;
   __shared__ float s_acc[4 * planes * BWDG_THREADS];
+  __shared__ float s_shc[4 * planes * BWDG_THREADS];
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t < (long long)*n_list) bwd_one<DEG>(a, cs, list[t], s_acc + threadIdx.x);
+  if (t < (long long)*n_list) bwd_one<DEG>(a, cs, list[t], s_acc + threadIdx.x, s_shc + threadIdx.x);
 }
 
 }  // namespace adp

@@ -18,7 +18,7 @@
 #define ADP_FUSED_PX 4
 #endif
 #ifndef ADP_FUSED_MINB  // resident blocks per SM the register budget is sized for
-#define ADP_FUSED_MINB 1
+#define ADP_FUSED_MINB 12
 #endif
 
 namespace adp {
