@@ -281,36 +281,58 @@ def run_ours(args, rank, world, local_rank):
     ms_per_step = total_ms / args.steps
     value = job_rate(args.steps, world, total_ms / 1e3)
 
-    # end to end through the public API: inputs from pinned host memory each step,
-    # the split decisions read back each step
-    host = {k: v for k, v in sc.items()}
+    # end to end through the public API: every step's inputs (the Gaussian parameters,
+    # the target, the fallback noise) come from pinned host memory and the split
+    # decisions are read back and waited for. The inputs are double-buffered: step
+    # k + 1's host-to-device copy runs on a copy stream into a device staging buffer
+    # while step k computes, and a device-to-device copy moves them into the step's
+    # buffers before it starts
     pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
               (stepper.g.mean_logit.cpu().numpy(), stepper.g.logscale.cpu().numpy(),
-               stepper.g.quat.cpu().numpy(), stepper.g.sh.cpu().numpy())]
-    tgt_h = target.cpu().pin_memory()
-    noise_h = noise.cpu().pin_memory()
+               stepper.g.quat.cpu().numpy(), stepper.g.sh.cpu().numpy(),
+               target.cpu().numpy(), noise.cpu().numpy())]
+    dsts = stepper.g.tensors() + [target, noise]
+    staging = [[torch.empty_like(d) for d in dsts] for _ in range(2)]
     st_h = torch.empty(stepper.k, dtype=torch.uint8).pin_memory()
     nc_h = torch.empty(stepper.k, dtype=torch.int32).pin_memory()
-    e2e_steps = max(1, min(args.steps, 5))
-    h2d = sum(p.numel() * p.element_size() for p in pinned) + tgt_h.numel() * 4 + noise_h.numel() * 4
+    e2e_steps = max(2, min(args.steps, 6))
+    h2d = sum(p.numel() * p.element_size() for p in pinned)
     d2h = stepper.k * (1 + 4)
+    copy_stream = torch.cuda.Stream(device=dev)
+    loaded = [torch.cuda.Event() for _ in range(2)]    # staging buffer filled
+    consumed = [torch.cuda.Event() for _ in range(2)]  # staging buffer copied out
+    for ev in consumed:
+        ev.record(stream)
+
+    def h2d_into(buf):
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(consumed[buf])
+            for s_, src in zip(staging[buf], pinned):
+                s_.copy_(src.view(s_.shape), non_blocking=True)
+            loaded[buf].record(copy_stream)
+
     torch.cuda.synchronize()
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(e2e_steps):
-        for dst, src in zip(stepper.g.tensors(), pinned):
-            dst.copy_(src.view(dst.shape), non_blocking=True)
-        target.copy_(tgt_h, non_blocking=True)
-        noise.copy_(noise_h, non_blocking=True)
+    h2d_into(0)
+    for k_ in range(e2e_steps):
+        buf = k_ % 2
+        if k_ + 1 < e2e_steps:
+            h2d_into(1 - buf)  # the next step's inputs, beside this step
+        stream.wait_event(loaded[buf])
+        for d_, s_ in zip(dsts, staging[buf]):
+            d_.copy_(s_, non_blocking=True)
+        consumed[buf].record(stream)
         out = stepper.replay() if use_graph else stepper.step(noise)
         st_h.copy_(out[3].status, non_blocking=True)
         nc_h.copy_(out[3].n_children, non_blocking=True)
-        stream.synchronize()
+        stream.synchronize()  # the host has the step's decisions
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dev)
+    del staging
 
     # roofline of the dominant stage
     n = g.n

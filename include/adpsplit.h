@@ -14,9 +14,10 @@
  *  - Every call is asynchronous on the given stream (a cudaStream_t; NULL is the
  *    legacy default stream) and does not synchronise, except adp_split_plan,
  *    which reads one integer back when asked to (see there). The overlapped
- *    split (adp_split_plan_overlapped and its two compaction calls) also puts
- *    work on a stream the library keeps per device, forked from and joined back
- *    into the given stream (see there).
+ *    split (adp_split_plan_overlapped and its two compaction calls) and the
+ *    batched step (adp_train_step_batched) also put work on a stream the library
+ *    keeps per device, forked from and joined back into the given stream (see
+ *    there).
  *  - Every call returns an adp_status. A host-side argument error returns
  *    ADP_ERR_INVALID_ARG before anything is launched; a CUDA launch error returns
  *    ADP_ERR_CUDA. adp_last_error_string() describes the last failure of the
@@ -445,7 +446,11 @@ ADP_API int adp_render_backward(const adp_gaussians* g, const adp_projected* pr,
  * views' pixels), count and mass (n, zeroed by the call), grad (zeroed or masked
  * rows), the optional Eq. 2 accumulators, d_status (see the conventions). The
  * workspace size depends on n, n_views and bins->capacity (0 for invalid
- * arguments). Asynchronous and capturable in a CUDA graph. */
+ * arguments). Asynchronous and capturable in a CUDA graph. The error
+ * normalisation runs on the library's auxiliary stream of the device, forked from
+ * `stream` after the per-tile kernel and joined back before the call returns (as
+ * in the overlapped split); the first call on a device creates that stream, so it
+ * must come before any stream capture that includes the call. */
 ADP_API size_t adp_train_step_batched_workspace_size(int64_t n, int32_t n_views,
                                                      const adp_camera* cams,
                                                      const adp_params* prm, int64_t capacity);

@@ -212,15 +212,14 @@ extern "C" ADP_API int adp_train_step_batched(
     w.item_ctr = c.take<int>(1);
     ADP_CHECK_ARG(c.ok, "internal: workspace carve failed");
   }
-  // 1-2. projection and binning of every view
-  rc = adp_project(g, cams, n_views, prm, pr, stream);
+  // 1-2. projection (zeroing the backward's moment rows of the visible records) and
+  // binning of every view
+  rc = project_launch(g, cams, n_views, prm, pr, w.g2d, st);
   if (rc) return rc;
   rc = adp_bin_sort(n, pr, cams, n_views, prm, bins, w.bins_ws, w.bins_bytes, d_status, stream);
   if (rc) return rc;
   if (n == 0) return ADP_OK;
   // 3. the fused forward + error epilogue + backward over the (view, tile) queue
-  rc = zero_visible_moments(pr->tiles_touched, n * n_views, w.g2d, st);
-  if (rc) return rc;
   ADP_CUDA(cudaMemsetAsync(w.n_list, 0, sizeof(unsigned long long), st));
   ADP_CUDA(cudaMemsetAsync(w.item_ctr, 0, sizeof(int), st));
   rc = error_minmax_init(maps, n_views, st);
@@ -264,10 +263,27 @@ extern "C" ADP_API int adp_train_step_batched(
       break;
   }
   ADP_LAUNCH_CHECK();
-  // 4. E, M, B and the per-Gaussian count and mass (Eq. 6, Sec. 5.1)
-  rc = error_norm_phase(maps, img->dominant, n, cs, prm, count, mass, st);
+  // 4. E, M, B and the per-Gaussian count and mass (Eq. 6, Sec. 5.1) on the
+  // auxiliary stream, beside 5. the per-Gaussian chain rule summed over views: the
+  // first is bound by its divisions and atomics, the second by gather latency
+  AuxStream* aux = nullptr;
+  rc = aux_stream(&aux);
   if (rc) return rc;
-  // 5. the per-Gaussian chain rule, summed over views
-  return backward_gauss_phase(g, pr, cs, prm, grad, grad2d_accum, grad2d_visits, w.g2d, w.list,
-                              w.n_list, st);
+  {
+    std::lock_guard<std::mutex> lock(aux_mutex());
+    ADP_CUDA(cudaEventRecord(aux->forked, st));
+    ADP_CUDA(cudaStreamWaitEvent(aux->stream, aux->forked, 0));
+  }
+  const int rc_err = error_norm_phase(maps, img->dominant, n, cs, prm, count, mass, aux->stream);
+  {
+    std::lock_guard<std::mutex> lock(aux_mutex());
+    ADP_CUDA(cudaEventRecord(aux->joined, aux->stream));
+  }
+  const int rc_bwd = backward_gauss_phase(g, pr, cs, prm, grad, grad2d_accum, grad2d_visits,
+                                          w.g2d, w.list, w.n_list, st);
+  {  // joined even after an error, so a capture stays valid
+    std::lock_guard<std::mutex> lock(aux_mutex());
+    ADP_CUDA(cudaStreamWaitEvent(st, aux->joined, 0));
+  }
+  return rc_err ? rc_err : rc_bwd;
 }

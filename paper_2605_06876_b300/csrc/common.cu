@@ -361,6 +361,31 @@ int radix_sort_pairs(unsigned* keys, unsigned* vals, long long* d_n, long long n
   return ADP_OK;
 }
 
+constexpr int AUX_MAX_DEVICES = 64;
+static AuxStream g_aux[AUX_MAX_DEVICES];
+static std::mutex g_aux_mu;
+
+std::mutex& aux_mutex() { return g_aux_mu; }
+
+int aux_stream(AuxStream** out) {
+  int dev = 0;
+  ADP_CUDA(cudaGetDevice(&dev));
+  ADP_CHECK_ARG(dev >= 0 && dev < AUX_MAX_DEVICES, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_aux_mu);
+  AuxStream& a = g_aux[dev];
+  if (!a.stream) {
+    int lo = 0, hi = 0;
+    ADP_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    ADP_CUDA(cudaEventCreateWithFlags(&a.planned, cudaEventDisableTiming));
+    ADP_CUDA(cudaEventCreateWithFlags(&a.merged, cudaEventDisableTiming));
+    ADP_CUDA(cudaEventCreateWithFlags(&a.forked, cudaEventDisableTiming));
+    ADP_CUDA(cudaEventCreateWithFlags(&a.joined, cudaEventDisableTiming));
+    ADP_CUDA(cudaStreamCreateWithPriority(&a.stream, cudaStreamNonBlocking, hi));
+  }
+  *out = &a;
+  return ADP_OK;
+}
+
 __global__ void count_guard_kernel(const unsigned long long* err, long long* count) {
   if (*err != 0ull) *count = 0;
 }

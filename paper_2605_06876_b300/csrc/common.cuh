@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <mutex>
 
 #include "adpsplit.h"
 
@@ -108,6 +109,21 @@ __device__ __forceinline__ T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+
+// ----------------------------------------------------------------- auxiliary stream
+
+// The library's auxiliary stream of the current device (highest priority) and the
+// events that fork work onto it and join it back: `planned` and `merged` for the
+// overlapped split's plan, `forked` and `joined` for the batched step. Created on
+// the first use on a device (so that use must come before any stream capture that
+// includes it); the mutex serialises the event records and waits of host threads.
+struct AuxStream {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t planned = nullptr, merged = nullptr;
+  cudaEvent_t forked = nullptr, joined = nullptr;
+};
+int aux_stream(AuxStream** out);
+std::mutex& aux_mutex();
 
 // ----------------------------------------------------------------- bounded waits
 

@@ -6,6 +6,13 @@
 
 namespace adp {
 
+// adp_project's launch; zero_moments (optional, [V*n][3] float4) additionally gets
+// the three rows of every record the projection makes visible zeroed (the
+// backward's pixel moments, which are only read for visible records).
+int project_launch(const adp_gaussians* g, const adp_camera* cams, int n_views,
+                   const adp_params* prm, adp_projected* out, float4* zero_moments,
+                   cudaStream_t st);
+
 // Presets the per-view min/max words of maps->minmax for the raw L1 reduction.
 int error_minmax_init(adp_error_maps* maps, int n_views, cudaStream_t st);
 

@@ -6,6 +6,7 @@
 // there are several, reading each Gaussian's mean and scales once) and project
 // the surviving pairs with full warps.
 #include "gauss_math.cuh"
+#include "phases.cuh"
 
 namespace adp {
 
@@ -22,6 +23,7 @@ struct ProjectArgs {
   float4* rgb;
   int4* rect;
   int* tiles;
+  float4* zero_moments;  // optional [V*n][3]: zeroed for every visible record
 };
 
 // The view-independent part of a Gaussian: opacity sigmoid(logit) and the six
@@ -132,6 +134,12 @@ __device__ __forceinline__ void project_view(const ProjectArgs& a, const CamSet&
   a.rgb[rec] = out2;
   a.rect[rec] = rc;
   a.tiles[rec] = nt;
+  if (a.zero_moments && nt > 0) {  // the backward's pixel moments of this record
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    a.zero_moments[3 * rec] = z;
+    a.zero_moments[3 * rec + 1] = z;
+    a.zero_moments[3 * rec + 2] = z;
+  }
 }
 
 // Full projection of Gaussian i into view v (the one-view kernel's compacted
@@ -254,6 +262,12 @@ using namespace adp;
 extern "C" ADP_API int adp_project(const adp_gaussians* g, const adp_camera* cams, int32_t n_views,
                                    const adp_params* prm, adp_projected* out,
                                    adp_stream_t stream) {
+  return project_launch(g, cams, n_views, prm, out, nullptr, (cudaStream_t)stream);
+}
+
+int adp::project_launch(const adp_gaussians* g, const adp_camera* cams, int n_views,
+                        const adp_params* prm, adp_projected* out, float4* zero_moments,
+                        cudaStream_t st) {
   ADP_CHECK_ARG(g && out, "NULL argument");
   ADP_CHECK_ARG(g->n >= 0 && g->n < (1LL << 31), "n = %lld out of range", (long long)g->n);
   ADP_CHECK_ARG(g->sh_degree >= 0 && g->sh_degree <= 3, "sh_degree must be 0..3");
@@ -284,7 +298,7 @@ extern "C" ADP_API int adp_project(const adp_gaussians* g, const adp_camera* cam
   a.rgb = reinterpret_cast<float4*>(out->rgb);
   a.rect = reinterpret_cast<int4*>(out->rect);
   a.tiles = out->tiles_touched;
-  cudaStream_t st = (cudaStream_t)stream;
+  a.zero_moments = zero_moments;
   if (n_views == 1) {  // survivors compacted to full warps
     dim3 grid((unsigned)((g->n + PROJ_CHUNK - 1) / PROJ_CHUNK), n_views);
     switch (g->sh_degree) {

@@ -995,35 +995,6 @@ static int plan_phase_b(const PlanCall& pc, const SplitWs& w, cudaStream_t st) {
   return ADP_OK;
 }
 
-// The library's auxiliary stream of the current device (highest priority), and
-// the two events of an overlapped plan: `planned` (phase A done, on the caller's
-// stream) and `merged` (phase B done, on the auxiliary stream). Created on first
-// use.
-struct AuxStream {
-  cudaStream_t stream = nullptr;
-  cudaEvent_t planned = nullptr, merged = nullptr;
-};
-constexpr int AUX_MAX_DEVICES = 64;
-static AuxStream g_aux[AUX_MAX_DEVICES];
-static std::mutex g_aux_mu;
-
-static int aux_stream(AuxStream** out) {
-  int dev = 0;
-  ADP_CUDA(cudaGetDevice(&dev));
-  ADP_CHECK_ARG(dev >= 0 && dev < AUX_MAX_DEVICES, "device %d out of range", dev);
-  std::lock_guard<std::mutex> lock(g_aux_mu);
-  AuxStream& a = g_aux[dev];
-  if (!a.stream) {
-    int lo = 0, hi = 0;
-    ADP_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-    ADP_CUDA(cudaEventCreateWithFlags(&a.planned, cudaEventDisableTiming));
-    ADP_CUDA(cudaEventCreateWithFlags(&a.merged, cudaEventDisableTiming));
-    ADP_CUDA(cudaStreamCreateWithPriority(&a.stream, cudaStreamNonBlocking, hi));
-  }
-  *out = &a;
-  return ADP_OK;
-}
-
 }  // namespace adp
 
 extern "C" ADP_API int adp_split_plan(const adp_gaussians* g, const adp_camera* cams,
@@ -1071,12 +1042,12 @@ extern "C" ADP_API int adp_split_plan_overlapped(const adp_gaussians* g, const a
   rc = plan_phase_a(pc, w, st);
   if (rc) return rc;
   {  // fork: phase B on the auxiliary stream once phase A is done
-    std::lock_guard<std::mutex> lock(g_aux_mu);
+    std::lock_guard<std::mutex> lock(aux_mutex());
     ADP_CUDA(cudaEventRecord(aux->planned, st));
     ADP_CUDA(cudaStreamWaitEvent(aux->stream, aux->planned, 0));
   }
   rc = plan_phase_b(pc, w, aux->stream);
-  std::lock_guard<std::mutex> lock(g_aux_mu);
+  std::lock_guard<std::mutex> lock(aux_mutex());
   ADP_CUDA(cudaEventRecord(aux->merged, aux->stream));
   if (rc) {
     // join the fork before reporting the failure, so that a capture in progress
@@ -1174,7 +1145,7 @@ static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
     return ADP_OK;
   }
   if (overlapped) {  // join the plan's second part
-    std::lock_guard<std::mutex> lock(g_aux_mu);
+    std::lock_guard<std::mutex> lock(aux_mutex());
     ADP_CUDA(cudaStreamWaitEvent(st, aux->merged, 0));
   }
   if (overlapped && n > 0) {
