@@ -218,7 +218,8 @@ extern "C" ADP_API int adp_train_step_batched(
   if (rc) return rc;
   rc = adp_bin_sort(n, pr, cams, n_views, prm, bins, w.bins_ws, w.bins_bytes, d_status, stream);
   if (rc) return rc;
-  if (n == 0) return ADP_OK;
+  // (with no Gaussian every tile list is empty: the image is the background, and the
+  // error maps and the statistics follow from it)
   // 3. the fused forward + error epilogue + backward over the (view, tile) queue
   ADP_CUDA(cudaMemsetAsync(w.n_list, 0, sizeof(unsigned long long), st));
   ADP_CUDA(cudaMemsetAsync(w.item_ctr, 0, sizeof(int), st));

@@ -347,7 +347,11 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
   int np = 0;
   for (int s = 0; s < 32; s += 8) passes[np++] = DigitOp{s, 0u};
   if (n_views > 1) passes[np++] = DigitOp{0, (unsigned)n};
-  rc = radix_sort_pairs(vkeys, vvals, &w.counters[0], nv, passes, np, w.sort, st);
+  // the sorted records stay where the last pass wrote them (the tile sort reuses
+  // the alternate buffers only after the duplication has read them)
+  unsigned* skeys = nullptr;
+  rc = radix_sort_pairs(vkeys, vvals, &w.counters[0], nv, passes, np, w.sort, st, false, false,
+                        &skeys, &vvals);
   if (rc) return rc;
 
   // 3. instance offsets in sorted order; total -> n_instances

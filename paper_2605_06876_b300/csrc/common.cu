@@ -90,7 +90,10 @@ __global__ void rs_hist_kernel(const unsigned* keys, const unsigned* vals, const
   }
 }
 
-// One block per digit: exclusive scan of that digit's per-tile counts.
+// One block per digit: exclusive scan of that digit's per-tile counts, each thread
+// taking RS_SCAN_ITEMS consecutive tiles of a round (so a block needs few rounds,
+// each with two barriers, even for tens of thousands of tiles).
+constexpr int RS_SCAN_ITEMS = 8;
 __global__ void rs_scan_kernel(unsigned* hist, const long long* d_n, long long tiles_max,
                                unsigned* digit_tot) {
   __shared__ unsigned s_warp[RS_WARPS];
@@ -102,22 +105,35 @@ __global__ void rs_scan_kernel(unsigned* hist, const long long* d_n, long long t
   if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (long long base = 0; base < nt; base += RS_THREADS) {
-    long long i = base + threadIdx.x;
-    unsigned x = i < nt ? row[i] : 0u;
-    unsigned inc = x;
+  for (long long base = 0; base < nt; base += (long long)RS_THREADS * RS_SCAN_ITEMS) {
+    const long long i0 = base + (long long)threadIdx.x * RS_SCAN_ITEMS;
+    unsigned x[RS_SCAN_ITEMS];
+    unsigned tsum = 0;
+#pragma unroll
+    for (int k = 0; k < RS_SCAN_ITEMS; ++k) {
+      x[k] = i0 + k < nt ? row[i0 + k] : 0u;
+      tsum += x[k];
+    }
+    unsigned inc = tsum;
     for (int o = 1; o < 32; o <<= 1) {
       unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
       if (lane >= o) inc += y;
     }
     if (lane == 31) s_warp[w] = inc;
     __syncthreads();
-    unsigned wpre = 0;
-    for (int k = 0; k < w; ++k) wpre += s_warp[k];
-    unsigned excl = s_carry + wpre + inc - x;
-    if (i < nt) row[i] = excl;
-    __syncthreads();
-    if (threadIdx.x == RS_THREADS - 1) s_carry = excl + x;
+    unsigned wpre = 0, btot = 0;
+    for (int k = 0; k < RS_WARPS; ++k) {
+      wpre += k < w ? s_warp[k] : 0u;
+      btot += s_warp[k];
+    }
+    unsigned run = s_carry + wpre + inc - tsum;
+#pragma unroll
+    for (int k = 0; k < RS_SCAN_ITEMS; ++k) {
+      if (i0 + k < nt) row[i0 + k] = run;
+      run += x[k];
+    }
+    __syncthreads();  // every thread has read s_carry and s_warp
+    if (threadIdx.x == 0) s_carry += btot;
     __syncthreads();
   }
   if (threadIdx.x == 0) digit_tot[blockIdx.x] = s_carry;
@@ -329,7 +345,10 @@ __global__ void rs_kept_count_kernel(const unsigned* digit_tot, long long* d_n) 
 
 int radix_sort_pairs(unsigned* keys, unsigned* vals, long long* d_n, long long n_max,
                      const DigitOp* passes, int n_passes, const SortWorkspace& w,
-                     cudaStream_t st, bool first_hist_done, bool drop_none) {
+                     cudaStream_t st, bool first_hist_done, bool drop_none, unsigned** res_keys,
+                     unsigned** res_vals) {
+  if (res_keys) *res_keys = keys;
+  if (res_vals) *res_vals = vals;
   if (n_max <= 0 || n_passes <= 0) return ADP_OK;
   if (n_max <= SMALL_SORT_MAX && n_passes <= 4 && !first_hist_done) {  // one small launch
     SmallPasses sp;
@@ -355,6 +374,11 @@ int radix_sort_pairs(unsigned* keys, unsigned* vals, long long* d_n, long long n
     unsigned* tv = va; va = vb; vb = tv;
   }
   if (ka != keys) {  // odd pass count: results live in the alternate buffers
+    if (res_keys && res_vals) {
+      *res_keys = ka;
+      *res_vals = va;
+      return ADP_OK;
+    }
     ADP_CUDA(cudaMemcpyAsync(keys, ka, sizeof(unsigned) * n_max, cudaMemcpyDeviceToDevice, st));
     ADP_CUDA(cudaMemcpyAsync(vals, va, sizeof(unsigned) * n_max, cudaMemcpyDeviceToDevice, st));
   }

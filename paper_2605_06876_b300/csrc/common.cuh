@@ -372,9 +372,13 @@ constexpr unsigned RS_DROP_KEY = 0xffffffffu;
 // drop_none (with first_hist_done and a writable count): the first pass drops the
 // items whose key is RS_DROP_KEY (the caller's histograms leave them out) and sets
 // *d_n to the items kept, which the later passes sort.
+// res_keys, res_vals (optional): receive where the sorted pairs are (keys/vals, or
+// the workspace's alternate buffers after an odd number of passes), instead of the
+// copy back into keys/vals.
 int radix_sort_pairs(unsigned* keys, unsigned* vals, long long* d_n, long long n_max,
                      const DigitOp* passes, int n_passes, const SortWorkspace& w, cudaStream_t st,
-                     bool first_hist_done = false, bool drop_none = false);
+                     bool first_hist_done = false, bool drop_none = false,
+                     unsigned** res_keys = nullptr, unsigned** res_vals = nullptr);
 
 inline int bits_for(long long v) {
   int b = 0;

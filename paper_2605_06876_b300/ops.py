@@ -81,10 +81,10 @@ class Gaussians:
         g = cls(n, deg, device, zero=False)
         ml = np.concatenate([scene["mean"], scene["logit"][:, None]], 1)
         ls = np.concatenate([scene["logscale"], np.zeros((n, 1), np.float32)], 1)
-        flat = scene["sh"].reshape(n, -1)
+        flat = scene["sh"].reshape(n, 3 * sh_coeffs(deg))
         pad = np.zeros((n, 4 * sh_planes(deg)), np.float32)
         pad[:, :flat.shape[1]] = flat
-        sh = pad.reshape(n, -1, 4).transpose(1, 0, 2)
+        sh = pad.reshape(n, sh_planes(deg), 4).transpose(1, 0, 2)
         g.mean_logit.copy_(torch.from_numpy(np.ascontiguousarray(ml, np.float32)))
         g.logscale.copy_(torch.from_numpy(np.ascontiguousarray(ls, np.float32)))
         g.quat.copy_(torch.from_numpy(np.ascontiguousarray(scene["quat"], np.float32)))
@@ -95,7 +95,7 @@ class Gaussians:
         n, deg = self.n, self.sh_degree
         K = sh_coeffs(deg)
         ml = self.mean_logit.cpu().numpy()
-        sh = self.sh.cpu().numpy().transpose(1, 0, 2).reshape(n, -1)[:, :3 * K]
+        sh = self.sh.cpu().numpy().transpose(1, 0, 2).reshape(n, 4 * sh_planes(deg))[:, :3 * K]
         return {"mean": ml[:, :3].copy(), "logit": ml[:, 3].copy(),
                 "logscale": self.logscale.cpu().numpy()[:, :3].copy(),
                 "quat": self.quat.cpu().numpy().copy(), "sh": sh.reshape(n, K, 3).copy(),

@@ -189,3 +189,53 @@ def test_batched_3m_uneven_16_views_sampled_pixels():
         compare_render(np_(img.rgb[idx]), np_(img.T[idx]), np_(img.n_contrib[idx]),
                        np_(img.dominant[idx]), o,
                        f"batched 3M Gaussians, view {v} {cam['width']}x{cam['height']}")
+
+
+def _one_stage_image(g, cams, target, bg):
+    pr = ops.project(g, cams)
+    bins = ops.bin_sort(g.n, pr, cams)
+    img = ops.render(g.n, pr, bins, cams, bg)
+    maps, count, mass = ops.error_stats(img.rgb, target, img.dominant, g.n, cams)
+    torch.cuda.synchronize()
+    return img, maps, count, mass
+
+
+@pytest.mark.parametrize("case", ["empty", "behind", "one_pixel", "max_views"])
+def test_batched_edge_cases(case):
+    """Degenerate inputs of the batched call against the one-stage calls: no
+    Gaussian at all, every Gaussian behind every camera, a 1x1 view beside ragged
+    ones, and the maximum number of views (ADP_MAX_VIEWS, small ones)."""
+    bg = (0.25, 0.5, 0.75)
+    sc, _ = small_cluster_inputs(4000, 8, 8, seed=40)
+    if case == "empty":
+        sc = {k: (v[:0] if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
+        cams = _uneven_cams(41)
+    elif case == "behind":
+        sc = dict(sc, mean=(sc["mean"] * np.float32(0.1) + np.float32([0, 0, -30])).astype(np.float32))
+        cams = [scenes.camera_origin_forward(97, 61), scenes.camera_origin_forward(64, 64)]
+    elif case == "one_pixel":
+        cams = [scenes.camera_look_at((0, 0, -4), (0, 0, 0), 1, 1),
+                scenes.camera_look_at((0.3, 0, -4), (0, 0, 0), 37, 19)]
+    else:
+        cams = [scenes.camera_look_at((4 * np.cos(a), -0.5, 4 * np.sin(a)), (0, 0, 0), 48, 32)
+                for a in np.linspace(0, 2 * np.pi, A.ADP_MAX_VIEWS, endpoint=False)]
+    P = ops.n_pixels(cams)
+    target = torch.rand((P, 3), device=DEV, generator=torch.Generator(DEV).manual_seed(4))
+    g = ops.Gaussians.from_scene(sc, DEV)
+    status = ops.status_word(DEV)
+    pr, bins, img, maps, count, mass, grad = ops.train_step_batched(g, cams, target, bg=bg,
+                                                                    status=status)
+    torch.cuda.synchronize()
+    ops.check_status(status)
+    ref, rmaps, rcount, rmass = _one_stage_image(g, cams, target, bg)
+    for x, y in zip((img.rgb, img.T, img.n_contrib, img.dominant), (ref.rgb, ref.T, ref.n_contrib,
+                                                                     ref.dominant)):
+        assert torch.equal(x, y)
+    assert torch.equal(maps.E, rmaps.E) and torch.equal(maps.mask, rmaps.mask)
+    if g.n:
+        assert torch.equal(count, rcount) and torch.equal(mass, rmass)
+    if case in ("empty", "behind"):  # nothing rendered: the background everywhere
+        want = torch.tensor(bg, device=DEV).expand(P, 3)
+        assert torch.equal(img.rgb, want) and bool((img.dominant == -1).all())
+        if g.n:
+            assert not bool(grad.rows.any()) and not bool(count.any())
