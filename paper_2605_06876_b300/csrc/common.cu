@@ -155,22 +155,23 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned* s_w) {
   return pre + inc - x;
 }
 
-// Stable scatter of one pass. Ranks come from warp match masks in item order;
-// the tile is first reordered by digit in shared memory, so each digit's run is
+// Stable scatter of one pass. A warp ranks its RS_ROUNDS rounds of 32 items in
+// item order: the lanes holding the same digit are found with eight ballots, and
+// the lowest of them adds the run to the warp's count of that digit with one
+// shared atomic, the rounds separated by __syncwarp (which orders the atomics of
+// different lanes) so that all are in flight before the first result is read.
+// The tile is then reordered by digit in shared memory and each digit's run is
 // written to global memory by consecutive threads.
-#ifdef ADP_RS_SCATTER_MINB
-#define ADP_RS_SCATTER_BOUNDS __launch_bounds__(RS_THREADS, ADP_RS_SCATTER_MINB)
-#else
-#define ADP_RS_SCATTER_BOUNDS __launch_bounds__(RS_THREADS)
-#endif
-__global__ void ADP_RS_SCATTER_BOUNDS
+// Four resident blocks per SM (64 registers, no spills) hide the shared-memory
+// latency of the ranking better than three at the unconstrained 76-80 registers.
+__global__ void __launch_bounds__(RS_THREADS, 4)
     rs_scatter_kernel(const unsigned* keys_in, const unsigned* vals_in, unsigned* keys_out,
                       unsigned* vals_out, const long long* d_n, long long tiles_max, DigitOp op,
                       const unsigned* hist, const unsigned* digit_tot, bool drop_none) {
   __shared__ unsigned s_base[RS_BINS];             // global start of every digit
   __shared__ unsigned s_whist[RS_WARPS][RS_BINS];  // per-warp counts, then warp prefixes
   __shared__ unsigned s_lbase[RS_BINS];            // start of every digit within the tile
-  __shared__ unsigned s_gpos[RS_BINS];             // global start of the tile's digit run
+  __shared__ unsigned s_delta[RS_BINS];            // global minus tile position of the digit
   __shared__ unsigned s_w[RS_WARPS];
   __shared__ unsigned s_keys[RS_TILE];
   __shared__ unsigned s_vals[RS_TILE];
@@ -185,11 +186,10 @@ __global__ void ADP_RS_SCATTER_BOUNDS
     for (int d = threadIdx.x; d < RS_WARPS * RS_BINS; d += RS_THREADS) (&s_whist[0][0])[d] = 0;
     __syncthreads();
     const long long tile0 = t * RS_TILE;
-    const int in_tile = (int)min((long long)RS_TILE, N - tile0);
     const long long base = tile0 + (long long)warp * (RS_ROUNDS * 32);
-    unsigned key[RS_ROUNDS], val[RS_ROUNDS], dig[RS_ROUNDS], off[RS_ROUNDS];
+    unsigned key[RS_ROUNDS], val[RS_ROUNDS], dig[RS_ROUNDS], peers[RS_ROUNDS], off[RS_ROUNDS];
 #pragma unroll
-    for (int r = 0; r < RS_ROUNDS; ++r) {  // issue every load before the ranking loop
+    for (int r = 0; r < RS_ROUNDS; ++r) {  // issue every load before the ranking
       long long i = base + r * 32 + lane;
       key[r] = i < N ? keys_in[i] : 0u;
       val[r] = i < N ? vals_in[i] : 0u;
@@ -197,15 +197,28 @@ __global__ void ADP_RS_SCATTER_BOUNDS
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
       long long i = base + r * 32 + lane;
-      bool valid = i < N && !(drop_none && key[r] == RS_DROP_KEY);
-      unsigned d = valid ? op(key[r], val[r]) : (unsigned)RS_BINS;
+      const bool valid = i < N && !(drop_none && key[r] == RS_DROP_KEY);
+      const unsigned d = valid ? op(key[r], val[r]) : (unsigned)RS_BINS;
       dig[r] = d;
-      unsigned peers = __match_any_sync(0xffffffffu, d);
-      unsigned before = valid ? s_whist[warp][d] : 0u;
-      off[r] = before + __popc(peers & lt);
+      unsigned p = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const unsigned m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+        p &= ((d >> b) & 1u) ? m : ~m;
+      }
+      peers[r] = valid ? p : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+      off[r] = 0u;
+      if (peers[r] != 0u && (peers[r] & lt) == 0u)
+        off[r] = atomicAdd(&s_whist[warp][dig[r]], (unsigned)__popc(peers[r]));
       __syncwarp();
-      if (valid && (peers & lt) == 0) s_whist[warp][d] = before + __popc(peers);
-      __syncwarp();
+    }
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+      const int leader = peers[r] != 0u ? __ffs(peers[r]) - 1 : lane;
+      off[r] = __shfl_sync(0xffffffffu, off[r], leader) + __popc(peers[r] & lt);
     }
     __syncthreads();
     unsigned cnt;
@@ -222,7 +235,7 @@ __global__ void ADP_RS_SCATTER_BOUNDS
     unsigned lb = block_excl_scan(cnt, s_w);
     s_lbase[threadIdx.x] = lb;
     if (threadIdx.x == RS_BINS - 1) s_kept = lb + cnt;
-    s_gpos[threadIdx.x] = s_base[threadIdx.x] + hist[(size_t)threadIdx.x * tiles_max + t];
+    s_delta[threadIdx.x] = s_base[threadIdx.x] + hist[(size_t)threadIdx.x * tiles_max + t] - lb;
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
@@ -235,12 +248,15 @@ __global__ void ADP_RS_SCATTER_BOUNDS
     }
     __syncthreads();
     const int kept = (int)s_kept;
-    for (int j = threadIdx.x; j < kept; j += RS_THREADS) {
-      unsigned k = s_keys[j], vv = s_vals[j];
-      unsigned d = op(k, vv);
-      unsigned pos = s_gpos[d] + (unsigned)j - s_lbase[d];
-      keys_out[pos] = k;
-      vals_out[pos] = vv;
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {  // kept <= RS_TILE
+      const int j = r * RS_THREADS + (int)threadIdx.x;
+      if (j < kept) {
+        const unsigned k = s_keys[j], vv = s_vals[j];
+        const unsigned pos = s_delta[op(k, vv)] + (unsigned)j;
+        keys_out[pos] = k;
+        vals_out[pos] = vv;
+      }
     }
     __syncthreads();
   }
