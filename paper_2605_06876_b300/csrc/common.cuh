@@ -301,7 +301,7 @@ int scan_exclusive(Load load, Store store, long long n_max, const long long* d_n
 // Stable LSD radix sort of (uint32 key, uint32 value) pairs, 8-bit digits, the
 // item count read from device memory. Each pass: per-tile digit histograms, a
 // per-digit scan over tiles, and a stable scatter whose ranks come from warp
-// match masks in item order.
+// ballots in item order.
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ROUNDS = 8;  // items per lane

@@ -6,9 +6,11 @@ the forward, the L1 error statistics, the backward and the error regions of thos
 views. Two exchanges make every rank's result that of one process doing all views:
 
 - the per-Gaussian sums over views -- the gradient, the error-pixel counts and the
-  error masses -- are summed over ranks (all-reduce). The masses are sums of
-  float32 E values above the threshold, which are exact in float64, so their sum
-  over ranks does not depend on the order; the gradient agrees to float rounding;
+  error masses -- are summed over ranks (all-reduce; the gradient's rows that a
+  rank did not render are zeroed first, and its row mask becomes the union). The
+  masses are sums of float32 E values above the threshold, which are exact in
+  float64, so their sum over ranks does not depend on the order; the gradient
+  agrees to float rounding;
 - the error regions of each rank's views are gathered by every rank (the tables
   have different lengths) and put in the global (view, label) order before the
   per-parent merge of Eqs. 11-12, which then sees every view's proposals.
@@ -37,6 +39,24 @@ def allreduce_sums(tensors, group=None):
     for t in tensors:
         dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     return tensors
+
+
+def allreduce_masked_gradient(planes, rows, group=None):
+    """Sums a row-masked gradient over the ranks, in place.
+
+    planes: the gradient's float planes ([n, 4] tensors, or [P, n, 4] for the SH
+    planes); rows: uint8 [n], 1 where this rank wrote the row. Rows with rows == 0
+    hold no defined values (the backward never writes them), so they are zeroed
+    before the sum; the mask becomes the union over ranks."""
+    unset = rows == 0
+    for t in planes:
+        if t.dim() == 3:
+            t.masked_fill_(unset[None, :, None], 0.0)
+        else:
+            t.masked_fill_(unset[:, None], 0.0)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    dist.all_reduce(rows, op=dist.ReduceOp.MAX, group=group)
+    return planes, rows
 
 
 def _gather_rows(t, group=None):
@@ -111,7 +131,8 @@ class ViewShardedStep:
         ops = self.ops
         st = self.local
         st.run()
-        allreduce_sums([*st.grad.tensors(), st.count, st.mass], self.group)
+        allreduce_masked_gradient(st.grad.tensors(), st.grad.rows, self.group)
+        allreduce_sums([st.count, st.mass], self.group)
         ops.select_topk(st.mass, self.g.n, self.k, self.cand, status=st.status)
         regs = ops.error_regions(st.maps, st.img.dominant, self.target, self.g.n, self.cams,
                                  self.cand, self.params, status=st.status)

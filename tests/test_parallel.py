@@ -121,3 +121,59 @@ def test_view_sharded_exchange_equals_one_process():
         assert res["new_n"] == sp["new_n"]
         assert np.array_equal(res["theta"], sp["theta"])
     assert (ref["split"]["status"] == O.ADAPTIVE).sum() > 0
+
+
+def _masked_rank_main(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    from paper_2605_06876_b300.parallel import allreduce_masked_gradient
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        n = 40
+        rng = np.random.default_rng(7)  # the same draws on both ranks
+        dense = [rng.standard_normal((2, n, 4)).astype(np.float32) for _ in range(2)]  # [rank]
+        sh = [rng.standard_normal((2, 3, n, 4)).astype(np.float32) for _ in range(2)]
+        marks = rng.random((2, n)) < 0.4
+        rows = torch.as_tensor(marks[rank].astype(np.uint8))
+        planes = [torch.as_tensor(dense[0][rank].copy()), torch.as_tensor(dense[1][rank].copy()),
+                  torch.as_tensor(sh[0][rank].copy())]
+        # rows this rank did not write hold no defined values
+        for t in planes:
+            if t.dim() == 3:
+                t[:, ~torch.as_tensor(marks[rank])] = float("nan")
+            else:
+                t[~torch.as_tensor(marks[rank])] = float("nan")
+        allreduce_masked_gradient(planes, rows)
+        out.put((rank, [t.numpy() for t in planes], rows.numpy(), dense, sh, marks))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_masked_gradient_allreduce_ignores_unwritten_rows():
+    """Each rank's row-masked gradient leaves the rows it did not render undefined
+    (NaN here); the exchange must give on every rank the sum of the ranks' written
+    rows (zero where no rank wrote) and the union of the masks."""
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_masked_rank_main, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = [out.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, planes, rows, dense, sh, marks in got:
+        m = marks.astype(np.float32)
+        want = [sum(dense[0][r] * m[r][:, None] for r in range(2)),
+                sum(dense[1][r] * m[r][:, None] for r in range(2)),
+                sum(sh[0][r] * m[r][None, :, None] for r in range(2))]
+        for a, b in zip(planes, want):
+            assert np.isfinite(a).all()
+            np.testing.assert_allclose(a, b, rtol=0, atol=1e-6)
+        np.testing.assert_array_equal(rows, (marks[0] | marks[1]).astype(np.uint8))
