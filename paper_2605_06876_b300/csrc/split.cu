@@ -640,24 +640,31 @@ __device__ __forceinline__ float4* plane_of(const GaussPtrs& g, int q, long long
 // Kept rows: one thread per (row, plane), blockIdx.y the plane (0 mean+logit,
 // 1 log-scale, 2 quaternion, 3.. SH), so a block streams one plane of the
 // parameters and moments (and gradients); the row's destination is one 32-bit
-// word, so re-reading it for every plane costs little. With ADAM, each kept
+// word, re-read for every plane from L2. With ADAM, each kept
 // non-candidate row gets the update adp_adam_step makes, bit for bit (candidates
 // got theirs before the plan); moments in and out are then required.
+
+// The row streams are read and written with the evict-first (streaming) cache
+// hint, so the destination words and the gradient row mask, which every plane
+// reads again, stay in L2 while the 15 planes stream past.
+__device__ __forceinline__ float4 ld_row(const float4* p) { return __ldcs(p); }
+__device__ __forceinline__ void st_row(float4* p, float4 v) { __stcs(p, v); }
+
 template <bool ADAM>
 __device__ __forceinline__ void keep_row(const ApplyArgs& a, int q, long long i) {
   if (i >= a.in.n) return;
-  // every independent load first (the destination and the streams), then the
-  // gradient, whose load waits only for the row mask; removed rows are read in vain
+  // the destination first: a removed candidate's row is not read; then every
+  // stream, and the gradient, whose load waits only for the row mask
   const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
   const long long n_new = *a.fit;
   const unsigned d = a.dest[i];
-  const bool gl = ADAM && (!a.grad_rows || a.grad_rows[i]);
-  float4 p = *plane_of(a.in, q, i);
-  float4 m = a.has_m_in ? *plane_of(a.min_, q, i) : z;
-  float4 v = a.has_v_in ? *plane_of(a.vin, q, i) : z;
-  const float4 g = gl ? *plane_of(a.grad, q, i) : z;
-  if (n_new > a.out.n) return;  // the new population does not fit: write nothing
   if (d == 0xffffffffu) return;  // a removed candidate
+  const bool gl = ADAM && (!a.grad_rows || a.grad_rows[i]);
+  float4 p = ld_row(plane_of(a.in, q, i));
+  float4 m = a.has_m_in ? ld_row(plane_of(a.min_, q, i)) : z;
+  float4 v = a.has_v_in ? ld_row(plane_of(a.vin, q, i)) : z;
+  const float4 g = gl ? ld_row(plane_of(a.grad, q, i)) : z;
+  if (n_new > a.out.n) return;  // the new population does not fit: write nothing
   const long long j = d & 0x7fffffffu;
   if (j >= a.out.n) return;
   if (ADAM && !(d >> 31)) {  // candidates got their step before the plan
@@ -665,9 +672,9 @@ __device__ __forceinline__ void keep_row(const ApplyArgs& a, int q, long long i)
     adam_plane_lr(a.adam, q, lr4);
     adam_vec4(p, g, m, v, lr4, a.adam, adam_bias(a.adam));
   }
-  *plane_of(a.out, q, j) = p;
-  if (a.has_m_out) *plane_of(a.mout, q, j) = m;
-  if (a.has_v_out) *plane_of(a.vout, q, j) = v;
+  st_row(plane_of(a.out, q, j), p);
+  if (a.has_m_out) st_row(plane_of(a.mout, q, j), m);
+  if (a.has_v_out) st_row(plane_of(a.vout, q, j), v);
 }
 
 template <bool ADAM>
