@@ -122,12 +122,24 @@ __global__ void err_norm_kernel(float* E, uint8_t* mask, const unsigned* minmax_
 }
 
 // Converts the fixed-point mass sums (held in the mass array) to doubles in place.
+// q * 2^-shift as a double, exactly, for q < 2^53: the IEEE-754 fields are built
+// from the integer (exponent from the leading bit, the bits below it as the
+// fraction), with no FP64 instruction (B300's FP64 rate is a small fraction of its
+// FP32 rate). Larger q take the FP64 conversion.
+__device__ __forceinline__ double fixed_to_double(unsigned long long q, int shift) {
+  if (q == 0ull) return 0.0;
+  if (q >> 53) return (double)q * ldexp(1.0, -shift);
+  const int e = 63 - __clzll((long long)q);  // q in [2^e, 2^(e+1))
+  const unsigned long long frac = (q << (52 - e)) & ((1ull << 52) - 1ull);
+  const unsigned long long bits = ((unsigned long long)(1023 + e - shift) << 52) | frac;
+  return __longlong_as_double((long long)bits);
+}
+
 __global__ void mass_finalize_kernel(double* mass, long long n, int mass_shift) {
-  const double inv = ldexp(1.0, -mass_shift);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    unsigned long long q = reinterpret_cast<unsigned long long*>(mass)[i];
-    mass[i] = (double)q * inv;
+    const unsigned long long q = reinterpret_cast<unsigned long long*>(mass)[i];
+    mass[i] = fixed_to_double(q, mass_shift);
   }
 }
 
