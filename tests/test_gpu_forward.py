@@ -189,3 +189,27 @@ def test_full_size_sampled_pixels():
     sub = ops.Image(*(t[torch.as_tensor(pix, device=DEV)] for t in
                       (img.rgb, img.T, img.n_contrib, img.last, img.dominant)))
     _compare_render(sub, o, "1M Gaussians 1280x832, sampled")
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2, 3])
+def test_multi_view_projection_equals_single_view(deg):
+    """The several-view projection kernel (one screening of each Gaussian for all
+    views, survivors projected per block) against the one-view kernel, per SH
+    degree: every view's records, bit for bit."""
+    sc = scenes.scene_clusters(60 + deg, 30000, deg)
+    cams = scenes.ring_cameras(61, 3, 4.0, 160, 96)
+    g = ops.Gaussians.from_scene(sc, DEV)
+    pr = ops.project(g, cams)
+    torch.cuda.synchronize()
+    n = g.n
+    for v, cam in enumerate(cams):
+        p1 = ops.project(g, [cam])
+        torch.cuda.synchronize()
+        t1 = np_(p1.tiles)
+        assert np.array_equal(t1, np_(pr.tiles)[v * n:(v + 1) * n])
+        vis = t1 > 0
+        assert vis.sum() > 1000
+        for name in ("xyod", "conic", "rgb", "rect"):
+            a = np_(getattr(p1, name))[:n][vis]
+            b = np_(getattr(pr, name))[v * n:(v + 1) * n][vis]
+            assert np.array_equal(a, b), (v, name)
