@@ -181,11 +181,32 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i, fl
   }
 #pragma unroll
   for (int f = 0; f < 4 * planes; ++f) acc[f * BWDG_THREADS] = 0.f;
-  for (int v = 0; v < cs.n_views; ++v) {
-    long long rec = (long long)v * a.n + i;
-    if (a.tiles[rec] <= 0) continue;
-    // pixel moments of dL/dalpha * alpha (see the per-pixel pass)
-    float4 q0 = a.g2d[3 * rec], q1 = a.g2d[3 * rec + 1], q2 = a.g2d[3 * rec + 2];
+  // the views that render this Gaussian, from loads issued together; the next
+  // view's pixel moments are fetched while the current one is worked on
+  unsigned vmask = 0u;
+  for (int v = 0; v < cs.n_views; ++v)
+    vmask |= (a.tiles[(long long)v * a.n + i] > 0 ? 1u : 0u) << v;
+  float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0, n2 = n0;
+  float nw = 0.f;
+  if (vmask) {
+    const long long r0 = (long long)(__ffs(vmask) - 1) * a.n + i;
+    n0 = a.g2d[3 * r0];
+    n1 = a.g2d[3 * r0 + 1];
+    n2 = a.g2d[3 * r0 + 2];
+    nw = a.rgb[r0].w;
+  }
+  while (vmask) {
+    const int v = __ffs(vmask) - 1;
+    vmask &= vmask - 1u;
+    const float4 q0 = n0, q1 = n1, q2 = n2;  // pixel moments of dL/dalpha * alpha
+    const int clamped = (int)nw;
+    if (vmask) {
+      const long long rn = (long long)(__ffs(vmask) - 1) * a.n + i;
+      n0 = a.g2d[3 * rn];
+      n1 = a.g2d[3 * rn + 1];
+      n2 = a.g2d[3 * rn + 2];
+      nw = a.rgb[rn].w;
+    }
     const float mS = q0.x, mSx = q0.y, mSy = q0.z;
     float gA = -0.5f * q0.w, gB = -q1.x, gC = -0.5f * q1.y;
     float gcol[3] = {q1.z, q1.w, q2.x};
@@ -207,7 +228,6 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i, fl
     float Y[16];
     sh_eval_basis(DEG, u[0], u[1], u[2], Y);
     // channels the projection clamped at 0 pass no gradient
-    const int clamped = (int)a.rgb[rec].w;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch)
       if (clamped & (1 << ch)) gcol[ch] = 0.f;
@@ -237,8 +257,7 @@ __device__ void bwd_one(const BwdGaussArgs& a, const CamSet& cs, long long i, fl
     float ud = gu[0] * u[0] + gu[1] * u[1] + gu[2] * u[2];
     for (int k = 0; k < 3; ++k) gmu[k] += (gu[k] - ud * u[k]) * il;
     // EWA
-    float limx = 1.3f * (float)cam.width / (2.f * cam.fx);
-    float limy = 1.3f * (float)cam.height / (2.f * cam.fy);
+    const float limx = cs.lim_x[v], limy = cs.lim_y[v];
     float txz = pc[0] * iz, tyz = pc[1] * iz;
     bool clx = txz < -limx || txz > limx, cly = tyz < -limy || tyz > limy;
     float ux = fminf(limx, fmaxf(-limx, txz)), uy = fminf(limy, fmaxf(-limy, tyz));

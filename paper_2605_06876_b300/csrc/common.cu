@@ -45,6 +45,8 @@ int make_camset(const adp_camera* cams, int n_views, const adp_params* prm, CamS
                   "view %d: bad size %dx%d", v, c.width, c.height);
     ADP_CHECK_ARG(c.fx > 0 && c.fy > 0, "view %d: focal lengths must be positive", v);
     cs->cam[v] = c;
+    cs->lim_x[v] = 1.3f * (float)c.width / (2.f * c.fx);
+    cs->lim_y[v] = 1.3f * (float)c.height / (2.f * c.fy);
     cs->tiles_x[v] = (c.width + prm->tile_w - 1) / prm->tile_w;
     cs->tiles_y[v] = (c.height + prm->tile_h - 1) / prm->tile_h;
     long long nt = (long long)cs->tile_base[v] + (long long)cs->tiles_x[v] * cs->tiles_y[v];

@@ -80,6 +80,11 @@ struct CamSet {
   int tiles_y[ADP_MAX_VIEWS];
   int tile_base[ADP_MAX_VIEWS + 1];
   long long pix_base[ADP_MAX_VIEWS + 1];
+  // the EWA Jacobian's clamp of x/z and y/z: 1.3 times the tangent of the half
+  // field of view, 1.3 W / (2 fx) and 1.3 H / (2 fy), each a product and a
+  // correctly rounded division, so the host computes exactly what a kernel would
+  float lim_x[ADP_MAX_VIEWS];
+  float lim_y[ADP_MAX_VIEWS];
 };
 
 int make_camset(const adp_camera* cams, int n_views, const adp_params* prm, CamSet* cs);

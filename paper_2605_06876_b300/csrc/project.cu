@@ -62,8 +62,7 @@ __device__ __forceinline__ void project_view(const ProjectArgs& a, const CamSet&
   if (vis) {
     // J with x/z, y/z clamped to 1.3x the half field of view
     float inv_z = 1.f / pcz;
-    float limx = 1.3f * (float)cam.width / (2.f * cam.fx);
-    float limy = 1.3f * (float)cam.height / (2.f * cam.fy);
+    const float limx = cs.lim_x[v], limy = cs.lim_y[v];
     float ux = fminf(limx, fmaxf(-limx, pcx * inv_z));
     float uy = fminf(limy, fmaxf(-limy, pcy * inv_z));
     float j00 = cam.fx * inv_z, j02 = -cam.fx * ux * inv_z;
@@ -186,12 +185,6 @@ __device__ __forceinline__ CullG cull_gaussian(const ProjectArgs& a, float4 ml, 
   return c;
 }
 
-// The clamp of the EWA Jacobian: 1.3 times the tangent of the half field of view.
-__device__ __forceinline__ float2 cull_limits(const adp_camera& cam) {
-  return make_float2(1.3f * (float)cam.width / (2.f * cam.fx),
-                     1.3f * (float)cam.height / (2.f * cam.fy));
-}
-
 __device__ __forceinline__ bool cull_view(const ProjectArgs& a, const adp_camera& cam, float2 lim,
                                           const CullG& c) {
   const float* Rw = cam.R;
@@ -240,8 +233,6 @@ template <int DEG>
 __global__ void __launch_bounds__(VIEWS_THREADS) project_views_kernel(ProjectArgs a, CamSet cs) {
   __shared__ int s_list[VIEWS_CHUNK * ADP_MAX_VIEWS];
   __shared__ int s_cnt;
-  __shared__ float2 s_lim[ADP_MAX_VIEWS];
-  if (threadIdx.x < cs.n_views) s_lim[threadIdx.x] = cull_limits(cs.cam[threadIdx.x]);
   for (long long c0 = (long long)blockIdx.x * VIEWS_CHUNK; c0 < a.n;
        c0 += (long long)gridDim.x * VIEWS_CHUNK) {
     if (threadIdx.x == 0) s_cnt = 0;
@@ -254,7 +245,8 @@ __global__ void __launch_bounds__(VIEWS_THREADS) project_views_kernel(ProjectArg
       c.live = false;
       if (in) c = cull_gaussian(a, a.mean_logit[i], a.logscale[i]);
       for (int v = 0; v < cs.n_views; ++v) {
-        const bool vis = c.live && cull_view(a, cs.cam[v], s_lim[v], c);
+        const bool vis =
+            c.live && cull_view(a, cs.cam[v], make_float2(cs.lim_x[v], cs.lim_y[v]), c);
         if (in && !vis) write_culled(a, (long long)v * a.n + i);
         append_survivor(s_list, &s_cnt, vis, (v << 16) | q);
       }
@@ -280,7 +272,7 @@ __global__ void __launch_bounds__(PROJ_THREADS) project_kernel(ProjectArgs a, Ca
   __shared__ int s_list[PROJ_CHUNK];
   __shared__ int s_cnt;
   const int v = blockIdx.y;
-  const float2 lim = cull_limits(cs.cam[v]);
+  const float2 lim = make_float2(cs.lim_x[v], cs.lim_y[v]);
   for (long long c0 = (long long)blockIdx.x * PROJ_CHUNK; c0 < a.n;
        c0 += (long long)gridDim.x * PROJ_CHUNK) {
     if (threadIdx.x == 0) s_cnt = 0;
