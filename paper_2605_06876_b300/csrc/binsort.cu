@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
     const unsigned* vvals, const long long* offs, const int* chunk_first, const long long* d_nvis,
     const long long* d_K, long long cap, const int4* rect, const float4* xyod, const float4* conic,
     float alpha_min, long long n, CamSet cs, int view_shift, unsigned* tkeys, int* inst,
-    bool inst_vec, unsigned* hist, long long tiles_max) {
+    bool inst_vec, unsigned hist_mask, unsigned* hist, long long tiles_max) {
   __shared__ int s_off[DUP_CHUNK + 1];  // record offsets of the chunk (the first may be < 0)
   __shared__ int s_i[DUP_REC];          // Gaussian id
   __shared__ int s_org[DUP_REC];        // first tile column | first tile row << 16
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
         }
         keys[h] = key;
         ids[h] = s_i[q];
-        if (key != TILE_NONE) atomicAdd(&s_h[key & 255u], 1u);  // the sort drops the others
+        if (key != TILE_NONE) atomicAdd(&s_h[key & hist_mask], 1u);  // the sort drops the others
       }
       __syncthreads();  // the batch's records and marks are no longer read
     }
@@ -213,7 +213,8 @@ __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
         }
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < RS_BINS; d += DUP_THREADS) hist[(size_t)d * tiles_max + t] = s_h[d];
+    for (int d = threadIdx.x; d <= (int)hist_mask; d += DUP_THREADS)
+      hist[(size_t)d * tiles_max + t] = s_h[d];
   }
 }
 
@@ -346,7 +347,7 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
   DigitOp passes[5];
   int np = 0;
   for (int s = 0; s < 32; s += 8) passes[np++] = DigitOp{s, 0u};
-  if (n_views > 1) passes[np++] = DigitOp{0, (unsigned)n};
+  if (n_views > 1) passes[np++] = DigitOp{0, (unsigned)n, bits_for(n_views - 1)};
   // the sorted records stay where the last pass wrote them (the tile sort reuses
   // the alternate buffers only after the duplication has read them)
   unsigned* skeys = nullptr;
@@ -379,16 +380,23 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
   // stable), and the runs are ordered by local tile, then view. Instances whose
   // ellipse misses their tile get the key TILE_NONE, which the first pass drops.
   if (cap > 0) {
+    // the tile passes split the tile bits evenly (13 bits: 7 + 6), fewer bits per
+    // pass than 8 where that takes no extra pass
+    DigitOp tp[4];
+    const int ntp = (tile_bits + 7) / 8 > 0 ? (tile_bits + 7) / 8 : 1;
+    for (int q = 0, s = 0; q < ntp; ++q) {
+      const int b = (tile_bits - s + (ntp - q) - 1) / (ntp - q);  // ceil of the rest
+      tp[q] = DigitOp{s, 0u, b < 1 ? 1 : b};
+      s += b;
+    }
     duplicate_kernel<<<(unsigned)std::min<long long>((cap + DUP_CHUNK - 1) / DUP_CHUNK, 148 * 8),
                        DUP_THREADS, 0, st>>>(
         vvals, offs, chunk_first, &w.counters[0], &w.counters[1], cap,
         reinterpret_cast<const int4*>(pr->rect), xyod,
         reinterpret_cast<const float4*>(pr->conic), prm->alpha_min, n, cs, view_shift, w.tkeys,
-        bins->inst_gauss, aligned(bins->inst_gauss, 16), w.sort.hist, w.sort.tiles_max);
+        bins->inst_gauss, aligned(bins->inst_gauss, 16), tp[0].mask(), w.sort.hist,
+        w.sort.tiles_max);
     ADP_LAUNCH_CHECK();
-    DigitOp tp[4];
-    int ntp = 0;
-    for (int s = 0; s < tile_bits; s += 8) tp[ntp++] = DigitOp{s, 0u};
     // the first pass's tile histograms come from the duplication, which leaves out the
     // instances whose ellipse misses their tile; the first pass drops them and the
     // count becomes the kept instances

@@ -87,7 +87,7 @@ __global__ void rs_hist_kernel(const unsigned* keys, const unsigned* vals, const
     for (int k = 0; k < RS_ROUNDS; ++k)
       if (d[k] < (unsigned)RS_BINS) atomicAdd(&s_hist[d[k]], 1u);
     __syncthreads();
-    hist[(size_t)threadIdx.x * tiles_max + t] = s_hist[threadIdx.x];
+    if ((int)threadIdx.x < op.bins()) hist[(size_t)threadIdx.x * tiles_max + t] = s_hist[threadIdx.x];
     __syncthreads();
   }
 }
@@ -97,9 +97,13 @@ __global__ void rs_hist_kernel(const unsigned* keys, const unsigned* vals, const
 // each with two barriers, even for tens of thousands of tiles).
 constexpr int RS_SCAN_ITEMS = 8;
 __global__ void rs_scan_kernel(unsigned* hist, const long long* d_n, long long tiles_max,
-                               unsigned* digit_tot) {
+                               int bins, unsigned* digit_tot) {
   __shared__ unsigned s_warp[RS_WARPS];
   __shared__ unsigned s_carry;
+  if ((int)blockIdx.x >= bins) {  // a digit the pass cannot produce
+    if (threadIdx.x == 0) digit_tot[blockIdx.x] = 0u;
+    return;
+  }
   long long N = *d_n;
   long long nt = (N + RS_TILE - 1) / RS_TILE;
   if (nt > tiles_max) nt = tiles_max;
@@ -205,8 +209,10 @@ __global__ void __launch_bounds__(RS_THREADS, 4)
       unsigned p = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
-        const unsigned m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-        p &= ((d >> b) & 1u) ? m : ~m;
+        if (b < op.bits) {  // uniform: the pass's digit width
+          const unsigned m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+          p &= ((d >> b) & 1u) ? m : ~m;
+        }
       }
       peers[r] = valid ? p : 0u;
     }
@@ -237,7 +243,9 @@ __global__ void __launch_bounds__(RS_THREADS, 4)
     unsigned lb = block_excl_scan(cnt, s_w);
     s_lbase[threadIdx.x] = lb;
     if (threadIdx.x == RS_BINS - 1) s_kept = lb + cnt;
-    s_delta[threadIdx.x] = s_base[threadIdx.x] + hist[(size_t)threadIdx.x * tiles_max + t] - lb;
+    s_delta[threadIdx.x] =
+        s_base[threadIdx.x] +
+        ((int)threadIdx.x < op.bins() ? hist[(size_t)threadIdx.x * tiles_max + t] : 0u) - lb;
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
@@ -382,7 +390,8 @@ int radix_sort_pairs(unsigned* keys, unsigned* vals, long long* d_n, long long n
     if (p > 0 || !first_hist_done)
       rs_hist_kernel<<<(unsigned)grid, RS_THREADS, 0, st>>>(ka, va, d_n, w.tiles_max, passes[p],
                                                              w.hist);
-    rs_scan_kernel<<<RS_BINS, RS_THREADS, 0, st>>>(w.hist, d_n, w.tiles_max, w.digit_tot);
+    rs_scan_kernel<<<RS_BINS, RS_THREADS, 0, st>>>(w.hist, d_n, w.tiles_max, passes[p].bins(),
+                                                    w.digit_tot);
     const bool drop = drop_none && first_hist_done && p == 0;
     rs_scatter_kernel<<<(unsigned)grid, RS_THREADS, 0, st>>>(ka, va, kb, vb, d_n, w.tiles_max,
                                                               passes[p], w.hist, w.digit_tot, drop);

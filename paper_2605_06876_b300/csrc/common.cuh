@@ -340,13 +340,17 @@ inline SortWorkspace carve_sort(Carver& c, long long n_max) {
   return w;
 }
 
-// Digit of an item: from the key (shift) or, when by_value, value / divisor
-// (used to order by view after a depth sort).
+// Digit of an item: `bits` bits (1 to 8) of the key from `shift` or, with a
+// divisor, of value / divisor (used to order by view after a depth sort). A pass
+// with fewer bits ranks with fewer ballots and scans fewer histogram rows.
 struct DigitOp {
   int shift;
   unsigned divisor;  // 0: digit from key
+  int bits = 8;
+  __host__ __device__ __forceinline__ unsigned mask() const { return (1u << bits) - 1u; }
+  __host__ __device__ __forceinline__ int bins() const { return 1 << bits; }
   __device__ __forceinline__ unsigned operator()(unsigned key, unsigned val) const {
-    return divisor ? (val / divisor) & 255u : (key >> shift) & 255u;
+    return divisor ? (val / divisor) & mask() : (key >> shift) & mask();
   }
 };
 
@@ -360,7 +364,7 @@ struct SmallPasses {
 __global__ void rs_hist_kernel(const unsigned* keys, const unsigned* vals, const long long* d_n,
                                long long tiles_max, DigitOp op, unsigned* hist);
 __global__ void rs_scan_kernel(unsigned* hist, const long long* d_n, long long tiles_max,
-                               unsigned* digit_tot);
+                               int bins, unsigned* digit_tot);
 __global__ void rs_scatter_kernel(const unsigned* keys_in, const unsigned* vals_in,
                                   unsigned* keys_out, unsigned* vals_out, const long long* d_n,
                                   long long tiles_max, DigitOp op, const unsigned* hist,
