@@ -213,3 +213,30 @@ def test_multi_view_projection_equals_single_view(deg):
             a = np_(getattr(p1, name))[:n][vis]
             b = np_(getattr(pr, name))[v * n:(v + 1) * n][vis]
             assert np.array_equal(a, b), (v, name)
+
+
+def test_large_binning_equals_per_view_binning():
+    """16 views of 150,000 Gaussians (2.4M records, one launch of every binning
+    kernel over all views): every (view, tile) list equals that view's list binned
+    alone, entry for entry."""
+    sc = scenes.scene_clusters(70, 150_000, 3)
+    cams = scenes.ring_cameras(71, 16, 4.0, 320, 208)
+    g = ops.Gaussians.from_scene(sc, DEV)
+    assert g.n * len(cams) >= 1 << 21
+    pr = ops.project(g, cams)
+    bins = ops.bin_sort(g.n, pr, cams)
+    torch.cuda.synchronize()
+    ranges = np_(bins.ranges).reshape(-1, 2)
+    inst = np_(bins.inst)
+    per_view_tiles = ranges.shape[0] // len(cams)
+    for v, cam in enumerate(cams):
+        p1 = ops.project(g, [cam])
+        b1 = ops.bin_sort(g.n, p1, [cam])
+        torch.cuda.synchronize()
+        r1 = np_(b1.ranges).reshape(-1, 2)
+        i1 = np_(b1.inst)
+        assert r1.shape[0] == per_view_tiles
+        for t in range(per_view_tiles):
+            a0, a1 = ranges[v * per_view_tiles + t]
+            c0, c1 = r1[t]
+            assert np.array_equal(inst[a0:a1], i1[c0:c1]), (v, t)
