@@ -239,3 +239,23 @@ def test_batched_edge_cases(case):
         assert torch.equal(img.rgb, want) and bool((img.dominant == -1).all())
         if g.n:
             assert not bool(grad.rows.any()) and not bool(count.any())
+
+
+def test_batched_instance_overflow_is_reported():
+    """Too small an instance capacity (1,024 for about a million instances): the
+    call runs to its end without a device error, writes nothing past the capacity
+    and reports the count it needs, which equals the count an ample capacity sees."""
+    sc, _ = small_cluster_inputs(20000, 8, 8, seed=44)
+    cams = _uneven_cams(45)
+    target = _target(cams, 46)
+    g = ops.Gaussians.from_scene(sc, DEV)
+    small = BatchedStep(g, cams, target, bins_margin=0.0)
+    assert small.bins.capacity == 1024
+    small.run()
+    torch.cuda.synchronize()
+    assert not small.fits()  # fits() also checks the status word
+    ample = BatchedStep(g, cams, target)
+    ample.run()
+    torch.cuda.synchronize()
+    assert ample.fits()
+    assert int(small.bins.n_inst.item()) == int(ample.bins.n_inst.item()) > 1024
