@@ -162,10 +162,11 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned* s_w) {
 }
 
 // Stable scatter of one pass. A warp ranks its RS_ROUNDS rounds of 32 items in
-// item order: the lanes holding the same digit are found with eight ballots, and
-// the lowest of them adds the run to the warp's count of that digit with one
-// shared atomic, the rounds separated by __syncwarp (which orders the atomics of
-// different lanes) so that all are in flight before the first result is read.
+// item order: the lanes holding the same digit are found with one ballot per digit
+// bit (the pass's 1 to 8), and the lowest of them adds the run to the warp's count
+// of that digit with one shared atomic, the rounds separated by __syncwarp (which
+// orders the atomics of different lanes) so that all are in flight before the first
+// result is read.
 // The tile is then reordered by digit in shared memory and each digit's run is
 // written to global memory by consecutive threads.
 // Four resident blocks per SM (64 registers, no spills) hide the shared-memory
