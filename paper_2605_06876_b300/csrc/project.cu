@@ -141,8 +141,8 @@ __device__ __forceinline__ void project_view(const ProjectArgs& a, const CamSet&
   }
 }
 
-// Full projection of Gaussian i into view v (the one-view kernel's compacted
-// survivors). The SH degree is a template parameter so that the SH arrays stay in
+// Full projection of Gaussian i into view v (a survivor of either kernel's
+// screen test). The SH degree is a template parameter so that the SH arrays stay in
 // registers.
 template <int DEG>
 __device__ void project_one(const ProjectArgs& a, const CamSet& cs, long long i, int v) {
