@@ -462,10 +462,12 @@ extern "C" ADP_API int adp_render_backward(const adp_gaussians* g, const adp_pro
   int* list = cv.take<int>(g->n);
   unsigned long long* n_list = cv.take<unsigned long long>(1);
   int* tile_ctr = cv.take<int>(1);
-  rc = zero_visible_moments(pr->tiles_touched, (long long)g->n * n_views, g2d, st);
+  // the list count and the tile counter are reset by the same launch
+  FillSet fill;
+  fill.add(n_list, sizeof(unsigned long long));
+  fill.add(tile_ctr, sizeof(int));
+  rc = zero_visible_moments(pr->tiles_touched, (long long)g->n * n_views, g2d, fill, st);
   if (rc) return rc;
-  ADP_CUDA(cudaMemsetAsync(n_list, 0, sizeof(unsigned long long), st));
-  ADP_CUDA(cudaMemsetAsync(tile_ctr, 0, sizeof(int), st));
   BwdPixArgs pa;
   pa.xyod = reinterpret_cast<const float4*>(pr->xy_opacity_depth);
   pa.conic = reinterpret_cast<const float4*>(pr->conic);
@@ -505,7 +507,9 @@ namespace adp {
 // Zeroes the pixel-moment rows (three float4) of the visible records only: the
 // per-pixel pass adds to records in tile lists, and the per-Gaussian pass reads
 // records with tiles_touched > 0, so nothing reads the rows of culled records.
-__global__ void zero_visible_kernel(const int* tiles, long long n_rec, float4* g2d) {
+__global__ void zero_visible_kernel(const int* tiles, long long n_rec, float4* g2d, FillSet f) {
+  fill_ranges_device(f, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                     (long long)gridDim.x * blockDim.x);
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n_rec;
        r += (long long)gridDim.x * blockDim.x) {
     if (tiles[r] > 0) {
@@ -517,9 +521,10 @@ __global__ void zero_visible_kernel(const int* tiles, long long n_rec, float4* g
   }
 }
 
-int zero_visible_moments(const int* tiles, long long n_rec, float4* g2d, cudaStream_t st) {
-  if (n_rec <= 0) return ADP_OK;
-  zero_visible_kernel<<<grid_for(n_rec, 256, 148 * 16), 256, 0, st>>>(tiles, n_rec, g2d);
+int zero_visible_moments(const int* tiles, long long n_rec, float4* g2d, const FillSet& f,
+                         cudaStream_t st) {
+  if (n_rec <= 0) return launch_fill(f, st);
+  zero_visible_kernel<<<grid_for(n_rec, 256, 148 * 16), 256, 0, st>>>(tiles, n_rec, g2d, f);
   ADP_LAUNCH_CHECK();
   return ADP_OK;
 }

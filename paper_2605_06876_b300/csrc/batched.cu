@@ -221,9 +221,12 @@ extern "C" ADP_API int adp_train_step_batched(
   // (with no Gaussian every tile list is empty: the image is the background, and the
   // error maps and the statistics follow from it)
   // 3. the fused forward + error epilogue + backward over the (view, tile) queue
-  ADP_CUDA(cudaMemsetAsync(w.n_list, 0, sizeof(unsigned long long), st));
-  ADP_CUDA(cudaMemsetAsync(w.item_ctr, 0, sizeof(int), st));
-  rc = error_minmax_init(maps, n_views, st);
+  // the queue counters and the error statistics' presets, in one launch
+  FillSet fill;
+  fill.add(w.n_list, sizeof(unsigned long long));
+  fill.add(w.item_ctr, sizeof(int));
+  error_init_fill(fill, maps, n_views, count, mass, n);
+  rc = launch_fill(fill, st);
   if (rc) return rc;
   FusedArgs a;
   a.xyod = reinterpret_cast<const float4*>(pr->xy_opacity_depth);

@@ -256,7 +256,8 @@ __global__ void tile_ranges_kernel(const unsigned* tkeys, const long long* d_n, 
 
 struct BinWs {
   long long* counters;  // [0] visible; [1] clamped instance count, then the kept ones
-  void* scan;
+  void* scan;   // the compaction's scan
+  void* scan2;  // the instance offsets' scan
   unsigned* vkeys;
   unsigned* vvals;
   long long* offs;
@@ -269,7 +270,7 @@ static long long dup_chunks(long long cap) { return (cap + DUP_CHUNK - 1) / DUP_
 
 static size_t bin_ws_bytes(long long nv, long long cap) {
   long long m = nv > cap ? nv : cap;
-  return carve_bytes<long long>(4) + scan_workspace_bytes(nv) + 2 * carve_bytes<unsigned>(nv) +
+  return carve_bytes<long long>(4) + 2 * scan_workspace_bytes(nv) + 2 * carve_bytes<unsigned>(nv) +
          carve_bytes<long long>(nv) + carve_bytes<unsigned>(cap) + carve_bytes<int>(dup_chunks(cap)) +
          sort_workspace_bytes(m);
 }
@@ -279,6 +280,7 @@ static BinWs carve_bin(Carver& c, long long nv, long long cap) {
   long long m = nv > cap ? nv : cap;
   w.counters = c.take<long long>(4);
   w.scan = c.take<char>(scan_workspace_bytes(nv));
+  w.scan2 = c.take<char>(scan_workspace_bytes(nv));
   w.vkeys = c.take<unsigned>(nv);
   w.vvals = c.take<unsigned>(nv);
   w.offs = c.take<long long>(nv);
@@ -323,11 +325,19 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
                 "too many tiles per view for the tile key");
   cudaStream_t st = (cudaStream_t)stream;
   long long n_tiles = cs.tile_base[n_views];
-  ADP_CUDA(cudaMemsetAsync(bins->tile_range, 0, sizeof(int2) * n_tiles, st));
-  ADP_CUDA(cudaMemsetAsync(bins->n_instances, 0, sizeof(long long), st));
-  if (nv == 0) return ADP_OK;
+  // the empty tile ranges, the instance count and both scans' status words, in one launch
+  FillSet fill;
+  fill.add(bins->tile_range, sizeof(int2) * n_tiles);
+  fill.add(bins->n_instances, sizeof(long long));
   Carver c(ws, ws_bytes);
-  BinWs w = carve_bin(c, nv, cap);
+  BinWs w;
+  if (nv > 0) {
+    w = carve_bin(c, nv, cap);
+    scan_clear(fill, w.scan, nv);
+    scan_clear(fill, w.scan2, nv);
+  }
+  rc = launch_fill(fill, st);
+  if (rc || nv == 0) return rc;
   const int* tiles = pr->tiles_touched;
   const float4* xyod = reinterpret_cast<const float4*>(pr->xy_opacity_depth);
 
@@ -342,7 +352,7 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
           vvals[pre] = (unsigned)p;
         }
       },
-      nv, nullptr, &w.counters[0], w.scan, st, d_status);
+      nv, nullptr, &w.counters[0], w.scan, st, d_status, /*cleared=*/true);
   if (rc) return rc;
   count_guard_kernel<<<1, 1, 0, st>>>(scan_error_flag(w.scan, nv), &w.counters[0]);
 
@@ -371,10 +381,11 @@ extern "C" ADP_API int adp_bin_sort(int64_t n, const adp_projected* pr, const ad
                              c < n_chunk_max && c * DUP_CHUNK < end; ++c)
                           chunk_first[c] = (int)j;
                       },
-                      nv, &w.counters[0], (long long*)bins->n_instances, w.scan, st, d_status);
+                      nv, &w.counters[0], (long long*)bins->n_instances, w.scan2, st, d_status,
+                      /*cleared=*/true);
   if (rc) return rc;
   clamp_count_kernel<<<1, 1, 0, st>>>((const long long*)bins->n_instances, cap,
-                                      scan_error_flag(w.scan, nv), &w.counters[1]);
+                                      scan_error_flag(w.scan2, nv), &w.counters[1]);
 
   // 4. duplicate into tiles, 5. stable sort by tile. The instance key is the
   // view-local tile with the view above the sorted bits: the tile sort takes

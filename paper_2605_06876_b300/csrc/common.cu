@@ -442,6 +442,21 @@ __global__ void count_guard_kernel(const unsigned long long* err, long long* cou
   if (*err != 0ull) *count = 0;
 }
 
+__global__ void __launch_bounds__(256) fill_kernel(FillSet f) {
+  fill_ranges_device(f, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                     (long long)gridDim.x * blockDim.x);
+}
+
+int launch_fill(const FillSet& f, cudaStream_t st) {
+  ADP_CHECK_ARG(!f.overflow, "internal: more than %d ranges in one fill", FILL_MAX);
+  long long chunks = 0;
+  for (int s = 0; s < f.n; ++s) chunks = std::max(chunks, (f.bytes[s] + 15) / 16);
+  if (chunks == 0) return ADP_OK;
+  fill_kernel<<<grid_for(chunks, 256, 148 * 4), 256, 0, st>>>(f);
+  ADP_LAUNCH_CHECK();
+  return ADP_OK;
+}
+
 }  // namespace adp
 
 extern "C" {

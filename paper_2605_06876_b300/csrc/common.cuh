@@ -69,6 +69,59 @@ inline size_t carve_bytes(size_t count) {
   return bytes == 0 ? 256 : bytes;
 }
 
+// ----------------------------------------------------------------- fills
+
+// Up to FILL_MAX device ranges, each set to a repeated 64-bit pattern (byte o of
+// a range gets byte o % 8 of the pattern, the lowest byte first), by one kernel.
+// Inside a captured graph a memset node costs about as much as three dependent
+// kernel launches, so a call that resets several ranges before its kernels
+// resets them all in one launch, or inside a kernel it launches first anyway
+// (fill_ranges_device).
+constexpr int FILL_MAX = 8;
+struct FillSet {
+  int n = 0;
+  bool overflow = false;
+  unsigned char* ptr[FILL_MAX];
+  long long bytes[FILL_MAX];
+  unsigned long long pattern[FILL_MAX];
+  void add(void* p, size_t b, unsigned long long pat = 0ull) {
+    if (b == 0) return;
+    if (n == FILL_MAX) {
+      overflow = true;
+      return;
+    }
+    ptr[n] = static_cast<unsigned char*>(p);
+    bytes[n] = (long long)b;
+    pattern[n] = pat;
+    ++n;
+  }
+};
+
+// The ranges of f, by threads tid = 0 .. nt-1 of a grid: 16-byte stores for the
+// aligned middle of each range, byte stores for its ends.
+__device__ __forceinline__ void fill_ranges_device(const FillSet& f, long long tid, long long nt) {
+  for (int s = 0; s < f.n; ++s) {
+    unsigned char* b = f.ptr[s];
+    const long long len = f.bytes[s];
+    const unsigned long long pat = f.pattern[s];
+    long long head = (long long)((16u - (unsigned)(reinterpret_cast<uintptr_t>(b) & 15u)) & 15u);
+    if (head > len) head = len;
+    const long long body = (len - head) >> 4;
+    for (long long o = tid; o < head; o += nt) b[o] = (unsigned char)(pat >> (8 * (o & 7)));
+    for (long long o = head + (body << 4) + tid; o < len; o += nt)
+      b[o] = (unsigned char)(pat >> (8 * (o & 7)));
+    // the 8-byte words of the middle start at offsets congruent to head mod 8
+    const int sh = (int)(head & 7) * 8;
+    const unsigned long long r = sh ? (pat >> sh) | (pat << (64 - sh)) : pat;
+    const ulonglong2 v = make_ulonglong2(r, r);
+    ulonglong2* q = reinterpret_cast<ulonglong2*>(b + head);
+    for (long long c = tid; c < body; c += nt) q[c] = v;
+  }
+}
+
+// One launch that fills the ranges of f (none when f is empty).
+int launch_fill(const FillSet& f, cudaStream_t st);
+
 // ----------------------------------------------------------------- cameras
 
 // Cameras of one launch, passed by value as a kernel parameter.
@@ -286,15 +339,34 @@ __global__ void __launch_bounds__(SCAN_THREADS)
   if (tile == nb - 1 && threadIdx.x == 0 && total) *total = s_excl + agg;
 }
 
+// The words of a scan workspace that must be zero when the scan starts.
+inline size_t scan_status_bytes(long long n_max) {
+  long long nb = scan_blocks(n_max);
+  if (nb == 0) nb = 1;
+  return sizeof(unsigned long long) * (size_t)(nb + 3);
+}
+// Adds those words of the scan workspace ws to a fill.
+inline void scan_clear(FillSet& f, void* ws, long long n_max) {
+  f.add(ws, scan_status_bytes(n_max));
+}
+
 // Exclusive scan: store(i, prefix_i); total (device, may be null) receives the sum.
 // d_status (device, may be null): the caller's status word (see bounded waits).
+// cleared: the caller has zeroed the workspace's status words (scan_clear) since
+// the last scan in it; otherwise the scan zeroes them itself first.
 template <class Load, class Store>
 int scan_exclusive(Load load, Store store, long long n_max, const long long* d_n,
-                   long long* total, void* ws, cudaStream_t st, int* d_status) {
+                   long long* total, void* ws, cudaStream_t st, int* d_status,
+                   bool cleared = false) {
   long long nb = scan_blocks(n_max);
   if (nb == 0) nb = 1;
   unsigned long long* status = static_cast<unsigned long long*>(ws);
-  ADP_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (size_t)(nb + 3), st));
+  if (!cleared) {
+    FillSet f;
+    scan_clear(f, ws, n_max);
+    const int rc = launch_fill(f, st);
+    if (rc) return rc;
+  }
   scan_lookback_kernel<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(load, store, n_max, d_n, status,
                                                               total, d_status, spin_limit());
   ADP_LAUNCH_CHECK();

@@ -71,8 +71,9 @@ extern "C" ADP_API int adp_densify_select(const float* grad2d_accum, const int32
   ADP_CHECK_ARG(ws_bytes >= need, "workspace %zu bytes, need %zu", ws_bytes, need);
   cudaStream_t st = (cudaStream_t)stream;
   if (g->n == 0) {
-    ADP_CUDA(cudaMemsetAsync(d_counts, 0, 2 * sizeof(int64_t), st));
-    return ADP_OK;
+    FillSet f;
+    f.add(d_counts, 2 * sizeof(int64_t));
+    return launch_fill(f, st);
   }
   Carver c(ws, ws_bytes);
   void* sw = c.take<char>(scan_workspace_bytes(g->n));

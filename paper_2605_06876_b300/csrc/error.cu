@@ -63,14 +63,6 @@ __global__ void err_raw_kernel(const float* img, const float* tgt, CamSet cs, fl
   }
 }
 
-__global__ void err_init_minmax_kernel(unsigned* mm, int n_views) {
-  int v = threadIdx.x;
-  if (v < n_views) {
-    mm[2 * v] = 0x7f800000u;
-    mm[2 * v + 1] = 0u;
-  }
-}
-
 // E, M, B and the per-Gaussian attribution of pre-erosion error pixels.
 __global__ void err_norm_kernel(float* E, uint8_t* mask, const unsigned* minmax_bits,
                                 const int* dominant, long long n, CamSet cs, float tau, int L,
@@ -185,7 +177,7 @@ static_assert(TOPK_THREADS >= 256 && TOPK_THREADS <= 1024 && TOPK_THREADS % 32 =
               "the digit sums take 256 threads and the flag scan one warp of warp totals");
 struct TopkCoop {
   unsigned* hist;              // [8][256], zeroed before the launch
-  unsigned long long* mm;      // [8][2] min, max of the matching keys (preset by the caller)
+  unsigned long long* mm;      // [8][2] min and ~max of the matching keys (all ones before)
   unsigned* bar;               // barrier counter, zeroed before the launch
   unsigned* err;               // set if a barrier wait gave up
   long long* blk;              // [2][gridDim.x] per-block counts
@@ -293,15 +285,15 @@ __global__ void __launch_bounds__(TOPK_THREADS)
         lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
         hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
       }
-      if (lane == 0 && lo <= hi) {
+      if (lane == 0 && lo <= hi) {  // the maximum as the complement of a minimum
         atomicMin(&w.mm[2 * p], lo);
-        atomicMax(&w.mm[2 * p + 1], hi);
+        atomicMin(&w.mm[2 * p + 1], ~hi);
       }
     }
     if (t < 256 && s_h[t]) atomicAdd(&w.hist[256 * p + t], s_h[t]);
     if (!topk_grid_barrier(w, ++round)) return;
     const unsigned long long glo = *(volatile unsigned long long*)&w.mm[2 * p];
-    const unsigned long long ghi = *(volatile unsigned long long*)&w.mm[2 * p + 1];
+    const unsigned long long ghi = ~*(volatile unsigned long long*)&w.mm[2 * p + 1];
     if (glo == ghi) {  // every key still in play is the threshold key
       prefix = glo;
       mask = ~0ull;
@@ -382,11 +374,6 @@ __global__ void __launch_bounds__(TOPK_THREADS)
   }
 }
 
-// Presets the per-pass min/max slots (min to all ones, max to zero).
-__global__ void topk_coop_init_kernel(unsigned long long* mm) {
-  if (threadIdx.x < 16) mm[threadIdx.x] = (threadIdx.x & 1) ? 0ull : ~0ull;
-}
-
 // Blocks of the cooperative top-k kernel on this device: TOPK_PER_SM per SM, or
 // as many as the kernel's occupancy allows (all resident).
 static int topk_coop_grid(int* grid) {
@@ -423,13 +410,16 @@ static int topk_coop_run(const double* mass, long long n, long long k, int32_t* 
   int grid = 0;
   int rc = topk_coop_grid(&grid);
   if (rc) return rc;
-  ADP_CUDA(cudaMemsetAsync(w.hist, 0, sizeof(unsigned) * 8 * 256, st));
-  ADP_CUDA(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st));
-  // -1 everywhere first: if a barrier wait gives up, the slots of the blocks that
-  // left hold -1, which every consumer of a candidate list skips
-  ADP_CUDA(cudaMemsetAsync(out_ids, 0xff, sizeof(int32_t) * (size_t)k, st));
-  topk_coop_init_kernel<<<1, 32, 0, st>>>(w.mm);
-  ADP_LAUNCH_CHECK();
+  // the histograms, the barrier and the min/max slots, and -1 in every output slot
+  // (if a barrier wait gives up, the slots of the blocks that left hold -1, which
+  // every consumer of a candidate list skips), in one launch
+  FillSet fill;
+  fill.add(w.hist, sizeof(unsigned) * 8 * 256);
+  fill.add(w.bar, 2 * sizeof(unsigned));
+  fill.add(w.mm, 16 * sizeof(unsigned long long), ~0ull);
+  fill.add(out_ids, sizeof(int32_t) * (size_t)k, ~0ull);
+  rc = launch_fill(fill, st);
+  if (rc) return rc;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3(TOPK_THREADS);
@@ -455,9 +445,13 @@ static int topk_coop_run(const double* mass, long long n, long long k, int32_t* 
 constexpr int ERODE_T = 32;
 constexpr int ERODE_RMAX = 64;
 
-__global__ void __launch_bounds__(256) erode_kernel(uint8_t* mask, CamSet cs, int r) {
+// The ranges of f are filled by the same launch (the call's resets; the erosion
+// reads none of them).
+__global__ void __launch_bounds__(256) erode_kernel(uint8_t* mask, CamSet cs, int r, FillSet f) {
   __shared__ uint8_t s_in[(ERODE_T + 2 * ERODE_RMAX) * (ERODE_T + 2 * ERODE_RMAX)];
   __shared__ uint8_t s_row[(ERODE_T + 2 * ERODE_RMAX) * ERODE_T];
+  fill_ranges_device(f, ((long long)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x,
+                     (long long)gridDim.x * gridDim.y * blockDim.x);
   const int v = blockIdx.y;
   const int W = cs.cam[v].width, H = cs.cam[v].height;
   const int ntx = (W + ERODE_T - 1) / ERODE_T, nty = (H + ERODE_T - 1) / ERODE_T;
@@ -917,19 +911,19 @@ using namespace adp;
 
 namespace adp {
 
-int error_minmax_init(adp_error_maps* maps, int n_views, cudaStream_t st) {
-  err_init_minmax_kernel<<<1, 32, 0, st>>>(reinterpret_cast<unsigned*>(maps->minmax), n_views);
-  ADP_LAUNCH_CHECK();
-  return ADP_OK;
+void error_init_fill(FillSet& f, adp_error_maps* maps, int n_views, int32_t* count,
+                     double* mass, long long n) {
+  // per view the word pair (min, max) = (+inf, 0): 0x7f800000 in the lower word
+  f.add(maps->minmax, 2 * sizeof(unsigned) * (size_t)n_views, 0x7f800000ull);
+  if (n > 0) {
+    f.add(count, sizeof(int32_t) * (size_t)n);
+    f.add(mass, sizeof(double) * (size_t)n);
+  }
 }
 
 int error_norm_phase(adp_error_maps* maps, const int32_t* dominant, long long n,
                      const CamSet& cs, const adp_params* prm, int32_t* count, double* mass,
                      cudaStream_t st) {
-  if (n > 0) {
-    ADP_CUDA(cudaMemsetAsync(count, 0, sizeof(int) * n, st));
-    ADP_CUDA(cudaMemsetAsync(mass, 0, sizeof(double) * n, st));
-  }
   const unsigned* mm = reinterpret_cast<const unsigned*>(maps->minmax);
   const dim3 grid(view_grid(cs), cs.n_views);
   const int shift = mass_shift_for(prm->tau_l1);
@@ -963,7 +957,10 @@ extern "C" ADP_API int adp_error_stats(const float* img, const float* target,
   ADP_CHECK_ARG(prm->n_levels >= 1 && prm->n_levels <= 15, "n_levels must be 1..15");
   cudaStream_t st = (cudaStream_t)stream;
   unsigned* mm = reinterpret_cast<unsigned*>(maps->minmax);
-  err_init_minmax_kernel<<<1, 32, 0, st>>>(mm, n_views);
+  FillSet fill;
+  error_init_fill(fill, maps, n_views, count, mass, n);
+  rc = launch_fill(fill, st);
+  if (rc) return rc;
   dim3 grid(view_grid(cs), n_views);
   err_raw_kernel<<<dim3(std::min(grid.x, 148u * 4u), n_views), 256, 0, st>>>(img, target, cs,
                                                                             maps->E, mm);
@@ -1007,14 +1004,15 @@ struct RegionWs {
   int* lroots;      // [P] the local roots
   long long* kept_idx;
   uint8_t* cand;
-  void* scan;
+  void* scan;   // the roots' scan
+  void* scan2;  // the area filter's scan
   long long* counters;  // [0] roots, [2] local roots
 };
 
 static size_t region_ws_bytes(long long n, long long P) {
   return 3 * carve_bytes<int>(P) + 2 * carve_bytes<long long>(6 * P) + carve_bytes<int>(P) +
-         carve_bytes<long long>(P) + carve_bytes<uint8_t>(n) + scan_workspace_bytes(P) +
-         carve_bytes<long long>(4);
+         carve_bytes<long long>(P) + carve_bytes<uint8_t>(n) +
+         2 * scan_workspace_bytes(P) + carve_bytes<long long>(4);
 }
 
 extern "C" ADP_API size_t adp_error_regions_workspace_size(int64_t n, int32_t n_views,
@@ -1062,7 +1060,16 @@ extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* do
   w.kept_idx = c.take<long long>(P);
   w.cand = c.take<uint8_t>(n);
   w.scan = c.take<char>(scan_workspace_bytes(P));
+  w.scan2 = c.take<char>(scan_workspace_bytes(P));
   w.counters = c.take<long long>(4);
+  // the candidate flags, the counters and both scans' status words are reset by
+  // the erosion's launch
+  FillSet fill;
+  fill.add(w.cand, (size_t)n);
+  fill.add(w.counters, 4 * sizeof(long long));
+  scan_clear(fill, w.scan, P);
+  scan_clear(fill, w.scan2, P);
+  ADP_CHECK_ARG(!fill.overflow, "internal: too many ranges in one fill");
 
   dim3 grid(view_grid(cs), n_views);
   // erosion -> mask bit 1
@@ -1072,16 +1079,14 @@ extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* do
       int t = ((cs.cam[v].width + ERODE_T - 1) / ERODE_T) * ((cs.cam[v].height + ERODE_T - 1) / ERODE_T);
       max_et = t > max_et ? t : max_et;
     }
-    erode_kernel<<<dim3(max_et, n_views), 256, 0, st>>>(maps->mask, cs, prm->r_erode);
+    erode_kernel<<<dim3(max_et, n_views), 256, 0, st>>>(maps->mask, cs, prm->r_erode, fill);
   }
   // candidate flags
-  if (n > 0) ADP_CUDA(cudaMemsetAsync(w.cand, 0, n, st));
   if (n_cand > 0)
     scatter_flag_kernel<<<grid_for(n_cand, 256, 4096), 256, 0, st>>>(candidates, n_cand, n,
                                                                       w.cand);
   // labelling
   unsigned gp = grid_for(P, 256, 148 * 16);
-  ADP_CUDA(cudaMemsetAsync(w.counters, 0, 4 * sizeof(long long), st));
   unsigned long long* n_lroots = reinterpret_cast<unsigned long long*>(&w.counters[2]);
   {
     int max_tiles = 0;
@@ -1108,7 +1113,7 @@ extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* do
                           root_pix[pre] = (int)p;
                         }
                       },
-                      P, nullptr, &w.counters[0], w.scan, st, d_status);
+                      P, nullptr, &w.counters[0], w.scan, st, d_status, /*cleared=*/true);
   if (rc) return rc;
   count_guard_kernel<<<1, 1, 0, st>>>(scan_error_flag(w.scan, P), &w.counters[0]);
   zero_i64_kernel<<<gp, 256, 0, st>>>(w.mom, &w.counters[0], 6);
@@ -1122,7 +1127,7 @@ extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* do
   rc = scan_exclusive(
       [=] __device__(long long r) -> long long { return mom[6 * r] >= m_min ? 1 : 0; },
       [=] __device__(long long r, long long pre) { kept[r] = pre; }, P, &w.counters[0],
-      (long long*)out->count, w.scan, st, d_status);
+      (long long*)out->count, w.scan2, st, d_status, /*cleared=*/true);
   if (rc) return rc;
   RegionArgs ra;
   ra.mom = w.mom;

@@ -13,18 +13,24 @@ int project_launch(const adp_gaussians* g, const adp_camera* cams, int n_views,
                    const adp_params* prm, adp_projected* out, float4* zero_moments,
                    cudaStream_t st);
 
-// Presets the per-view min/max words of maps->minmax for the raw L1 reduction.
-int error_minmax_init(adp_error_maps* maps, int n_views, cudaStream_t st);
+// Adds to f the presets of the error statistics: the per-view min/max words of
+// maps->minmax for the raw L1 reduction, and the zeroed per-Gaussian count and
+// mass that error_norm_phase accumulates into.
+void error_init_fill(FillSet& f, adp_error_maps* maps, int n_views, int32_t* count,
+                     double* mass, long long n);
 
 // Eq. 6 from the raw per-pixel L1 error in maps->E and its per-view min/max:
 // E, the mask M and the bands B (in place), and the per-Gaussian count and
-// error mass of the pre-erosion error pixels (zeroed first).
+// error mass of the pre-erosion error pixels (into the zeroed count and mass,
+// see error_init_fill).
 int error_norm_phase(adp_error_maps* maps, const int32_t* dominant, long long n,
                      const CamSet& cs, const adp_params* prm, int32_t* count, double* mass,
                      cudaStream_t st);
 
-// Zeroes the three float4 pixel-moment rows of every record with tiles > 0.
-int zero_visible_moments(const int* tiles, long long n_rec, float4* g2d, cudaStream_t st);
+// Zeroes the three float4 pixel-moment rows of every record with tiles > 0, and
+// fills the ranges of f in the same launch.
+int zero_visible_moments(const int* tiles, long long n_rec, float4* g2d, const FillSet& f,
+                         cudaStream_t st);
 
 // The per-Gaussian part of the render backward: from the per-(view, Gaussian)
 // pixel moments in g2d, the chain rule through the EWA projection and the SH

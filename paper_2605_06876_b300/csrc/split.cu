@@ -912,10 +912,17 @@ static MergeArgs merge_args(const PlanCall& pc, const SplitWs& w) {
 static int plan_phase_a(const PlanCall& pc, const SplitWs& w, cudaStream_t st) {
   const long long n = pc.n, nc = pc.nc, rcap = pc.rcap;
   int rc;
-  ADP_CUDA(cudaMemsetAsync(w.counters, 0, 8 * sizeof(long long), st));
-  if (n > 0) ADP_CUDA(cudaMemsetAsync(w.cand_of, 0xff, sizeof(int) * n, st));
+  // the counters, -1 in every Gaussian's candidate slot, the empty region
+  // segments and the status words of both parts' scans, in one launch
+  FillSet fill;
+  fill.add(w.counters, 8 * sizeof(long long));
+  fill.add(w.cand_of, sizeof(int) * (size_t)n, ~0ull);
+  fill.add(w.seg, sizeof(int2) * (size_t)nc);
+  scan_clear(fill, w.scan, n);
+  if (nc > 0) scan_clear(fill, w.scan2, nc);
+  rc = launch_fill(fill, st);
+  if (rc) return rc;
   if (nc > 0) {
-    ADP_CUDA(cudaMemsetAsync(w.seg, 0, sizeof(int2) * nc, st));
     cand_of_kernel<<<grid_for(nc, 256, 4096), 256, 0, st>>>(pc.candidates, nc, n, w.cand_of);
   }
   if (rcap > 0) {
@@ -949,7 +956,7 @@ static int plan_phase_a(const PlanCall& pc, const SplitWs& w, cudaStream_t st) {
         const bool kept = cc < 0 || cstatus[cc] == ADP_RESET;
         dest[i] = kept ? ((unsigned)pre | (cc >= 0 ? 0x80000000u : 0u)) : 0xffffffffu;
       },
-      n, nullptr, &w.counters[1], w.scan, st, pc.d_status);
+      n, nullptr, &w.counters[1], w.scan, st, pc.d_status, /*cleared=*/true);
   return rc;
 }
 
@@ -993,7 +1000,7 @@ static int plan_phase_b(const PlanCall& pc, const SplitWs& w, cudaStream_t st) {
           return s == ADP_ADAPTIVE ? 1 + nch[cc] : (s == ADP_FALLBACK ? 2 : 0);
         },
         [=] __device__(long long cc, long long pre) { app_off[cc] = pre; }, nc, nullptr,
-        &w.counters[2], w.scan2, st, pc.d_status);
+        &w.counters[2], w.scan2, st, pc.d_status, /*cleared=*/true);
     if (rc) return rc;
   }
   new_n_kernel<<<1, 1, 0, st>>>(w.counters, pc.d_new_n, scan_error_flag(w.scan, pc.n),

@@ -247,7 +247,12 @@ extern "C" ADP_API int adp_dssim_loss_grad(const float* img, const float* target
   a.loss = loss;
   a.lambda = lambda;
   a.P = cs.pix_base[n_views];
-  if (loss) ADP_CUDA(cudaMemsetAsync(loss, 0, sizeof(double) * 2 * n_views, st));
+  if (loss) {
+    FillSet f;
+    f.add(loss, sizeof(double) * 2 * n_views);
+    rc = launch_fill(f, st);
+    if (rc) return rc;
+  }
   int max_tiles = 0;
   for (int v = 0; v < n_views; ++v) {
     const int t = ((cams[v].width + SS_T - 1) / SS_T) * ((cams[v].height + SS_T - 1) / SS_T);
