@@ -186,7 +186,13 @@ def stage_bytes(n, n_vis, K, P, n_tiles, sh_planes, regions, k, kept, appended):
         # parameter, m, v
         "adam": n * gbytes * 6 + n_vis * gbytes + n,
         "adam_rows": k * gbytes * 6 + min(k, n_vis) * gbytes + k * 5,
-        "split_plan": regions * 300 + n * 12 + k * 16,
+        # the plan's first part (candidate slots, kept-row destinations, statuses),
+        # which the step runs on the side stream beside the backward
+        "split_statuses": n * 12 + k * 16,
+        # its second part (proposals and merges per region); in the step it runs on
+        # the library's auxiliary stream beside the kept rows, and the main stream's
+        # split_plan stage is only the fork
+        "split_plan": regions * 300,
         # compaction with the fused Adam step (apply_keep_kernel): kept rows as in
         # Adam (gradients of rendered rows only), one destination word and one mask
         # byte per row
@@ -454,7 +460,7 @@ def run_ours(args, rank, world, local_rank):
         "eq2_step": eq2,
         "densify_loop": loop,
         "stage_gbs": {k: round(sb[k] / (per_stage[k] * 1e-3) / 1e9, 1) for k in per_stage
-                      if k in sb and per_stage[k] > 0},
+                      if k in sb and per_stage[k] > 0.005},
         "workload_counts": {"visible": n_vis, "instances": K, "regions": R,
                             "pixel_evaluations": n_eval, "blended_pairs": n_blend,
                             "candidates": stepper.k, "new_population": new_n},

@@ -14,7 +14,7 @@
  *  - Every call is asynchronous on the given stream (a cudaStream_t; NULL is the
  *    legacy default stream) and does not synchronise, except adp_split_plan,
  *    which reads one integer back when asked to (see there). The overlapped
- *    split (adp_split_plan_overlapped and its two compaction calls) and the
+ *    split (adp_split_plan_overlapped or its second part, and its two compaction calls) and the
  *    batched step (adp_train_step_batched) also put work on a stream the library
  *    keeps per device, forked from and joined back into the given stream (see
  *    there).
@@ -383,7 +383,18 @@ ADP_API int adp_split_apply_adam(const adp_gaussians* g, const adp_gaussians* gr
  * stream capture that includes these calls (inside a capture the auxiliary
  * stream joins the capture as a forked stream). The workspace is that of
  * adp_split_plan. Arguments, ownership and errors as in adp_split_plan (without
- * h_new_n) and adp_split_apply_adam. */
+ * h_new_n) and adp_split_apply_adam.
+ * adp_split_plan_overlapped is adp_split_plan_statuses followed by
+ * adp_split_plan_proposals_overlapped on the same stream, with the same
+ * arguments. A caller may instead make the two calls itself. The first enqueues
+ * the part that needs no proposal on its `stream`. It reads the candidates, the
+ * regions and count, but no parameter of g (only g->n), so it may run on another
+ * stream before the candidates' Adam step (adp_adam_step_rows), e.g. beside the
+ * render backward. The second forks the proposals and merges onto the auxiliary
+ * stream after the work already enqueued on its `stream`. That stream must by
+ * then be ordered after the first call (an event) and after adp_adam_step_rows.
+ * The keep and append calls then follow on that stream as above. Between the
+ * two calls nothing else may use the workspace. */
 ADP_API int adp_split_plan_overlapped(const adp_gaussians* g, const adp_camera* cams,
                                       int32_t n_views, const adp_regions* regs,
                                       const int32_t* candidates, int64_t n_cand,
@@ -391,6 +402,17 @@ ADP_API int adp_split_plan_overlapped(const adp_gaussians* g, const adp_camera* 
                                       uint8_t* status, int32_t* n_children, int64_t* d_new_n,
                                       void* ws, size_t ws_bytes, int32_t* d_status,
                                       adp_stream_t stream);
+ADP_API int adp_split_plan_statuses(const adp_gaussians* g, const adp_camera* cams,
+                                    int32_t n_views, const adp_regions* regs,
+                                    const int32_t* candidates, int64_t n_cand,
+                                    const int32_t* count, const adp_params* prm, uint8_t* status,
+                                    int32_t* n_children, int64_t* d_new_n, void* ws,
+                                    size_t ws_bytes, int32_t* d_status, adp_stream_t stream);
+ADP_API int adp_split_plan_proposals_overlapped(
+    const adp_gaussians* g, const adp_camera* cams, int32_t n_views, const adp_regions* regs,
+    const int32_t* candidates, int64_t n_cand, const int32_t* count, const adp_params* prm,
+    uint8_t* status, int32_t* n_children, int64_t* d_new_n, void* ws, size_t ws_bytes,
+    int32_t* d_status, adp_stream_t stream);
 ADP_API int adp_split_keep_overlapped(
     const adp_gaussians* g, const adp_gaussians* grad, const adp_gaussians* m_in,
     const adp_gaussians* v_in, const adp_regions* regs, const int32_t* candidates, int64_t n_cand,

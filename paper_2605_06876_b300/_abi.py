@@ -112,6 +112,13 @@ _PROTOS = {
     "adp_split_plan_overlapped": (C.c_int, [P(AdpGaussians), P(AdpCamera), _i32, P(AdpRegions),
                                             _vp, _i64, _vp, P(AdpParams), _vp, _vp, _vp, _vp,
                                             C.c_size_t, _vp, _vp]),
+    "adp_split_plan_statuses": (C.c_int, [P(AdpGaussians), P(AdpCamera), _i32, P(AdpRegions),
+                                          _vp, _i64, _vp, P(AdpParams), _vp, _vp, _vp, _vp,
+                                          C.c_size_t, _vp, _vp]),
+    "adp_split_plan_proposals_overlapped": (C.c_int, [P(AdpGaussians), P(AdpCamera), _i32,
+                                                      P(AdpRegions), _vp, _i64, _vp,
+                                                      P(AdpParams), _vp, _vp, _vp, _vp,
+                                                      C.c_size_t, _vp, _vp]),
     "adp_split_keep_overlapped": (C.c_int, [P(AdpGaussians), P(AdpGaussians),
                                                   P(AdpGaussians), P(AdpGaussians), P(AdpRegions),
                                                   _vp, _i64, _vp, _vp, _vp, P(AdpParams), _i32,

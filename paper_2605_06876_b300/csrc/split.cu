@@ -1036,13 +1036,27 @@ extern "C" ADP_API int adp_split_plan(const adp_gaussians* g, const adp_camera* 
   return ADP_OK;
 }
 
-extern "C" ADP_API int adp_split_plan_overlapped(const adp_gaussians* g, const adp_camera* cams,
-                                                 int32_t n_views, const adp_regions* regs,
-                                                 const int32_t* candidates, int64_t n_cand,
-                                                 const int32_t* count, const adp_params* prm,
-                                                 uint8_t* status, int32_t* n_children,
-                                                 int64_t* d_new_n, void* ws, size_t ws_bytes,
-                                                 int32_t* d_status, adp_stream_t stream) {
+extern "C" ADP_API int adp_split_plan_statuses(const adp_gaussians* g, const adp_camera* cams,
+                                               int32_t n_views, const adp_regions* regs,
+                                               const int32_t* candidates, int64_t n_cand,
+                                               const int32_t* count, const adp_params* prm,
+                                               uint8_t* status, int32_t* n_children,
+                                               int64_t* d_new_n, void* ws, size_t ws_bytes,
+                                               int32_t* d_status, adp_stream_t stream) {
+  PlanCall pc;
+  int rc = plan_args(g, cams, n_views, regs, candidates, n_cand, count, prm, status, n_children,
+                     d_new_n, ws, ws_bytes, d_status, &pc);
+  if (rc) return rc;
+  Carver c(ws, ws_bytes);
+  SplitWs w = carve_split(c, pc.n, pc.nc, pc.rcap);
+  return plan_phase_a(pc, w, (cudaStream_t)stream);
+}
+
+extern "C" ADP_API int adp_split_plan_proposals_overlapped(
+    const adp_gaussians* g, const adp_camera* cams, int32_t n_views, const adp_regions* regs,
+    const int32_t* candidates, int64_t n_cand, const int32_t* count, const adp_params* prm,
+    uint8_t* status, int32_t* n_children, int64_t* d_new_n, void* ws, size_t ws_bytes,
+    int32_t* d_status, adp_stream_t stream) {
   PlanCall pc;
   int rc = plan_args(g, cams, n_views, regs, candidates, n_cand, count, prm, status, n_children,
                      d_new_n, ws, ws_bytes, d_status, &pc);
@@ -1053,9 +1067,7 @@ extern "C" ADP_API int adp_split_plan_overlapped(const adp_gaussians* g, const a
   cudaStream_t st = (cudaStream_t)stream;
   Carver c(ws, ws_bytes);
   SplitWs w = carve_split(c, pc.n, pc.nc, pc.rcap);
-  rc = plan_phase_a(pc, w, st);
-  if (rc) return rc;
-  {  // fork: phase B on the auxiliary stream once phase A is done
+  {  // fork: the second part on the auxiliary stream, after the work enqueued on st
     std::lock_guard<std::mutex> lock(aux_mutex());
     ADP_CUDA(cudaEventRecord(aux->planned, st));
     ADP_CUDA(cudaStreamWaitEvent(aux->stream, aux->planned, 0));
@@ -1070,6 +1082,29 @@ extern "C" ADP_API int adp_split_plan_overlapped(const adp_gaussians* g, const a
     return rc;
   }
   return ADP_OK;
+}
+
+extern "C" ADP_API int adp_split_plan_overlapped(const adp_gaussians* g, const adp_camera* cams,
+                                                 int32_t n_views, const adp_regions* regs,
+                                                 const int32_t* candidates, int64_t n_cand,
+                                                 const int32_t* count, const adp_params* prm,
+                                                 uint8_t* status, int32_t* n_children,
+                                                 int64_t* d_new_n, void* ws, size_t ws_bytes,
+                                                 int32_t* d_status, adp_stream_t stream) {
+  // the arguments and the auxiliary stream first, so that a failure leaves no work
+  PlanCall pc;
+  int rc = plan_args(g, cams, n_views, regs, candidates, n_cand, count, prm, status, n_children,
+                     d_new_n, ws, ws_bytes, d_status, &pc);
+  if (rc) return rc;
+  AuxStream* aux = nullptr;
+  rc = aux_stream(&aux);
+  if (rc) return rc;
+  rc = adp_split_plan_statuses(g, cams, n_views, regs, candidates, n_cand, count, prm, status,
+                               n_children, d_new_n, ws, ws_bytes, d_status, stream);
+  if (rc) return rc;
+  return adp_split_plan_proposals_overlapped(g, cams, n_views, regs, candidates, n_cand, count,
+                                             prm, status, n_children, d_new_n, ws, ws_bytes,
+                                             d_status, stream);
 }
 
 // Which part of the compaction a call enqueues: everything, or, after an

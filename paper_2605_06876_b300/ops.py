@@ -383,6 +383,10 @@ class SplitPlan:
     new_n: int
     ws: torch.Tensor
     d_new_n: torch.Tensor
+    # the whole status and child-count buffers (at least one entry), which the
+    # second part of a two-call overlapped plan writes through again
+    status_buf: torch.Tensor = None
+    nch_buf: torch.Tensor = None
 
 
 def split_plan(g: Gaussians, cams, regions: Regions, candidates, count, params=None, ws=None,
@@ -409,27 +413,36 @@ def split_plan(g: Gaussians, cams, regions: Regions, candidates, count, params=N
 
 
 def split_plan_overlapped(g: Gaussians, cams, regions: Regions, candidates, count, params=None,
-                          ws=None, stream=None, status_word=None):
+                          ws=None, stream=None, status_word=None, part="all", plan=None):
     """adp_split_plan_overlapped: the statuses and kept rows on the stream, the
     proposals and merges on the library's auxiliary stream; must be followed by
-    split_apply_adam(..., overlapped=True), which joins them."""
+    split_apply_adam(..., overlapped=True), which joins them. part="statuses"
+    enqueues only the first part (adp_split_plan_statuses) and returns the plan;
+    part="proposals" takes that plan (same arguments, the same workspace) and
+    enqueues the second (adp_split_plan_proposals_overlapped)."""
+    fn = {"all": "adp_split_plan_overlapped", "statuses": "adp_split_plan_statuses",
+          "proposals": "adp_split_plan_proposals_overlapped"}[part]
     params = params or A.default_params()
     ca = A.cameras(cams)
     dev = g.mean_logit.device
     nc = int(candidates.numel())
-    need = split_workspace_size(g.n, nc, regions.capacity)
-    if ws is None or ws.numel() < need:
-        ws = workspace(need, dev)
-    status = torch.empty(max(nc, 1), dtype=U8, device=dev)
-    nch = torch.empty(max(nc, 1), dtype=I32, device=dev)
-    d_new_n = torch.empty(1, dtype=I64, device=dev)
+    if part == "proposals":
+        if plan is None:
+            raise ValueError("part='proposals' needs the plan of part='statuses'")
+        ws = plan.ws
+        status, nch, d_new_n = plan.status_buf, plan.nch_buf, plan.d_new_n
+    else:
+        need = split_workspace_size(g.n, nc, regions.capacity)
+        if ws is None or ws.numel() < need:
+            ws = workspace(need, dev)
+        status = torch.empty(max(nc, 1), dtype=U8, device=dev)
+        nch = torch.empty(max(nc, 1), dtype=I32, device=dev)
+        d_new_n = torch.empty(1, dtype=I64, device=dev)
     gc, rc = g.c(), regions.c()
-    A.check(A.lib().adp_split_plan_overlapped(C.byref(gc), ca, len(cams), C.byref(rc),
-                                              _p(candidates), nc, _p(count), C.byref(params),
-                                              _p(status), _p(nch), _p(d_new_n), _p(ws),
-                                              ws.numel(), _p(status_word), _stream(stream)),
-            "adp_split_plan_overlapped")
-    return SplitPlan(status[:nc], nch[:nc], None, ws, d_new_n)
+    A.check(getattr(A.lib(), fn)(C.byref(gc), ca, len(cams), C.byref(rc), _p(candidates), nc,
+                                 _p(count), C.byref(params), _p(status), _p(nch), _p(d_new_n),
+                                 _p(ws), ws.numel(), _p(status_word), _stream(stream)), fn)
+    return SplitPlan(status[:nc], nch[:nc], None, ws, d_new_n, status, nch)
 
 
 def split_apply(g: Gaussians, plan: SplitPlan, regions: Regions, candidates, noise, params=None,

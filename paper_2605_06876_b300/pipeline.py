@@ -179,6 +179,7 @@ class PlainStep:
         mark("render")
         ops.render(n, self.pr, self.bins, cams, self.bg, prm, self.img)
         main = torch.cuda.current_stream()
+        overlap = self.fused_adam and self.overlap_split
         self.side.wait_stream(main)  # fork after the forward
         with torch.cuda.stream(self.side):
             mark("error_stats")
@@ -192,6 +193,13 @@ class PlainStep:
             ops.error_regions(self.maps, self.img.dominant, self.target, n, cams, self.cand, prm,
                               regions=self.regions, ws=self.ws_regions, grow=False,
                               status=self.status)
+            if overlap:
+                # the plan's first part (statuses, kept rows, the bound) reads no
+                # parameter, so it runs here, beside the backward
+                mark("split_statuses")
+                plan = ops.split_plan_overlapped(g, cams, self.regions, self.cand, self.count,
+                                                 prm, ws=self.ws_split, status_word=self.status,
+                                                 part="statuses")
             mark("error_end")
         if self.dssim_lambda > 0:
             mark("dssim")
@@ -215,11 +223,11 @@ class PlainStep:
         if not self.fused_adam:
             mark("adam")
             ops.adam_step(g, self.grad, self.m, self.v, self.adam_t, self.lr)
-        overlap = self.fused_adam and self.overlap_split
         mark("split_plan")
-        if overlap:
+        if overlap:  # the proposals and merges, forked onto the library's auxiliary stream
             plan = ops.split_plan_overlapped(g, cams, self.regions, self.cand, self.count, prm,
-                                             ws=self.ws_split, status_word=self.status)
+                                             ws=self.ws_split, status_word=self.status,
+                                             part="proposals", plan=plan)
         else:
             plan = ops.split_plan(g, cams, self.regions, self.cand, self.count, prm,
                                   ws=self.ws_split, sync=False, status_word=self.status)

@@ -98,18 +98,20 @@ def test_workspace_queries_and_argument_errors(abi):
 
 
 def test_overlapped_split_rejects_bad_arguments_before_any_launch(abi):
-    """The overlapped plan and both compaction calls validate on the host first (no
-    device, no auxiliary stream is touched): missing arrays, candidates without
-    their status arrays, and an unaligned workspace."""
+    """The overlapped plan (whole or in its two parts) and both compaction calls
+    validate on the host first (no device, no auxiliary stream is touched): missing
+    arrays, candidates without their status arrays, and an unaligned workspace."""
     L = abi.lib()
     cams = abi.cameras([{"width": 64, "height": 32, "fx": 50, "fy": 50, "px": 31.5, "py": 15.5,
                          "R": [1, 0, 0, 0, 1, 0, 0, 0, 1], "t": [0, 0, 0]}])
     p = abi.default_params()
     g = abi.AdpGaussians(0, 0, 0, None, None, None, None)
     regs = abi.AdpRegions()
-    rc = L.adp_split_plan_overlapped(C.byref(g), cams, 1, C.byref(regs), None, 0, None,
-                                     C.byref(p), None, None, None, None, 0, None, None)
-    assert rc == 1 and b"NULL" in L.adp_last_error_string()
+    for name in ("adp_split_plan_overlapped", "adp_split_plan_statuses",
+                 "adp_split_plan_proposals_overlapped"):
+        rc = getattr(L, name)(C.byref(g), cams, 1, C.byref(regs), None, 0, None, C.byref(p),
+                              None, None, None, None, 0, None, None)
+        assert rc == 1 and b"NULL" in L.adp_last_error_string(), name
     lr = (C.c_float * 6)(*([1e-3] * 6))
     for name in ("adp_split_keep_overlapped", "adp_split_append_overlapped"):
         fn = getattr(L, name)

@@ -6,6 +6,7 @@ identical; the new population is compared value by value (children through their
 covariance R diag(s^2) R^T, which is invariant to the sign and order freedom of the
 axes). Gradients are compared with the oracle's complex-step derivative.
 """
+import itertools
 import math
 
 import numpy as np
@@ -224,7 +225,8 @@ def test_overlapped_split_equals_two_call_split():
     """The overlapped plan and compaction (proposals and merges on the library's
     auxiliary stream while the kept rows stream) give, bit for bit, what the
     two-call plan and fused compaction give: statuses, child counts, new size,
-    population and moments. Three capacities: the worst case (kept rows written
+    population and moments. So does the overlapped plan made in two calls, its
+    first part on a side stream beside the candidates' Adam step. Three capacities: the worst case (kept rows written
     against the bound on the new size), exactly the new size (merges remove
     children here, so the bound exceeds the capacity and the kept rows are
     written after the join), and one row less (nothing written)."""
@@ -257,21 +259,33 @@ def test_overlapped_split_equals_two_call_split():
     n = g0.n
     worst = n + k * (n_max + 1)
 
-    def run(overlapped, cap):
+    def run(mode, cap):
         g, m, v = g0.clone(), m0.clone(), v0.clone()
         d_step = torch.full((1,), 3, dtype=torch.int32, device=DEV)
         out = [ops.Gaussians(cap, g.sh_degree, DEV, zero=True) for _ in range(3)]
-        ops.adam_step_rows(g, grad, m, v, cand, d_step, ops.ADAM_LR)
-        if overlapped:
-            plan = ops.split_plan_overlapped(g, cams, regs, cand, count, prm)
+        if mode == "two_call":
+            # the first part on a side stream, beside the candidates' Adam step
+            main, side = torch.cuda.current_stream(), torch.cuda.Stream()
+            side.wait_stream(main)
+            with torch.cuda.stream(side):
+                plan = ops.split_plan_overlapped(g, cams, regs, cand, count, prm,
+                                                 part="statuses")
+            ops.adam_step_rows(g, grad, m, v, cand, d_step, ops.ADAM_LR)
+            main.wait_stream(side)
+            plan = ops.split_plan_overlapped(g, cams, regs, cand, count, prm, part="proposals",
+                                             plan=plan)
         else:
-            plan = ops.split_plan(g, cams, regs, cand, count, prm, sync=False)
+            ops.adam_step_rows(g, grad, m, v, cand, d_step, ops.ADAM_LR)
+            if mode == "overlapped":
+                plan = ops.split_plan_overlapped(g, cams, regs, cand, count, prm)
+            else:
+                plan = ops.split_plan(g, cams, regs, cand, count, prm, sync=False)
         ops.split_apply_adam(g, grad, m, v, plan, regs, cand, noise, d_step, out[0], out[1],
-                             out[2], prm, ops.ADAM_LR, overlapped=overlapped)
+                             out[2], prm, ops.ADAM_LR, overlapped=mode != "plain")
         torch.cuda.synchronize()
         return plan, out, int(d_step.item())
 
-    ref_plan, ref_out, ref_step = run(False, worst)
+    ref_plan, ref_out, ref_step = run("plain", worst)
     n_new = int(ref_plan.d_new_n.item())
     st = np_(ref_plan.status)
     per_parent = np.bincount(rg["parent"], minlength=n)[orc["cand"]]
@@ -281,8 +295,8 @@ def test_overlapped_split_equals_two_call_split():
     def rows(gs, upto):
         return [t[:, :upto] if t.dim() == 3 else t[:upto] for x in gs for t in x.tensors()]
 
-    for cap in (worst, n_new, n_new - 1):
-        plan, out, step = run(True, cap)
+    for mode, cap in itertools.product(("overlapped", "two_call"), (worst, n_new, n_new - 1)):
+        plan, out, step = run(mode, cap)
         assert torch.equal(plan.status, ref_plan.status)
         assert torch.equal(plan.n_children, ref_plan.n_children)
         assert int(plan.d_new_n.item()) == n_new and step == ref_step == 4
