@@ -244,8 +244,13 @@ def run_ours(args, rank, world, local_rank):
     use_graph = not args.no_graph
     timer = StageTimer()
     if use_graph:
+        # two captures of the same step: one with the stage events (replayed after
+        # the timed region for the per-stage times) and the timed one, without them
         stepper.capture(noise, timer)
+        staged_graph = stepper.graph
+        stepper.capture(noise)
         for _ in range(args.warmup):
+            staged_graph.replay()
             stepper.replay()
         torch.cuda.synchronize()
 
@@ -266,20 +271,34 @@ def run_ours(args, rank, world, local_rank):
         flush.random_(0, 255)  # evict L2 between steps (not timed)
         ev0.record(stream)
         if use_graph:
-            out = stepper.replay()  # re-records the captured stage events
+            out = stepper.replay()
         else:
             timer = StageTimer()
             out = stepper.step(noise, timer)
         ev1.record(stream)
         torch.cuda.synchronize()
         step_ms.append(ev0.elapsed_time(ev1))
-        for kname, val in timer.durations().items():  # stages of this step
-            stage_ms[kname] = stage_ms.get(kname, 0.0) + val
+        if not use_graph:
+            for kname, val in timer.durations().items():  # stages of this step
+                stage_ms[kname] = stage_ms.get(kname, 0.0) + val
         last_plan = out[3]
     barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop(t_wall0, time.time())
     stage_steps = args.steps
+    staged_ms = None
+    if use_graph:  # the per-stage times, from the same number of instrumented replays
+        staged = []
+        for _ in range(args.steps):
+            flush.random_(0, 255)
+            ev0.record(stream)
+            staged_graph.replay()  # re-records the captured stage events
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            staged.append(ev0.elapsed_time(ev1))
+            for kname, val in timer.durations().items():
+                stage_ms[kname] = stage_ms.get(kname, 0.0) + val
+        staged_ms = sum(staged) / len(staged) if staged else None
     if not stepper.check_capacity(last_plan):
         raise RuntimeError("instance, region or population capacity exceeded in the timed region")
     new_n = int(last_plan.d_new_n.item())
@@ -452,6 +471,9 @@ def run_ours(args, rank, world, local_rank):
                      "stages": sorted(k for k in sb if k in per_stage)},
         "graph": use_graph,
         "stages_ms": {k: round(v, 4) for k, v in per_stage.items()},
+        # the step time of the instrumented graph the stage times come from (its
+        # stage events are graph nodes between the kernels)
+        "staged_ms_per_step": round(staged_ms, 4) if staged_ms else None,
         "batched_vs_plain": batched,
         "batched_c3": batched_c3,
         "backward_c2": c2,

@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(VIEWS_THREADS) project_views_kernel(ProjectArg
 }
 
 constexpr int PROJ_THREADS = 256;
-constexpr int PROJ_CHUNK = 1024;
+constexpr int PROJ_CHUNK = 512;
 
 // Each CTA takes PROJ_CHUNK Gaussians of one view: a cheap pass culls most of
 // them, the survivors are compacted in shared memory and projected by full
