@@ -447,9 +447,15 @@ constexpr int ERODE_RMAX = 64;
 
 // The ranges of f are filled by the same launch (the call's resets; the erosion
 // reads none of them).
+// Shared memory: the staged (32 + 2r)^2 block and its row-eroded (32 + 2r) x 32
+// block, sized for the call's radius (erode_smem_bytes; 30 KB at the largest).
+__host__ __device__ inline int erode_smem_bytes(int r) {
+  return (ERODE_T + 2 * r) * (ERODE_T + 2 * r) + (ERODE_T + 2 * r) * ERODE_T;
+}
 __global__ void __launch_bounds__(256) erode_kernel(uint8_t* mask, CamSet cs, int r, FillSet f) {
-  __shared__ uint8_t s_in[(ERODE_T + 2 * ERODE_RMAX) * (ERODE_T + 2 * ERODE_RMAX)];
-  __shared__ uint8_t s_row[(ERODE_T + 2 * ERODE_RMAX) * ERODE_T];
+  extern __shared__ uint8_t s_erode[];
+  uint8_t* s_in = s_erode;
+  uint8_t* s_row = s_erode + (ERODE_T + 2 * r) * (ERODE_T + 2 * r);
   fill_ranges_device(f, ((long long)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x,
                      (long long)gridDim.x * gridDim.y * blockDim.x);
   const int v = blockIdx.y;
@@ -1079,7 +1085,8 @@ extern "C" ADP_API int adp_error_regions(adp_error_maps* maps, const int32_t* do
       int t = ((cs.cam[v].width + ERODE_T - 1) / ERODE_T) * ((cs.cam[v].height + ERODE_T - 1) / ERODE_T);
       max_et = t > max_et ? t : max_et;
     }
-    erode_kernel<<<dim3(max_et, n_views), 256, 0, st>>>(maps->mask, cs, prm->r_erode, fill);
+    erode_kernel<<<dim3(max_et, n_views), 256, erode_smem_bytes(prm->r_erode), st>>>(
+        maps->mask, cs, prm->r_erode, fill);
   }
   // candidate flags
   if (n_cand > 0)
