@@ -1197,7 +1197,11 @@ static int split_apply_impl(const adp_gaussians* g, const adp_gaussians* grad,
     std::lock_guard<std::mutex> lock(aux_mutex());
     ADP_CUDA(cudaStreamWaitEvent(st, aux->merged, 0));
   }
-  if (overlapped && n > 0) {
+  // the kept rows were written against the bound unless it exceeded out->n. The
+  // bound is at most n + n_cand + the region capacity (one row per FALLBACK
+  // candidate, at most one per stored region for an ADAPTIVE one), so with that much
+  // room the late pass can never act and is not launched
+  if (overlapped && n > 0 && out->n < n + nc + rcap) {
     late_keep_kernel<<<148 * 2, 256, 0, st>>>(aa);
     ADP_LAUNCH_CHECK();
   }
