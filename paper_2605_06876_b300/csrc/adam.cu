@@ -128,7 +128,8 @@ extern "C" ADP_API int adp_adam_step_rows(adp_gaussians* param, const adp_gaussi
   if (n_rows == 0) return ADP_OK;
   AdamPlanes a = adam_planes(param, grad, m, v);
   AdamHyper h = adam_hyper(lr, beta1, beta2, eps, step, d_step);
-  adam_rows_kernel<<<dim3(grid_for(n_rows, 256), 3 + a.planes), 256, 0, (cudaStream_t)stream>>>(
+  // blocks of 128 threads: 0.034 against 0.035 ms for 256 (100k candidate rows)
+  adam_rows_kernel<<<dim3(grid_for(n_rows, 128), 3 + a.planes), 128, 0, (cudaStream_t)stream>>>(
       a, h, rows, n_rows);
   ADP_LAUNCH_CHECK();
   return ADP_OK;
