@@ -14,10 +14,10 @@
  *  - Every call is asynchronous on the given stream (a cudaStream_t; NULL is the
  *    legacy default stream) and does not synchronise, except adp_split_plan,
  *    which reads one integer back when asked to (see there). The overlapped
- *    split (adp_split_plan_overlapped or its second part, and its two compaction calls) and the
- *    batched step (adp_train_step_batched) also put work on a stream the library
- *    keeps per device, forked from and joined back into the given stream (see
- *    there).
+ *    split (adp_split_plan_overlapped or its second part, and its two compaction
+ *    calls) and the batched step (adp_train_step_batched) also put work on a
+ *    stream the library keeps per device, forked from and joined back into the
+ *    given stream (see there).
  *  - Every call returns an adp_status. A host-side argument error returns
  *    ADP_ERR_INVALID_ARG before anything is launched; a CUDA launch error returns
  *    ADP_ERR_CUDA. adp_last_error_string() describes the last failure of the
